@@ -1,0 +1,112 @@
+"""Pins of the oracle's Huffman stage (the lossless stage of Sec. III-B):
+hand-checked golden codes, Kraft equality, optimality against exhaustive
+search on small alphabets, decode(encode) = identity, length limiting."""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import fields
+import oracle
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden():
+    rows = []
+    with open(os.path.join(GOLD, "huffman_small.txt")) as f:
+        for ln in f:
+            if ln.strip() and not ln.startswith("#"):
+                rows.append([p.strip() for p in ln.split("|")])
+    return rows
+
+
+@pytest.mark.parametrize("row", _golden(), ids=lambda r: r[0])
+def test_golden_codes(row):
+    name, freqs, lens, codes, syms, words = row
+    f = np.array([int(v) for v in freqs.split()], dtype=np.uint64)
+    L = oracle.huffman_lengths(f)
+    assert list(L) == [int(v) for v in lens.split()]
+    C = oracle.canonical_codes(L)
+    for s, want in enumerate(codes.split()):
+        if want == "-":
+            assert L[s] == 0
+            continue
+        assert L[s] == len(want)
+        assert C[s] == int(want, 2)
+    sym = np.array([int(v) for v in syms.split()], dtype=np.uint16)
+    # encode the given symbols with a histogram that reproduces the golden lengths
+    hist_sym = np.repeat(np.arange(f.size), f.astype(np.int64)).astype(np.uint16)
+    allsym = np.concatenate([sym, hist_sym])
+    sec, meta = oracle.huffman_encode(allsym, f.size, chunk=len(sym))
+    # the histogram of allsym differs from f by the golden symbols; only check
+    # when that does not change the lengths
+    L2 = oracle.huffman_lengths(np.bincount(allsym, minlength=f.size).astype(np.uint64))
+    if list(L2) == list(L):
+        off_w = (meta["codebook_bytes"] + 7) // 8 * 8 + (4 * meta["n_chunks"] + 7) // 8 * 8
+        w0 = sec[off_w:off_w + 4].view(np.uint32)[0]
+        assert w0 == int(words, 16)
+
+
+def _kraft(L):
+    L = L[L > 0].astype(np.float64)
+    return np.sum(2.0 ** -L)
+
+
+def _exhaustive_optimum(f):
+    n = len(f)
+    best = None
+    for lens in itertools.product(range(1, n), repeat=n):
+        if sum(2.0 ** -l for l in lens) <= 1.0 + 1e-12:
+            cost = sum(a * b for a, b in zip(f, lens))
+            best = cost if best is None else min(best, cost)
+    return best
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_optimal_vs_exhaustive(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(2, 7))
+    f = rng.integers(1, 60, size=n).astype(np.uint64)
+    L = oracle.huffman_lengths(f)
+    assert abs(_kraft(L) - 1.0) < 1e-12
+    assert int(np.sum(f * L)) == _exhaustive_optimum([int(v) for v in f])
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_prefix_free_and_kraft_large(seed):
+    rng = np.random.default_rng(100 + seed)
+    f = np.zeros(8192, dtype=np.uint64)
+    idx = rng.choice(8192, size=3000, replace=False)
+    f[idx] = rng.geometric(0.001, size=3000).astype(np.uint64)
+    L = oracle.huffman_lengths(f)
+    assert np.all((L > 0) == (f > 0))
+    assert abs(_kraft(L) - 1.0) < 1e-9
+    C = oracle.canonical_codes(L)
+    words = sorted(format(int(C[s]), "0%db" % int(L[s])) for s in np.flatnonzero(L))
+    for a, b in zip(words, words[1:]):
+        assert not b.startswith(a)
+
+
+def test_length_limit_32():
+    # Fibonacci frequencies force a maximally skewed tree (depth n-1)
+    fib = [1, 1]
+    while len(fib) < 45:
+        fib.append(fib[-1] + fib[-2])
+    f = np.array(fib, dtype=np.uint64)
+    L = oracle.huffman_lengths(f)
+    assert L.max() <= 32
+    assert _kraft(L) <= 1.0 + 1e-12
+    # without the limit the depth would be 44
+    assert oracle.huffman_lengths(f[:20]).max() == 19
+
+
+@pytest.mark.parametrize("scale,esc,chunk", [(0.3, 0.0, 2048), (5.0, 0.001, 1000), (300.0, 0.01, 4096), (0.0, 0.0, 64)])
+def test_decode_inverts_encode(scale, esc, chunk):
+    radius = 4096
+    sym = fields.laplace_symbols(50_001, radius, scale, seed=9, escape_rate=esc)
+    sec, meta = oracle.huffman_encode(sym, 2 * radius, chunk)
+    assert meta["n_chunks"] == (sym.size + chunk - 1) // chunk
+    back = oracle.huffman_decode(sec, meta, sym.size, 2 * radius, chunk)
+    np.testing.assert_array_equal(back, sym)
