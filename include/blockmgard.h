@@ -1,0 +1,157 @@
+/*
+ * blockmgard.h — C ABI of the GB300 (sm_103a) BlockMGARD compressor.
+ *
+ * The library implements the data-parallel hot path of BlockMGARD (SC26):
+ *   (a) In-cache Block multilevel decomposition of fixed B^3 blocks held in
+ *       shared memory (Sec. III-A), fused with (c) quantisation (Sec. III-D);
+ *   (b) the hybrid hand-off: M global MGARD levels on the gathered
+ *       block-coarse nodes (Sec. III-B);
+ *   (c) ROI-aware, level-scaled quantisation with per-block tolerances and
+ *       tau_global = min_i tau_i (Sec. II-B error shares, Sec. III-C);
+ *   (d) Huffman coding of the quantised symbols (Sec. III-B lossless stage);
+ * and the inverse of all four.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* are device pointers (cudaMalloc'd or torch-owned) on
+ *     the current CUDA device; h_* are host pointers.  The caller owns every
+ *     buffer it passes.  The library allocates only internal scratch, cached
+ *     per CUDA stream and released by bm_release_workspace().
+ *   - `stream` is a cudaStream_t passed as void* (0 = legacy default stream).
+ *     All device work is ordered on that stream.  Calls that return sizes
+ *     (bm_compress) synchronise the stream before returning.
+ *   - Fields are 3-D, row-major (C order) with shape[2] varying fastest, each
+ *     extent >= 2.  dtype: BM_F32 or BM_F64.
+ *   - Every call returns a bm_status.  On failure a readable message is
+ *     available from bm_last_error_detail() (thread-local); no output buffer
+ *     is guaranteed to hold meaningful data.  Invalid arguments are rejected
+ *     on the host before any device work is issued.
+ *   - The library is not re-entrant on the same stream from several host
+ *     threads at once; distinct streams may be used concurrently.
+ */
+#ifndef BLOCKMGARD_H
+#define BLOCKMGARD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { BM_F32 = 0, BM_F64 = 1 } bm_dtype;
+
+typedef enum {
+  BM_OK = 0,
+  BM_ERR_ARG = 1,          /* invalid argument (shape, tolerance, parameters) */
+  BM_ERR_CUDA = 2,         /* a CUDA runtime call failed                      */
+  BM_ERR_CAPACITY = 3,     /* output buffer smaller than needed               */
+  BM_ERR_CORRUPT = 4,      /* input stream malformed or truncated             */
+  BM_ERR_UNSUPPORTED = 5,  /* valid but not supported by this build           */
+  BM_ERR_OOM = 6           /* scratch allocation failed                       */
+} bm_status;
+
+/* Tolerance mode: BM_ABS = tol is absolute; BM_REL = tol (and every ROI entry)
+ * is relative to max|u| (the paper's L-inf relative bound, Sec. IV-A). */
+typedef enum { BM_ABS = 0, BM_REL = 1 } bm_tol_mode;
+
+/* Hierarchy parameters (Sec. III-A block size, Sec. III-B L/M; the paper's L
+ * is incache_levels here).  Zero-initialised fields take the defaults. */
+typedef struct {
+  int block_nodes;     /* B: nodes per block edge; this build supports 9, 17 (default 17) */
+  int incache_levels;  /* K >= 1: levels done while the block is resident (default 2)    */
+  int global_levels;   /* M >= 0: MGARD levels on the gathered coarse grid (default 2;
+                          -1 selects 0)                                                  */
+  int chunk_symbols;   /* Huffman chunk length in symbols, multiple of 32, 64..8192
+                          (default 2048)                                                 */
+  int dict_radius;     /* quantisation codes with |code| < radius become symbols
+                          code + radius; others are outliers.  16..4096 (default 4096)   */
+} bm_params;
+
+/* Upper bound on the stream size for a field of this shape and dtype: the raw
+ * fallback (256-byte header + the field) always fits.  0 on invalid input. */
+size_t bm_compress_bound(int ndim, const int64_t* shape, bm_dtype dtype);
+
+/* Compress one field (Sec. III, the whole pipeline of Fig. 1).
+ *   d_field     device pointer to the field, shape[0]*shape[1]*shape[2] values
+ *               of `dtype`, row-major.
+ *   tol         error tolerance (> 0, finite); absolute or relative (tol_mode).
+ *   h_roi_tol   optional host array with one tolerance per block of B^3 nodes,
+ *               row-major over the block grid ceil(shape[d]/B); same mode as
+ *               tol.  Block i's tolerance is min(tol, h_roi_tol[i]) (Sec. III-C
+ *               block-wise tolerance assignment).  NULL = uniform.  At most 255
+ *               distinct values.
+ *   d_out       device buffer for the stream; out_capacity bytes (use
+ *               bm_compress_bound()).
+ *   out_bytes   receives the stream length (host pointer).
+ * Guarantee: decompression reproduces every node of block i within its
+ * tolerance (L-inf), including floating-point round-off, or the stream is a
+ * raw copy of the field (when the field holds non-finite values, the tolerance
+ * is too close to round-off, or coding would not shrink it). */
+bm_status bm_compress(const void* d_field, int ndim, const int64_t* shape, bm_dtype dtype, double tol,
+                      bm_tol_mode tol_mode, const double* h_roi_tol, const bm_params* params, void* d_out,
+                      size_t out_capacity, size_t* out_bytes, void* stream);
+
+/* Header of a stream (the first 256 bytes, host or device memory: set
+ * `in_is_device`).  Any output pointer may be NULL. */
+bm_status bm_stream_info(const void* in, size_t in_bytes, int in_is_device, int* ndim, int64_t shape[3],
+                         bm_dtype* dtype, size_t* n_coeffs);
+
+/* Decompress a stream produced by bm_compress into d_field (device, sized by
+ * bm_stream_info).  Inverse of every stage (Sec. III; Huffman decode,
+ * dequantisation, global then In-cache Block recomposition).  Malformed
+ * streams give BM_ERR_CORRUPT; device-side decoding checks every read against
+ * the stream bounds and reports through a status word rather than trapping. */
+bm_status bm_decompress(const void* d_in, size_t in_bytes, void* d_field, void* stream);
+
+/* Multilevel decomposition only (Sec. II-B / III-A / III-B), no quantisation:
+ * writes the n_coeffs full-precision coefficients to d_coeffs (same dtype as
+ * the field) in stream order: blocks row-major; inside a block levels finest
+ * to coarsest, each level's non-coarse nodes row-major; then the global
+ * levels finest to coarsest (row-major); then the coarsest grid (row-major).
+ * n_coeffs comes from bm_coeff_count(). */
+bm_status bm_decompose(const void* d_field, int ndim, const int64_t* shape, bm_dtype dtype,
+                       const bm_params* params, void* d_coeffs, void* stream);
+
+/* Inverse of bm_decompose (recomposition, Sec. II-B): coefficients in stream
+ * order to the field. */
+bm_status bm_recompose(const void* d_coeffs, int ndim, const int64_t* shape, bm_dtype dtype,
+                       const bm_params* params, void* d_field, void* stream);
+
+/* Number of coefficients (= quantised symbols) for a shape and parameters. */
+bm_status bm_coeff_count(int ndim, const int64_t* shape, const bm_params* params, size_t* n_coeffs);
+
+/* Integer quantisation codes of a (non-raw) stream, decoded on the device:
+ * d_codes receives n_coeffs int32 values in stream order (outliers applied). */
+bm_status bm_stream_codes(const void* d_in, size_t in_bytes, int32_t* d_codes, void* stream);
+
+/* Stand-alone Huffman stage (Sec. III-B lossless stage; cuSZ-style chunked
+ * coding, "deflate" = concatenation of chunk codes): encodes n uint16 symbols
+ * (each < dict_size, dict_size <= 8192) into the section layout used inside
+ * streams: codebook runs | u32 chunk word counts | u32 code words, each part
+ * padded to 8 bytes.  sizes_out[0..4] = codebook bytes, runs, chunks, words,
+ * total bytes.  Synchronises the stream. */
+bm_status bm_huffman_encode(const uint16_t* d_symbols, uint64_t n, int dict_size, int chunk_symbols,
+                            void* d_out, size_t out_capacity, uint64_t sizes_out[5], void* stream);
+
+/* Inverse of bm_huffman_encode: sizes as returned by it; writes n symbols. */
+bm_status bm_huffman_decode(const void* d_section, const uint64_t sizes[5], uint64_t n, int dict_size,
+                            int chunk_symbols, uint16_t* d_symbols, void* stream);
+
+/* Free the scratch cached for `stream` (NULL/0 = every stream). */
+void bm_release_workspace(void* stream);
+
+/* Instrumentation: when enabled, every stage records CUDA events on the
+ * call's stream; bm_stage_times() returns the last call's per-stage
+ * milliseconds (names[i] static strings), up to max_stages entries. */
+void bm_set_timing(int enabled);
+int bm_stage_times(const char** names, float* ms, int max_stages);
+/* Count of kernels this library has launched since load (monotonic). */
+uint64_t bm_launch_count(void);
+
+const char* bm_error_string(bm_status s);
+const char* bm_last_error_detail(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BLOCKMGARD_H */

@@ -168,7 +168,7 @@ def canonical_codes(lengths):
 
 
 def huffman_encode(sym, dict_size, chunk):
-    """Huffman section bytes (codebook runs | chunk word counts | words) and
+    """Huffman section bytes (chunk word counts | codebook runs | words) and
     its sizes dict."""
     s = np.ascontiguousarray(np.asarray(sym, dtype=np.uint16))
     cap = 64 + 8 * s.size + 8 * dict_size + 8 * (s.size // max(chunk, 1) + 2)
@@ -184,12 +184,13 @@ def huffman_encode(sym, dict_size, chunk):
 def huffman_decode(section, meta, n, dict_size, chunk):
     sec = np.ascontiguousarray(np.asarray(section, dtype=np.uint8))
     cb = meta["codebook_bytes"]
-    off_ch = (cb + 7) // 8 * 8
-    off_w = off_ch + (4 * meta["n_chunks"] + 7) // 8 * 8
-    chunks = np.ascontiguousarray(sec[off_ch:off_ch + 4 * meta["n_chunks"]].view(np.uint32))
+    off_cb = (4 * meta["n_chunks"] + 7) // 8 * 8
+    off_w = off_cb + (cb + 7) // 8 * 8
+    chunks = np.ascontiguousarray(sec[:4 * meta["n_chunks"]].view(np.uint32))
     words = np.ascontiguousarray(sec[off_w:off_w + 4 * meta["n_words"]].view(np.uint32))
+    cbk = np.ascontiguousarray(sec[off_cb:off_cb + cb])
     out = np.zeros(n, dtype=np.uint16)
-    _check(lib().or_huffman_decode(_ptr(sec, ctypes.c_uint8), cb, meta["n_runs"], dict_size,
+    _check(lib().or_huffman_decode(_ptr(cbk, ctypes.c_uint8), cb, meta["n_runs"], dict_size,
                                    _ptr(chunks, ctypes.c_uint32), _ptr(words, ctypes.c_uint32), meta["n_words"], n,
                                    chunk, _ptr(out, ctypes.c_uint16)))
     return out

@@ -761,13 +761,13 @@ std::vector<uint8_t> compress(const double* u, const int64_t* shape, bool f64, d
     if (!std::isfinite(u[i])) finite = false;
     max_abs = std::max(max_abs, std::fabs(u[i]));
   }
-  // Per-block absolute tolerances tau_i = min(tol, roi_i) (times max|u| in REL mode),
-  // deduplicated into tiers in ascending order.
+  // Per-block tolerances min(tol, roi_i), deduplicated into ascending tiers;
+  // a tier's absolute tolerance is its value times max|u| in REL mode.
   std::vector<double> btau((size_t)p.nblocks);
   for (int64_t b = 0; b < p.nblocks; ++b) {
     double t = tol;
     if (roi) t = std::min(t, roi[b]);
-    btau[(size_t)b] = rel ? t * max_abs : t;
+    btau[(size_t)b] = t;
   }
   std::vector<double> tiers = btau;
   std::sort(tiers.begin(), tiers.end());
@@ -776,6 +776,8 @@ std::vector<uint8_t> compress(const double* u, const int64_t* shape, bool f64, d
   std::vector<uint8_t> block_tier((size_t)p.nblocks);
   for (int64_t b = 0; b < p.nblocks; ++b)
     block_tier[(size_t)b] = (uint8_t)(std::lower_bound(tiers.begin(), tiers.end(), btau[(size_t)b]) - tiers.begin());
+  if (rel)
+    for (double& t : tiers) t = t * max_abs;
   const int ntiers = (int)tiers.size();
   Budget bud = make_budget(p, tiers, max_abs, f64);
   bool raw = bud.raw || !finite;
@@ -1071,16 +1073,17 @@ int or_canonical_codes(const uint8_t* len, int nsym, uint32_t* code_out) {
   return 0;
 }
 
-// Huffman section of the stream for symbols sym[0..n): codebook runs, chunk
-// word counts, bitstream, concatenated in that order (each padded to 8 bytes).
+// Huffman section for symbols sym[0..n): chunk word counts, codebook runs,
+// bitstream, concatenated in that order (each padded to 8 bytes), the order
+// these parts take inside a stream.
 // sizes[0..3] = codebook bytes, n_runs, n_chunks, n_words.
 int or_huffman_encode(const uint16_t* sym, uint64_t n, int dict, int chunk, uint8_t* out, uint64_t cap,
                       uint64_t* sizes) {
   HuffOut h = huffman_encode(sym, n, dict, chunk);
   Writer w;
-  w.b.insert(w.b.end(), h.codebook.begin(), h.codebook.end());
-  w.pad8();
   for (uint32_t c : h.chunk_words) w.put<uint32_t>(c);
+  w.pad8();
+  w.b.insert(w.b.end(), h.codebook.begin(), h.codebook.end());
   w.pad8();
   for (uint32_t x : h.words) w.put<uint32_t>(x);
   w.pad8();

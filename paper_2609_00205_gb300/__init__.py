@@ -1,0 +1,262 @@
+"""BlockMGARD on GB300: Python binding of the C-ABI library ``libbm.so``.
+
+Only argument marshalling lives here: every step of compression and
+decompression runs in the library's CUDA kernels.  PyTorch supplies device
+memory and streams.  There is no CPU fallback: if the library is missing or
+cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import _build
+
+__all__ = [
+    "BM_F32", "BM_F64", "BlockMGARDError", "load", "compress", "decompress", "decompose", "recompose",
+    "coeff_count", "stream_info", "stream_codes", "huffman_encode", "huffman_decode", "compress_bound",
+    "set_timing", "stage_times", "launch_count", "release_workspace", "library_path",
+]
+
+BM_F32, BM_F64 = 0, 1
+BM_ABS, BM_REL = 0, 1
+_STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "output capacity too small", 4: "corrupt stream",
+           5: "unsupported", 6: "out of device memory"}
+
+
+class BlockMGARDError(RuntimeError):
+    def __init__(self, status: int, detail: str):
+        super().__init__("%s: %s" % (_STATUS.get(status, "status %d" % status), detail))
+        self.status = status
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("block_nodes", ctypes.c_int), ("incache_levels", ctypes.c_int), ("global_levels", ctypes.c_int),
+                ("chunk_symbols", ctypes.c_int), ("dict_radius", ctypes.c_int)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libbm.so (built by ``__graft_entry__.build()`` / ``_build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("libbm.so is not built (%s); run __graft_entry__.build()" % _build.LIB)
+    L = ctypes.CDLL(_build.LIB)
+    P = ctypes.POINTER
+    vp, sz, i64, u64 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int64, ctypes.c_uint64
+    L.bm_compress_bound.argtypes = [ctypes.c_int, P(i64), ctypes.c_int]
+    L.bm_compress_bound.restype = sz
+    L.bm_compress.argtypes = [vp, ctypes.c_int, P(i64), ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                              P(ctypes.c_double), P(_Params), vp, sz, P(sz), vp]
+    L.bm_stream_info.argtypes = [vp, sz, ctypes.c_int, P(ctypes.c_int), P(i64), P(ctypes.c_int), P(sz)]
+    L.bm_decompress.argtypes = [vp, sz, vp, vp]
+    L.bm_decompose.argtypes = [vp, ctypes.c_int, P(i64), ctypes.c_int, P(_Params), vp, vp]
+    L.bm_recompose.argtypes = [vp, ctypes.c_int, P(i64), ctypes.c_int, P(_Params), vp, vp]
+    L.bm_coeff_count.argtypes = [ctypes.c_int, P(i64), P(_Params), P(sz)]
+    L.bm_stream_codes.argtypes = [vp, sz, vp, vp]
+    L.bm_huffman_encode.argtypes = [vp, u64, ctypes.c_int, ctypes.c_int, vp, sz, P(u64), vp]
+    L.bm_huffman_decode.argtypes = [vp, P(u64), u64, ctypes.c_int, ctypes.c_int, vp, vp]
+    L.bm_release_workspace.argtypes = [vp]
+    L.bm_release_workspace.restype = None
+    L.bm_set_timing.argtypes = [ctypes.c_int]
+    L.bm_set_timing.restype = None
+    L.bm_stage_times.argtypes = [P(ctypes.c_char_p), P(ctypes.c_float), ctypes.c_int]
+    L.bm_launch_count.restype = u64
+    L.bm_error_string.restype = ctypes.c_char_p
+    L.bm_last_error_detail.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != 0:
+        raise BlockMGARDError(status, load().bm_last_error_detail().decode())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _shape(shape):
+    return (ctypes.c_int64 * 3)(*[int(v) for v in shape])
+
+
+def _dtype(t):
+    if t == torch.float32:
+        return BM_F32
+    if t == torch.float64:
+        return BM_F64
+    raise TypeError("fields must be float32 or float64")
+
+
+def _params(block=17, levels=2, global_levels=2, chunk=2048, radius=4096):
+    return _Params(int(block), int(levels), int(global_levels) if global_levels != 0 else -1, int(chunk), int(radius))
+
+
+def _dev_check(t):
+    if not t.is_cuda:
+        raise ValueError("tensor must live on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+
+
+def compress_bound(shape, dtype=torch.float32) -> int:
+    return int(load().bm_compress_bound(3, _shape(shape), _dtype(dtype)))
+
+
+def compress(field: torch.Tensor, tol: float, mode: str = "rel", roi=None, block=17, levels=2, global_levels=2,
+             chunk=2048, radius=4096, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Compress a 3-D float32/float64 CUDA tensor; returns the stream as a
+    uint8 CUDA tensor (a view of ``out`` when given).  ``roi``: optional
+    per-block tolerances (same mode as ``tol``), row-major over the block grid."""
+    _dev_check(field)
+    if field.dim() != 3:
+        raise ValueError("fields must be 3-D")
+    L = load()
+    cap = compress_bound(field.shape, field.dtype)
+    if out is None:
+        out = torch.empty(cap, dtype=torch.uint8, device=field.device)
+    elif out.numel() < cap or out.dtype != torch.uint8 or not out.is_cuda:
+        raise ValueError("out must be a CUDA uint8 tensor of at least compress_bound() bytes")
+    roi_ptr = None
+    if roi is not None:
+        import numpy as np
+        r = np.ascontiguousarray(np.asarray(roi, dtype=np.float64).ravel())
+        roi_ptr = r.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    nbytes = ctypes.c_size_t(0)
+    p = _params(block, levels, global_levels, chunk, radius)
+    with torch.cuda.device(field.device):
+        _check(L.bm_compress(ctypes.c_void_p(field.data_ptr()), 3, _shape(field.shape), _dtype(field.dtype),
+                             float(tol), BM_REL if mode == "rel" else BM_ABS, roi_ptr, ctypes.byref(p),
+                             ctypes.c_void_p(out.data_ptr()), ctypes.c_size_t(out.numel()), ctypes.byref(nbytes),
+                             _stream(stream)))
+    return out[: nbytes.value]
+
+
+def stream_info(buf: torch.Tensor) -> dict:
+    L = load()
+    nd = ctypes.c_int(0)
+    shp = (ctypes.c_int64 * 3)()
+    dt = ctypes.c_int(0)
+    nc = ctypes.c_size_t(0)
+    if buf.is_cuda:
+        with torch.cuda.device(buf.device):
+            _check(L.bm_stream_info(ctypes.c_void_p(buf.data_ptr()), buf.numel(), 1, ctypes.byref(nd), shp,
+                                    ctypes.byref(dt), ctypes.byref(nc)))
+    else:
+        b = buf.contiguous()
+        _check(L.bm_stream_info(ctypes.c_void_p(b.data_ptr()), b.numel(), 0, ctypes.byref(nd), shp, ctypes.byref(dt),
+                                ctypes.byref(nc)))
+    return {"shape": tuple(shp), "dtype": torch.float64 if dt.value == BM_F64 else torch.float32,
+            "n_coeffs": nc.value}
+
+
+def decompress(buf: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    _dev_check(buf)
+    L = load()
+    info = stream_info(buf)
+    if out is None:
+        out = torch.empty(info["shape"], dtype=info["dtype"], device=buf.device)
+    with torch.cuda.device(buf.device):
+        _check(L.bm_decompress(ctypes.c_void_p(buf.data_ptr()), buf.numel(), ctypes.c_void_p(out.data_ptr()),
+                               _stream(stream)))
+    return out
+
+
+def coeff_count(shape, block=17, levels=2, global_levels=2) -> int:
+    n = ctypes.c_size_t(0)
+    p = _params(block, levels, global_levels)
+    _check(load().bm_coeff_count(3, _shape(shape), ctypes.byref(p), ctypes.byref(n)))
+    return n.value
+
+
+def decompose(field: torch.Tensor, block=17, levels=2, global_levels=2, stream=None) -> torch.Tensor:
+    """Full-precision multilevel coefficients in stream order."""
+    _dev_check(field)
+    n = coeff_count(field.shape, block, levels, global_levels)
+    out = torch.empty(n, dtype=field.dtype, device=field.device)
+    p = _params(block, levels, global_levels)
+    with torch.cuda.device(field.device):
+        _check(load().bm_decompose(ctypes.c_void_p(field.data_ptr()), 3, _shape(field.shape), _dtype(field.dtype),
+                                   ctypes.byref(p), ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+def recompose(coeffs: torch.Tensor, shape, block=17, levels=2, global_levels=2, stream=None) -> torch.Tensor:
+    _dev_check(coeffs)
+    out = torch.empty(tuple(shape), dtype=coeffs.dtype, device=coeffs.device)
+    p = _params(block, levels, global_levels)
+    with torch.cuda.device(coeffs.device):
+        _check(load().bm_recompose(ctypes.c_void_p(coeffs.data_ptr()), 3, _shape(shape), _dtype(coeffs.dtype),
+                                   ctypes.byref(p), ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+def stream_codes(buf: torch.Tensor, stream=None) -> torch.Tensor:
+    _dev_check(buf)
+    info = stream_info(buf)
+    out = torch.empty(info["n_coeffs"], dtype=torch.int32, device=buf.device)
+    with torch.cuda.device(buf.device):
+        _check(load().bm_stream_codes(ctypes.c_void_p(buf.data_ptr()), buf.numel(), ctypes.c_void_p(out.data_ptr()),
+                                      _stream(stream)))
+    return out
+
+
+def huffman_encode(symbols: torch.Tensor, dict_size: int, chunk: int = 2048, stream=None):
+    """Huffman section of int16/uint16 symbols; returns (uint8 tensor, sizes)."""
+    _dev_check(symbols)
+    if symbols.element_size() != 2:
+        raise TypeError("symbols must be a 16-bit tensor")
+    n = symbols.numel()
+    nch = (n + chunk - 1) // chunk
+    cap = 64 + 8 * nch + 2 * dict_size + 16 * 1024 + 4 * n + 8 * nch
+    out = torch.empty(cap, dtype=torch.uint8, device=symbols.device)
+    sizes = (ctypes.c_uint64 * 5)()
+    with torch.cuda.device(symbols.device):
+        _check(load().bm_huffman_encode(ctypes.c_void_p(symbols.data_ptr()), n, int(dict_size), int(chunk),
+                                        ctypes.c_void_p(out.data_ptr()), cap, sizes, _stream(stream)))
+    s = [int(v) for v in sizes]
+    meta = {"codebook_bytes": s[0], "n_runs": s[1], "n_chunks": s[2], "n_words": s[3], "bytes": s[4]}
+    return out[: s[4]], meta
+
+
+def huffman_decode(section: torch.Tensor, meta: dict, n: int, dict_size: int, chunk: int = 2048, stream=None):
+    _dev_check(section)
+    out = torch.empty(n, dtype=torch.int16, device=section.device)
+    sizes = (ctypes.c_uint64 * 5)(meta["codebook_bytes"], meta["n_runs"], meta["n_chunks"], meta["n_words"],
+                                  meta["bytes"])
+    with torch.cuda.device(section.device):
+        _check(load().bm_huffman_decode(ctypes.c_void_p(section.data_ptr()), sizes, n, int(dict_size), int(chunk),
+                                        ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+def set_timing(enabled: bool):
+    load().bm_set_timing(1 if enabled else 0)
+
+
+def stage_times() -> list:
+    L = load()
+    names = (ctypes.c_char_p * 64)()
+    ms = (ctypes.c_float * 64)()
+    n = L.bm_stage_times(names, ms, 64)
+    return [(names[i].decode(), float(ms[i])) for i in range(n)]
+
+
+def launch_count() -> int:
+    return int(load().bm_launch_count())
+
+
+def release_workspace(stream=None):
+    load().bm_release_workspace(None if stream is None else ctypes.c_void_p(stream.cuda_stream))

@@ -1,0 +1,1338 @@
+// C ABI of the BlockMGARD GPU library: argument checks, plans, scratch,
+// stream layout and the order of the kernels of each entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/blockmgard.h"
+#include "bm_global.cuh"
+#include "bm_huffman.cuh"
+#include "bm_internal.h"
+#include "bm_plan.h"
+
+namespace bm {
+namespace {
+
+// ---------------------------------------------------------------------------
+// Errors, counters, timing
+// ---------------------------------------------------------------------------
+thread_local std::string g_detail;
+std::atomic<uint64_t> g_launches{0};
+std::atomic<int> g_timing{0};
+
+struct StageTimer {
+  struct Rec { const char* name; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  std::vector<std::pair<const char*, float>> last;
+  cudaStream_t s = nullptr;
+  bool on = false;
+  void begin(cudaStream_t st) {
+    clear();
+    s = st;
+    on = g_timing.load() != 0;
+  }
+  void clear() {
+    for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    recs.clear();
+  }
+  int open(const char* name) {
+    if (!on) return -1;
+    Rec r{name, nullptr, nullptr};
+    cudaEventCreate(&r.a);
+    cudaEventCreate(&r.b);
+    cudaEventRecord(r.a, s);
+    recs.push_back(r);
+    return (int)recs.size() - 1;
+  }
+  void close(int i) {
+    if (i >= 0) cudaEventRecord(recs[i].b, s);
+  }
+  void collect() {
+    if (!on) return;
+    last.clear();
+    for (auto& r : recs) {
+      float ms = 0.f;
+      cudaEventSynchronize(r.b);
+      cudaEventElapsedTime(&ms, r.a, r.b);
+      last.push_back({r.name, ms});
+    }
+    clear();
+  }
+};
+std::mutex g_timer_mu;
+StageTimer g_timer;
+
+struct Stage {
+  int i;
+  explicit Stage(const char* n) : i(g_timer.open(n)) {}
+  ~Stage() { g_timer.close(i); }
+};
+
+bm_status fail(bm_status s, const std::string& msg) {
+  g_detail = msg;
+  return s;
+}
+
+#define BM_CUDA(call)                                                                       \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) return fail(BM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define BM_LAUNCHED() g_launches.fetch_add(1)
+
+int num_sms() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  static std::mutex mu;
+  static std::map<int, int> cache;
+  std::lock_guard<std::mutex> g(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  cache[dev] = n > 0 ? n : 1;
+  return cache[dev];
+}
+
+// ---------------------------------------------------------------------------
+// Scratch: one grow-only device buffer (+ pinned host buffer) per stream
+// ---------------------------------------------------------------------------
+struct Workspace {
+  void* d = nullptr;
+  size_t dbytes = 0;
+  void* h = nullptr;
+  size_t hbytes = 0;
+  int dev = -1;
+};
+std::mutex g_ws_mu;
+std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
+
+bm_status get_ws(cudaStream_t s, size_t dbytes, size_t hbytes, Workspace** out) {
+  int dev = 0;
+  BM_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> g(g_ws_mu);
+  Workspace& w = g_ws[{dev, s}];
+  w.dev = dev;
+  if (w.dbytes < dbytes) {
+    if (w.d) { cudaStreamSynchronize(s); cudaFree(w.d); w.d = nullptr; w.dbytes = 0; }
+    size_t want = dbytes + dbytes / 8 + (1 << 20);
+    if (cudaMalloc(&w.d, want) != cudaSuccess) {
+      cudaGetLastError();
+      w.d = nullptr;
+      return fail(BM_ERR_OOM, "cudaMalloc of " + std::to_string(want) + " scratch bytes failed");
+    }
+    w.dbytes = want;
+  }
+  if (w.hbytes < hbytes) {
+    if (w.h) { cudaStreamSynchronize(s); cudaFreeHost(w.h); w.h = nullptr; w.hbytes = 0; }
+    size_t want = hbytes + (1 << 16);
+    if (cudaMallocHost(&w.h, want) != cudaSuccess) {
+      cudaGetLastError();
+      w.h = nullptr;
+      return fail(BM_ERR_OOM, "pinned host scratch allocation failed");
+    }
+    w.hbytes = want;
+  }
+  *out = &w;
+  return BM_OK;
+}
+
+// Sequential sub-allocation of a scratch buffer, 256-byte aligned.
+struct Carver {
+  size_t off = 0;
+  unsigned char* base = nullptr;
+  template <typename X>
+  X* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    X* p = reinterpret_cast<X*>(base ? base + off : nullptr);
+    off += count * sizeof(X);
+    return p;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Plans (host tables + device copies of the global-level tables)
+// ---------------------------------------------------------------------------
+struct PlanDev {
+  PlanHost h;
+  void* dtab[2] = {nullptr, nullptr};  // per dtype
+  int dev[2] = {-1, -1};
+  std::vector<GLevel<float>> gf;
+  std::vector<GLevel<double>> gd;
+};
+std::mutex g_plan_mu;
+std::map<std::tuple<int64_t, int64_t, int64_t, int, int, int>, std::unique_ptr<PlanDev>> g_plans;
+
+template <typename T>
+std::vector<GLevel<T>>& glevels(PlanDev& p);
+template <>
+std::vector<GLevel<float>>& glevels<float>(PlanDev& p) { return p.gf; }
+template <>
+std::vector<GLevel<double>>& glevels<double>(PlanDev& p) { return p.gd; }
+
+template <typename T>
+bm_status upload_tables(PlanDev& P) {
+  const int di = sizeof(T) == 8 ? 1 : 0;
+  int dev = 0;
+  BM_CUDA(cudaGetDevice(&dev));
+  if (P.dtab[di] && P.dev[di] == dev) return BM_OK;
+  // host image: per level per dim the arrays in a fixed order
+  std::vector<unsigned char> img;
+  auto put = [&](const void* src, size_t bytes) {
+    size_t off = (img.size() + 15) & ~size_t(15);
+    img.resize(off + bytes);
+    if (bytes) std::memcpy(img.data() + off, src, bytes);
+    return off;
+  };
+  struct Offs { size_t cidx, jlo, jhi, wl, wr, cb, isc, f0, band, tm, tib, tsup; };
+  std::vector<Offs> offs;
+  for (auto& L3 : P.h.glev)
+    for (auto& D : L3) {
+      auto cvt = [](const std::vector<double>& v) {
+        std::vector<T> o(v.size());
+        for (size_t i = 0; i < v.size(); ++i) o[i] = (T)v[i];
+        return o;
+      };
+      std::vector<T> wl = cvt(D.wl), wr = cvt(D.wr), band = cvt(D.band), tm = cvt(D.tm), tib = cvt(D.tib),
+                     tsup = cvt(D.tsup);
+      Offs o;
+      o.cidx = put(D.cidx.data(), D.cidx.size() * 4);
+      o.jlo = put(D.jlo.data(), D.jlo.size() * 4);
+      o.jhi = put(D.jhi.data(), D.jhi.size() * 4);
+      o.wl = put(wl.data(), wl.size() * sizeof(T));
+      o.wr = put(wr.data(), wr.size() * sizeof(T));
+      o.cb = put(D.cb.data(), D.cb.size() * 4);
+      o.isc = put(D.isc.data(), D.isc.size());
+      o.f0 = put(D.f0.data(), D.f0.size() * 4);
+      o.band = put(band.data(), band.size() * sizeof(T));
+      o.tm = put(tm.data(), tm.size() * sizeof(T));
+      o.tib = put(tib.data(), tib.size() * sizeof(T));
+      o.tsup = put(tsup.data(), tsup.size() * sizeof(T));
+      offs.push_back(o);
+    }
+  if (P.dtab[di]) { cudaFree(P.dtab[di]); P.dtab[di] = nullptr; }
+  if (!img.empty()) {
+    BM_CUDA(cudaMalloc(&P.dtab[di], img.size()));
+    BM_CUDA(cudaMemcpy(P.dtab[di], img.data(), img.size(), cudaMemcpyHostToDevice));
+  }
+  P.dev[di] = dev;
+  auto& G = glevels<T>(P);
+  G.clear();
+  const unsigned char* base = reinterpret_cast<const unsigned char*>(P.dtab[di]);
+  for (int l = 0; l < P.h.M; ++l) {
+    GLevel<T> L;
+    for (int d = 0; d < 3; ++d) {
+      const Offs& o = offs[l * 3 + d];
+      const Dim1DHost& D = P.h.glev[l][d];
+      GDim<T>& g = L.d[d];
+      g.n = D.n; g.c = D.c;
+      g.cidx = reinterpret_cast<const int*>(base + o.cidx);
+      g.jlo = reinterpret_cast<const int*>(base + o.jlo);
+      g.jhi = reinterpret_cast<const int*>(base + o.jhi);
+      g.wl = reinterpret_cast<const T*>(base + o.wl);
+      g.wr = reinterpret_cast<const T*>(base + o.wr);
+      g.cb = reinterpret_cast<const int*>(base + o.cb);
+      g.isc = reinterpret_cast<const uint8_t*>(base + o.isc);
+      g.f0 = reinterpret_cast<const int*>(base + o.f0);
+      g.band = reinterpret_cast<const T*>(base + o.band);
+      g.tm = reinterpret_cast<const T*>(base + o.tm);
+      g.tib = reinterpret_cast<const T*>(base + o.tib);
+      g.tsup = reinterpret_cast<const T*>(base + o.tsup);
+    }
+    L.sym_off = P.h.sym_off[l];
+    G.push_back(L);
+  }
+  return BM_OK;
+}
+
+bm_status get_plan(const int64_t* shape, int B, int K, int M, PlanDev** out) {
+  std::lock_guard<std::mutex> g(g_plan_mu);
+  auto key = std::make_tuple(shape[0], shape[1], shape[2], B, K, M);
+  auto it = g_plans.find(key);
+  if (it == g_plans.end()) {
+    auto p = std::make_unique<PlanDev>();
+    std::string err = make_plan(shape, B, K, M, p->h);
+    if (!err.empty()) return fail(BM_ERR_ARG, err);
+    it = g_plans.emplace(key, std::move(p)).first;
+  }
+  *out = it->second.get();
+  return BM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Parameters and shapes
+// ---------------------------------------------------------------------------
+struct Params { int B, K, M, chunk, radius; };
+
+bm_status check_params(const bm_params* p, Params& o) {
+  o.B = (p && p->block_nodes) ? p->block_nodes : 17;
+  o.K = (p && p->incache_levels) ? p->incache_levels : 2;
+  o.M = (p && p->global_levels) ? p->global_levels : 2;
+  if (p && p->global_levels < 0) o.M = 0;
+  o.chunk = (p && p->chunk_symbols) ? p->chunk_symbols : 2048;
+  o.radius = (p && p->dict_radius) ? p->dict_radius : 4096;
+  if (o.B != 9 && o.B != 17) return fail(BM_ERR_UNSUPPORTED, "block_nodes must be 9 or 17 in this build");
+  const int kmax = o.B == 9 ? 3 : 4;
+  if (o.K < 1 || o.K > kmax) return fail(BM_ERR_ARG, "incache_levels out of range for this block size");
+  if (o.M > 16) return fail(BM_ERR_ARG, "global_levels too large");
+  if (o.chunk < 64 || o.chunk > 8192 || o.chunk % 32) return fail(BM_ERR_ARG, "chunk_symbols must be a multiple of 32 in [64, 8192]");
+  if (o.radius < 16 || o.radius > kMaxDict / 2) return fail(BM_ERR_ARG, "dict_radius must be in [16, 4096]");
+  return BM_OK;
+}
+
+bm_status check_shape(int ndim, const int64_t* shape) {
+  if (ndim != 3) return fail(ndim >= 1 && ndim <= 3 ? BM_ERR_UNSUPPORTED : BM_ERR_ARG, "only 3-D fields are supported");
+  if (!shape) return fail(BM_ERR_ARG, "shape is NULL");
+  for (int d = 0; d < 3; ++d)
+    if (shape[d] < 2 || shape[d] > (int64_t(1) << 31)) return fail(BM_ERR_ARG, "every extent must be in [2, 2^31]");
+  return BM_OK;
+}
+
+int64_t nel3(const int64_t* s) { return s[0] * s[1] * s[2]; }
+
+// Sizes of the global-level scratch arrays (elements): U[l] per level, D, W1, W2.
+struct GSizes {
+  std::vector<int64_t> U;
+  int64_t D = 0, W1 = 0, W2 = 0;
+};
+GSizes gsizes(const PlanHost& h) {
+  GSizes g;
+  for (int l = 0; l <= h.M; ++l) g.U.push_back(h.lshape[3 * l] * h.lshape[3 * l + 1] * h.lshape[3 * l + 2]);
+  g.D = g.U[0];
+  for (int l = 0; l < h.M; ++l) {
+    const int64_t n0 = h.lshape[3 * l], n1 = h.lshape[3 * l + 1];
+    const int64_t c0 = h.lshape[3 * l + 3], c1 = h.lshape[3 * l + 4], c2 = h.lshape[3 * l + 5];
+    g.W1 = std::max(g.W1, n0 * n1 * c2);
+    g.W2 = std::max(g.W2, std::max(n0 * c1 * c2, c0 * c1 * c2));
+  }
+  return g;
+}
+
+int grid_for(int64_t work, int threads, int per_sm = 8) {
+  int64_t g = (work + threads - 1) / threads;
+  const int64_t cap = (int64_t)num_sms() * per_sm;
+  if (g > cap) g = cap;
+  return (int)std::max<int64_t>(g, 1);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Small kernels of the API layer
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void maxabs_kernel(const T* __restrict__ u, int64_t n, Scalars* sc) {
+  T m = T(0);
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const T v = fabs(u[i]);
+    if (v != v) bad = true;
+    else {
+      if (isinf(v)) bad = true;
+      m = v > m ? v : m;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const T y = __shfl_xor_sync(0xffffffffu, m, o);
+    m = y > m ? y : m;
+  }
+  bad = __any_sync(0xffffffffu, bad);
+  if ((threadIdx.x & 31) == 0) {
+    if (sizeof(T) == 4) atomicMax(&sc->maxabs_bits, (unsigned long long)__float_as_uint((float)m));
+    else atomicMax(&sc->maxabs_bits, (unsigned long long)__double_as_longlong((double)m));
+    if (bad) atomicOr(&sc->status, ST_RAW);
+  }
+}
+
+// Quantiser widths of every (tier, level), in IEEE double arithmetic without
+// contraction: tau' = tau - margin, margin = kappa eps (N+1) max|u|;
+// q_level = 2 tau'/((N+1) A_level), q_coarsest = 2 tau_g'/(N+1).
+struct QtabArgs {
+  const double* tiers;  // relative or absolute, ascending
+  int ntiers, rel, K, M;
+  double A[24];
+  double kappa, eps;
+  double* qd;           // [ntiers*K + M + 1]
+  void* rq;             // same count, field dtype
+  int f64;
+  uint8_t* out;         // stream (tiers + qtab sections) or null
+  unsigned long long off_tiers, off_qtab;
+  Scalars* sc;
+};
+
+__global__ void qtab_kernel(QtabArgs a) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double max_abs = a.f64 ? __longlong_as_double((long long)a.sc->maxabs_bits)
+                               : (double)__uint_as_float((unsigned)a.sc->maxabs_bits);
+  const int N = a.K + a.M;
+  const double t = (double)(N + 1);
+  const double margin = __dmul_rn(__dmul_rn(__dmul_rn(a.kappa, a.eps), t), max_abs);
+  bool raw = !isfinite(max_abs);
+  double taug = INFINITY;
+  const int nq = a.ntiers * a.K + a.M + 1;
+  for (int i = 0; i < a.ntiers; ++i) {
+    const double tau = a.rel ? __dmul_rn(a.tiers[i], max_abs) : a.tiers[i];
+    if (a.out) reinterpret_cast<double*>(a.out + a.off_tiers)[i] = tau;
+    const double taup = __dsub_rn(tau, margin);
+    if (!(taup > __dmul_rn(0.5, tau))) raw = true;
+    taug = fmin(taug, taup);
+    for (int l = 0; l < a.K; ++l)
+      a.qd[i * a.K + l] = __dmul_rn(2.0, __ddiv_rn(taup, __dmul_rn(t, a.A[l])));
+  }
+  for (int l = 0; l < a.M; ++l) a.qd[a.ntiers * a.K + l] = __dmul_rn(2.0, __ddiv_rn(taug, __dmul_rn(t, a.A[a.K + l])));
+  a.qd[nq - 1] = __dmul_rn(2.0, __ddiv_rn(taug, t));
+  for (int i = 0; i < nq; ++i) {
+    const double r = __ddiv_rn(1.0, a.qd[i]);
+    if (a.f64) reinterpret_cast<double*>(a.rq)[i] = r;
+    else reinterpret_cast<float*>(a.rq)[i] = __double2float_rn(r);
+    if (a.out) reinterpret_cast<double*>(a.out + a.off_qtab)[i] = a.qd[i];
+  }
+  a.sc->max_abs = max_abs;
+  a.sc->margin = margin;
+  if (raw) atomicOr(&a.sc->status, ST_RAW);
+}
+
+struct HeaderArgs {
+  uint8_t* out;
+  int f64, B, K, M, chunk, radius, ntiers, m, rel;
+  int64_t shape[3];
+  int nb[3];
+  double tol;
+  unsigned long long n_symbols, n_chunks, off_tiers, off_qtab, off_btier, off_chunks, off_codebook;
+  Scalars* sc;
+};
+
+template <typename V>
+__device__ __forceinline__ void put(uint8_t* p, size_t off, V v) { *reinterpret_cast<V*>(p + off) = v; }
+
+// Header of a coded stream; also zeroes the padding after the bitstream and
+// the outlier section.
+__global__ void header_kernel(HeaderArgs a) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  Scalars* sc = a.sc;
+  if (sc->status & ST_RAW) return;
+  uint8_t* o = a.out;
+  put<uint32_t>(o, 0, kMagic);
+  put<uint16_t>(o, 4, 1);
+  put<uint16_t>(o, 6, (uint16_t)(a.f64 ? 2 : 0));
+  put<int32_t>(o, 8, 3);
+  put<int32_t>(o, 12, a.B);
+  for (int d = 0; d < 3; ++d) put<int64_t>(o, 16 + 8 * d, a.shape[d]);
+  put<int32_t>(o, 40, a.K);
+  put<int32_t>(o, 44, a.M);
+  put<int32_t>(o, 48, a.chunk);
+  put<int32_t>(o, 52, a.radius);
+  put<int32_t>(o, 56, a.ntiers);
+  put<int32_t>(o, 60, a.m);
+  for (int d = 0; d < 3; ++d) put<int32_t>(o, 64 + 4 * d, a.nb[d]);
+  put<int32_t>(o, 76, a.rel);
+  put<double>(o, 80, sc->max_abs);
+  put<double>(o, 88, a.tol);
+  put<uint64_t>(o, 96, a.n_symbols);
+  put<uint64_t>(o, 104, a.n_chunks);
+  put<uint64_t>(o, 112, sc->n_outliers);
+  put<uint64_t>(o, 120, sc->n_words);
+  put<uint64_t>(o, 128, a.off_tiers);
+  put<uint64_t>(o, 136, a.off_qtab);
+  put<uint64_t>(o, 144, a.off_btier);
+  put<uint64_t>(o, 152, a.off_chunks);
+  put<uint64_t>(o, 160, a.off_codebook);
+  put<uint64_t>(o, 168, sc->off_bits);
+  put<uint64_t>(o, 176, sc->off_outliers);
+  put<uint64_t>(o, 184, sc->total);
+  put<uint32_t>(o, 192, (uint32_t)sc->codebook_bytes);
+  put<uint32_t>(o, 196, (uint32_t)sc->n_runs);
+  put<double>(o, 200, sc->margin);
+  for (int i = 208; i < kHeaderBytes; ++i) o[i] = 0;
+  const unsigned long long wend = sc->off_bits + 4ull * sc->n_words;
+  for (unsigned long long i = wend; i < sc->off_outliers; ++i) o[i] = 0;
+  const unsigned long long oend = sc->off_outliers + 12ull * sc->n_outliers;
+  for (unsigned long long i = oend; i < sc->total; ++i) o[i] = 0;
+}
+
+__global__ void raw_header_kernel(uint8_t* o, int f64, int B, int64_t s0, int64_t s1, int64_t s2, int rel, double tol,
+                                  unsigned long long total, Scalars* sc) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = 0; i < kHeaderBytes; ++i) o[i] = 0;
+  put<uint32_t>(o, 0, kMagic);
+  put<uint16_t>(o, 4, 1);
+  put<uint16_t>(o, 6, (uint16_t)(1 | (f64 ? 2 : 0)));
+  put<int32_t>(o, 8, 3);
+  put<int32_t>(o, 12, B);
+  put<int64_t>(o, 16, s0);
+  put<int64_t>(o, 24, s1);
+  put<int64_t>(o, 32, s2);
+  put<int32_t>(o, 76, rel);
+  const double max_abs = f64 ? __longlong_as_double((long long)sc->maxabs_bits)
+                             : (double)__uint_as_float((unsigned)sc->maxabs_bits);
+  put<double>(o, 80, max_abs);
+  put<double>(o, 88, tol);
+  put<uint64_t>(o, 168, (unsigned long long)kHeaderBytes);
+  put<uint64_t>(o, 184, total);
+}
+
+// Decoder-side scan: chunk word counts -> word offsets; checks the total.
+__global__ void __launch_bounds__(kCbThreads) word_scan_kernel(const unsigned* chunk_words, unsigned long long nch,
+                                                              unsigned long long* word_off, unsigned long long n_words,
+                                                              Scalars* sc) {
+  __shared__ unsigned long long wt[32];
+  __shared__ unsigned long long carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (unsigned long long base = 0; base < nch; base += blockDim.x) {
+    const unsigned long long i = base + threadIdx.x;
+    const unsigned long long w = i < nch ? chunk_words[i] : 0ull;
+    unsigned long long x = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wt[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      unsigned long long t = wt[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      wt[lane] = t;
+    }
+    __syncthreads();
+    if (i < nch) word_off[i] = carry + (wid ? wt[wid - 1] : 0ull) + x - w;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += wt[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    word_off[nch] = carry;
+    if (carry != n_words) atomicOr(&sc->status, ST_CORRUPT);
+  }
+}
+
+__global__ void zero_tail_kernel(uint8_t* base, Scalars* sc) {
+  // stand-alone Huffman section: zero the padding after the words
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (sc->status & ST_RAW) return;
+  const unsigned long long wend = sc->off_bits + 4ull * sc->n_words;
+  for (unsigned long long i = wend; i < pad8(wend); ++i) base[i] = 0;
+}
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Pipelines
+// ---------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_block(int dir, int B, int K, int mode, const BlockArgs<T>& a, cudaStream_t s);
+template <>
+cudaError_t launch_block<float>(int dir, int B, int K, int mode, const BlockArgs<float>& a, cudaStream_t s) {
+  BM_LAUNCHED();
+  return B == 9 ? launch_block_f32_b9(dir, K, mode, a, s, num_sms()) : launch_block_f32_b17(dir, K, mode, a, s, num_sms());
+}
+template <>
+cudaError_t launch_block<double>(int dir, int B, int K, int mode, const BlockArgs<double>& a, cudaStream_t s) {
+  BM_LAUNCHED();
+  return B == 9 ? launch_block_f64_b9(dir, K, mode, a, s, num_sms()) : launch_block_f64_b17(dir, K, mode, a, s, num_sms());
+}
+
+// Outputs of the decomposition (mode 0: symbols + escapes + histogram).
+template <typename T>
+struct FwdOut {
+  uint16_t* sym = nullptr;
+  int32_t* esc = nullptr;
+  T* coef = nullptr;
+  unsigned* hist = nullptr;
+  const uint8_t* tier = nullptr;
+  const T* rq = nullptr;  // [ntiers*K + M + 1]
+  int ntiers = 1;
+  int radius = 0;
+  Scalars* sc = nullptr;
+};
+
+template <typename T>
+bm_status run_decompose(PlanDev& P, const T* field, int mode, const FwdOut<T>& o, Carver& cv, cudaStream_t s) {
+  const PlanHost& h = P.h;
+  if (bm_status st = upload_tables<T>(P)) return st;
+  const GSizes gs = gsizes(h);
+  std::vector<T*> U;
+  for (int l = 0; l <= h.M; ++l) U.push_back(cv.take<T>((size_t)gs.U[l]));
+  T* Dbuf = cv.take<T>((size_t)gs.D);
+  T* W1 = cv.take<T>((size_t)std::max<int64_t>(gs.W1, 1));
+  T* W2 = cv.take<T>((size_t)std::max<int64_t>(gs.W2, 1));
+  {
+    Stage st("incache_decompose");
+    BlockArgs<T> a{};
+    a.field = const_cast<T*>(field);
+    a.n0 = h.shape[0]; a.n1 = h.shape[1]; a.n2 = h.shape[2];
+    a.nb0 = h.nb[0]; a.nb1 = h.nb[1]; a.nb2 = h.nb[2];
+    a.nblocks = h.nblocks;
+    a.G = U[0];
+    a.g1 = h.gshape[1]; a.g2 = h.gshape[2];
+    a.sym = o.sym; a.esc = o.esc; a.coef = o.coef;
+    a.tier = o.tier; a.rq = o.rq; a.hist = o.hist; a.radius = o.radius; a.sc = o.sc;
+    BM_CUDA(launch_block<T>(0, h.B, h.K, mode, a, s));
+  }
+  auto& G = glevels<T>(P);
+  for (int l = 0; l < h.M; ++l) {
+    Stage st("global_decompose");
+    const GLevel<T>& L = G[l];
+    const int64_t nn = gs.U[l];
+    const T* rq = o.rq ? o.rq + o.ntiers * h.K + l : nullptr;
+    if (mode == 0) gl_fwd_detail<T, 0><<<grid_for(nn, 256), 256, 0, s>>>(L, U[l], Dbuf, o.sym, o.esc, o.coef, rq, o.hist, o.radius, o.sc);
+    else gl_fwd_detail<T, 1><<<grid_for(nn, 256), 256, 0, s>>>(L, U[l], Dbuf, o.sym, o.esc, o.coef, rq, o.hist, o.radius, o.sc);
+    BM_LAUNCHED();
+    const int64_t l2 = (int64_t)L.d[0].n * L.d[1].n, l1 = (int64_t)L.d[0].n * L.d[2].c, l0 = (int64_t)L.d[1].c * L.d[2].c;
+    gl_restrict<T, 2, 0><<<grid_for(l2, 128, 16), 128, 0, s>>>(L, Dbuf, W1, nullptr);
+    gl_restrict<T, 1, 0><<<grid_for(l1, 128, 16), 128, 0, s>>>(L, W1, W2, nullptr);
+    gl_restrict<T, 0, 1><<<grid_for(l0, 128, 16), 128, 0, s>>>(L, W2, U[l + 1], U[l]);
+    g_launches.fetch_add(3);
+    BM_CUDA(cudaGetLastError());
+  }
+  {
+    Stage st("coarsest");
+    const int64_t cnt = gs.U[h.M];
+    const T* rq = o.rq ? o.rq + o.ntiers * h.K + h.M : nullptr;
+    if (mode == 0) coarsest_fwd<T, 0><<<grid_for(cnt, 256), 256, 0, s>>>(U[h.M], cnt, h.sym_off[h.M], o.sym, o.esc, o.coef, rq, o.hist, o.radius, o.sc);
+    else coarsest_fwd<T, 1><<<grid_for(cnt, 256), 256, 0, s>>>(U[h.M], cnt, h.sym_off[h.M], o.sym, o.esc, o.coef, rq, o.hist, o.radius, o.sc);
+    BM_LAUNCHED();
+    BM_CUDA(cudaGetLastError());
+  }
+  return BM_OK;
+}
+
+template <typename T>
+struct InvIn {
+  const uint16_t* sym = nullptr;
+  const int32_t* esc = nullptr;
+  const T* coef = nullptr;
+  const uint8_t* tier = nullptr;
+  const double* q = nullptr;  // [ntiers*K + M + 1]
+  int ntiers = 1;
+  int radius = 0;
+};
+
+template <typename T>
+bm_status run_recompose(PlanDev& P, T* field, int mode, const InvIn<T>& in, Carver& cv, cudaStream_t s) {
+  const PlanHost& h = P.h;
+  if (bm_status st = upload_tables<T>(P)) return st;
+  const GSizes gs = gsizes(h);
+  std::vector<T*> U;
+  for (int l = 0; l <= h.M; ++l) U.push_back(cv.take<T>((size_t)gs.U[l]));
+  T* Dbuf = cv.take<T>((size_t)gs.D);
+  T* W1 = cv.take<T>((size_t)std::max<int64_t>(gs.W1, 1));
+  T* W2 = cv.take<T>((size_t)std::max<int64_t>(gs.W2, 1));
+  (void)Dbuf;
+  {
+    Stage st("coarsest");
+    const int64_t cnt = gs.U[h.M];
+    const double* q = in.q ? in.q + in.ntiers * h.K + h.M : nullptr;
+    if (mode == 0) coarsest_inv<T, 0><<<grid_for(cnt, 256), 256, 0, s>>>(U[h.M], cnt, h.sym_off[h.M], in.sym, in.esc, in.coef, q, in.radius);
+    else coarsest_inv<T, 1><<<grid_for(cnt, 256), 256, 0, s>>>(U[h.M], cnt, h.sym_off[h.M], in.sym, in.esc, in.coef, q, in.radius);
+    BM_LAUNCHED();
+    BM_CUDA(cudaGetLastError());
+  }
+  auto& G = glevels<T>(P);
+  for (int l = h.M - 1; l >= 0; --l) {
+    Stage st("global_recompose");
+    const GLevel<T>& L = G[l];
+    const int64_t nn = gs.U[l];
+    const double* q = in.q ? in.q + in.ntiers * h.K + l : nullptr;
+    // U[l] <- dequantised coefficients; z = P D; coarse' = U[l+1] - z (into W1); U[l] = I coarse' + D
+    if (mode == 0) gl_inv_dequant<T, 0><<<grid_for(nn, 256), 256, 0, s>>>(L, in.sym, in.esc, in.coef, q, in.radius, U[l]);
+    else gl_inv_dequant<T, 1><<<grid_for(nn, 256), 256, 0, s>>>(L, in.sym, in.esc, in.coef, q, in.radius, U[l]);
+    const int64_t l2 = (int64_t)L.d[0].n * L.d[1].n, l1 = (int64_t)L.d[0].n * L.d[2].c, l0 = (int64_t)L.d[1].c * L.d[2].c;
+    T* Cn = Dbuf;  // corrected coarse values (size of U[l+1] <= size of U[0])
+    gl_restrict<T, 2, 0><<<grid_for(l2, 128, 16), 128, 0, s>>>(L, U[l], W1, nullptr);
+    gl_restrict<T, 1, 0><<<grid_for(l1, 128, 16), 128, 0, s>>>(L, W1, W2, nullptr);
+    gl_restrict<T, 0, 2><<<grid_for(l0, 128, 16), 128, 0, s>>>(L, W2, Cn, U[l + 1]);
+    gl_inv_interp<T><<<grid_for(nn, 256), 256, 0, s>>>(L, Cn, U[l]);
+    g_launches.fetch_add(5);
+    BM_CUDA(cudaGetLastError());
+  }
+  {
+    Stage st("incache_recompose");
+    BlockArgs<T> a{};
+    a.field = field;
+    a.n0 = h.shape[0]; a.n1 = h.shape[1]; a.n2 = h.shape[2];
+    a.nb0 = h.nb[0]; a.nb1 = h.nb[1]; a.nb2 = h.nb[2];
+    a.nblocks = h.nblocks;
+    a.G = U[0];
+    a.g1 = h.gshape[1]; a.g2 = h.gshape[2];
+    a.sym = const_cast<uint16_t*>(in.sym);
+    a.esc = const_cast<int32_t*>(in.esc);
+    a.coef = const_cast<T*>(in.coef);
+    a.tier = in.tier;
+    a.q = in.q;
+    a.radius = in.radius;
+    BM_CUDA(launch_block<T>(1, h.B, h.K, mode, a, s));
+  }
+  return BM_OK;
+}
+
+size_t decompose_scratch(const PlanHost& h, size_t esize) {
+  const GSizes gs = gsizes(h);
+  size_t b = 0;
+  for (int64_t u : gs.U) b += (size_t)u * esize + 256;
+  b += ((size_t)gs.D + gs.W1 + gs.W2 + 3) * esize + 768;
+  return b;
+}
+
+// Layout of the host-known part of a stream.
+struct StreamLayout {
+  unsigned long long off_tiers, off_qtab, off_btier, off_chunks, off_codebook, nch;
+  int nq;
+};
+StreamLayout layout(const PlanHost& h, int ntiers, int chunk) {
+  StreamLayout L;
+  L.nq = ntiers * h.K + h.M + 1;
+  L.nch = ((unsigned long long)h.n_coeffs + chunk - 1) / chunk;
+  L.off_tiers = kHeaderBytes;
+  L.off_qtab = L.off_tiers + pad8(8ull * ntiers);
+  L.off_btier = L.off_qtab + pad8(8ull * L.nq);
+  L.off_chunks = L.off_btier + (ntiers > 1 ? pad8((unsigned long long)h.nblocks) : 0ull);
+  L.off_codebook = L.off_chunks + pad8(4ull * L.nch);
+  return L;
+}
+
+template <typename T>
+bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, double tol, int rel, const double* roi,
+                     uint8_t* out, size_t cap, size_t* out_bytes, cudaStream_t s) {
+  PlanDev* P = nullptr;
+  if (bm_status st = get_plan(shape, prm.B, prm.K, prm.M, &P)) return st;
+  const PlanHost& h = P->h;
+  if (h.n_coeffs >= (int64_t(1) << 32)) return fail(BM_ERR_UNSUPPORTED, "more than 2^32 - 1 coefficients");
+  if (prm.M + prm.K > 24) return fail(BM_ERR_ARG, "too many levels");
+  const bool f64 = sizeof(T) == 8;
+  const int64_t nel = nel3(shape);
+  const unsigned long long raw_total = kHeaderBytes + (unsigned long long)nel * sizeof(T);
+  if (cap < raw_total) return fail(BM_ERR_CAPACITY, "out_capacity below bm_compress_bound()");
+  // tiers: distinct min(tol, roi_i) values, ascending
+  std::vector<double> bt((size_t)h.nblocks, tol);
+  if (roi)
+    for (int64_t b = 0; b < h.nblocks; ++b) {
+      if (!(roi[b] > 0.0) || !std::isfinite(roi[b])) return fail(BM_ERR_ARG, "ROI tolerances must be finite and > 0");
+      bt[(size_t)b] = std::min(tol, roi[b]);
+    }
+  std::vector<double> tiers = bt;
+  std::sort(tiers.begin(), tiers.end());
+  tiers.erase(std::unique(tiers.begin(), tiers.end()), tiers.end());
+  if (tiers.size() > 255) return fail(BM_ERR_ARG, "more than 255 distinct tolerances");
+  const int ntiers = (int)tiers.size();
+  std::vector<uint8_t> btier;
+  if (ntiers > 1) {
+    btier.resize((size_t)h.nblocks);
+    for (int64_t b = 0; b < h.nblocks; ++b)
+      btier[(size_t)b] = (uint8_t)(std::lower_bound(tiers.begin(), tiers.end(), bt[(size_t)b]) - tiers.begin());
+  }
+  const StreamLayout L = layout(h, ntiers, prm.chunk);
+  const int dict = 2 * prm.radius;
+
+  // scratch
+  Carver cv;
+  auto carve_all = [&](Carver& c, unsigned char* base) {
+    c.base = base;
+    c.off = 0;
+  };
+  Carver probe;
+  carve_all(probe, nullptr);
+  probe.take<Scalars>(1); probe.take<unsigned>(dict); probe.take<uint8_t>(dict); probe.take<unsigned>(dict);
+  probe.take<double>(L.nq); probe.take<T>(L.nq); probe.take<double>(ntiers); probe.take<uint8_t>(h.nblocks);
+  probe.take<uint16_t>((size_t)h.n_coeffs); probe.take<int32_t>((size_t)h.n_coeffs);
+  probe.take<unsigned>(L.nch); probe.take<unsigned long long>(L.nch + 1); probe.take<unsigned long long>(L.nch + 1);
+  const size_t need = probe.off + decompose_scratch(h, sizeof(T)) + 4096;
+  const size_t hneed = sizeof(Scalars) + 8 * ntiers + (size_t)h.nblocks + 4096;
+  Workspace* ws = nullptr;
+  if (bm_status st = get_ws(s, need, hneed, &ws)) return st;
+  carve_all(cv, reinterpret_cast<unsigned char*>(ws->d));
+  Scalars* sc = cv.take<Scalars>(1);
+  unsigned* hist = cv.take<unsigned>(dict);
+  uint8_t* lens = cv.take<uint8_t>(dict);
+  unsigned* codes = cv.take<unsigned>(dict);
+  double* qd = cv.take<double>(L.nq);
+  T* rq = cv.take<T>(L.nq);
+  double* dtiers = cv.take<double>(ntiers);
+  uint8_t* dbt = cv.take<uint8_t>(h.nblocks);
+  uint16_t* sym = cv.take<uint16_t>((size_t)h.n_coeffs);
+  int32_t* esc = cv.take<int32_t>((size_t)h.n_coeffs);
+  unsigned* chunk_esc = cv.take<unsigned>(L.nch);
+  unsigned long long* word_off = cv.take<unsigned long long>(L.nch + 1);
+  unsigned long long* esc_off = cv.take<unsigned long long>(L.nch + 1);
+
+  unsigned char* hp = reinterpret_cast<unsigned char*>(ws->h);
+  Scalars* hsc = reinterpret_cast<Scalars*>(hp);
+  double* htiers = reinterpret_cast<double*>(hp + 256);
+  uint8_t* hbt = hp + 256 + 8 * 256;
+  std::memcpy(htiers, tiers.data(), 8 * ntiers);
+  if (ntiers > 1) std::memcpy(hbt, btier.data(), btier.size());
+
+  const bool prefix_fits = L.off_codebook <= cap;
+  {
+    Stage st("setup");
+    BM_CUDA(cudaMemsetAsync(sc, 0, sizeof(Scalars), s));
+    BM_CUDA(cudaMemsetAsync(hist, 0, 4ull * dict, s));
+    BM_CUDA(cudaMemcpyAsync(dtiers, htiers, 8 * ntiers, cudaMemcpyHostToDevice, s));
+    if (ntiers > 1) BM_CUDA(cudaMemcpyAsync(dbt, hbt, (size_t)h.nblocks, cudaMemcpyHostToDevice, s));
+    if (prefix_fits) {
+      BM_CUDA(cudaMemsetAsync(out, 0, L.off_codebook, s));
+      if (ntiers > 1) BM_CUDA(cudaMemcpyAsync(out + L.off_btier, dbt, (size_t)h.nblocks, cudaMemcpyDeviceToDevice, s));
+    }
+  }
+  {
+    Stage st("maxabs");
+    maxabs_kernel<T><<<grid_for(nel, 256, 8), 256, 0, s>>>(field, nel, sc);
+    BM_LAUNCHED();
+    QtabArgs qa{};
+    qa.tiers = dtiers; qa.ntiers = ntiers; qa.rel = rel; qa.K = h.K; qa.M = h.M;
+    for (size_t i = 0; i < h.A.size() && i < 24; ++i) qa.A[i] = h.A[i];
+    qa.kappa = 8.0;
+    qa.eps = f64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
+    qa.qd = qd; qa.rq = rq; qa.f64 = f64;
+    qa.out = prefix_fits ? out : nullptr;
+    qa.off_tiers = L.off_tiers; qa.off_qtab = L.off_qtab; qa.sc = sc;
+    qtab_kernel<<<1, 32, 0, s>>>(qa);
+    BM_LAUNCHED();
+    BM_CUDA(cudaGetLastError());
+  }
+  if (!prefix_fits) {  // not even the tables fit: the raw copy is the stream
+    BM_CUDA(cudaMemsetAsync(sc, 0, sizeof(Scalars), s));
+    maxabs_kernel<T><<<grid_for(nel, 256, 8), 256, 0, s>>>(field, nel, sc);
+    raw_header_kernel<<<1, 32, 0, s>>>(out, f64, h.B, shape[0], shape[1], shape[2], rel, tol, raw_total, sc);
+    g_launches.fetch_add(2);
+    BM_CUDA(cudaMemcpyAsync(out + kHeaderBytes, field, (size_t)nel * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    BM_CUDA(cudaStreamSynchronize(s));
+    *out_bytes = (size_t)raw_total;
+    return BM_OK;
+  }
+  FwdOut<T> fo;
+  fo.sym = sym; fo.esc = esc; fo.hist = hist; fo.tier = ntiers > 1 ? dbt : nullptr; fo.rq = rq;
+  fo.ntiers = ntiers; fo.radius = prm.radius; fo.sc = sc;
+  if (bm_status st = run_decompose<T>(*P, field, 0, fo, cv, s)) return st;
+  {
+    Stage st("huffman_codebook");
+    CodebookArgs ca{hist, dict, lens, codes, prefix_fits ? out : nullptr, L.off_codebook, cap, sc};
+    BM_CUDA(cudaFuncSetAttribute(codebook_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CbSmem)));
+    codebook_kernel<<<1, kCbThreads, sizeof(CbSmem), s>>>(ca);
+    BM_LAUNCHED();
+    BM_CUDA(cudaGetLastError());
+  }
+  {
+    Stage st("huffman_encode");
+    EncodeArgs ea{};
+    ea.sym = sym; ea.esc = esc; ea.n = (unsigned long long)h.n_coeffs; ea.chunk = prm.chunk;
+    ea.lens = lens; ea.codes = codes; ea.dict = dict;
+    ea.chunk_words = reinterpret_cast<unsigned*>(out + L.off_chunks);
+    ea.chunk_esc = chunk_esc; ea.word_off = word_off; ea.esc_off = esc_off; ea.nch = L.nch;
+    ea.out = out; ea.sc = sc;
+    chunk_bits_kernel<8><<<grid_for((int64_t)L.nch * 32, 256, 16), 256, 0, s>>>(ea);
+    chunk_scan_kernel<<<1, kCbThreads, 0, s>>>(ea.chunk_words, chunk_esc, L.nch, word_off, esc_off, sc, L.off_codebook,
+                                               raw_total, cap);
+    encode_kernel<8><<<grid_for((int64_t)L.nch * 32, 256, 16), 256, 0, s>>>(ea);
+    g_launches.fetch_add(3);
+    HeaderArgs ha{};
+    ha.out = out; ha.f64 = f64; ha.B = h.B; ha.K = h.K; ha.M = h.M; ha.chunk = prm.chunk; ha.radius = prm.radius;
+    ha.ntiers = ntiers; ha.m = h.m; ha.rel = rel;
+    for (int d = 0; d < 3; ++d) { ha.shape[d] = shape[d]; ha.nb[d] = h.nb[d]; }
+    ha.tol = tol; ha.n_symbols = (unsigned long long)h.n_coeffs; ha.n_chunks = L.nch;
+    ha.off_tiers = L.off_tiers; ha.off_qtab = L.off_qtab; ha.off_btier = ntiers > 1 ? L.off_btier : L.off_chunks;
+    ha.off_chunks = L.off_chunks; ha.off_codebook = L.off_codebook; ha.sc = sc;
+    header_kernel<<<1, 32, 0, s>>>(ha);
+    BM_LAUNCHED();
+    BM_CUDA(cudaGetLastError());
+    BM_CUDA(cudaMemcpyAsync(hsc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+  }
+  BM_CUDA(cudaStreamSynchronize(s));
+  if (hsc->status & ST_RAW) {
+    Stage st("raw_copy");
+    raw_header_kernel<<<1, 32, 0, s>>>(out, f64, h.B, shape[0], shape[1], shape[2], rel, tol, raw_total, sc);
+    BM_LAUNCHED();
+    BM_CUDA(cudaMemcpyAsync(out + kHeaderBytes, field, (size_t)nel * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    BM_CUDA(cudaStreamSynchronize(s));
+    *out_bytes = (size_t)raw_total;
+  } else {
+    *out_bytes = (size_t)hsc->total;
+  }
+  return BM_OK;
+}
+
+// Parsed and checked header of a stream.
+struct Header {
+  bool raw, f64;
+  int B, K, M, chunk, radius, ntiers, m, rel;
+  int64_t shape[3];
+  unsigned long long n_symbols, n_chunks, n_outliers, n_words, off_tiers, off_qtab, off_btier, off_chunks,
+      off_codebook, off_bits, off_outliers, total;
+  unsigned codebook_bytes, n_runs;
+};
+
+template <typename V>
+V rd(const unsigned char* p, size_t off) {
+  V v;
+  std::memcpy(&v, p + off, sizeof(V));
+  return v;
+}
+
+bm_status parse_header(const unsigned char* hb, size_t in_bytes, Header& H) {
+  if (in_bytes < (size_t)kHeaderBytes) return fail(BM_ERR_CORRUPT, "stream shorter than its header");
+  if (rd<uint32_t>(hb, 0) != kMagic) return fail(BM_ERR_CORRUPT, "bad magic");
+  if (rd<uint16_t>(hb, 4) != 1) return fail(BM_ERR_CORRUPT, "unknown stream version");
+  const uint16_t flags = rd<uint16_t>(hb, 6);
+  H.raw = flags & 1;
+  H.f64 = flags & 2;
+  if (rd<int32_t>(hb, 8) != 3) return fail(BM_ERR_CORRUPT, "ndim");
+  H.B = rd<int32_t>(hb, 12);
+  for (int d = 0; d < 3; ++d) {
+    H.shape[d] = rd<int64_t>(hb, 16 + 8 * d);
+    if (H.shape[d] < 2 || H.shape[d] > (int64_t(1) << 31)) return fail(BM_ERR_CORRUPT, "shape");
+  }
+  H.total = rd<uint64_t>(hb, 184);
+  if (H.total != in_bytes) return fail(BM_ERR_CORRUPT, "stream length does not match its header");
+  const unsigned long long nel = (unsigned long long)H.shape[0] * H.shape[1] * H.shape[2];
+  if (H.raw) {
+    if (in_bytes != kHeaderBytes + nel * (H.f64 ? 8 : 4)) return fail(BM_ERR_CORRUPT, "raw stream size");
+    return BM_OK;
+  }
+  H.K = rd<int32_t>(hb, 40); H.M = rd<int32_t>(hb, 44); H.chunk = rd<int32_t>(hb, 48); H.radius = rd<int32_t>(hb, 52);
+  H.ntiers = rd<int32_t>(hb, 56); H.m = rd<int32_t>(hb, 60); H.rel = rd<int32_t>(hb, 76);
+  H.n_symbols = rd<uint64_t>(hb, 96); H.n_chunks = rd<uint64_t>(hb, 104); H.n_outliers = rd<uint64_t>(hb, 112);
+  H.n_words = rd<uint64_t>(hb, 120);
+  H.off_tiers = rd<uint64_t>(hb, 128); H.off_qtab = rd<uint64_t>(hb, 136); H.off_btier = rd<uint64_t>(hb, 144);
+  H.off_chunks = rd<uint64_t>(hb, 152); H.off_codebook = rd<uint64_t>(hb, 160); H.off_bits = rd<uint64_t>(hb, 168);
+  H.off_outliers = rd<uint64_t>(hb, 176);
+  H.codebook_bytes = rd<uint32_t>(hb, 192); H.n_runs = rd<uint32_t>(hb, 196);
+  if ((H.B != 9 && H.B != 17) || H.K < 1 || H.K > (H.B == 9 ? 3 : 4) || H.M < 0 || H.M > 16 || H.chunk < 64 ||
+      H.chunk > 8192 || H.chunk % 32 || H.radius < 16 || H.radius > kMaxDict / 2 || H.ntiers < 1 || H.ntiers > 255)
+    return fail(BM_ERR_CORRUPT, "header parameters out of range");
+  const unsigned long long nq = (unsigned long long)H.ntiers * H.K + H.M + 1;
+  if (H.off_tiers != kHeaderBytes || H.off_qtab != H.off_tiers + pad8(8ull * H.ntiers) ||
+      H.off_btier != H.off_qtab + pad8(8ull * nq) || H.off_chunks < H.off_btier ||
+      H.off_codebook != H.off_chunks + pad8(4ull * H.n_chunks) ||
+      H.off_bits != H.off_codebook + pad8(H.codebook_bytes) || H.off_outliers != H.off_bits + pad8(4ull * H.n_words) ||
+      H.total != H.off_outliers + pad8(12ull * H.n_outliers))
+    return fail(BM_ERR_CORRUPT, "section offsets inconsistent");
+  if (H.n_chunks != (H.n_symbols + H.chunk - 1) / H.chunk) return fail(BM_ERR_CORRUPT, "chunk count");
+  if (H.n_outliers > H.n_symbols) return fail(BM_ERR_CORRUPT, "outlier count");
+  return BM_OK;
+}
+
+bm_status read_header(const void* in, size_t in_bytes, bool is_device, cudaStream_t s, Header& H) {
+  unsigned char hb[kHeaderBytes];
+  if (in_bytes < (size_t)kHeaderBytes) return fail(BM_ERR_CORRUPT, "stream shorter than its header");
+  if (is_device) {
+    Workspace* ws = nullptr;
+    if (bm_status st = get_ws(s, 1 << 12, 1 << 12, &ws)) return st;
+    BM_CUDA(cudaMemcpyAsync(ws->h, in, kHeaderBytes, cudaMemcpyDeviceToHost, s));
+    BM_CUDA(cudaStreamSynchronize(s));
+    std::memcpy(hb, ws->h, kHeaderBytes);
+  } else {
+    std::memcpy(hb, in, kHeaderBytes);
+  }
+  return parse_header(hb, in_bytes, H);
+}
+
+// Decode the Huffman part of a stream into symbols + escape codes.
+bm_status decode_symbols(const uint8_t* in, const Header& H, Carver& cv, uint16_t** sym_out, int32_t** esc_out,
+                         Scalars** sc_out, cudaStream_t s) {
+  Scalars* sc = cv.take<Scalars>(1);
+  uint16_t* sym = cv.take<uint16_t>(H.n_symbols);
+  int32_t* esc = cv.take<int32_t>(H.n_symbols);
+  unsigned long long* word_off = cv.take<unsigned long long>(H.n_chunks + 1);
+  DecodeTables* dt = cv.take<DecodeTables>(1);
+  BM_CUDA(cudaMemsetAsync(sc, 0, sizeof(Scalars), s));
+  {
+    Stage st("huffman_tables");
+    word_scan_kernel<<<1, kCbThreads, 0, s>>>(reinterpret_cast<const unsigned*>(in + H.off_chunks), H.n_chunks,
+                                              word_off, H.n_words, sc);
+    BM_CUDA(cudaFuncSetAttribute(decode_tables_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DtSmem)));
+    decode_tables_kernel<<<1, kCbThreads, sizeof(DtSmem), s>>>(in + H.off_codebook, H.codebook_bytes, H.n_runs,
+                                                               2 * H.radius, dt, sc);
+    g_launches.fetch_add(2);
+    BM_CUDA(cudaGetLastError());
+  }
+  {
+    Stage st("huffman_decode");
+    DecodeArgs da{};
+    da.words = reinterpret_cast<const unsigned*>(in + H.off_bits);
+    da.n_words = H.n_words; da.word_off = word_off; da.nch = H.n_chunks; da.n = H.n_symbols; da.chunk = H.chunk;
+    da.tab = dt; da.sym = sym; da.sc = sc;
+    decode_kernel<<<grid_for((int64_t)H.n_chunks, 256, 8), 256, 0, s>>>(da);
+    BM_LAUNCHED();
+    if (H.n_outliers) {
+      outlier_scatter_kernel<<<grid_for((int64_t)H.n_outliers, 256), 256, 0, s>>>(
+          reinterpret_cast<const unsigned long long*>(in + H.off_outliers),
+          reinterpret_cast<const int32_t*>(in + H.off_outliers + 8ull * H.n_outliers), H.n_outliers, H.n_symbols, esc,
+          sc);
+      BM_LAUNCHED();
+    }
+    BM_CUDA(cudaGetLastError());
+  }
+  *sym_out = sym;
+  *esc_out = esc;
+  *sc_out = sc;
+  return BM_OK;
+}
+
+size_t decode_scratch(const Header& H) {
+  return sizeof(Scalars) + 2ull * H.n_symbols + 4ull * H.n_symbols + 8ull * (H.n_chunks + 1) + sizeof(DecodeTables) +
+         4096;
+}
+
+bm_status check_status(Scalars* sc, cudaStream_t s) {
+  Workspace* ws = nullptr;
+  if (bm_status st = get_ws(s, 0, 4096, &ws)) return st;
+  BM_CUDA(cudaMemcpyAsync(ws->h, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+  BM_CUDA(cudaStreamSynchronize(s));
+  const Scalars* h = reinterpret_cast<const Scalars*>(ws->h);
+  if (h->status & ST_CORRUPT) return fail(BM_ERR_CORRUPT, "stream failed a bound check while decoding");
+  return BM_OK;
+}
+
+template <typename T>
+bm_status decompress_t(const uint8_t* in, const Header& H, T* field, cudaStream_t s) {
+  PlanDev* P = nullptr;
+  if (bm_status st = get_plan(H.shape, H.B, H.K, H.M, &P)) return fail(BM_ERR_CORRUPT, g_detail);
+  const PlanHost& h = P->h;
+  if ((unsigned long long)h.n_coeffs != H.n_symbols || h.m != H.m) return fail(BM_ERR_CORRUPT, "symbol count");
+  if (H.ntiers > 1 && H.off_chunks != H.off_btier + pad8((unsigned long long)h.nblocks))
+    return fail(BM_ERR_CORRUPT, "block tier section size");
+  const size_t need = decode_scratch(H) + decompose_scratch(h, sizeof(T)) + 8192;
+  Workspace* ws = nullptr;
+  if (bm_status st = get_ws(s, need, 4096, &ws)) return st;
+  Carver cv;
+  cv.base = reinterpret_cast<unsigned char*>(ws->d);
+  uint16_t* sym;
+  int32_t* esc;
+  Scalars* sc;
+  if (bm_status st = decode_symbols(in, H, cv, &sym, &esc, &sc, s)) return st;
+  InvIn<T> ii;
+  ii.sym = sym; ii.esc = esc; ii.radius = H.radius; ii.ntiers = H.ntiers;
+  ii.q = reinterpret_cast<const double*>(in + H.off_qtab);
+  ii.tier = H.ntiers > 1 ? in + H.off_btier : nullptr;
+  if (bm_status st = run_recompose<T>(*P, field, 0, ii, cv, s)) return st;
+  return check_status(sc, s);
+}
+
+}  // namespace
+}  // namespace bm
+
+using namespace bm;
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* bm_error_string(bm_status s) {
+  switch (s) {
+    case BM_OK: return "ok";
+    case BM_ERR_ARG: return "invalid argument";
+    case BM_ERR_CUDA: return "CUDA error";
+    case BM_ERR_CAPACITY: return "output capacity too small";
+    case BM_ERR_CORRUPT: return "corrupt stream";
+    case BM_ERR_UNSUPPORTED: return "unsupported";
+    case BM_ERR_OOM: return "out of device memory";
+  }
+  return "unknown status";
+}
+
+const char* bm_last_error_detail(void) { return g_detail.c_str(); }
+
+uint64_t bm_launch_count(void) { return g_launches.load(); }
+
+void bm_set_timing(int enabled) { g_timing.store(enabled ? 1 : 0); }
+
+int bm_stage_times(const char** names, float* ms, int max_stages) {
+  std::lock_guard<std::mutex> g(g_timer_mu);
+  g_timer.collect();
+  int n = 0;
+  for (auto& r : g_timer.last) {
+    if (n >= max_stages) break;
+    if (names) names[n] = r.first;
+    if (ms) ms[n] = r.second;
+    ++n;
+  }
+  return n;
+}
+
+size_t bm_compress_bound(int ndim, const int64_t* shape, bm_dtype dtype) {
+  if (ndim != 3 || !shape) return 0;
+  for (int d = 0; d < 3; ++d)
+    if (shape[d] < 2 || shape[d] > (int64_t(1) << 31)) return 0;
+  return (size_t)kHeaderBytes + (size_t)nel3(shape) * (dtype == BM_F64 ? 8 : 4);
+}
+
+bm_status bm_coeff_count(int ndim, const int64_t* shape, const bm_params* params, size_t* n_coeffs) {
+  if (bm_status st = check_shape(ndim, shape)) return st;
+  Params prm;
+  if (bm_status st = check_params(params, prm)) return st;
+  PlanDev* P = nullptr;
+  if (bm_status st = get_plan(shape, prm.B, prm.K, prm.M, &P)) return st;
+  if (n_coeffs) *n_coeffs = (size_t)P->h.n_coeffs;
+  return BM_OK;
+}
+
+bm_status bm_compress(const void* d_field, int ndim, const int64_t* shape, bm_dtype dtype, double tol,
+                      bm_tol_mode tol_mode, const double* h_roi_tol, const bm_params* params, void* d_out,
+                      size_t out_capacity, size_t* out_bytes, void* stream) {
+  if (!d_field || !d_out || !out_bytes) return fail(BM_ERR_ARG, "NULL pointer argument");
+  if (bm_status st = check_shape(ndim, shape)) return st;
+  if (dtype != BM_F32 && dtype != BM_F64) return fail(BM_ERR_ARG, "dtype");
+  if (!(tol > 0.0) || !std::isfinite(tol)) return fail(BM_ERR_ARG, "tolerance must be finite and > 0");
+  if (tol_mode != BM_ABS && tol_mode != BM_REL) return fail(BM_ERR_ARG, "tol_mode");
+  Params prm;
+  if (bm_status st = check_params(params, prm)) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> g(g_timer_mu);
+  g_timer.begin(s);
+  bm_status st;
+  if (dtype == BM_F32)
+    st = compress_t<float>(reinterpret_cast<const float*>(d_field), shape, prm, tol, tol_mode == BM_REL, h_roi_tol,
+                           reinterpret_cast<uint8_t*>(d_out), out_capacity, out_bytes, s);
+  else
+    st = compress_t<double>(reinterpret_cast<const double*>(d_field), shape, prm, tol, tol_mode == BM_REL, h_roi_tol,
+                            reinterpret_cast<uint8_t*>(d_out), out_capacity, out_bytes, s);
+  return st;
+}
+
+bm_status bm_stream_info(const void* in, size_t in_bytes, int in_is_device, int* ndim, int64_t shape[3],
+                         bm_dtype* dtype, size_t* n_coeffs) {
+  if (!in) return fail(BM_ERR_ARG, "NULL stream");
+  Header H{};
+  if (bm_status st = read_header(in, in_bytes, in_is_device != 0, nullptr, H)) return st;
+  if (ndim) *ndim = 3;
+  if (shape) for (int d = 0; d < 3; ++d) shape[d] = H.shape[d];
+  if (dtype) *dtype = H.f64 ? BM_F64 : BM_F32;
+  if (n_coeffs) *n_coeffs = H.raw ? 0 : (size_t)H.n_symbols;
+  return BM_OK;
+}
+
+bm_status bm_decompress(const void* d_in, size_t in_bytes, void* d_field, void* stream) {
+  if (!d_in || !d_field) return fail(BM_ERR_ARG, "NULL pointer argument");
+  if (reinterpret_cast<uintptr_t>(d_in) % 8) return fail(BM_ERR_ARG, "stream pointer must be 8-byte aligned");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> g(g_timer_mu);
+  g_timer.begin(s);
+  Header H{};
+  if (bm_status st = read_header(d_in, in_bytes, true, s, H)) return st;
+  const uint8_t* in = reinterpret_cast<const uint8_t*>(d_in);
+  if (H.raw) {
+    const size_t nb = (size_t)nel3(H.shape) * (H.f64 ? 8 : 4);
+    BM_CUDA(cudaMemcpyAsync(d_field, in + kHeaderBytes, nb, cudaMemcpyDeviceToDevice, s));
+    BM_CUDA(cudaStreamSynchronize(s));
+    return BM_OK;
+  }
+  return H.f64 ? decompress_t<double>(in, H, reinterpret_cast<double*>(d_field), s)
+               : decompress_t<float>(in, H, reinterpret_cast<float*>(d_field), s);
+}
+
+bm_status bm_decompose(const void* d_field, int ndim, const int64_t* shape, bm_dtype dtype, const bm_params* params,
+                       void* d_coeffs, void* stream) {
+  if (!d_field || !d_coeffs) return fail(BM_ERR_ARG, "NULL pointer argument");
+  if (bm_status st = check_shape(ndim, shape)) return st;
+  Params prm;
+  if (bm_status st = check_params(params, prm)) return st;
+  PlanDev* P = nullptr;
+  if (bm_status st = get_plan(shape, prm.B, prm.K, prm.M, &P)) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> g(g_timer_mu);
+  g_timer.begin(s);
+  const size_t esize = dtype == BM_F64 ? 8 : 4;
+  Workspace* ws = nullptr;
+  if (bm_status st = get_ws(s, decompose_scratch(P->h, esize) + 4096, 4096, &ws)) return st;
+  Carver cv;
+  cv.base = reinterpret_cast<unsigned char*>(ws->d);
+  if (dtype == BM_F64) {
+    FwdOut<double> o;
+    o.coef = reinterpret_cast<double*>(d_coeffs);
+    return run_decompose<double>(*P, reinterpret_cast<const double*>(d_field), 1, o, cv, s);
+  }
+  FwdOut<float> o;
+  o.coef = reinterpret_cast<float*>(d_coeffs);
+  return run_decompose<float>(*P, reinterpret_cast<const float*>(d_field), 1, o, cv, s);
+}
+
+bm_status bm_recompose(const void* d_coeffs, int ndim, const int64_t* shape, bm_dtype dtype, const bm_params* params,
+                       void* d_field, void* stream) {
+  if (!d_field || !d_coeffs) return fail(BM_ERR_ARG, "NULL pointer argument");
+  if (bm_status st = check_shape(ndim, shape)) return st;
+  Params prm;
+  if (bm_status st = check_params(params, prm)) return st;
+  PlanDev* P = nullptr;
+  if (bm_status st = get_plan(shape, prm.B, prm.K, prm.M, &P)) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> g(g_timer_mu);
+  g_timer.begin(s);
+  const size_t esize = dtype == BM_F64 ? 8 : 4;
+  Workspace* ws = nullptr;
+  if (bm_status st = get_ws(s, decompose_scratch(P->h, esize) + 4096, 4096, &ws)) return st;
+  Carver cv;
+  cv.base = reinterpret_cast<unsigned char*>(ws->d);
+  if (dtype == BM_F64) {
+    InvIn<double> in;
+    in.coef = reinterpret_cast<const double*>(d_coeffs);
+    return run_recompose<double>(*P, reinterpret_cast<double*>(d_field), 1, in, cv, s);
+  }
+  InvIn<float> in;
+  in.coef = reinterpret_cast<const float*>(d_coeffs);
+  return run_recompose<float>(*P, reinterpret_cast<float*>(d_field), 1, in, cv, s);
+}
+
+bm_status bm_stream_codes(const void* d_in, size_t in_bytes, int32_t* d_codes, void* stream) {
+  if (!d_in || !d_codes) return fail(BM_ERR_ARG, "NULL pointer argument");
+  if (reinterpret_cast<uintptr_t>(d_in) % 8) return fail(BM_ERR_ARG, "stream pointer must be 8-byte aligned");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> g(g_timer_mu);
+  g_timer.begin(s);
+  Header H{};
+  if (bm_status st = read_header(d_in, in_bytes, true, s, H)) return st;
+  if (H.raw) return fail(BM_ERR_ARG, "raw stream has no codes");
+  Workspace* ws = nullptr;
+  if (bm_status st = get_ws(s, decode_scratch(H) + 4096, 4096, &ws)) return st;
+  Carver cv;
+  cv.base = reinterpret_cast<unsigned char*>(ws->d);
+  uint16_t* sym;
+  int32_t* esc;
+  Scalars* sc;
+  const uint8_t* in = reinterpret_cast<const uint8_t*>(d_in);
+  if (bm_status st = decode_symbols(in, H, cv, &sym, &esc, &sc, s)) return st;
+  codes_from_symbols_kernel<<<grid_for((int64_t)H.n_symbols, 256), 256, 0, s>>>(sym, esc, H.n_symbols, H.radius, d_codes);
+  BM_LAUNCHED();
+  BM_CUDA(cudaGetLastError());
+  return check_status(sc, s);
+}
+
+bm_status bm_huffman_encode(const uint16_t* d_symbols, uint64_t n, int dict_size, int chunk_symbols, void* d_out,
+                            size_t out_capacity, uint64_t sizes_out[5], void* stream) {
+  if (!d_symbols || !d_out || !sizes_out) return fail(BM_ERR_ARG, "NULL pointer argument");
+  if (n == 0 || n >= (uint64_t(1) << 32)) return fail(BM_ERR_ARG, "symbol count must be in [1, 2^32)");
+  if (dict_size < 2 || dict_size > kMaxDict) return fail(BM_ERR_ARG, "dict_size must be in [2, 8192]");
+  if (chunk_symbols < 64 || chunk_symbols > 8192 || chunk_symbols % 32) return fail(BM_ERR_ARG, "chunk_symbols");
+  if (reinterpret_cast<uintptr_t>(d_out) % 8) return fail(BM_ERR_ARG, "output pointer must be 8-byte aligned");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> g(g_timer_mu);
+  g_timer.begin(s);
+  const unsigned long long nch = (n + chunk_symbols - 1) / chunk_symbols;
+  const unsigned long long off_cb = pad8(4ull * nch);
+  if (off_cb > out_capacity) return fail(BM_ERR_CAPACITY, "capacity below the chunk table");
+  Carver probe;
+  probe.take<Scalars>(1); probe.take<unsigned>(dict_size); probe.take<uint8_t>(dict_size);
+  probe.take<unsigned>(dict_size); probe.take<unsigned>(nch); probe.take<unsigned long long>(nch + 1);
+  probe.take<unsigned long long>(nch + 1);
+  Workspace* ws = nullptr;
+  if (bm_status st = get_ws(s, probe.off + 4096, 4096, &ws)) return st;
+  Carver cv;
+  cv.base = reinterpret_cast<unsigned char*>(ws->d);
+  Scalars* sc = cv.take<Scalars>(1);
+  unsigned* hist = cv.take<unsigned>(dict_size);
+  uint8_t* lens = cv.take<uint8_t>(dict_size);
+  unsigned* codes = cv.take<unsigned>(dict_size);
+  unsigned* chunk_esc = cv.take<unsigned>(nch);
+  unsigned long long* word_off = cv.take<unsigned long long>(nch + 1);
+  unsigned long long* esc_off = cv.take<unsigned long long>(nch + 1);
+  uint8_t* out = reinterpret_cast<uint8_t*>(d_out);
+  BM_CUDA(cudaMemsetAsync(sc, 0, sizeof(Scalars), s));
+  BM_CUDA(cudaMemsetAsync(hist, 0, 4ull * dict_size, s));
+  BM_CUDA(cudaMemsetAsync(out, 0, off_cb, s));
+  {
+    Stage st("huffman_histogram");
+    hist_kernel<<<grid_for((int64_t)n, 256, 4), 256, 4 * dict_size, s>>>(d_symbols, n, dict_size, hist, sc);
+    BM_LAUNCHED();
+  }
+  {
+    Stage st("huffman_codebook");
+    CodebookArgs ca{hist, dict_size, lens, codes, out, off_cb, out_capacity, sc};
+    BM_CUDA(cudaFuncSetAttribute(codebook_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CbSmem)));
+    codebook_kernel<<<1, kCbThreads, sizeof(CbSmem), s>>>(ca);
+    BM_LAUNCHED();
+  }
+  {
+    Stage st("huffman_encode");
+    EncodeArgs ea{};
+    ea.sym = d_symbols; ea.esc = nullptr; ea.n = n; ea.chunk = chunk_symbols; ea.lens = lens; ea.codes = codes;
+    ea.dict = dict_size; ea.chunk_words = reinterpret_cast<unsigned*>(out); ea.chunk_esc = chunk_esc;
+    ea.word_off = word_off; ea.esc_off = esc_off; ea.nch = nch; ea.out = out; ea.sc = sc;
+    chunk_bits_kernel<8><<<grid_for((int64_t)nch * 32, 256, 16), 256, 0, s>>>(ea);
+    chunk_scan_kernel<<<1, kCbThreads, 0, s>>>(ea.chunk_words, chunk_esc, nch, word_off, esc_off, sc, off_cb, ~0ull,
+                                               out_capacity);
+    encode_kernel<8><<<grid_for((int64_t)nch * 32, 256, 16), 256, 0, s>>>(ea);
+    zero_tail_kernel<<<1, 32, 0, s>>>(out, sc);
+    g_launches.fetch_add(4);
+    BM_CUDA(cudaGetLastError());
+  }
+  Scalars* hsc = reinterpret_cast<Scalars*>(ws->h);
+  BM_CUDA(cudaMemcpyAsync(hsc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+  BM_CUDA(cudaStreamSynchronize(s));
+  if (hsc->status & ST_CORRUPT) return fail(BM_ERR_ARG, "a symbol is not below dict_size");
+  if (hsc->status & (ST_RAW | ST_CAPACITY)) return fail(BM_ERR_CAPACITY, "output capacity too small");
+  sizes_out[0] = hsc->codebook_bytes;
+  sizes_out[1] = hsc->n_runs;
+  sizes_out[2] = nch;
+  sizes_out[3] = hsc->n_words;
+  sizes_out[4] = pad8(hsc->off_bits + 4ull * hsc->n_words);
+  return BM_OK;
+}
+
+bm_status bm_huffman_decode(const void* d_section, const uint64_t sizes[5], uint64_t n, int dict_size,
+                            int chunk_symbols, uint16_t* d_symbols, void* stream) {
+  if (!d_section || !sizes || !d_symbols) return fail(BM_ERR_ARG, "NULL pointer argument");
+  if (dict_size < 2 || dict_size > kMaxDict) return fail(BM_ERR_ARG, "dict_size must be in [2, 8192]");
+  if (chunk_symbols < 64 || chunk_symbols > 8192 || chunk_symbols % 32) return fail(BM_ERR_ARG, "chunk_symbols");
+  if (reinterpret_cast<uintptr_t>(d_section) % 8) return fail(BM_ERR_ARG, "section pointer must be 8-byte aligned");
+  const unsigned long long nch = (n + chunk_symbols - 1) / chunk_symbols;
+  if (sizes[2] != nch) return fail(BM_ERR_CORRUPT, "chunk count does not match n");
+  const unsigned long long off_cb = pad8(4ull * nch), off_w = off_cb + pad8(sizes[0]);
+  if (sizes[4] < off_w + 4ull * sizes[3]) return fail(BM_ERR_CORRUPT, "section sizes inconsistent");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> g(g_timer_mu);
+  g_timer.begin(s);
+  Header H{};
+  H.n_symbols = n; H.n_chunks = nch; H.n_words = sizes[3]; H.n_outliers = 0; H.off_chunks = 0;
+  H.off_codebook = off_cb; H.off_bits = off_w; H.codebook_bytes = (unsigned)sizes[0]; H.n_runs = (unsigned)sizes[1];
+  H.radius = dict_size / 2;  // only 2*radius = dict is used by the decoder
+  H.chunk = chunk_symbols;
+  Workspace* ws = nullptr;
+  if (bm_status st = get_ws(s, decode_scratch(H) + 4096, 4096, &ws)) return st;
+  Carver cv;
+  cv.base = reinterpret_cast<unsigned char*>(ws->d);
+  uint16_t* sym;
+  int32_t* esc;
+  Scalars* sc;
+  if (dict_size & 1) return fail(BM_ERR_ARG, "dict_size must be even");
+  if (bm_status st = decode_symbols(reinterpret_cast<const uint8_t*>(d_section), H, cv, &sym, &esc, &sc, s)) return st;
+  BM_CUDA(cudaMemcpyAsync(d_symbols, sym, 2 * n, cudaMemcpyDeviceToDevice, s));
+  return check_status(sc, s);
+}
+
+void bm_release_workspace(void* stream) {
+  std::lock_guard<std::mutex> g(g_ws_mu);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  for (auto it = g_ws.begin(); it != g_ws.end();) {
+    if (stream == nullptr || it->first.second == s) {
+      int cur = 0;
+      cudaGetDevice(&cur);
+      cudaSetDevice(it->second.dev);
+      cudaStreamSynchronize(it->first.second);
+      if (it->second.d) cudaFree(it->second.d);
+      if (it->second.h) cudaFreeHost(it->second.h);
+      cudaSetDevice(cur);
+      it = g_ws.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,428 @@
+// In-cache Block kernels (Sec. III-A, III-D): one CTA keeps a B^3 block in
+// shared memory through K decomposition levels, quantises the coefficients on
+// the spot and writes only symbols (u16) and the block's coarse values.
+//
+// Level structure (Sec. II-B): for a level of N (odd) nodes per dimension
+//   Phase A  lines (i0,i1) along dim 2: coefficients d = u - I(u|C) at every
+//            node (zero at all-coarse nodes), emitted as symbols or values;
+//            then z2 = M_c^-1 I^T M_f d along the line        -> T1 (N,N,C)
+//   Phase B  lines (i0,j2) along dim 1 of T1                   -> T2 (N,C,C)
+//   Phase C  lines (j1,j2) along dim 0 of T2, coarse = u|C + z -> out (C,C,C)
+// The shrinking arrays N^3 -> N^2 C -> N C^2 -> C^3 are the paper's
+// 8x8x8 -> 5x8x8 -> 5x5x8 -> 5x5x5 sequence for the block size used.
+#pragma once
+
+#include "bm_common.cuh"
+#include "bm_internal.h"
+
+namespace bm {
+
+// __constant__ tables, one per (dtype, level size), built at compile time.
+#define BM_TAB(T, N) \
+  static __constant__ BlockLevel<T, N> c_tab_##T##_##N = make_block_level<T, N>();
+BM_TAB(float, 3)
+BM_TAB(float, 5)
+BM_TAB(float, 9)
+BM_TAB(float, 17)
+BM_TAB(double, 3)
+BM_TAB(double, 5)
+BM_TAB(double, 9)
+BM_TAB(double, 17)
+#undef BM_TAB
+
+template <typename T, int N>
+__device__ __forceinline__ const BlockLevel<T, N>& block_tab();
+#define BM_TABREF(T, N) \
+  template <>           \
+  __device__ __forceinline__ const BlockLevel<T, N>& block_tab<T, N>() { return c_tab_##T##_##N; }
+BM_TABREF(float, 3)
+BM_TABREF(float, 5)
+BM_TABREF(float, 9)
+BM_TABREF(float, 17)
+BM_TABREF(double, 3)
+BM_TABREF(double, 5)
+BM_TABREF(double, 9)
+BM_TABREF(double, 17)
+#undef BM_TABREF
+
+constexpr int lvl_n(int B, int l) { return l == 0 ? B : (lvl_n(B, l - 1) + 1) / 2; }
+constexpr int cube(int x) { return x * x * x; }
+constexpr int per_block_count(int B, int K) {
+  return K == 0 ? 0 : cube(B) - cube((B + 1) / 2) + per_block_count((B + 1) / 2, K - 1);
+}
+constexpr int lvl_offset(int B, int l) {  // first symbol of level l inside a block
+  return l == 0 ? 0 : cube(lvl_n(B, l - 1)) - cube(lvl_n(B, l)) + lvl_offset(B, l - 1);
+}
+
+template <typename T, int B, int K>
+struct BlockCfg {
+  static constexpr int NT = ((B * B + 31) / 32) * 32;
+  static constexpr int C1 = (B + 1) / 2;
+  static constexpr int C2 = (C1 + 1) / 2;
+  static constexpr int A = B * B * B;
+  static constexpr int T1 = B * B * C1;
+  static constexpr int T2 = B * C1 * C1;
+  static constexpr int CB0 = C1 * C1 * C1;
+  static constexpr int CB1 = C2 * C2 * C2;
+  static constexpr int PB = per_block_count(B, K);
+  static constexpr int M = lvl_n(B, K);
+  static constexpr size_t fwd_smem =
+      sizeof(T) * (2 * A + T1 + T2 + CB0 + CB1) + ((2 * PB + 15) / 16) * 16 + 4 * kHistWin;
+  static constexpr size_t inv_smem(int mode) {
+    return sizeof(T) * (A + T1 + T2 + CB0 + CB1) + (((mode ? sizeof(T) : 2) * PB + 15) / 16) * 16;
+  }
+};
+
+// Per-thread histogram run: consecutive equal symbols of a line are counted
+// once (the common case at loose tolerances is long runs of the zero code).
+struct HistRun {
+  unsigned sym = 0xFFFFFFFFu;
+  unsigned cnt = 0;
+};
+
+__device__ __forceinline__ void hist_add(unsigned* hloc, unsigned* hglob, int radius, unsigned s, unsigned n) {
+  const int bin = (int)s - (radius - kHistWin / 2);
+  if (bin >= 0 && bin < kHistWin) atomicAdd(hloc + bin, n);
+  else atomicAdd(hglob + s, n);
+}
+__device__ __forceinline__ void hist_push(HistRun& r, unsigned* hloc, unsigned* hglob, int radius, unsigned s) {
+  if (s == r.sym) { ++r.cnt; return; }
+  if (r.cnt) hist_add(hloc, hglob, radius, r.sym, r.cnt);
+  r.sym = s;
+  r.cnt = 1;
+}
+
+// ---------------------------------------------------------------------------
+// Forward level
+// ---------------------------------------------------------------------------
+template <typename T, int N, int MODE>
+__device__ __forceinline__ void level_fwd(const T* __restrict__ X, T* __restrict__ T1, T* __restrict__ T2,
+                                          T* __restrict__ out, const int lvl_off, const T rq, uint16_t* stage,
+                                          int32_t* __restrict__ esc_blk, T* __restrict__ coef_blk, unsigned* hloc,
+                                          unsigned* hglob, const int radius, bool& ovf) {
+  constexpr int C = (N + 1) / 2;
+  const auto& tb = block_tab<T, N>();
+  for (int L = threadIdx.x; L < N * N; L += blockDim.x) {
+    const int i0 = L / N, i1 = L - i0 * N;
+    const bool f0 = i0 & 1, f1 = i1 & 1;
+    const int lo0 = f0 ? i0 - 1 : i0, hi0 = f0 ? i0 + 1 : i0;
+    const int lo1 = f1 ? i1 - 1 : i1, hi1 = f1 ? i1 + 1 : i1;
+    const T* r00 = X + (lo0 * N + lo1) * N;
+    const T* r01 = X + (lo0 * N + hi1) * N;
+    const T* r10 = X + (hi0 * N + lo1) * N;
+    const T* r11 = X + (hi0 * N + hi1) * N;
+    T w[C];
+#pragma unroll
+    for (int J = 0; J < C; ++J) w[J] = T(0.25) * ((r00[2 * J] + r01[2 * J]) + (r10[2 * J] + r11[2 * J]));
+    T d[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const T u = X[L * N + k];
+      const T e = (k & 1) ? T(0.5) * (w[k / 2] + w[k / 2 + 1]) : w[k / 2];
+      d[k] = u - e;
+    }
+    const bool cc = !f0 && !f1;
+    const int cc_before = ((i0 + 1) / 2) * C + (f0 ? 0 : (i1 + 1) / 2);
+    const int base = lvl_off + L * N - cc_before * C;
+    HistRun run;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      if ((k & 1) || !cc) {
+        const int pos = base + (cc ? k / 2 : k);
+        if (MODE == 0) {
+          const int code = quantize(d[k], rq, ovf);
+          const bool in = code > -radius && code < radius;
+          const unsigned s = in ? (unsigned)(code + radius) : 0u;
+          stage[pos] = (uint16_t)s;
+          if (!in) esc_blk[pos] = code;
+          hist_push(run, hloc, hglob, radius, s);
+        } else {
+          coef_blk[pos] = d[k];
+        }
+      }
+    }
+    if (MODE == 0 && run.cnt) hist_add(hloc, hglob, radius, run.sym, run.cnt);
+    T z[C];
+    restrict_solve<T, N>(tb, d, z);
+#pragma unroll
+    for (int j = 0; j < C; ++j) T1[L * C + j] = z[j];
+  }
+  __syncthreads();
+  for (int L = threadIdx.x; L < N * C; L += blockDim.x) {
+    const int i0 = L / C, j2 = L - i0 * C;
+    T d[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) d[i] = T1[(i0 * N + i) * C + j2];
+    T z[C];
+    restrict_solve<T, N>(tb, d, z);
+#pragma unroll
+    for (int j = 0; j < C; ++j) T2[(i0 * C + j) * C + j2] = z[j];
+  }
+  __syncthreads();
+  for (int L = threadIdx.x; L < C * C; L += blockDim.x) {
+    const int j1 = L / C, j2 = L - j1 * C;
+    T d[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) d[i] = T2[(i * C + j1) * C + j2];
+    T z[C];
+    restrict_solve<T, N>(tb, d, z);
+#pragma unroll
+    for (int J = 0; J < C; ++J) out[(J * C + j1) * C + j2] = X[((2 * J) * N + 2 * j1) * N + 2 * j2] + z[J];
+  }
+  __syncthreads();
+}
+
+// Buffer of level output j (0 = the block itself): ping-pong between two
+// coarse buffers so a level never writes the array it reads.
+template <typename T>
+struct LevelBufs {
+  T* A;
+  T* cb0;
+  T* cb1;
+  __device__ __forceinline__ T* operator()(int j) const { return j == 0 ? A : ((j & 1) ? cb0 : cb1); }
+};
+
+template <typename T, int N, int L, int K, int B, int MODE>
+struct FwdLevels {
+  __device__ __forceinline__ static void run(const LevelBufs<T>& bufs, T* T1, T* T2, const T* rq, uint16_t* stage,
+                                             int32_t* esc_blk, T* coef_blk, unsigned* hloc, unsigned* hglob,
+                                             int radius, bool& ovf) {
+    level_fwd<T, N, MODE>(bufs(L), T1, T2, bufs(L + 1), lvl_offset(B, L), rq[L], stage, esc_blk, coef_blk, hloc,
+                          hglob, radius, ovf);
+    if constexpr (L + 1 < K)
+      FwdLevels<T, (N + 1) / 2, L + 1, K, B, MODE>::run(bufs, T1, T2, rq, stage, esc_blk, coef_blk, hloc, hglob,
+                                                         radius, ovf);
+  }
+};
+
+template <typename T, int B>
+__device__ __forceinline__ void issue_block_load(T* dst, const T* __restrict__ field, int64_t n0, int64_t n1,
+                                                 int64_t n2, int64_t b0, int64_t b1, int64_t b2) {
+  for (int e = threadIdx.x; e < B * B * B; e += blockDim.x) {
+    const int i0 = e / (B * B);
+    const int r = e - i0 * (B * B);
+    const int i1 = r / B;
+    const int k = r - i1 * B;
+    const int64_t g0 = b0 * B + i0, g1 = b1 * B + i1, g2 = b2 * B + k;
+    const bool valid = g0 < n0 && g1 < n1 && g2 < n2;
+    const T* src = valid ? field + (g0 * n1 + g1) * n2 + g2 : field;
+    cp_async_zfill<sizeof(T)>(dst + e, src, valid);
+  }
+}
+
+// Forward: persistent CTAs walk the blocks; the next block is prefetched with
+// cp.async (zero fill outside the domain) while the current one is processed.
+template <typename T, int B, int K, int MODE>
+__global__ void __launch_bounds__(BlockCfg<T, B, K>::NT) block_fwd_kernel(BlockArgs<T> a) {
+  using Cfg = BlockCfg<T, B, K>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Abuf = reinterpret_cast<T*>(smem_raw);
+  T* T1 = Abuf + 2 * Cfg::A;
+  T* T2 = T1 + Cfg::T1;
+  T* cb0 = T2 + Cfg::T2;
+  T* cb1 = cb0 + Cfg::CB0;
+  uint16_t* stage = reinterpret_cast<uint16_t*>(cb1 + Cfg::CB1);
+  unsigned* hloc = reinterpret_cast<unsigned*>(reinterpret_cast<unsigned char*>(stage) + ((2 * Cfg::PB + 15) / 16) * 16);
+
+  if (MODE == 0)
+    for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) hloc[i] = 0;
+  bool ovf = false;
+  const int64_t nbc = (int64_t)a.nb1 * a.nb2;
+  int64_t b = blockIdx.x;
+  int buf = 0;
+  if (b < a.nblocks)
+    issue_block_load<T, B>(Abuf, a.field, a.n0, a.n1, a.n2, b / nbc, (b / a.nb2) % a.nb1, b % a.nb2);
+  cp_async_commit();
+  for (; b < a.nblocks; b += gridDim.x) {
+    const int64_t nx = b + gridDim.x;
+    if (nx < a.nblocks)
+      issue_block_load<T, B>(Abuf + (buf ^ 1) * Cfg::A, a.field, a.n0, a.n1, a.n2, nx / nbc, (nx / a.nb2) % a.nb1,
+                             nx % a.nb2);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+
+    T rq[K];
+    const int tier = a.tier ? a.tier[b] : 0;
+#pragma unroll
+    for (int l = 0; l < K; ++l) rq[l] = MODE == 0 ? a.rq[tier * K + l] : T(0);
+    const int64_t sbase = b * (int64_t)Cfg::PB;
+    LevelBufs<T> bufs{Abuf + buf * Cfg::A, cb0, cb1};
+    FwdLevels<T, B, 0, K, B, MODE>::run(bufs, T1, T2, rq, stage, a.esc + (MODE == 0 ? sbase : 0),
+                                        a.coef + (MODE == 1 ? sbase : 0), hloc, a.hist, a.radius, ovf);
+    // block coarse values -> gathered grid G
+    {
+      constexpr int M = Cfg::M;
+      const T* cf = bufs(K);
+      const int64_t b0 = b / nbc, b1 = (b / a.nb2) % a.nb1, b2 = b % a.nb2;
+      for (int e = threadIdx.x; e < M * M * M; e += blockDim.x) {
+        const int j0 = e / (M * M), r = e - j0 * M * M, j1 = r / M, j2 = r - j1 * M;
+        a.G[((b0 * M + j0) * a.g1 + (b1 * M + j1)) * a.g2 + (b2 * M + j2)] = cf[e];
+      }
+    }
+    if (MODE == 0) {
+      uint16_t* dst = a.sym + sbase;
+      if (((sbase & 1) == 0)) {
+        const uint32_t* s32 = reinterpret_cast<const uint32_t*>(stage);
+        uint32_t* d32 = reinterpret_cast<uint32_t*>(dst);
+        for (int i = threadIdx.x; i < Cfg::PB / 2; i += blockDim.x) d32[i] = s32[i];
+        if ((Cfg::PB & 1) && threadIdx.x == 0) dst[Cfg::PB - 1] = stage[Cfg::PB - 1];
+      } else {
+        for (int i = threadIdx.x; i < Cfg::PB; i += blockDim.x) dst[i] = stage[i];
+      }
+    }
+    __syncthreads();
+    buf ^= 1;
+  }
+  cp_async_wait<0>();
+  if (MODE == 0) {
+    if (ovf) atomicOr(&a.sc->status, ST_OVERFLOW);
+    __syncthreads();
+    const int lo = a.radius - kHistWin / 2;
+    for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) {
+      const unsigned v = hloc[i];
+      if (v && lo + i >= 0 && lo + i < 2 * a.radius) atomicAdd(a.hist + lo + i, v);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Inverse level: coarse values `cin` (C^3) and the level's coefficients give
+// the N^3 values in X.  z = P D (three passes), u|C = c - z, u = I u|C + D.
+// ---------------------------------------------------------------------------
+template <typename T, int N, int MODE>
+__device__ __forceinline__ void level_inv(T* __restrict__ X, T* __restrict__ T1, T* __restrict__ T2,
+                                          T* __restrict__ cin, const int lvl_off, const T q,
+                                          const void* stage, const int32_t* __restrict__ esc_blk, const int radius) {
+  constexpr int C = (N + 1) / 2;
+  const auto& tb = block_tab<T, N>();
+  for (int L = threadIdx.x; L < N * N; L += blockDim.x) {
+    const int i0 = L / N, i1 = L - i0 * N;
+    const bool f0 = i0 & 1, f1 = i1 & 1;
+    const bool cc = !f0 && !f1;
+    const int cc_before = ((i0 + 1) / 2) * C + (f0 ? 0 : (i1 + 1) / 2);
+    const int base = lvl_off + L * N - cc_before * C;
+    T d[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      T v = T(0);
+      if ((k & 1) || !cc) {
+        const int pos = base + (cc ? k / 2 : k);
+        if (MODE == 0) {
+          const unsigned s = reinterpret_cast<const uint16_t*>(stage)[pos];
+          const int code = s ? (int)s - radius : esc_blk[pos];
+          v = dequant(code, q);
+        } else {
+          v = reinterpret_cast<const T*>(stage)[pos];
+        }
+      }
+      d[k] = v;
+      X[L * N + k] = v;
+    }
+    T z[C];
+    restrict_solve<T, N>(tb, d, z);
+#pragma unroll
+    for (int j = 0; j < C; ++j) T1[L * C + j] = z[j];
+  }
+  __syncthreads();
+  for (int L = threadIdx.x; L < N * C; L += blockDim.x) {
+    const int i0 = L / C, j2 = L - i0 * C;
+    T d[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) d[i] = T1[(i0 * N + i) * C + j2];
+    T z[C];
+    restrict_solve<T, N>(tb, d, z);
+#pragma unroll
+    for (int j = 0; j < C; ++j) T2[(i0 * C + j) * C + j2] = z[j];
+  }
+  __syncthreads();
+  for (int L = threadIdx.x; L < C * C; L += blockDim.x) {
+    const int j1 = L / C, j2 = L - j1 * C;
+    T d[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) d[i] = T2[(i * C + j1) * C + j2];
+    T z[C];
+    restrict_solve<T, N>(tb, d, z);
+#pragma unroll
+    for (int J = 0; J < C; ++J) cin[(J * C + j1) * C + j2] -= z[J];
+  }
+  __syncthreads();
+  for (int L = threadIdx.x; L < N * N; L += blockDim.x) {
+    const int i0 = L / N, i1 = L - i0 * N;
+    const int a0 = i0 >> 1, b0 = (i0 + 1) >> 1, a1 = i1 >> 1, b1 = (i1 + 1) >> 1;
+    const T* r00 = cin + (a0 * C + a1) * C;
+    const T* r01 = cin + (a0 * C + b1) * C;
+    const T* r10 = cin + (b0 * C + a1) * C;
+    const T* r11 = cin + (b0 * C + b1) * C;
+    T w[C];
+#pragma unroll
+    for (int J = 0; J < C; ++J) w[J] = T(0.25) * ((r00[J] + r01[J]) + (r10[J] + r11[J]));
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const T e = (k & 1) ? T(0.5) * (w[k / 2] + w[k / 2 + 1]) : w[k / 2];
+      X[L * N + k] = e + X[L * N + k];
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T, int N, int L, int B, int MODE>
+struct InvLevels {  // recompose levels L, L-1, ..., 0 (level L has N nodes)
+  __device__ __forceinline__ static void run(const LevelBufs<T>& bufs, T* T1, T* T2, const double* q, int K,
+                                             const void* stage, const int32_t* esc_blk, int radius) {
+    const T qv = MODE == 0 ? (T)q[L] : T(0);
+    level_inv<T, N, MODE>(bufs(L), T1, T2, bufs(L + 1), lvl_offset(B, L), qv, stage, esc_blk, radius);
+    if constexpr (L > 0) InvLevels<T, 2 * N - 1, L - 1, B, MODE>::run(bufs, T1, T2, q, K, stage, esc_blk, radius);
+  }
+};
+
+template <typename T, int B, int K, int MODE>
+__global__ void __launch_bounds__(BlockCfg<T, B, K>::NT) block_inv_kernel(BlockArgs<T> a) {
+  using Cfg = BlockCfg<T, B, K>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* A = reinterpret_cast<T*>(smem_raw);
+  T* T1 = A + Cfg::A;
+  T* T2 = T1 + Cfg::T1;
+  T* cb0 = T2 + Cfg::T2;
+  T* cb1 = cb0 + Cfg::CB0;
+  void* stage = cb1 + Cfg::CB1;
+  const int64_t nbc = (int64_t)a.nb1 * a.nb2;
+  LevelBufs<T> bufs{A, cb0, cb1};
+  constexpr int M = Cfg::M;
+  for (int64_t b = blockIdx.x; b < a.nblocks; b += gridDim.x) {
+    const int64_t b0 = b / nbc, b1 = (b / a.nb2) % a.nb1, b2 = b % a.nb2;
+    const int64_t sbase = b * (int64_t)Cfg::PB;
+    if (MODE == 0) {
+      uint16_t* st = reinterpret_cast<uint16_t*>(stage);
+      const uint16_t* src = a.sym + sbase;
+      if ((sbase & 1) == 0) {
+        const uint32_t* s32 = reinterpret_cast<const uint32_t*>(src);
+        uint32_t* d32 = reinterpret_cast<uint32_t*>(st);
+        for (int i = threadIdx.x; i < Cfg::PB / 2; i += blockDim.x) d32[i] = __ldg(s32 + i);
+        if ((Cfg::PB & 1) && threadIdx.x == 0) st[Cfg::PB - 1] = src[Cfg::PB - 1];
+      } else {
+        for (int i = threadIdx.x; i < Cfg::PB; i += blockDim.x) st[i] = src[i];
+      }
+    } else {
+      T* st = reinterpret_cast<T*>(stage);
+      for (int i = threadIdx.x; i < Cfg::PB; i += blockDim.x) st[i] = a.coef[sbase + i];
+    }
+    T* cf = bufs(K);
+    for (int e = threadIdx.x; e < M * M * M; e += blockDim.x) {
+      const int j0 = e / (M * M), r = e - j0 * M * M, j1 = r / M, j2 = r - j1 * M;
+      cf[e] = a.G[((b0 * M + j0) * a.g1 + (b1 * M + j1)) * a.g2 + (b2 * M + j2)];
+    }
+    __syncthreads();
+    const int tier = (MODE == 0 && a.tier) ? a.tier[b] : 0;
+    InvLevels<T, M * 2 - 1, K - 1, B, MODE>::run(bufs, T1, T2, a.q + tier * K, K, stage,
+                                                  MODE == 0 ? a.esc + sbase : nullptr, a.radius);
+    for (int e = threadIdx.x; e < B * B * B; e += blockDim.x) {
+      const int i0 = e / (B * B), r = e - i0 * (B * B), i1 = r / B, k = r - i1 * B;
+      const int64_t g0 = b0 * B + i0, g1 = b1 * B + i1, g2 = b2 * B + k;
+      if (g0 < a.n0 && g1 < a.n1 && g2 < a.n2) a.field[(g0 * a.n1 + g1) * a.n2 + g2] = A[e];
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace bm

@@ -1,0 +1,15 @@
+// In-cache Block kernels instantiated for double fields and 9-node blocks.
+#include "bm_block_launch.cuh"
+
+namespace bm {
+
+cudaError_t launch_block_f64_b9(int dir, int K, int mode, const BlockArgs<double>& a, cudaStream_t s, int nsm) {
+  switch (K) {
+    case 1: return launch_mode<double, 9, 1>(dir, mode, a, s, nsm);
+    case 2: return launch_mode<double, 9, 2>(dir, mode, a, s, nsm);
+    case 3: return launch_mode<double, 9, 3>(dir, mode, a, s, nsm);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace bm

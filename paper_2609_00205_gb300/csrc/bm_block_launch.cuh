@@ -1,0 +1,33 @@
+// Launch helpers of the In-cache Block kernels for one (dtype, block size).
+#pragma once
+
+#include "bm_block.cuh"
+#include "bm_internal.h"
+
+namespace bm {
+
+template <typename T, int B, int K, int MODE>
+cudaError_t launch_one(int dir, const BlockArgs<T>& a, cudaStream_t s, int nsm) {
+  using Cfg = BlockCfg<T, B, K>;
+  const void* fn = dir == 0 ? (const void*)block_fwd_kernel<T, B, K, MODE> : (const void*)block_inv_kernel<T, B, K, MODE>;
+  const size_t smem = dir == 0 ? Cfg::fwd_smem : Cfg::inv_smem(MODE);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, Cfg::NT, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int64_t grid = (int64_t)per_sm * nsm;
+  if (grid > a.nblocks) grid = a.nblocks;
+  if (grid < 1) return cudaSuccess;
+  if (dir == 0) block_fwd_kernel<T, B, K, MODE><<<(unsigned)grid, Cfg::NT, smem, s>>>(a);
+  else block_inv_kernel<T, B, K, MODE><<<(unsigned)grid, Cfg::NT, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int B, int K>
+cudaError_t launch_mode(int dir, int mode, const BlockArgs<T>& a, cudaStream_t s, int nsm) {
+  return mode == 0 ? launch_one<T, B, K, 0>(dir, a, s, nsm) : launch_one<T, B, K, 1>(dir, a, s, nsm);
+}
+
+}  // namespace bm

@@ -1,0 +1,41 @@
+// Host-side plan of one hierarchy: sizes, stream-order offsets, the tables of
+// the global levels and the level error constants.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace bm {
+
+// One dimension of one global level, in double precision (converted to the
+// field's dtype when uploaded).
+struct Dim1DHost {
+  int n = 0, c = 0;
+  std::vector<double> x;       // node coordinates
+  std::vector<int> cidx, jlo, jhi, cb, f0;
+  std::vector<uint8_t> isc;
+  std::vector<double> wl, wr;  // interpolation weights
+  std::vector<double> band;    // [5c] rows of I^T M_f
+  std::vector<double> tm, tib, tsup;  // Thomas factors of M_c
+};
+
+struct PlanHost {
+  int64_t shape[3];
+  int B, K, M;
+  int nb[3];
+  int64_t nblocks;
+  int m;                 // coarse nodes per block edge after K levels
+  int64_t per_block;
+  int64_t gshape[3];     // gathered grid
+  std::vector<int64_t> lshape;  // [3*(M+1)]: grid of global level l (l = 0 is G), last = coarsest
+  std::vector<int64_t> sym_off; // [M+2]: first symbol of global level l; sym_off[M] = coarsest
+  int64_t n_coeffs;
+  std::vector<std::vector<Dim1DHost>> glev;  // [M][3]
+  std::vector<double> A;  // level error constants: local 1..K then global 1..M (rounded)
+};
+
+// Builds the plan; returns an empty string on success, else a message.
+std::string make_plan(const int64_t* shape, int B, int K, int M, PlanHost& p);
+
+}  // namespace bm

@@ -1,0 +1,218 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars (per the workload statement): coefficients within 1e-5 (FP32) / 1e-12
+(FP64) of max|u|; codes identical except +-1 flips explained by a coefficient
+sitting within the coefficient tolerance of a bin edge (counted); Huffman
+codebook and bitstream bit-exact given identical symbols; the L-inf bound
+holds at every node of every region.
+"""
+import numpy as np
+import pytest
+import torch
+
+import fields
+import oracle
+
+from _util import classify_flips, per_block_tau, q_per_coeff
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+# (name, shape, dtype, B, K, M): sizes the oracle finishes in seconds, spanning
+# several blocks with ragged tails
+CASES = [
+    ("bumps65_b9k3", (65, 65, 65), np.float32, 9, 3, 0),
+    ("grf_b17k2m2", (70, 61, 53), np.float32, 17, 2, 2),
+    ("grf_b9k1m3", (37, 29, 44), np.float32, 9, 1, 3),
+    ("roi_f64_b9k2m2", (47, 41, 33), np.float64, 9, 2, 2),
+    ("f64_b17k3m1", (35, 18, 40), np.float64, 17, 3, 1),
+    ("tiny_2x3x2", (2, 3, 2), np.float32, 9, 1, 1),
+]
+
+
+@pytest.fixture(scope="module")
+def bm():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2609_00205_gb300 as m
+
+    return m
+
+
+def _field(name, shape, dtype):
+    if name.startswith("bumps"):
+        u = fields.gaussian_bumps(shape, seed=1)
+    elif name.startswith("roi"):
+        u = fields.roi_field(shape, seed=3).numpy()
+    else:
+        u = fields.power_law_grf(shape, seed=2).numpy()
+    return np.ascontiguousarray(u.astype(dtype))
+
+
+def _coef_tol(u):
+    return (1e-5 if u.dtype == np.float32 else 1e-12) * float(np.abs(u).max())
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_decompose_matches_oracle(bm, case):
+    name, shape, dt, B, K, M = case
+    u = _field(name, shape, dt)
+    g = bm.decompose(torch.from_numpy(u).to(DEV), block=B, levels=K, global_levels=M).cpu().numpy()
+    o = oracle.decompose(u.astype(np.float64), B, K, M)
+    assert g.shape == o.shape
+    err = np.abs(g.astype(np.float64) - o).max()
+    assert err <= _coef_tol(u), err
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_recompose_matches_oracle(bm, case):
+    """GPU recomposition of the oracle's coefficients equals the oracle's."""
+    name, shape, dt, B, K, M = case
+    u = _field(name, shape, dt)
+    o = oracle.decompose(u.astype(np.float64), B, K, M)
+    g = bm.recompose(torch.from_numpy(o.astype(dt)).to(DEV), shape, block=B, levels=K, global_levels=M).cpu().numpy()
+    r = oracle.recompose(o.astype(dt).astype(np.float64), shape, B, K, M)
+    assert np.abs(g.astype(np.float64) - r).max() <= 4 * _coef_tol(u)
+    # and it inverts the decomposition
+    assert np.abs(g.astype(np.float64) - u).max() <= 8 * _coef_tol(u)
+
+
+@pytest.mark.parametrize("tol", [1e-2, 1e-4])
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_compress_parity(bm, case, tol):
+    name, shape, dt, B, K, M = case
+    u = _field(name, shape, dt)
+    f64 = dt == np.float64
+    roi = None
+    if name.startswith("roi"):
+        mask = fields.gradient_roi(u, B)
+        roi = np.where(mask, tol * 1e-2, tol)
+    t = torch.from_numpy(u).to(DEV)
+    sg = bm.compress(t, tol, mode="rel", roi=roi, block=B, levels=K, global_levels=M).cpu().numpy()
+    so, co = oracle.compress(u, tol, rel=True, roi=roi, B=B, K=K, M=M, want_codes=True)
+    hg, ho = oracle.stream_header(sg), oracle.stream_header(so)
+    assert hg["raw"] == ho["raw"]
+    # the L-inf bound at every node of every region (GPU decode of the GPU stream)
+    d = bm.decompress(torch.from_numpy(sg).to(DEV)).cpu().numpy().astype(np.float64)
+    tau = per_block_tau(sg, shape, B) if not hg["raw"] else 0.0
+    assert np.all(np.abs(d - u) <= tau)
+    if hg["raw"]:
+        np.testing.assert_array_equal(sg, so)
+        return
+    for k in ["K", "M", "chunk", "radius", "n_tiers", "m", "nb", "n_symbols", "n_chunks", "max_abs", "margin",
+              "off_tiers", "off_qtab", "off_blocktier", "off_chunks"]:
+        assert hg[k] == ho[k], k
+    # q table and tiers bit-exact
+    a, b = ho["off_tiers"], ho["off_chunks"]
+    np.testing.assert_array_equal(sg[a:b], so[a:b])
+    # codes: identical except explained +-1 flips
+    cg = bm.stream_codes(torch.from_numpy(sg).to(DEV)).cpu().numpy()
+    coef = oracle.decompose(u.astype(np.float64), B, K, M)
+    q = q_per_coeff(so)
+    nflip, nwin, bad = classify_flips(cg, co, coef, q, _coef_tol(u))
+    assert bad == 0, (nflip, nwin, bad)
+    if nflip == 0:
+        np.testing.assert_array_equal(sg, so)  # whole stream bit-exact
+    if f64:
+        assert nflip <= 2
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_gpu_decodes_oracle_stream(bm, case):
+    """The GPU decoder reproduces the oracle's decompression of the oracle's stream."""
+    name, shape, dt, B, K, M = case
+    u = _field(name, shape, dt)
+    so = oracle.compress(u, 1e-3, rel=True, B=B, K=K, M=M)
+    do = oracle.decompress(so).astype(np.float64)
+    st = torch.from_numpy(so).to(DEV)
+    dg = bm.decompress(st).cpu().numpy().astype(np.float64)
+    assert np.abs(dg - do).max() <= 8 * _coef_tol(u)
+    if not oracle.stream_header(so)["raw"]:
+        _, codes = oracle.decompress(so, want_codes=True)
+        np.testing.assert_array_equal(bm.stream_codes(st).cpu().numpy(), codes)
+
+
+@pytest.mark.parametrize("scale,esc,chunk,dict_size", [
+    (0.3, 0.0, 2048, 8192), (5.0, 0.001, 1024, 8192), (300.0, 0.01, 4096, 8192), (0.0, 0.0, 64, 64),
+    (40.0, 0.0, 8192, 1024), (2000.0, 0.0, 2048, 8192),
+])
+def test_huffman_bit_exact(bm, scale, esc, chunk, dict_size):
+    sym = fields.laplace_symbols(300_007, dict_size // 2, scale, seed=17, escape_rate=esc)
+    so, mo = oracle.huffman_encode(sym, dict_size, chunk)
+    t = torch.from_numpy(sym.view(np.int16)).to(DEV)
+    sg, mg = bm.huffman_encode(t, dict_size, chunk)
+    assert mg == mo
+    np.testing.assert_array_equal(sg.cpu().numpy(), so)
+    back = bm.huffman_decode(sg, mg, sym.size, dict_size, chunk).cpu().numpy().view(np.uint16)
+    np.testing.assert_array_equal(back, sym)
+
+
+def test_huffman_single_symbol(bm):
+    sym = np.full(5000, 77, dtype=np.uint16)
+    so, mo = oracle.huffman_encode(sym, 128, 256)
+    sg, mg = bm.huffman_encode(torch.from_numpy(sym.view(np.int16)).to(DEV), 128, 256)
+    assert mg == mo
+    np.testing.assert_array_equal(sg.cpu().numpy(), so)
+
+
+def test_raw_fallbacks(bm):
+    u = fields.gaussian_bumps((20, 21, 22), seed=4)
+    u[3, 4, 5] = np.nan
+    sg = bm.compress(torch.from_numpy(u).to(DEV), 1e-2, block=9, levels=2, global_levels=1).cpu().numpy()
+    np.testing.assert_array_equal(sg, oracle.compress(u, 1e-2, rel=True, B=9, K=2, M=1))
+    d = bm.decompress(torch.from_numpy(sg).to(DEV)).cpu().numpy()
+    np.testing.assert_array_equal(d.view(np.uint32), u.view(np.uint32))
+    v = fields.gaussian_bumps((20, 21, 22), seed=4)
+    sg = bm.compress(torch.from_numpy(v).to(DEV), 1e-7, block=9, levels=2, global_levels=1).cpu().numpy()
+    assert oracle.stream_header(sg)["raw"]
+    np.testing.assert_array_equal(sg, oracle.compress(v, 1e-7, rel=True, B=9, K=2, M=1))
+
+
+def test_corrupt_streams_rejected(bm):
+    u = fields.gaussian_bumps((30, 30, 30), seed=5)
+    s = bm.compress(torch.from_numpy(u).to(DEV), 1e-3, block=9, levels=2, global_levels=1)
+    good = s.clone()
+    with pytest.raises(bm.BlockMGARDError) as e:
+        bm.decompress(good[:-8].clone())
+    assert e.value.status == 4
+    bad = good.clone()
+    bad[0] ^= 0x55
+    with pytest.raises(bm.BlockMGARDError):
+        bm.decompress(bad)
+    # chunk word counts no longer add up to the bitstream length
+    h = oracle.stream_header(good.cpu().numpy())
+    bad = good.clone()
+    bad[h["off_chunks"]] = (int(bad[h["off_chunks"]]) + 1) % 256
+    with pytest.raises(bm.BlockMGARDError) as e:
+        bm.decompress(bad)
+    assert e.value.status == 4
+    # random bit flips inside the bitstream: either detected or decoded, never a fault
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        bad = good.clone()
+        pos = int(rng.integers(h["off_bits"], h["off_outliers"]))
+        bad[pos] ^= 0x10
+        try:
+            bm.decompress(bad)
+        except bm.BlockMGARDError as err:
+            assert err.status == 4
+    torch.cuda.synchronize()
+    # the context is still usable
+    d = bm.decompress(good).cpu().numpy()
+    assert np.abs(d - u).max() <= 1e-3 * np.abs(u).max()
+
+
+def test_invalid_arguments(bm):
+    t = torch.zeros((10, 10, 10), device=DEV)
+    with pytest.raises(bm.BlockMGARDError) as e:
+        bm.compress(t, -1.0)
+    assert e.value.status == 1
+    with pytest.raises(bm.BlockMGARDError) as e:
+        bm.compress(t, 1e-3, block=8)
+    assert e.value.status == 5
+    with pytest.raises(bm.BlockMGARDError):
+        bm.compress(t, 1e-3, block=9, levels=4)
+    with pytest.raises(bm.BlockMGARDError):
+        bm.compress(t, 1e-3, chunk=100)
