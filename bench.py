@@ -1,0 +1,364 @@
+"""Throughput benchmark of the BlockMGARD GPU path (one JSON line on stdout).
+
+Workload: one 513^3 FP32 Gaussian random field with a k^-5/3 power spectrum
+(unit variance, seeded), hybrid hierarchy with 17^3-node In-cache Blocks,
+K = 2 in-cache levels and M = 2 global levels, uniform relative L-inf
+tolerances 1e-2, 1e-3, 1e-4, 1e-5.  A step compresses the field once at each
+of the four tolerances; `value` is input bytes of the step / step time
+(compress GB/s over the sweep).  Decompression is timed the same way and
+reported beside it, with the compression ratio and the L-inf check of every
+tolerance.  The field (540 MB) is larger than the L2 cache, so no flush is
+needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank compresses its own field (seed + rank): the
+problems are independent, there is no collective on the data path, scaling
+is weak and `value` is the sum over ranks of bytes / the max over ranks of
+time.  `--impl reference` times the CPU oracle on a bounded sample of the
+same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SHAPE = (513, 513, 513)
+TOLS = (1e-2, 1e-3, 1e-4, 1e-5)
+PARAMS = dict(block=17, levels=2, global_levels=2)
+METRIC = "compress/decompress GB/s on 1 GB300, fraction of HBM peak, CR at L-inf bound"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    """CPU oracle (FP64 C++, one thread) on a bounded sample of the workload."""
+    import numpy as np
+
+    import fields
+    import oracle
+
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    n = args.ref_edge
+    u = fields.power_law_grf((513, 513, 513), seed=2).numpy()[:n, :n, :n].copy()
+    oracle.build()
+    times = []
+    crs = {}
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for tol in TOLS:
+            s = oracle.compress(u, tol, rel=True, B=PARAMS["block"], K=PARAMS["levels"], M=PARAMS["global_levels"])
+            crs[tol] = u.nbytes / s.size
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    bytes_step = u.nbytes * len(TOLS)
+    sec = statistics.median(times)
+    value = bytes_step / sec / 1e9
+    sample = "%dx%dx%d corner of the 513^3 field (seed 2), %d tolerances per step" % (n, n, n, len(TOLS))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "grf513_f32_b17k2m2_tolsweep", "shape": [513, 513, 513], "sample_shape": [n, n, n],
+                   "B": PARAMS["block"], "K": PARAMS["levels"], "M": PARAMS["global_levels"], "tols": list(TOLS),
+                   "tol_mode": "relative to max|u|"},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "cr": {str(k): v for k, v in crs.items()},
+    }
+    print(json.dumps(line))
+
+
+def cpu_baseline(u_np, edge):
+    import oracle
+
+    sub = u_np[:edge, :edge, :edge].copy()
+    oracle.build()
+    t0 = time.perf_counter()
+    for tol in TOLS:
+        oracle.compress(sub, tol, rel=True, B=PARAMS["block"], K=PARAMS["levels"], M=PARAMS["global_levels"])
+    dt = time.perf_counter() - t0
+    return {"value": sub.nbytes * len(TOLS) / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": "%dx%dx%d corner of the same field, compressed at the %d tolerances (%.1f s)"
+                      % (edge, edge, edge, len(TOLS), dt)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--ref-edge", type=int, default=102)
+    ap.add_argument("--cpu-edge", type=int, default=221)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--edge", type=int, default=513, help="field edge (513 = the workload; smaller for profiling)")
+    ap.add_argument("--quick", action="store_true", help="compress steps only (profiling runs)")
+    args = ap.parse_args()
+    global SHAPE
+    SHAPE = (args.edge,) * 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import fields
+    import paper_2609_00205_gb300 as bm
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    bm.load()
+    stream = torch.cuda.current_stream(dev)
+
+    u = fields.power_law_grf(SHAPE, seed=2 + rank, dtype=torch.float32, device=dev).contiguous()
+    nbytes = u.numel() * 4
+    cap = bm.compress_bound(SHAPE, torch.float32)
+    bufs = [torch.empty(cap, dtype=torch.uint8, device=dev) for _ in TOLS]
+    out_field = torch.empty_like(u)
+    maxabs = float(u.abs().max())
+
+    def compress_all(timing=False):
+        res = []
+        for tol, b in zip(TOLS, bufs):
+            s = bm.compress(u, tol, mode="rel", out=b, **PARAMS)
+            st = bm.stage_times() if timing else None
+            res.append((s, st))
+        return res
+
+    # correctness of what is timed: L-inf bound at every tolerance
+    checks = {}
+    for (s, _), tol in zip(compress_all(), TOLS):
+        d = bm.decompress(s, out=out_field)
+        err = float((d - u).abs().max())
+        checks[tol] = {"cr": nbytes / s.numel(), "max_err_rel": err / maxabs, "bound_ok": err <= tol * maxabs}
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        compress_all()
+    bm.set_timing(True)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = bm.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stage_ms = {}
+    ev0.record(stream)
+    for _ in range(args.steps):
+        for (s, st) in compress_all(timing=True):
+            for name, ms in st:
+                stage_ms.setdefault(name, []).append(ms)
+    ev1.record(stream)
+    barrier()
+    launches = bm.launch_count() - l0
+    clk = clocks.stop()
+    bm.set_timing(False)
+    comp_ms = ev0.elapsed_time(ev1) / args.steps
+    if ws > 1:
+        t = torch.tensor([comp_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        comp_ms = float(t)
+    value = ws * nbytes * len(TOLS) / (comp_ms * 1e-3) / 1e9
+
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+                              "warmup": args.warmup, "ms_per_step": comp_ms, "quick": True,
+                              "config": {"shape": list(SHAPE)},
+                              "stage_ms": {k: statistics.mean(v) for k, v in stage_ms.items()},
+                              "gpu_launches": launches, "clocks": clk}))
+        return
+    # decompression, same protocol
+    streams = [s for s, _ in compress_all()]
+    for _ in range(args.warmup):
+        for s in streams:
+            bm.decompress(s, out=out_field)
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        for s in streams:
+            bm.decompress(s, out=out_field)
+    ev1.record(stream)
+    barrier()
+    decomp_ms = ev0.elapsed_time(ev1) / args.steps
+    decomp_gbs = ws * nbytes * len(TOLS) / (decomp_ms * 1e-3) / 1e9
+
+    # per tolerance throughput (single compress / decompress)
+    per_tol = {}
+    for tol, b in zip(TOLS, bufs):
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            s = bm.compress(u, tol, mode="rel", out=b, **PARAMS)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        c_ms = e0.elapsed_time(e1) / 3
+        e0.record(stream)
+        for _ in range(3):
+            bm.decompress(s, out=out_field)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        d_ms = e0.elapsed_time(e1) / 3
+        per_tol[str(tol)] = {"compress_gbs": nbytes / c_ms / 1e6, "decompress_gbs": nbytes / d_ms / 1e6,
+                             "cr": checks[tol]["cr"], "max_err_rel": checks[tol]["max_err_rel"],
+                             "bound_ok": checks[tol]["bound_ok"]}
+
+    # end to end through the C ABI with host buffers: pinned H2D of the field,
+    # compress at every tolerance, D2H of every stream
+    host_in = torch.empty(SHAPE, dtype=torch.float32, pin_memory=True)
+    host_in.copy_(u.cpu())
+    host_out = [torch.empty(cap, dtype=torch.uint8, pin_memory=True) for _ in TOLS]
+    dev_in = torch.empty_like(u)
+    e2e_steps = max(2, args.steps // 2)
+    d2h = 0
+    barrier()
+    ev0.record(stream)
+    for _ in range(e2e_steps):
+        dev_in.copy_(host_in, non_blocking=True)
+        d2h = 0
+        for tol, b, ho in zip(TOLS, bufs, host_out):
+            s = bm.compress(dev_in, tol, mode="rel", out=b, **PARAMS)
+            ho[: s.numel()].copy_(s, non_blocking=True)
+            d2h += s.numel()
+    ev1.record(stream)
+    barrier()
+    e2e_ms = ev0.elapsed_time(ev1) / e2e_steps
+    e2e = {"value": ws * nbytes * len(TOLS) / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
+           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": d2h}
+
+    # roofline of the dominant kernel (fused In-cache Block decompose + quantise)
+    peak, peak_kind = _peaks()
+    k_ms = statistics.mean(stage_ms.get("incache_decompose", [float("nan")]))
+    nb = [-(-n // PARAMS["block"]) for n in SHAPE]
+    nblocks = nb[0] * nb[1] * nb[2]
+    per_block = 17 ** 3 - 9 ** 3 + 9 ** 3 - 5 ** 3   # coefficients of the two in-cache levels
+    g_vals = nblocks * 5 ** 3                          # block-coarse values handed to the global levels
+    alg_bytes = nbytes + 2 * nblocks * per_block + 4 * g_vals
+    achieved = alg_bytes / (k_ms * 1e-3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "incache_decompose_grf513.json")
+    if os.path.exists(prof):
+        try:
+            with open(prof) as f:
+                traffic = json.load(f).get("traffic_bytes_per_launch")
+        except Exception:
+            traffic = None
+    stage_avg = {k: statistics.mean(v) for k, v in stage_ms.items()}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": comp_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "grf513_f32_b17k2m2_tolsweep", "shape": list(SHAPE), "B": 17, "K": 2, "M": 2,
+                       "tols": list(TOLS), "tol_mode": "relative to max|u|", "spectrum": "k^-5/3",
+                       "l2": "input 540 MB > 129 MB L2, no flush", "step": "compress at each of the 4 tolerances"},
+            "decompress": {"value": decomp_gbs, "unit": "GB/s", "ms_per_step": decomp_ms},
+            "per_tol": per_tol,
+            "roofline": {"bound": "hbm", "kernel": "block_fwd_kernel<float,17,2,0> (incache_decompose)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": peak_kind, "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
+                         "ms_per_launch": k_ms},
+            "stage_ms": stage_avg,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(u.cpu().numpy(), args.cpu_edge)
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

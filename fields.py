@@ -10,9 +10,11 @@ Hurricane ISABEL, SCALE-LETKF, Miranda, S3D; Table I), which are not available
 here.  Shapes, dtypes and value structure follow the workloads below:
 
 * ``gaussian_bumps``   65^3 FP32: sum of 8 Gaussian bumps + N(0, 1e-3) noise.
-* ``power_law_grf``    Gaussian random field with |u_hat(k)|^2 ~ k^p (p = -5/3
-                       for the 513^3 FP32 hybrid workload, p = -3 for the ROI
-                       background), unit variance.
+* ``power_law_grf``    Gaussian random field whose shell-integrated power
+                       spectrum is E(k) ~ k^p (p = -5/3, the Kolmogorov
+                       spectrum, for the 513^3 FP32 hybrid workload; p = -3 for
+                       the ROI background), i.e. |u_hat(k)|^2 ~ k^(p-2) in 3-D;
+                       unit variance.
 * ``roi_field``        385x385x257 FP64: k^-3 GRF + 12 tanh fronts + 6 vortex tubes.
 * ``gradient_roi``     per-block ROI: blocks whose max |grad u| exceeds the 95th
                        percentile of the pointwise |grad u|.
@@ -47,7 +49,8 @@ def gaussian_bumps(shape=(65, 65, 65), seed: int = 1, n_bumps: int = 8,
 
 
 def _wavenumber_amplitude(shape, exponent, device):
-    """|k|^(exponent/2) on the rfft grid (k in integer-index units), 0 at k=0."""
+    """|k|^(exponent/2) on the rfft grid (k in integer-index units), 0 at k=0;
+    ``exponent`` is that of the modal spectrum |u_hat(k)|^2."""
     ks = []
     for d, n in enumerate(shape):
         if d == len(shape) - 1:
@@ -67,7 +70,8 @@ def _wavenumber_amplitude(shape, exponent, device):
 
 def power_law_grf(shape, exponent: float = -5.0 / 3.0, seed: int = 2,
                   dtype=torch.float32, device="cpu") -> torch.Tensor:
-    """Gaussian random field with power spectrum |u_hat(k)|^2 ~ k^exponent
+    """Gaussian random field whose shell-integrated spectrum is
+    E(k) ~ k^exponent, i.e. modal spectrum |u_hat(k)|^2 ~ k^(exponent - (d-1))
     (k = 0 removed), FFT synthesis from seeded white noise, unit variance.
 
     White noise is drawn on the CPU with a seeded torch generator so every
@@ -78,7 +82,7 @@ def power_law_grf(shape, exponent: float = -5.0 / 3.0, seed: int = 2,
     noise = torch.randn(tuple(shape), generator=gen, dtype=work).to(device)
     spec = torch.fft.rfftn(noise)
     del noise
-    amp = _wavenumber_amplitude(shape, exponent, device).to(spec.real.dtype)
+    amp = _wavenumber_amplitude(shape, exponent - (len(shape) - 1), device).to(spec.real.dtype)
     spec.mul_(amp)
     del amp
     u = torch.fft.irfftn(spec, s=tuple(shape))

@@ -255,5 +255,5 @@ def stream_header(s):
         "n_symbols": u64(96), "n_chunks": u64(104), "n_outliers": u64(112), "n_words": u64(120),
         "off_tiers": u64(128), "off_qtab": u64(136), "off_blocktier": u64(144), "off_chunks": u64(152),
         "off_codebook": u64(160), "off_bits": u64(168), "off_outliers": u64(176), "total": u64(184),
-        "codebook_bytes": u32(192), "n_runs": u32(196), "margin": f64(200),
+        "codebook_bytes": u32(192), "n_runs": u32(196), "margin": f64(200), "off_chunk_esc": u64(208),
     }

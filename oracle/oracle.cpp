@@ -643,6 +643,7 @@ struct HuffOut {
   std::vector<uint8_t> codebook;  // runs {u32 first, u32 count, u8 len[count], pad4}
   uint32_t n_runs = 0;
   std::vector<uint32_t> chunk_words;
+  std::vector<uint32_t> chunk_esc;  // symbols 0 (escapes) per chunk
   std::vector<uint32_t> words;
 };
 
@@ -670,7 +671,9 @@ HuffOut huffman_encode(const uint16_t* sym, size_t n, int dict, int chunk) {
     size_t s0 = c * chunk, s1 = std::min(n, s0 + (size_t)chunk);
     uint64_t bitpos = 0;
     std::vector<uint32_t> cw;
+    uint32_t nesc = 0;
     for (size_t i = s0; i < s1; ++i) {
+      nesc += sym[i] == 0;
       int L = len[sym[i]];
       uint32_t cd = code[sym[i]];
       for (int t = L - 1; t >= 0; --t) {  // MSB first
@@ -682,6 +685,7 @@ HuffOut huffman_encode(const uint16_t* sym, size_t n, int dict, int chunk) {
       }
     }
     h.chunk_words.push_back((uint32_t)cw.size());
+    h.chunk_esc.push_back(nesc);
     h.words.insert(h.words.end(), cw.begin(), cw.end());
   }
   return h;
@@ -783,8 +787,7 @@ std::vector<uint8_t> compress(const double* u, const int64_t* shape, bool f64, d
   bool raw = bud.raw || !finite;
 
   std::vector<uint16_t> sym;
-  std::vector<uint64_t> out_idx;
-  std::vector<int32_t> out_code;
+  std::vector<int32_t> out_code;  // codes of the escaped symbols, in stream order
   if (!raw) {
     std::vector<double> coef = decompose(u, p);
     std::vector<uint32_t> qi = coeff_q_index(p, block_tier, ntiers);
@@ -798,7 +801,6 @@ std::vector<uint8_t> compress(const double* u, const int64_t* shape, bool f64, d
         sym[i] = (uint16_t)(r.code + o.radius);
       } else {
         sym[i] = 0;
-        out_idx.push_back(i);
         out_code.push_back((int32_t)r.code);
       }
     }
@@ -846,7 +848,7 @@ std::vector<uint8_t> compress(const double* u, const int64_t* shape, bool f64, d
   for (int d = 0; d < 3; ++d) w.put_at<int32_t>(64 + 4 * d, (int32_t)p.nb[d]);
   w.put_at<uint64_t>(96, (uint64_t)sym.size());
   w.put_at<uint64_t>(104, (uint64_t)h.chunk_words.size());
-  w.put_at<uint64_t>(112, (uint64_t)out_idx.size());
+  w.put_at<uint64_t>(112, (uint64_t)out_code.size());
   w.put_at<uint64_t>(120, (uint64_t)h.words.size());
   w.put_at<uint32_t>(192, (uint32_t)h.codebook.size());
   w.put_at<uint32_t>(196, h.n_runs);
@@ -870,8 +872,12 @@ std::vector<uint8_t> compress(const double* u, const int64_t* shape, bool f64, d
   w.put_at<uint64_t>(168, (uint64_t)w.b.size());
   for (uint32_t x : h.words) w.put<uint32_t>(x);
   w.pad8();
+  // escape counts per chunk, present only when there are outliers
+  w.put_at<uint64_t>(208, (uint64_t)w.b.size());
+  if (!out_code.empty())
+    for (uint32_t c : h.chunk_esc) w.put<uint32_t>(c);
+  w.pad8();
   w.put_at<uint64_t>(176, (uint64_t)w.b.size());
-  for (uint64_t x : out_idx) w.put<uint64_t>(x);
   for (int32_t x : out_code) w.put<int32_t>(x);
   w.pad8();
   w.put_at<uint64_t>(184, (uint64_t)w.b.size());
@@ -930,15 +936,20 @@ bool decompress(const uint8_t* s, size_t nbytes, std::vector<double>& u, int64_t
     g_err = "bitstream";
     return false;
   }
+  // escaped symbols take the outlier codes in stream order
   std::vector<int64_t> code(nsym);
-  for (size_t i = 0; i < nsym; ++i) code[i] = (int64_t)sym[i] - o.radius;
   size_t ooff = rd<uint64_t>(s, 176);
-  for (uint64_t t = 0; t < nout; ++t) {
-    uint64_t idx = rd<uint64_t>(s, ooff + 8 * t);
-    int32_t c = rd<int32_t>(s, ooff + 8 * nout + 4 * t);
-    if (idx >= nsym) { g_err = "outlier index"; return false; }
-    code[idx] = c;
+  uint64_t next = 0;
+  for (size_t i = 0; i < nsym; ++i) {
+    if (sym[i]) {
+      code[i] = (int64_t)sym[i] - o.radius;
+    } else {
+      if (next >= nout) { g_err = "more escapes than outliers"; return false; }
+      code[i] = rd<int32_t>(s, ooff + 4 * next);
+      ++next;
+    }
   }
+  if (next != nout) { g_err = "outlier count"; return false; }
   if (codes_out) *codes_out = code;
   std::vector<uint32_t> qi = coeff_q_index(p, block_tier, ntiers);
   std::vector<double> coef(nsym);

@@ -454,10 +454,13 @@ __global__ void header_kernel(HeaderArgs a) {
   put<uint32_t>(o, 192, (uint32_t)sc->codebook_bytes);
   put<uint32_t>(o, 196, (uint32_t)sc->n_runs);
   put<double>(o, 200, sc->margin);
-  for (int i = 208; i < kHeaderBytes; ++i) o[i] = 0;
+  put<uint64_t>(o, 208, sc->off_chunk_esc);
+  for (int i = 216; i < kHeaderBytes; ++i) o[i] = 0;
   const unsigned long long wend = sc->off_bits + 4ull * sc->n_words;
-  for (unsigned long long i = wend; i < sc->off_outliers; ++i) o[i] = 0;
-  const unsigned long long oend = sc->off_outliers + 12ull * sc->n_outliers;
+  for (unsigned long long i = wend; i < sc->off_chunk_esc; ++i) o[i] = 0;
+  const unsigned long long cend = sc->off_chunk_esc + (sc->n_outliers ? 4ull * a.n_chunks : 0ull);
+  for (unsigned long long i = cend; i < sc->off_outliers; ++i) o[i] = 0;
+  const unsigned long long oend = sc->off_outliers + 4ull * sc->n_outliers;
   for (unsigned long long i = oend; i < sc->total; ++i) o[i] = 0;
 }
 
@@ -839,7 +842,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     ea.out = out; ea.sc = sc;
     chunk_bits_kernel<8><<<grid_for((int64_t)L.nch * 32, 256, 16), 256, 0, s>>>(ea);
     chunk_scan_kernel<<<1, kCbThreads, 0, s>>>(ea.chunk_words, chunk_esc, L.nch, word_off, esc_off, sc, L.off_codebook,
-                                               raw_total, cap);
+                                               raw_total, cap, out);
     encode_kernel<8><<<grid_for((int64_t)L.nch * 32, 256, 16), 256, 0, s>>>(ea);
     g_launches.fetch_add(3);
     HeaderArgs ha{};
@@ -874,7 +877,7 @@ struct Header {
   int B, K, M, chunk, radius, ntiers, m, rel;
   int64_t shape[3];
   unsigned long long n_symbols, n_chunks, n_outliers, n_words, off_tiers, off_qtab, off_btier, off_chunks,
-      off_codebook, off_bits, off_outliers, total;
+      off_codebook, off_bits, off_chunk_esc, off_outliers, total;
   unsigned codebook_bytes, n_runs;
 };
 
@@ -912,6 +915,7 @@ bm_status parse_header(const unsigned char* hb, size_t in_bytes, Header& H) {
   H.off_tiers = rd<uint64_t>(hb, 128); H.off_qtab = rd<uint64_t>(hb, 136); H.off_btier = rd<uint64_t>(hb, 144);
   H.off_chunks = rd<uint64_t>(hb, 152); H.off_codebook = rd<uint64_t>(hb, 160); H.off_bits = rd<uint64_t>(hb, 168);
   H.off_outliers = rd<uint64_t>(hb, 176);
+  H.off_chunk_esc = rd<uint64_t>(hb, 208);
   H.codebook_bytes = rd<uint32_t>(hb, 192); H.n_runs = rd<uint32_t>(hb, 196);
   if ((H.B != 9 && H.B != 17) || H.K < 1 || H.K > (H.B == 9 ? 3 : 4) || H.M < 0 || H.M > 16 || H.chunk < 64 ||
       H.chunk > 8192 || H.chunk % 32 || H.radius < 16 || H.radius > kMaxDict / 2 || H.ntiers < 1 || H.ntiers > 255)
@@ -920,8 +924,9 @@ bm_status parse_header(const unsigned char* hb, size_t in_bytes, Header& H) {
   if (H.off_tiers != kHeaderBytes || H.off_qtab != H.off_tiers + pad8(8ull * H.ntiers) ||
       H.off_btier != H.off_qtab + pad8(8ull * nq) || H.off_chunks < H.off_btier ||
       H.off_codebook != H.off_chunks + pad8(4ull * H.n_chunks) ||
-      H.off_bits != H.off_codebook + pad8(H.codebook_bytes) || H.off_outliers != H.off_bits + pad8(4ull * H.n_words) ||
-      H.total != H.off_outliers + pad8(12ull * H.n_outliers))
+      H.off_bits != H.off_codebook + pad8(H.codebook_bytes) || H.off_chunk_esc != H.off_bits + pad8(4ull * H.n_words) ||
+      H.off_outliers != H.off_chunk_esc + (H.n_outliers ? pad8(4ull * H.n_chunks) : 0ull) ||
+      H.total != H.off_outliers + pad8(4ull * H.n_outliers))
     return fail(BM_ERR_CORRUPT, "section offsets inconsistent");
   if (H.n_chunks != (H.n_symbols + H.chunk - 1) / H.chunk) return fail(BM_ERR_CORRUPT, "chunk count");
   if (H.n_outliers > H.n_symbols) return fail(BM_ERR_CORRUPT, "outlier count");
@@ -945,21 +950,25 @@ bm_status read_header(const void* in, size_t in_bytes, bool is_device, cudaStrea
 
 // Decode the Huffman part of a stream into symbols + escape codes.
 bm_status decode_symbols(const uint8_t* in, const Header& H, Carver& cv, uint16_t** sym_out, int32_t** esc_out,
-                         Scalars** sc_out, cudaStream_t s) {
+                         Scalars** sc_out, cudaStream_t s, int stream_mode = 1) {
   Scalars* sc = cv.take<Scalars>(1);
   uint16_t* sym = cv.take<uint16_t>(H.n_symbols);
   int32_t* esc = cv.take<int32_t>(H.n_symbols);
   unsigned long long* word_off = cv.take<unsigned long long>(H.n_chunks + 1);
+  unsigned long long* esc_off = cv.take<unsigned long long>(H.n_chunks + 1);
   DecodeTables* dt = cv.take<DecodeTables>(1);
   BM_CUDA(cudaMemsetAsync(sc, 0, sizeof(Scalars), s));
   {
     Stage st("huffman_tables");
     word_scan_kernel<<<1, kCbThreads, 0, s>>>(reinterpret_cast<const unsigned*>(in + H.off_chunks), H.n_chunks,
                                               word_off, H.n_words, sc);
+    if (H.n_outliers)
+      word_scan_kernel<<<1, kCbThreads, 0, s>>>(reinterpret_cast<const unsigned*>(in + H.off_chunk_esc), H.n_chunks,
+                                                esc_off, H.n_outliers, sc);
     BM_CUDA(cudaFuncSetAttribute(decode_tables_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DtSmem)));
     decode_tables_kernel<<<1, kCbThreads, sizeof(DtSmem), s>>>(in + H.off_codebook, H.codebook_bytes, H.n_runs,
                                                                2 * H.radius, dt, sc);
-    g_launches.fetch_add(2);
+    g_launches.fetch_add(H.n_outliers ? 3 : 2);
     BM_CUDA(cudaGetLastError());
   }
   {
@@ -968,15 +977,14 @@ bm_status decode_symbols(const uint8_t* in, const Header& H, Carver& cv, uint16_
     da.words = reinterpret_cast<const unsigned*>(in + H.off_bits);
     da.n_words = H.n_words; da.word_off = word_off; da.nch = H.n_chunks; da.n = H.n_symbols; da.chunk = H.chunk;
     da.tab = dt; da.sym = sym; da.sc = sc;
+    da.stream_mode = stream_mode;
+    if (H.n_outliers) {
+      da.esc_off = esc_off;
+      da.ocode = reinterpret_cast<const int32_t*>(in + H.off_outliers);
+      da.esc = esc;
+    }
     decode_kernel<<<grid_for((int64_t)H.n_chunks, 256, 8), 256, 0, s>>>(da);
     BM_LAUNCHED();
-    if (H.n_outliers) {
-      outlier_scatter_kernel<<<grid_for((int64_t)H.n_outliers, 256), 256, 0, s>>>(
-          reinterpret_cast<const unsigned long long*>(in + H.off_outliers),
-          reinterpret_cast<const int32_t*>(in + H.off_outliers + 8ull * H.n_outliers), H.n_outliers, H.n_symbols, esc,
-          sc);
-      BM_LAUNCHED();
-    }
     BM_CUDA(cudaGetLastError());
   }
   *sym_out = sym;
@@ -986,7 +994,7 @@ bm_status decode_symbols(const uint8_t* in, const Header& H, Carver& cv, uint16_
 }
 
 size_t decode_scratch(const Header& H) {
-  return sizeof(Scalars) + 2ull * H.n_symbols + 4ull * H.n_symbols + 8ull * (H.n_chunks + 1) + sizeof(DecodeTables) +
+  return sizeof(Scalars) + 2ull * H.n_symbols + 4ull * H.n_symbols + 16ull * (H.n_chunks + 1) + sizeof(DecodeTables) +
          4096;
 }
 
@@ -1266,7 +1274,7 @@ bm_status bm_huffman_encode(const uint16_t* d_symbols, uint64_t n, int dict_size
     ea.word_off = word_off; ea.esc_off = esc_off; ea.nch = nch; ea.out = out; ea.sc = sc;
     chunk_bits_kernel<8><<<grid_for((int64_t)nch * 32, 256, 16), 256, 0, s>>>(ea);
     chunk_scan_kernel<<<1, kCbThreads, 0, s>>>(ea.chunk_words, chunk_esc, nch, word_off, esc_off, sc, off_cb, ~0ull,
-                                               out_capacity);
+                                               out_capacity, nullptr);
     encode_kernel<8><<<grid_for((int64_t)nch * 32, 256, 16), 256, 0, s>>>(ea);
     zero_tail_kernel<<<1, 32, 0, s>>>(out, sc);
     g_launches.fetch_add(4);
@@ -1311,7 +1319,8 @@ bm_status bm_huffman_decode(const void* d_section, const uint64_t sizes[5], uint
   int32_t* esc;
   Scalars* sc;
   if (dict_size & 1) return fail(BM_ERR_ARG, "dict_size must be even");
-  if (bm_status st = decode_symbols(reinterpret_cast<const uint8_t*>(d_section), H, cv, &sym, &esc, &sc, s)) return st;
+  if (bm_status st = decode_symbols(reinterpret_cast<const uint8_t*>(d_section), H, cv, &sym, &esc, &sc, s, 0))
+    return st;
   BM_CUDA(cudaMemcpyAsync(d_symbols, sym, 2 * n, cudaMemcpyDeviceToDevice, s));
   return check_status(sc, s);
 }

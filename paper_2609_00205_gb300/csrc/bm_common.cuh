@@ -33,6 +33,7 @@ struct Scalars {
   unsigned long long codebook_bytes;
   unsigned long long n_runs;
   unsigned long long off_bits;     // stream offsets decided on the device
+  unsigned long long off_chunk_esc;
   unsigned long long off_outliers;
   unsigned long long total;
   double max_abs;
@@ -162,7 +163,9 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int NLEFT>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NLEFT)); }
 
-// Histogram window kept in shared memory (symbols around the dictionary centre).
-constexpr int kHistWin = 2048;
+// Histogram bins kept in shared memory by every kernel that produces
+// symbols: the whole dictionary, so no symbol goes to a global atomic before
+// the per-CTA flush (a single hot global bin serialises on one L2 slice).
+constexpr int kHistWin = kMaxDict;
 
 }  // namespace bm

@@ -234,6 +234,10 @@ __global__ void gl_inv_interp(GLevel<T> L, const T* __restrict__ Uc, T* __restri
 template <typename T, int MODE>
 __global__ void coarsest_fwd(const T* __restrict__ U, int64_t count, int64_t sym_off, uint16_t* sym, int32_t* esc,
                              T* coef, const T* rq_ptr, unsigned* hist, int radius, Scalars* sc) {
+  __shared__ unsigned hloc[kHistWin];
+  if (MODE == 0)
+    for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) hloc[i] = 0;
+  __syncthreads();
   const T rq = MODE == 0 ? *rq_ptr : T(0);
   bool ovf = false;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
@@ -243,12 +247,22 @@ __global__ void coarsest_fwd(const T* __restrict__ U, int64_t count, int64_t sym
       const unsigned sv = in ? (unsigned)(code + radius) : 0u;
       sym[sym_off + i] = (uint16_t)sv;
       if (!in) esc[sym_off + i] = code;
-      atomicAdd(hist + sv, 1u);
+      const int bin = (int)sv - (radius - kHistWin / 2);
+      if (bin >= 0 && bin < kHistWin) atomicAdd(hloc + bin, 1u);
+      else atomicAdd(hist + sv, 1u);
     } else {
       coef[sym_off + i] = U[i];
     }
   }
-  if (MODE == 0 && ovf) atomicOr(&sc->status, ST_OVERFLOW);
+  if (MODE == 0) {
+    if (ovf) atomicOr(&sc->status, ST_OVERFLOW);
+    __syncthreads();
+    const int lo = radius - kHistWin / 2;
+    for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) {
+      const unsigned v = hloc[i];
+      if (v && lo + i >= 0 && lo + i < 2 * radius) atomicAdd(hist + lo + i, v);
+    }
+  }
 }
 
 template <typename T, int MODE>

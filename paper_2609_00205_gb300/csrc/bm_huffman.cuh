@@ -426,15 +426,17 @@ __global__ void __launch_bounds__(WARPS * 32) chunk_bits_kernel(EncodeArgs a) {
 }
 
 // Exclusive scans of the chunk word counts and escape counts (one CTA), then
-// the stream offsets of the bitstream and outlier sections.
+// the stream offsets of the bitstream, the per-chunk escape counts (present
+// only when there are escapes) and the outlier codes.
 __global__ void __launch_bounds__(kCbThreads) chunk_scan_kernel(const unsigned* chunk_words, const unsigned* chunk_esc,
                                                                 unsigned long long nch, unsigned long long* word_off,
                                                                 unsigned long long* esc_off, Scalars* sc,
                                                                 unsigned long long off_codebook,
                                                                 unsigned long long raw_total,
-                                                                unsigned long long capacity) {
+                                                                unsigned long long capacity, uint8_t* out) {
   __shared__ unsigned long long wt[32], et[32];
   __shared__ unsigned long long carry_w, carry_e;
+  __shared__ int s_write;
   if (threadIdx.x == 0) { carry_w = 0; carry_e = 0; }
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -476,13 +478,21 @@ __global__ void __launch_bounds__(kCbThreads) chunk_scan_kernel(const unsigned* 
     sc->n_words = carry_w;
     sc->n_outliers = carry_e;
     const unsigned long long off_bits = off_codebook + pad8(sc->codebook_bytes);
-    const unsigned long long off_out = off_bits + pad8(4ull * carry_w);
-    const unsigned long long total = off_out + pad8(12ull * carry_e);
+    const unsigned long long off_ce = off_bits + pad8(4ull * carry_w);
+    const unsigned long long off_out = off_ce + (carry_e ? pad8(4ull * nch) : 0ull);
+    const unsigned long long total = off_out + pad8(4ull * carry_e);
     sc->off_bits = off_bits;
+    sc->off_chunk_esc = off_ce;
     sc->off_outliers = off_out;
     sc->total = total;
     if (total >= raw_total || total > capacity) atomicOr(&sc->status, ST_RAW);
     if (sc->status & ST_OVERFLOW) atomicOr(&sc->status, ST_RAW);
+    s_write = out && carry_e && !(sc->status & ST_RAW);
+  }
+  __syncthreads();
+  if (s_write) {
+    unsigned* dst = reinterpret_cast<unsigned*>(out + sc->off_chunk_esc);
+    for (unsigned long long i = threadIdx.x; i < nch; i += blockDim.x) dst[i] = chunk_esc[i];
   }
 }
 
@@ -495,8 +505,7 @@ __global__ void __launch_bounds__(WARPS * 32) encode_kernel(EncodeArgs a) {
   __syncthreads();
   const int lane = threadIdx.x & 31;
   unsigned* words = reinterpret_cast<unsigned*>(a.out + a.sc->off_bits);
-  unsigned long long* oidx = reinterpret_cast<unsigned long long*>(a.out + a.sc->off_outliers);
-  int32_t* ocode = reinterpret_cast<int32_t*>(a.out + a.sc->off_outliers + 8ull * a.sc->n_outliers);
+  int32_t* ocode = reinterpret_cast<int32_t*>(a.out + a.sc->off_outliers);
   for (unsigned long long c = blockIdx.x * (unsigned long long)WARPS + (threadIdx.x >> 5); c < a.nch;
        c += (unsigned long long)gridDim.x * WARPS) {
     unsigned long long s0, s1;
@@ -537,11 +546,7 @@ __global__ void __launch_bounds__(WARPS * 32) encode_kernel(EncodeArgs a) {
         nb -= 32;
         acc &= (nb ? ((1ull << nb) - 1ull) : 0ull);
       }
-      if (s == 0 && a.esc) {
-        oidx[epos] = i;
-        ocode[epos] = a.esc[i];
-        ++epos;
-      }
+      if (s == 0 && a.esc) ocode[epos++] = a.esc[i];
     }
     if (nb) atomicOr(words + widx, (unsigned)(acc << (32 - nb)));
     __syncwarp();
@@ -627,6 +632,10 @@ __global__ void __launch_bounds__(kCbThreads) decode_tables_kernel(const uint8_t
 struct DecodeArgs {
   const unsigned* words;            // bitstream
   unsigned long long n_words;
+  const unsigned long long* esc_off;  // [nch+1] first outlier of each chunk, or null without outliers
+  const int32_t* ocode;               // outlier codes in stream order
+  int32_t* esc;                       // codes of escaped symbols, indexed like sym
+  int stream_mode;                    // symbol 0 is the escape symbol (must have an outlier code)
   const unsigned long long* word_off;  // [nch+1]
   unsigned long long nch;
   unsigned long long n;
@@ -662,6 +671,8 @@ __global__ void __launch_bounds__(256) decode_kernel(DecodeArgs a) {
     unsigned long long buf = 0;
     int nbits = 0;
     bool bad = false;
+    unsigned long long epos = a.esc_off ? a.esc_off[c] : 0ull;
+    const unsigned long long eend = a.esc_off ? a.esc_off[c + 1] : 0ull;
     for (unsigned long long i = s0; i < s1; ++i) {
       while (nbits <= 32 && w < wend) {
         buf |= (unsigned long long)a.words[w++] << (32 - nbits);
@@ -685,18 +696,13 @@ __global__ void __launch_bounds__(256) decode_kernel(DecodeArgs a) {
       buf <<= L;
       nbits -= (int)L;
       a.sym[i] = (uint16_t)s;
+      if (s == 0 && a.stream_mode) {
+        if (epos >= eend) { bad = true; break; }
+        a.esc[i] = a.ocode[epos++];
+      }
     }
+    if (a.esc_off && !bad && epos != eend) bad = true;
     if (bad) atomicOr(&a.sc->status, ST_CORRUPT);
-  }
-}
-
-__global__ void outlier_scatter_kernel(const unsigned long long* idx, const int32_t* code, unsigned long long n_out,
-                                       unsigned long long n, int32_t* esc, Scalars* sc) {
-  for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < n_out;
-       t += (unsigned long long)gridDim.x * blockDim.x) {
-    const unsigned long long i = idx[t];
-    if (i >= n) { atomicOr(&sc->status, ST_CORRUPT); continue; }
-    esc[i] = code[t];
   }
 }
 
