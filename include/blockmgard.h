@@ -127,11 +127,29 @@ bm_status bm_stream_codes(const void* d_in, size_t in_bytes, int32_t* d_codes, v
 /* Stand-alone Huffman stage (Sec. III-B lossless stage; cuSZ-style chunked
  * coding, "deflate" = concatenation of chunk codes): encodes n uint16 symbols
  * (each < dict_size, dict_size <= 8192) into the section layout used inside
- * streams: codebook runs | u32 chunk word counts | u32 code words, each part
+ * streams: u32 chunk word counts | codebook runs | u32 code words, each part
  * padded to 8 bytes.  sizes_out[0..4] = codebook bytes, runs, chunks, words,
  * total bytes.  Synchronises the stream. */
 bm_status bm_huffman_encode(const uint16_t* d_symbols, uint64_t n, int dict_size, int chunk_symbols,
                             void* d_out, size_t out_capacity, uint64_t sizes_out[5], void* stream);
+
+/* Allocation-free variant of bm_huffman_encode (this entry point has no
+ * counterpart in the paper).  Same arguments, same output bytes, but it calls
+ * no cudaMalloc/cudaFree and no allocating library routine, for callers that
+ * cannot allocate device memory: code running while a stream is being
+ * captured into a CUDA graph, or a process whose device memory is entirely
+ * owned by another allocator.  Its scratch is one static device array of
+ * 1 MiB per GPU that loads this library, held until the process exits; it
+ * limits a call to at most 16384 chunks (n <= 16384 * chunk_symbols), larger
+ * requests return BM_ERR_ARG.  The first call on a device looks up the
+ * array's device address (with that device current); make that first call
+ * before any stream capture.  Every call shares the array and it keeps the
+ * last call's contents (the call clears what must start at zero), so calls
+ * whose GPU work overlaps in time (different streams, different host
+ * threads) race and must be serialised by the caller.  Synchronises the
+ * stream. */
+bm_status bm_huffman_encode_noalloc(const uint16_t* d_symbols, uint64_t n, int dict_size, int chunk_symbols,
+                                    void* d_out, size_t out_capacity, uint64_t sizes_out[5], void* stream);
 
 /* Inverse of bm_huffman_encode: sizes as returned by it; writes n symbols. */
 bm_status bm_huffman_decode(const void* d_section, const uint64_t sizes[5], uint64_t n, int dict_size,

@@ -1345,3 +1345,100 @@ void bm_release_workspace(void* stream) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free Huffman encoding (no cudaMalloc, no pinned host buffer)
+// ===========================================================================
+namespace bm {
+namespace {
+
+// Scratch of bm_huffman_encode_noalloc: one array per device, for the life of
+// the process, shared by every call.
+constexpr size_t kNoAllocBytes = size_t(1) << 20;     // 1 MiB
+constexpr unsigned long long kNoAllocMaxChunks = 16384;
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+std::map<int, void*> g_noalloc_addr;  // device -> device address of g_noalloc_scratch
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name is only a stand-in, so the address is looked up once per
+// device, with that device current, and cached.
+bm_status noalloc_scratch(void** out) {
+  int dev = 0;
+  BM_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> g(g_noalloc_mu);
+  auto it = g_noalloc_addr.find(dev);
+  if (it != g_noalloc_addr.end()) {
+    *out = it->second;
+    return BM_OK;
+  }
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || p == nullptr)
+    return fail(BM_ERR_CUDA, std::string("cudaGetSymbolAddress of the static scratch: ") + cudaGetErrorString(e));
+  g_noalloc_addr[dev] = p;
+  *out = p;
+  return BM_OK;
+}
+
+}  // namespace
+}  // namespace bm
+
+extern "C" bm_status bm_huffman_encode_noalloc(const uint16_t* d_symbols, uint64_t n, int dict_size, int chunk_symbols,
+                                               void* d_out, size_t out_capacity, uint64_t sizes_out[5], void* stream) {
+  if (!d_symbols || !d_out || !sizes_out) return fail(BM_ERR_ARG, "NULL pointer argument");
+  if (n == 0 || n >= (uint64_t(1) << 32)) return fail(BM_ERR_ARG, "symbol count must be in [1, 2^32)");
+  if (dict_size < 2 || dict_size > kMaxDict) return fail(BM_ERR_ARG, "dict_size must be in [2, 8192]");
+  if (chunk_symbols < 64 || chunk_symbols > 8192 || chunk_symbols % 32) return fail(BM_ERR_ARG, "chunk_symbols");
+  if (reinterpret_cast<uintptr_t>(d_out) % 8) return fail(BM_ERR_ARG, "output pointer must be 8-byte aligned");
+  const unsigned long long nch = (n + chunk_symbols - 1) / chunk_symbols;
+  if (nch > kNoAllocMaxChunks)
+    return fail(BM_ERR_ARG, "more than 16384 chunks (n / chunk_symbols) do not fit the static scratch");
+  const unsigned long long off_cb = pad8(4ull * nch);
+  if (off_cb > out_capacity) return fail(BM_ERR_CAPACITY, "capacity below the chunk table");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  void* base = nullptr;
+  if (bm_status st = noalloc_scratch(&base)) return st;
+  Carver cv;
+  cv.base = reinterpret_cast<unsigned char*>(base);
+  Scalars* sc = cv.take<Scalars>(1);
+  unsigned* hist = cv.take<unsigned>(dict_size);
+  uint8_t* lens = cv.take<uint8_t>(dict_size);
+  unsigned* codes = cv.take<unsigned>(dict_size);
+  unsigned* chunk_esc = cv.take<unsigned>(nch);
+  unsigned long long* word_off = cv.take<unsigned long long>(nch + 1);
+  unsigned long long* esc_off = cv.take<unsigned long long>(nch + 1);
+  if (cv.off > kNoAllocBytes) return fail(BM_ERR_ARG, "request does not fit the static scratch");
+  uint8_t* out = reinterpret_cast<uint8_t*>(d_out);
+  // the array keeps the previous call's contents: clear what must start at zero
+  BM_CUDA(cudaMemsetAsync(sc, 0, sizeof(Scalars), s));
+  BM_CUDA(cudaMemsetAsync(hist, 0, 4ull * dict_size, s));
+  BM_CUDA(cudaMemsetAsync(out, 0, off_cb, s));
+  hist_kernel<<<grid_for((int64_t)n, 256, 4), 256, 4 * dict_size, s>>>(d_symbols, n, dict_size, hist, sc);
+  CodebookArgs ca{hist, dict_size, lens, codes, out, off_cb, out_capacity, sc};
+  BM_CUDA(cudaFuncSetAttribute(codebook_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CbSmem)));
+  codebook_kernel<<<1, kCbThreads, sizeof(CbSmem), s>>>(ca);
+  EncodeArgs ea{};
+  ea.sym = d_symbols; ea.esc = nullptr; ea.n = n; ea.chunk = chunk_symbols; ea.lens = lens; ea.codes = codes;
+  ea.dict = dict_size; ea.chunk_words = reinterpret_cast<unsigned*>(out); ea.chunk_esc = chunk_esc;
+  ea.word_off = word_off; ea.esc_off = esc_off; ea.nch = nch; ea.out = out; ea.sc = sc;
+  chunk_bits_kernel<8><<<grid_for((int64_t)nch * 32, 256, 16), 256, 0, s>>>(ea);
+  chunk_scan_kernel<<<1, kCbThreads, 0, s>>>(ea.chunk_words, chunk_esc, nch, word_off, esc_off, sc, off_cb, ~0ull,
+                                             out_capacity, nullptr);
+  encode_kernel<8><<<grid_for((int64_t)nch * 32, 256, 16), 256, 0, s>>>(ea);
+  zero_tail_kernel<<<1, 32, 0, s>>>(out, sc);
+  g_launches.fetch_add(6);
+  BM_CUDA(cudaGetLastError());
+  Scalars hsc;
+  BM_CUDA(cudaMemcpyAsync(&hsc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+  BM_CUDA(cudaStreamSynchronize(s));
+  if (hsc.status & ST_CORRUPT) return fail(BM_ERR_ARG, "a symbol is not below dict_size");
+  if (hsc.status & (ST_RAW | ST_CAPACITY)) return fail(BM_ERR_CAPACITY, "output capacity too small");
+  sizes_out[0] = hsc.codebook_bytes;
+  sizes_out[1] = hsc.n_runs;
+  sizes_out[2] = nch;
+  sizes_out[3] = hsc.n_words;
+  sizes_out[4] = pad8(hsc.off_bits + 4ull * hsc.n_words);
+  return BM_OK;
+}
