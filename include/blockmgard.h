@@ -61,7 +61,7 @@ typedef struct {
   int incache_levels;  /* K >= 1: levels done while the block is resident (default 2)    */
   int global_levels;   /* M >= 0: MGARD levels on the gathered coarse grid (default 2;
                           -1 selects 0)                                                  */
-  int chunk_symbols;   /* Huffman chunk length in symbols, multiple of 32, 64..8192
+  int chunk_symbols;   /* Huffman chunk length in symbols, multiple of 32, 64..2048
                           (default 2048)                                                 */
   int dict_radius;     /* quantisation codes with |code| < radius become symbols
                           code + radius; others are outliers.  16..4096 (default 4096)   */
@@ -126,9 +126,10 @@ bm_status bm_stream_codes(const void* d_in, size_t in_bytes, int32_t* d_codes, v
 
 /* Stand-alone Huffman stage (Sec. III-B lossless stage; cuSZ-style chunked
  * coding, "deflate" = concatenation of chunk codes): encodes n uint16 symbols
- * (each < dict_size, dict_size <= 8192) into the section layout used inside
- * streams: u32 chunk word counts | codebook runs | u32 code words, each part
- * padded to 8 bytes.  sizes_out[0..4] = codebook bytes, runs, chunks, words,
+ * (each < dict_size, dict_size <= 8192; n < 2^31) into the section layout used inside
+ * streams: u32 chunk word counts | u16 split offsets (bit offsets of the
+ * eighths 1..7 of every chunk) | codebook runs | u32 code words, each part
+ * padded to 8 bytes.  chunk_symbols: multiple of 32 in [64, 2048].  sizes_out[0..4] = codebook bytes, runs, chunks, words,
  * total bytes.  Synchronises the stream. */
 bm_status bm_huffman_encode(const uint16_t* d_symbols, uint64_t n, int dict_size, int chunk_symbols,
                             void* d_out, size_t out_capacity, uint64_t sizes_out[5], void* stream);

@@ -168,10 +168,10 @@ def canonical_codes(lengths):
 
 
 def huffman_encode(sym, dict_size, chunk):
-    """Huffman section bytes (chunk word counts | codebook runs | words) and
-    its sizes dict."""
+    """Huffman section bytes (chunk word counts | split offsets | codebook
+    runs | words) and its sizes dict."""
     s = np.ascontiguousarray(np.asarray(sym, dtype=np.uint16))
-    cap = 64 + 8 * s.size + 8 * dict_size + 8 * (s.size // max(chunk, 1) + 2)
+    cap = 64 + 8 * s.size + 8 * dict_size + 24 * (s.size // max(chunk, 1) + 2)
     out = np.zeros(cap, dtype=np.uint8)
     sizes = np.zeros(5, dtype=np.uint64)
     _check(lib().or_huffman_encode(_ptr(s, ctypes.c_uint16), s.size, dict_size, chunk, _ptr(out, ctypes.c_uint8),
@@ -184,7 +184,7 @@ def huffman_encode(sym, dict_size, chunk):
 def huffman_decode(section, meta, n, dict_size, chunk):
     sec = np.ascontiguousarray(np.asarray(section, dtype=np.uint8))
     cb = meta["codebook_bytes"]
-    off_cb = (4 * meta["n_chunks"] + 7) // 8 * 8
+    off_cb = (4 * meta["n_chunks"] + 7) // 8 * 8 + (14 * meta["n_chunks"] + 7) // 8 * 8
     off_w = off_cb + (cb + 7) // 8 * 8
     chunks = np.ascontiguousarray(sec[:4 * meta["n_chunks"]].view(np.uint32))
     words = np.ascontiguousarray(sec[off_w:off_w + 4 * meta["n_words"]].view(np.uint32))
@@ -256,4 +256,5 @@ def stream_header(s):
         "off_tiers": u64(128), "off_qtab": u64(136), "off_blocktier": u64(144), "off_chunks": u64(152),
         "off_codebook": u64(160), "off_bits": u64(168), "off_outliers": u64(176), "total": u64(184),
         "codebook_bytes": u32(192), "n_runs": u32(196), "margin": f64(200), "off_chunk_esc": u64(208),
+        "off_splits": u64(216),
     }

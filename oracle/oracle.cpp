@@ -644,8 +644,13 @@ struct HuffOut {
   uint32_t n_runs = 0;
   std::vector<uint32_t> chunk_words;
   std::vector<uint32_t> chunk_esc;  // symbols 0 (escapes) per chunk
+  std::vector<uint16_t> splits;     // per chunk: bit offsets of its eighths 1..7 from the chunk start
   std::vector<uint32_t> words;
 };
+
+// A chunk is split into eight equal runs of chunk/8 symbols; the stream keeps
+// where runs 1..7 start so a decoder can work on the eight runs in parallel.
+constexpr int kSplits = 8;
 
 HuffOut huffman_encode(const uint16_t* sym, size_t n, int dict, int chunk) {
   HuffOut h;
@@ -672,7 +677,10 @@ HuffOut huffman_encode(const uint16_t* sym, size_t n, int dict, int chunk) {
     uint64_t bitpos = 0;
     std::vector<uint32_t> cw;
     uint32_t nesc = 0;
+    const size_t sub = std::max<size_t>(1, (size_t)chunk / kSplits);
+    uint16_t split[kSplits] = {};
     for (size_t i = s0; i < s1; ++i) {
+      if ((i - s0) % sub == 0 && (i - s0) / sub > 0) split[(i - s0) / sub] = (uint16_t)bitpos;
       nesc += sym[i] == 0;
       int L = len[sym[i]];
       uint32_t cd = code[sym[i]];
@@ -684,6 +692,10 @@ HuffOut huffman_encode(const uint16_t* sym, size_t n, int dict, int chunk) {
         ++bitpos;
       }
     }
+    // runs past the end of a short last chunk start where the chunk ends
+    for (int k = 1; k < kSplits; ++k)
+      if (s0 + k * sub >= s1) split[k] = (uint16_t)bitpos;
+    for (int k = 1; k < kSplits; ++k) h.splits.push_back(split[k]);
     h.chunk_words.push_back((uint32_t)cw.size());
     h.chunk_esc.push_back(nesc);
     h.words.insert(h.words.end(), cw.begin(), cw.end());
@@ -865,6 +877,9 @@ std::vector<uint8_t> compress(const double* u, const int64_t* shape, bool f64, d
   w.pad8();
   w.put_at<uint64_t>(152, (uint64_t)w.b.size());
   for (uint32_t c : h.chunk_words) w.put<uint32_t>(c);
+  w.pad8();
+  w.put_at<uint64_t>(216, (uint64_t)w.b.size());
+  for (uint16_t v : h.splits) w.put<uint16_t>(v);
   w.pad8();
   w.put_at<uint64_t>(160, (uint64_t)w.b.size());
   w.b.insert(w.b.end(), h.codebook.begin(), h.codebook.end());
@@ -1084,15 +1099,17 @@ int or_canonical_codes(const uint8_t* len, int nsym, uint32_t* code_out) {
   return 0;
 }
 
-// Huffman section for symbols sym[0..n): chunk word counts, codebook runs,
-// bitstream, concatenated in that order (each padded to 8 bytes), the order
-// these parts take inside a stream.
+// Huffman section for symbols sym[0..n): chunk word counts, split offsets,
+// codebook runs, bitstream, concatenated in that order (each padded to 8
+// bytes), the order these parts take inside a stream.
 // sizes[0..3] = codebook bytes, n_runs, n_chunks, n_words.
 int or_huffman_encode(const uint16_t* sym, uint64_t n, int dict, int chunk, uint8_t* out, uint64_t cap,
                       uint64_t* sizes) {
   HuffOut h = huffman_encode(sym, n, dict, chunk);
   Writer w;
   for (uint32_t c : h.chunk_words) w.put<uint32_t>(c);
+  w.pad8();
+  for (uint16_t v : h.splits) w.put<uint16_t>(v);
   w.pad8();
   w.b.insert(w.b.end(), h.codebook.begin(), h.codebook.end());
   w.pad8();

@@ -285,7 +285,7 @@ bm_status check_params(const bm_params* p, Params& o) {
   const int kmax = o.B == 9 ? 3 : 4;
   if (o.K < 1 || o.K > kmax) return fail(BM_ERR_ARG, "incache_levels out of range for this block size");
   if (o.M > 16) return fail(BM_ERR_ARG, "global_levels too large");
-  if (o.chunk < 64 || o.chunk > 8192 || o.chunk % 32) return fail(BM_ERR_ARG, "chunk_symbols must be a multiple of 32 in [64, 8192]");
+  if (o.chunk < 64 || o.chunk > 2048 || o.chunk % 32) return fail(BM_ERR_ARG, "chunk_symbols must be a multiple of 32 in [64, 2048]");
   if (o.radius < 16 || o.radius > kMaxDict / 2) return fail(BM_ERR_ARG, "dict_radius must be in [16, 4096]");
   return BM_OK;
 }
@@ -331,17 +331,32 @@ int grid_for(int64_t work, int threads, int per_sm = 8) {
 // Small kernels of the API layer
 // ---------------------------------------------------------------------------
 template <typename T>
+__device__ __forceinline__ void maxabs_acc(T x, T& m, bool& bad) {
+  const T v = fabs(x);
+  if (v != v || isinf(v)) bad = true;
+  else m = v > m ? v : m;
+}
+
+// max |u| (NaN ignored, non-finite values flagged), 16-byte loads over the
+// aligned bulk of the field.
+template <typename T>
 __global__ void maxabs_kernel(const T* __restrict__ u, int64_t n, Scalars* sc) {
   T m = T(0);
   bool bad = false;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const T v = fabs(u[i]);
-    if (v != v) bad = true;
-    else {
-      if (isinf(v)) bad = true;
-      m = v > m ? v : m;
-    }
+  constexpr int V = 16 / sizeof(T);
+  const int64_t head = (int64_t)((16 - (reinterpret_cast<uintptr_t>(u) & 15)) & 15) / (int64_t)sizeof(T);
+  const int64_t h = head < n ? head : n;
+  const int64_t nv = (n - h) / V;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+  const uint4* pv = reinterpret_cast<const uint4*>(u + h);
+  for (int64_t i = tid; i < nv; i += nth) {
+    const uint4 q = __ldg(pv + i);
+    const T* t = reinterpret_cast<const T*>(&q);
+#pragma unroll
+    for (int j = 0; j < V; ++j) maxabs_acc(t[j], m, bad);
   }
+  for (int64_t i = tid; i < h; i += nth) maxabs_acc(u[i], m, bad);
+  for (int64_t i = h + nv * V + tid; i < n; i += nth) maxabs_acc(u[i], m, bad);
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     const T y = __shfl_xor_sync(0xffffffffu, m, o);
@@ -409,7 +424,7 @@ struct HeaderArgs {
   int64_t shape[3];
   int nb[3];
   double tol;
-  unsigned long long n_symbols, n_chunks, off_tiers, off_qtab, off_btier, off_chunks, off_codebook;
+  unsigned long long n_symbols, n_chunks, off_tiers, off_qtab, off_btier, off_chunks, off_splits, off_codebook;
   Scalars* sc;
 };
 
@@ -455,7 +470,8 @@ __global__ void header_kernel(HeaderArgs a) {
   put<uint32_t>(o, 196, (uint32_t)sc->n_runs);
   put<double>(o, 200, sc->margin);
   put<uint64_t>(o, 208, sc->off_chunk_esc);
-  for (int i = 216; i < kHeaderBytes; ++i) o[i] = 0;
+  put<uint64_t>(o, 216, a.off_splits);
+  for (int i = 224; i < kHeaderBytes; ++i) o[i] = 0;
   const unsigned long long wend = sc->off_bits + 4ull * sc->n_words;
   for (unsigned long long i = wend; i < sc->off_chunk_esc; ++i) o[i] = 0;
   const unsigned long long cend = sc->off_chunk_esc + (sc->n_outliers ? 4ull * a.n_chunks : 0ull);
@@ -599,9 +615,9 @@ bm_status run_decompose(PlanDev& P, const T* field, int mode, const FwdOut<T>& o
     else gl_fwd_detail<T, 1><<<grid_for(nn, 256), 256, 0, s>>>(L, U[l], Dbuf, o.sym, o.esc, o.coef, rq, o.hist, o.radius, o.sc);
     BM_LAUNCHED();
     const int64_t l2 = (int64_t)L.d[0].n * L.d[1].n, l1 = (int64_t)L.d[0].n * L.d[2].c, l0 = (int64_t)L.d[1].c * L.d[2].c;
-    gl_restrict<T, 2, 0><<<grid_for(l2, 128, 16), 128, 0, s>>>(L, Dbuf, W1, nullptr);
-    gl_restrict<T, 1, 0><<<grid_for(l1, 128, 16), 128, 0, s>>>(L, W1, W2, nullptr);
-    gl_restrict<T, 0, 1><<<grid_for(l0, 128, 16), 128, 0, s>>>(L, W2, U[l + 1], U[l]);
+    gl_restrict<T, 2, 0><<<grid_for(l2, 32, 64), 32, 0, s>>>(L, Dbuf, W1, nullptr);
+    gl_restrict<T, 1, 0><<<grid_for(l1, 32, 64), 32, 0, s>>>(L, W1, W2, nullptr);
+    gl_restrict<T, 0, 1><<<grid_for(l0, 32, 64), 32, 0, s>>>(L, W2, U[l + 1], U[l]);
     g_launches.fetch_add(3);
     BM_CUDA(cudaGetLastError());
   }
@@ -659,9 +675,9 @@ bm_status run_recompose(PlanDev& P, T* field, int mode, const InvIn<T>& in, Carv
     else gl_inv_dequant<T, 1><<<grid_for(nn, 256), 256, 0, s>>>(L, in.sym, in.esc, in.coef, q, in.radius, U[l]);
     const int64_t l2 = (int64_t)L.d[0].n * L.d[1].n, l1 = (int64_t)L.d[0].n * L.d[2].c, l0 = (int64_t)L.d[1].c * L.d[2].c;
     T* Cn = Dbuf;  // corrected coarse values (size of U[l+1] <= size of U[0])
-    gl_restrict<T, 2, 0><<<grid_for(l2, 128, 16), 128, 0, s>>>(L, U[l], W1, nullptr);
-    gl_restrict<T, 1, 0><<<grid_for(l1, 128, 16), 128, 0, s>>>(L, W1, W2, nullptr);
-    gl_restrict<T, 0, 2><<<grid_for(l0, 128, 16), 128, 0, s>>>(L, W2, Cn, U[l + 1]);
+    gl_restrict<T, 2, 0><<<grid_for(l2, 32, 64), 32, 0, s>>>(L, U[l], W1, nullptr);
+    gl_restrict<T, 1, 0><<<grid_for(l1, 32, 64), 32, 0, s>>>(L, W1, W2, nullptr);
+    gl_restrict<T, 0, 2><<<grid_for(l0, 32, 64), 32, 0, s>>>(L, W2, Cn, U[l + 1]);
     gl_inv_interp<T><<<grid_for(nn, 256), 256, 0, s>>>(L, Cn, U[l]);
     g_launches.fetch_add(5);
     BM_CUDA(cudaGetLastError());
@@ -696,7 +712,7 @@ size_t decompose_scratch(const PlanHost& h, size_t esize) {
 
 // Layout of the host-known part of a stream.
 struct StreamLayout {
-  unsigned long long off_tiers, off_qtab, off_btier, off_chunks, off_codebook, nch;
+  unsigned long long off_tiers, off_qtab, off_btier, off_chunks, off_splits, off_codebook, nch;
   int nq;
 };
 StreamLayout layout(const PlanHost& h, int ntiers, int chunk) {
@@ -707,7 +723,8 @@ StreamLayout layout(const PlanHost& h, int ntiers, int chunk) {
   L.off_qtab = L.off_tiers + pad8(8ull * ntiers);
   L.off_btier = L.off_qtab + pad8(8ull * L.nq);
   L.off_chunks = L.off_btier + (ntiers > 1 ? pad8((unsigned long long)h.nblocks) : 0ull);
-  L.off_codebook = L.off_chunks + pad8(4ull * L.nch);
+  L.off_splits = L.off_chunks + pad8(4ull * L.nch);
+  L.off_codebook = L.off_splits + pad8(2ull * (kSplits - 1) * L.nch);
   return L;
 }
 
@@ -717,7 +734,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   PlanDev* P = nullptr;
   if (bm_status st = get_plan(shape, prm.B, prm.K, prm.M, &P)) return st;
   const PlanHost& h = P->h;
-  if (h.n_coeffs >= (int64_t(1) << 32)) return fail(BM_ERR_UNSUPPORTED, "more than 2^32 - 1 coefficients");
+  if (h.n_coeffs >= (int64_t(1) << 31)) return fail(BM_ERR_UNSUPPORTED, "more than 2^31 - 1 coefficients");
   if (prm.M + prm.K > 24) return fail(BM_ERR_ARG, "too many levels");
   const bool f64 = sizeof(T) == 8;
   const int64_t nel = nel3(shape);
@@ -755,7 +772,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   probe.take<Scalars>(1); probe.take<unsigned>(dict); probe.take<uint8_t>(dict); probe.take<unsigned>(dict);
   probe.take<double>(L.nq); probe.take<T>(L.nq); probe.take<double>(ntiers); probe.take<uint8_t>(h.nblocks);
   probe.take<uint16_t>((size_t)h.n_coeffs); probe.take<int32_t>((size_t)h.n_coeffs);
-  probe.take<unsigned>(L.nch); probe.take<unsigned long long>(L.nch + 1); probe.take<unsigned long long>(L.nch + 1);
+  probe.take<unsigned>(L.nch); probe.take<unsigned char>(256 + 16ull * L.nch); probe.take<int32_t>((size_t)h.n_coeffs);
   const size_t need = probe.off + decompose_scratch(h, sizeof(T)) + 4096;
   const size_t hneed = sizeof(Scalars) + 8 * ntiers + (size_t)h.nblocks + 4096;
   Workspace* ws = nullptr;
@@ -772,8 +789,9 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   uint16_t* sym = cv.take<uint16_t>((size_t)h.n_coeffs);
   int32_t* esc = cv.take<int32_t>((size_t)h.n_coeffs);
   unsigned* chunk_esc = cv.take<unsigned>(L.nch);
-  unsigned long long* word_off = cv.take<unsigned long long>(L.nch + 1);
-  unsigned long long* esc_off = cv.take<unsigned long long>(L.nch + 1);
+  unsigned char* tickets = cv.take<unsigned char>(256 + 16ull * L.nch);  // ticket, then look-back status words
+  unsigned long long* lb_status = reinterpret_cast<unsigned long long*>(tickets + 256);
+  int32_t* ocode = cv.take<int32_t>((size_t)h.n_coeffs);
 
   unsigned char* hp = reinterpret_cast<unsigned char*>(ws->h);
   Scalars* hsc = reinterpret_cast<Scalars*>(hp);
@@ -796,7 +814,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   }
   {
     Stage st("maxabs");
-    maxabs_kernel<T><<<grid_for(nel, 256, 8), 256, 0, s>>>(field, nel, sc);
+    maxabs_kernel<T><<<num_sms() * 8, 256, 0, s>>>(field, nel, sc);
     BM_LAUNCHED();
     QtabArgs qa{};
     qa.tiers = dtiers; qa.ntiers = ntiers; qa.rel = rel; qa.K = h.K; qa.M = h.M;
@@ -812,7 +830,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   }
   if (!prefix_fits) {  // not even the tables fit: the raw copy is the stream
     BM_CUDA(cudaMemsetAsync(sc, 0, sizeof(Scalars), s));
-    maxabs_kernel<T><<<grid_for(nel, 256, 8), 256, 0, s>>>(field, nel, sc);
+    maxabs_kernel<T><<<num_sms() * 8, 256, 0, s>>>(field, nel, sc);
     raw_header_kernel<<<1, 32, 0, s>>>(out, f64, h.B, shape[0], shape[1], shape[2], rel, tol, raw_total, sc);
     g_launches.fetch_add(2);
     BM_CUDA(cudaMemcpyAsync(out + kHeaderBytes, field, (size_t)nel * sizeof(T), cudaMemcpyDeviceToDevice, s));
@@ -834,30 +852,32 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   }
   {
     Stage st("huffman_encode");
-    EncodeArgs ea{};
+    BM_CUDA(cudaMemsetAsync(tickets, 0, 256 + 16ull * L.nch, s));
+    FusedEncodeArgs ea{};
     ea.sym = sym; ea.esc = esc; ea.n = (unsigned long long)h.n_coeffs; ea.chunk = prm.chunk;
-    ea.lens = lens; ea.codes = codes; ea.dict = dict;
-    ea.chunk_words = reinterpret_cast<unsigned*>(out + L.off_chunks);
-    ea.chunk_esc = chunk_esc; ea.word_off = word_off; ea.esc_off = esc_off; ea.nch = L.nch;
-    ea.out = out; ea.sc = sc;
-    chunk_bits_kernel<8><<<grid_for((int64_t)L.nch * 32, 256, 16), 256, 0, s>>>(ea);
-    chunk_scan_kernel<<<1, kCbThreads, 0, s>>>(ea.chunk_words, chunk_esc, L.nch, word_off, esc_off, sc, L.off_codebook,
-                                               raw_total, cap, out);
-    encode_kernel<8><<<grid_for((int64_t)L.nch * 32, 256, 16), 256, 0, s>>>(ea);
-    g_launches.fetch_add(3);
+    ea.lens = lens; ea.codes = codes; ea.dict = dict; ea.nch = L.nch;
+    ea.ticket = reinterpret_cast<unsigned*>(tickets); ea.st = lb_status;
+    ea.chunk_words = reinterpret_cast<unsigned*>(out + L.off_chunks); ea.chunk_esc = chunk_esc; ea.ocode = ocode;
+    ea.splits = reinterpret_cast<uint16_t*>(out + L.off_splits);
+    ea.out = out; ea.off_codebook = L.off_codebook; ea.capacity = cap; ea.sc = sc;
+    encode_fused_kernel<8><<<grid_for((int64_t)L.nch * 32, 256, 8), 256, 0, s>>>(ea);
+    encode_finish_kernel<<<grid_for((int64_t)L.nch, 256, 4), 256, 0, s>>>(chunk_esc, L.nch, ocode, out, L.off_codebook,
+                                                                        raw_total, cap, sc);
+    g_launches.fetch_add(2);
     HeaderArgs ha{};
     ha.out = out; ha.f64 = f64; ha.B = h.B; ha.K = h.K; ha.M = h.M; ha.chunk = prm.chunk; ha.radius = prm.radius;
     ha.ntiers = ntiers; ha.m = h.m; ha.rel = rel;
     for (int d = 0; d < 3; ++d) { ha.shape[d] = shape[d]; ha.nb[d] = h.nb[d]; }
     ha.tol = tol; ha.n_symbols = (unsigned long long)h.n_coeffs; ha.n_chunks = L.nch;
     ha.off_tiers = L.off_tiers; ha.off_qtab = L.off_qtab; ha.off_btier = ntiers > 1 ? L.off_btier : L.off_chunks;
-    ha.off_chunks = L.off_chunks; ha.off_codebook = L.off_codebook; ha.sc = sc;
+    ha.off_chunks = L.off_chunks; ha.off_splits = L.off_splits; ha.off_codebook = L.off_codebook; ha.sc = sc;
     header_kernel<<<1, 32, 0, s>>>(ha);
     BM_LAUNCHED();
     BM_CUDA(cudaGetLastError());
     BM_CUDA(cudaMemcpyAsync(hsc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
   }
   BM_CUDA(cudaStreamSynchronize(s));
+  if (hsc->status & ST_TIMEOUT) return fail(BM_ERR_CUDA, "encoder look-back wait timed out");
   if (hsc->status & ST_RAW) {
     Stage st("raw_copy");
     raw_header_kernel<<<1, 32, 0, s>>>(out, f64, h.B, shape[0], shape[1], shape[2], rel, tol, raw_total, sc);
@@ -877,7 +897,7 @@ struct Header {
   int B, K, M, chunk, radius, ntiers, m, rel;
   int64_t shape[3];
   unsigned long long n_symbols, n_chunks, n_outliers, n_words, off_tiers, off_qtab, off_btier, off_chunks,
-      off_codebook, off_bits, off_chunk_esc, off_outliers, total;
+      off_codebook, off_bits, off_chunk_esc, off_outliers, total, off_splits;
   unsigned codebook_bytes, n_runs;
 };
 
@@ -916,14 +936,16 @@ bm_status parse_header(const unsigned char* hb, size_t in_bytes, Header& H) {
   H.off_chunks = rd<uint64_t>(hb, 152); H.off_codebook = rd<uint64_t>(hb, 160); H.off_bits = rd<uint64_t>(hb, 168);
   H.off_outliers = rd<uint64_t>(hb, 176);
   H.off_chunk_esc = rd<uint64_t>(hb, 208);
+  H.off_splits = rd<uint64_t>(hb, 216);
   H.codebook_bytes = rd<uint32_t>(hb, 192); H.n_runs = rd<uint32_t>(hb, 196);
   if ((H.B != 9 && H.B != 17) || H.K < 1 || H.K > (H.B == 9 ? 3 : 4) || H.M < 0 || H.M > 16 || H.chunk < 64 ||
-      H.chunk > 8192 || H.chunk % 32 || H.radius < 16 || H.radius > kMaxDict / 2 || H.ntiers < 1 || H.ntiers > 255)
+      H.chunk > 2048 || H.chunk % 32 || H.radius < 16 || H.radius > kMaxDict / 2 || H.ntiers < 1 || H.ntiers > 255)
     return fail(BM_ERR_CORRUPT, "header parameters out of range");
   const unsigned long long nq = (unsigned long long)H.ntiers * H.K + H.M + 1;
   if (H.off_tiers != kHeaderBytes || H.off_qtab != H.off_tiers + pad8(8ull * H.ntiers) ||
       H.off_btier != H.off_qtab + pad8(8ull * nq) || H.off_chunks < H.off_btier ||
-      H.off_codebook != H.off_chunks + pad8(4ull * H.n_chunks) ||
+      H.off_splits != H.off_chunks + pad8(4ull * H.n_chunks) ||
+      H.off_codebook != H.off_splits + pad8(2ull * (kSplits - 1) * H.n_chunks) ||
       H.off_bits != H.off_codebook + pad8(H.codebook_bytes) || H.off_chunk_esc != H.off_bits + pad8(4ull * H.n_words) ||
       H.off_outliers != H.off_chunk_esc + (H.n_outliers ? pad8(4ull * H.n_chunks) : 0ull) ||
       H.total != H.off_outliers + pad8(4ull * H.n_outliers))
@@ -976,15 +998,15 @@ bm_status decode_symbols(const uint8_t* in, const Header& H, Carver& cv, uint16_
     DecodeArgs da{};
     da.words = reinterpret_cast<const unsigned*>(in + H.off_bits);
     da.n_words = H.n_words; da.word_off = word_off; da.nch = H.n_chunks; da.n = H.n_symbols; da.chunk = H.chunk;
+    da.splits = reinterpret_cast<const uint16_t*>(in + H.off_splits);
     da.tab = dt; da.sym = sym; da.sc = sc;
-    da.stream_mode = stream_mode;
-    if (H.n_outliers) {
-      da.esc_off = esc_off;
-      da.ocode = reinterpret_cast<const int32_t*>(in + H.off_outliers);
-      da.esc = esc;
-    }
-    decode_kernel<<<grid_for((int64_t)H.n_chunks, 256, 8), 256, 0, s>>>(da);
+    decode_kernel<<<grid_for((int64_t)H.n_chunks * kSplits, 128, 16), 128, 0, s>>>(da);
     BM_LAUNCHED();
+    if (stream_mode && H.n_outliers) {
+      escape_fixup_kernel<<<grid_for((int64_t)H.n_chunks * 32, 256, 8), 256, 0, s>>>(
+          sym, H.n_symbols, H.chunk, H.n_chunks, esc_off, reinterpret_cast<const int32_t*>(in + H.off_outliers), esc, sc);
+      BM_LAUNCHED();
+    }
     BM_CUDA(cudaGetLastError());
   }
   *sym_out = sym;
@@ -1225,20 +1247,20 @@ bm_status bm_stream_codes(const void* d_in, size_t in_bytes, int32_t* d_codes, v
 bm_status bm_huffman_encode(const uint16_t* d_symbols, uint64_t n, int dict_size, int chunk_symbols, void* d_out,
                             size_t out_capacity, uint64_t sizes_out[5], void* stream) {
   if (!d_symbols || !d_out || !sizes_out) return fail(BM_ERR_ARG, "NULL pointer argument");
-  if (n == 0 || n >= (uint64_t(1) << 32)) return fail(BM_ERR_ARG, "symbol count must be in [1, 2^32)");
+  if (n == 0 || n >= (uint64_t(1) << 31)) return fail(BM_ERR_ARG, "symbol count must be in [1, 2^31)");
   if (dict_size < 2 || dict_size > kMaxDict) return fail(BM_ERR_ARG, "dict_size must be in [2, 8192]");
-  if (chunk_symbols < 64 || chunk_symbols > 8192 || chunk_symbols % 32) return fail(BM_ERR_ARG, "chunk_symbols");
+  if (chunk_symbols < 64 || chunk_symbols > 2048 || chunk_symbols % 32) return fail(BM_ERR_ARG, "chunk_symbols");
   if (reinterpret_cast<uintptr_t>(d_out) % 8) return fail(BM_ERR_ARG, "output pointer must be 8-byte aligned");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   std::lock_guard<std::mutex> g(g_timer_mu);
   g_timer.begin(s);
   const unsigned long long nch = (n + chunk_symbols - 1) / chunk_symbols;
-  const unsigned long long off_cb = pad8(4ull * nch);
+  const unsigned long long off_sp = pad8(4ull * nch);
+  const unsigned long long off_cb = off_sp + pad8(2ull * (kSplits - 1) * nch);
   if (off_cb > out_capacity) return fail(BM_ERR_CAPACITY, "capacity below the chunk table");
   Carver probe;
   probe.take<Scalars>(1); probe.take<unsigned>(dict_size); probe.take<uint8_t>(dict_size);
-  probe.take<unsigned>(dict_size); probe.take<unsigned>(nch); probe.take<unsigned long long>(nch + 1);
-  probe.take<unsigned long long>(nch + 1);
+  probe.take<unsigned>(dict_size); probe.take<unsigned>(nch); probe.take<unsigned char>(256 + 16ull * nch);
   Workspace* ws = nullptr;
   if (bm_status st = get_ws(s, probe.off + 4096, 4096, &ws)) return st;
   Carver cv;
@@ -1248,12 +1270,12 @@ bm_status bm_huffman_encode(const uint16_t* d_symbols, uint64_t n, int dict_size
   uint8_t* lens = cv.take<uint8_t>(dict_size);
   unsigned* codes = cv.take<unsigned>(dict_size);
   unsigned* chunk_esc = cv.take<unsigned>(nch);
-  unsigned long long* word_off = cv.take<unsigned long long>(nch + 1);
-  unsigned long long* esc_off = cv.take<unsigned long long>(nch + 1);
+  unsigned char* tickets = cv.take<unsigned char>(256 + 16ull * nch);
   uint8_t* out = reinterpret_cast<uint8_t*>(d_out);
   BM_CUDA(cudaMemsetAsync(sc, 0, sizeof(Scalars), s));
   BM_CUDA(cudaMemsetAsync(hist, 0, 4ull * dict_size, s));
   BM_CUDA(cudaMemsetAsync(out, 0, off_cb, s));
+  BM_CUDA(cudaMemsetAsync(tickets, 0, 256 + 16ull * nch, s));
   {
     Stage st("huffman_histogram");
     hist_kernel<<<grid_for((int64_t)n, 256, 4), 256, 4 * dict_size, s>>>(d_symbols, n, dict_size, hist, sc);
@@ -1268,21 +1290,23 @@ bm_status bm_huffman_encode(const uint16_t* d_symbols, uint64_t n, int dict_size
   }
   {
     Stage st("huffman_encode");
-    EncodeArgs ea{};
+    FusedEncodeArgs ea{};
     ea.sym = d_symbols; ea.esc = nullptr; ea.n = n; ea.chunk = chunk_symbols; ea.lens = lens; ea.codes = codes;
-    ea.dict = dict_size; ea.chunk_words = reinterpret_cast<unsigned*>(out); ea.chunk_esc = chunk_esc;
-    ea.word_off = word_off; ea.esc_off = esc_off; ea.nch = nch; ea.out = out; ea.sc = sc;
-    chunk_bits_kernel<8><<<grid_for((int64_t)nch * 32, 256, 16), 256, 0, s>>>(ea);
-    chunk_scan_kernel<<<1, kCbThreads, 0, s>>>(ea.chunk_words, chunk_esc, nch, word_off, esc_off, sc, off_cb, ~0ull,
-                                               out_capacity, nullptr);
-    encode_kernel<8><<<grid_for((int64_t)nch * 32, 256, 16), 256, 0, s>>>(ea);
+    ea.dict = dict_size; ea.nch = nch; ea.ticket = reinterpret_cast<unsigned*>(tickets);
+    ea.st = reinterpret_cast<unsigned long long*>(tickets + 256);
+    ea.chunk_words = reinterpret_cast<unsigned*>(out); ea.chunk_esc = chunk_esc; ea.ocode = nullptr; ea.out = out;
+    ea.splits = reinterpret_cast<uint16_t*>(out + off_sp);
+    ea.off_codebook = off_cb; ea.capacity = out_capacity; ea.sc = sc;
+    encode_fused_kernel<8><<<grid_for((int64_t)nch * 32, 256, 8), 256, 0, s>>>(ea);
+    encode_finish_kernel<<<1, 256, 0, s>>>(chunk_esc, nch, nullptr, out, off_cb, ~0ull, out_capacity, sc);
     zero_tail_kernel<<<1, 32, 0, s>>>(out, sc);
-    g_launches.fetch_add(4);
+    g_launches.fetch_add(3);
     BM_CUDA(cudaGetLastError());
   }
   Scalars* hsc = reinterpret_cast<Scalars*>(ws->h);
   BM_CUDA(cudaMemcpyAsync(hsc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
   BM_CUDA(cudaStreamSynchronize(s));
+  if (hsc->status & ST_TIMEOUT) return fail(BM_ERR_CUDA, "encoder look-back wait timed out");
   if (hsc->status & ST_CORRUPT) return fail(BM_ERR_ARG, "a symbol is not below dict_size");
   if (hsc->status & (ST_RAW | ST_CAPACITY)) return fail(BM_ERR_CAPACITY, "output capacity too small");
   sizes_out[0] = hsc->codebook_bytes;
@@ -1297,17 +1321,18 @@ bm_status bm_huffman_decode(const void* d_section, const uint64_t sizes[5], uint
                             int chunk_symbols, uint16_t* d_symbols, void* stream) {
   if (!d_section || !sizes || !d_symbols) return fail(BM_ERR_ARG, "NULL pointer argument");
   if (dict_size < 2 || dict_size > kMaxDict) return fail(BM_ERR_ARG, "dict_size must be in [2, 8192]");
-  if (chunk_symbols < 64 || chunk_symbols > 8192 || chunk_symbols % 32) return fail(BM_ERR_ARG, "chunk_symbols");
+  if (chunk_symbols < 64 || chunk_symbols > 2048 || chunk_symbols % 32) return fail(BM_ERR_ARG, "chunk_symbols");
   if (reinterpret_cast<uintptr_t>(d_section) % 8) return fail(BM_ERR_ARG, "section pointer must be 8-byte aligned");
   const unsigned long long nch = (n + chunk_symbols - 1) / chunk_symbols;
   if (sizes[2] != nch) return fail(BM_ERR_CORRUPT, "chunk count does not match n");
-  const unsigned long long off_cb = pad8(4ull * nch), off_w = off_cb + pad8(sizes[0]);
+  const unsigned long long off_sp = pad8(4ull * nch);
+  const unsigned long long off_cb = off_sp + pad8(2ull * (kSplits - 1) * nch), off_w = off_cb + pad8(sizes[0]);
   if (sizes[4] < off_w + 4ull * sizes[3]) return fail(BM_ERR_CORRUPT, "section sizes inconsistent");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   std::lock_guard<std::mutex> g(g_timer_mu);
   g_timer.begin(s);
   Header H{};
-  H.n_symbols = n; H.n_chunks = nch; H.n_words = sizes[3]; H.n_outliers = 0; H.off_chunks = 0;
+  H.n_symbols = n; H.n_chunks = nch; H.n_words = sizes[3]; H.n_outliers = 0; H.off_chunks = 0; H.off_splits = off_sp;
   H.off_codebook = off_cb; H.off_bits = off_w; H.codebook_bytes = (unsigned)sizes[0]; H.n_runs = (unsigned)sizes[1];
   H.radius = dict_size / 2;  // only 2*radius = dict is used by the decoder
   H.chunk = chunk_symbols;
@@ -1388,14 +1413,15 @@ bm_status noalloc_scratch(void** out) {
 extern "C" bm_status bm_huffman_encode_noalloc(const uint16_t* d_symbols, uint64_t n, int dict_size, int chunk_symbols,
                                                void* d_out, size_t out_capacity, uint64_t sizes_out[5], void* stream) {
   if (!d_symbols || !d_out || !sizes_out) return fail(BM_ERR_ARG, "NULL pointer argument");
-  if (n == 0 || n >= (uint64_t(1) << 32)) return fail(BM_ERR_ARG, "symbol count must be in [1, 2^32)");
+  if (n == 0 || n >= (uint64_t(1) << 31)) return fail(BM_ERR_ARG, "symbol count must be in [1, 2^31)");
   if (dict_size < 2 || dict_size > kMaxDict) return fail(BM_ERR_ARG, "dict_size must be in [2, 8192]");
-  if (chunk_symbols < 64 || chunk_symbols > 8192 || chunk_symbols % 32) return fail(BM_ERR_ARG, "chunk_symbols");
+  if (chunk_symbols < 64 || chunk_symbols > 2048 || chunk_symbols % 32) return fail(BM_ERR_ARG, "chunk_symbols");
   if (reinterpret_cast<uintptr_t>(d_out) % 8) return fail(BM_ERR_ARG, "output pointer must be 8-byte aligned");
   const unsigned long long nch = (n + chunk_symbols - 1) / chunk_symbols;
   if (nch > kNoAllocMaxChunks)
     return fail(BM_ERR_ARG, "more than 16384 chunks (n / chunk_symbols) do not fit the static scratch");
-  const unsigned long long off_cb = pad8(4ull * nch);
+  const unsigned long long off_sp = pad8(4ull * nch);
+  const unsigned long long off_cb = off_sp + pad8(2ull * (kSplits - 1) * nch);
   if (off_cb > out_capacity) return fail(BM_ERR_CAPACITY, "capacity below the chunk table");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   void* base = nullptr;
@@ -1407,32 +1433,34 @@ extern "C" bm_status bm_huffman_encode_noalloc(const uint16_t* d_symbols, uint64
   uint8_t* lens = cv.take<uint8_t>(dict_size);
   unsigned* codes = cv.take<unsigned>(dict_size);
   unsigned* chunk_esc = cv.take<unsigned>(nch);
-  unsigned long long* word_off = cv.take<unsigned long long>(nch + 1);
-  unsigned long long* esc_off = cv.take<unsigned long long>(nch + 1);
+  unsigned char* tickets = cv.take<unsigned char>(256 + 16ull * nch);
   if (cv.off > kNoAllocBytes) return fail(BM_ERR_ARG, "request does not fit the static scratch");
   uint8_t* out = reinterpret_cast<uint8_t*>(d_out);
   // the array keeps the previous call's contents: clear what must start at zero
   BM_CUDA(cudaMemsetAsync(sc, 0, sizeof(Scalars), s));
   BM_CUDA(cudaMemsetAsync(hist, 0, 4ull * dict_size, s));
+  BM_CUDA(cudaMemsetAsync(tickets, 0, 256 + 16ull * nch, s));
   BM_CUDA(cudaMemsetAsync(out, 0, off_cb, s));
   hist_kernel<<<grid_for((int64_t)n, 256, 4), 256, 4 * dict_size, s>>>(d_symbols, n, dict_size, hist, sc);
   CodebookArgs ca{hist, dict_size, lens, codes, out, off_cb, out_capacity, sc};
   BM_CUDA(cudaFuncSetAttribute(codebook_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CbSmem)));
   codebook_kernel<<<1, kCbThreads, sizeof(CbSmem), s>>>(ca);
-  EncodeArgs ea{};
+  FusedEncodeArgs ea{};
   ea.sym = d_symbols; ea.esc = nullptr; ea.n = n; ea.chunk = chunk_symbols; ea.lens = lens; ea.codes = codes;
-  ea.dict = dict_size; ea.chunk_words = reinterpret_cast<unsigned*>(out); ea.chunk_esc = chunk_esc;
-  ea.word_off = word_off; ea.esc_off = esc_off; ea.nch = nch; ea.out = out; ea.sc = sc;
-  chunk_bits_kernel<8><<<grid_for((int64_t)nch * 32, 256, 16), 256, 0, s>>>(ea);
-  chunk_scan_kernel<<<1, kCbThreads, 0, s>>>(ea.chunk_words, chunk_esc, nch, word_off, esc_off, sc, off_cb, ~0ull,
-                                             out_capacity, nullptr);
-  encode_kernel<8><<<grid_for((int64_t)nch * 32, 256, 16), 256, 0, s>>>(ea);
+  ea.dict = dict_size; ea.nch = nch; ea.ticket = reinterpret_cast<unsigned*>(tickets);
+  ea.st = reinterpret_cast<unsigned long long*>(tickets + 256);
+  ea.chunk_words = reinterpret_cast<unsigned*>(out); ea.chunk_esc = chunk_esc; ea.ocode = nullptr; ea.out = out;
+  ea.splits = reinterpret_cast<uint16_t*>(out + off_sp);
+  ea.off_codebook = off_cb; ea.capacity = out_capacity; ea.sc = sc;
+  encode_fused_kernel<8><<<grid_for((int64_t)nch * 32, 256, 8), 256, 0, s>>>(ea);
+  encode_finish_kernel<<<1, 256, 0, s>>>(chunk_esc, nch, nullptr, out, off_cb, ~0ull, out_capacity, sc);
   zero_tail_kernel<<<1, 32, 0, s>>>(out, sc);
   g_launches.fetch_add(6);
   BM_CUDA(cudaGetLastError());
   Scalars hsc;
   BM_CUDA(cudaMemcpyAsync(&hsc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
   BM_CUDA(cudaStreamSynchronize(s));
+  if (hsc.status & ST_TIMEOUT) return fail(BM_ERR_CUDA, "encoder look-back wait timed out");
   if (hsc.status & ST_CORRUPT) return fail(BM_ERR_ARG, "a symbol is not below dict_size");
   if (hsc.status & (ST_RAW | ST_CAPACITY)) return fail(BM_ERR_CAPACITY, "output capacity too small");
   sizes_out[0] = hsc.codebook_bytes;

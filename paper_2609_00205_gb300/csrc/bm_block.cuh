@@ -5,9 +5,11 @@
 // Level structure (Sec. II-B): for a level of N (odd) nodes per dimension
 //   Phase A  lines (i0,i1) along dim 2: coefficients d = u - I(u|C) at every
 //            node (zero at all-coarse nodes), emitted as symbols or values;
-//            then z2 = M_c^-1 I^T M_f d along the line        -> T1 (N,N,C)
-//   Phase B  lines (i0,j2) along dim 1 of T1                   -> T2 (N,C,C)
-//   Phase C  lines (j1,j2) along dim 0 of T2, coarse = u|C + z -> out (C,C,C)
+//            then z2 = M_c^-1 I^T M_f d along the line     -> T1, stored (i0,j2,i1)
+//   Phase B  lines (i0,j2) along dim 1                      -> T2, stored (j1,j2,i0)
+//   Phase C  lines (j1,j2) along dim 0, coarse = u|C + z    -> out (C,C,C)
+// T1 and T2 are stored transposed so that every thread of phases B and C
+// reads its line contiguously (stride N between threads: no bank conflicts).
 // The shrinking arrays N^3 -> N^2 C -> N C^2 -> C^3 are the paper's
 // 8x8x8 -> 5x8x8 -> 5x5x8 -> 5x5x5 sequence for the block size used.
 #pragma once
@@ -73,23 +75,17 @@ struct BlockCfg {
   }
 };
 
-// Per-thread histogram run: consecutive equal symbols of a line are counted
-// once (the common case at loose tolerances is long runs of the zero code).
-struct HistRun {
-  unsigned sym = 0xFFFFFFFFu;
-  unsigned cnt = 0;
-};
-
-__device__ __forceinline__ void hist_add(unsigned* hloc, unsigned* hglob, int radius, unsigned s, unsigned n) {
+// Histogram of one CTA: the whole dictionary in shared memory; the centre
+// symbol (code 0, most of the symbols at loose tolerances) is counted in a
+// register per thread and added once at the end.
+__device__ __forceinline__ void hist_count(unsigned* hloc, unsigned* hglob, int radius, unsigned s, unsigned& centre) {
+  if (s == (unsigned)radius) {
+    ++centre;
+    return;
+  }
   const int bin = (int)s - (radius - kHistWin / 2);
-  if (bin >= 0 && bin < kHistWin) atomicAdd(hloc + bin, n);
-  else atomicAdd(hglob + s, n);
-}
-__device__ __forceinline__ void hist_push(HistRun& r, unsigned* hloc, unsigned* hglob, int radius, unsigned s) {
-  if (s == r.sym) { ++r.cnt; return; }
-  if (r.cnt) hist_add(hloc, hglob, radius, r.sym, r.cnt);
-  r.sym = s;
-  r.cnt = 1;
+  if (bin >= 0 && bin < kHistWin) atomicAdd(hloc + bin, 1u);
+  else atomicAdd(hglob + s, 1u);
 }
 
 // ---------------------------------------------------------------------------
@@ -99,7 +95,7 @@ template <typename T, int N, int MODE>
 __device__ __forceinline__ void level_fwd(const T* __restrict__ X, T* __restrict__ T1, T* __restrict__ T2,
                                           T* __restrict__ out, const int lvl_off, const T rq, uint16_t* stage,
                                           int32_t* __restrict__ esc_blk, T* __restrict__ coef_blk, unsigned* hloc,
-                                          unsigned* hglob, const int radius, bool& ovf) {
+                                          unsigned* hglob, const int radius, bool& ovf, unsigned& centre) {
   constexpr int C = (N + 1) / 2;
   const auto& tb = block_tab<T, N>();
   for (int L = threadIdx.x; L < N * N; L += blockDim.x) {
@@ -124,46 +120,58 @@ __device__ __forceinline__ void level_fwd(const T* __restrict__ X, T* __restrict
     const bool cc = !f0 && !f1;
     const int cc_before = ((i0 + 1) / 2) * C + (f0 ? 0 : (i1 + 1) / 2);
     const int base = lvl_off + L * N - cc_before * C;
-    HistRun run;
+    if (MODE == 0) {
+      bool any_esc = false;
 #pragma unroll
-    for (int k = 0; k < N; ++k) {
-      if ((k & 1) || !cc) {
-        const int pos = base + (cc ? k / 2 : k);
-        if (MODE == 0) {
+      for (int k = 0; k < N; ++k) {
+        if ((k & 1) || !cc) {
+          const int pos = base + (cc ? k / 2 : k);
           const int code = quantize(d[k], rq, ovf);
-          const bool in = code > -radius && code < radius;
-          const unsigned s = in ? (unsigned)(code + radius) : 0u;
-          stage[pos] = (uint16_t)s;
-          if (!in) esc_blk[pos] = code;
-          hist_push(run, hloc, hglob, radius, s);
-        } else {
-          coef_blk[pos] = d[k];
+          const unsigned u = (unsigned)(code + radius);
+          const bool in = (u - 1u) < (unsigned)(2 * radius - 1);
+          const unsigned sv = in ? u : 0u;
+          any_esc |= !in;
+          stage[pos] = (uint16_t)sv;
+          hist_count(hloc, hglob, radius, sv, centre);
         }
       }
+      if (any_esc) {  // rare: store the codes of escaped symbols
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          if ((k & 1) || !cc) {
+            bool dummy = false;
+            const int code = quantize(d[k], rq, dummy);
+            if ((unsigned)(code + radius) - 1u >= (unsigned)(2 * radius - 1)) esc_blk[base + (cc ? k / 2 : k)] = code;
+          }
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < N; ++k)
+        if ((k & 1) || !cc) coef_blk[base + (cc ? k / 2 : k)] = d[k];
     }
-    if (MODE == 0 && run.cnt) hist_add(hloc, hglob, radius, run.sym, run.cnt);
     T z[C];
     restrict_solve<T, N>(tb, d, z);
 #pragma unroll
-    for (int j = 0; j < C; ++j) T1[L * C + j] = z[j];
+    for (int j = 0; j < C; ++j) T1[(i0 * C + j) * N + i1] = z[j];
   }
   __syncthreads();
-  for (int L = threadIdx.x; L < N * C; L += blockDim.x) {
+  for (int L = threadIdx.x; L < N * C; L += blockDim.x) {  // L = i0*C + j2
     const int i0 = L / C, j2 = L - i0 * C;
     T d[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) d[i] = T1[(i0 * N + i) * C + j2];
+    for (int i = 0; i < N; ++i) d[i] = T1[L * N + i];
     T z[C];
     restrict_solve<T, N>(tb, d, z);
 #pragma unroll
-    for (int j = 0; j < C; ++j) T2[(i0 * C + j) * C + j2] = z[j];
+    for (int j = 0; j < C; ++j) T2[(j * C + j2) * N + i0] = z[j];
   }
   __syncthreads();
-  for (int L = threadIdx.x; L < C * C; L += blockDim.x) {
+  for (int L = threadIdx.x; L < C * C; L += blockDim.x) {  // L = j1*C + j2
     const int j1 = L / C, j2 = L - j1 * C;
     T d[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) d[i] = T2[(i * C + j1) * C + j2];
+    for (int i = 0; i < N; ++i) d[i] = T2[L * N + i];
     T z[C];
     restrict_solve<T, N>(tb, d, z);
 #pragma unroll
@@ -186,27 +194,60 @@ template <typename T, int N, int L, int K, int B, int MODE>
 struct FwdLevels {
   __device__ __forceinline__ static void run(const LevelBufs<T>& bufs, T* T1, T* T2, const T* rq, uint16_t* stage,
                                              int32_t* esc_blk, T* coef_blk, unsigned* hloc, unsigned* hglob,
-                                             int radius, bool& ovf) {
+                                             int radius, bool& ovf, unsigned& centre) {
     level_fwd<T, N, MODE>(bufs(L), T1, T2, bufs(L + 1), lvl_offset(B, L), rq[L], stage, esc_blk, coef_blk, hloc,
-                          hglob, radius, ovf);
+                          hglob, radius, ovf, centre);
     if constexpr (L + 1 < K)
       FwdLevels<T, (N + 1) / 2, L + 1, K, B, MODE>::run(bufs, T1, T2, rq, stage, esc_blk, coef_blk, hloc, hglob,
-                                                         radius, ovf);
+                                                         radius, ovf, centre);
   }
 };
 
+// Consecutive threads copy consecutive elements of the block (row-major), so
+// every warp instruction covers ~32 contiguous values of one or two rows;
+// the block origin and its in-domain extents are computed once per block and
+// the divisions are by compile-time constants.  cp.async zero-fills past the
+// domain.
 template <typename T, int B>
 __device__ __forceinline__ void issue_block_load(T* dst, const T* __restrict__ field, int64_t n0, int64_t n1,
                                                  int64_t n2, int64_t b0, int64_t b1, int64_t b2) {
+  const int64_t r0 = n0 - b0 * B, r1 = n1 - b1 * B, r2 = n2 - b2 * B;
+  const int lim0 = r0 < B ? (int)r0 : B, lim1 = r1 < B ? (int)r1 : B, lim2 = r2 < B ? (int)r2 : B;
+  const T* base = field + ((b0 * B) * n1 + b1 * B) * n2 + b2 * B;
+  const int64_t s0 = n1 * n2;
   for (int e = threadIdx.x; e < B * B * B; e += blockDim.x) {
     const int i0 = e / (B * B);
     const int r = e - i0 * (B * B);
     const int i1 = r / B;
     const int k = r - i1 * B;
-    const int64_t g0 = b0 * B + i0, g1 = b1 * B + i1, g2 = b2 * B + k;
-    const bool valid = g0 < n0 && g1 < n1 && g2 < n2;
-    const T* src = valid ? field + (g0 * n1 + g1) * n2 + g2 : field;
-    cp_async_zfill<sizeof(T)>(dst + e, src, valid);
+    const bool ok = (i0 < lim0) & (i1 < lim1) & (k < lim2);
+    const T* src = ok ? base + (i0 * s0 + i1 * n2 + k) : field;
+    cp_async_zfill<sizeof(T)>(dst + e, src, ok);
+  }
+}
+
+// Copy of n u16 symbols from shared to global memory with the widest aligned
+// stores the per-block offset allows.
+template <int PB>
+__device__ __forceinline__ void store_symbols(uint16_t* __restrict__ dst, const uint16_t* __restrict__ src,
+                                              int64_t sbase) {
+  if constexpr ((PB % 4) == 0) {
+    const uint2* s2 = reinterpret_cast<const uint2*>(src);
+    uint2* d2 = reinterpret_cast<uint2*>(dst);
+    for (int i = threadIdx.x; i < PB / 4; i += blockDim.x) d2[i] = s2[i];
+  } else if constexpr ((PB % 2) == 0) {
+    const uint32_t* s32 = reinterpret_cast<const uint32_t*>(src);
+    uint32_t* d32 = reinterpret_cast<uint32_t*>(dst);
+    for (int i = threadIdx.x; i < PB / 2; i += blockDim.x) d32[i] = s32[i];
+  } else {
+    if ((sbase & 1) == 0) {
+      const uint32_t* s32 = reinterpret_cast<const uint32_t*>(src);
+      uint32_t* d32 = reinterpret_cast<uint32_t*>(dst);
+      for (int i = threadIdx.x; i < PB / 2; i += blockDim.x) d32[i] = s32[i];
+      if (threadIdx.x == 0) dst[PB - 1] = src[PB - 1];
+    } else {
+      for (int i = threadIdx.x; i < PB; i += blockDim.x) dst[i] = src[i];
+    }
   }
 }
 
@@ -227,6 +268,7 @@ __global__ void __launch_bounds__(BlockCfg<T, B, K>::NT) block_fwd_kernel(BlockA
   if (MODE == 0)
     for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) hloc[i] = 0;
   bool ovf = false;
+  unsigned centre = 0;
   const int64_t nbc = (int64_t)a.nb1 * a.nb2;
   int64_t b = blockIdx.x;
   int buf = 0;
@@ -249,7 +291,7 @@ __global__ void __launch_bounds__(BlockCfg<T, B, K>::NT) block_fwd_kernel(BlockA
     const int64_t sbase = b * (int64_t)Cfg::PB;
     LevelBufs<T> bufs{Abuf + buf * Cfg::A, cb0, cb1};
     FwdLevels<T, B, 0, K, B, MODE>::run(bufs, T1, T2, rq, stage, a.esc + (MODE == 0 ? sbase : 0),
-                                        a.coef + (MODE == 1 ? sbase : 0), hloc, a.hist, a.radius, ovf);
+                                        a.coef + (MODE == 1 ? sbase : 0), hloc, a.hist, a.radius, ovf, centre);
     // block coarse values -> gathered grid G
     {
       constexpr int M = Cfg::M;
@@ -260,23 +302,16 @@ __global__ void __launch_bounds__(BlockCfg<T, B, K>::NT) block_fwd_kernel(BlockA
         a.G[((b0 * M + j0) * a.g1 + (b1 * M + j1)) * a.g2 + (b2 * M + j2)] = cf[e];
       }
     }
-    if (MODE == 0) {
-      uint16_t* dst = a.sym + sbase;
-      if (((sbase & 1) == 0)) {
-        const uint32_t* s32 = reinterpret_cast<const uint32_t*>(stage);
-        uint32_t* d32 = reinterpret_cast<uint32_t*>(dst);
-        for (int i = threadIdx.x; i < Cfg::PB / 2; i += blockDim.x) d32[i] = s32[i];
-        if ((Cfg::PB & 1) && threadIdx.x == 0) dst[Cfg::PB - 1] = stage[Cfg::PB - 1];
-      } else {
-        for (int i = threadIdx.x; i < Cfg::PB; i += blockDim.x) dst[i] = stage[i];
-      }
-    }
+    if (MODE == 0) store_symbols<Cfg::PB>(a.sym + sbase, stage, sbase);
     __syncthreads();
     buf ^= 1;
   }
   cp_async_wait<0>();
   if (MODE == 0) {
     if (ovf) atomicOr(&a.sc->status, ST_OVERFLOW);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) centre += __shfl_xor_sync(0xffffffffu, centre, o);
+    if ((threadIdx.x & 31) == 0 && centre) atomicAdd(hloc + (kHistWin / 2), centre);
     __syncthreads();
     const int lo = a.radius - kHistWin / 2;
     for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) {
@@ -322,25 +357,25 @@ __device__ __forceinline__ void level_inv(T* __restrict__ X, T* __restrict__ T1,
     T z[C];
     restrict_solve<T, N>(tb, d, z);
 #pragma unroll
-    for (int j = 0; j < C; ++j) T1[L * C + j] = z[j];
+    for (int j = 0; j < C; ++j) T1[(i0 * C + j) * N + i1] = z[j];
   }
   __syncthreads();
-  for (int L = threadIdx.x; L < N * C; L += blockDim.x) {
+  for (int L = threadIdx.x; L < N * C; L += blockDim.x) {  // L = i0*C + j2
     const int i0 = L / C, j2 = L - i0 * C;
     T d[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) d[i] = T1[(i0 * N + i) * C + j2];
+    for (int i = 0; i < N; ++i) d[i] = T1[L * N + i];
     T z[C];
     restrict_solve<T, N>(tb, d, z);
 #pragma unroll
-    for (int j = 0; j < C; ++j) T2[(i0 * C + j) * C + j2] = z[j];
+    for (int j = 0; j < C; ++j) T2[(j * C + j2) * N + i0] = z[j];
   }
   __syncthreads();
-  for (int L = threadIdx.x; L < C * C; L += blockDim.x) {
+  for (int L = threadIdx.x; L < C * C; L += blockDim.x) {  // L = j1*C + j2
     const int j1 = L / C, j2 = L - j1 * C;
     T d[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) d[i] = T2[(i * C + j1) * C + j2];
+    for (int i = 0; i < N; ++i) d[i] = T2[L * N + i];
     T z[C];
     restrict_solve<T, N>(tb, d, z);
 #pragma unroll

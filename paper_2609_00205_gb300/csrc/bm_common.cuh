@@ -14,6 +14,7 @@ enum : unsigned {
   ST_CORRUPT = 2u,    // decoding ran past a chunk / table bound
   ST_CAPACITY = 4u,   // a write would pass the output capacity
   ST_RAW = 8u,        // the stream must fall back to a raw copy
+  ST_TIMEOUT = 16u,   // a bounded wait gave up (never expected on a healthy GPU)
 };
 
 constexpr int kHeaderBytes = 256;

@@ -140,8 +140,9 @@ __global__ void gl_restrict(GLevel<T> L, const T* __restrict__ in, T* out, const
       ibase = (int64_t)j1 * c2 + j2; istride = (int64_t)c1 * c2; obase = ibase; ostride = istride; x = j1; y = j2;
     }
     const int n = D.n, c = D.c;
-    // forward sweep: y_J = r_J - tm_J y_{J-1}, stored in out
-    T yprev = T(0);
+    // band products r_J of the whole line first: independent loads that can
+    // be in flight together
+#pragma unroll 4
     for (int J = 0; J < c; ++J) {
       const int f = D.f0[J];
       T r = T(0);
@@ -150,7 +151,12 @@ __global__ void gl_restrict(GLevel<T> L, const T* __restrict__ in, T* out, const
         const int col = f + m;
         if (col < n) r = fma(D.band[5 * J + m], in[ibase + col * istride], r);
       }
-      const T yv = J ? fma(-D.tm[J], yprev, r) : r;
+      out[obase + J * ostride] = r;
+    }
+    // forward sweep: y_J = r_J - tm_J y_{J-1}, in place
+    T yprev = out[obase];
+    for (int J = 1; J < c; ++J) {
+      const T yv = fma(-D.tm[J], yprev, out[obase + J * ostride]);
       out[obase + J * ostride] = yv;
       yprev = yv;
     }

@@ -17,6 +17,9 @@ namespace bm {
 
 constexpr int kCbThreads = 1024;
 constexpr int kLutBits = 12;
+// Every chunk is split into eight equal runs; the stream stores the bit
+// offsets of runs 1..7 so that eight decoders can work on one chunk.
+constexpr int kSplits = 8;
 
 // Canonical-code tables shared by encoder and decoder.
 struct CanonTables {
@@ -367,189 +370,283 @@ __global__ void hist_kernel(const uint16_t* __restrict__ sym, unsigned long long
 }
 
 // ---------------------------------------------------------------------------
-// Encoding: one warp per chunk; lane j codes a contiguous slice of the chunk.
+// Single-pass encoder (decoupled look-back, Merrill & Garland 2016)
 // ---------------------------------------------------------------------------
-struct EncodeArgs {
+// Warps take chunks in ticket order.  A warp codes its chunk's bit count from
+// the symbols it holds in registers, publishes the chunk's (words, escapes)
+// aggregate, walks back over its predecessors until one has published an
+// inclusive prefix (bounded wait), publishes its own inclusive prefix and then
+// packs its codes at the now known word offset.  Every word is written once:
+// a lane's last, partial word is handed to the next lane by a shuffle.
+// Status word of a chunk: [flag:2][words:31][escapes:31], so one load sees a
+// consistent pair (inputs hold fewer than 2^31 symbols).
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagIncl = 2ull << 62;
+constexpr unsigned long long kM31 = (1ull << 31) - 1;
+constexpr long kSpinLimit = 1l << 24;
+__device__ __forceinline__ unsigned long long pack_status(unsigned long long flag, unsigned long long w,
+                                                          unsigned long long e) {
+  return flag | ((w & kM31) << 31) | (e & kM31);
+}
+
+struct FusedEncodeArgs {
   const uint16_t* sym;
-  const int32_t* esc;          // codes of escaped symbols (symbol 0), or null
+  const int32_t* esc;            // codes of escaped symbols (stream mode) or null
   unsigned long long n;
-  int chunk;
+  int chunk;                     // multiple of 32
   const uint8_t* lens;
   const unsigned* codes;
   int dict;
-  unsigned* chunk_words;       // [nch] (stream section)
-  unsigned* chunk_esc;         // [nch] scratch
-  unsigned long long* word_off;  // [nch+1]
-  unsigned long long* esc_off;   // [nch+1]
   unsigned long long nch;
-  uint8_t* out;                // stream base
+  unsigned* ticket;              // zeroed before launch
+  unsigned long long* st;        // [nch] look-back status words (zeroed)
+  unsigned* chunk_words;         // stream chunk table
+  uint16_t* splits;              // stream split offsets [nch][7]
+  unsigned* chunk_esc;           // scratch [nch]
+  int32_t* ocode;                // scratch outlier codes, stream order
+  uint8_t* out;                  // stream base
+  unsigned long long off_codebook;  // the bitstream starts at off_codebook + pad8(codebook bytes)
+  unsigned long long capacity;
   Scalars* sc;
 };
 
-__device__ __forceinline__ void lane_slice(const EncodeArgs& a, unsigned long long c, int lane,
-                                           unsigned long long& s0, unsigned long long& s1) {
-  const int per = a.chunk / 32;
-  const unsigned long long cb = c * (unsigned long long)a.chunk;
-  s0 = cb + (unsigned long long)lane * per;
-  s1 = s0 + per;
-  const unsigned long long ce = min(a.n, cb + (unsigned long long)a.chunk);
-  if (s0 > ce) s0 = ce;
-  if (s1 > ce) s1 = ce;
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.volatile.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
 }
+
+// Symbols of a lane's slice as eight groups of eight (one 16-byte load per
+// group); partial slices (the last chunk, or chunk lengths other than 2048)
+// are read one symbol at a time.
+struct LaneSlice {
+  const uint16_t* p;
+  int cnt;       // symbols in the slice
+  bool vec;      // 64 symbols, 16-byte aligned
+  __device__ __forceinline__ uint4 group(int g) const { return __ldg(reinterpret_cast<const uint4*>(p) + g); }
+};
 
 template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) chunk_bits_kernel(EncodeArgs a) {
-  __shared__ uint8_t lens[kMaxDict];
-  for (int i = threadIdx.x; i < a.dict; i += blockDim.x) lens[i] = a.lens[i];
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  for (unsigned long long c = blockIdx.x * (unsigned long long)WARPS + (threadIdx.x >> 5); c < a.nch;
-       c += (unsigned long long)gridDim.x * WARPS) {
-    unsigned long long s0, s1;
-    lane_slice(a, c, lane, s0, s1);
-    unsigned bits = 0, esc = 0;
-    for (unsigned long long i = s0; i < s1; ++i) {
-      const unsigned s = min((unsigned)a.sym[i], (unsigned)(a.dict - 1));
-      bits += lens[s];
-      esc += (s == 0);
-    }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      bits += __shfl_xor_sync(0xffffffffu, bits, o);
-      esc += __shfl_xor_sync(0xffffffffu, esc, o);
-    }
-    if (lane == 0) {
-      if (a.chunk_words) a.chunk_words[c] = (bits + 31u) >> 5;
-      a.chunk_esc[c] = a.esc ? esc : 0u;
-    }
-  }
-}
-
-// Exclusive scans of the chunk word counts and escape counts (one CTA), then
-// the stream offsets of the bitstream, the per-chunk escape counts (present
-// only when there are escapes) and the outlier codes.
-__global__ void __launch_bounds__(kCbThreads) chunk_scan_kernel(const unsigned* chunk_words, const unsigned* chunk_esc,
-                                                                unsigned long long nch, unsigned long long* word_off,
-                                                                unsigned long long* esc_off, Scalars* sc,
-                                                                unsigned long long off_codebook,
-                                                                unsigned long long raw_total,
-                                                                unsigned long long capacity, uint8_t* out) {
-  __shared__ unsigned long long wt[32], et[32];
-  __shared__ unsigned long long carry_w, carry_e;
-  __shared__ int s_write;
-  if (threadIdx.x == 0) { carry_w = 0; carry_e = 0; }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (unsigned long long base = 0; base < nch; base += blockDim.x) {
-    const unsigned long long i = base + threadIdx.x;
-    unsigned long long w = i < nch ? chunk_words[i] : 0ull;
-    unsigned long long e = i < nch ? chunk_esc[i] : 0ull;
-    unsigned long long xw = w, xe = e;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long yw = __shfl_up_sync(0xffffffffu, xw, o);
-      const unsigned long long ye = __shfl_up_sync(0xffffffffu, xe, o);
-      if (lane >= o) { xw += yw; xe += ye; }
-    }
-    if (lane == 31) { wt[wid] = xw; et[wid] = xe; }
-    __syncthreads();
-    if (wid == 0) {
-      unsigned long long tw = wt[lane], te = et[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long yw = __shfl_up_sync(0xffffffffu, tw, o);
-        const unsigned long long ye = __shfl_up_sync(0xffffffffu, te, o);
-        if (lane >= o) { tw += yw; te += ye; }
-      }
-      wt[lane] = tw;
-      et[lane] = te;
-    }
-    __syncthreads();
-    const unsigned long long bw = carry_w + (wid ? wt[wid - 1] : 0ull) + xw - w;
-    const unsigned long long be = carry_e + (wid ? et[wid - 1] : 0ull) + xe - e;
-    if (i < nch) { word_off[i] = bw; esc_off[i] = be; }
-    __syncthreads();
-    if (threadIdx.x == 0) { carry_w += wt[31]; carry_e += et[31]; }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    word_off[nch] = carry_w;
-    esc_off[nch] = carry_e;
-    sc->n_words = carry_w;
-    sc->n_outliers = carry_e;
-    const unsigned long long off_bits = off_codebook + pad8(sc->codebook_bytes);
-    const unsigned long long off_ce = off_bits + pad8(4ull * carry_w);
-    const unsigned long long off_out = off_ce + (carry_e ? pad8(4ull * nch) : 0ull);
-    const unsigned long long total = off_out + pad8(4ull * carry_e);
-    sc->off_bits = off_bits;
-    sc->off_chunk_esc = off_ce;
-    sc->off_outliers = off_out;
-    sc->total = total;
-    if (total >= raw_total || total > capacity) atomicOr(&sc->status, ST_RAW);
-    if (sc->status & ST_OVERFLOW) atomicOr(&sc->status, ST_RAW);
-    s_write = out && carry_e && !(sc->status & ST_RAW);
-  }
-  __syncthreads();
-  if (s_write) {
-    unsigned* dst = reinterpret_cast<unsigned*>(out + sc->off_chunk_esc);
-    for (unsigned long long i = threadIdx.x; i < nch; i += blockDim.x) dst[i] = chunk_esc[i];
-  }
-}
-
-template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) encode_kernel(EncodeArgs a) {
+__global__ void __launch_bounds__(WARPS * 32) encode_fused_kernel(FusedEncodeArgs a) {
   __shared__ uint8_t lens[kMaxDict];
   __shared__ unsigned codes[kMaxDict];
-  if (a.sc && (a.sc->status & ST_RAW)) return;
   for (int i = threadIdx.x; i < a.dict; i += blockDim.x) { lens[i] = a.lens[i]; codes[i] = a.codes[i]; }
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  unsigned* words = reinterpret_cast<unsigned*>(a.out + a.sc->off_bits);
-  int32_t* ocode = reinterpret_cast<int32_t*>(a.out + a.sc->off_outliers);
-  for (unsigned long long c = blockIdx.x * (unsigned long long)WARPS + (threadIdx.x >> 5); c < a.nch;
-       c += (unsigned long long)gridDim.x * WARPS) {
-    unsigned long long s0, s1;
-    lane_slice(a, c, lane, s0, s1);
-    unsigned bits = 0, esc = 0;
-    for (unsigned long long i = s0; i < s1; ++i) {
-      const unsigned s = min((unsigned)a.sym[i], (unsigned)(a.dict - 1));
-      bits += lens[s];
-      esc += (s == 0);
+  const unsigned dmax = (unsigned)(a.dict - 1);
+  const unsigned long long off_bits = a.off_codebook + pad8(a.sc->codebook_bytes);
+  unsigned* words = reinterpret_cast<unsigned*>(a.out + off_bits);
+  const unsigned long long word_cap = a.capacity > off_bits ? (a.capacity - off_bits) / 4 : 0ull;
+  const int per = a.chunk / 32;
+  while (true) {
+    unsigned long long c = 0;
+    if (lane == 0) c = atomicAdd(a.ticket, 1u);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    if (c >= a.nch) break;
+    const unsigned long long cb = c * (unsigned long long)a.chunk;
+    const unsigned long long ce = min(a.n, cb + (unsigned long long)a.chunk);
+    const unsigned long long s0 = min(ce, cb + (unsigned long long)lane * per);
+    const unsigned long long s1 = min(ce, s0 + per);
+    LaneSlice sl{a.sym + s0, (int)(s1 - s0), false};
+    sl.vec = sl.cnt == 64 && ((s0 & 7ull) == 0);
+    const bool warp_vec = __all_sync(0xffffffffu, sl.vec);
+    // pass 1: bits and escapes of the slice
+    unsigned bits = 0, nesc = 0;
+    if (warp_vec) {
+#pragma unroll 1
+      for (int g = 0; g < 8; ++g) {
+        const uint4 q = sl.group(g);
+        const unsigned w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+          const unsigned s = min((h & 1) ? (w4[h >> 1] >> 16) : (w4[h >> 1] & 0xFFFFu), dmax);
+          bits += lens[s];
+          nesc += s == 0;
+        }
+      }
+    } else {
+      for (int t = 0; t < sl.cnt; ++t) {
+        const unsigned s = min((unsigned)sl.p[t], dmax);
+        bits += lens[s];
+        nesc += s == 0;
+      }
     }
-    unsigned xb = bits, xe = esc;
+    if (!a.esc) nesc = 0;
+    unsigned xb = bits, xe = nesc;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const unsigned yb = __shfl_up_sync(0xffffffffu, xb, o);
       const unsigned ye = __shfl_up_sync(0xffffffffu, xe, o);
       if (lane >= o) { xb += yb; xe += ye; }
     }
-    const unsigned bit0 = xb - bits, esc0 = xe - esc;
-    const unsigned long long wbase = a.word_off[c];
-    const unsigned nw = (unsigned)(a.word_off[c + 1] - wbase);
-    for (unsigned w = lane; w < nw; w += 32) words[wbase + w] = 0u;
-    __syncwarp();
+    const unsigned tot_bits = __shfl_sync(0xffffffffu, xb, 31);
+    const unsigned tot_esc = __shfl_sync(0xffffffffu, xe, 31);
+    const unsigned W = (tot_bits + 31u) >> 5;
+    // publish the aggregate, then look back (a window of 32 predecessors per
+    // step, one per lane) until an inclusive prefix is found
+    unsigned long long pw = 0, pe = 0;
+    int timed_out = 0;
+    if (c == 0) {
+      if (lane == 0) atomicExch(a.st + 0, pack_status(kFlagIncl, W, tot_esc));
+    } else {
+      if (lane == 0) atomicExch(a.st + c, pack_status(kFlagAgg, W, tot_esc));
+      long long top = (long long)c - 1;  // highest predecessor not yet summed
+      long spins = 0;
+      while (top >= 0) {
+        const long long p = top - lane;
+        const unsigned long long sv = p >= 0 ? ld_volatile_u64(a.st + p) : kFlagIncl;  // before chunk 0: prefix 0
+        const unsigned flag = (unsigned)(sv >> 62);
+        // only the lanes up to the first unpublished one can be used
+        const unsigned unpub = __ballot_sync(0xffffffffu, flag == 0);
+        const unsigned incl = __ballot_sync(0xffffffffu, flag == 2);
+        const int first_incl = incl ? __ffs(incl) - 1 : 32;
+        const int first_unpub = unpub ? __ffs(unpub) - 1 : 32;
+        if (first_unpub <= first_incl && first_unpub < 32) {
+          if (first_unpub == 0) {  // nearest predecessor not published yet: wait
+            if (++spins > kSpinLimit) { timed_out = 1; break; }
+            __nanosleep(32);
+            continue;
+          }
+        }
+        const int take = min(first_incl + 1, first_unpub);  // lanes [0, take) are summed
+        unsigned long long w = 0, e = 0;
+        if (lane < take && p >= 0) { w = (sv >> 31) & kM31; e = sv & kM31; }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+          w += __shfl_xor_sync(0xffffffffu, w, o);
+          e += __shfl_xor_sync(0xffffffffu, e, o);
+        }
+        pw += w;
+        pe += e;
+        if (first_incl < take) break;  // reached an inclusive prefix (or the start)
+        top -= take;
+      }
+      timed_out = __shfl_sync(0xffffffffu, timed_out, 0);
+      if (!timed_out && lane == 0) {
+        __threadfence();
+        atomicExch(a.st + c, pack_status(kFlagIncl, pw + W, pe + tot_esc));
+      }
+    }
+    if (lane == 0) {
+      a.chunk_words[c] = W;
+      a.chunk_esc[c] = tot_esc;
+      if (c == a.nch - 1) {
+        a.sc->n_words = pw + W;
+        a.sc->n_outliers = pe + tot_esc;
+      }
+    }
+    timed_out = __shfl_sync(0xffffffffu, timed_out, 0);
+    if (timed_out) {
+      if (lane == 0) atomicOr(&a.sc->status, ST_TIMEOUT | ST_RAW);
+      break;
+    }
+    pw = __shfl_sync(0xffffffffu, pw, 0);
+    pe = __shfl_sync(0xffffffffu, pe, 0);
+    if (pw + W > word_cap) {  // the stream would not fit: it becomes a raw copy
+      if (lane == 0) atomicOr(&a.sc->status, ST_RAW);
+      continue;
+    }
+    if (!warp_vec) {  // a partial chunk: zero its words, shared words are ORed below
+      for (unsigned w = lane; w < W; w += 32) words[pw + w] = 0u;
+      __syncwarp();
+    }
+    // pass 2: pack MSB-first.  Complete words are stored as they fill (the
+    // first one is held back when it is shared with the previous lane).
+    const unsigned bit0 = xb - bits;
+    if ((lane & 3) == 0 && lane) a.splits[c * (kSplits - 1) + (lane >> 2) - 1] = (uint16_t)bit0;
+    unsigned long long epos = pe + (xe - nesc);
     unsigned long long acc = 0;
     unsigned nb = bit0 & 31u;
-    unsigned long long widx = wbase + (bit0 >> 5);
-    bool shared_first = (bit0 & 31u) != 0;
-    unsigned long long epos = a.esc_off[c] + esc0;
-    for (unsigned long long i = s0; i < s1; ++i) {
-      const unsigned s = min((unsigned)a.sym[i], (unsigned)(a.dict - 1));
+    const unsigned long long head_idx = pw + (bit0 >> 5);
+    unsigned long long widx = head_idx;
+    const bool head_partial = (bit0 & 31u) != 0;
+    bool pending_head = head_partial;
+    unsigned head = 0;
+    auto code_one = [&](unsigned s, int32_t ecode) {
+      s = min(s, dmax);
       const unsigned L = lens[s];
       acc = (acc << L) | codes[s];
       nb += L;
-      if (nb >= 32) {
-        const unsigned word = (unsigned)(acc >> (nb - 32));
-        if (shared_first) { atomicOr(words + widx, word); shared_first = false; }
-        else words[widx] = word;
-        ++widx;
-        nb -= 32;
-        acc &= (nb ? ((1ull << nb) - 1ull) : 0ull);
+      const bool full = nb >= 32;
+      const unsigned word = (unsigned)(acc >> (full ? nb - 32 : 0));
+      const bool keep = full && pending_head;
+      head = keep ? word : head;
+      if (full && !keep) words[widx] = word;
+      pending_head = pending_head && !full;
+      widx += full ? 1 : 0;
+      nb -= full ? 32 : 0;
+      acc &= (1ull << nb) - 1ull;
+      if (s == 0 && a.esc) a.ocode[epos++] = ecode;
+    };
+    if (warp_vec) {
+#pragma unroll 1
+      for (int g = 0; g < 8; ++g) {
+        const uint4 q = sl.group(g);
+        const unsigned w4[4] = {q.x, q.y, q.z, q.w};
+        // codes of this group's escaped symbols, loaded together
+        int32_t ev[8];
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+          const unsigned sh = (h & 1) ? (w4[h >> 1] >> 16) : (w4[h >> 1] & 0xFFFFu);
+          ev[h] = (sh == 0 && a.esc) ? __ldg(a.esc + s0 + 8 * g + h) : 0;
+        }
+#pragma unroll
+        for (int h = 0; h < 8; ++h)
+          code_one((h & 1) ? (w4[h >> 1] >> 16) : (w4[h >> 1] & 0xFFFFu), ev[h]);
       }
-      if (s == 0 && a.esc) ocode[epos++] = a.esc[i];
+      // every lane holds >= 64 bits here, so a shared word has exactly two owners
+      const unsigned tail = nb ? (unsigned)(acc << (32 - nb)) : 0u;
+      const unsigned from_prev = __shfl_up_sync(0xffffffffu, tail, 1);
+      if (head_partial) words[head_idx] = head | from_prev;
+      if (lane == 31 && nb) words[widx] = tail;
+    } else {
+      for (int t = 0; t < sl.cnt; ++t) {
+        const unsigned st = (unsigned)sl.p[t];
+        code_one(st, (st == 0 && a.esc) ? a.esc[s0 + t] : 0);
+      }
+      __syncwarp();
+      if (head_partial && !pending_head) atomicOr(words + head_idx, head);
+      if (nb) atomicOr(words + widx, (unsigned)(acc << (32 - nb)));
     }
-    if (nb) atomicOr(words + widx, (unsigned)(acc << (32 - nb)));
-    __syncwarp();
+  }
+}
+
+// After the fused encoder: stream offsets, per-chunk escape counts and the
+// outlier codes (moved from scratch), raw decision.
+__global__ void __launch_bounds__(256) encode_finish_kernel(const unsigned* chunk_esc, unsigned long long nch,
+                                                            const int32_t* ocode, uint8_t* out,
+                                                            unsigned long long off_codebook,
+                                                            unsigned long long raw_total,
+                                                            unsigned long long capacity, Scalars* sc) {
+  __shared__ int s_go;
+  __shared__ unsigned long long s_ce, s_out;
+  if (threadIdx.x == 0) {
+    const unsigned long long nw = sc->n_words, ne = sc->n_outliers;
+    const unsigned long long off_bits = off_codebook + pad8(sc->codebook_bytes);
+    const unsigned long long off_ce = off_bits + pad8(4ull * nw);
+    const unsigned long long off_out = off_ce + (ne ? pad8(4ull * nch) : 0ull);
+    const unsigned long long total = off_out + pad8(4ull * ne);
+    if (blockIdx.x == 0) {
+      sc->off_bits = off_bits;
+      sc->off_chunk_esc = off_ce;
+      sc->off_outliers = off_out;
+      sc->total = total;
+      if (total >= raw_total || total > capacity) atomicOr(&sc->status, ST_RAW);
+      if (sc->status & ST_OVERFLOW) atomicOr(&sc->status, ST_RAW);
+    }
+    const bool raw = (sc->status & (ST_RAW | ST_OVERFLOW)) || total >= raw_total || total > capacity;
+    s_go = !raw;
+    s_ce = off_ce;
+    s_out = off_out;
+  }
+  __syncthreads();
+  if (!s_go) return;
+  const unsigned long long ne = sc->n_outliers;
+  if (ne) {
+    unsigned* ce = reinterpret_cast<unsigned*>(out + s_ce);
+    for (unsigned long long i = blockIdx.x * 256ull + threadIdx.x; i < nch; i += gridDim.x * 256ull) ce[i] = chunk_esc[i];
+    int32_t* oc = reinterpret_cast<int32_t*>(out + s_out);
+    for (unsigned long long i = blockIdx.x * 256ull + threadIdx.x; i < ne; i += gridDim.x * 256ull) oc[i] = ocode[i];
   }
 }
 
@@ -630,13 +727,10 @@ __global__ void __launch_bounds__(kCbThreads) decode_tables_kernel(const uint8_t
 }
 
 struct DecodeArgs {
-  const unsigned* words;            // bitstream
+  const unsigned* words;               // bitstream
   unsigned long long n_words;
-  const unsigned long long* esc_off;  // [nch+1] first outlier of each chunk, or null without outliers
-  const int32_t* ocode;               // outlier codes in stream order
-  int32_t* esc;                       // codes of escaped symbols, indexed like sym
-  int stream_mode;                    // symbol 0 is the escape symbol (must have an outlier code)
   const unsigned long long* word_off;  // [nch+1]
+  const uint16_t* splits;              // [nch][7] bit offsets of runs 1..7
   unsigned long long nch;
   unsigned long long n;
   int chunk;
@@ -645,8 +739,10 @@ struct DecodeArgs {
   Scalars* sc;
 };
 
-// One thread per chunk, table-driven canonical decoding with a 64-bit window.
-__global__ void __launch_bounds__(256) decode_kernel(DecodeArgs a) {
+// One thread per run (an eighth of a chunk): table-driven canonical decoding
+// with a 64-bit window and a one-word look-ahead.  A run must end exactly
+// where the next one starts (the last run of a chunk within the chunk).
+__global__ void __launch_bounds__(128) decode_kernel(DecodeArgs a) {
   __shared__ unsigned lut[1 << kLutBits];
   __shared__ uint16_t canon[kMaxDict];
   __shared__ unsigned long long limit[kMaxLen + 2];
@@ -661,23 +757,44 @@ __global__ void __launch_bounds__(256) decode_kernel(DecodeArgs a) {
     fpos[threadIdx.x] = T->ct.first_pos[threadIdx.x];
   }
   __syncthreads();
-  for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < a.nch;
-       c += (unsigned long long)gridDim.x * blockDim.x) {
-    unsigned long long w = a.word_off[c];
-    const unsigned long long wend = a.word_off[c + 1];
-    if (wend < w || wend > a.n_words) { atomicOr(&a.sc->status, ST_CORRUPT); continue; }
-    const unsigned long long s0 = c * (unsigned long long)a.chunk;
-    const unsigned long long s1 = min(a.n, s0 + (unsigned long long)a.chunk);
+  const unsigned long long nruns = a.nch * kSplits;
+  const int sub = a.chunk / kSplits;
+  for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < nruns;
+       r += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long c = r / kSplits;
+    const int k = (int)(r % kSplits);
+    const unsigned long long cw0 = a.word_off[c], cw1 = a.word_off[c + 1];
+    if (cw1 < cw0 || cw1 > a.n_words) { atomicOr(&a.sc->status, ST_CORRUPT); continue; }
+    const unsigned long long cbits = (cw1 - cw0) * 32ull;
+    const unsigned long long b0 = k ? a.splits[c * (kSplits - 1) + k - 1] : 0ull;
+    const unsigned long long b1 = k < kSplits - 1 ? a.splits[c * (kSplits - 1) + k] : cbits;
+    if (b0 > b1 || b1 > cbits) { atomicOr(&a.sc->status, ST_CORRUPT); continue; }
+    const unsigned long long s0 = c * (unsigned long long)a.chunk + (unsigned long long)k * sub;
+    const unsigned long long s1 = min(a.n, s0 + (unsigned long long)sub);
+    // window: bits from bit position pos = cw0*32 + b0 on
+    unsigned long long w = cw0 + (b0 >> 5);
+    const unsigned long long wend = cw1;
+    const int skip = (int)(b0 & 31);
     unsigned long long buf = 0;
     int nbits = 0;
-    bool bad = false;
-    unsigned long long epos = a.esc_off ? a.esc_off[c] : 0ull;
-    const unsigned long long eend = a.esc_off ? a.esc_off[c + 1] : 0ull;
-    for (unsigned long long i = s0; i < s1; ++i) {
-      while (nbits <= 32 && w < wend) {
-        buf |= (unsigned long long)a.words[w++] << (32 - nbits);
+    unsigned nextw = w < wend ? __ldg(a.words + w) : 0u;
+    auto refill = [&]() {
+      if (nbits <= 32 && w < wend) {
+        buf |= (unsigned long long)nextw << (32 - nbits);
         nbits += 32;
+        ++w;
+        nextw = w < wend ? __ldg(a.words + w) : 0u;
       }
+    };
+    refill();
+    refill();
+    buf <<= skip;
+    nbits -= skip;
+    unsigned long long used = b0;  // bits consumed, from the chunk start
+    bool bad = false;
+    unsigned long long pack = 0;
+    for (unsigned long long i = s0; i < s1; ++i) {
+      refill();
       const unsigned peek = (unsigned)(buf >> 32);
       const unsigned e = lut[peek >> (32 - kLutBits)];
       unsigned s, L;
@@ -695,14 +812,46 @@ __global__ void __launch_bounds__(256) decode_kernel(DecodeArgs a) {
       if ((int)L > nbits) { bad = true; break; }
       buf <<= L;
       nbits -= (int)L;
-      a.sym[i] = (uint16_t)s;
-      if (s == 0 && a.stream_mode) {
-        if (epos >= eend) { bad = true; break; }
-        a.esc[i] = a.ocode[epos++];
+      used += L;
+      pack |= (unsigned long long)s << (16 * (i & 3));
+      if ((i & 3) == 3) {
+        *reinterpret_cast<unsigned long long*>(a.sym + (i - 3)) = pack;
+        pack = 0;
       }
     }
-    if (a.esc_off && !bad && epos != eend) bad = true;
+    if (!bad && (s1 & 3) && s1 > s0) {
+      for (unsigned long long i = max(s0, s1 & ~3ull); i < s1; ++i) a.sym[i] = (uint16_t)(pack >> (16 * (i & 3)));
+    }
+    if (!bad && (k < kSplits - 1 ? used != b1 : used > b1)) bad = true;
     if (bad) atomicOr(&a.sc->status, ST_CORRUPT);
+  }
+}
+
+// Escaped symbols (symbol 0) take the outlier codes in stream order: one
+// warp per chunk, each lane a slice of chunk/32 symbols.
+__global__ void __launch_bounds__(256) escape_fixup_kernel(const uint16_t* sym, unsigned long long n, int chunk,
+                                                           unsigned long long nch, const unsigned long long* esc_off,
+                                                           const int32_t* ocode, int32_t* esc, Scalars* sc) {
+  const int lane = threadIdx.x & 31;
+  const int per = chunk / 32;
+  for (unsigned long long c = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) / 32; c < nch;
+       c += (unsigned long long)gridDim.x * blockDim.x / 32) {
+    const unsigned long long cb = c * (unsigned long long)chunk;
+    const unsigned long long s0 = min(n, cb + (unsigned long long)lane * per), s1 = min(n, s0 + per);
+    unsigned cnt = 0;
+    for (unsigned long long i = s0; i < s1; ++i) cnt += sym[i] == 0;
+    unsigned x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    const unsigned total = __shfl_sync(0xffffffffu, x, 31);
+    if (lane == 0 && esc_off[c] + total != esc_off[c + 1]) atomicOr(&sc->status, ST_CORRUPT);
+    if (esc_off[c] + total != esc_off[c + 1]) continue;
+    unsigned long long e = esc_off[c] + (x - cnt);
+    for (unsigned long long i = s0; i < s1; ++i)
+      if (sym[i] == 0) esc[i] = ocode[e++];
   }
 }
 

@@ -135,8 +135,8 @@ def test_gpu_decodes_oracle_stream(bm, case):
 
 
 @pytest.mark.parametrize("scale,esc,chunk,dict_size", [
-    (0.3, 0.0, 2048, 8192), (5.0, 0.001, 1024, 8192), (300.0, 0.01, 4096, 8192), (0.0, 0.0, 64, 64),
-    (40.0, 0.0, 8192, 1024), (2000.0, 0.0, 2048, 8192),
+    (0.3, 0.0, 2048, 8192), (5.0, 0.001, 1024, 8192), (300.0, 0.01, 1536, 8192), (0.0, 0.0, 64, 64),
+    (40.0, 0.0, 256, 1024), (2000.0, 0.0, 2048, 8192),
 ])
 def test_huffman_bit_exact(bm, scale, esc, chunk, dict_size):
     sym = fields.laplace_symbols(300_007, dict_size // 2, scale, seed=17, escape_rate=esc)
@@ -216,3 +216,5 @@ def test_invalid_arguments(bm):
         bm.compress(t, 1e-3, block=9, levels=4)
     with pytest.raises(bm.BlockMGARDError):
         bm.compress(t, 1e-3, chunk=100)
+    with pytest.raises(bm.BlockMGARDError):
+        bm.compress(t, 1e-3, chunk=4096)

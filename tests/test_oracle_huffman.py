@@ -44,7 +44,8 @@ def test_golden_codes(row):
     # when that does not change the lengths
     L2 = oracle.huffman_lengths(np.bincount(allsym, minlength=f.size).astype(np.uint64))
     if list(L2) == list(L):
-        off_w = (4 * meta["n_chunks"] + 7) // 8 * 8 + (meta["codebook_bytes"] + 7) // 8 * 8
+        off_w = ((4 * meta["n_chunks"] + 7) // 8 * 8 + (14 * meta["n_chunks"] + 7) // 8 * 8
+                 + (meta["codebook_bytes"] + 7) // 8 * 8)
         w0 = sec[off_w:off_w + 4].view(np.uint32)[0]
         assert w0 == int(words, 16)
 
