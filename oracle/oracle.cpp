@@ -18,9 +18,14 @@
 //   * per-block ROI tolerance, tau_global = min_i tau_i ............ Sec. III-C
 //   * Huffman coding of the quantised symbols (outliers, histogram,
 //     codebook, encoding, concatenation) .......................... Sec. III-B
-// Readings where the paper is silent (coordinates of the global levels, the
-// exact error split, the FP round-off margin, rounding ties, Huffman tie
-// breaks, the byte layout of the stream) are the ones listed in the design doc.
+// Where the paper is silent this oracle takes these readings: the global
+// levels use the physical coordinates of the gathered nodes; the error budget
+// gives every level an equal share tau'/(N+1) divided by the level's exact
+// L-inf operator constant A_l; tau' = tau minus a round-off margin of
+// kappa*eps*(N+1)*max|u| (kappa = 8); quantisation rounds half up
+// (floor(c/q + 1/2)); Huffman merging takes a leaf before an internal node of
+// equal weight, and canonical codes are assigned in (length, symbol) order;
+// the byte layout of the stream is the one written by compress() below.
 //
 // Everything is dense and direct: the 1-D operators are assembled as full
 // matrices (I, M_f, M_c, P = M_c^{-1} I^T M_f) and applied as mode products.
@@ -622,7 +627,12 @@ std::vector<uint32_t> canonical_codes(const std::vector<uint8_t>& len) {
 }
 
 // ---------------------------------------------------------------------------
-// Byte stream (layout in DESIGN.md, "Stream format")
+// Byte stream.  A 256-byte header (magic, flags, shape, parameters, counts and
+// the byte offset of every section), then, each padded to 8 bytes: tolerance
+// tiers (f64), q table (f64), block tiers (u8, only with several tiers), chunk
+// word counts (u32), split offsets (u16, 7 per chunk), codebook runs, escape
+// counts per chunk (u32, only with outliers), outlier codes (i32), bitstream
+// (u32 words).  A raw stream is the header followed by the field.
 // ---------------------------------------------------------------------------
 constexpr uint32_t kMagic = 0x31474D42u;  // "BMG1"
 constexpr size_t kHeader = 256;
@@ -884,9 +894,6 @@ std::vector<uint8_t> compress(const double* u, const int64_t* shape, bool f64, d
   w.put_at<uint64_t>(160, (uint64_t)w.b.size());
   w.b.insert(w.b.end(), h.codebook.begin(), h.codebook.end());
   w.pad8();
-  w.put_at<uint64_t>(168, (uint64_t)w.b.size());
-  for (uint32_t x : h.words) w.put<uint32_t>(x);
-  w.pad8();
   // escape counts per chunk, present only when there are outliers
   w.put_at<uint64_t>(208, (uint64_t)w.b.size());
   if (!out_code.empty())
@@ -894,6 +901,11 @@ std::vector<uint8_t> compress(const double* u, const int64_t* shape, bool f64, d
   w.pad8();
   w.put_at<uint64_t>(176, (uint64_t)w.b.size());
   for (int32_t x : out_code) w.put<int32_t>(x);
+  w.pad8();
+  // the bitstream comes last: every offset before it follows from the
+  // codebook and the number of outliers alone
+  w.put_at<uint64_t>(168, (uint64_t)w.b.size());
+  for (uint32_t x : h.words) w.put<uint32_t>(x);
   w.pad8();
   w.put_at<uint64_t>(184, (uint64_t)w.b.size());
   if (w.b.size() >= kHeader + nel * esize) return finish_raw();

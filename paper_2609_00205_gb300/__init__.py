@@ -41,7 +41,9 @@ _lib = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    """libbm.so in the package tree; BM_LIBRARY overrides it (a build of the
+    same sources with other compile-time options)."""
+    return os.environ.get("BM_LIBRARY", _build.LIB)
 
 
 def load():
@@ -49,9 +51,10 @@ def load():
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(_build.LIB):
-        raise RuntimeError("libbm.so is not built (%s); run __graft_entry__.build()" % _build.LIB)
-    L = ctypes.CDLL(_build.LIB)
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError("libbm.so is not built (%s); run __graft_entry__.build()" % path)
+    L = ctypes.CDLL(path)
     P = ctypes.POINTER
     vp, sz, i64, u64 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int64, ctypes.c_uint64
     L.bm_compress_bound.argtypes = [ctypes.c_int, P(i64), ctypes.c_int]

@@ -51,11 +51,16 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, jobs: int | None = None, out: str | None = None,
+          defines: tuple = ()) -> str:
+    """Compile and link libbm.so (into ``out`` if given, with extra -D
+    ``defines``)."""
+    lib = out or LIB
+    if not force and out is None and not defines and up_to_date():
         return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
-    obj_dir = os.path.join(OUT_DIR, "obj")
+    out_dir = os.path.dirname(lib)
+    os.makedirs(out_dir, exist_ok=True)
+    obj_dir = os.path.join(out_dir, "obj")
     os.makedirs(obj_dir, exist_ok=True)
     nvcc = _nvcc()
     cmds = []
@@ -63,7 +68,7 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
     for src in CU_SOURCES:
         obj = os.path.join(obj_dir, src.replace(".cu", ".o"))
         objs.append(obj)
-        cmds.append([nvcc, *NVCC_FLAGS, *ARCH, "-c", os.path.join(CSRC, src), "-o", obj])
+        cmds.append([nvcc, *NVCC_FLAGS, *["-D" + d for d in defines], *ARCH, "-c", os.path.join(CSRC, src), "-o", obj])
     for src in CPP_SOURCES:
         obj = os.path.join(obj_dir, src.replace(".cpp", ".o"))
         objs.append(obj)
@@ -80,10 +85,10 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
         for out in ex.map(run, cmds):
             if verbose and out.strip():
                 print(out)
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

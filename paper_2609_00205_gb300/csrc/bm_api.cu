@@ -20,6 +20,10 @@
 #include "bm_internal.h"
 #include "bm_plan.h"
 
+#ifndef BM_FWD_HIST
+#define BM_FWD_HIST 0
+#endif
+
 namespace bm {
 namespace {
 
@@ -472,12 +476,12 @@ __global__ void header_kernel(HeaderArgs a) {
   put<uint64_t>(o, 208, sc->off_chunk_esc);
   put<uint64_t>(o, 216, a.off_splits);
   for (int i = 224; i < kHeaderBytes; ++i) o[i] = 0;
-  const unsigned long long wend = sc->off_bits + 4ull * sc->n_words;
-  for (unsigned long long i = wend; i < sc->off_chunk_esc; ++i) o[i] = 0;
   const unsigned long long cend = sc->off_chunk_esc + (sc->n_outliers ? 4ull * a.n_chunks : 0ull);
   for (unsigned long long i = cend; i < sc->off_outliers; ++i) o[i] = 0;
   const unsigned long long oend = sc->off_outliers + 4ull * sc->n_outliers;
-  for (unsigned long long i = oend; i < sc->total; ++i) o[i] = 0;
+  for (unsigned long long i = oend; i < sc->off_bits; ++i) o[i] = 0;
+  const unsigned long long wend = sc->off_bits + 4ull * sc->n_words;
+  for (unsigned long long i = wend; i < sc->total; ++i) o[i] = 0;
 }
 
 __global__ void raw_header_kernel(uint8_t* o, int f64, int B, int64_t s0, int64_t s1, int64_t s2, int rel, double tol,
@@ -788,10 +792,8 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   uint8_t* dbt = cv.take<uint8_t>(h.nblocks);
   uint16_t* sym = cv.take<uint16_t>((size_t)h.n_coeffs);
   int32_t* esc = cv.take<int32_t>((size_t)h.n_coeffs);
-  unsigned* chunk_esc = cv.take<unsigned>(L.nch);
   unsigned char* tickets = cv.take<unsigned char>(256 + 16ull * L.nch);  // ticket, then look-back status words
   unsigned long long* lb_status = reinterpret_cast<unsigned long long*>(tickets + 256);
-  int32_t* ocode = cv.take<int32_t>((size_t)h.n_coeffs);
 
   unsigned char* hp = reinterpret_cast<unsigned char*>(ws->h);
   Scalars* hsc = reinterpret_cast<Scalars*>(hp);
@@ -842,9 +844,16 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   fo.sym = sym; fo.esc = esc; fo.hist = hist; fo.tier = ntiers > 1 ? dbt : nullptr; fo.rq = rq;
   fo.ntiers = ntiers; fo.radius = prm.radius; fo.sc = sc;
   if (bm_status st = run_decompose<T>(*P, field, 0, fo, cv, s)) return st;
+  if (!BM_FWD_HIST) {  // the block kernel did not count its symbols
+    Stage st("histogram");
+    const unsigned long long nloc = (unsigned long long)h.nblocks * h.per_block;
+    hist_range_kernel<<<num_sms() * 4, 256, 0, s>>>(sym, 0, nloc, dict, (unsigned)prm.radius, hist);
+    BM_LAUNCHED();
+  }
   {
     Stage st("huffman_codebook");
-    CodebookArgs ca{hist, dict, lens, codes, prefix_fits ? out : nullptr, L.off_codebook, cap, sc};
+    CodebookArgs ca{hist, dict, lens, codes, prefix_fits ? out : nullptr, L.off_codebook, cap, sc, 1, L.nch,
+                    raw_total};
     BM_CUDA(cudaFuncSetAttribute(codebook_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CbSmem)));
     codebook_kernel<<<1, kCbThreads, sizeof(CbSmem), s>>>(ca);
     BM_LAUNCHED();
@@ -857,12 +866,11 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     ea.sym = sym; ea.esc = esc; ea.n = (unsigned long long)h.n_coeffs; ea.chunk = prm.chunk;
     ea.lens = lens; ea.codes = codes; ea.dict = dict; ea.nch = L.nch;
     ea.ticket = reinterpret_cast<unsigned*>(tickets); ea.st = lb_status;
-    ea.chunk_words = reinterpret_cast<unsigned*>(out + L.off_chunks); ea.chunk_esc = chunk_esc; ea.ocode = ocode;
+    ea.chunk_words = reinterpret_cast<unsigned*>(out + L.off_chunks);
     ea.splits = reinterpret_cast<uint16_t*>(out + L.off_splits);
-    ea.out = out; ea.off_codebook = L.off_codebook; ea.capacity = cap; ea.sc = sc;
-    encode_fused_kernel<8><<<grid_for((int64_t)L.nch * 32, 256, 8), 256, 0, s>>>(ea);
-    encode_finish_kernel<<<grid_for((int64_t)L.nch, 256, 4), 256, 0, s>>>(chunk_esc, L.nch, ocode, out, L.off_codebook,
-                                                                        raw_total, cap, sc);
+    ea.out = out; ea.capacity = cap; ea.sc = sc;
+    encode_fused_kernel<8><<<grid_for((int64_t)L.nch * 32, 256, 4), 256, 0, s>>>(ea);
+    encode_finish_kernel<<<1, 32, 0, s>>>(raw_total, cap, sc);
     g_launches.fetch_add(2);
     HeaderArgs ha{};
     ha.out = out; ha.f64 = f64; ha.B = h.B; ha.K = h.K; ha.M = h.M; ha.chunk = prm.chunk; ha.radius = prm.radius;
@@ -878,6 +886,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   }
   BM_CUDA(cudaStreamSynchronize(s));
   if (hsc->status & ST_TIMEOUT) return fail(BM_ERR_CUDA, "encoder look-back wait timed out");
+  if (hsc->status & ST_CORRUPT) return fail(BM_ERR_CUDA, "internal error: escape count differs from the histogram");
   if (hsc->status & ST_RAW) {
     Stage st("raw_copy");
     raw_header_kernel<<<1, 32, 0, s>>>(out, f64, h.B, shape[0], shape[1], shape[2], rel, tol, raw_total, sc);
@@ -946,9 +955,9 @@ bm_status parse_header(const unsigned char* hb, size_t in_bytes, Header& H) {
       H.off_btier != H.off_qtab + pad8(8ull * nq) || H.off_chunks < H.off_btier ||
       H.off_splits != H.off_chunks + pad8(4ull * H.n_chunks) ||
       H.off_codebook != H.off_splits + pad8(2ull * (kSplits - 1) * H.n_chunks) ||
-      H.off_bits != H.off_codebook + pad8(H.codebook_bytes) || H.off_chunk_esc != H.off_bits + pad8(4ull * H.n_words) ||
+      H.off_chunk_esc != H.off_codebook + pad8(H.codebook_bytes) ||
       H.off_outliers != H.off_chunk_esc + (H.n_outliers ? pad8(4ull * H.n_chunks) : 0ull) ||
-      H.total != H.off_outliers + pad8(4ull * H.n_outliers))
+      H.off_bits != H.off_outliers + pad8(4ull * H.n_outliers) || H.total != H.off_bits + pad8(4ull * H.n_words))
     return fail(BM_ERR_CORRUPT, "section offsets inconsistent");
   if (H.n_chunks != (H.n_symbols + H.chunk - 1) / H.chunk) return fail(BM_ERR_CORRUPT, "chunk count");
   if (H.n_outliers > H.n_symbols) return fail(BM_ERR_CORRUPT, "outlier count");
@@ -1004,7 +1013,8 @@ bm_status decode_symbols(const uint8_t* in, const Header& H, Carver& cv, uint16_
     BM_LAUNCHED();
     if (stream_mode && H.n_outliers) {
       escape_fixup_kernel<<<grid_for((int64_t)H.n_chunks * 32, 256, 8), 256, 0, s>>>(
-          sym, H.n_symbols, H.chunk, H.n_chunks, esc_off, reinterpret_cast<const int32_t*>(in + H.off_outliers), esc, sc);
+          sym, H.n_symbols, H.chunk, H.n_chunks, esc_off, reinterpret_cast<const int32_t*>(in + H.off_outliers),
+          H.n_outliers, esc, sc);
       BM_LAUNCHED();
     }
     BM_CUDA(cudaGetLastError());
@@ -1269,7 +1279,6 @@ bm_status bm_huffman_encode(const uint16_t* d_symbols, uint64_t n, int dict_size
   unsigned* hist = cv.take<unsigned>(dict_size);
   uint8_t* lens = cv.take<uint8_t>(dict_size);
   unsigned* codes = cv.take<unsigned>(dict_size);
-  unsigned* chunk_esc = cv.take<unsigned>(nch);
   unsigned char* tickets = cv.take<unsigned char>(256 + 16ull * nch);
   uint8_t* out = reinterpret_cast<uint8_t*>(d_out);
   BM_CUDA(cudaMemsetAsync(sc, 0, sizeof(Scalars), s));
@@ -1283,7 +1292,7 @@ bm_status bm_huffman_encode(const uint16_t* d_symbols, uint64_t n, int dict_size
   }
   {
     Stage st("huffman_codebook");
-    CodebookArgs ca{hist, dict_size, lens, codes, out, off_cb, out_capacity, sc};
+    CodebookArgs ca{hist, dict_size, lens, codes, out, off_cb, out_capacity, sc, 0, nch, ~0ull};
     BM_CUDA(cudaFuncSetAttribute(codebook_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CbSmem)));
     codebook_kernel<<<1, kCbThreads, sizeof(CbSmem), s>>>(ca);
     BM_LAUNCHED();
@@ -1294,11 +1303,11 @@ bm_status bm_huffman_encode(const uint16_t* d_symbols, uint64_t n, int dict_size
     ea.sym = d_symbols; ea.esc = nullptr; ea.n = n; ea.chunk = chunk_symbols; ea.lens = lens; ea.codes = codes;
     ea.dict = dict_size; ea.nch = nch; ea.ticket = reinterpret_cast<unsigned*>(tickets);
     ea.st = reinterpret_cast<unsigned long long*>(tickets + 256);
-    ea.chunk_words = reinterpret_cast<unsigned*>(out); ea.chunk_esc = chunk_esc; ea.ocode = nullptr; ea.out = out;
+    ea.chunk_words = reinterpret_cast<unsigned*>(out); ea.out = out;
     ea.splits = reinterpret_cast<uint16_t*>(out + off_sp);
-    ea.off_codebook = off_cb; ea.capacity = out_capacity; ea.sc = sc;
-    encode_fused_kernel<8><<<grid_for((int64_t)nch * 32, 256, 8), 256, 0, s>>>(ea);
-    encode_finish_kernel<<<1, 256, 0, s>>>(chunk_esc, nch, nullptr, out, off_cb, ~0ull, out_capacity, sc);
+    ea.capacity = out_capacity; ea.sc = sc;
+    encode_fused_kernel<8><<<grid_for((int64_t)nch * 32, 256, 4), 256, 0, s>>>(ea);
+    encode_finish_kernel<<<1, 32, 0, s>>>(~0ull, out_capacity, sc);
     zero_tail_kernel<<<1, 32, 0, s>>>(out, sc);
     g_launches.fetch_add(3);
     BM_CUDA(cudaGetLastError());
@@ -1432,7 +1441,6 @@ extern "C" bm_status bm_huffman_encode_noalloc(const uint16_t* d_symbols, uint64
   unsigned* hist = cv.take<unsigned>(dict_size);
   uint8_t* lens = cv.take<uint8_t>(dict_size);
   unsigned* codes = cv.take<unsigned>(dict_size);
-  unsigned* chunk_esc = cv.take<unsigned>(nch);
   unsigned char* tickets = cv.take<unsigned char>(256 + 16ull * nch);
   if (cv.off > kNoAllocBytes) return fail(BM_ERR_ARG, "request does not fit the static scratch");
   uint8_t* out = reinterpret_cast<uint8_t*>(d_out);
@@ -1442,18 +1450,18 @@ extern "C" bm_status bm_huffman_encode_noalloc(const uint16_t* d_symbols, uint64
   BM_CUDA(cudaMemsetAsync(tickets, 0, 256 + 16ull * nch, s));
   BM_CUDA(cudaMemsetAsync(out, 0, off_cb, s));
   hist_kernel<<<grid_for((int64_t)n, 256, 4), 256, 4 * dict_size, s>>>(d_symbols, n, dict_size, hist, sc);
-  CodebookArgs ca{hist, dict_size, lens, codes, out, off_cb, out_capacity, sc};
+  CodebookArgs ca{hist, dict_size, lens, codes, out, off_cb, out_capacity, sc, 0, nch, ~0ull};
   BM_CUDA(cudaFuncSetAttribute(codebook_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CbSmem)));
   codebook_kernel<<<1, kCbThreads, sizeof(CbSmem), s>>>(ca);
   FusedEncodeArgs ea{};
   ea.sym = d_symbols; ea.esc = nullptr; ea.n = n; ea.chunk = chunk_symbols; ea.lens = lens; ea.codes = codes;
   ea.dict = dict_size; ea.nch = nch; ea.ticket = reinterpret_cast<unsigned*>(tickets);
   ea.st = reinterpret_cast<unsigned long long*>(tickets + 256);
-  ea.chunk_words = reinterpret_cast<unsigned*>(out); ea.chunk_esc = chunk_esc; ea.ocode = nullptr; ea.out = out;
+  ea.chunk_words = reinterpret_cast<unsigned*>(out); ea.out = out;
   ea.splits = reinterpret_cast<uint16_t*>(out + off_sp);
-  ea.off_codebook = off_cb; ea.capacity = out_capacity; ea.sc = sc;
-  encode_fused_kernel<8><<<grid_for((int64_t)nch * 32, 256, 8), 256, 0, s>>>(ea);
-  encode_finish_kernel<<<1, 256, 0, s>>>(chunk_esc, nch, nullptr, out, off_cb, ~0ull, out_capacity, sc);
+  ea.capacity = out_capacity; ea.sc = sc;
+  encode_fused_kernel<8><<<grid_for((int64_t)nch * 32, 256, 4), 256, 0, s>>>(ea);
+  encode_finish_kernel<<<1, 32, 0, s>>>(~0ull, out_capacity, sc);
   zero_tail_kernel<<<1, 32, 0, s>>>(out, sc);
   g_launches.fetch_add(6);
   BM_CUDA(cudaGetLastError());

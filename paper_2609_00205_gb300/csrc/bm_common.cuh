@@ -28,7 +28,7 @@ __host__ __device__ inline uint64_t pad8(uint64_t x) { return (x + 7) & ~uint64_
 struct Scalars {
   unsigned long long maxabs_bits;  // max |u| as IEEE bits (float bits in the low word for FP32)
   unsigned status;                 // ST_* bits
-  unsigned pad0;
+  unsigned skip;                   // set before the encoder when the stream is already known to be raw
   unsigned long long n_words;      // Huffman words of the whole stream
   unsigned long long n_outliers;
   unsigned long long codebook_bytes;
@@ -40,6 +40,7 @@ struct Scalars {
   double max_abs;
   double margin;
   unsigned long long max_len;
+  unsigned long long esc_seen;     // escapes the encoder met (must equal n_outliers)
 };
 
 // ---------------------------------------------------------------------------

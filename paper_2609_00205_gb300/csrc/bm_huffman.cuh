@@ -152,6 +152,9 @@ struct CodebookArgs {
   unsigned long long off;
   unsigned long long capacity;
   Scalars* sc;
+  int esc_mode;                  // symbol 0 is the escape of an outlier code
+  unsigned long long nch;        // chunks
+  unsigned long long raw_total;  // size of the raw stream (~0: no raw fallback)
 };
 
 // Shared memory of the codebook kernel (dynamic).
@@ -171,7 +174,9 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(CodebookArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CbSmem& S = *reinterpret_cast<CbSmem*>(smem_raw);
   __shared__ unsigned s_n, s_lp, s_qp, s_qe, s_pl, s_pq, s_leaves, s_rounds, s_maxd, s_total;
+  __shared__ unsigned long long s_bits;
   const int dict = a.dict;
+  if (threadIdx.x == 0) s_bits = 0;
   uint16_t* merged = reinterpret_cast<uint16_t*>(S.keys);                      // [2*kMaxDict]
   uint16_t* round_end = reinterpret_cast<uint16_t*>(S.keys) + 2 * kMaxDict;    // [kMaxDict]
   for (int shift = 0;; ++shift) {
@@ -342,11 +347,32 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(CodebookArgs a) {
     if (threadIdx.x == 0)
       for (unsigned long long t = total; t < pad8(total); ++t) a.out[a.off + t] = 0;
   }
+  // 6. layout of the rest of the stream (escape counts, outlier codes, then
+  // the bitstream) and a lower bound on its size: the bitstream holds exactly
+  // sum_s f_s len_s bits plus the padding of each chunk to whole words
+  unsigned long long my_bits = 0;
+  for (int s = threadIdx.x; s < dict; s += blockDim.x) my_bits += (unsigned long long)a.hist[s] * S.len[s];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) my_bits += __shfl_xor_sync(0xffffffffu, my_bits, o);
+  if ((threadIdx.x & 31) == 0 && my_bits) atomicAdd(&s_bits, my_bits);
+  __syncthreads();
   if (threadIdx.x == 0) {
-    a.sc->codebook_bytes = total;
-    a.sc->n_runs = (unsigned long long)nruns;
-    a.sc->max_len = S.ct.max_len;
-    if (a.out && !fits) atomicOr(&a.sc->status, ST_CAPACITY | ST_RAW);
+    Scalars* sc = a.sc;
+    sc->codebook_bytes = total;
+    sc->n_runs = (unsigned long long)nruns;
+    sc->max_len = S.ct.max_len;
+    if (a.out && !fits) atomicOr(&sc->status, ST_CAPACITY | ST_RAW);
+    const unsigned long long nout = a.esc_mode ? (unsigned long long)a.hist[0] : 0ull;
+    const unsigned long long off_ce = a.off + pad8(total);
+    const unsigned long long off_out = off_ce + (nout ? pad8(4ull * a.nch) : 0ull);
+    const unsigned long long off_bits = off_out + pad8(4ull * nout);
+    const unsigned long long min_total = off_bits + pad8(4ull * ((s_bits + 31ull) / 32ull));
+    sc->n_outliers = nout;
+    sc->off_chunk_esc = off_ce;
+    sc->off_outliers = off_out;
+    sc->off_bits = off_bits;
+    if (min_total >= a.raw_total || off_bits > a.capacity) atomicOr(&sc->status, ST_RAW);
+    sc->skip = (sc->status & (ST_RAW | ST_OVERFLOW)) ? 1u : 0u;
   }
 }
 
@@ -364,6 +390,53 @@ __global__ void hist_kernel(const uint16_t* __restrict__ sym, unsigned long long
     else bad = true;
   }
   if (bad) atomicOr(&sc->status, ST_CORRUPT);
+  __syncthreads();
+  for (int i = threadIdx.x; i < dict; i += blockDim.x)
+    if (hs[i]) atomicAdd(hist + i, hs[i]);
+}
+
+// Histogram of a symbol range [s0, s1) with 16-byte loads.  The seven
+// symbols around the centre (codes -3..3, most of the symbols of quantised
+// coefficients) are counted in registers; the rest with shared atomics.
+__global__ void __launch_bounds__(256) hist_range_kernel(const uint16_t* __restrict__ sym, unsigned long long s0,
+                                                         unsigned long long s1, int dict, unsigned centre_sym,
+                                                         unsigned* hist) {
+  __shared__ unsigned hs[kMaxDict];
+  for (int i = threadIdx.x; i < dict; i += blockDim.x) hs[i] = 0;
+  __syncthreads();
+  unsigned c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0, c6 = 0;
+  const unsigned lo = centre_sym - 3u;
+  auto count = [&](unsigned s) {
+    const unsigned d = s - lo;
+    c0 += d == 0; c1 += d == 1; c2 += d == 2; c3 += d == 3; c4 += d == 4; c5 += d == 5; c6 += d == 6;
+    if (d > 6u && s < (unsigned)dict) atomicAdd(hs + s, 1u);
+  };
+  const unsigned long long a0 = min(s1, (s0 + 7) & ~7ull);  // 16-byte aligned start
+  const unsigned long long tid = blockIdx.x * 256ull + threadIdx.x, nth = gridDim.x * 256ull;
+  for (unsigned long long i = s0 + tid; i < a0; i += nth) count(sym[i]);
+  const unsigned long long nv = (s1 - a0) / 8;
+  const uint4* pv = reinterpret_cast<const uint4*>(sym + a0);
+  unsigned long long v = tid;
+  for (; v + nth < nv; v += 2 * nth) {
+    const uint4 q = __ldg(pv + v), r = __ldg(pv + v + nth);
+    const unsigned w8[8] = {q.x, q.y, q.z, q.w, r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int h = 0; h < 8; ++h) { count(w8[h] & 0xFFFFu); count(w8[h] >> 16); }
+  }
+  for (; v < nv; v += nth) {
+    const uint4 q = __ldg(pv + v);
+    const unsigned w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int h = 0; h < 4; ++h) { count(w4[h] & 0xFFFFu); count(w4[h] >> 16); }
+  }
+  for (unsigned long long i = a0 + nv * 8 + tid; i < s1; i += nth) count(sym[i]);
+  unsigned cc[7] = {c0, c1, c2, c3, c4, c5, c6};
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) cc[j] += __shfl_xor_sync(0xffffffffu, cc[j], o);
+    if ((threadIdx.x & 31) == 0 && cc[j] && lo + j < (unsigned)dict) atomicAdd(hs + lo + j, cc[j]);
+  }
   __syncthreads();
   for (int i = threadIdx.x; i < dict; i += blockDim.x)
     if (hs[i]) atomicAdd(hist + i, hs[i]);
@@ -402,10 +475,7 @@ struct FusedEncodeArgs {
   unsigned long long* st;        // [nch] look-back status words (zeroed)
   unsigned* chunk_words;         // stream chunk table
   uint16_t* splits;              // stream split offsets [nch][7]
-  unsigned* chunk_esc;           // scratch [nch]
-  int32_t* ocode;                // scratch outlier codes, stream order
-  uint8_t* out;                  // stream base
-  unsigned long long off_codebook;  // the bitstream starts at off_codebook + pad8(codebook bytes)
+  uint8_t* out;                  // stream base; the codebook kernel put the section offsets in sc
   unsigned long long capacity;
   Scalars* sc;
 };
@@ -416,28 +486,107 @@ __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned lon
   return v;
 }
 
-// Symbols of a lane's slice as eight groups of eight (one 16-byte load per
-// group); partial slices (the last chunk, or chunk lengths other than 2048)
-// are read one symbol at a time.
-struct LaneSlice {
-  const uint16_t* p;
-  int cnt;       // symbols in the slice
-  bool vec;      // 64 symbols, 16-byte aligned
-  __device__ __forceinline__ uint4 group(int g) const { return __ldg(reinterpret_cast<const uint4*>(p) + g); }
-};
+constexpr int kEncGroups = 8;  // a lane's slice: up to 8 groups of 8 symbols (chunk <= 2048)
 
+__device__ __forceinline__ unsigned sym_of(const uint4* q, int i) {
+  const unsigned w = (i & 4) ? ((i & 2) ? q[i >> 3].w : q[i >> 3].z) : ((i & 2) ? q[i >> 3].y : q[i >> 3].x);
+  return (i & 1) ? (w >> 16) : (w & 0xFFFFu);
+}
+
+// Codes of a symbol: (code, length) from one packed word (code | len << 26)
+// when every code has at most 26 bits, else from two tables.
+template <bool PACKED>
+__device__ __forceinline__ void code_of(const unsigned* codes, const uint8_t* lens, unsigned s, unsigned& c,
+                                        unsigned& L) {
+  const unsigned cw = codes[s];
+  if (PACKED) { c = cw & 0x3FFFFFFu; L = cw >> 26; }
+  else { c = cw; L = lens[s]; }
+}
+
+// Bits and escape mask of a lane's vector slice (G groups held in registers).
+template <bool PACKED>
+__device__ __forceinline__ void slice_bits(const uint4* q, int G, unsigned dmax, const unsigned* codes,
+                                           const uint8_t* lens, unsigned& bits, unsigned long long& emask) {
+  bits = 0;
+  emask = 0;
+#pragma unroll
+  for (int i = 0; i < 8 * kEncGroups; ++i) {
+    if ((i >> 3) < G) {
+      const unsigned s = min(sym_of(q, i), dmax);
+      unsigned c, L;
+      code_of<PACKED>(codes, lens, s, c, L);
+      bits += L;
+      emask |= (unsigned long long)(s == 0) << i;
+    }
+  }
+}
+
+// MSB-first packing of a lane's vector slice.  `acc` holds the pending bits in
+// its low `nb` bits (garbage above is shifted out and never stored).  A full
+// word is stored as soon as it fills, except the lane's first one when it is
+// shared with the previous lane: that one is returned in `head`.
+template <bool PACKED>
+__device__ __forceinline__ void slice_pack(const uint4* q, int G, unsigned dmax, const unsigned* codes,
+                                           const uint8_t* lens, unsigned* __restrict__ words,
+                                           unsigned long long widx, unsigned nb, bool pending_head,
+                                           unsigned long long& acc_out, unsigned& nb_out,
+                                           unsigned long long& widx_out, unsigned& head) {
+  unsigned long long acc = 0;
+#pragma unroll
+  for (int i = 0; i < 8 * kEncGroups; ++i) {
+    if ((i >> 3) < G) {
+      const unsigned s = min(sym_of(q, i), dmax);
+      unsigned c, L;
+      code_of<PACKED>(codes, lens, s, c, L);
+      acc = (acc << L) | c;
+      nb += L;
+      if (nb >= 32u) {
+        nb -= 32u;
+        const unsigned word = (unsigned)(acc >> nb);
+        if (pending_head) head = word;
+        else words[widx] = word;
+        pending_head = false;
+        ++widx;
+      }
+    }
+  }
+  acc_out = acc;
+  nb_out = nb;
+  widx_out = widx;
+}
+
+// Warps take chunks in ticket order.  A warp codes its chunk's bit count from
+// the symbols it holds in registers, publishes the chunk's (words, escapes)
+// aggregate, walks back over its predecessors until one has published an
+// inclusive prefix (bounded wait), publishes its own inclusive prefix and then
+// packs its codes at the now known word offset.  Every word is written once:
+// a lane's last, partial word is handed to the next lane by a shuffle.
+// Status word of a chunk: [flag:2][words:31][escapes:31], so one load sees a
+// consistent pair (inputs hold fewer than 2^31 symbols).
 template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) encode_fused_kernel(FusedEncodeArgs a) {
+__global__ void __launch_bounds__(WARPS * 32, 4) encode_fused_kernel(FusedEncodeArgs a) {
   __shared__ uint8_t lens[kMaxDict];
   __shared__ unsigned codes[kMaxDict];
-  for (int i = threadIdx.x; i < a.dict; i += blockDim.x) { lens[i] = a.lens[i]; codes[i] = a.codes[i]; }
+  Scalars* sc = a.sc;
+  if (sc->skip) return;  // the stream is already known to be a raw copy
+  // codes of at most 26 bits are packed with their length into one word
+  // (code | len << 26): one shared-memory lookup per symbol
+  const bool packed = sc->max_len <= 26;
+  for (int i = threadIdx.x; i < a.dict; i += blockDim.x) {
+    lens[i] = a.lens[i];
+    codes[i] = packed ? (a.codes[i] | ((unsigned)a.lens[i] << 26)) : a.codes[i];
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const unsigned dmax = (unsigned)(a.dict - 1);
-  const unsigned long long off_bits = a.off_codebook + pad8(a.sc->codebook_bytes);
+  const unsigned long long off_bits = sc->off_bits;
+  const unsigned long long n_out = sc->n_outliers;
   unsigned* words = reinterpret_cast<unsigned*>(a.out + off_bits);
+  unsigned* chunk_esc = (a.esc && n_out) ? reinterpret_cast<unsigned*>(a.out + sc->off_chunk_esc) : nullptr;
+  int32_t* ocode = reinterpret_cast<int32_t*>(a.out + sc->off_outliers);
   const unsigned long long word_cap = a.capacity > off_bits ? (a.capacity - off_bits) / 4 : 0ull;
   const int per = a.chunk / 32;
+  const int G = per / 8;
   while (true) {
     unsigned long long c = 0;
     if (lane == 0) c = atomicAdd(a.ticket, 1u);
@@ -447,26 +596,25 @@ __global__ void __launch_bounds__(WARPS * 32) encode_fused_kernel(FusedEncodeArg
     const unsigned long long ce = min(a.n, cb + (unsigned long long)a.chunk);
     const unsigned long long s0 = min(ce, cb + (unsigned long long)lane * per);
     const unsigned long long s1 = min(ce, s0 + per);
-    LaneSlice sl{a.sym + s0, (int)(s1 - s0), false};
-    sl.vec = sl.cnt == 64 && ((s0 & 7ull) == 0);
-    const bool warp_vec = __all_sync(0xffffffffu, sl.vec);
+    const int cnt = (int)(s1 - s0);
+    // vector slices: whole groups of 8 symbols, 16-byte aligned, every lane
+    // full with at least 32 symbols (so at least 32 bits: a word never has
+    // more than two owners)
+    const bool warp_vec = __all_sync(0xffffffffu, (per & 7) == 0 && per >= 32 && cnt == per && (s0 & 7ull) == 0);
+    uint4 q[kEncGroups];
     // pass 1: bits and escapes of the slice
     unsigned bits = 0, nesc = 0;
+    unsigned long long emask = 0;
     if (warp_vec) {
-#pragma unroll 1
-      for (int g = 0; g < 8; ++g) {
-        const uint4 q = sl.group(g);
-        const unsigned w4[4] = {q.x, q.y, q.z, q.w};
+      const uint4* p = reinterpret_cast<const uint4*>(a.sym + s0);
 #pragma unroll
-        for (int h = 0; h < 8; ++h) {
-          const unsigned s = min((h & 1) ? (w4[h >> 1] >> 16) : (w4[h >> 1] & 0xFFFFu), dmax);
-          bits += lens[s];
-          nesc += s == 0;
-        }
-      }
+      for (int g = 0; g < kEncGroups; ++g) q[g] = g < G ? __ldg(p + g) : make_uint4(0, 0, 0, 0);
+      if (packed) slice_bits<true>(q, G, dmax, codes, lens, bits, emask);
+      else slice_bits<false>(q, G, dmax, codes, lens, bits, emask);
+      nesc = __popcll(emask);
     } else {
-      for (int t = 0; t < sl.cnt; ++t) {
-        const unsigned s = min((unsigned)sl.p[t], dmax);
+      for (int t = 0; t < cnt; ++t) {
+        const unsigned s = min((unsigned)a.sym[s0 + t], dmax);
         bits += lens[s];
         nesc += s == 0;
       }
@@ -493,8 +641,8 @@ __global__ void __launch_bounds__(WARPS * 32) encode_fused_kernel(FusedEncodeArg
       long long top = (long long)c - 1;  // highest predecessor not yet summed
       long spins = 0;
       while (top >= 0) {
-        const long long p = top - lane;
-        const unsigned long long sv = p >= 0 ? ld_volatile_u64(a.st + p) : kFlagIncl;  // before chunk 0: prefix 0
+        const long long pidx = top - lane;
+        const unsigned long long sv = pidx >= 0 ? ld_volatile_u64(a.st + pidx) : kFlagIncl;  // before chunk 0: prefix 0
         const unsigned flag = (unsigned)(sv >> 62);
         // only the lanes up to the first unpublished one can be used
         const unsigned unpub = __ballot_sync(0xffffffffu, flag == 0);
@@ -510,7 +658,7 @@ __global__ void __launch_bounds__(WARPS * 32) encode_fused_kernel(FusedEncodeArg
         }
         const int take = min(first_incl + 1, first_unpub);  // lanes [0, take) are summed
         unsigned long long w = 0, e = 0;
-        if (lane < take && p >= 0) { w = (sv >> 31) & kM31; e = sv & kM31; }
+        if (lane < take && pidx >= 0) { w = (sv >> 31) & kM31; e = sv & kM31; }
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
           w += __shfl_xor_sync(0xffffffffu, w, o);
@@ -529,80 +677,89 @@ __global__ void __launch_bounds__(WARPS * 32) encode_fused_kernel(FusedEncodeArg
     }
     if (lane == 0) {
       a.chunk_words[c] = W;
-      a.chunk_esc[c] = tot_esc;
+      if (chunk_esc) chunk_esc[c] = tot_esc;
       if (c == a.nch - 1) {
-        a.sc->n_words = pw + W;
-        a.sc->n_outliers = pe + tot_esc;
+        sc->n_words = pw + W;
+        sc->esc_seen = pe + tot_esc;
       }
     }
     timed_out = __shfl_sync(0xffffffffu, timed_out, 0);
     if (timed_out) {
-      if (lane == 0) atomicOr(&a.sc->status, ST_TIMEOUT | ST_RAW);
+      if (lane == 0) atomicOr(&sc->status, ST_TIMEOUT | ST_RAW);
       break;
     }
     pw = __shfl_sync(0xffffffffu, pw, 0);
     pe = __shfl_sync(0xffffffffu, pe, 0);
     if (pw + W > word_cap) {  // the stream would not fit: it becomes a raw copy
-      if (lane == 0) atomicOr(&a.sc->status, ST_RAW);
+      if (lane == 0) atomicOr(&sc->status, ST_RAW);
       continue;
     }
-    if (!warp_vec) {  // a partial chunk: zero its words, shared words are ORed below
-      for (unsigned w = lane; w < W; w += 32) words[pw + w] = 0u;
-      __syncwarp();
-    }
-    // pass 2: pack MSB-first.  Complete words are stored as they fill (the
-    // first one is held back when it is shared with the previous lane).
-    const unsigned bit0 = xb - bits;
-    if ((lane & 3) == 0 && lane) a.splits[c * (kSplits - 1) + (lane >> 2) - 1] = (uint16_t)bit0;
+    // outlier codes of the slice, in stream order
     unsigned long long epos = pe + (xe - nesc);
-    unsigned long long acc = 0;
-    unsigned nb = bit0 & 31u;
-    const unsigned long long head_idx = pw + (bit0 >> 5);
-    unsigned long long widx = head_idx;
-    const bool head_partial = (bit0 & 31u) != 0;
-    bool pending_head = head_partial;
-    unsigned head = 0;
-    auto code_one = [&](unsigned s, int32_t ecode) {
-      s = min(s, dmax);
-      const unsigned L = lens[s];
-      acc = (acc << L) | codes[s];
-      nb += L;
-      const bool full = nb >= 32;
-      const unsigned word = (unsigned)(acc >> (full ? nb - 32 : 0));
-      const bool keep = full && pending_head;
-      head = keep ? word : head;
-      if (full && !keep) words[widx] = word;
-      pending_head = pending_head && !full;
-      widx += full ? 1 : 0;
-      nb -= full ? 32 : 0;
-      acc &= (1ull << nb) - 1ull;
-      if (s == 0 && a.esc) a.ocode[epos++] = ecode;
-    };
-    if (warp_vec) {
-#pragma unroll 1
-      for (int g = 0; g < 8; ++g) {
-        const uint4 q = sl.group(g);
-        const unsigned w4[4] = {q.x, q.y, q.z, q.w};
-        // codes of this group's escaped symbols, loaded together
-        int32_t ev[8];
+    if (a.esc && nesc) {
+      if (warp_vec) {
+        unsigned long long m = emask;
+        while (m) {
+          int idx[4];
+          int k = 0;
 #pragma unroll
-        for (int h = 0; h < 8; ++h) {
-          const unsigned sh = (h & 1) ? (w4[h >> 1] >> 16) : (w4[h >> 1] & 0xFFFFu);
-          ev[h] = (sh == 0 && a.esc) ? __ldg(a.esc + s0 + 8 * g + h) : 0;
+          for (int t = 0; t < 4; ++t) {
+            idx[t] = m ? __ffsll((long long)m) - 1 : -1;
+            m &= m ? m - 1 : 0ull;
+            k += idx[t] >= 0;
+          }
+          int32_t v[4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) v[t] = idx[t] >= 0 ? __ldg(a.esc + s0 + idx[t]) : 0;
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            if (idx[t] >= 0 && epos + t < n_out) ocode[epos + t] = v[t];
+          epos += k;
         }
-#pragma unroll
-        for (int h = 0; h < 8; ++h)
-          code_one((h & 1) ? (w4[h >> 1] >> 16) : (w4[h >> 1] & 0xFFFFu), ev[h]);
+      } else {
+        for (int t = 0; t < cnt; ++t)
+          if (a.sym[s0 + t] == 0) {
+            if (epos < n_out) ocode[epos] = a.esc[s0 + t];
+            ++epos;
+          }
       }
+    }
+    if ((lane & 3) == 0 && lane) a.splits[c * (kSplits - 1) + (lane >> 2) - 1] = (uint16_t)(xb - bits);
+    // pass 2: pack MSB-first
+    const unsigned bit0 = xb - bits;
+    const unsigned long long head_idx = pw + (bit0 >> 5);
+    const bool head_partial = (bit0 & 31u) != 0;
+    if (warp_vec) {
+      unsigned long long acc, widx;
+      unsigned nb, head = 0;
+      if (packed)
+        slice_pack<true>(q, G, dmax, codes, lens, words, head_idx, bit0 & 31u, head_partial, acc, nb, widx, head);
+      else
+        slice_pack<false>(q, G, dmax, codes, lens, words, head_idx, bit0 & 31u, head_partial, acc, nb, widx, head);
       // every lane holds >= 64 bits here, so a shared word has exactly two owners
       const unsigned tail = nb ? (unsigned)(acc << (32 - nb)) : 0u;
       const unsigned from_prev = __shfl_up_sync(0xffffffffu, tail, 1);
       if (head_partial) words[head_idx] = head | from_prev;
       if (lane == 31 && nb) words[widx] = tail;
-    } else {
-      for (int t = 0; t < sl.cnt; ++t) {
-        const unsigned st = (unsigned)sl.p[t];
-        code_one(st, (st == 0 && a.esc) ? a.esc[s0 + t] : 0);
+    } else {  // a partial chunk: zero its words, shared words are ORed
+      for (unsigned w = lane; w < W; w += 32) words[pw + w] = 0u;
+      __syncwarp();
+      unsigned long long acc = 0, widx = head_idx;
+      unsigned nb = bit0 & 31u, head = 0;
+      bool pending_head = head_partial;
+      for (int t = 0; t < cnt; ++t) {
+        const unsigned s = min((unsigned)a.sym[s0 + t], dmax);
+        const unsigned L = lens[s];
+        acc = (acc << L) | (packed ? (codes[s] & 0x3FFFFFFu) : codes[s]);
+        nb += L;
+        if (nb >= 32u) {
+          nb -= 32u;
+          const unsigned word = (unsigned)(acc >> nb);
+          if (pending_head) head = word;
+          else words[widx] = word;
+          pending_head = false;
+          ++widx;
+        }
       }
       __syncwarp();
       if (head_partial && !pending_head) atomicOr(words + head_idx, head);
@@ -611,43 +768,14 @@ __global__ void __launch_bounds__(WARPS * 32) encode_fused_kernel(FusedEncodeArg
   }
 }
 
-// After the fused encoder: stream offsets, per-chunk escape counts and the
-// outlier codes (moved from scratch), raw decision.
-__global__ void __launch_bounds__(256) encode_finish_kernel(const unsigned* chunk_esc, unsigned long long nch,
-                                                            const int32_t* ocode, uint8_t* out,
-                                                            unsigned long long off_codebook,
-                                                            unsigned long long raw_total,
-                                                            unsigned long long capacity, Scalars* sc) {
-  __shared__ int s_go;
-  __shared__ unsigned long long s_ce, s_out;
-  if (threadIdx.x == 0) {
-    const unsigned long long nw = sc->n_words, ne = sc->n_outliers;
-    const unsigned long long off_bits = off_codebook + pad8(sc->codebook_bytes);
-    const unsigned long long off_ce = off_bits + pad8(4ull * nw);
-    const unsigned long long off_out = off_ce + (ne ? pad8(4ull * nch) : 0ull);
-    const unsigned long long total = off_out + pad8(4ull * ne);
-    if (blockIdx.x == 0) {
-      sc->off_bits = off_bits;
-      sc->off_chunk_esc = off_ce;
-      sc->off_outliers = off_out;
-      sc->total = total;
-      if (total >= raw_total || total > capacity) atomicOr(&sc->status, ST_RAW);
-      if (sc->status & ST_OVERFLOW) atomicOr(&sc->status, ST_RAW);
-    }
-    const bool raw = (sc->status & (ST_RAW | ST_OVERFLOW)) || total >= raw_total || total > capacity;
-    s_go = !raw;
-    s_ce = off_ce;
-    s_out = off_out;
-  }
-  __syncthreads();
-  if (!s_go) return;
-  const unsigned long long ne = sc->n_outliers;
-  if (ne) {
-    unsigned* ce = reinterpret_cast<unsigned*>(out + s_ce);
-    for (unsigned long long i = blockIdx.x * 256ull + threadIdx.x; i < nch; i += gridDim.x * 256ull) ce[i] = chunk_esc[i];
-    int32_t* oc = reinterpret_cast<int32_t*>(out + s_out);
-    for (unsigned long long i = blockIdx.x * 256ull + threadIdx.x; i < ne; i += gridDim.x * 256ull) oc[i] = ocode[i];
-  }
+// After the fused encoder: stream length and the raw decision.
+__global__ void encode_finish_kernel(unsigned long long raw_total, unsigned long long capacity, Scalars* sc) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (sc->skip) return;  // already raw
+  const unsigned long long total = sc->off_bits + pad8(4ull * sc->n_words);
+  sc->total = total;
+  if (sc->esc_seen != sc->n_outliers) atomicOr(&sc->status, ST_CORRUPT | ST_RAW);
+  if (total >= raw_total || total > capacity || (sc->status & ST_OVERFLOW)) atomicOr(&sc->status, ST_RAW);
 }
 
 // ---------------------------------------------------------------------------
@@ -828,30 +956,64 @@ __global__ void __launch_bounds__(128) decode_kernel(DecodeArgs a) {
 }
 
 // Escaped symbols (symbol 0) take the outlier codes in stream order: one
-// warp per chunk, each lane a slice of chunk/32 symbols.
+// warp per chunk, each lane a slice of chunk/32 (<= 64) symbols read as 16-byte
+// vectors when the slices allow it; a lane's escapes are a 64-bit mask.
 __global__ void __launch_bounds__(256) escape_fixup_kernel(const uint16_t* sym, unsigned long long n, int chunk,
                                                            unsigned long long nch, const unsigned long long* esc_off,
-                                                           const int32_t* ocode, int32_t* esc, Scalars* sc) {
+                                                           const int32_t* ocode, unsigned long long n_out,
+                                                           int32_t* esc, Scalars* sc) {
   const int lane = threadIdx.x & 31;
   const int per = chunk / 32;
+  const int G = per / 8;
   for (unsigned long long c = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) / 32; c < nch;
        c += (unsigned long long)gridDim.x * blockDim.x / 32) {
     const unsigned long long cb = c * (unsigned long long)chunk;
     const unsigned long long s0 = min(n, cb + (unsigned long long)lane * per), s1 = min(n, s0 + per);
-    unsigned cnt = 0;
-    for (unsigned long long i = s0; i < s1; ++i) cnt += sym[i] == 0;
-    unsigned x = cnt;
+    const int cnt = (int)(s1 - s0);
+    const bool vec = __all_sync(0xffffffffu, (per & 7) == 0 && cnt == per && (s0 & 7ull) == 0);
+    unsigned long long m = 0;
+    if (vec) {
+      const uint4* p = reinterpret_cast<const uint4*>(sym + s0);
+      uint4 q[kEncGroups];
+#pragma unroll
+      for (int g = 0; g < kEncGroups; ++g) q[g] = g < G ? __ldg(p + g) : make_uint4(1u, 1u, 1u, 1u);
+#pragma unroll
+      for (int i = 0; i < 8 * kEncGroups; ++i)
+        if ((i >> 3) < G) m |= (unsigned long long)(sym_of(q, i) == 0) << i;
+    } else {
+      for (int t = 0; t < cnt; ++t) m |= (unsigned long long)(sym[s0 + t] == 0) << t;
+    }
+    const unsigned ne = __popcll(m);
+    unsigned x = ne;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
     const unsigned total = __shfl_sync(0xffffffffu, x, 31);
-    if (lane == 0 && esc_off[c] + total != esc_off[c + 1]) atomicOr(&sc->status, ST_CORRUPT);
-    if (esc_off[c] + total != esc_off[c + 1]) continue;
-    unsigned long long e = esc_off[c] + (x - cnt);
-    for (unsigned long long i = s0; i < s1; ++i)
-      if (sym[i] == 0) esc[i] = ocode[e++];
+    const unsigned long long e0 = esc_off[c], e1 = esc_off[c + 1];
+    if (e0 + total != e1 || e1 > n_out) {  // the outlier reads stay inside the outlier section
+      if (lane == 0) atomicOr(&sc->status, ST_CORRUPT);
+      continue;
+    }
+    unsigned long long e = e0 + (x - ne);
+    while (m) {
+      int idx[4];
+      int k = 0;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        idx[t] = m ? __ffsll((long long)m) - 1 : -1;
+        m &= m ? m - 1 : 0ull;
+        k += idx[t] >= 0;
+      }
+      int32_t v[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) v[t] = idx[t] >= 0 ? __ldg(ocode + e + t) : 0;
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (idx[t] >= 0) esc[s0 + idx[t]] = v[t];
+      e += k;
+    }
   }
 }
 

@@ -192,7 +192,7 @@ def test_corrupt_streams_rejected(bm):
     rng = np.random.default_rng(0)
     for _ in range(5):
         bad = good.clone()
-        pos = int(rng.integers(h["off_bits"], h["off_outliers"]))
+        pos = int(rng.integers(h["off_bits"], h["total"]))
         bad[pos] ^= 0x10
         try:
             bm.decompress(bad)
