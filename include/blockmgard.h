@@ -164,6 +164,11 @@ void bm_release_workspace(void* stream);
  * milliseconds (names[i] static strings), up to max_stages entries. */
 void bm_set_timing(int enabled);
 int bm_stage_times(const char** names, float* ms, int max_stages);
+/* Test hook: cap the persistent grid of the In-cache Block kernels at
+ * max_ctas CTAs (0 = the occupancy-based default), so that small fields also
+ * make every CTA walk several blocks.  Process-wide; results do not depend on
+ * it. */
+void bm_set_block_grid_limit(int max_ctas);
 /* Count of kernels this library has launched since load (monotonic). */
 uint64_t bm_launch_count(void);
 

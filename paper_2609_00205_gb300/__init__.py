@@ -73,6 +73,8 @@ def load():
     L.bm_release_workspace.restype = None
     L.bm_set_timing.argtypes = [ctypes.c_int]
     L.bm_set_timing.restype = None
+    L.bm_set_block_grid_limit.argtypes = [ctypes.c_int]
+    L.bm_set_block_grid_limit.restype = None
     L.bm_stage_times.argtypes = [P(ctypes.c_char_p), P(ctypes.c_float), ctypes.c_int]
     L.bm_launch_count.restype = u64
     L.bm_error_string.restype = ctypes.c_char_p
@@ -255,6 +257,11 @@ def stage_times() -> list:
     ms = (ctypes.c_float * 64)()
     n = L.bm_stage_times(names, ms, 64)
     return [(names[i].decode(), float(ms[i])) for i in range(n)]
+
+
+def set_block_grid_limit(max_ctas: int):
+    """Cap the persistent grid of the In-cache Block kernels (0 = default)."""
+    load().bm_set_block_grid_limit(int(max_ctas))
 
 
 def launch_count() -> int:

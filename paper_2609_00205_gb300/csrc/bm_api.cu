@@ -561,15 +561,20 @@ namespace {
 // ---------------------------------------------------------------------------
 template <typename T>
 cudaError_t launch_block(int dir, int B, int K, int mode, const BlockArgs<T>& a, cudaStream_t s);
+std::atomic<int> g_block_grid_cap{0};  // bm_set_block_grid_limit
 template <>
 cudaError_t launch_block<float>(int dir, int B, int K, int mode, const BlockArgs<float>& a, cudaStream_t s) {
   BM_LAUNCHED();
-  return B == 9 ? launch_block_f32_b9(dir, K, mode, a, s, num_sms()) : launch_block_f32_b17(dir, K, mode, a, s, num_sms());
+  const int cap = g_block_grid_cap.load();
+  return B == 9 ? launch_block_f32_b9(dir, K, mode, a, s, num_sms(), cap)
+                : launch_block_f32_b17(dir, K, mode, a, s, num_sms(), cap);
 }
 template <>
 cudaError_t launch_block<double>(int dir, int B, int K, int mode, const BlockArgs<double>& a, cudaStream_t s) {
   BM_LAUNCHED();
-  return B == 9 ? launch_block_f64_b9(dir, K, mode, a, s, num_sms()) : launch_block_f64_b17(dir, K, mode, a, s, num_sms());
+  const int cap = g_block_grid_cap.load();
+  return B == 9 ? launch_block_f64_b9(dir, K, mode, a, s, num_sms(), cap)
+                : launch_block_f64_b17(dir, K, mode, a, s, num_sms(), cap);
 }
 
 // Outputs of the decomposition (mode 0: symbols + escapes + histogram).
@@ -646,6 +651,7 @@ struct InvIn {
   const double* q = nullptr;  // [ntiers*K + M + 1]
   int ntiers = 1;
   int radius = 0;
+  Scalars* sc = nullptr;      // status word for corrupt-stream checks (may be null)
 };
 
 template <typename T>
@@ -701,6 +707,8 @@ bm_status run_recompose(PlanDev& P, T* field, int mode, const InvIn<T>& in, Carv
     a.tier = in.tier;
     a.q = in.q;
     a.radius = in.radius;
+    a.ntiers = in.ntiers;
+    a.sc = in.sc;
     BM_CUDA(launch_block<T>(1, h.B, h.K, mode, a, s));
   }
   return BM_OK;
@@ -1058,7 +1066,7 @@ bm_status decompress_t(const uint8_t* in, const Header& H, T* field, cudaStream_
   Scalars* sc;
   if (bm_status st = decode_symbols(in, H, cv, &sym, &esc, &sc, s)) return st;
   InvIn<T> ii;
-  ii.sym = sym; ii.esc = esc; ii.radius = H.radius; ii.ntiers = H.ntiers;
+  ii.sym = sym; ii.esc = esc; ii.radius = H.radius; ii.ntiers = H.ntiers; ii.sc = sc;
   ii.q = reinterpret_cast<const double*>(in + H.off_qtab);
   ii.tier = H.ntiers > 1 ? in + H.off_btier : nullptr;
   if (bm_status st = run_recompose<T>(*P, field, 0, ii, cv, s)) return st;
@@ -1093,6 +1101,8 @@ const char* bm_last_error_detail(void) { return g_detail.c_str(); }
 uint64_t bm_launch_count(void) { return g_launches.load(); }
 
 void bm_set_timing(int enabled) { g_timing.store(enabled ? 1 : 0); }
+
+void bm_set_block_grid_limit(int max_ctas) { g_block_grid_cap.store(max_ctas > 0 ? max_ctas : 0); }
 
 int bm_stage_times(const char** names, float* ms, int max_stages) {
   std::lock_guard<std::mutex> g(g_timer_mu);

@@ -476,7 +476,11 @@ __global__ void __launch_bounds__(BlockCfg<T, B, K>::NT) block_inv_kernel(BlockA
       cf[e] = a.G[((b0 * M + j0) * a.g1 + (b1 * M + j1)) * a.g2 + (b2 * M + j2)];
     }
     __syncthreads();
-    const int tier = (MODE == 0 && a.tier) ? a.tier[b] : 0;
+    int tier = (MODE == 0 && a.tier) ? a.tier[b] : 0;
+    if (tier >= a.ntiers) {  // corrupt stream: keep the q reads inside the table
+      if (threadIdx.x == 0 && a.sc) atomicOr(&a.sc->status, ST_CORRUPT);
+      tier = 0;
+    }
     InvLevels<T, M * 2 - 1, K - 1, B, MODE>::run(bufs, T1, T2, a.q + tier * K, K, stage,
                                                   MODE == 0 ? a.esc + sbase : nullptr, a.radius);
     for (int e = threadIdx.x; e < B * B * B; e += blockDim.x) {

@@ -3,12 +3,13 @@
 
 namespace bm {
 
-cudaError_t launch_block_f64_b17(int dir, int K, int mode, const BlockArgs<double>& a, cudaStream_t s, int nsm) {
+cudaError_t launch_block_f64_b17(int dir, int K, int mode, const BlockArgs<double>& a, cudaStream_t s, int nsm,
+                                 int max_grid) {
   switch (K) {
-    case 1: return launch_mode<double, 17, 1>(dir, mode, a, s, nsm);
-    case 2: return launch_mode<double, 17, 2>(dir, mode, a, s, nsm);
-    case 3: return launch_mode<double, 17, 3>(dir, mode, a, s, nsm);
-    case 4: return launch_mode<double, 17, 4>(dir, mode, a, s, nsm);
+    case 1: return launch_mode<double, 17, 1>(dir, mode, a, s, nsm, max_grid);
+    case 2: return launch_mode<double, 17, 2>(dir, mode, a, s, nsm, max_grid);
+    case 3: return launch_mode<double, 17, 3>(dir, mode, a, s, nsm, max_grid);
+    case 4: return launch_mode<double, 17, 4>(dir, mode, a, s, nsm, max_grid);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -3,11 +3,12 @@
 
 namespace bm {
 
-cudaError_t launch_block_f64_b9(int dir, int K, int mode, const BlockArgs<double>& a, cudaStream_t s, int nsm) {
+cudaError_t launch_block_f64_b9(int dir, int K, int mode, const BlockArgs<double>& a, cudaStream_t s, int nsm,
+                                 int max_grid) {
   switch (K) {
-    case 1: return launch_mode<double, 9, 1>(dir, mode, a, s, nsm);
-    case 2: return launch_mode<double, 9, 2>(dir, mode, a, s, nsm);
-    case 3: return launch_mode<double, 9, 3>(dir, mode, a, s, nsm);
+    case 1: return launch_mode<double, 9, 1>(dir, mode, a, s, nsm, max_grid);
+    case 2: return launch_mode<double, 9, 2>(dir, mode, a, s, nsm, max_grid);
+    case 3: return launch_mode<double, 9, 3>(dir, mode, a, s, nsm, max_grid);
     default: return cudaErrorInvalidValue;
   }
 }

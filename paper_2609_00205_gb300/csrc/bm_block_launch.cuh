@@ -7,7 +7,7 @@
 namespace bm {
 
 template <typename T, int B, int K, int MODE>
-cudaError_t launch_one(int dir, const BlockArgs<T>& a, cudaStream_t s, int nsm) {
+cudaError_t launch_one(int dir, const BlockArgs<T>& a, cudaStream_t s, int nsm, int max_grid) {
   using Cfg = BlockCfg<T, B, K>;
   const void* fn = dir == 0 ? (const void*)block_fwd_kernel<T, B, K, MODE> : (const void*)block_inv_kernel<T, B, K, MODE>;
   const size_t smem = dir == 0 ? Cfg::fwd_smem : Cfg::inv_smem(MODE);
@@ -18,6 +18,7 @@ cudaError_t launch_one(int dir, const BlockArgs<T>& a, cudaStream_t s, int nsm) 
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   int64_t grid = (int64_t)per_sm * nsm;
+  if (max_grid > 0 && grid > max_grid) grid = max_grid;
   if (grid > a.nblocks) grid = a.nblocks;
   if (grid < 1) return cudaSuccess;
   if (dir == 0) block_fwd_kernel<T, B, K, MODE><<<(unsigned)grid, Cfg::NT, smem, s>>>(a);
@@ -26,8 +27,8 @@ cudaError_t launch_one(int dir, const BlockArgs<T>& a, cudaStream_t s, int nsm) 
 }
 
 template <typename T, int B, int K>
-cudaError_t launch_mode(int dir, int mode, const BlockArgs<T>& a, cudaStream_t s, int nsm) {
-  return mode == 0 ? launch_one<T, B, K, 0>(dir, a, s, nsm) : launch_one<T, B, K, 1>(dir, a, s, nsm);
+cudaError_t launch_mode(int dir, int mode, const BlockArgs<T>& a, cudaStream_t s, int nsm, int max_grid) {
+  return mode == 0 ? launch_one<T, B, K, 0>(dir, a, s, nsm, max_grid) : launch_one<T, B, K, 1>(dir, a, s, nsm, max_grid);
 }
 
 }  // namespace bm

@@ -371,8 +371,10 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(CodebookArgs a) {
     sc->off_chunk_esc = off_ce;
     sc->off_outliers = off_out;
     sc->off_bits = off_bits;
-    if (min_total >= a.raw_total || off_bits > a.capacity) atomicOr(&sc->status, ST_RAW);
-    sc->skip = (sc->status & (ST_RAW | ST_OVERFLOW)) ? 1u : 0u;
+    // a quantisation overflow, a size bound at or above the raw copy, or sections
+    // that do not fit all make the stream a raw copy: skip the encoder
+    if ((sc->status & ST_OVERFLOW) || min_total >= a.raw_total || off_bits > a.capacity) atomicOr(&sc->status, ST_RAW);
+    sc->skip = (sc->status & ST_RAW) ? 1u : 0u;
   }
 }
 

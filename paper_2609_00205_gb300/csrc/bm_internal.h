@@ -24,15 +24,21 @@ struct BlockArgs {
   unsigned* hist;       // global histogram [2*radius]
   int radius;
   Scalars* sc;
+  int ntiers;           // inv: tiers in the q table (a block tier at or above it is corrupt)
 };
 
 
 // In-cache Block kernels for one (dtype, B): dir 0 = decompose (+quantise),
 // dir 1 = recompose; mode 0 = symbols, 1 = full-precision coefficients.
 // Returns cudaErrorInvalidValue for an unsupported K.
-cudaError_t launch_block_f32_b9(int dir, int K, int mode, const BlockArgs<float>& a, cudaStream_t s, int nsm);
-cudaError_t launch_block_f32_b17(int dir, int K, int mode, const BlockArgs<float>& a, cudaStream_t s, int nsm);
-cudaError_t launch_block_f64_b9(int dir, int K, int mode, const BlockArgs<double>& a, cudaStream_t s, int nsm);
-cudaError_t launch_block_f64_b17(int dir, int K, int mode, const BlockArgs<double>& a, cudaStream_t s, int nsm);
+// max_grid > 0 caps the persistent grid (several blocks per CTA at any size).
+cudaError_t launch_block_f32_b9(int dir, int K, int mode, const BlockArgs<float>& a, cudaStream_t s, int nsm,
+                                int max_grid);
+cudaError_t launch_block_f32_b17(int dir, int K, int mode, const BlockArgs<float>& a, cudaStream_t s, int nsm,
+                                 int max_grid);
+cudaError_t launch_block_f64_b9(int dir, int K, int mode, const BlockArgs<double>& a, cudaStream_t s, int nsm,
+                                int max_grid);
+cudaError_t launch_block_f64_b17(int dir, int K, int mode, const BlockArgs<double>& a, cudaStream_t s, int nsm,
+                                 int max_grid);
 
 }  // namespace bm

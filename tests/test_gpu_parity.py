@@ -204,6 +204,41 @@ def test_corrupt_streams_rejected(bm):
     assert np.abs(d - u).max() <= 1e-3 * np.abs(u).max()
 
 
+@pytest.mark.parametrize("case", [CASES[1], CASES[3], CASES[0]], ids=["grf_b17k2m2", "roi_f64_b9k2m2", "bumps65_b9k3"])
+def test_several_blocks_per_cta(bm, case):
+    """Every CTA walks several blocks (capped persistent grid): same streams and
+    coefficients as the oracle, and the GPU round trip within the bound."""
+    name, shape, dt, B, K, M = case
+    u = _field(name, shape, dt)
+    t = torch.from_numpy(u).to(DEV)
+    ref = {tol: bm.compress(t, tol, mode="rel", block=B, levels=K, global_levels=M).cpu().numpy() for tol in (1e-2, 1e-4)}
+    try:
+        bm.set_block_grid_limit(3)
+        g = bm.decompose(t, block=B, levels=K, global_levels=M).cpu().numpy()
+        o = oracle.decompose(u.astype(np.float64), B, K, M)
+        assert np.abs(g.astype(np.float64) - o).max() <= _coef_tol(u)
+        r = bm.recompose(torch.from_numpy(g).to(DEV), shape, block=B, levels=K, global_levels=M).cpu().numpy()
+        assert np.abs(r.astype(np.float64) - u).max() <= 8 * _coef_tol(u)
+        for tol in (1e-2, 1e-4):
+            sg = bm.compress(t, tol, mode="rel", block=B, levels=K, global_levels=M).cpu().numpy()
+            np.testing.assert_array_equal(sg, ref[tol])  # independent of the grid
+            d = bm.decompress(torch.from_numpy(sg).to(DEV)).cpu().numpy().astype(np.float64)
+            assert np.abs(d - u).max() <= tol * np.abs(u).max()
+    finally:
+        bm.set_block_grid_limit(0)
+
+
+def test_overflow_gives_raw(bm):
+    """Values near the FP32 maximum overflow the FP32 interpolation (the FP64
+    oracle does not): the stream must fall back to an exact raw copy."""
+    u = np.full((20, 21, 22), 3.0e38, dtype=np.float32)
+    u[3, 4, 5] = 2.9e38
+    sg = bm.compress(torch.from_numpy(u).to(DEV), 1e-2, mode="rel", block=9, levels=2, global_levels=1)
+    assert oracle.stream_header(sg.cpu().numpy())["raw"]
+    d = bm.decompress(sg).cpu().numpy()
+    np.testing.assert_array_equal(d.view(np.uint32), u.view(np.uint32))
+
+
 def test_invalid_arguments(bm):
     t = torch.zeros((10, 10, 10), device=DEV)
     with pytest.raises(bm.BlockMGARDError) as e:
