@@ -224,26 +224,94 @@ struct FwdLevels {
   }
 };
 
-// Consecutive threads copy consecutive elements of the block (row-major), so
-// every warp instruction covers ~32 contiguous values of one or two rows;
-// the block origin and its in-domain extents are computed once per block and
-// the divisions are by compile-time constants.  cp.async zero-fills past the
-// domain.
+// Block coordinates (b0, b1, b2) of linear block index b: two 32-bit divisions
+// per block (the block grid has fewer than 2^31 blocks).
+struct BlockCoord {
+  int b0, b1, b2;
+  __device__ __forceinline__ BlockCoord(int64_t b, int nb1, int nb2) {
+    const unsigned ub = (unsigned)b, q2 = ub / (unsigned)nb2, q1 = q2 / (unsigned)nb1;
+    b2 = (int)(ub - q2 * (unsigned)nb2);
+    b1 = (int)(q2 - q1 * (unsigned)nb1);
+    b0 = (int)q1;
+  }
+};
+
+// First element of block (b0, b1, b2) in the field, and its in-domain extents.
 template <typename T, int B>
-__device__ __forceinline__ void issue_block_load(T* dst, const T* __restrict__ field, int64_t n0, int64_t n1,
-                                                 int64_t n2, int64_t b0, int64_t b1, int64_t b2) {
-  const int64_t r0 = n0 - b0 * B, r1 = n1 - b1 * B, r2 = n2 - b2 * B;
-  const int lim0 = r0 < B ? (int)r0 : B, lim1 = r1 < B ? (int)r1 : B, lim2 = r2 < B ? (int)r2 : B;
-  const T* base = field + ((b0 * B) * n1 + b1 * B) * n2 + b2 * B;
-  const int64_t s0 = n1 * n2;
-  for (int e = threadIdx.x; e < B * B * B; e += blockDim.x) {
-    const int i0 = e / (B * B);
-    const int r = e - i0 * (B * B);
-    const int i1 = r / B;
-    const int k = r - i1 * B;
-    const bool ok = (i0 < lim0) & (i1 < lim1) & (k < lim2);
-    const T* src = ok ? base + (i0 * s0 + i1 * n2 + k) : field;
-    cp_async_zfill<sizeof(T)>(dst + e, src, ok);
+struct BlockSpan {
+  T* base;
+  int lim0, lim1, lim2;
+  __device__ __forceinline__ BlockSpan(T* field, int64_t n0, int64_t n1, int64_t n2, const BlockCoord& c) {
+    base = field + ((int64_t)c.b0 * B * n1 + (int64_t)c.b1 * B) * n2 + (int64_t)c.b2 * B;
+    const int64_t r0 = n0 - (int64_t)c.b0 * B, r1 = n1 - (int64_t)c.b1 * B, r2 = n2 - (int64_t)c.b2 * B;
+    lim0 = r0 < B ? (int)r0 : B;
+    lim1 = r1 < B ? (int)r1 : B;
+    lim2 = r2 < B ? (int)r2 : B;
+  }
+};
+
+// Copy of one B^3 block into shared memory (row-major), zero filled outside the
+// domain.  Thread t < B(B+1) owns column k = t % B and the rows r0 + (B+1) j
+// of the block (r0 = t / B, j < B): each step moves one plane down and one row
+// on (i0+1, i1+1, i1 wrapping once), so the source advances by the constant
+// s0 + n2, corrected once by s0 - B n2 at the wrap, and the destination by
+// B(B+1) elements.  Consecutive threads read consecutive elements of a row.
+template <typename T, int B>
+__device__ __forceinline__ void issue_block_load(T* dst, const T* __restrict__ field, const BlockSpan<const T, B>& sp,
+                                                 int64_t n1, int64_t n2) {
+  static_assert(BlockCfg<T, B, 1>::NT >= B * (B + 1), "one thread per (column, first row)");
+  const int t = threadIdx.x;
+  if (t >= B * (B + 1)) return;
+  const int k = t % B, r0 = t / B, jc = B - r0;
+  const int64_t s0 = n1 * n2, D = s0 + n2, E = s0 - (int64_t)B * n2;
+  const T* p = sp.base + (int64_t)r0 * n2 + k;
+  T* q = dst + t;
+  if ((sp.lim0 == B) & (sp.lim1 == B) & (sp.lim2 == B)) {  // interior block
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      if (j < B - 1 || r0 == 0) cp_async_zfill<sizeof(T)>(q + j * B * (B + 1), p + (j >= jc ? E : 0), true);
+      p += D;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      if (j < B - 1 || r0 == 0) {
+        const int carry = j >= jc;
+        const int i0 = j + carry, i1 = r0 + j - (carry ? B : 0);
+        const bool ok = (i0 < sp.lim0) & (i1 < sp.lim1) & (k < sp.lim2);
+        cp_async_zfill<sizeof(T)>(q + j * B * (B + 1), ok ? p + (carry ? E : 0) : field, ok);
+      }
+      p += D;
+    }
+  }
+}
+
+// The inverse copy: the in-domain part of the block from shared memory to the
+// field, with the same thread-to-element assignment.
+template <typename T, int B>
+__device__ __forceinline__ void store_block(const BlockSpan<T, B>& sp, const T* src, int64_t n1, int64_t n2) {
+  const int t = threadIdx.x;
+  if (t >= B * (B + 1)) return;
+  const int k = t % B, r0 = t / B, jc = B - r0;
+  const int64_t s0 = n1 * n2, D = s0 + n2, E = s0 - (int64_t)B * n2;
+  T* p = sp.base + (int64_t)r0 * n2 + k;
+  const T* q = src + t;
+  if ((sp.lim0 == B) & (sp.lim1 == B) & (sp.lim2 == B)) {
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      if (j < B - 1 || r0 == 0) p[j >= jc ? E : 0] = q[j * B * (B + 1)];
+      p += D;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      if (j < B - 1 || r0 == 0) {
+        const int carry = j >= jc;
+        const int i0 = j + carry, i1 = r0 + j - (carry ? B : 0);
+        if ((i0 < sp.lim0) & (i1 < sp.lim1) & (k < sp.lim2)) p[carry ? E : 0] = q[j * B * (B + 1)];
+      }
+      p += D;
+    }
   }
 }
 
@@ -290,22 +358,20 @@ __global__ void __launch_bounds__(BlockCfg<T, B, K>::NT, BM_FWD_MIN_CTAS) block_
     for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) hloc[i] = 0;
   bool ovf = false;
   unsigned centre = 0;
-  const int64_t nbc = (int64_t)a.nb1 * a.nb2;
+  auto span = [&](int64_t bi) { return BlockSpan<const T, B>(a.field, a.n0, a.n1, a.n2, BlockCoord(bi, a.nb1, a.nb2)); };
   int64_t b = blockIdx.x;
   int buf = 0;
-  if (BM_FWD_DOUBLE_BUFFER && b < a.nblocks)
-    issue_block_load<T, B>(Abuf, a.field, a.n0, a.n1, a.n2, b / nbc, (b / a.nb2) % a.nb1, b % a.nb2);
+  if (BM_FWD_DOUBLE_BUFFER && b < a.nblocks) issue_block_load<T, B>(Abuf, a.field, span(b), a.n1, a.n2);
   cp_async_commit();
   for (; b < a.nblocks; b += gridDim.x) {
+    const BlockCoord bc(b, a.nb1, a.nb2);
     if (BM_FWD_DOUBLE_BUFFER) {
       const int64_t nx = b + gridDim.x;
-      if (nx < a.nblocks)
-        issue_block_load<T, B>(Abuf + (buf ^ 1) * Cfg::A, a.field, a.n0, a.n1, a.n2, nx / nbc, (nx / a.nb2) % a.nb1,
-                               nx % a.nb2);
+      if (nx < a.nblocks) issue_block_load<T, B>(Abuf + (buf ^ 1) * Cfg::A, a.field, span(nx), a.n1, a.n2);
       cp_async_commit();
       cp_async_wait<1>();
     } else {
-      issue_block_load<T, B>(Abuf, a.field, a.n0, a.n1, a.n2, b / nbc, (b / a.nb2) % a.nb1, b % a.nb2);
+      issue_block_load<T, B>(Abuf, a.field, BlockSpan<const T, B>(a.field, a.n0, a.n1, a.n2, bc), a.n1, a.n2);
       cp_async_commit();
       cp_async_wait<0>();
     }
@@ -323,10 +389,10 @@ __global__ void __launch_bounds__(BlockCfg<T, B, K>::NT, BM_FWD_MIN_CTAS) block_
     {
       constexpr int M = Cfg::M;
       const T* cf = bufs(K);
-      const int64_t b0 = b / nbc, b1 = (b / a.nb2) % a.nb1, b2 = b % a.nb2;
+      T* g = a.G + (((int64_t)bc.b0 * M) * a.g1 + (int64_t)bc.b1 * M) * a.g2 + (int64_t)bc.b2 * M;
       for (int e = threadIdx.x; e < M * M * M; e += blockDim.x) {
         const int j0 = e / (M * M), r = e - j0 * M * M, j1 = r / M, j2 = r - j1 * M;
-        a.G[((b0 * M + j0) * a.g1 + (b1 * M + j1)) * a.g2 + (b2 * M + j2)] = cf[e];
+        g[((int64_t)j0 * a.g1 + j1) * a.g2 + j2] = cf[e];
       }
     }
     if (MODE == 0) store_symbols<Cfg::PB>(a.sym + sbase, stage, sbase);
@@ -449,11 +515,10 @@ __global__ void __launch_bounds__(BlockCfg<T, B, K>::NT) block_inv_kernel(BlockA
   T* cb0 = T2 + Cfg::T2;
   T* cb1 = cb0 + Cfg::CB0;
   void* stage = smem_raw + Cfg::inv_stage_off;
-  const int64_t nbc = (int64_t)a.nb1 * a.nb2;
   LevelBufs<T> bufs{A, cb0, cb1};
   constexpr int M = Cfg::M;
   for (int64_t b = blockIdx.x; b < a.nblocks; b += gridDim.x) {
-    const int64_t b0 = b / nbc, b1 = (b / a.nb2) % a.nb1, b2 = b % a.nb2;
+    const BlockCoord bc(b, a.nb1, a.nb2);
     const int64_t sbase = b * (int64_t)Cfg::PB;
     if (MODE == 0) {
       uint16_t* st = reinterpret_cast<uint16_t*>(stage);
@@ -471,9 +536,10 @@ __global__ void __launch_bounds__(BlockCfg<T, B, K>::NT) block_inv_kernel(BlockA
       for (int i = threadIdx.x; i < Cfg::PB; i += blockDim.x) st[i] = a.coef[sbase + i];
     }
     T* cf = bufs(K);
+    const T* g = a.G + (((int64_t)bc.b0 * M) * a.g1 + (int64_t)bc.b1 * M) * a.g2 + (int64_t)bc.b2 * M;
     for (int e = threadIdx.x; e < M * M * M; e += blockDim.x) {
       const int j0 = e / (M * M), r = e - j0 * M * M, j1 = r / M, j2 = r - j1 * M;
-      cf[e] = a.G[((b0 * M + j0) * a.g1 + (b1 * M + j1)) * a.g2 + (b2 * M + j2)];
+      cf[e] = g[((int64_t)j0 * a.g1 + j1) * a.g2 + j2];
     }
     __syncthreads();
     int tier = (MODE == 0 && a.tier) ? a.tier[b] : 0;
@@ -483,11 +549,7 @@ __global__ void __launch_bounds__(BlockCfg<T, B, K>::NT) block_inv_kernel(BlockA
     }
     InvLevels<T, M * 2 - 1, K - 1, B, MODE>::run(bufs, T1, T2, a.q + tier * K, K, stage,
                                                   MODE == 0 ? a.esc + sbase : nullptr, a.radius);
-    for (int e = threadIdx.x; e < B * B * B; e += blockDim.x) {
-      const int i0 = e / (B * B), r = e - i0 * (B * B), i1 = r / B, k = r - i1 * B;
-      const int64_t g0 = b0 * B + i0, g1 = b1 * B + i1, g2 = b2 * B + k;
-      if (g0 < a.n0 && g1 < a.n1 && g2 < a.n2) a.field[(g0 * a.n1 + g1) * a.n2 + g2] = A[e];
-    }
+    store_block<T, B>(BlockSpan<T, B>(a.field, a.n0, a.n1, a.n2, bc), A, a.n1, a.n2);
     __syncthreads();
   }
 }
