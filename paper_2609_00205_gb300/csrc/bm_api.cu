@@ -198,7 +198,7 @@ bm_status upload_tables(PlanDev& P) {
     if (bytes) std::memcpy(img.data() + off, src, bytes);
     return off;
   };
-  struct Offs { size_t cidx, jlo, jhi, wl, wr, cb, isc, f0, band, tm, tib, tsup; };
+  struct Offs { size_t cidx, jlo, jhi, wl, wr, cb, isc, f0, band, tm, tib, tsup, proj; };
   std::vector<Offs> offs;
   for (auto& L3 : P.h.glev)
     for (auto& D : L3) {
@@ -208,7 +208,7 @@ bm_status upload_tables(PlanDev& P) {
         return o;
       };
       std::vector<T> wl = cvt(D.wl), wr = cvt(D.wr), band = cvt(D.band), tm = cvt(D.tm), tib = cvt(D.tib),
-                     tsup = cvt(D.tsup);
+                     tsup = cvt(D.tsup), proj = cvt(D.P);
       Offs o;
       o.cidx = put(D.cidx.data(), D.cidx.size() * 4);
       o.jlo = put(D.jlo.data(), D.jlo.size() * 4);
@@ -222,6 +222,7 @@ bm_status upload_tables(PlanDev& P) {
       o.tm = put(tm.data(), tm.size() * sizeof(T));
       o.tib = put(tib.data(), tib.size() * sizeof(T));
       o.tsup = put(tsup.data(), tsup.size() * sizeof(T));
+      o.proj = put(proj.data(), proj.size() * sizeof(T));
       offs.push_back(o);
     }
   if (P.dtab[di]) { cudaFree(P.dtab[di]); P.dtab[di] = nullptr; }
@@ -252,6 +253,7 @@ bm_status upload_tables(PlanDev& P) {
       g.tm = reinterpret_cast<const T*>(base + o.tm);
       g.tib = reinterpret_cast<const T*>(base + o.tib);
       g.tsup = reinterpret_cast<const T*>(base + o.tsup);
+      g.P = reinterpret_cast<const T*>(base + o.proj);
     }
     L.sym_off = P.h.sym_off[l];
     G.push_back(L);
@@ -577,6 +579,14 @@ cudaError_t launch_block<double>(int dir, int B, int K, int mode, const BlockArg
                 : launch_block_f64_b17(dir, K, mode, a, s, num_sms(), cap);
 }
 
+// One dense restriction pass of a global level (gl_apply).
+template <typename T, int DIM, int FINAL>
+void launch_apply(const GLevel<T>& L, const T* in, T* out, const T* U, cudaStream_t s) {
+  const ApplyShape S = apply_shape(L, DIM);
+  const int64_t ctas = S.nb * ((S.ncol + kApplyCols - 1) / kApplyCols);
+  gl_apply<T, DIM, FINAL><<<(unsigned)ctas, 256, 0, s>>>(L, S, in, out, U);
+}
+
 // Outputs of the decomposition (mode 0: symbols + escapes + histogram).
 template <typename T>
 struct FwdOut {
@@ -620,13 +630,14 @@ bm_status run_decompose(PlanDev& P, const T* field, int mode, const FwdOut<T>& o
     const GLevel<T>& L = G[l];
     const int64_t nn = gs.U[l];
     const T* rq = o.rq ? o.rq + o.ntiers * h.K + l : nullptr;
-    if (mode == 0) gl_fwd_detail<T, 0><<<grid_for(nn, 256), 256, 0, s>>>(L, U[l], Dbuf, o.sym, o.esc, o.coef, rq, o.hist, o.radius, o.sc);
-    else gl_fwd_detail<T, 1><<<grid_for(nn, 256), 256, 0, s>>>(L, U[l], Dbuf, o.sym, o.esc, o.coef, rq, o.hist, o.radius, o.sc);
+    const int64_t rows = (int64_t)L.d[0].n * L.d[1].n;  // one warp per row, 8 rows per CTA
+    if (mode == 0) gl_fwd_detail<T, 0><<<grid_for(rows * 32, 256, 2), 256, 0, s>>>(L, U[l], Dbuf, o.sym, o.esc, o.coef, rq, o.hist, o.radius, o.sc);
+    else gl_fwd_detail<T, 1><<<grid_for(rows * 32, 256, 8), 256, 0, s>>>(L, U[l], Dbuf, o.sym, o.esc, o.coef, rq, o.hist, o.radius, o.sc);
+    (void)nn;
     BM_LAUNCHED();
-    const int64_t l2 = (int64_t)L.d[0].n * L.d[1].n, l1 = (int64_t)L.d[0].n * L.d[2].c, l0 = (int64_t)L.d[1].c * L.d[2].c;
-    gl_restrict<T, 2, 0><<<grid_for(l2, 32, 64), 32, 0, s>>>(L, Dbuf, W1, nullptr);
-    gl_restrict<T, 1, 0><<<grid_for(l1, 32, 64), 32, 0, s>>>(L, W1, W2, nullptr);
-    gl_restrict<T, 0, 1><<<grid_for(l0, 32, 64), 32, 0, s>>>(L, W2, U[l + 1], U[l]);
+    launch_apply<T, 2, 0>(L, Dbuf, W1, nullptr, s);
+    launch_apply<T, 1, 0>(L, W1, W2, nullptr, s);
+    launch_apply<T, 0, 1>(L, W2, U[l + 1], U[l], s);
     g_launches.fetch_add(3);
     BM_CUDA(cudaGetLastError());
   }
@@ -683,11 +694,10 @@ bm_status run_recompose(PlanDev& P, T* field, int mode, const InvIn<T>& in, Carv
     // U[l] <- dequantised coefficients; z = P D; coarse' = U[l+1] - z (into W1); U[l] = I coarse' + D
     if (mode == 0) gl_inv_dequant<T, 0><<<grid_for(nn, 256), 256, 0, s>>>(L, in.sym, in.esc, in.coef, q, in.radius, U[l]);
     else gl_inv_dequant<T, 1><<<grid_for(nn, 256), 256, 0, s>>>(L, in.sym, in.esc, in.coef, q, in.radius, U[l]);
-    const int64_t l2 = (int64_t)L.d[0].n * L.d[1].n, l1 = (int64_t)L.d[0].n * L.d[2].c, l0 = (int64_t)L.d[1].c * L.d[2].c;
     T* Cn = Dbuf;  // corrected coarse values (size of U[l+1] <= size of U[0])
-    gl_restrict<T, 2, 0><<<grid_for(l2, 32, 64), 32, 0, s>>>(L, U[l], W1, nullptr);
-    gl_restrict<T, 1, 0><<<grid_for(l1, 32, 64), 32, 0, s>>>(L, W1, W2, nullptr);
-    gl_restrict<T, 0, 2><<<grid_for(l0, 32, 64), 32, 0, s>>>(L, W2, Cn, U[l + 1]);
+    launch_apply<T, 2, 0>(L, U[l], W1, nullptr, s);
+    launch_apply<T, 1, 0>(L, W1, W2, nullptr, s);
+    launch_apply<T, 0, 2>(L, W2, Cn, U[l + 1], s);
     gl_inv_interp<T><<<grid_for(nn, 256), 256, 0, s>>>(L, Cn, U[l]);
     g_launches.fetch_add(5);
     BM_CUDA(cudaGetLastError());

@@ -26,6 +26,7 @@ struct GDim {
   const T* tm;          // [c] Thomas multipliers of M_c
   const T* tib;         // [c] inverse pivots
   const T* tsup;        // [c] super-diagonal
+  const T* P;           // [c x n] row-major projection M_c^{-1} I^T M_f
 };
 
 template <typename T>
@@ -52,50 +53,58 @@ __device__ __forceinline__ int64_t nc_rank(const GLevel<T>& L, int i0, int i1, i
 
 // Coefficients of one global level: D = U - I(U|C) at every node (0 at
 // all-coarse nodes, exactly), written to Dfull; the non-coarse ones are
-// quantised (mode 0) or stored (mode 1) at their stream position.
+// quantised (mode 0) or stored (mode 1) at their stream position.  One warp
+// per grid row (i0, i1): the row's interpolation sources, weights and stream
+// offset are computed once, the lanes walk i2.
 template <typename T, int MODE>
-__global__ void gl_fwd_detail(GLevel<T> L, const T* __restrict__ U, T* __restrict__ Dfull, uint16_t* sym,
-                              int32_t* esc, T* coef, const T* rq_ptr, unsigned* hist, int radius, Scalars* sc) {
+__global__ void __launch_bounds__(256) gl_fwd_detail(GLevel<T> L, const T* __restrict__ U, T* __restrict__ Dfull,
+                                                     uint16_t* sym, int32_t* esc, T* coef, const T* rq_ptr,
+                                                     unsigned* hist, int radius, Scalars* sc) {
   __shared__ unsigned hloc[kHistWin];
   if (MODE == 0)
     for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) hloc[i] = 0;
   __syncthreads();
-  const int n0 = L.d[0].n, n1 = L.d[1].n, n2 = L.d[2].n;
-  const int64_t total = (int64_t)n0 * n1 * n2;
+  const GDim<T>&D0 = L.d[0], &D1 = L.d[1], &D2 = L.d[2];
+  const int n1 = D1.n, n2 = D2.n;
+  const int64_t rows = (int64_t)D0.n * n1, c12 = (int64_t)D1.c * D2.c;
   const T rq = MODE == 0 ? *rq_ptr : T(0);
+  const unsigned dict = 2u * (unsigned)radius;
   bool ovf = false;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int i2 = (int)(idx % n2);
-    const int64_t t = idx / n2;
-    const int i1 = (int)(t % n1);
-    const int i0 = (int)(t / n1);
-    const int a0 = L.d[0].cidx[L.d[0].jlo[i0]], b0 = L.d[0].cidx[L.d[0].jhi[i0]];
-    const int a1 = L.d[1].cidx[L.d[1].jlo[i1]], b1 = L.d[1].cidx[L.d[1].jhi[i1]];
-    const int a2 = L.d[2].cidx[L.d[2].jlo[i2]], b2 = L.d[2].cidx[L.d[2].jhi[i2]];
-    const T wl0 = L.d[0].wl[i0], wr0 = L.d[0].wr[i0];
-    const T wl1 = L.d[1].wl[i1], wr1 = L.d[1].wr[i1];
-    const T wl2 = L.d[2].wl[i2], wr2 = L.d[2].wr[i2];
-    auto s = [&](int x0, int x1) {
-      const T* row = U + ((int64_t)x0 * n1 + x1) * n2;
-      return fma(wl2, row[a2], wr2 * row[b2]);
-    };
-    const T ta = fma(wl1, s(a0, a1), wr1 * s(a0, b1));
-    const T tb = fma(wl1, s(b0, a1), wr1 * s(b0, b1));
-    const T e = fma(wl0, ta, wr0 * tb);
-    const T dv = U[idx] - e;
-    Dfull[idx] = dv;
-    if (!all_coarse(L.d[0].isc, L.d[1].isc, L.d[2].isc, i0, i1, i2)) {
-      const int64_t pos = L.sym_off + nc_rank(L, i0, i1, i2, idx);
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows; row += nwarps) {
+    const int i0 = (int)(row / n1), i1 = (int)(row - (int64_t)i0 * n1);
+    const int a0 = D0.cidx[D0.jlo[i0]], b0 = D0.cidx[D0.jhi[i0]];
+    const int a1 = D1.cidx[D1.jlo[i1]], b1 = D1.cidx[D1.jhi[i1]];
+    const T wl0 = D0.wl[i0], wr0 = D0.wr[i0], wl1 = D1.wl[i1], wr1 = D1.wr[i1];
+    const T* r00 = U + ((int64_t)a0 * n1 + a1) * n2;
+    const T* r01 = U + ((int64_t)a0 * n1 + b1) * n2;
+    const T* r10 = U + ((int64_t)b0 * n1 + a1) * n2;
+    const T* r11 = U + ((int64_t)b0 * n1 + b1) * n2;
+    const bool cc01 = D0.isc[i0] && D1.isc[i1];  // the row holds all-coarse nodes
+    // stream rank of the row's first node: flat index minus the all-coarse nodes before it
+    int64_t before = (int64_t)D0.cb[i0] * c12;
+    if (D0.isc[i0]) before += (int64_t)D1.cb[i1] * D2.c;
+    const int64_t rbase = L.sym_off + row * n2 - before;
+    for (int i2 = lane; i2 < n2; i2 += 32) {
+      const int a2 = D2.cidx[D2.jlo[i2]], b2 = D2.cidx[D2.jhi[i2]];
+      const T wl2 = D2.wl[i2], wr2 = D2.wr[i2];
+      const T ta = fma(wl1, fma(wl2, r00[a2], wr2 * r00[b2]), wr1 * fma(wl2, r01[a2], wr2 * r01[b2]));
+      const T tb = fma(wl1, fma(wl2, r10[a2], wr2 * r10[b2]), wr1 * fma(wl2, r11[a2], wr2 * r11[b2]));
+      const T e = fma(wl0, ta, wr0 * tb);
+      const int64_t idx = row * n2 + i2;
+      const T dv = U[idx] - e;
+      Dfull[idx] = dv;
+      if (cc01 && D2.isc[i2]) continue;  // all-coarse node: no coefficient
+      const int64_t pos = rbase + i2 - (cc01 ? D2.cb[i2] : 0);
       if (MODE == 0) {
         const int code = quantize(dv, rq, ovf);
-        const bool in = code > -radius && code < radius;
-        const unsigned sv = in ? (unsigned)(code + radius) : 0u;
+        const unsigned u = (unsigned)(code + radius);
+        const bool in = u - 1u < dict - 1u;
+        const unsigned sv = in ? u : 0u;
         sym[pos] = (uint16_t)sv;
         if (!in) esc[pos] = code;
-        const int bin = (int)sv - (radius - kHistWin / 2);
-        if (bin >= 0 && bin < kHistWin) atomicAdd(hloc + bin, 1u);
-        else atomicAdd(hist + sv, 1u);
+        atomicAdd(hloc + sv, 1u);
       } else {
         coef[pos] = dv;
       }
@@ -104,10 +113,9 @@ __global__ void gl_fwd_detail(GLevel<T> L, const T* __restrict__ U, T* __restric
   if (MODE == 0) {
     if (ovf) atomicOr(&sc->status, ST_OVERFLOW);
     __syncthreads();
-    const int lo = radius - kHistWin / 2;
-    for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) {
+    for (int i = threadIdx.x; i < (int)dict; i += blockDim.x) {
       const unsigned v = hloc[i];
-      if (v && lo + i >= 0 && lo + i < 2 * radius) atomicAdd(hist + lo + i, v);
+      if (v) atomicAdd(hist + i, v);
     }
   }
 }
@@ -174,6 +182,102 @@ __global__ void gl_restrict(GLevel<T> L, const T* __restrict__ in, T* out, const
         out[obase + J * ostride] = U[obase + J * ostride] - z;
       } else {
         out[obase + J * ostride] = z;
+      }
+    }
+  }
+}
+
+// One restriction pass of a global level as a dense contraction with the
+// level's projection P = M_c^{-1} I^T M_f (c x n) along dimension DIM:
+//   out[b][J][col] = sum_i P[J][i] in[b][i][col]
+// (the same operator as band products followed by the tridiagonal solve).
+// A CTA owns 64 columns of one batch; 32 x 64 tiles of `in` (its unit-stride
+// index varying fastest across threads) and 32 x 32 tiles of P are staged in
+// shared memory; a thread keeps 8 outputs of each 32-row tile of J.
+//   DIM 2: in (n0,n1,n2) -> out (n0,n1,c2), columns = lines (n0*n1)
+//   DIM 1: in (n0,n1,c2) -> out (n0,c1,c2), batches i0, columns j2
+//   DIM 0: in (n0,c1,c2) -> out (c0,c1,c2), columns (j1,j2); FINAL 1: out =
+//          U|C + z (forward), FINAL 2: out = U - z (inverse, U compact)
+struct ApplyShape {
+  int64_t nb, ncol;
+  int64_t in_b, in_i, in_c;
+  int64_t out_b, out_j, out_c;
+};
+
+template <typename T>
+ApplyShape apply_shape(const GLevel<T>& L, int dim) {
+  const int64_t n0 = L.d[0].n, n1 = L.d[1].n, n2 = L.d[2].n, c1 = L.d[1].c, c2 = L.d[2].c;
+  ApplyShape S{};
+  if (dim == 2) {
+    S.nb = 1; S.ncol = n0 * n1; S.in_i = 1; S.in_c = n2; S.out_j = 1; S.out_c = c2;
+  } else if (dim == 1) {
+    S.nb = n0; S.ncol = c2; S.in_b = n1 * c2; S.in_i = c2; S.in_c = 1; S.out_b = c1 * c2; S.out_j = c2; S.out_c = 1;
+  } else {
+    S.nb = 1; S.ncol = c1 * c2; S.in_i = c1 * c2; S.in_c = 1; S.out_j = c1 * c2; S.out_c = 1;
+  }
+  return S;
+}
+
+constexpr int kApplyCols = 64, kApplyK = 32, kApplyJ = 32;
+
+template <typename T, int DIM, int FINAL>
+__global__ void __launch_bounds__(256) gl_apply(GLevel<T> L, ApplyShape S, const T* __restrict__ in,
+                                                T* __restrict__ out, const T* __restrict__ U) {
+  __shared__ T s_in[kApplyK][kApplyCols + 1];
+  __shared__ T s_p[kApplyJ][kApplyK + 1];
+  const GDim<T>& D = L.d[DIM];
+  const int n = D.n, c = D.c;
+  const int64_t tiles = (S.ncol + kApplyCols - 1) / kApplyCols;
+  const int64_t b = blockIdx.x / tiles;
+  const int64_t col0 = (blockIdx.x - b * tiles) * kApplyCols;
+  const int tid = threadIdx.x, tc = tid & (kApplyCols - 1), jg = tid >> 6;
+  const T* inb = in + b * S.in_b;
+  const bool unit_i = S.in_i == 1;
+  for (int jt = 0; jt < c; jt += kApplyJ) {
+    T acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = T(0);
+    for (int i0 = 0; i0 < n; i0 += kApplyK) {
+      __syncthreads();  // the previous tile has been consumed
+#pragma unroll
+      for (int r = 0; r < kApplyK * kApplyCols / 256; ++r) {
+        const int e = tid + 256 * r;
+        const int ii = unit_i ? (e & (kApplyK - 1)) : (e >> 6);
+        const int cc = unit_i ? (e >> 5) : (e & (kApplyCols - 1));
+        const int64_t col = col0 + cc;
+        T v = T(0);
+        if (i0 + ii < n && col < S.ncol) v = inb[(int64_t)(i0 + ii) * S.in_i + col * S.in_c];
+        s_in[ii][cc] = v;
+      }
+#pragma unroll
+      for (int r = 0; r < kApplyJ * kApplyK / 256; ++r) {
+        const int e = tid + 256 * r, ii = e & (kApplyK - 1), jj = e >> 5;
+        s_p[jj][ii] = (jt + jj < c && i0 + ii < n) ? D.P[(int64_t)(jt + jj) * n + i0 + ii] : T(0);
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int ii = 0; ii < kApplyK; ++ii) {
+        const T x = s_in[ii][tc];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = fma(s_p[jg * 8 + q][ii], x, acc[q]);
+      }
+    }
+    const int64_t col = col0 + tc;
+    if (col < S.ncol) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int J = jt + jg * 8 + q;
+        if (J >= c) break;
+        const int64_t o = b * S.out_b + (int64_t)J * S.out_j + col * S.out_c;
+        if (FINAL == 1) {
+          const int c2 = L.d[2].c, j1 = (int)(col / c2), j2 = (int)(col - (int64_t)j1 * c2);
+          const int64_t u = ((int64_t)L.d[0].cidx[J] * L.d[1].n + L.d[1].cidx[j1]) * L.d[2].n + L.d[2].cidx[j2];
+          out[o] = U[u] + acc[q];
+        } else if (FINAL == 2) {
+          out[o] = U[o] - acc[q];
+        } else {
+          out[o] = acc[q];
+        }
       }
     }
   }

@@ -224,6 +224,7 @@ std::string make_plan(const int64_t* shape, int B, int K, int M, PlanHost& p) {
     for (int d = 0; d < 3; ++d) {
       if (gx[d].size() < 2) return "global level on a dimension with fewer than 2 nodes";
       L3.push_back(make_dim(gx[d]));
+      L3.back().P = projection(L3.back());
     }
     const int64_t cnt = (int64_t)L3[0].n * L3[1].n * L3[2].n - (int64_t)L3[0].c * L3[1].c * L3[2].c;
     pos += cnt;
