@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <functional>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -23,6 +24,14 @@
 #ifndef BM_FWD_HIST
 #define BM_FWD_HIST 0
 #endif
+// The block region's histogram: on a second stream beside the global levels
+// (BM_HIST_OVERLAP) with BM_HIST_CTAS CTAs per SM.
+#ifndef BM_HIST_OVERLAP
+#define BM_HIST_OVERLAP 1
+#endif
+#ifndef BM_HIST_CTAS
+#define BM_HIST_CTAS 2
+#endif
 
 namespace bm {
 namespace {
@@ -35,7 +44,7 @@ std::atomic<uint64_t> g_launches{0};
 std::atomic<int> g_timing{0};
 
 struct StageTimer {
-  struct Rec { const char* name; cudaEvent_t a, b; };
+  struct Rec { const char* name; cudaEvent_t a, b; cudaStream_t s; };
   std::vector<Rec> recs;
   std::vector<std::pair<const char*, float>> last;
   cudaStream_t s = nullptr;
@@ -49,17 +58,17 @@ struct StageTimer {
     for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     recs.clear();
   }
-  int open(const char* name) {
+  int open(const char* name, cudaStream_t st) {
     if (!on) return -1;
-    Rec r{name, nullptr, nullptr};
+    Rec r{name, nullptr, nullptr, st ? st : s};
     cudaEventCreate(&r.a);
     cudaEventCreate(&r.b);
-    cudaEventRecord(r.a, s);
+    cudaEventRecord(r.a, r.s);
     recs.push_back(r);
     return (int)recs.size() - 1;
   }
   void close(int i) {
-    if (i >= 0) cudaEventRecord(recs[i].b, s);
+    if (i >= 0) cudaEventRecord(recs[i].b, recs[i].s);
   }
   void collect() {
     if (!on) return;
@@ -76,9 +85,9 @@ struct StageTimer {
 std::mutex g_timer_mu;
 StageTimer g_timer;
 
-struct Stage {
+struct Stage {  // times a stage on the call's stream (or on `st`)
   int i;
-  explicit Stage(const char* n) : i(g_timer.open(n)) {}
+  explicit Stage(const char* n, cudaStream_t st = nullptr) : i(g_timer.open(n, st)) {}
   ~Stage() { g_timer.close(i); }
 };
 
@@ -117,7 +126,19 @@ struct Workspace {
   void* h = nullptr;
   size_t hbytes = 0;
   int dev = -1;
+  // second stream for work that runs beside the caller's stream, joined back
+  // into it by an event before the call returns
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
+
+bm_status ensure_aux(Workspace* w) {
+  if (w->aux) return BM_OK;
+  BM_CUDA(cudaStreamCreateWithFlags(&w->aux, cudaStreamNonBlocking));
+  BM_CUDA(cudaEventCreateWithFlags(&w->ev_fork, cudaEventDisableTiming));
+  BM_CUDA(cudaEventCreateWithFlags(&w->ev_join, cudaEventDisableTiming));
+  return BM_OK;
+}
 std::mutex g_ws_mu;
 std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
 
@@ -602,7 +623,8 @@ struct FwdOut {
 };
 
 template <typename T>
-bm_status run_decompose(PlanDev& P, const T* field, int mode, const FwdOut<T>& o, Carver& cv, cudaStream_t s) {
+bm_status run_decompose(PlanDev& P, const T* field, int mode, const FwdOut<T>& o, Carver& cv, cudaStream_t s,
+                        const std::function<bm_status()>& after_block = nullptr) {
   const PlanHost& h = P.h;
   if (bm_status st = upload_tables<T>(P)) return st;
   const GSizes gs = gsizes(h);
@@ -624,6 +646,8 @@ bm_status run_decompose(PlanDev& P, const T* field, int mode, const FwdOut<T>& o
     a.tier = o.tier; a.rq = o.rq; a.hist = o.hist; a.radius = o.radius; a.sc = o.sc;
     BM_CUDA(launch_block<T>(0, h.B, h.K, mode, a, s));
   }
+  if (after_block)
+    if (bm_status st = after_block()) return st;
   auto& G = glevels<T>(P);
   for (int l = 0; l < h.M; ++l) {
     Stage st("global_decompose");
@@ -861,12 +885,32 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   FwdOut<T> fo;
   fo.sym = sym; fo.esc = esc; fo.hist = hist; fo.tier = ntiers > 1 ? dbt : nullptr; fo.rq = rq;
   fo.ntiers = ntiers; fo.radius = prm.radius; fo.sc = sc;
-  if (bm_status st = run_decompose<T>(*P, field, 0, fo, cv, s)) return st;
-  if (!BM_FWD_HIST) {  // the block kernel did not count its symbols
-    Stage st("histogram");
-    const unsigned long long nloc = (unsigned long long)h.nblocks * h.per_block;
-    hist_range_kernel<<<num_sms() * 4, 256, 0, s>>>(sym, 0, nloc, dict, (unsigned)prm.radius, hist);
-    BM_LAUNCHED();
+  // the block kernel does not count its symbols: their histogram is taken on
+  // a second stream while the global levels run on the call's stream
+  auto block_hist = [&]() -> bm_status {
+    if (BM_FWD_HIST) return BM_OK;
+    cudaStream_t hs = s;
+    if (BM_HIST_OVERLAP) {
+      if (bm_status st = ensure_aux(ws)) return st;
+      BM_CUDA(cudaEventRecord(ws->ev_fork, s));
+      BM_CUDA(cudaStreamWaitEvent(ws->aux, ws->ev_fork, 0));
+      hs = ws->aux;
+    }
+    {
+      Stage st("histogram", hs);
+      const unsigned long long nloc = (unsigned long long)h.nblocks * h.per_block;
+      hist_range_kernel<<<num_sms() * BM_HIST_CTAS, 256, 0, hs>>>(sym, 0, nloc, dict, (unsigned)prm.radius, hist);
+      BM_LAUNCHED();
+    }
+    if (BM_HIST_OVERLAP) BM_CUDA(cudaEventRecord(ws->ev_join, ws->aux));
+    return BM_OK;
+  };
+  {
+    const bm_status st = run_decompose<T>(*P, field, 0, fo, cv, s, block_hist);
+    // join the second stream before anything else (also on errors: no work
+    // of this call may outlive it)
+    if (!BM_FWD_HIST && BM_HIST_OVERLAP && ws->aux) BM_CUDA(cudaStreamWaitEvent(s, ws->ev_join, 0));
+    if (st) return st;
   }
   {
     Stage st("huffman_codebook");
@@ -1390,6 +1434,12 @@ void bm_release_workspace(void* stream) {
       cudaStreamSynchronize(it->first.second);
       if (it->second.d) cudaFree(it->second.d);
       if (it->second.h) cudaFreeHost(it->second.h);
+      if (it->second.aux) {
+        cudaStreamSynchronize(it->second.aux);
+        cudaStreamDestroy(it->second.aux);
+        cudaEventDestroy(it->second.ev_fork);
+        cudaEventDestroy(it->second.ev_join);
+      }
       cudaSetDevice(cur);
       it = g_ws.erase(it);
     } else {

@@ -397,47 +397,54 @@ __global__ void hist_kernel(const uint16_t* __restrict__ sym, unsigned long long
     if (hs[i]) atomicAdd(hist + i, hs[i]);
 }
 
-// Histogram of a symbol range [s0, s1) with 16-byte loads.  The seven
-// symbols around the centre (codes -3..3, most of the symbols of quantised
-// coefficients) are counted in registers; the rest with shared atomics.
+// Histogram of a symbol range [s0, s1) with 16-byte loads.  Build-time choice
+// BM_HIST_METHOD: 1 = the centre symbol (code 0) counted in a register, the
+// rest with shared atomics; 7 = the seven symbols around the centre in
+// registers; 0 = equal symbols of a warp instruction merged first
+// (__match_any_sync), one shared atomic per distinct symbol.
+#ifndef BM_HIST_METHOD
+#define BM_HIST_METHOD 1
+#endif
 __global__ void __launch_bounds__(256) hist_range_kernel(const uint16_t* __restrict__ sym, unsigned long long s0,
                                                          unsigned long long s1, int dict, unsigned centre_sym,
                                                          unsigned* hist) {
   __shared__ unsigned hs[kMaxDict];
   for (int i = threadIdx.x; i < dict; i += blockDim.x) hs[i] = 0;
   __syncthreads();
-  unsigned c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0, c6 = 0;
-  const unsigned lo = centre_sym - 3u;
+  constexpr int NC = BM_HIST_METHOD == 7 ? 7 : 1;
+  unsigned cnt[NC];
+#pragma unroll
+  for (int j = 0; j < NC; ++j) cnt[j] = 0;
+  const unsigned lo = centre_sym - (NC / 2);
   auto count = [&](unsigned s) {
+    if (BM_HIST_METHOD == 0) {
+      const unsigned m = __match_any_sync(__activemask(), s);
+      if ((unsigned)(threadIdx.x & 31) == (unsigned)(__ffs(m) - 1) && s < (unsigned)dict) atomicAdd(hs + s, __popc(m));
+      return;
+    }
     const unsigned d = s - lo;
-    c0 += d == 0; c1 += d == 1; c2 += d == 2; c3 += d == 3; c4 += d == 4; c5 += d == 5; c6 += d == 6;
-    if (d > 6u && s < (unsigned)dict) atomicAdd(hs + s, 1u);
+#pragma unroll
+    for (int j = 0; j < NC; ++j) cnt[j] += d == (unsigned)j;
+    if (d >= (unsigned)NC && s < (unsigned)dict) atomicAdd(hs + s, 1u);
   };
   const unsigned long long a0 = min(s1, (s0 + 7) & ~7ull);  // 16-byte aligned start
   const unsigned long long tid = blockIdx.x * 256ull + threadIdx.x, nth = gridDim.x * 256ull;
   for (unsigned long long i = s0 + tid; i < a0; i += nth) count(sym[i]);
   const unsigned long long nv = (s1 - a0) / 8;
   const uint4* pv = reinterpret_cast<const uint4*>(sym + a0);
-  unsigned long long v = tid;
-  for (; v + nth < nv; v += 2 * nth) {
-    const uint4 q = __ldg(pv + v), r = __ldg(pv + v + nth);
-    const unsigned w8[8] = {q.x, q.y, q.z, q.w, r.x, r.y, r.z, r.w};
-#pragma unroll
-    for (int h = 0; h < 8; ++h) { count(w8[h] & 0xFFFFu); count(w8[h] >> 16); }
-  }
-  for (; v < nv; v += nth) {
+  for (unsigned long long v = tid; v < nv; v += nth) {
     const uint4 q = __ldg(pv + v);
     const unsigned w4[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
     for (int h = 0; h < 4; ++h) { count(w4[h] & 0xFFFFu); count(w4[h] >> 16); }
   }
   for (unsigned long long i = a0 + nv * 8 + tid; i < s1; i += nth) count(sym[i]);
-  unsigned cc[7] = {c0, c1, c2, c3, c4, c5, c6};
 #pragma unroll
-  for (int j = 0; j < 7; ++j) {
+  for (int j = 0; j < NC; ++j) {
+    unsigned c = cnt[j];
 #pragma unroll
-    for (int o = 16; o; o >>= 1) cc[j] += __shfl_xor_sync(0xffffffffu, cc[j], o);
-    if ((threadIdx.x & 31) == 0 && cc[j] && lo + j < (unsigned)dict) atomicAdd(hs + lo + j, cc[j]);
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (BM_HIST_METHOD != 0 && (threadIdx.x & 31) == 0 && c && lo + j < (unsigned)dict) atomicAdd(hs + lo + j, c);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < dict; i += blockDim.x)
