@@ -66,20 +66,75 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* warp_t
   return before;
 }
 
-template <typename K>
-__device__ void bitonic_sort(K* keys, int P) {
+// Bitonic sort of 1024*E keys (ascending) by one block of 1024 threads, E
+// consecutive keys per thread in registers: exchanges within a thread need no
+// communication, partners up to 31 threads away are reached by shuffles, and
+// only the longer strides go through shared memory.
+template <typename K, int E, int J>
+__device__ __forceinline__ void sort_stage_regs(K (&v)[E], int t, int k) {
+#pragma unroll
+  for (int e = 0; e < E; ++e)
+    if ((e & J) == 0) {
+      const bool up = ((t * E + e) & k) == 0;
+      const K a = v[e], b = v[e + J];
+      const bool sw = (a > b) == up;
+      v[e] = sw ? b : a;
+      v[e + J] = sw ? a : b;
+    }
+}
+
+template <typename K, int E>
+__device__ void block_sort_regs(K* keys) {
+  constexpr int P = 1024 * E;
+  const int t = threadIdx.x;
+  K v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) v[e] = keys[t * E + e];
   for (int k = 2; k <= P; k <<= 1)
     for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        const int ixj = i ^ j;
-        if (ixj > i) {
-          const K a = keys[i], b = keys[ixj];
-          const bool up = (i & k) == 0;
-          if ((a > b) == up) { keys[i] = b; keys[ixj] = a; }
+      if (j < E) {
+        if (E > 4 && j == 4) sort_stage_regs<K, E, (E > 4 ? 4 : 1)>(v, t, k);
+        else if (E > 2 && j == 2) sort_stage_regs<K, E, (E > 2 ? 2 : 1)>(v, t, k);
+        else sort_stage_regs<K, E, 1>(v, t, k);
+        continue;
+      }
+      const int m = j / E;  // partner thread distance
+      const bool keep_min = (((t & m) == 0) == (((t * E) & k) == 0));
+      if (m < 32) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const K o = __shfl_xor_sync(0xffffffffu, v[e], m);
+          v[e] = keep_min ? (o < v[e] ? o : v[e]) : (o > v[e] ? o : v[e]);
+        }
+      } else {
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < E; ++e) keys[t * E + e] = v[e];
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const K o = keys[(t ^ m) * E + e];
+          v[e] = keep_min ? (o < v[e] ? o : v[e]) : (o > v[e] ? o : v[e]);
         }
       }
-      __syncthreads();
     }
+  __syncthreads();
+#pragma unroll
+  for (int e = 0; e < E; ++e) keys[t * E + e] = v[e];
+  __syncthreads();
+}
+
+// Sorts keys[0..P) (P a power of two <= kMaxDict, the array holding at least
+// max(P, 1024) keys); padding up to 1024 uses the largest key value.
+template <typename K>
+__device__ void bitonic_sort(K* keys, int P) {
+  const int Q = P < 1024 ? 1024 : P;
+  for (int i = P + threadIdx.x; i < Q; i += blockDim.x) keys[i] = ~K(0);
+  __syncthreads();
+  if (Q == 1024) block_sort_regs<K, 1>(keys);
+  else if (Q == 2048) block_sort_regs<K, 2>(keys);
+  else if (Q == 4096) block_sort_regs<K, 4>(keys);
+  else block_sort_regs<K, 8>(keys);
 }
 
 __device__ __forceinline__ int upper_bound_u32(const unsigned* a, int lo, int hi, unsigned v) {
