@@ -148,6 +148,41 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+BLOCK_KERNEL_SOURCES = ("paper_2609_00205_gb300/csrc/bm_block.cuh", "paper_2609_00205_gb300/csrc/bm_common.cuh")
+
+
+def kernel_source_digest():
+    """sha256 over the sources of the In-cache Block kernel (staleness check of
+    the DRAM counters recorded under profiles/)."""
+    import hashlib
+    h = hashlib.sha256()
+    for rel in BLOCK_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def _profiled_traffic():
+    """DRAM bytes per launch of the block kernel recorded by ncu (summary in
+    profiles/), or None when absent or taken on other kernel sources."""
+    prof = os.path.join(ROOT, "profiles", "block_fwd_grf513.md")
+    if not os.path.exists(prof):
+        return None
+    vals = {}
+    with open(prof) as f:
+        for line in f:
+            if ":" in line and line.lstrip("- ").split(":")[0].strip() in ("traffic_bytes_per_launch",
+                                                                          "kernel_source_sha256"):
+                k, v = line.lstrip("- ").split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256") != kernel_source_digest():
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def cpu_baseline(u_np, edge):
     import oracle
 
@@ -324,14 +359,7 @@ def main():
     g_vals = nblocks * 5 ** 3                          # block-coarse values handed to the global levels
     alg_bytes = nbytes + 2 * nblocks * per_block + 4 * g_vals
     achieved = alg_bytes / (k_ms * 1e-3) / 1e9
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "incache_decompose_grf513.json")
-    if os.path.exists(prof):
-        try:
-            with open(prof) as f:
-                traffic = json.load(f).get("traffic_bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = _profiled_traffic()
     stage_avg = {k: statistics.mean(v) for k, v in stage_ms.items()}
 
     if rank == 0:
