@@ -219,7 +219,7 @@ bm_status upload_tables(PlanDev& P) {
     if (bytes) std::memcpy(img.data() + off, src, bytes);
     return off;
   };
-  struct Offs { size_t cidx, jlo, jhi, wl, wr, cb, isc, f0, band, tm, tib, tsup, proj; };
+  struct Offs { size_t cidx, jlo, jhi, wl, wr, cb, isc, proj; };
   std::vector<Offs> offs;
   for (auto& L3 : P.h.glev)
     for (auto& D : L3) {
@@ -228,8 +228,7 @@ bm_status upload_tables(PlanDev& P) {
         for (size_t i = 0; i < v.size(); ++i) o[i] = (T)v[i];
         return o;
       };
-      std::vector<T> wl = cvt(D.wl), wr = cvt(D.wr), band = cvt(D.band), tm = cvt(D.tm), tib = cvt(D.tib),
-                     tsup = cvt(D.tsup), proj = cvt(D.P);
+      std::vector<T> wl = cvt(D.wl), wr = cvt(D.wr), proj = cvt(D.P);
       Offs o;
       o.cidx = put(D.cidx.data(), D.cidx.size() * 4);
       o.jlo = put(D.jlo.data(), D.jlo.size() * 4);
@@ -238,11 +237,6 @@ bm_status upload_tables(PlanDev& P) {
       o.wr = put(wr.data(), wr.size() * sizeof(T));
       o.cb = put(D.cb.data(), D.cb.size() * 4);
       o.isc = put(D.isc.data(), D.isc.size());
-      o.f0 = put(D.f0.data(), D.f0.size() * 4);
-      o.band = put(band.data(), band.size() * sizeof(T));
-      o.tm = put(tm.data(), tm.size() * sizeof(T));
-      o.tib = put(tib.data(), tib.size() * sizeof(T));
-      o.tsup = put(tsup.data(), tsup.size() * sizeof(T));
       o.proj = put(proj.data(), proj.size() * sizeof(T));
       offs.push_back(o);
     }
@@ -269,11 +263,6 @@ bm_status upload_tables(PlanDev& P) {
       g.wr = reinterpret_cast<const T*>(base + o.wr);
       g.cb = reinterpret_cast<const int*>(base + o.cb);
       g.isc = reinterpret_cast<const uint8_t*>(base + o.isc);
-      g.f0 = reinterpret_cast<const int*>(base + o.f0);
-      g.band = reinterpret_cast<const T*>(base + o.band);
-      g.tm = reinterpret_cast<const T*>(base + o.tm);
-      g.tib = reinterpret_cast<const T*>(base + o.tib);
-      g.tsup = reinterpret_cast<const T*>(base + o.tsup);
       g.P = reinterpret_cast<const T*>(base + o.proj);
     }
     L.sym_off = P.h.sym_off[l];

@@ -142,7 +142,9 @@ __device__ __forceinline__ void level_fwd(const T* __restrict__ X, T* __restrict
     const int cc_before = ((i0 + 1) / 2) * C + (f0 ? 0 : (i1 + 1) / 2);
     const int base = lvl_off + L * N - cc_before * C;
     if (MODE == 0) {
-      bool any_esc = false;
+      // symbol code + radius for |code| < radius, else the escape symbol 0
+      // and the code itself at the same position of the escape array (a
+      // predicated store: no memory traffic unless the symbol escapes)
 #pragma unroll
       for (int k = 0; k < N; ++k) {
         if ((k & 1) || !cc) {
@@ -151,19 +153,9 @@ __device__ __forceinline__ void level_fwd(const T* __restrict__ X, T* __restrict
           const unsigned u = (unsigned)(code + radius);
           const bool in = (u - 1u) < (unsigned)(2 * radius - 1);
           const unsigned sv = in ? u : 0u;
-          any_esc |= !in;
           stage[pos] = (uint16_t)sv;
+          if (!in) esc_blk[pos] = code;
           if (BM_FWD_HIST) hist_count(hloc, hglob, radius, sv, centre);
-        }
-      }
-      if (any_esc) {  // rare: store the codes of escaped symbols
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-          if ((k & 1) || !cc) {
-            bool dummy = false;
-            const int code = quantize(d[k], rq, dummy);
-            if ((unsigned)(code + radius) - 1u >= (unsigned)(2 * radius - 1)) esc_blk[base + (cc ? k / 2 : k)] = code;
-          }
         }
       }
     } else {

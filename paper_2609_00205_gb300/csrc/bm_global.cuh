@@ -1,10 +1,10 @@
 // Global MGARD levels on the gathered block-coarse grid G (Sec. III-B hybrid
 // hierarchy: L local levels, then M whole-grid levels).  Each level is a
-// handful of whole-grid passes: coefficients, three restriction+solve passes
-// (one per dimension, shrinking it) and the coarse correction; the inverse
-// runs them backwards.  Node coordinates are physical (block offset plus the
-// node's in-block coordinate), so every per-dimension operator comes from a
-// host-built table.
+// handful of whole-grid passes: coefficients, three restriction passes (one
+// per dimension, shrinking it, each the dense projection M_c^-1 I^T M_f of
+// that dimension) and the coarse correction; the inverse runs them backwards.
+// Node coordinates are physical (block offset plus the node's in-block
+// coordinate), so every per-dimension operator comes from a host-built table.
 #pragma once
 
 #include "bm_common.cuh"
@@ -21,11 +21,6 @@ struct GDim {
   const T* wr;
   const int* cb;        // [n] number of coarse indices below i
   const uint8_t* isc;   // [n] 1 at coarse nodes
-  const int* f0;        // [c] first fine column of row J of I^T M_f
-  const T* band;        // [5c] that row's entries f0 .. f0+4 (zero past n)
-  const T* tm;          // [c] Thomas multipliers of M_c
-  const T* tib;         // [c] inverse pivots
-  const T* tsup;        // [c] super-diagonal
   const T* P;           // [c x n] row-major projection M_c^{-1} I^T M_f
 };
 
@@ -116,73 +111,6 @@ __global__ void __launch_bounds__(256) gl_fwd_detail(GLevel<T> L, const T* __res
     for (int i = threadIdx.x; i < (int)dict; i += blockDim.x) {
       const unsigned v = hloc[i];
       if (v) atomicAdd(hist + i, v);
-    }
-  }
-}
-
-// Restriction + tridiagonal solve along dimension DIM, one thread per line.
-//   DIM 2: in (n0,n1,n2) -> out (n0,n1,c2)
-//   DIM 1: in (n0,n1,c2) -> out (n0,c1,c2)
-//   DIM 0: in (n0,c1,c2) -> out (c0,c1,c2); FINAL = 1: out = U|C + z (forward),
-//          FINAL = 2: out = out - z (inverse, out holds the coarse values)
-template <typename T, int DIM, int FINAL>
-__global__ void gl_restrict(GLevel<T> L, const T* __restrict__ in, T* out, const T* __restrict__ U) {
-  const GDim<T>& D = L.d[DIM];
-  const int n0 = L.d[0].n, n1 = L.d[1].n, n2 = L.d[2].n;
-  const int c1 = L.d[1].c, c2 = L.d[2].c;
-  int64_t nlines;
-  if (DIM == 2) nlines = (int64_t)n0 * n1;
-  else if (DIM == 1) nlines = (int64_t)n0 * c2;
-  else nlines = (int64_t)c1 * c2;
-  for (int64_t line = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; line < nlines;
-       line += (int64_t)gridDim.x * blockDim.x) {
-    int64_t ibase, istride, obase, ostride;
-    int x, y;  // the two fixed indices of the line
-    if (DIM == 2) {
-      ibase = line * n2; istride = 1; obase = line * c2; ostride = 1; x = 0; y = 0;
-    } else if (DIM == 1) {
-      const int64_t i0 = line / c2, j2 = line % c2;
-      ibase = i0 * n1 * c2 + j2; istride = c2; obase = i0 * (int64_t)c1 * c2 + j2; ostride = c2; x = 0; y = 0;
-    } else {
-      const int j1 = (int)(line / c2), j2 = (int)(line % c2);
-      ibase = (int64_t)j1 * c2 + j2; istride = (int64_t)c1 * c2; obase = ibase; ostride = istride; x = j1; y = j2;
-    }
-    const int n = D.n, c = D.c;
-    // band products r_J of the whole line first: independent loads that can
-    // be in flight together
-#pragma unroll 4
-    for (int J = 0; J < c; ++J) {
-      const int f = D.f0[J];
-      T r = T(0);
-#pragma unroll
-      for (int m = 0; m < 5; ++m) {
-        const int col = f + m;
-        if (col < n) r = fma(D.band[5 * J + m], in[ibase + col * istride], r);
-      }
-      out[obase + J * ostride] = r;
-    }
-    // forward sweep: y_J = r_J - tm_J y_{J-1}, in place
-    T yprev = out[obase];
-    for (int J = 1; J < c; ++J) {
-      const T yv = fma(-D.tm[J], yprev, out[obase + J * ostride]);
-      out[obase + J * ostride] = yv;
-      yprev = yv;
-    }
-    // backward sweep
-    T znext = T(0);
-    for (int J = c - 1; J >= 0; --J) {
-      const T yv = out[obase + J * ostride];
-      const T z = (J == c - 1 ? yv : fma(-D.tsup[J], znext, yv)) * D.tib[J];
-      znext = z;
-      if (FINAL == 1) {
-        const int64_t u = ((int64_t)L.d[0].cidx[J] * n1 + L.d[1].cidx[x]) * n2 + L.d[2].cidx[y];
-        out[obase + J * ostride] = U[u] + z;
-      } else if (FINAL == 2) {
-        // inverse: the coarse values live in U (compact); out aliases nothing
-        out[obase + J * ostride] = U[obase + J * ostride] - z;
-      } else {
-        out[obase + J * ostride] = z;
-      }
     }
   }
 }
