@@ -54,15 +54,29 @@ struct StageTimer {
     s = st;
     on = g_timing.load() != 0;
   }
+  std::vector<std::pair<int, cudaEvent_t>> pool;  // (device, event), reused across calls
+  cudaEvent_t take() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    for (size_t i = pool.size(); i-- > 0;)
+      if (pool[i].first == dev) {
+        cudaEvent_t e = pool[i].second;
+        pool.erase(pool.begin() + (long)i);
+        return e;
+      }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
   void clear() {
-    for (auto& r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    for (auto& r : recs) { pool.push_back({dev, r.a}); pool.push_back({dev, r.b}); }
     recs.clear();
   }
   int open(const char* name, cudaStream_t st) {
     if (!on) return -1;
-    Rec r{name, nullptr, nullptr, st ? st : s};
-    cudaEventCreate(&r.a);
-    cudaEventCreate(&r.b);
+    Rec r{name, take(), take(), st ? st : s};
     cudaEventRecord(r.a, r.s);
     recs.push_back(r);
     return (int)recs.size() - 1;
@@ -334,6 +348,20 @@ GSizes gsizes(const PlanHost& h) {
   return g;
 }
 
+// cudaFuncAttributeMaxDynamicSharedMemorySize set once per device for a kernel.
+std::atomic<unsigned> g_cb_attr{0}, g_dt_attr{0};
+template <class F>
+cudaError_t set_smem_once(F* fn, int bytes, std::atomic<unsigned>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned bit = 1u << (dev & 31);
+  if (done.load() & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.fetch_or(bit);
+  return e;
+}
+
 int grid_for(int64_t work, int threads, int per_sm = 8) {
   int64_t g = (work + threads - 1) / threads;
   const int64_t cap = (int64_t)num_sms() * per_sm;
@@ -353,43 +381,11 @@ __device__ __forceinline__ void maxabs_acc(T x, T& m, bool& bad) {
   else m = v > m ? v : m;
 }
 
-// max |u| (NaN ignored, non-finite values flagged), 16-byte loads over the
-// aligned bulk of the field.
-template <typename T>
-__global__ void maxabs_kernel(const T* __restrict__ u, int64_t n, Scalars* sc) {
-  T m = T(0);
-  bool bad = false;
-  constexpr int V = 16 / sizeof(T);
-  const int64_t head = (int64_t)((16 - (reinterpret_cast<uintptr_t>(u) & 15)) & 15) / (int64_t)sizeof(T);
-  const int64_t h = head < n ? head : n;
-  const int64_t nv = (n - h) / V;
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
-  const uint4* pv = reinterpret_cast<const uint4*>(u + h);
-  for (int64_t i = tid; i < nv; i += nth) {
-    const uint4 q = __ldg(pv + i);
-    const T* t = reinterpret_cast<const T*>(&q);
-#pragma unroll
-    for (int j = 0; j < V; ++j) maxabs_acc(t[j], m, bad);
-  }
-  for (int64_t i = tid; i < h; i += nth) maxabs_acc(u[i], m, bad);
-  for (int64_t i = h + nv * V + tid; i < n; i += nth) maxabs_acc(u[i], m, bad);
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    const T y = __shfl_xor_sync(0xffffffffu, m, o);
-    m = y > m ? y : m;
-  }
-  bad = __any_sync(0xffffffffu, bad);
-  if ((threadIdx.x & 31) == 0) {
-    if (sizeof(T) == 4) atomicMax(&sc->maxabs_bits, (unsigned long long)__float_as_uint((float)m));
-    else atomicMax(&sc->maxabs_bits, (unsigned long long)__double_as_longlong((double)m));
-    if (bad) atomicOr(&sc->status, ST_RAW);
-  }
-}
-
 // Quantiser widths of every (tier, level), in IEEE double arithmetic without
 // contraction: tau' = tau - margin, margin = kappa eps (N+1) max|u|;
 // q_level = 2 tau'/((N+1) A_level), q_coarsest = 2 tau_g'/(N+1).
 struct QtabArgs {
+  int enabled;
   const double* tiers;  // relative or absolute, ascending
   int ntiers, rel, K, M;
   double A[24];
@@ -402,8 +398,7 @@ struct QtabArgs {
   Scalars* sc;
 };
 
-__global__ void qtab_kernel(QtabArgs a) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ void qtab_compute(const QtabArgs& a) {
   const double max_abs = a.f64 ? __longlong_as_double((long long)a.sc->maxabs_bits)
                                : (double)__uint_as_float((unsigned)a.sc->maxabs_bits);
   const int N = a.K + a.M;
@@ -434,6 +429,50 @@ __global__ void qtab_kernel(QtabArgs a) {
   if (raw) atomicOr(&a.sc->status, ST_RAW);
 }
 
+// max |u| (NaN ignored, non-finite values flagged), 16-byte loads over the
+// aligned bulk of the field.  The last CTA to finish computes the quantiser
+// table from it (qtab_compute) when qa.enabled.
+template <typename T>
+__global__ void __launch_bounds__(256) maxabs_kernel(const T* __restrict__ u, int64_t n, Scalars* sc, QtabArgs qa) {
+  __shared__ bool s_last;
+  T m = T(0);
+  bool bad = false;
+  constexpr int V = 16 / sizeof(T);
+  const int64_t head = (int64_t)((16 - (reinterpret_cast<uintptr_t>(u) & 15)) & 15) / (int64_t)sizeof(T);
+  const int64_t h = head < n ? head : n;
+  const int64_t nv = (n - h) / V;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+  const uint4* pv = reinterpret_cast<const uint4*>(u + h);
+  for (int64_t i = tid; i < nv; i += nth) {
+    const uint4 q = __ldg(pv + i);
+    const T* t = reinterpret_cast<const T*>(&q);
+#pragma unroll
+    for (int j = 0; j < V; ++j) maxabs_acc(t[j], m, bad);
+  }
+  for (int64_t i = tid; i < h; i += nth) maxabs_acc(u[i], m, bad);
+  for (int64_t i = h + nv * V + tid; i < n; i += nth) maxabs_acc(u[i], m, bad);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const T y = __shfl_xor_sync(0xffffffffu, m, o);
+    m = y > m ? y : m;
+  }
+  bad = __any_sync(0xffffffffu, bad);
+  if ((threadIdx.x & 31) == 0) {
+    if (sizeof(T) == 4) atomicMax(&sc->maxabs_bits, (unsigned long long)__float_as_uint((float)m));
+    else atomicMax(&sc->maxabs_bits, (unsigned long long)__double_as_longlong((double)m));
+    if (bad) atomicOr(&sc->status, ST_RAW);
+  }
+  if (!qa.enabled) return;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&sc->maxabs_done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    __threadfence();
+    qtab_compute(qa);
+  }
+}
+
 struct HeaderArgs {
   uint8_t* out;
   int f64, B, K, M, chunk, radius, ntiers, m, rel;
@@ -441,6 +480,7 @@ struct HeaderArgs {
   int nb[3];
   double tol;
   unsigned long long n_symbols, n_chunks, off_tiers, off_qtab, off_btier, off_chunks, off_splits, off_codebook;
+  unsigned long long raw_total, capacity;
   Scalars* sc;
 };
 
@@ -452,6 +492,7 @@ __device__ __forceinline__ void put(uint8_t* p, size_t off, V v) { *reinterpret_
 __global__ void header_kernel(HeaderArgs a) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   Scalars* sc = a.sc;
+  encode_finish(a.raw_total, a.capacity, sc);
   if (sc->status & ST_RAW) return;
   uint8_t* o = a.out;
   put<uint32_t>(o, 0, kMagic);
@@ -515,6 +556,47 @@ __global__ void raw_header_kernel(uint8_t* o, int f64, int B, int64_t s0, int64_
   put<double>(o, 88, tol);
   put<uint64_t>(o, 168, (unsigned long long)kHeaderBytes);
   put<uint64_t>(o, 184, total);
+}
+
+// The raw fallback decided on the device: when the status says raw, the
+// header of a raw stream and a copy of the field (16-byte vectors when both
+// ends allow it); otherwise nothing.
+template <typename T>
+__global__ void __launch_bounds__(256) raw_stream_kernel(uint8_t* o, const T* __restrict__ field, int64_t nel, int f64,
+                                                         int B, int64_t s0, int64_t s1, int64_t s2, int rel, double tol,
+                                                         unsigned long long total, Scalars* sc) {
+  if (!(sc->status & ST_RAW)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int i = 0; i < kHeaderBytes; ++i) o[i] = 0;
+    put<uint32_t>(o, 0, kMagic);
+    put<uint16_t>(o, 4, 1);
+    put<uint16_t>(o, 6, (uint16_t)(1 | (f64 ? 2 : 0)));
+    put<int32_t>(o, 8, 3);
+    put<int32_t>(o, 12, B);
+    put<int64_t>(o, 16, s0);
+    put<int64_t>(o, 24, s1);
+    put<int64_t>(o, 32, s2);
+    put<int32_t>(o, 76, rel);
+    const double max_abs = f64 ? __longlong_as_double((long long)sc->maxabs_bits)
+                               : (double)__uint_as_float((unsigned)sc->maxabs_bits);
+    put<double>(o, 80, max_abs);
+    put<double>(o, 88, tol);
+    put<uint64_t>(o, 168, (unsigned long long)kHeaderBytes);
+    put<uint64_t>(o, 184, total);
+  }
+  uint8_t* dst = o + kHeaderBytes;
+  const unsigned long long bytes = (unsigned long long)nel * sizeof(T);
+  const unsigned long long tid = blockIdx.x * 256ull + threadIdx.x, nth = gridDim.x * 256ull;
+  const uint8_t* src = reinterpret_cast<const uint8_t*>(field);
+  if (((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15) == 0) {
+    const unsigned long long nv = bytes / 16;
+    for (unsigned long long i = tid; i < nv; i += nth)
+      reinterpret_cast<uint4*>(dst)[i] = __ldg(reinterpret_cast<const uint4*>(src) + i);
+    for (unsigned long long i = nv * 16 + tid; i < bytes; i += nth) dst[i] = src[i];
+  } else {
+    const unsigned long long nv = bytes / sizeof(T);
+    for (unsigned long long i = tid; i < nv; i += nth) reinterpret_cast<T*>(dst)[i] = field[i];
+  }
 }
 
 // Decoder-side scan: chunk word counts -> word offsets; checks the total.
@@ -775,24 +857,26 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   const int64_t nel = nel3(shape);
   const unsigned long long raw_total = kHeaderBytes + (unsigned long long)nel * sizeof(T);
   if (cap < raw_total) return fail(BM_ERR_CAPACITY, "out_capacity below bm_compress_bound()");
-  // tiers: distinct min(tol, roi_i) values, ascending
-  std::vector<double> bt((size_t)h.nblocks, tol);
-  if (roi)
+  // tiers: distinct min(tol, roi_i) values, ascending (one tier without a ROI map)
+  std::vector<double> tiers{tol};
+  std::vector<uint8_t> btier;
+  if (roi) {
+    std::vector<double> bt((size_t)h.nblocks, tol);
     for (int64_t b = 0; b < h.nblocks; ++b) {
       if (!(roi[b] > 0.0) || !std::isfinite(roi[b])) return fail(BM_ERR_ARG, "ROI tolerances must be finite and > 0");
       bt[(size_t)b] = std::min(tol, roi[b]);
     }
-  std::vector<double> tiers = bt;
-  std::sort(tiers.begin(), tiers.end());
-  tiers.erase(std::unique(tiers.begin(), tiers.end()), tiers.end());
-  if (tiers.size() > 255) return fail(BM_ERR_ARG, "more than 255 distinct tolerances");
-  const int ntiers = (int)tiers.size();
-  std::vector<uint8_t> btier;
-  if (ntiers > 1) {
-    btier.resize((size_t)h.nblocks);
-    for (int64_t b = 0; b < h.nblocks; ++b)
-      btier[(size_t)b] = (uint8_t)(std::lower_bound(tiers.begin(), tiers.end(), bt[(size_t)b]) - tiers.begin());
+    tiers = bt;
+    std::sort(tiers.begin(), tiers.end());
+    tiers.erase(std::unique(tiers.begin(), tiers.end()), tiers.end());
+    if (tiers.size() > 255) return fail(BM_ERR_ARG, "more than 255 distinct tolerances");
+    if (tiers.size() > 1) {
+      btier.resize((size_t)h.nblocks);
+      for (int64_t b = 0; b < h.nblocks; ++b)
+        btier[(size_t)b] = (uint8_t)(std::lower_bound(tiers.begin(), tiers.end(), bt[(size_t)b]) - tiers.begin());
+    }
   }
+  const int ntiers = (int)tiers.size();
   const StreamLayout L = layout(h, ntiers, prm.chunk);
   const int dict = 2 * prm.radius;
 
@@ -807,7 +891,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   probe.take<Scalars>(1); probe.take<unsigned>(dict); probe.take<uint8_t>(dict); probe.take<unsigned>(dict);
   probe.take<double>(L.nq); probe.take<T>(L.nq); probe.take<double>(ntiers); probe.take<uint8_t>(h.nblocks);
   probe.take<uint16_t>((size_t)h.n_coeffs); probe.take<int32_t>((size_t)h.n_coeffs);
-  probe.take<unsigned>(L.nch); probe.take<unsigned char>(256 + 16ull * L.nch); probe.take<int32_t>((size_t)h.n_coeffs);
+  probe.take<unsigned char>(256 + 16ull * L.nch);
   const size_t need = probe.off + decompose_scratch(h, sizeof(T)) + 4096;
   const size_t hneed = sizeof(Scalars) + 8 * ntiers + (size_t)h.nblocks + 4096;
   Workspace* ws = nullptr;
@@ -845,11 +929,11 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
       if (ntiers > 1) BM_CUDA(cudaMemcpyAsync(out + L.off_btier, dbt, (size_t)h.nblocks, cudaMemcpyDeviceToDevice, s));
     }
   }
+  const int mgrid = (int)std::min<int64_t>((int64_t)num_sms() * 8, std::max<int64_t>(1, (nel + 4095) / 4096));
   {
     Stage st("maxabs");
-    maxabs_kernel<T><<<num_sms() * 8, 256, 0, s>>>(field, nel, sc);
-    BM_LAUNCHED();
     QtabArgs qa{};
+    qa.enabled = prefix_fits;
     qa.tiers = dtiers; qa.ntiers = ntiers; qa.rel = rel; qa.K = h.K; qa.M = h.M;
     for (size_t i = 0; i < h.A.size() && i < 24; ++i) qa.A[i] = h.A[i];
     qa.kappa = 8.0;
@@ -857,15 +941,13 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     qa.qd = qd; qa.rq = rq; qa.f64 = f64;
     qa.out = prefix_fits ? out : nullptr;
     qa.off_tiers = L.off_tiers; qa.off_qtab = L.off_qtab; qa.sc = sc;
-    qtab_kernel<<<1, 32, 0, s>>>(qa);
+    maxabs_kernel<T><<<mgrid, 256, 0, s>>>(field, nel, sc, qa);
     BM_LAUNCHED();
     BM_CUDA(cudaGetLastError());
   }
   if (!prefix_fits) {  // not even the tables fit: the raw copy is the stream
-    BM_CUDA(cudaMemsetAsync(sc, 0, sizeof(Scalars), s));
-    maxabs_kernel<T><<<num_sms() * 8, 256, 0, s>>>(field, nel, sc);
     raw_header_kernel<<<1, 32, 0, s>>>(out, f64, h.B, shape[0], shape[1], shape[2], rel, tol, raw_total, sc);
-    g_launches.fetch_add(2);
+    BM_LAUNCHED();
     BM_CUDA(cudaMemcpyAsync(out + kHeaderBytes, field, (size_t)nel * sizeof(T), cudaMemcpyDeviceToDevice, s));
     BM_CUDA(cudaStreamSynchronize(s));
     *out_bytes = (size_t)raw_total;
@@ -905,7 +987,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     Stage st("huffman_codebook");
     CodebookArgs ca{hist, dict, lens, codes, prefix_fits ? out : nullptr, L.off_codebook, cap, sc, 1, L.nch,
                     raw_total};
-    BM_CUDA(cudaFuncSetAttribute(codebook_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CbSmem)));
+    BM_CUDA(set_smem_once(codebook_kernel, (int)sizeof(CbSmem), g_cb_attr));
     codebook_kernel<<<1, kCbThreads, sizeof(CbSmem), s>>>(ca);
     BM_LAUNCHED();
     BM_CUDA(cudaGetLastError());
@@ -921,9 +1003,12 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     ea.splits = reinterpret_cast<uint16_t*>(out + L.off_splits);
     ea.out = out; ea.capacity = cap; ea.sc = sc;
     encode_fused_kernel<8><<<grid_for((int64_t)L.nch * 32, 256, 4), 256, 0, s>>>(ea);
-    encode_finish_kernel<<<1, 32, 0, s>>>(raw_total, cap, sc);
-    g_launches.fetch_add(2);
+    BM_LAUNCHED();
+  }
+  {
+    Stage st("finish");
     HeaderArgs ha{};
+    ha.raw_total = raw_total; ha.capacity = cap;
     ha.out = out; ha.f64 = f64; ha.B = h.B; ha.K = h.K; ha.M = h.M; ha.chunk = prm.chunk; ha.radius = prm.radius;
     ha.ntiers = ntiers; ha.m = h.m; ha.rel = rel;
     for (int d = 0; d < 3; ++d) { ha.shape[d] = shape[d]; ha.nb[d] = h.nb[d]; }
@@ -931,23 +1016,17 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     ha.off_tiers = L.off_tiers; ha.off_qtab = L.off_qtab; ha.off_btier = ntiers > 1 ? L.off_btier : L.off_chunks;
     ha.off_chunks = L.off_chunks; ha.off_splits = L.off_splits; ha.off_codebook = L.off_codebook; ha.sc = sc;
     header_kernel<<<1, 32, 0, s>>>(ha);
-    BM_LAUNCHED();
+    // a raw fallback is written on the device in the same pass (no second host round trip)
+    raw_stream_kernel<T><<<mgrid, 256, 0, s>>>(out, field, nel, f64, h.B, shape[0], shape[1], shape[2], rel, tol,
+                                               raw_total, sc);
+    g_launches.fetch_add(2);
     BM_CUDA(cudaGetLastError());
     BM_CUDA(cudaMemcpyAsync(hsc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
   }
   BM_CUDA(cudaStreamSynchronize(s));
   if (hsc->status & ST_TIMEOUT) return fail(BM_ERR_CUDA, "encoder look-back wait timed out");
   if (hsc->status & ST_CORRUPT) return fail(BM_ERR_CUDA, "internal error: escape count differs from the histogram");
-  if (hsc->status & ST_RAW) {
-    Stage st("raw_copy");
-    raw_header_kernel<<<1, 32, 0, s>>>(out, f64, h.B, shape[0], shape[1], shape[2], rel, tol, raw_total, sc);
-    BM_LAUNCHED();
-    BM_CUDA(cudaMemcpyAsync(out + kHeaderBytes, field, (size_t)nel * sizeof(T), cudaMemcpyDeviceToDevice, s));
-    BM_CUDA(cudaStreamSynchronize(s));
-    *out_bytes = (size_t)raw_total;
-  } else {
-    *out_bytes = (size_t)hsc->total;
-  }
+  *out_bytes = (hsc->status & ST_RAW) ? (size_t)raw_total : (size_t)hsc->total;
   return BM_OK;
 }
 
@@ -1047,7 +1126,7 @@ bm_status decode_symbols(const uint8_t* in, const Header& H, Carver& cv, uint16_
     if (H.n_outliers)
       word_scan_kernel<<<1, kCbThreads, 0, s>>>(reinterpret_cast<const unsigned*>(in + H.off_chunk_esc), H.n_chunks,
                                                 esc_off, H.n_outliers, sc);
-    BM_CUDA(cudaFuncSetAttribute(decode_tables_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DtSmem)));
+    BM_CUDA(set_smem_once(decode_tables_kernel, (int)sizeof(DtSmem), g_dt_attr));
     decode_tables_kernel<<<1, kCbThreads, sizeof(DtSmem), s>>>(in + H.off_codebook, H.codebook_bytes, H.n_runs,
                                                                2 * H.radius, dt, sc);
     g_launches.fetch_add(H.n_outliers ? 3 : 2);
@@ -1346,7 +1425,7 @@ bm_status bm_huffman_encode(const uint16_t* d_symbols, uint64_t n, int dict_size
   {
     Stage st("huffman_codebook");
     CodebookArgs ca{hist, dict_size, lens, codes, out, off_cb, out_capacity, sc, 0, nch, ~0ull};
-    BM_CUDA(cudaFuncSetAttribute(codebook_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CbSmem)));
+    BM_CUDA(set_smem_once(codebook_kernel, (int)sizeof(CbSmem), g_cb_attr));
     codebook_kernel<<<1, kCbThreads, sizeof(CbSmem), s>>>(ca);
     BM_LAUNCHED();
   }
@@ -1510,7 +1589,7 @@ extern "C" bm_status bm_huffman_encode_noalloc(const uint16_t* d_symbols, uint64
   BM_CUDA(cudaMemsetAsync(out, 0, off_cb, s));
   hist_kernel<<<grid_for((int64_t)n, 256, 4), 256, 4 * dict_size, s>>>(d_symbols, n, dict_size, hist, sc);
   CodebookArgs ca{hist, dict_size, lens, codes, out, off_cb, out_capacity, sc, 0, nch, ~0ull};
-  BM_CUDA(cudaFuncSetAttribute(codebook_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(CbSmem)));
+  BM_CUDA(set_smem_once(codebook_kernel, (int)sizeof(CbSmem), g_cb_attr));
   codebook_kernel<<<1, kCbThreads, sizeof(CbSmem), s>>>(ca);
   FusedEncodeArgs ea{};
   ea.sym = d_symbols; ea.esc = nullptr; ea.n = n; ea.chunk = chunk_symbols; ea.lens = lens; ea.codes = codes;

@@ -1,6 +1,8 @@
 // Launch helpers of the In-cache Block kernels for one (dtype, block size).
 #pragma once
 
+#include <atomic>
+
 #include "bm_block.cuh"
 #include "bm_internal.h"
 
@@ -11,12 +13,20 @@ cudaError_t launch_one(int dir, const BlockArgs<T>& a, cudaStream_t s, int nsm, 
   using Cfg = BlockCfg<T, B, K>;
   const void* fn = dir == 0 ? (const void*)block_fwd_kernel<T, B, K, MODE> : (const void*)block_inv_kernel<T, B, K, MODE>;
   const size_t smem = dir == 0 ? Cfg::fwd_smem : Cfg::inv_smem(MODE);
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // shared-memory attribute and occupancy, once per device and direction
+  static std::atomic<int> cached[2][64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, Cfg::NT, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int per_sm = dev < 64 ? cached[dir][dev].load() : 0;
+  if (per_sm <= 0) {
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, Cfg::NT, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (dev < 64) cached[dir][dev].store(per_sm);
+  }
   int64_t grid = (int64_t)per_sm * nsm;
   if (max_grid > 0 && grid > max_grid) grid = max_grid;
   if (grid > a.nblocks) grid = a.nblocks;

@@ -41,6 +41,8 @@ struct Scalars {
   double margin;
   unsigned long long max_len;
   unsigned long long esc_seen;     // escapes the encoder met (must equal n_outliers)
+  unsigned maxabs_done;            // CTAs of the max|u| pass that have finished
+  unsigned pad1;
 };
 
 // ---------------------------------------------------------------------------

@@ -832,14 +832,16 @@ __global__ void __launch_bounds__(WARPS * 32, 4) encode_fused_kernel(FusedEncode
   }
 }
 
-// After the fused encoder: stream length and the raw decision.
-__global__ void encode_finish_kernel(unsigned long long raw_total, unsigned long long capacity, Scalars* sc) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// After the fused encoder (one thread): stream length and the raw decision.
+__device__ __forceinline__ void encode_finish(unsigned long long raw_total, unsigned long long capacity, Scalars* sc) {
   if (sc->skip) return;  // already raw
   const unsigned long long total = sc->off_bits + pad8(4ull * sc->n_words);
   sc->total = total;
   if (sc->esc_seen != sc->n_outliers) atomicOr(&sc->status, ST_CORRUPT | ST_RAW);
   if (total >= raw_total || total > capacity || (sc->status & ST_OVERFLOW)) atomicOr(&sc->status, ST_RAW);
+}
+__global__ void encode_finish_kernel(unsigned long long raw_total, unsigned long long capacity, Scalars* sc) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) encode_finish(raw_total, capacity, sc);
 }
 
 // ---------------------------------------------------------------------------
