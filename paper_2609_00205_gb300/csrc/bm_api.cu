@@ -1002,7 +1002,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     ea.chunk_words = reinterpret_cast<unsigned*>(out + L.off_chunks);
     ea.splits = reinterpret_cast<uint16_t*>(out + L.off_splits);
     ea.out = out; ea.capacity = cap; ea.sc = sc;
-    encode_fused_kernel<8><<<grid_for((int64_t)L.nch * 32, 256, 4), 256, 0, s>>>(ea);
+    encode_fused_kernel<8, false><<<grid_for((int64_t)L.nch * 32, 256, 4), 256, 0, s>>>(ea);
     BM_LAUNCHED();
   }
   {
@@ -1438,7 +1438,7 @@ bm_status bm_huffman_encode(const uint16_t* d_symbols, uint64_t n, int dict_size
     ea.chunk_words = reinterpret_cast<unsigned*>(out); ea.out = out;
     ea.splits = reinterpret_cast<uint16_t*>(out + off_sp);
     ea.capacity = out_capacity; ea.sc = sc;
-    encode_fused_kernel<8><<<grid_for((int64_t)nch * 32, 256, 4), 256, 0, s>>>(ea);
+    encode_fused_kernel<8, true><<<grid_for((int64_t)nch * 32, 256, 4), 256, 0, s>>>(ea);
     encode_finish_kernel<<<1, 32, 0, s>>>(~0ull, out_capacity, sc);
     zero_tail_kernel<<<1, 32, 0, s>>>(out, sc);
     g_launches.fetch_add(3);
@@ -1598,7 +1598,7 @@ extern "C" bm_status bm_huffman_encode_noalloc(const uint16_t* d_symbols, uint64
   ea.chunk_words = reinterpret_cast<unsigned*>(out); ea.out = out;
   ea.splits = reinterpret_cast<uint16_t*>(out + off_sp);
   ea.capacity = out_capacity; ea.sc = sc;
-  encode_fused_kernel<8><<<grid_for((int64_t)nch * 32, 256, 4), 256, 0, s>>>(ea);
+  encode_fused_kernel<8, true><<<grid_for((int64_t)nch * 32, 256, 4), 256, 0, s>>>(ea);
   encode_finish_kernel<<<1, 32, 0, s>>>(~0ull, out_capacity, sc);
   zero_tail_kernel<<<1, 32, 0, s>>>(out, sc);
   g_launches.fetch_add(6);

@@ -509,14 +509,8 @@ __global__ void __launch_bounds__(256) hist_range_kernel(const uint16_t* __restr
 // ---------------------------------------------------------------------------
 // Single-pass encoder (decoupled look-back, Merrill & Garland 2016)
 // ---------------------------------------------------------------------------
-// Warps take chunks in ticket order.  A warp codes its chunk's bit count from
-// the symbols it holds in registers, publishes the chunk's (words, escapes)
-// aggregate, walks back over its predecessors until one has published an
-// inclusive prefix (bounded wait), publishes its own inclusive prefix and then
-// packs its codes at the now known word offset.  Every word is written once:
-// a lane's last, partial word is handed to the next lane by a shuffle.
-// Status word of a chunk: [flag:2][words:31][escapes:31], so one load sees a
-// consistent pair (inputs hold fewer than 2^31 symbols).
+// Status word of a chunk for the look-back: [flag:2][words:31][escapes:31],
+// so one load sees a consistent pair (inputs hold fewer than 2^31 symbols).
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagIncl = 2ull << 62;
 constexpr unsigned long long kM31 = (1ull << 31) - 1;
@@ -568,7 +562,9 @@ __device__ __forceinline__ void code_of(const unsigned* codes, const uint8_t* le
 }
 
 // Bits and escape mask of a lane's vector slice (G groups held in registers).
-template <bool PACKED>
+// CLAMP: symbols may be out of the dictionary (caller-supplied) and are
+// clamped; the compressor's own symbols are in range by construction.
+template <bool PACKED, bool CLAMP>
 __device__ __forceinline__ void slice_bits(const uint4* q, int G, unsigned dmax, const unsigned* codes,
                                            const uint8_t* lens, unsigned& bits, unsigned long long& emask) {
   bits = 0;
@@ -576,7 +572,7 @@ __device__ __forceinline__ void slice_bits(const uint4* q, int G, unsigned dmax,
 #pragma unroll
   for (int i = 0; i < 8 * kEncGroups; ++i) {
     if ((i >> 3) < G) {
-      const unsigned s = min(sym_of(q, i), dmax);
+      const unsigned s = CLAMP ? min(sym_of(q, i), dmax) : sym_of(q, i);
       unsigned c, L;
       code_of<PACKED>(codes, lens, s, c, L);
       bits += L;
@@ -586,48 +582,42 @@ __device__ __forceinline__ void slice_bits(const uint4* q, int G, unsigned dmax,
 }
 
 // MSB-first packing of a lane's vector slice.  `acc` holds the pending bits in
-// its low `nb` bits (garbage above is shifted out and never stored).  A full
-// word is stored as soon as it fills, except the lane's first one when it is
-// shared with the previous lane: that one is returned in `head`.
-template <bool PACKED>
+// its low `nb` bits (garbage above is shifted out and never stored); every
+// word is stored through `wp` as soon as it fills.  The lane's first word may
+// start with the previous lane's last bits: it is stored with zeros there and
+// the previous lane ORs its bits in afterwards.
+template <bool PACKED, bool CLAMP>
 __device__ __forceinline__ void slice_pack(const uint4* q, int G, unsigned dmax, const unsigned* codes,
-                                           const uint8_t* lens, unsigned* __restrict__ words,
-                                           unsigned long long widx, unsigned nb, bool pending_head,
-                                           unsigned long long& acc_out, unsigned& nb_out,
-                                           unsigned long long& widx_out, unsigned& head) {
+                                           const uint8_t* lens, unsigned* wp, unsigned nb,
+                                           unsigned long long& acc_out, unsigned& nb_out, unsigned*& wp_out) {
   unsigned long long acc = 0;
 #pragma unroll
   for (int i = 0; i < 8 * kEncGroups; ++i) {
     if ((i >> 3) < G) {
-      const unsigned s = min(sym_of(q, i), dmax);
+      const unsigned s = CLAMP ? min(sym_of(q, i), dmax) : sym_of(q, i);
       unsigned c, L;
       code_of<PACKED>(codes, lens, s, c, L);
       acc = (acc << L) | c;
       nb += L;
       if (nb >= 32u) {
         nb -= 32u;
-        const unsigned word = (unsigned)(acc >> nb);
-        if (pending_head) head = word;
-        else words[widx] = word;
-        pending_head = false;
-        ++widx;
+        *wp++ = (unsigned)(acc >> nb);
       }
     }
   }
   acc_out = acc;
   nb_out = nb;
-  widx_out = widx;
+  wp_out = wp;
 }
 
 // Warps take chunks in ticket order.  A warp codes its chunk's bit count from
 // the symbols it holds in registers, publishes the chunk's (words, escapes)
 // aggregate, walks back over its predecessors until one has published an
 // inclusive prefix (bounded wait), publishes its own inclusive prefix and then
-// packs its codes at the now known word offset.  Every word is written once:
-// a lane's last, partial word is handed to the next lane by a shuffle.
-// Status word of a chunk: [flag:2][words:31][escapes:31], so one load sees a
-// consistent pair (inputs hold fewer than 2^31 symbols).
-template <int WARPS>
+// packs its codes at the now known word offset.  Each lane stores its full
+// words; a word shared by two lanes is completed by an atomic OR of the
+// earlier lane's last bits.
+template <int WARPS, bool CLAMP>
 __global__ void __launch_bounds__(WARPS * 32, 4) encode_fused_kernel(FusedEncodeArgs a) {
   __shared__ uint8_t lens[kMaxDict];
   __shared__ unsigned codes[kMaxDict];
@@ -673,12 +663,12 @@ __global__ void __launch_bounds__(WARPS * 32, 4) encode_fused_kernel(FusedEncode
       const uint4* p = reinterpret_cast<const uint4*>(a.sym + s0);
 #pragma unroll
       for (int g = 0; g < kEncGroups; ++g) q[g] = g < G ? __ldg(p + g) : make_uint4(0, 0, 0, 0);
-      if (packed) slice_bits<true>(q, G, dmax, codes, lens, bits, emask);
-      else slice_bits<false>(q, G, dmax, codes, lens, bits, emask);
+      if (packed) slice_bits<true, CLAMP>(q, G, dmax, codes, lens, bits, emask);
+      else slice_bits<false, CLAMP>(q, G, dmax, codes, lens, bits, emask);
       nesc = __popcll(emask);
     } else {
       for (int t = 0; t < cnt; ++t) {
-        const unsigned s = min((unsigned)a.sym[s0 + t], dmax);
+        const unsigned s = CLAMP ? min((unsigned)a.sym[s0 + t], dmax) : (unsigned)a.sym[s0 + t];
         bits += lens[s];
         nesc += s == 0;
       }
@@ -794,17 +784,20 @@ __global__ void __launch_bounds__(WARPS * 32, 4) encode_fused_kernel(FusedEncode
     const unsigned long long head_idx = pw + (bit0 >> 5);
     const bool head_partial = (bit0 & 31u) != 0;
     if (warp_vec) {
-      unsigned long long acc, widx;
-      unsigned nb, head = 0;
-      if (packed)
-        slice_pack<true>(q, G, dmax, codes, lens, words, head_idx, bit0 & 31u, head_partial, acc, nb, widx, head);
-      else
-        slice_pack<false>(q, G, dmax, codes, lens, words, head_idx, bit0 & 31u, head_partial, acc, nb, widx, head);
-      // every lane holds >= 64 bits here, so a shared word has exactly two owners
-      const unsigned tail = nb ? (unsigned)(acc << (32 - nb)) : 0u;
-      const unsigned from_prev = __shfl_up_sync(0xffffffffu, tail, 1);
-      if (head_partial) words[head_idx] = head | from_prev;
-      if (lane == 31 && nb) words[widx] = tail;
+      unsigned long long acc;
+      unsigned nb;
+      unsigned* wp;
+      if (packed) slice_pack<true, CLAMP>(q, G, dmax, codes, lens, words + head_idx, bit0 & 31u, acc, nb, wp);
+      else slice_pack<false, CLAMP>(q, G, dmax, codes, lens, words + head_idx, bit0 & 31u, acc, nb, wp);
+      // every lane holds >= 32 bits, so the word of its last bits is the next
+      // lane's first word (already stored, zeros in these bits); the last
+      // lane's last word is its own
+      __syncwarp();
+      if (nb) {
+        const unsigned tail = (unsigned)(acc << (32 - nb));
+        if (lane == 31) *wp = tail;
+        else atomicOr(wp, tail);
+      }
     } else {  // a partial chunk: zero its words, shared words are ORed
       for (unsigned w = lane; w < W; w += 32) words[pw + w] = 0u;
       __syncwarp();
@@ -812,7 +805,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) encode_fused_kernel(FusedEncode
       unsigned nb = bit0 & 31u, head = 0;
       bool pending_head = head_partial;
       for (int t = 0; t < cnt; ++t) {
-        const unsigned s = min((unsigned)a.sym[s0 + t], dmax);
+        const unsigned s = CLAMP ? min((unsigned)a.sym[s0 + t], dmax) : (unsigned)a.sym[s0 + t];
         const unsigned L = lens[s];
         acc = (acc << L) | (packed ? (codes[s] & 0x3FFFFFFu) : codes[s]);
         nb += L;
