@@ -600,43 +600,52 @@ __global__ void __launch_bounds__(256) raw_stream_kernel(uint8_t* o, const T* __
 }
 
 // Decoder-side scan: chunk word counts -> word offsets; checks the total.
+// One block; each warp owns a contiguous segment and walks it 32 counts at a
+// time (coalesced loads, shuffle scan, running carry); the warps' totals are
+// scanned across the block and a second walk writes the offsets.
 __global__ void __launch_bounds__(kCbThreads) word_scan_kernel(const unsigned* chunk_words, unsigned long long nch,
                                                               unsigned long long* word_off, unsigned long long n_words,
                                                               Scalars* sc) {
   __shared__ unsigned long long wt[32];
-  __shared__ unsigned long long carry;
-  if (threadIdx.x == 0) carry = 0;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned long long seg = (nch + nw - 1) / nw;
+  const unsigned long long a0 = min(nch, (unsigned long long)wid * seg), a1 = min(nch, a0 + seg);
+  unsigned long long tot = 0;
+  for (unsigned long long i = a0 + lane; i - lane < a1; i += 32) {  // warp-uniform trip count
+    const unsigned long long v = i < a1 ? chunk_words[i] : 0ull;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    tot += x;
+  }
+  if (lane == 0) wt[wid] = tot;
   __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (unsigned long long base = 0; base < nch; base += blockDim.x) {
-    const unsigned long long i = base + threadIdx.x;
-    const unsigned long long w = i < nch ? chunk_words[i] : 0ull;
-    unsigned long long x = w;
+  if (wid == 0) {
+    unsigned long long t = lane < nw ? wt[lane] : 0ull;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < nw) wt[lane] = t;  // inclusive
+  }
+  __syncthreads();
+  unsigned long long carry = wid ? wt[wid - 1] : 0ull;
+  for (unsigned long long i = a0 + lane; i - lane < a1; i += 32) {
+    const unsigned long long v = i < a1 ? chunk_words[i] : 0ull;
+    unsigned long long x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
-    if (lane == 31) wt[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-      unsigned long long t = wt[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
-        if (lane >= o) t += y;
-      }
-      wt[lane] = t;
-    }
-    __syncthreads();
-    if (i < nch) word_off[i] = carry + (wid ? wt[wid - 1] : 0ull) + x - w;
-    __syncthreads();
-    if (threadIdx.x == 0) carry += wt[31];
-    __syncthreads();
+    if (i < a1) word_off[i] = carry + x - v;
+    carry += __shfl_sync(0xffffffffu, x, 31);
   }
   if (threadIdx.x == 0) {
-    word_off[nch] = carry;
-    if (carry != n_words) atomicOr(&sc->status, ST_CORRUPT);
+    const unsigned long long total = wt[nw - 1];
+    word_off[nch] = total;
+    if (total != n_words) atomicOr(&sc->status, ST_CORRUPT);
   }
 }
 
