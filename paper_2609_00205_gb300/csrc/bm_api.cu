@@ -610,10 +610,18 @@ __global__ void __launch_bounds__(kCbThreads) word_scan_kernel(const unsigned* c
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const unsigned long long seg = (nch + nw - 1) / nw;
   const unsigned long long a0 = min(nch, (unsigned long long)wid * seg), a1 = min(nch, a0 + seg);
+  // eight loads in flight per lane (256 counts per step)
   unsigned long long tot = 0;
-  for (unsigned long long i = a0 + lane; i - lane < a1; i += 32) {  // warp-uniform trip count
-    const unsigned long long v = i < a1 ? chunk_words[i] : 0ull;
-    unsigned long long x = v;
+  for (unsigned long long b0 = a0; b0 < a1; b0 += 256) {
+    unsigned v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const unsigned long long i = b0 + j * 32 + lane;
+      v[j] = i < a1 ? chunk_words[i] : 0u;
+    }
+    unsigned long long x = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x += v[j];
 #pragma unroll
     for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     tot += x;
@@ -631,16 +639,25 @@ __global__ void __launch_bounds__(kCbThreads) word_scan_kernel(const unsigned* c
   }
   __syncthreads();
   unsigned long long carry = wid ? wt[wid - 1] : 0ull;
-  for (unsigned long long i = a0 + lane; i - lane < a1; i += 32) {
-    const unsigned long long v = i < a1 ? chunk_words[i] : 0ull;
-    unsigned long long x = v;
+  for (unsigned long long b0 = a0; b0 < a1; b0 += 256) {
+    unsigned v[8];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
+    for (int j = 0; j < 8; ++j) {
+      const unsigned long long i = b0 + j * 32 + lane;
+      v[j] = i < a1 ? chunk_words[i] : 0u;
     }
-    if (i < a1) word_off[i] = carry + x - v;
-    carry += __shfl_sync(0xffffffffu, x, 31);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const unsigned long long i = b0 + j * 32 + lane;
+      unsigned long long x = v[j];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (i < a1) word_off[i] = carry + x - v[j];
+      carry += __shfl_sync(0xffffffffu, x, 31);
+    }
   }
   if (threadIdx.x == 0) {
     const unsigned long long total = wt[nw - 1];
