@@ -377,8 +377,8 @@ int grid_for(int64_t work, int threads, int per_sm = 8) {
 template <typename T>
 __device__ __forceinline__ void maxabs_acc(T x, T& m, bool& bad) {
   const T v = fabs(x);
-  if (v != v || isinf(v)) bad = true;
-  else m = v > m ? v : m;
+  bad |= !(v < T(INFINITY));  // NaN or infinity: the stream will be raw
+  m = v > m ? v : m;          // NaN never compares greater: ignored; infinity kept
 }
 
 // Quantiser widths of every (tier, level), in IEEE double arithmetic without
@@ -443,7 +443,19 @@ __global__ void __launch_bounds__(256) maxabs_kernel(const T* __restrict__ u, in
   const int64_t nv = (n - h) / V;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
   const uint4* pv = reinterpret_cast<const uint4*>(u + h);
-  for (int64_t i = tid; i < nv; i += nth) {
+  int64_t i = tid;
+  for (; i + 3 * nth < nv; i += 4 * nth) {  // four 16-byte loads in flight
+    uint4 q[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) q[r] = __ldg(pv + i + r * nth);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const T* t = reinterpret_cast<const T*>(&q[r]);
+#pragma unroll
+      for (int j = 0; j < V; ++j) maxabs_acc(t[j], m, bad);
+    }
+  }
+  for (; i < nv; i += nth) {
     const uint4 q = __ldg(pv + i);
     const T* t = reinterpret_cast<const T*>(&q);
 #pragma unroll

@@ -164,6 +164,10 @@ def test_raw_fallbacks(bm):
     np.testing.assert_array_equal(sg, oracle.compress(u, 1e-2, rel=True, B=9, K=2, M=1))
     d = bm.decompress(torch.from_numpy(sg).to(DEV)).cpu().numpy()
     np.testing.assert_array_equal(d.view(np.uint32), u.view(np.uint32))
+    w = fields.gaussian_bumps((20, 21, 22), seed=4)
+    w[1, 2, 3] = -np.inf
+    sg = bm.compress(torch.from_numpy(w).to(DEV), 1e-2, block=9, levels=2, global_levels=1).cpu().numpy()
+    np.testing.assert_array_equal(sg, oracle.compress(w, 1e-2, rel=True, B=9, K=2, M=1))
     v = fields.gaussian_bumps((20, 21, 22), seed=4)
     sg = bm.compress(torch.from_numpy(v).to(DEV), 1e-7, block=9, levels=2, global_levels=1).cpu().numpy()
     assert oracle.stream_header(sg)["raw"]
