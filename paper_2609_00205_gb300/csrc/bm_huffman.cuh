@@ -106,14 +106,14 @@ __device__ void block_sort_regs(K* keys) {
           const K o = __shfl_xor_sync(0xffffffffu, v[e], m);
           v[e] = keep_min ? (o < v[e] ? o : v[e]) : (o > v[e] ? o : v[e]);
         }
-      } else {
+      } else {  // element-major in shared memory: neighbouring threads, neighbouring words
         __syncthreads();
 #pragma unroll
-        for (int e = 0; e < E; ++e) keys[t * E + e] = v[e];
+        for (int e = 0; e < E; ++e) keys[e * 1024 + t] = v[e];
         __syncthreads();
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-          const K o = keys[(t ^ m) * E + e];
+          const K o = keys[e * 1024 + (t ^ m)];
           v[e] = keep_min ? (o < v[e] ? o : v[e]) : (o > v[e] ? o : v[e]);
         }
       }
