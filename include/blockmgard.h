@@ -164,6 +164,9 @@ void bm_release_workspace(void* stream);
  * milliseconds (names[i] static strings), up to max_stages entries. */
 void bm_set_timing(int enabled);
 int bm_stage_times(const char** names, float* ms, int max_stages);
+/* The same, plus each stage's start in milliseconds after the start of the
+ * call's first stage (stages on the second stream overlap the others). */
+int bm_stage_timeline(const char** names, float* ms, float* start_ms, int max_stages);
 /* Test hook: cap the persistent grid of the In-cache Block kernels at
  * max_ctas CTAs (0 = the occupancy-based default), so that small fields also
  * make every CTA walk several blocks.  Process-wide; results do not depend on

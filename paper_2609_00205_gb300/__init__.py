@@ -17,7 +17,7 @@ from . import _build
 __all__ = [
     "BM_F32", "BM_F64", "BlockMGARDError", "load", "compress", "decompress", "decompose", "recompose",
     "coeff_count", "stream_info", "stream_codes", "huffman_encode", "huffman_decode", "compress_bound",
-    "set_timing", "stage_times", "launch_count", "release_workspace", "library_path",
+    "set_timing", "stage_times", "stage_timeline", "launch_count", "release_workspace", "library_path",
 ]
 
 BM_F32, BM_F64 = 0, 1
@@ -76,6 +76,7 @@ def load():
     L.bm_set_block_grid_limit.argtypes = [ctypes.c_int]
     L.bm_set_block_grid_limit.restype = None
     L.bm_stage_times.argtypes = [P(ctypes.c_char_p), P(ctypes.c_float), ctypes.c_int]
+    L.bm_stage_timeline.argtypes = [P(ctypes.c_char_p), P(ctypes.c_float), P(ctypes.c_float), ctypes.c_int]
     L.bm_launch_count.restype = u64
     L.bm_error_string.restype = ctypes.c_char_p
     L.bm_last_error_detail.restype = ctypes.c_char_p
@@ -249,6 +250,16 @@ def huffman_decode(section: torch.Tensor, meta: dict, n: int, dict_size: int, ch
 
 def set_timing(enabled: bool):
     load().bm_set_timing(1 if enabled else 0)
+
+
+def stage_timeline() -> list:
+    """(name, start_ms, ms) of every stage of the last timed call."""
+    L = load()
+    names = (ctypes.c_char_p * 64)()
+    ms = (ctypes.c_float * 64)()
+    t0 = (ctypes.c_float * 64)()
+    n = L.bm_stage_timeline(names, ms, t0, 64)
+    return [(names[i].decode(), float(t0[i]), float(ms[i])) for i in range(n)]
 
 
 def stage_times() -> list:

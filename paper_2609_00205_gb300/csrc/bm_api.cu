@@ -46,7 +46,8 @@ std::atomic<int> g_timing{0};
 struct StageTimer {
   struct Rec { const char* name; cudaEvent_t a, b; cudaStream_t s; };
   std::vector<Rec> recs;
-  std::vector<std::pair<const char*, float>> last;
+  struct Done { const char* name; float ms, start; };
+  std::vector<Done> last;
   cudaStream_t s = nullptr;
   bool on = false;
   void begin(cudaStream_t st) {
@@ -88,10 +89,11 @@ struct StageTimer {
     if (!on) return;
     last.clear();
     for (auto& r : recs) {
-      float ms = 0.f;
+      float ms = 0.f, t0 = 0.f;
       cudaEventSynchronize(r.b);
       cudaEventElapsedTime(&ms, r.a, r.b);
-      last.push_back({r.name, ms});
+      cudaEventElapsedTime(&t0, recs[0].a, r.a);
+      last.push_back({r.name, ms, t0});
     }
     clear();
   }
@@ -233,7 +235,7 @@ bm_status upload_tables(PlanDev& P) {
     if (bytes) std::memcpy(img.data() + off, src, bytes);
     return off;
   };
-  struct Offs { size_t cidx, jlo, jhi, wl, wr, cb, isc, proj; };
+  struct Offs { size_t cidx, jlo, jhi, wl, wr, cb, isc, proj, f0, band, tm, tib, tsup; };
   std::vector<Offs> offs;
   for (auto& L3 : P.h.glev)
     for (auto& D : L3) {
@@ -242,7 +244,8 @@ bm_status upload_tables(PlanDev& P) {
         for (size_t i = 0; i < v.size(); ++i) o[i] = (T)v[i];
         return o;
       };
-      std::vector<T> wl = cvt(D.wl), wr = cvt(D.wr), proj = cvt(D.P);
+      std::vector<T> wl = cvt(D.wl), wr = cvt(D.wr), proj = cvt(D.P), band = cvt(D.band), tm = cvt(D.tm),
+                     tib = cvt(D.tib), tsup = cvt(D.tsup);
       Offs o;
       o.cidx = put(D.cidx.data(), D.cidx.size() * 4);
       o.jlo = put(D.jlo.data(), D.jlo.size() * 4);
@@ -252,6 +255,11 @@ bm_status upload_tables(PlanDev& P) {
       o.cb = put(D.cb.data(), D.cb.size() * 4);
       o.isc = put(D.isc.data(), D.isc.size());
       o.proj = put(proj.data(), proj.size() * sizeof(T));
+      o.f0 = put(D.f0.data(), D.f0.size() * 4);
+      o.band = put(band.data(), band.size() * sizeof(T));
+      o.tm = put(tm.data(), tm.size() * sizeof(T));
+      o.tib = put(tib.data(), tib.size() * sizeof(T));
+      o.tsup = put(tsup.data(), tsup.size() * sizeof(T));
       offs.push_back(o);
     }
   if (P.dtab[di]) { cudaFree(P.dtab[di]); P.dtab[di] = nullptr; }
@@ -278,6 +286,11 @@ bm_status upload_tables(PlanDev& P) {
       g.cb = reinterpret_cast<const int*>(base + o.cb);
       g.isc = reinterpret_cast<const uint8_t*>(base + o.isc);
       g.P = reinterpret_cast<const T*>(base + o.proj);
+      g.f0 = reinterpret_cast<const int*>(base + o.f0);
+      g.band = reinterpret_cast<const T*>(base + o.band);
+      g.tm = reinterpret_cast<const T*>(base + o.tm);
+      g.tib = reinterpret_cast<const T*>(base + o.tib);
+      g.tsup = reinterpret_cast<const T*>(base + o.tsup);
     }
     L.sym_off = P.h.sym_off[l];
     G.push_back(L);
@@ -709,12 +722,39 @@ cudaError_t launch_block<double>(int dir, int B, int K, int mode, const BlockArg
                 : launch_block_f64_b17(dir, K, mode, a, s, num_sms(), cap);
 }
 
-// One dense restriction pass of a global level (gl_apply).
+// One restriction pass of a global level: band product and tridiagonal solve
+// per line (gl_line), or the dense projection (gl_apply) for lines longer than
+// gl_line takes.
+template <typename T, int DIM, int FINAL, int E>
+cudaError_t launch_line(const GLevel<T>& L, const ApplyShape& S, const T* in, T* out, const T* U, cudaStream_t s) {
+  const GDim<T>& D = L.d[DIM];
+  const size_t smem = line_smem<T>(D.n, D.c);
+  static std::atomic<int> attr{0};  // largest dynamic shared memory enabled so far
+  if ((int)smem > 48 * 1024 && (int)smem > attr.load()) {
+    const cudaError_t e = cudaFuncSetAttribute(gl_line<T, DIM, FINAL, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+    if (e != cudaSuccess) return e;
+    attr.store((int)smem);
+  }
+  const int64_t ctas = S.nb * ((S.ncol + line_tile<T>() - 1) / line_tile<T>());
+  gl_line<T, DIM, FINAL, E><<<(unsigned)ctas, 256, smem, s>>>(L, S, in, out, U);
+  return cudaGetLastError();
+}
+
 template <typename T, int DIM, int FINAL>
-void launch_apply(const GLevel<T>& L, const T* in, T* out, const T* U, cudaStream_t s) {
+cudaError_t launch_apply(const GLevel<T>& L, const T* in, T* out, const T* U, cudaStream_t s) {
   const ApplyShape S = apply_shape(L, DIM);
+  if (S.nb * S.ncol == 0) return cudaSuccess;
+  switch (line_segment(L.d[DIM].c)) {
+    case 1: return launch_line<T, DIM, FINAL, 1>(L, S, in, out, U, s);
+    case 3: return launch_line<T, DIM, FINAL, 3>(L, S, in, out, U, s);
+    case 9: return launch_line<T, DIM, FINAL, 9>(L, S, in, out, U, s);
+    case 17: return launch_line<T, DIM, FINAL, 17>(L, S, in, out, U, s);
+    default: break;
+  }
   const int64_t ctas = S.nb * ((S.ncol + kApplyCols - 1) / kApplyCols);
   gl_apply<T, DIM, FINAL><<<(unsigned)ctas, 256, 0, s>>>(L, S, in, out, U);
+  return cudaGetLastError();
 }
 
 // Outputs of the decomposition (mode 0: symbols + escapes + histogram).
@@ -764,22 +804,29 @@ bm_status run_decompose(PlanDev& P, const T* field, int mode, const FwdOut<T>& o
     const int64_t nn = gs.U[l];
     const T* rq = o.rq ? o.rq + o.ntiers * h.K + l : nullptr;
     const int64_t rows = (int64_t)L.d[0].n * L.d[1].n;  // one warp per row, 8 rows per CTA
-    if (mode == 0) gl_fwd_detail<T, 0><<<grid_for(rows * 32, 256, 2), 256, 0, s>>>(L, U[l], Dbuf, o.sym, o.esc, o.coef, rq, o.hist, o.radius, o.sc);
-    else gl_fwd_detail<T, 1><<<grid_for(rows * 32, 256, 8), 256, 0, s>>>(L, U[l], Dbuf, o.sym, o.esc, o.coef, rq, o.hist, o.radius, o.sc);
+    if (mode == 0) gl_fwd_detail<T, 0><<<grid_for(rows * 32, 256, 8), 256, 0, s>>>(L, U[l], Dbuf, o.sym, o.esc, o.coef, rq, o.radius, o.sc);
+    else gl_fwd_detail<T, 1><<<grid_for(rows * 32, 256, 8), 256, 0, s>>>(L, U[l], Dbuf, o.sym, o.esc, o.coef, rq, o.radius, o.sc);
     (void)nn;
     BM_LAUNCHED();
-    launch_apply<T, 2, 0>(L, Dbuf, W1, nullptr, s);
-    launch_apply<T, 1, 0>(L, W1, W2, nullptr, s);
-    launch_apply<T, 0, 1>(L, W2, U[l + 1], U[l], s);
+    BM_CUDA((launch_apply<T, 2, 0>(L, Dbuf, W1, nullptr, s)));
+    BM_CUDA((launch_apply<T, 1, 0>(L, W1, W2, nullptr, s)));
+    BM_CUDA((launch_apply<T, 0, 1>(L, W2, U[l + 1], U[l], s)));
     g_launches.fetch_add(3);
-    BM_CUDA(cudaGetLastError());
   }
   {
     Stage st("coarsest");
     const int64_t cnt = gs.U[h.M];
     const T* rq = o.rq ? o.rq + o.ntiers * h.K + h.M : nullptr;
-    if (mode == 0) coarsest_fwd<T, 0><<<grid_for(cnt, 256), 256, 0, s>>>(U[h.M], cnt, h.sym_off[h.M], o.sym, o.esc, o.coef, rq, o.hist, o.radius, o.sc);
-    else coarsest_fwd<T, 1><<<grid_for(cnt, 256), 256, 0, s>>>(U[h.M], cnt, h.sym_off[h.M], o.sym, o.esc, o.coef, rq, o.hist, o.radius, o.sc);
+    if (mode == 0) coarsest_fwd<T, 0><<<grid_for(cnt, 256), 256, 0, s>>>(U[h.M], cnt, h.sym_off[h.M], o.sym, o.esc, o.coef, rq, o.radius, o.sc);
+    else coarsest_fwd<T, 1><<<grid_for(cnt, 256), 256, 0, s>>>(U[h.M], cnt, h.sym_off[h.M], o.sym, o.esc, o.coef, rq, o.radius, o.sc);
+    BM_LAUNCHED();
+    BM_CUDA(cudaGetLastError());
+  }
+  if (mode == 0 && o.hist) {  // histogram of the global levels' and the coarsest array's symbols
+    Stage st("global_histogram");
+    const unsigned long long s0 = (unsigned long long)h.sym_off[0], s1 = (unsigned long long)h.n_coeffs;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(num_sms(), (int64_t)(s1 - s0) / 16384));
+    hist_range_kernel<<<grid, 256, 0, s>>>(o.sym, s0, s1, 2 * o.radius, (unsigned)o.radius, o.hist);
     BM_LAUNCHED();
     BM_CUDA(cudaGetLastError());
   }
@@ -828,9 +875,9 @@ bm_status run_recompose(PlanDev& P, T* field, int mode, const InvIn<T>& in, Carv
     if (mode == 0) gl_inv_dequant<T, 0><<<grid_for(nn, 256), 256, 0, s>>>(L, in.sym, in.esc, in.coef, q, in.radius, U[l]);
     else gl_inv_dequant<T, 1><<<grid_for(nn, 256), 256, 0, s>>>(L, in.sym, in.esc, in.coef, q, in.radius, U[l]);
     T* Cn = Dbuf;  // corrected coarse values (size of U[l+1] <= size of U[0])
-    launch_apply<T, 2, 0>(L, U[l], W1, nullptr, s);
-    launch_apply<T, 1, 0>(L, W1, W2, nullptr, s);
-    launch_apply<T, 0, 2>(L, W2, Cn, U[l + 1], s);
+    BM_CUDA((launch_apply<T, 2, 0>(L, U[l], W1, nullptr, s)));
+    BM_CUDA((launch_apply<T, 1, 0>(L, W1, W2, nullptr, s)));
+    BM_CUDA((launch_apply<T, 0, 2>(L, W2, Cn, U[l + 1], s)));
     gl_inv_interp<T><<<grid_for(nn, 256), 256, 0, s>>>(L, Cn, U[l]);
     g_launches.fetch_add(5);
     BM_CUDA(cudaGetLastError());
@@ -1264,17 +1311,22 @@ void bm_set_timing(int enabled) { g_timing.store(enabled ? 1 : 0); }
 
 void bm_set_block_grid_limit(int max_ctas) { g_block_grid_cap.store(max_ctas > 0 ? max_ctas : 0); }
 
-int bm_stage_times(const char** names, float* ms, int max_stages) {
+int bm_stage_timeline(const char** names, float* ms, float* start_ms, int max_stages) {
   std::lock_guard<std::mutex> g(g_timer_mu);
   g_timer.collect();
   int n = 0;
   for (auto& r : g_timer.last) {
     if (n >= max_stages) break;
-    if (names) names[n] = r.first;
-    if (ms) ms[n] = r.second;
+    if (names) names[n] = r.name;
+    if (ms) ms[n] = r.ms;
+    if (start_ms) start_ms[n] = r.start;
     ++n;
   }
   return n;
+}
+
+int bm_stage_times(const char** names, float* ms, int max_stages) {
+  return bm_stage_timeline(names, ms, nullptr, max_stages);
 }
 
 size_t bm_compress_bound(int ndim, const int64_t* shape, bm_dtype dtype) {

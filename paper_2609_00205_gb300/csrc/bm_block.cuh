@@ -10,6 +10,8 @@
 //   Phase C  lines (j1,j2) along dim 0, coarse = u|C + z    -> out (C,C,C)
 // T1 and T2 are stored transposed so that every thread of phases B and C
 // reads its line contiguously (stride N between threads: no bank conflicts).
+// The forward pass copies u|C into `out` during phase A, after which the
+// level's input is dead, so T2 takes the input's place in shared memory.
 // The shrinking arrays N^3 -> N^2 C -> N C^2 -> C^3 are the paper's
 // 8x8x8 -> 5x8x8 -> 5x5x8 -> 5x5x5 sequence for the block size used.
 #pragma once
@@ -20,10 +22,15 @@
 // Build-time choices of the forward kernel: whether it keeps the symbol
 // histogram itself (BM_FWD_HIST; otherwise a separate pass counts the
 // symbols), prefetches the next block into a second buffer
-// (BM_FWD_DOUBLE_BUFFER), and the minimum CTAs per SM it is compiled for
-// (BM_FWD_MIN_CTAS).  The defaults are the fastest measured on GB300 for the
-// 513^3 FP32 workload: the in-kernel histogram's shared atomics and its 32 KB
-// cost more than a separate pass, and three resident CTAs beat prefetching.
+// (BM_FWD_DOUBLE_BUFFER), its threads per CTA (BM_FWD_THREADS; 0 = one per
+// line of the first pass, B^2 rounded up to whole warps) and the CTAs per SM
+// it is compiled for (BM_FWD_MIN_CTAS, capped by what shared memory holds);
+// BM_INV_THREADS and BM_INV_MIN_CTAS are the last two for the inverse.  The
+// defaults are the fastest measured on GB300 for the 513^3 FP32 workload: the
+// in-kernel histogram's shared atomics and its 32 KB cost more than a separate
+// pass, prefetching costs more than it hides, and five-warp CTAs (two lines of
+// the first pass per thread, four or more CTAs per SM) let one CTA's barrier
+// waits overlap the others' work.
 #ifndef BM_FWD_HIST
 #define BM_FWD_HIST 0
 #endif
@@ -31,7 +38,16 @@
 #define BM_FWD_DOUBLE_BUFFER 0
 #endif
 #ifndef BM_FWD_MIN_CTAS
-#define BM_FWD_MIN_CTAS 3
+#define BM_FWD_MIN_CTAS 4
+#endif
+#ifndef BM_FWD_THREADS
+#define BM_FWD_THREADS 160
+#endif
+#ifndef BM_INV_THREADS
+#define BM_INV_THREADS 160
+#endif
+#ifndef BM_INV_MIN_CTAS
+#define BM_INV_MIN_CTAS 4
 #endif
 
 namespace bm {
@@ -76,6 +92,8 @@ constexpr int lvl_offset(int B, int l) {  // first symbol of level l inside a bl
 template <typename T, int B, int K>
 struct BlockCfg {
   static constexpr int NT = ((B * B + 31) / 32) * 32;
+  static constexpr int NT_FWD = (BM_FWD_THREADS > 0 && BM_FWD_THREADS < NT) ? BM_FWD_THREADS : NT;
+  static constexpr int NT_INV = (BM_INV_THREADS > 0 && BM_INV_THREADS < NT) ? BM_INV_THREADS : NT;
   static constexpr int C1 = (B + 1) / 2;
   static constexpr int C2 = (C1 + 1) / 2;
   static constexpr int A = B * B * B;
@@ -89,11 +107,18 @@ struct BlockCfg {
   // byte offsets: the symbol staging area and the histogram start on 16-byte
   // boundaries (the staging area is copied out with 8-byte vectors)
   static constexpr size_t up16(size_t x) { return (x + 15) / 16 * 16; }
-  static constexpr size_t fwd_stage_off = up16(sizeof(T) * (NBUF * A + T1 + T2 + CB0 + CB1));
+  static constexpr size_t fwd_stage_off = up16(sizeof(T) * (NBUF * A + T1 + CB0 + CB1));  // T2 overlays A
   static constexpr size_t fwd_hist_off = up16(fwd_stage_off + 2 * PB);
   static constexpr size_t fwd_smem = fwd_hist_off + (BM_FWD_HIST ? 4 * kHistWin : 0);
   static constexpr size_t inv_stage_off = up16(sizeof(T) * (A + T1 + T2 + CB0 + CB1));
   static constexpr size_t inv_smem(int mode) { return inv_stage_off + up16((mode ? sizeof(T) : 2) * PB); }
+  // CTAs per SM the forward kernel is compiled for: BM_FWD_MIN_CTAS, or as many
+  // as the shared memory of an SM holds (228 KB, 1 KB reserved per CTA) when
+  // fewer, so the register budget is not cut for residency that cannot happen.
+  static constexpr int fwd_fit = (int)((228u * 1024u) / (fwd_smem + 1024u));
+  static constexpr int FWD_MIN_CTAS = fwd_fit < 1 ? 1 : (fwd_fit < BM_FWD_MIN_CTAS ? fwd_fit : BM_FWD_MIN_CTAS);
+  static constexpr int inv_fit = (int)((228u * 1024u) / (inv_smem(1) + 1024u));
+  static constexpr int INV_MIN_CTAS = inv_fit < 1 ? 1 : (inv_fit < BM_INV_MIN_CTAS ? inv_fit : BM_INV_MIN_CTAS);
 };
 
 // Histogram of one CTA: the whole dictionary in shared memory; the centre
@@ -113,10 +138,10 @@ __device__ __forceinline__ void hist_count(unsigned* hloc, unsigned* hglob, int 
 // Forward level
 // ---------------------------------------------------------------------------
 template <typename T, int N, int MODE>
-__device__ __forceinline__ void level_fwd(const T* __restrict__ X, T* __restrict__ T1, T* __restrict__ T2,
-                                          T* __restrict__ out, const int lvl_off, const T rq, uint16_t* stage,
-                                          int32_t* __restrict__ esc_blk, T* __restrict__ coef_blk, unsigned* hloc,
-                                          unsigned* hglob, const int radius, bool& ovf, unsigned& centre) {
+__device__ __forceinline__ void level_fwd(T* X, T* __restrict__ T1, T* __restrict__ out, const int lvl_off, const T rq,
+                                          uint16_t* stage, int32_t* __restrict__ esc_blk, T* __restrict__ coef_blk,
+                                          unsigned* hloc, unsigned* hglob, const int radius, bool& ovf,
+                                          unsigned& centre) {
   constexpr int C = (N + 1) / 2;
   const auto& tb = block_tab<T, N>();
   for (int L = threadIdx.x; L < N * N; L += blockDim.x) {
@@ -139,6 +164,10 @@ __device__ __forceinline__ void level_fwd(const T* __restrict__ X, T* __restrict
       d[k] = u - e;
     }
     const bool cc = !f0 && !f1;
+    if (cc) {  // u|C of this line: the start of the coarse values (phase C adds z)
+#pragma unroll
+      for (int J = 0; J < C; ++J) out[((i0 / 2) * C + i1 / 2) * C + J] = X[L * N + 2 * J];
+    }
     const int cc_before = ((i0 + 1) / 2) * C + (f0 ? 0 : (i1 + 1) / 2);
     const int base = lvl_off + L * N - cc_before * C;
     if (MODE == 0) {
@@ -169,6 +198,7 @@ __device__ __forceinline__ void level_fwd(const T* __restrict__ X, T* __restrict
     for (int j = 0; j < C; ++j) T1[(i0 * C + j) * N + i1] = z[j];
   }
   __syncthreads();
+  T* T2 = X;
   for (int L = threadIdx.x; L < N * C; L += blockDim.x) {  // L = i0*C + j2
     const int i0 = L / C, j2 = L - i0 * C;
     T d[N];
@@ -188,7 +218,7 @@ __device__ __forceinline__ void level_fwd(const T* __restrict__ X, T* __restrict
     T z[C];
     restrict_solve<T, N>(tb, d, z);
 #pragma unroll
-    for (int J = 0; J < C; ++J) out[(J * C + j1) * C + j2] = X[((2 * J) * N + 2 * j1) * N + 2 * j2] + z[J];
+    for (int J = 0; J < C; ++J) out[(J * C + j1) * C + j2] += z[J];
   }
   __syncthreads();
 }
@@ -205,13 +235,13 @@ struct LevelBufs {
 
 template <typename T, int N, int L, int K, int B, int MODE>
 struct FwdLevels {
-  __device__ __forceinline__ static void run(const LevelBufs<T>& bufs, T* T1, T* T2, const T* rq, uint16_t* stage,
+  __device__ __forceinline__ static void run(const LevelBufs<T>& bufs, T* T1, const T* rq, uint16_t* stage,
                                              int32_t* esc_blk, T* coef_blk, unsigned* hloc, unsigned* hglob,
                                              int radius, bool& ovf, unsigned& centre) {
-    level_fwd<T, N, MODE>(bufs(L), T1, T2, bufs(L + 1), lvl_offset(B, L), rq[L], stage, esc_blk, coef_blk, hloc,
+    level_fwd<T, N, MODE>(bufs(L), T1, bufs(L + 1), lvl_offset(B, L), rq[L], stage, esc_blk, coef_blk, hloc,
                           hglob, radius, ovf, centre);
     if constexpr (L + 1 < K)
-      FwdLevels<T, (N + 1) / 2, L + 1, K, B, MODE>::run(bufs, T1, T2, rq, stage, esc_blk, coef_blk, hloc, hglob,
+      FwdLevels<T, (N + 1) / 2, L + 1, K, B, MODE>::run(bufs, T1, rq, stage, esc_blk, coef_blk, hloc, hglob,
                                                          radius, ovf, centre);
   }
 };
@@ -243,37 +273,37 @@ struct BlockSpan {
 };
 
 // Copy of one B^3 block into shared memory (row-major), zero filled outside the
-// domain.  Thread t < B(B+1) owns column k = t % B and the rows r0 + (B+1) j
-// of the block (r0 = t / B, j < B): each step moves one plane down and one row
+// domain.  Work item t < B(B+1) (threads stride over the items) owns column
+// k = t % B and the rows r0 + (B+1) j of the block (r0 = t / B, j < B): each
+// step moves one plane down and one row
 // on (i0+1, i1+1, i1 wrapping once), so the source advances by the constant
 // s0 + n2, corrected once by s0 - B n2 at the wrap, and the destination by
 // B(B+1) elements.  Consecutive threads read consecutive elements of a row.
 template <typename T, int B>
 __device__ __forceinline__ void issue_block_load(T* dst, const T* __restrict__ field, const BlockSpan<const T, B>& sp,
                                                  int64_t n1, int64_t n2) {
-  static_assert(BlockCfg<T, B, 1>::NT >= B * (B + 1), "one thread per (column, first row)");
-  const int t = threadIdx.x;
-  if (t >= B * (B + 1)) return;
-  const int k = t % B, r0 = t / B, jc = B - r0;
-  const int64_t s0 = n1 * n2, D = s0 + n2, E = s0 - (int64_t)B * n2;
-  const T* p = sp.base + (int64_t)r0 * n2 + k;
-  T* q = dst + t;
-  if ((sp.lim0 == B) & (sp.lim1 == B) & (sp.lim2 == B)) {  // interior block
+  for (int t = threadIdx.x; t < B * (B + 1); t += blockDim.x) {
+    const int k = t % B, r0 = t / B, jc = B - r0;
+    const int64_t s0 = n1 * n2, D = s0 + n2, E = s0 - (int64_t)B * n2;
+    const T* p = sp.base + (int64_t)r0 * n2 + k;
+    T* q = dst + t;
+    if ((sp.lim0 == B) & (sp.lim1 == B) & (sp.lim2 == B)) {  // interior block
 #pragma unroll
-    for (int j = 0; j < B; ++j) {
-      if (j < B - 1 || r0 == 0) cp_async_zfill<sizeof(T)>(q + j * B * (B + 1), p + (j >= jc ? E : 0), true);
-      p += D;
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < B; ++j) {
-      if (j < B - 1 || r0 == 0) {
-        const int carry = j >= jc;
-        const int i0 = j + carry, i1 = r0 + j - (carry ? B : 0);
-        const bool ok = (i0 < sp.lim0) & (i1 < sp.lim1) & (k < sp.lim2);
-        cp_async_zfill<sizeof(T)>(q + j * B * (B + 1), ok ? p + (carry ? E : 0) : field, ok);
+      for (int j = 0; j < B; ++j) {
+        if (j < B - 1 || r0 == 0) cp_async_zfill<sizeof(T)>(q + j * B * (B + 1), p + (j >= jc ? E : 0), true);
+        p += D;
       }
-      p += D;
+    } else {
+#pragma unroll
+      for (int j = 0; j < B; ++j) {
+        if (j < B - 1 || r0 == 0) {
+          const int carry = j >= jc;
+          const int i0 = j + carry, i1 = r0 + j - (carry ? B : 0);
+          const bool ok = (i0 < sp.lim0) & (i1 < sp.lim1) & (k < sp.lim2);
+          cp_async_zfill<sizeof(T)>(q + j * B * (B + 1), ok ? p + (carry ? E : 0) : field, ok);
+        }
+        p += D;
+      }
     }
   }
 }
@@ -282,27 +312,27 @@ __device__ __forceinline__ void issue_block_load(T* dst, const T* __restrict__ f
 // field, with the same thread-to-element assignment.
 template <typename T, int B>
 __device__ __forceinline__ void store_block(const BlockSpan<T, B>& sp, const T* src, int64_t n1, int64_t n2) {
-  const int t = threadIdx.x;
-  if (t >= B * (B + 1)) return;
-  const int k = t % B, r0 = t / B, jc = B - r0;
-  const int64_t s0 = n1 * n2, D = s0 + n2, E = s0 - (int64_t)B * n2;
-  T* p = sp.base + (int64_t)r0 * n2 + k;
-  const T* q = src + t;
-  if ((sp.lim0 == B) & (sp.lim1 == B) & (sp.lim2 == B)) {
+  for (int t = threadIdx.x; t < B * (B + 1); t += blockDim.x) {
+    const int k = t % B, r0 = t / B, jc = B - r0;
+    const int64_t s0 = n1 * n2, D = s0 + n2, E = s0 - (int64_t)B * n2;
+    T* p = sp.base + (int64_t)r0 * n2 + k;
+    const T* q = src + t;
+    if ((sp.lim0 == B) & (sp.lim1 == B) & (sp.lim2 == B)) {
 #pragma unroll
-    for (int j = 0; j < B; ++j) {
-      if (j < B - 1 || r0 == 0) p[j >= jc ? E : 0] = q[j * B * (B + 1)];
-      p += D;
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < B; ++j) {
-      if (j < B - 1 || r0 == 0) {
-        const int carry = j >= jc;
-        const int i0 = j + carry, i1 = r0 + j - (carry ? B : 0);
-        if ((i0 < sp.lim0) & (i1 < sp.lim1) & (k < sp.lim2)) p[carry ? E : 0] = q[j * B * (B + 1)];
+      for (int j = 0; j < B; ++j) {
+        if (j < B - 1 || r0 == 0) p[j >= jc ? E : 0] = q[j * B * (B + 1)];
+        p += D;
       }
-      p += D;
+    } else {
+#pragma unroll
+      for (int j = 0; j < B; ++j) {
+        if (j < B - 1 || r0 == 0) {
+          const int carry = j >= jc;
+          const int i0 = j + carry, i1 = r0 + j - (carry ? B : 0);
+          if ((i0 < sp.lim0) & (i1 < sp.lim1) & (k < sp.lim2)) p[carry ? E : 0] = q[j * B * (B + 1)];
+        }
+        p += D;
+      }
     }
   }
 }
@@ -335,13 +365,13 @@ __device__ __forceinline__ void store_symbols(uint16_t* __restrict__ dst, const 
 // Forward: persistent CTAs walk the blocks; the next block is prefetched with
 // cp.async (zero fill outside the domain) while the current one is processed.
 template <typename T, int B, int K, int MODE>
-__global__ void __launch_bounds__(BlockCfg<T, B, K>::NT, BM_FWD_MIN_CTAS) block_fwd_kernel(BlockArgs<T> a) {
+__global__ void __launch_bounds__(BlockCfg<T, B, K>::NT_FWD, BlockCfg<T, B, K>::FWD_MIN_CTAS)
+    block_fwd_kernel(BlockArgs<T> a) {
   using Cfg = BlockCfg<T, B, K>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Abuf = reinterpret_cast<T*>(smem_raw);
   T* T1 = Abuf + Cfg::NBUF * Cfg::A;
-  T* T2 = T1 + Cfg::T1;
-  T* cb0 = T2 + Cfg::T2;
+  T* cb0 = T1 + Cfg::T1;
   T* cb1 = cb0 + Cfg::CB0;
   uint16_t* stage = reinterpret_cast<uint16_t*>(smem_raw + Cfg::fwd_stage_off);
   unsigned* hloc = reinterpret_cast<unsigned*>(smem_raw + Cfg::fwd_hist_off);
@@ -375,7 +405,7 @@ __global__ void __launch_bounds__(BlockCfg<T, B, K>::NT, BM_FWD_MIN_CTAS) block_
     for (int l = 0; l < K; ++l) rq[l] = MODE == 0 ? a.rq[tier * K + l] : T(0);
     const int64_t sbase = b * (int64_t)Cfg::PB;
     LevelBufs<T> bufs{Abuf + (BM_FWD_DOUBLE_BUFFER ? buf : 0) * Cfg::A, cb0, cb1};
-    FwdLevels<T, B, 0, K, B, MODE>::run(bufs, T1, T2, rq, stage, a.esc + (MODE == 0 ? sbase : 0),
+    FwdLevels<T, B, 0, K, B, MODE>::run(bufs, T1, rq, stage, a.esc + (MODE == 0 ? sbase : 0),
                                         a.coef + (MODE == 1 ? sbase : 0), hloc, a.hist, a.radius, ovf, centre);
     // block coarse values -> gathered grid G
     {
@@ -498,7 +528,8 @@ struct InvLevels {  // recompose levels L, L-1, ..., 0 (level L has N nodes)
 };
 
 template <typename T, int B, int K, int MODE>
-__global__ void __launch_bounds__(BlockCfg<T, B, K>::NT) block_inv_kernel(BlockArgs<T> a) {
+__global__ void __launch_bounds__(BlockCfg<T, B, K>::NT_INV, BlockCfg<T, B, K>::INV_MIN_CTAS)
+    block_inv_kernel(BlockArgs<T> a) {
   using Cfg = BlockCfg<T, B, K>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* A = reinterpret_cast<T*>(smem_raw);

@@ -22,7 +22,7 @@ cudaError_t launch_one(int dir, const BlockArgs<T>& a, cudaStream_t s, int nsm, 
   if (per_sm <= 0) {
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, Cfg::NT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, dir == 0 ? Cfg::NT_FWD : Cfg::NT_INV, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     if (dev < 64) cached[dir][dev].store(per_sm);
@@ -31,8 +31,8 @@ cudaError_t launch_one(int dir, const BlockArgs<T>& a, cudaStream_t s, int nsm, 
   if (max_grid > 0 && grid > max_grid) grid = max_grid;
   if (grid > a.nblocks) grid = a.nblocks;
   if (grid < 1) return cudaSuccess;
-  if (dir == 0) block_fwd_kernel<T, B, K, MODE><<<(unsigned)grid, Cfg::NT, smem, s>>>(a);
-  else block_inv_kernel<T, B, K, MODE><<<(unsigned)grid, Cfg::NT, smem, s>>>(a);
+  if (dir == 0) block_fwd_kernel<T, B, K, MODE><<<(unsigned)grid, Cfg::NT_FWD, smem, s>>>(a);
+  else block_inv_kernel<T, B, K, MODE><<<(unsigned)grid, Cfg::NT_INV, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -1,8 +1,9 @@
 // Global MGARD levels on the gathered block-coarse grid G (Sec. III-B hybrid
 // hierarchy: L local levels, then M whole-grid levels).  Each level is a
 // handful of whole-grid passes: coefficients, three restriction passes (one
-// per dimension, shrinking it, each the dense projection M_c^-1 I^T M_f of
-// that dimension) and the coarse correction; the inverse runs them backwards.
+// per dimension, shrinking it: the band product I^T M_f and the tridiagonal
+// solve with M_c of that dimension) and the coarse correction; the inverse
+// runs them backwards.
 // Node coordinates are physical (block offset plus the node's in-block
 // coordinate), so every per-dimension operator comes from a host-built table.
 #pragma once
@@ -22,6 +23,11 @@ struct GDim {
   const int* cb;        // [n] number of coarse indices below i
   const uint8_t* isc;   // [n] 1 at coarse nodes
   const T* P;           // [c x n] row-major projection M_c^{-1} I^T M_f
+  const int* f0;        // [c] first fine column of row J of I^T M_f
+  const T* band;        // [5c] row J of I^T M_f over fine columns f0[J] .. f0[J]+4
+  const T* tm;          // [c] Thomas factors of M_c: y_J = r_J - tm_J y_{J-1},
+  const T* tib;         //     z_J = (y_J - tsup_J z_{J+1}) tib_J
+  const T* tsup;
 };
 
 template <typename T>
@@ -48,17 +54,14 @@ __device__ __forceinline__ int64_t nc_rank(const GLevel<T>& L, int i0, int i1, i
 
 // Coefficients of one global level: D = U - I(U|C) at every node (0 at
 // all-coarse nodes, exactly), written to Dfull; the non-coarse ones are
-// quantised (mode 0) or stored (mode 1) at their stream position.  One warp
+// quantised (mode 0; a histogram pass counts the symbols afterwards) or stored
+// (mode 1) at their stream position.  One warp
 // per grid row (i0, i1): the row's interpolation sources, weights and stream
 // offset are computed once, the lanes walk i2.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) gl_fwd_detail(GLevel<T> L, const T* __restrict__ U, T* __restrict__ Dfull,
                                                      uint16_t* sym, int32_t* esc, T* coef, const T* rq_ptr,
-                                                     unsigned* hist, int radius, Scalars* sc) {
-  __shared__ unsigned hloc[kHistWin];
-  if (MODE == 0)
-    for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) hloc[i] = 0;
-  __syncthreads();
+                                                     int radius, Scalars* sc) {
   const GDim<T>&D0 = L.d[0], &D1 = L.d[1], &D2 = L.d[2];
   const int n1 = D1.n, n2 = D2.n;
   const int64_t rows = (int64_t)D0.n * n1, c12 = (int64_t)D1.c * D2.c;
@@ -99,20 +102,12 @@ __global__ void __launch_bounds__(256) gl_fwd_detail(GLevel<T> L, const T* __res
         const unsigned sv = in ? u : 0u;
         sym[pos] = (uint16_t)sv;
         if (!in) esc[pos] = code;
-        atomicAdd(hloc + sv, 1u);
       } else {
         coef[pos] = dv;
       }
     }
   }
-  if (MODE == 0) {
-    if (ovf) atomicOr(&sc->status, ST_OVERFLOW);
-    __syncthreads();
-    for (int i = threadIdx.x; i < (int)dict; i += blockDim.x) {
-      const unsigned v = hloc[i];
-      if (v) atomicAdd(hist + i, v);
-    }
-  }
+  if (MODE == 0 && ovf) atomicOr(&sc->status, ST_OVERFLOW);
 }
 
 // One restriction pass of a global level as a dense contraction with the
@@ -211,6 +206,159 @@ __global__ void __launch_bounds__(256) gl_apply(GLevel<T> L, ApplyShape S, const
   }
 }
 
+// One restriction pass of a global level, line by line along dimension DIM:
+// r = I^T M_f d (five-point band), then M_c z = r by the Thomas recurrences,
+// each evaluated as a warp scan of affine maps (lane l owns the E coarse rows
+// l*E .. l*E+E-1, composes their maps, combines them across the warp with
+// shuffles, then replays its rows from the combined input).  The same
+// operator as the dense projection in gl_apply, in O(n) work per line.
+// A CTA stages kLineTile lines (one 128-byte row of columns) in shared memory,
+// read coalesced along the line when it is contiguous (DIM 2) and across the
+// lines otherwise; eight warps take one line at a time.  Shapes and FINAL as
+// for gl_apply.  E is odd, so the lanes' rows of a segment never share a bank.
+template <typename T>
+constexpr int line_tile() {
+  return 128 / (int)sizeof(T);
+}
+inline int line_segment(int c) {  // rows per lane (0: the line is too long for gl_line)
+  const int e = (c + 31) / 32;
+  return e <= 1 ? 1 : e <= 3 ? 3 : e <= 9 ? 9 : e <= 17 ? 17 : 0;
+}
+template <typename T>
+size_t line_smem(int n, int c) {
+  return (size_t)line_tile<T>() * (size_t)((n | 1) + (c | 1)) * sizeof(T);
+}
+
+template <typename T, int DIM, int FINAL, int E>
+__global__ void __launch_bounds__(256) gl_line(GLevel<T> L, ApplyShape S, const T* __restrict__ in,
+                                               T* __restrict__ out, const T* __restrict__ U) {
+  constexpr int LT = line_tile<T>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const GDim<T>& D = L.d[DIM];
+  const int n = D.n, c = D.c, sn = n | 1, sc = c | 1;
+  T* s_in = reinterpret_cast<T*>(smem_raw);  // [LT][sn] the lines
+  T* s_out = s_in + LT * sn;                  // [LT][sc] r, then z
+  const int64_t tiles = (S.ncol + LT - 1) / LT;
+  const int64_t b = blockIdx.x / tiles;
+  const int64_t col0 = (blockIdx.x - b * tiles) * LT;
+  const int nl = (int)(S.ncol - col0 < LT ? S.ncol - col0 : LT);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const T* inb = in + b * S.in_b;
+  if (S.in_i == 1) {
+    for (int w = warp; w < nl; w += 8)
+      for (int i = lane; i < n; i += 32) s_in[w * sn + i] = inb[(col0 + w) * S.in_c + i];
+  } else {
+    for (int e = threadIdx.x; e < n * LT; e += 256) {
+      const int i = e / LT, w = e - i * LT;
+      if (w < nl) s_in[w * sn + i] = inb[(int64_t)i * S.in_i + (col0 + w) * S.in_c];
+    }
+  }
+  __syncthreads();
+  for (int w = warp; w < nl; w += 8) {
+    const T* x = s_in + w * sn;
+    T* r = s_out + w * sc;
+    if (c == n) {  // a dimension of at most two nodes is not coarsened
+      for (int J = lane; J < c; J += 32) r[J] = x[J];
+      continue;
+    }
+    for (int J = lane; J < c; J += 32) {
+      const int f = D.f0[J];
+      T v = T(0);
+#pragma unroll
+      for (int m = 0; m < 5; ++m)
+        if (f + m < n) v = fma(D.band[5 * J + m], x[f + m], v);
+      r[J] = v;
+    }
+    __syncwarp();
+    const int j0 = lane * E;
+    T y[E];
+    // forward recurrence y_J = r_J - tm_J y_{J-1} (y_{-1} = 0)
+    T a = T(0), m = T(1);
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const int J = j0 + k;
+      if (J < c) {
+        const T t = D.tm[J];
+        a = fma(-t, a, r[J]);
+        m = -t * m;
+      }
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const T pa = __shfl_up_sync(0xffffffffu, a, off), pm = __shfl_up_sync(0xffffffffu, m, off);
+      if (lane >= off) {
+        a = fma(m, pa, a);
+        m *= pm;
+      }
+    }
+    T prev = __shfl_up_sync(0xffffffffu, a, 1);
+    if (lane == 0) prev = T(0);
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const int J = j0 + k;
+      if (J < c) {
+        y[k] = fma(-D.tm[J], prev, r[J]);
+        prev = y[k];
+      }
+    }
+    // backward recurrence z_J = (y_J - tsup_J z_{J+1}) tib_J (z_c = 0)
+    a = T(0);
+    m = T(1);
+#pragma unroll
+    for (int k = E - 1; k >= 0; --k) {
+      const int J = j0 + k;
+      if (J < c) {
+        const T ib = D.tib[J], q = -D.tsup[J] * ib;
+        a = fma(q, a, y[k] * ib);
+        m = q * m;
+      }
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const T pa = __shfl_down_sync(0xffffffffu, a, off), pm = __shfl_down_sync(0xffffffffu, m, off);
+      if (lane + off < 32) {
+        a = fma(m, pa, a);
+        m *= pm;
+      }
+    }
+    T next = __shfl_down_sync(0xffffffffu, a, 1);
+    if (lane == 31) next = T(0);
+    __syncwarp();  // every lane has read its r before any z overwrites it
+#pragma unroll
+    for (int k = E - 1; k >= 0; --k) {
+      const int J = j0 + k;
+      if (J < c) {
+        next = fma(-D.tsup[J], next, y[k]) * D.tib[J];
+        r[J] = next;
+      }
+    }
+  }
+  __syncthreads();
+  auto emit = [&](int J, int w) {
+    const int64_t col = col0 + w;
+    const int64_t o = b * S.out_b + (int64_t)J * S.out_j + col * S.out_c;
+    const T z = s_out[w * sc + J];
+    if (FINAL == 1) {
+      const int c2 = L.d[2].c, j1 = (int)(col / c2), j2 = (int)(col - (int64_t)j1 * c2);
+      const int64_t u = ((int64_t)L.d[0].cidx[J] * L.d[1].n + L.d[1].cidx[j1]) * L.d[2].n + L.d[2].cidx[j2];
+      out[o] = U[u] + z;
+    } else if (FINAL == 2) {
+      out[o] = U[o] - z;
+    } else {
+      out[o] = z;
+    }
+  };
+  if (S.out_j == 1) {
+    for (int w = warp; w < nl; w += 8)
+      for (int J = lane; J < c; J += 32) emit(J, w);
+  } else {
+    for (int e = threadIdx.x; e < c * LT; e += 256) {
+      const int J = e / LT, w = e - J * LT;
+      if (w < nl) emit(J, w);
+    }
+  }
+}
+
 // Inverse: dequantised coefficients into a full grid (0 at all-coarse nodes).
 template <typename T, int MODE>
 __global__ void gl_inv_dequant(GLevel<T> L, const uint16_t* __restrict__ sym, const int32_t* __restrict__ esc,
@@ -271,11 +419,7 @@ __global__ void gl_inv_interp(GLevel<T> L, const T* __restrict__ Uc, T* __restri
 // Coarsest array: quantised directly (mode 0) or stored (mode 1).
 template <typename T, int MODE>
 __global__ void coarsest_fwd(const T* __restrict__ U, int64_t count, int64_t sym_off, uint16_t* sym, int32_t* esc,
-                             T* coef, const T* rq_ptr, unsigned* hist, int radius, Scalars* sc) {
-  __shared__ unsigned hloc[kHistWin];
-  if (MODE == 0)
-    for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) hloc[i] = 0;
-  __syncthreads();
+                             T* coef, const T* rq_ptr, int radius, Scalars* sc) {
   const T rq = MODE == 0 ? *rq_ptr : T(0);
   bool ovf = false;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
@@ -285,22 +429,11 @@ __global__ void coarsest_fwd(const T* __restrict__ U, int64_t count, int64_t sym
       const unsigned sv = in ? (unsigned)(code + radius) : 0u;
       sym[sym_off + i] = (uint16_t)sv;
       if (!in) esc[sym_off + i] = code;
-      const int bin = (int)sv - (radius - kHistWin / 2);
-      if (bin >= 0 && bin < kHistWin) atomicAdd(hloc + bin, 1u);
-      else atomicAdd(hist + sv, 1u);
     } else {
       coef[sym_off + i] = U[i];
     }
   }
-  if (MODE == 0) {
-    if (ovf) atomicOr(&sc->status, ST_OVERFLOW);
-    __syncthreads();
-    const int lo = radius - kHistWin / 2;
-    for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) {
-      const unsigned v = hloc[i];
-      if (v && lo + i >= 0 && lo + i < 2 * radius) atomicAdd(hist + lo + i, v);
-    }
-  }
+  if (MODE == 0 && ovf) atomicOr(&sc->status, ST_OVERFLOW);
 }
 
 template <typename T, int MODE>

@@ -460,6 +460,9 @@ __global__ void hist_kernel(const uint16_t* __restrict__ sym, unsigned long long
 #ifndef BM_HIST_METHOD
 #define BM_HIST_METHOD 1
 #endif
+#ifndef BM_HIST_INFLIGHT
+#define BM_HIST_INFLIGHT 8
+#endif
 __global__ void __launch_bounds__(256) hist_range_kernel(const uint16_t* __restrict__ sym, unsigned long long s0,
                                                          unsigned long long s1, int dict, unsigned centre_sym,
                                                          unsigned* hist) {
@@ -487,11 +490,22 @@ __global__ void __launch_bounds__(256) hist_range_kernel(const uint16_t* __restr
   for (unsigned long long i = s0 + tid; i < a0; i += nth) count(sym[i]);
   const unsigned long long nv = (s1 - a0) / 8;
   const uint4* pv = reinterpret_cast<const uint4*>(sym + a0);
-  for (unsigned long long v = tid; v < nv; v += nth) {
-    const uint4 q = __ldg(pv + v);
-    const unsigned w4[4] = {q.x, q.y, q.z, q.w};
+  // BM_HIST_INFLIGHT 16-byte loads per thread are issued before any is counted
+  constexpr int NF = BM_HIST_INFLIGHT;
+  for (unsigned long long v = tid; v < nv; v += NF * nth) {
+    uint4 q[NF];
 #pragma unroll
-    for (int h = 0; h < 4; ++h) { count(w4[h] & 0xFFFFu); count(w4[h] >> 16); }
+    for (int f = 0; f < NF; ++f) {
+      const unsigned long long vf = v + f * nth;
+      q[f] = vf < nv ? __ldg(pv + vf) : make_uint4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      if (v + f * nth >= nv) break;
+      const unsigned w4[4] = {q[f].x, q[f].y, q[f].z, q[f].w};
+#pragma unroll
+      for (int h = 0; h < 4; ++h) { count(w4[h] & 0xFFFFu); count(w4[h] >> 16); }
+    }
   }
   for (unsigned long long i = a0 + nv * 8 + tid; i < s1; i += nth) count(sym[i]);
 #pragma unroll
