@@ -362,7 +362,7 @@ GSizes gsizes(const PlanHost& h) {
 }
 
 // cudaFuncAttributeMaxDynamicSharedMemorySize set once per device for a kernel.
-std::atomic<unsigned> g_cb_attr{0}, g_dt_attr{0};
+std::atomic<unsigned> g_cb_attr{0}, g_dt_attr{0}, g_dec_attr{0};
 template <class F>
 cudaError_t set_smem_once(F* fn, int bytes, std::atomic<unsigned>& done) {
   int dev = 0;
@@ -1224,7 +1224,8 @@ bm_status decode_symbols(const uint8_t* in, const Header& H, Carver& cv, uint16_
     da.n_words = H.n_words; da.word_off = word_off; da.nch = H.n_chunks; da.n = H.n_symbols; da.chunk = H.chunk;
     da.splits = reinterpret_cast<const uint16_t*>(in + H.off_splits);
     da.tab = dt; da.sym = sym; da.sc = sc;
-    decode_kernel<<<grid_for((int64_t)H.n_chunks * kSplits, 128, 16), 128, 0, s>>>(da);
+    BM_CUDA(set_smem_once(decode_kernel, (int)kDecSmem, g_dec_attr));
+    decode_kernel<<<grid_for((int64_t)H.n_chunks * kSplits, kDecThreads, 3), kDecThreads, kDecSmem, s>>>(da);
     BM_LAUNCHED();
     if (stream_mode && H.n_outliers) {
       escape_fixup_kernel<<<grid_for((int64_t)H.n_chunks * 32, 256, 8), 256, 0, s>>>(

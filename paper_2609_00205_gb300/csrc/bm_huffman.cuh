@@ -16,7 +16,7 @@
 namespace bm {
 
 constexpr int kCbThreads = 1024;
-constexpr int kLutBits = 12;
+constexpr int kLutBits = 14;
 // Every chunk is split into eight equal runs; the stream stores the bit
 // offsets of runs 1..7 so that eight decoders can work on one chunk.
 constexpr int kSplits = 8;
@@ -33,7 +33,7 @@ struct CanonTables {
 
 struct DecodeTables {
   CanonTables ct;
-  unsigned lut[1 << kLutBits];  // sym | len << 16 for codes of <= kLutBits bits, 0 otherwise
+  alignas(16) unsigned lut[1 << kLutBits];  // sym | len << 16 for codes of <= kLutBits bits, 0 otherwise
   uint16_t canon[kMaxDict];     // symbols in canonical order
 };
 
@@ -578,20 +578,26 @@ __device__ __forceinline__ void code_of(const unsigned* codes, const uint8_t* le
 // Bits and escape mask of a lane's vector slice (G groups held in registers).
 // CLAMP: symbols may be out of the dictionary (caller-supplied) and are
 // clamped; the compressor's own symbols are in range by construction.
-template <bool PACKED, bool CLAMP>
+template <bool PACKED, bool CLAMP, int GC>
 __device__ __forceinline__ void slice_bits(const uint4* q, int G, unsigned dmax, const unsigned* codes,
                                            const uint8_t* lens, unsigned& bits, unsigned long long& emask) {
   bits = 0;
-  emask = 0;
+  unsigned nz = 0;
 #pragma unroll
   for (int i = 0; i < 8 * kEncGroups; ++i) {
-    if ((i >> 3) < G) {
+    if ((i >> 3) < (GC ? GC : G)) {
       const unsigned s = CLAMP ? min(sym_of(q, i), dmax) : sym_of(q, i);
-      unsigned c, L;
-      code_of<PACKED>(codes, lens, s, c, L);
-      bits += L;
-      emask |= (unsigned long long)(s == 0) << i;
+      bits += PACKED ? (codes[s] >> 26) : (unsigned)lens[s];
+      nz += s == 0;
     }
+  }
+  emask = 0;
+  if (nz) {  // escapes (symbol 0): their positions, for the outlier codes
+    unsigned em[2] = {0u, 0u};
+#pragma unroll
+    for (int i = 0; i < 8 * kEncGroups; ++i)
+      if ((i >> 3) < (GC ? GC : G)) em[i >> 5] |= (unsigned)(sym_of(q, i) == 0) << (i & 31);
+    emask = ((unsigned long long)em[1] << 32) | em[0];
   }
 }
 
@@ -600,26 +606,35 @@ __device__ __forceinline__ void slice_bits(const uint4* q, int G, unsigned dmax,
 // word is stored through `wp` as soon as it fills.  The lane's first word may
 // start with the previous lane's last bits: it is stored with zeros there and
 // the previous lane ORs its bits in afterwards.
-template <bool PACKED, bool CLAMP>
+template <bool PACKED, bool CLAMP, int GC>
 __device__ __forceinline__ void slice_pack(const uint4* q, int G, unsigned dmax, const unsigned* codes,
                                            const uint8_t* lens, unsigned* wp, unsigned nb,
                                            unsigned long long& acc_out, unsigned& nb_out, unsigned*& wp_out) {
-  unsigned long long acc = 0;
+  // acc = hi:lo; packed codes have at most 26 bits, so the shifts stay below
+  // 32 and each is one funnel shift (and a plain shift of the low word)
+  unsigned hi = 0, lo = 0;
 #pragma unroll
   for (int i = 0; i < 8 * kEncGroups; ++i) {
-    if ((i >> 3) < G) {
+    if ((i >> 3) < (GC ? GC : G)) {
       const unsigned s = CLAMP ? min(sym_of(q, i), dmax) : sym_of(q, i);
       unsigned c, L;
       code_of<PACKED>(codes, lens, s, c, L);
-      acc = (acc << L) | c;
+      if (PACKED) {
+        hi = __funnelshift_l(lo, hi, L);
+        lo = (lo << L) | c;
+      } else {
+        const unsigned long long acc = ((((unsigned long long)hi << 32) | lo) << L) | c;
+        hi = (unsigned)(acc >> 32);
+        lo = (unsigned)acc;
+      }
       nb += L;
       if (nb >= 32u) {
         nb -= 32u;
-        *wp++ = (unsigned)(acc >> nb);
+        *wp++ = __funnelshift_r(lo, hi, nb);
       }
     }
   }
-  acc_out = acc;
+  acc_out = ((unsigned long long)hi << 32) | lo;
   nb_out = nb;
   wp_out = wp;
 }
@@ -677,8 +692,14 @@ __global__ void __launch_bounds__(WARPS * 32, 4) encode_fused_kernel(FusedEncode
       const uint4* p = reinterpret_cast<const uint4*>(a.sym + s0);
 #pragma unroll
       for (int g = 0; g < kEncGroups; ++g) q[g] = g < G ? __ldg(p + g) : make_uint4(0, 0, 0, 0);
-      if (packed) slice_bits<true, CLAMP>(q, G, dmax, codes, lens, bits, emask);
-      else slice_bits<false, CLAMP>(q, G, dmax, codes, lens, bits, emask);
+      // G is 8 at the default chunk of 2048 symbols: a fully unrolled slice
+      if (G == kEncGroups) {
+        if (packed) slice_bits<true, CLAMP, kEncGroups>(q, G, dmax, codes, lens, bits, emask);
+        else slice_bits<false, CLAMP, kEncGroups>(q, G, dmax, codes, lens, bits, emask);
+      } else {
+        if (packed) slice_bits<true, CLAMP, 0>(q, G, dmax, codes, lens, bits, emask);
+        else slice_bits<false, CLAMP, 0>(q, G, dmax, codes, lens, bits, emask);
+      }
       nesc = __popcll(emask);
     } else {
       for (int t = 0; t < cnt; ++t) {
@@ -801,8 +822,15 @@ __global__ void __launch_bounds__(WARPS * 32, 4) encode_fused_kernel(FusedEncode
       unsigned long long acc;
       unsigned nb;
       unsigned* wp;
-      if (packed) slice_pack<true, CLAMP>(q, G, dmax, codes, lens, words + head_idx, bit0 & 31u, acc, nb, wp);
-      else slice_pack<false, CLAMP>(q, G, dmax, codes, lens, words + head_idx, bit0 & 31u, acc, nb, wp);
+      unsigned* const w0 = words + head_idx;
+      const unsigned nb0 = bit0 & 31u;
+      if (G == kEncGroups) {
+        if (packed) slice_pack<true, CLAMP, kEncGroups>(q, G, dmax, codes, lens, w0, nb0, acc, nb, wp);
+        else slice_pack<false, CLAMP, kEncGroups>(q, G, dmax, codes, lens, w0, nb0, acc, nb, wp);
+      } else {
+        if (packed) slice_pack<true, CLAMP, 0>(q, G, dmax, codes, lens, w0, nb0, acc, nb, wp);
+        else slice_pack<false, CLAMP, 0>(q, G, dmax, codes, lens, w0, nb0, acc, nb, wp);
+      }
       // every lane holds >= 32 bits, so the word of its last bits is the next
       // lane's first word (already stored, zeros in these bits); the last
       // lane's last word is its own
@@ -912,17 +940,21 @@ __global__ void __launch_bounds__(kCbThreads) decode_tables_kernel(const uint8_t
     return;
   }
   build_canonical(S.len, dict, S.key32, S.canon, &S.ct, S.scan_tmp);
-  for (int i = threadIdx.x; i < (1 << kLutBits); i += blockDim.x) out->lut[i] = 0;
   for (int i = threadIdx.x; i < (int)S.ct.n; i += blockDim.x) out->canon[i] = S.canon[i];
   __syncthreads();
-  for (int i = threadIdx.x; i < (int)S.ct.n; i += blockDim.x) {
-    const int s = S.canon[i];
-    const unsigned L = S.len[s];
+  // every LUT entry from its own bits: the length is the first whose
+  // left-justified limit lies above them (canonical order), the symbol that
+  // code's canonical rank
+  for (int p = threadIdx.x; p < (1 << kLutBits); p += blockDim.x) {
+    const unsigned long long peek = (unsigned long long)p << (32 - kLutBits);
+    unsigned L = 1;
+    while (L <= (unsigned)kLutBits && peek >= S.ct.limit[L]) ++L;
+    unsigned e = 0;
     if (L <= (unsigned)kLutBits) {
-      const unsigned code = S.ct.first_code[L] + (unsigned)(i - (int)S.ct.first_pos[L]);
-      const unsigned b0 = code << (kLutBits - L), cnt = 1u << (kLutBits - L);
-      for (unsigned t = 0; t < cnt; ++t) out->lut[b0 + t] = (unsigned)s | (L << 16);
+      const unsigned idx = S.ct.first_pos[L] + (((unsigned)peek >> (32 - L)) - S.ct.first_code[L]);
+      if (idx < S.ct.n) e = (unsigned)S.canon[idx] | (L << 16);
     }
+    out->lut[p] = e;
   }
   if (threadIdx.x == 0) out->ct = S.ct;
 }
@@ -941,22 +973,36 @@ struct DecodeArgs {
 };
 
 // One thread per run (an eighth of a chunk): table-driven canonical decoding
-// with a 64-bit window and a one-word look-ahead.  A run must end exactly
-// where the next one starts (the last run of a chunk within the chunk).
-__global__ void __launch_bounds__(128) decode_kernel(DecodeArgs a) {
-  __shared__ unsigned lut[1 << kLutBits];
-  __shared__ uint16_t canon[kMaxDict];
-  __shared__ unsigned long long limit[kMaxLen + 2];
-  __shared__ unsigned fcode[kMaxLen + 2], fpos[kMaxLen + 2];
+// with a 64-bit window refilled a word at a time from registers loaded ahead
+// in 16-byte groups, sixteen symbols per step stored as one 32-byte sector.  Codes of at most
+// kLutBits bits (nearly all) take one shared-memory lookup; longer ones walk
+// the left-justified limits.  A run must end exactly where the next one
+// starts (the last run of a chunk within the chunk); reading past the chunk
+// reads zeros and shows in that check.  Persistent CTAs: the tables are
+// staged once per CTA.
+constexpr int kDecThreads = 256;
+constexpr size_t kDecSmem = sizeof(unsigned) * (1u << kLutBits) + sizeof(unsigned long long) * (kMaxLen + 2) +
+                            2 * sizeof(unsigned) * (kMaxLen + 2);
+
+__global__ void __launch_bounds__(kDecThreads) decode_kernel(DecodeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned* lut = reinterpret_cast<unsigned*>(smem_raw);
+  unsigned long long* limit = reinterpret_cast<unsigned long long*>(lut + (1 << kLutBits));
+  unsigned* fcode = reinterpret_cast<unsigned*>(limit + kMaxLen + 2);
+  unsigned* fpos = fcode + kMaxLen + 2;
   const DecodeTables* T = a.tab;
-  for (int i = threadIdx.x; i < (1 << kLutBits); i += blockDim.x) lut[i] = T->lut[i];
-  const unsigned nsym = T->ct.n;
-  for (int i = threadIdx.x; i < (int)nsym; i += blockDim.x) canon[i] = T->canon[i];
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(T->lut);
+    uint4* dst = reinterpret_cast<uint4*>(lut);
+    for (int i = threadIdx.x; i < (1 << kLutBits) / 4; i += blockDim.x) dst[i] = src[i];
+  }
   if (threadIdx.x < kMaxLen + 2) {
     limit[threadIdx.x] = T->ct.limit[threadIdx.x];
     fcode[threadIdx.x] = T->ct.first_code[threadIdx.x];
     fpos[threadIdx.x] = T->ct.first_pos[threadIdx.x];
   }
+  const unsigned nsym = T->ct.n;
+  const uint16_t* canon = T->canon;
   __syncthreads();
   const unsigned long long nruns = a.nch * kSplits;
   const int sub = a.chunk / kSplits;
@@ -971,60 +1017,90 @@ __global__ void __launch_bounds__(128) decode_kernel(DecodeArgs a) {
     const unsigned long long b1 = k < kSplits - 1 ? a.splits[c * (kSplits - 1) + k] : cbits;
     if (b0 > b1 || b1 > cbits) { atomicOr(&a.sc->status, ST_CORRUPT); continue; }
     const unsigned long long s0 = c * (unsigned long long)a.chunk + (unsigned long long)k * sub;
-    const unsigned long long s1 = min(a.n, s0 + (unsigned long long)sub);
-    // window: bits from bit position pos = cw0*32 + b0 on
-    unsigned long long w = cw0 + (b0 >> 5);
-    const unsigned long long wend = cw1;
-    const int skip = (int)(b0 & 31);
-    unsigned long long buf = 0;
-    int nbits = 0;
-    unsigned nextw = w < wend ? __ldg(a.words + w) : 0u;
-    auto refill = [&]() {
-      if (nbits <= 32 && w < wend) {
-        buf |= (unsigned long long)nextw << (32 - nbits);
-        nbits += 32;
-        ++w;
-        nextw = w < wend ? __ldg(a.words + w) : 0u;
-      }
+    const int cnt = (int)(min(a.n, s0 + (unsigned long long)sub) - s0);
+    // words enter the window from a queue (c0..c3, cl of them valid) filled
+    // from aligned 16-byte groups, the next group (n) in flight; a group is
+    // read as one vector unless it reaches past the bitstream (words past a
+    // chunk's end are never consumed by a valid run and show in the check below)
+    const unsigned* const wall = a.words + a.n_words;
+    auto ld = [&](const unsigned* q) { return q < wall ? __ldg(q) : 0u; };
+    auto ld4 = [&](const unsigned* g) {
+      if (g + 4 <= wall) return __ldg(reinterpret_cast<const uint4*>(g));
+      return make_uint4(ld(g), ld(g + 1), ld(g + 2), ld(g + 3));
     };
-    refill();
-    refill();
-    buf <<= skip;
-    nbits -= skip;
-    unsigned long long used = b0;  // bits consumed, from the chunk start
+    const unsigned* gp = a.words + cw0 + (b0 >> 5);
+    const unsigned w0 = ld(gp), w1 = ld(gp + 1);
+    gp += 2;
+    const int m = (int)((reinterpret_cast<uintptr_t>(gp) >> 2) & 3);
+    const unsigned* gq = gp - m;  // 16-byte aligned
+    const uint4 A = ld4(gq);
+    uint4 n = ld4(gq + 4);
+    gq += 8;
+    unsigned c0 = m == 0 ? A.x : m == 1 ? A.y : m == 2 ? A.z : A.w;
+    unsigned c1 = m == 0 ? A.y : m == 1 ? A.z : A.w;
+    unsigned c2 = m == 0 ? A.z : A.w;
+    unsigned c3 = A.w;
+    int cl = 4 - m;
+    const int skip = (int)(b0 & 31);
+    unsigned long long buf = (((unsigned long long)w0 << 32) | w1) << skip;
+    int nbits = 64 - skip;
+    unsigned nwords = 2;  // words entered into the window
     bool bad = false;
-    unsigned long long pack = 0;
-    for (unsigned long long i = s0; i < s1; ++i) {
-      refill();
-      const unsigned peek = (unsigned)(buf >> 32);
-      const unsigned e = lut[peek >> (32 - kLutBits)];
-      unsigned s, L;
-      if (e >> 16) {
-        L = e >> 16;
-        s = e & 0xFFFFu;
-      } else {
-        L = kLutBits + 1;
-        while (L <= (unsigned)kMaxLen && (unsigned long long)peek >= limit[L]) ++L;
-        if (L > (unsigned)kMaxLen) { bad = true; break; }
-        const unsigned idx = fpos[L] + ((peek >> (32 - L)) - fcode[L]);
-        if (idx >= nsym) { bad = true; break; }
-        s = canon[idx];
+    auto one = [&]() -> unsigned {
+      if (nbits <= 32) {
+        buf |= (unsigned long long)c0 << (32 - nbits);
+        nbits += 32;
+        ++nwords;
+        c0 = c1;
+        c1 = c2;
+        c2 = c3;
+        if (--cl == 0) {
+          c0 = n.x;
+          c1 = n.y;
+          c2 = n.z;
+          c3 = n.w;
+          n = ld4(gq);
+          gq += 4;
+          cl = 4;
+        }
       }
-      if ((int)L > nbits) { bad = true; break; }
+      const unsigned peek = (unsigned)(buf >> 32);
+      unsigned e = lut[peek >> (32 - kLutBits)];
+      if (e == 0u) {  // a code longer than kLutBits bits
+        unsigned L = kLutBits + 1;
+        while (L <= (unsigned)kMaxLen && (unsigned long long)peek >= limit[L]) ++L;
+        const unsigned idx = L <= (unsigned)kMaxLen ? fpos[L] + ((peek >> (32 - L)) - fcode[L]) : nsym;
+        if (idx >= nsym) {
+          bad = true;
+          e = 1u << 16;
+        } else {
+          e = (unsigned)canon[idx] | (L << 16);
+        }
+      }
+      const unsigned L = e >> 16;
       buf <<= L;
       nbits -= (int)L;
-      used += L;
-      pack |= (unsigned long long)s << (16 * (i & 3));
-      if ((i & 3) == 3) {
-        *reinterpret_cast<unsigned long long*>(a.sym + (i - 3)) = pack;
-        pack = 0;
+      return e & 0xFFFFu;
+    };
+    uint16_t* out = a.sym + s0;
+    int i = 0;
+    if ((reinterpret_cast<uintptr_t>(out) & 31) == 0) {  // sixteen symbols: one whole 32-byte sector
+      for (; i + 16 <= cnt; i += 16) {
+        unsigned v[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const unsigned lo = one();
+          v[t] = lo | (one() << 16);
+        }
+        uint4* o = reinterpret_cast<uint4*>(out + i);
+        o[0] = make_uint4(v[0], v[1], v[2], v[3]);
+        o[1] = make_uint4(v[4], v[5], v[6], v[7]);
       }
     }
-    if (!bad && (s1 & 3) && s1 > s0) {
-      for (unsigned long long i = max(s0, s1 & ~3ull); i < s1; ++i) a.sym[i] = (uint16_t)(pack >> (16 * (i & 3)));
-    }
-    if (!bad && (k < kSplits - 1 ? used != b1 : used > b1)) bad = true;
-    if (bad) atomicOr(&a.sc->status, ST_CORRUPT);
+    for (; i < cnt; ++i) out[i] = (uint16_t)one();
+    // bits consumed from the chunk start
+    const unsigned long long used = b0 + (unsigned long long)nwords * 32ull - (unsigned long long)skip - nbits;
+    if (bad || (k < kSplits - 1 ? used != b1 : used > b1)) atomicOr(&a.sc->status, ST_CORRUPT);
   }
 }
 
