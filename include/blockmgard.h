@@ -117,6 +117,20 @@ bm_status bm_decompose(const void* d_field, int ndim, const int64_t* shape, bm_d
 bm_status bm_recompose(const void* d_coeffs, int ndim, const int64_t* shape, bm_dtype dtype,
                        const bm_params* params, void* d_field, void* stream);
 
+/* Adjoints (transposes) of the two linear operators above, for gradients
+ * (Sec. II-B: each level is linear; its transpose is built from M_f I M_c^-1
+ * and I^T along each dimension).  bm_decompose_adjoint: d_coeff_grad
+ * (n_coeffs values, stream order, read) -> d_field_grad (the field's shape,
+ * written; nodes outside the domain of a padded block have no field entry
+ * and receive nothing).  bm_recompose_adjoint: d_field_grad (read) ->
+ * d_coeff_grad (n_coeffs, written).  Same dtype, parameters and errors as
+ * bm_decompose; both run asynchronously on `stream` and allocate nothing
+ * beyond the cached workspace. */
+bm_status bm_decompose_adjoint(const void* d_coeff_grad, int ndim, const int64_t* shape, bm_dtype dtype,
+                               const bm_params* params, void* d_field_grad, void* stream);
+bm_status bm_recompose_adjoint(const void* d_field_grad, int ndim, const int64_t* shape, bm_dtype dtype,
+                               const bm_params* params, void* d_coeff_grad, void* stream);
+
 /* Number of coefficients (= quantised symbols) for a shape and parameters. */
 bm_status bm_coeff_count(int ndim, const int64_t* shape, const bm_params* params, size_t* n_coeffs);
 

@@ -120,6 +120,44 @@ def recompose(coef, shape, B, K, M):
     return u
 
 
+def decompose_matrix(shape, B, K, M):
+    """The decomposition as an explicit matrix (n_coeffs x prod(shape)), built
+    column by column from unit inputs: the plain definition of the operator
+    whose transpose the adjoint kernels must equal (small grids only)."""
+    shape = tuple(int(v) for v in shape)
+    n = int(np.prod(shape))
+    A = np.zeros((plan(shape, B, K, M)["n_coeffs"], n))
+    e = np.zeros(n)
+    for j in range(n):
+        e[j] = 1.0
+        A[:, j] = decompose(e.reshape(shape), B, K, M)
+        e[j] = 0.0
+    return A
+
+
+def recompose_matrix(shape, B, K, M):
+    """The recomposition as an explicit matrix (prod(shape) x n_coeffs)."""
+    shape = tuple(int(v) for v in shape)
+    nc = plan(shape, B, K, M)["n_coeffs"]
+    R = np.zeros((int(np.prod(shape)), nc))
+    e = np.zeros(nc)
+    for j in range(nc):
+        e[j] = 1.0
+        R[:, j] = recompose(e, shape, B, K, M).ravel()
+        e[j] = 0.0
+    return R
+
+
+def decompose_adjoint(coef_grad, shape, B, K, M):
+    """Transpose of the decomposition applied to coefficient gradients."""
+    return (decompose_matrix(shape, B, K, M).T @ np.asarray(coef_grad, dtype=np.float64)).reshape(shape)
+
+
+def recompose_adjoint(field_grad, shape, B, K, M):
+    """Transpose of the recomposition applied to field gradients."""
+    return recompose_matrix(shape, B, K, M).T @ np.asarray(field_grad, dtype=np.float64).ravel()
+
+
 def block_coeffs(u, B, K, block):
     u = np.ascontiguousarray(np.asarray(u, dtype=np.float64))
     p = plan(u.shape, B, K, 0)

@@ -17,7 +17,8 @@ from . import _build
 __all__ = [
     "BM_F32", "BM_F64", "BlockMGARDError", "load", "compress", "decompress", "decompose", "recompose",
     "coeff_count", "stream_info", "stream_codes", "huffman_encode", "huffman_decode", "compress_bound",
-    "set_timing", "stage_times", "stage_timeline", "launch_count", "release_workspace", "library_path",
+    "set_timing", "stage_times", "stage_timeline", "decompose_adjoint", "recompose_adjoint", "Decompose",
+    "Recompose", "decompose_ad", "recompose_ad", "launch_count", "release_workspace", "library_path",
 ]
 
 BM_F32, BM_F64 = 0, 1
@@ -65,6 +66,8 @@ def load():
     L.bm_decompress.argtypes = [vp, sz, vp, vp]
     L.bm_decompose.argtypes = [vp, ctypes.c_int, P(i64), ctypes.c_int, P(_Params), vp, vp]
     L.bm_recompose.argtypes = [vp, ctypes.c_int, P(i64), ctypes.c_int, P(_Params), vp, vp]
+    L.bm_decompose_adjoint.argtypes = [vp, ctypes.c_int, P(i64), ctypes.c_int, P(_Params), vp, vp]
+    L.bm_recompose_adjoint.argtypes = [vp, ctypes.c_int, P(i64), ctypes.c_int, P(_Params), vp, vp]
     L.bm_coeff_count.argtypes = [ctypes.c_int, P(i64), P(_Params), P(sz)]
     L.bm_stream_codes.argtypes = [vp, sz, vp, vp]
     L.bm_huffman_encode.argtypes = [vp, u64, ctypes.c_int, ctypes.c_int, vp, sz, P(u64), vp]
@@ -207,6 +210,75 @@ def recompose(coeffs: torch.Tensor, shape, block=17, levels=2, global_levels=2, 
         _check(load().bm_recompose(ctypes.c_void_p(coeffs.data_ptr()), 3, _shape(shape), _dtype(coeffs.dtype),
                                    ctypes.byref(p), ctypes.c_void_p(out.data_ptr()), _stream(stream)))
     return out
+
+
+def decompose_adjoint(coeff_grad: torch.Tensor, shape, block=17, levels=2, global_levels=2,
+                      stream=None) -> torch.Tensor:
+    """Transpose of :func:`decompose` applied to coefficient gradients: the
+    gradient with respect to the field (the field's shape)."""
+    _dev_check(coeff_grad)
+    if coeff_grad.numel() != coeff_count(shape, block, levels, global_levels):
+        raise ValueError("coefficient gradient has the wrong length")
+    out = torch.empty(tuple(shape), dtype=coeff_grad.dtype, device=coeff_grad.device)
+    p = _params(block, levels, global_levels)
+    with torch.cuda.device(coeff_grad.device):
+        _check(load().bm_decompose_adjoint(ctypes.c_void_p(coeff_grad.data_ptr()), 3, _shape(shape),
+                                           _dtype(coeff_grad.dtype), ctypes.byref(p), ctypes.c_void_p(out.data_ptr()),
+                                           _stream(stream)))
+    return out
+
+
+def recompose_adjoint(field_grad: torch.Tensor, block=17, levels=2, global_levels=2, stream=None) -> torch.Tensor:
+    """Transpose of :func:`recompose` applied to field gradients: the gradient
+    with respect to the coefficients (stream order)."""
+    _dev_check(field_grad)
+    if field_grad.dim() != 3:
+        raise ValueError("fields must be 3-D")
+    n = coeff_count(field_grad.shape, block, levels, global_levels)
+    out = torch.empty(n, dtype=field_grad.dtype, device=field_grad.device)
+    p = _params(block, levels, global_levels)
+    with torch.cuda.device(field_grad.device):
+        _check(load().bm_recompose_adjoint(ctypes.c_void_p(field_grad.data_ptr()), 3, _shape(field_grad.shape),
+                                           _dtype(field_grad.dtype), ctypes.byref(p), ctypes.c_void_p(out.data_ptr()),
+                                           _stream(stream)))
+    return out
+
+
+class Decompose(torch.autograd.Function):
+    """Differentiable decomposition: backward is the transposed operator (no
+    saved tensors: the operator is linear)."""
+
+    @staticmethod
+    def forward(ctx, field, block=17, levels=2, global_levels=2):
+        ctx.params = (tuple(field.shape), block, levels, global_levels)
+        return decompose(field.contiguous(), block, levels, global_levels)
+
+    @staticmethod
+    def backward(ctx, g):
+        shape, block, levels, global_levels = ctx.params
+        return decompose_adjoint(g.contiguous(), shape, block, levels, global_levels), None, None, None
+
+
+class Recompose(torch.autograd.Function):
+    """Differentiable recomposition: backward is the transposed operator."""
+
+    @staticmethod
+    def forward(ctx, coeffs, shape, block=17, levels=2, global_levels=2):
+        ctx.params = (block, levels, global_levels)
+        return recompose(coeffs.contiguous(), shape, block, levels, global_levels)
+
+    @staticmethod
+    def backward(ctx, g):
+        block, levels, global_levels = ctx.params
+        return recompose_adjoint(g.contiguous(), block, levels, global_levels), None, None, None, None
+
+
+def decompose_ad(field, block=17, levels=2, global_levels=2):
+    return Decompose.apply(field, block, levels, global_levels)
+
+
+def recompose_ad(coeffs, shape, block=17, levels=2, global_levels=2):
+    return Recompose.apply(coeffs, tuple(int(v) for v in shape), block, levels, global_levels)
 
 
 def stream_codes(buf: torch.Tensor, stream=None) -> torch.Tensor:

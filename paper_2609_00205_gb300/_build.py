@@ -23,6 +23,8 @@ CU_SOURCES = [
     "bm_block_f32_b17.cu",
     "bm_block_f64_b9.cu",
     "bm_block_f64_b17.cu",
+    "bm_adjoint_f32.cu",
+    "bm_adjoint_f64.cu",
 ]
 CPP_SOURCES = ["bm_plan.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../../include/blockmgard.h"
+#include "bm_adjoint.cuh"
 #include "bm_global.cuh"
 #include "bm_huffman.cuh"
 #include "bm_internal.h"
@@ -235,7 +236,7 @@ bm_status upload_tables(PlanDev& P) {
     if (bytes) std::memcpy(img.data() + off, src, bytes);
     return off;
   };
-  struct Offs { size_t cidx, jlo, jhi, wl, wr, cb, isc, proj, f0, band, tm, tib, tsup; };
+  struct Offs { size_t cidx, jlo, jhi, wl, wr, cb, isc, proj, f0, band, tm, tib, tsup, md, mo; };
   std::vector<Offs> offs;
   for (auto& L3 : P.h.glev)
     for (auto& D : L3) {
@@ -245,7 +246,7 @@ bm_status upload_tables(PlanDev& P) {
         return o;
       };
       std::vector<T> wl = cvt(D.wl), wr = cvt(D.wr), proj = cvt(D.P), band = cvt(D.band), tm = cvt(D.tm),
-                     tib = cvt(D.tib), tsup = cvt(D.tsup);
+                     tib = cvt(D.tib), tsup = cvt(D.tsup), md = cvt(D.md), mo = cvt(D.mo);
       Offs o;
       o.cidx = put(D.cidx.data(), D.cidx.size() * 4);
       o.jlo = put(D.jlo.data(), D.jlo.size() * 4);
@@ -260,6 +261,8 @@ bm_status upload_tables(PlanDev& P) {
       o.tm = put(tm.data(), tm.size() * sizeof(T));
       o.tib = put(tib.data(), tib.size() * sizeof(T));
       o.tsup = put(tsup.data(), tsup.size() * sizeof(T));
+      o.md = put(md.data(), md.size() * sizeof(T));
+      o.mo = put(mo.data(), mo.size() * sizeof(T));
       offs.push_back(o);
     }
   if (P.dtab[di]) { cudaFree(P.dtab[di]); P.dtab[di] = nullptr; }
@@ -291,6 +294,8 @@ bm_status upload_tables(PlanDev& P) {
       g.tm = reinterpret_cast<const T*>(base + o.tm);
       g.tib = reinterpret_cast<const T*>(base + o.tib);
       g.tsup = reinterpret_cast<const T*>(base + o.tsup);
+      g.md = reinterpret_cast<const T*>(base + o.md);
+      g.mo = reinterpret_cast<const T*>(base + o.mo);
     }
     L.sym_off = P.h.sym_off[l];
     G.push_back(L);
@@ -1289,6 +1294,115 @@ using namespace bm;
 // ===========================================================================
 // C ABI
 // ===========================================================================
+// ---------------------------------------------------------------------------
+// Transposed operators (adjoints of bm_decompose / bm_recompose)
+// ---------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_block_adj(int dir, int B, int K, const BlockArgs<T>& a, cudaStream_t s);
+template <>
+cudaError_t launch_block_adj<float>(int dir, int B, int K, const BlockArgs<float>& a, cudaStream_t s) {
+  BM_LAUNCHED();
+  return launch_block_adj_f32(dir, B, K, a, s, num_sms());
+}
+template <>
+cudaError_t launch_block_adj<double>(int dir, int B, int K, const BlockArgs<double>& a, cudaStream_t s) {
+  BM_LAUNCHED();
+  return launch_block_adj_f64(dir, B, K, a, s, num_sms());
+}
+
+// Expansion (M_f I M_c^-1) or restriction (I^T) along one dimension of a global level.
+template <typename T>
+void launch_gl_line(const GLevel<T>& L, int dim, bool expand, const T* in, T* out, cudaStream_t s) {
+  const LineShape S = line_shape(L, dim);
+  if (expand) {
+    gl_expand<T><<<grid_for(S.nb * S.ncol, 256), 256, 0, s>>>(L.d[dim], S, in, out);
+  } else {
+    gl_restrict_interp<T><<<grid_for(S.nb * S.ncol * L.d[dim].c, 256), 256, 0, s>>>(L.d[dim], S, in, out);
+  }
+  BM_LAUNCHED();
+}
+
+// dir 0: coefficient gradients (gcoef, read) -> field gradients (gfield, written);
+// dir 1: field gradients (gfield, read) -> coefficient gradients (gcoef, written).
+template <typename T>
+bm_status run_adjoint(PlanDev& P, int dir, T* gfield, T* gcoef, Carver& cv, cudaStream_t s) {
+  const PlanHost& h = P.h;
+  if (bm_status st = upload_tables<T>(P)) return st;
+  const GSizes gs = gsizes(h);
+  std::vector<T*> U;
+  for (int l = 0; l <= h.M; ++l) U.push_back(cv.take<T>((size_t)gs.U[l]));
+  T* Dbuf = cv.take<T>((size_t)gs.D);
+  T* W1 = cv.take<T>((size_t)std::max<int64_t>(gs.W1, 1));
+  T* W2 = cv.take<T>((size_t)std::max<int64_t>(gs.W2, 1));
+  auto& G = glevels<T>(P);
+  BlockArgs<T> a{};
+  a.field = gfield;
+  a.n0 = h.shape[0]; a.n1 = h.shape[1]; a.n2 = h.shape[2];
+  a.nb0 = h.nb[0]; a.nb1 = h.nb[1]; a.nb2 = h.nb[2];
+  a.nblocks = h.nblocks;
+  a.G = U[0];
+  a.g1 = h.gshape[1]; a.g2 = h.gshape[2];
+  a.coef = gcoef;
+  const int64_t ncoarsest = gs.U[h.M];
+  if (dir == 0) {
+    Stage st("adjoint_global");
+    BM_CUDA(cudaMemcpyAsync(U[h.M], gcoef + h.sym_off[h.M], (size_t)ncoarsest * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    for (int l = h.M - 1; l >= 0; --l) {
+      const GLevel<T>& L = G[l];
+      const int64_t nn = gs.U[l], nc = gs.U[l + 1];
+      // v = S_F^T g_D + P^T g_c
+      gl_inv_dequant<T, 1><<<grid_for(nn, 256), 256, 0, s>>>(L, nullptr, nullptr, gcoef, nullptr, 0, U[l]);
+      launch_gl_line<T>(L, 0, true, U[l + 1], W2, s);
+      launch_gl_line<T>(L, 1, true, W2, W1, s);
+      launch_gl_line<T>(L, 2, true, W1, Dbuf, s);
+      gl_axpy<T><<<grid_for(nn, 256), 256, 0, s>>>(U[l], Dbuf, nn);
+      // g_u = v + R_C^T (g_c - I^T v)
+      launch_gl_line<T>(L, 2, false, U[l], W1, s);
+      launch_gl_line<T>(L, 1, false, W1, W2, s);
+      launch_gl_line<T>(L, 0, false, W2, Dbuf, s);
+      gl_adj_correct<T><<<grid_for(nc, 256), 256, 0, s>>>(L, U[l], U[l + 1], Dbuf);
+      g_launches.fetch_add(3);
+      BM_CUDA(cudaGetLastError());
+    }
+  }
+  {
+    Stage st(dir == 0 ? "adjoint_incache_decompose" : "adjoint_incache_recompose");
+    BM_CUDA(launch_block_adj<T>(dir, h.B, h.K, a, s));
+  }
+  if (dir == 1) {
+    Stage st("adjoint_global");
+    for (int l = 0; l < h.M; ++l) {
+      const GLevel<T>& L = G[l];
+      const int64_t nn = gs.U[l];
+      // g_c = I^T g_u, then g_D = S_F (g_u - P^T g_c)
+      launch_gl_line<T>(L, 2, false, U[l], W1, s);
+      launch_gl_line<T>(L, 1, false, W1, W2, s);
+      launch_gl_line<T>(L, 0, false, W2, U[l + 1], s);
+      launch_gl_line<T>(L, 0, true, U[l + 1], W2, s);
+      launch_gl_line<T>(L, 1, true, W2, W1, s);
+      launch_gl_line<T>(L, 2, true, W1, Dbuf, s);
+      gl_adj_gather<T><<<grid_for(nn, 256), 256, 0, s>>>(L, U[l], Dbuf, gcoef);
+      g_launches.fetch_add(1);
+      BM_CUDA(cudaGetLastError());
+    }
+    BM_CUDA(cudaMemcpyAsync(gcoef + h.sym_off[h.M], U[h.M], (size_t)ncoarsest * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  }
+  return BM_OK;
+}
+
+template <typename T>
+bm_status adjoint_entry(int dir, const int64_t* shape, const Params& prm, T* gfield, T* gcoef, cudaStream_t s) {
+  PlanDev* P = nullptr;
+  if (bm_status st = get_plan(shape, prm.B, prm.K, prm.M, &P)) return st;
+  std::lock_guard<std::mutex> g(g_timer_mu);
+  g_timer.begin(s);
+  Workspace* ws = nullptr;
+  if (bm_status st = get_ws(s, decompose_scratch(P->h, sizeof(T)) + 4096, 4096, &ws)) return st;
+  Carver cv;
+  cv.base = reinterpret_cast<unsigned char*>(ws->d);
+  return run_adjoint<T>(*P, dir, gfield, gcoef, cv, s);
+}
+
 extern "C" {
 
 const char* bm_error_string(bm_status s) {
@@ -1451,6 +1565,34 @@ bm_status bm_recompose(const void* d_coeffs, int ndim, const int64_t* shape, bm_
   InvIn<float> in;
   in.coef = reinterpret_cast<const float*>(d_coeffs);
   return run_recompose<float>(*P, reinterpret_cast<float*>(d_field), 1, in, cv, s);
+}
+
+bm_status bm_decompose_adjoint(const void* d_coeff_grad, int ndim, const int64_t* shape, bm_dtype dtype,
+                               const bm_params* params, void* d_field_grad, void* stream) {
+  if (!d_coeff_grad || !d_field_grad) return fail(BM_ERR_ARG, "NULL pointer argument");
+  if (bm_status st = check_shape(ndim, shape)) return st;
+  Params prm;
+  if (bm_status st = check_params(params, prm)) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (dtype == BM_F64)
+    return adjoint_entry<double>(0, shape, prm, reinterpret_cast<double*>(d_field_grad),
+                                 const_cast<double*>(reinterpret_cast<const double*>(d_coeff_grad)), s);
+  return adjoint_entry<float>(0, shape, prm, reinterpret_cast<float*>(d_field_grad),
+                              const_cast<float*>(reinterpret_cast<const float*>(d_coeff_grad)), s);
+}
+
+bm_status bm_recompose_adjoint(const void* d_field_grad, int ndim, const int64_t* shape, bm_dtype dtype,
+                               const bm_params* params, void* d_coeff_grad, void* stream) {
+  if (!d_coeff_grad || !d_field_grad) return fail(BM_ERR_ARG, "NULL pointer argument");
+  if (bm_status st = check_shape(ndim, shape)) return st;
+  Params prm;
+  if (bm_status st = check_params(params, prm)) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (dtype == BM_F64)
+    return adjoint_entry<double>(1, shape, prm, const_cast<double*>(reinterpret_cast<const double*>(d_field_grad)),
+                                 reinterpret_cast<double*>(d_coeff_grad), s);
+  return adjoint_entry<float>(1, shape, prm, const_cast<float*>(reinterpret_cast<const float*>(d_field_grad)),
+                              reinterpret_cast<float*>(d_coeff_grad), s);
 }
 
 bm_status bm_stream_codes(const void* d_in, size_t in_bytes, int32_t* d_codes, void* stream) {

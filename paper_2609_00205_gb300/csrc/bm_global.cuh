@@ -28,6 +28,8 @@ struct GDim {
   const T* tm;          // [c] Thomas factors of M_c: y_J = r_J - tm_J y_{J-1},
   const T* tib;         //     z_J = (y_J - tsup_J z_{J+1}) tib_J
   const T* tsup;
+  const T* md;          // [n] diagonal of M_f
+  const T* mo;          // [n] mo[i] = M_f(i, i+1)
 };
 
 template <typename T>

@@ -41,4 +41,11 @@ cudaError_t launch_block_f64_b9(int dir, int K, int mode, const BlockArgs<double
 cudaError_t launch_block_f64_b17(int dir, int K, int mode, const BlockArgs<double>& a, cudaStream_t s, int nsm,
                                  int max_grid);
 
+// Transposed In-cache Block levels: dir 0 = transposed decomposition
+// (coefficient and block-coarse gradients -> field gradients), dir 1 =
+// transposed recomposition (field gradients -> coefficient and block-coarse
+// gradients).  cudaErrorInvalidValue for an unsupported (B, K).
+cudaError_t launch_block_adj_f32(int dir, int B, int K, const BlockArgs<float>& a, cudaStream_t s, int nsm);
+cudaError_t launch_block_adj_f64(int dir, int B, int K, const BlockArgs<double>& a, cudaStream_t s, int nsm);
+
 }  // namespace bm

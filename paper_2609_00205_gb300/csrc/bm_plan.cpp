@@ -60,6 +60,8 @@ Dim1DHost make_dim(const std::vector<double>& x) {
   }
   std::vector<double> md, mo;
   mass(x, md, mo);
+  D.md = md;
+  D.mo = mo;
   auto Mf = [&](int r, int c) -> double {
     if (r < 0 || c < 0 || r >= D.n || c >= D.n) return 0.0;
     if (r == c) return md[r];

@@ -18,6 +18,7 @@ struct Dim1DHost {
   std::vector<double> wl, wr;  // interpolation weights
   std::vector<double> band;    // [5c] rows of I^T M_f
   std::vector<double> tm, tib, tsup;  // Thomas factors of M_c
+  std::vector<double> md, mo;  // M_f: diagonal, and mo[i] = M_f(i, i+1) (adjoint passes)
   std::vector<double> P;       // [c x n] row-major: M_c^{-1} I^T M_f (global levels)
 };
 
