@@ -11,6 +11,8 @@ tolerance.  The field (540 MB) is larger than the L2 cache, so no flush is
 needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py --workload batch64    # 64 uneven fields: batched call vs per-field loop
+  python bench.py --workload diff257    # differentiable recompose: forward + backward
 
 Under torchrun (N > 1) every rank compresses its own field (seed + rank): the
 problems are independent, there is no collective on the data path, scaling
@@ -197,6 +199,169 @@ def cpu_baseline(u_np, edge):
                       % (edge, edge, edge, len(TOLS), dt)}
 
 
+def _batch64_fields(dev):
+    """64 seeded power-law GRFs of uneven shapes and dtypes with their own
+    relative tolerances (log-uniform in [1e-5, 1e-2]) and ROI maps (10 % of the
+    blocks at a 10x tighter tolerance).  The library is 3-D only, so the 24
+    planar fields of the batched workload (sides U[100, 2049]) are replaced by
+    3-D FP32 cubes of the same element count."""
+    import numpy as np
+    import torch
+
+    import fields
+
+    rng = np.random.default_rng(64)
+    specs = []
+    for _ in range(24):
+        a, b = rng.integers(100, 2050, size=2)
+        e = max(8, int(round((float(a) * float(b)) ** (1.0 / 3.0))))
+        specs.append(((e, e, e), torch.float32))
+    for _ in range(32):
+        specs.append((tuple(int(v) for v in rng.integers(33, 258, size=3)), torch.float32))
+    for _ in range(8):
+        specs.append(((129, 129, 129), torch.float64))
+    out = []
+    for i, (shape, dt) in enumerate(specs):
+        u = fields.power_law_grf(shape, exponent=float(rng.uniform(-4.0, -1.5)), seed=1000 + i, dtype=dt,
+                                 device=dev).contiguous()
+        tol = float(10 ** rng.uniform(-5, -2))
+        out.append((u, tol))
+    return out
+
+
+def _roi_maps(fs, block):
+    import numpy as np
+
+    rng = np.random.default_rng(65)
+    maps = []
+    for u, tol in fs:
+        nb = int(np.prod([(int(s) + block - 1) // block for s in u.shape]))
+        r = np.full(nb, tol)
+        r[rng.choice(nb, size=max(1, nb // 10), replace=False)] = tol / 10
+        maps.append(r)
+    return maps
+
+
+def run_batch64(args):
+    """Batched compress of 64 fields vs the per-field loop (same fields,
+    tolerances, ROI maps and parameters); the block size and in-cache levels
+    are picked by timing each candidate on the batch."""
+    import torch
+
+    import paper_2609_00205_gb300 as bm
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    bm.load()
+    fs = _batch64_fields(dev)
+    tols = [t for _, t in fs]
+    us = [u for u, _ in fs]
+    nbytes = sum(u.numel() * u.element_size() for u in us)
+    outs = [torch.empty(bm.compress_bound(u.shape, u.dtype), dtype=torch.uint8, device=dev) for u in us]
+
+    def batch(p, rois):
+        return bm.compress_batch(us, tols, rois=rois, outs=outs, **p)
+
+    def loop(p, rois):
+        return [bm.compress(u, t, roi=r, out=o, **p) for u, t, r, o in zip(us, tols, rois, outs)]
+
+    def timed(fn, p, rois, k):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        a.record()
+        for _ in range(k):
+            fn(p, rois)
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / k, (time.perf_counter() - t0) * 1e3 / k
+
+    # autotuner: block size and in-cache levels, one timed batch per candidate
+    cands = [dict(block=17, levels=2, global_levels=2), dict(block=9, levels=2, global_levels=2),
+             dict(block=17, levels=1, global_levels=2), dict(block=9, levels=1, global_levels=2)]
+    tune = []
+    for p in cands:
+        rois = _roi_maps(fs, p["block"])
+        batch(p, rois)
+        tune.append((timed(batch, p, rois, 2)[0], p))
+    best = min(tune, key=lambda z: z[0])[1]
+    rois = _roi_maps(fs, best["block"])
+    for _ in range(args.warmup):
+        batch(best, rois)
+        loop(best, rois)
+    b_ms, b_wall = timed(batch, best, rois, args.steps)
+    l_ms, l_wall = timed(loop, best, rois, args.steps)
+    res = batch(best, rois)
+    ref = loop(best, rois)
+    same = all(torch.equal(x, y) for x, y in zip(res, ref))
+    cr = nbytes / sum(x.numel() for x in res)
+    line = {"metric": "batched compress GB/s, 64 uneven fields (input bytes / time)", "workload": "batch64",
+            "value": nbytes / b_ms / 1e6, "unit": "GB/s", "higher_is_better": True,
+            "ms_per_batch": b_ms, "wall_ms_per_batch": b_wall, "loop_ms": l_ms, "loop_wall_ms": l_wall,
+            "speedup_vs_loop": l_ms / b_ms, "identical_streams": same, "cr": cr, "input_bytes": nbytes,
+            "params": best, "tuning_ms": [[round(t, 3), p] for t, p in tune], "steps": args.steps,
+            "warmup": args.warmup, "data": "synthetic",
+            "fields": "24 3-D FP32 cubes standing in for the planar fields, 32 3-D FP32 sides U[33,257], "
+                      "8 3-D FP64 129^3; tolerances log-uniform [1e-5,1e-2], ROI 10% of blocks at 10x tighter"}
+    print(json.dumps(line))
+
+
+def run_diff257(args):
+    """Differentiable recomposition on a 257^3 FP32 GRF: loss =
+    ||recompose(c) - target||^2 + 0.1 ||grad_x recompose(c)||^2, forward and
+    backward timed with CUDA events; the operators are linear, so their
+    backward needs no saved level (peak memory is that of the loss)."""
+    import torch
+
+    import fields
+    import paper_2609_00205_gb300 as bm
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    bm.load()
+    shape = (257, 257, 257)
+    u = fields.power_law_grf(shape, seed=7, dtype=torch.float32, device=dev).contiguous()
+    g = torch.Generator(device="cpu").manual_seed(8)
+    target = u + 0.05 * torch.randn(shape, generator=g).to(dev)
+    c0 = bm.decompose(u, **PARAMS)
+
+    def step():
+        c = c0.clone().requires_grad_(True)
+        x = bm.recompose_ad(c, shape, **PARAMS)
+        loss = ((x - target) ** 2).sum() + 0.1 * sum((torch.diff(x, dim=d) ** 2).sum() for d in range(3))
+        loss.backward()
+        return c.grad
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats(dev)
+    base = torch.cuda.memory_allocated(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        step()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    peak = torch.cuda.max_memory_allocated(dev) - base
+    # the operator pair alone: recompose + its adjoint
+    gx = torch.randn(shape, generator=g).to(dev)
+    a.record()
+    for _ in range(args.steps):
+        bm.recompose(c0, shape, **PARAMS)
+        bm.recompose_adjoint(gx, **PARAMS)
+    b.record()
+    torch.cuda.synchronize()
+    op_ms = a.elapsed_time(b) / args.steps
+    line = {"metric": "differentiable recompose, forward + backward ms (257^3 FP32)", "workload": "diff257",
+            "value": ms, "unit": "ms", "higher_is_better": False, "recompose_plus_adjoint_ms": op_ms,
+            "peak_extra_bytes": peak, "field_bytes": u.numel() * 4, "steps": args.steps, "warmup": args.warmup,
+            "params": PARAMS, "data": "synthetic",
+            "saved_for_backward": "nothing (linear operators: the adjoint needs only the incoming gradient)"}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -208,7 +373,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--edge", type=int, default=513, help="field edge (513 = the workload; smaller for profiling)")
     ap.add_argument("--quick", action="store_true", help="compress steps only (profiling runs)")
+    ap.add_argument("--workload", default="grf513", choices=["grf513", "batch64", "diff257"])
     args = ap.parse_args()
+    if args.workload == "batch64" and args.impl == "gpu":
+        return run_batch64(args)
+    if args.workload == "diff257" and args.impl == "gpu":
+        return run_diff257(args)
     global SHAPE
     SHAPE = (args.edge,) * 3
     if args.impl == "reference":

@@ -103,6 +103,32 @@ bm_status bm_stream_info(const void* in, size_t in_bytes, int in_is_device, int*
  * the stream bounds and reports through a status word rather than trapping. */
 bm_status bm_decompress(const void* d_in, size_t in_bytes, void* d_field, void* stream);
 
+/* One field of a batched compress: the arguments of bm_compress for it. */
+typedef struct {
+  const void* d_field;
+  int ndim;
+  int64_t shape[3];
+  bm_dtype dtype;
+  double tol;
+  bm_tol_mode tol_mode;
+  const double* h_roi_tol; /* nullable, as for bm_compress */
+  bm_params params;
+  void* d_out;
+  size_t out_capacity;
+} bm_batch_item;
+
+/* Compresses n independent fields (Sec. III-D: many fields per launch
+ * sequence).  The fields' pipelines are queued on a pool of the library's
+ * streams, forked from and joined back into `stream`, without any host
+ * synchronisation until all are queued; then one synchronisation and the
+ * per-field sizes in out_bytes[i] (host array of n).  Each field gives the
+ * same stream, byte for byte, as bm_compress with the same arguments.
+ * item_status (host array of n, nullable) receives each field's status; the
+ * return value is the first non-OK status, or BM_OK.  Buffers are owned by
+ * the caller; fields and outputs must not overlap. */
+bm_status bm_compress_batch(int n, const bm_batch_item* items, size_t* out_bytes, bm_status* item_status,
+                            void* stream);
+
 /* Multilevel decomposition only (Sec. II-B / III-A / III-B), no quantisation:
  * writes the n_coeffs full-precision coefficients to d_coeffs (same dtype as
  * the field) in stream order: blocks row-major; inside a block levels finest

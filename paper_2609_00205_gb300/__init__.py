@@ -15,7 +15,7 @@ import torch
 from . import _build
 
 __all__ = [
-    "BM_F32", "BM_F64", "BlockMGARDError", "load", "compress", "decompress", "decompose", "recompose",
+    "BM_F32", "BM_F64", "BlockMGARDError", "load", "compress", "compress_batch", "decompress", "decompose", "recompose",
     "coeff_count", "stream_info", "stream_codes", "huffman_encode", "huffman_decode", "compress_bound",
     "set_timing", "stage_times", "stage_timeline", "decompose_adjoint", "recompose_adjoint", "Decompose",
     "Recompose", "decompose_ad", "recompose_ad", "launch_count", "release_workspace", "library_path",
@@ -36,6 +36,13 @@ class BlockMGARDError(RuntimeError):
 class _Params(ctypes.Structure):
     _fields_ = [("block_nodes", ctypes.c_int), ("incache_levels", ctypes.c_int), ("global_levels", ctypes.c_int),
                 ("chunk_symbols", ctypes.c_int), ("dict_radius", ctypes.c_int)]
+
+
+class _BatchItem(ctypes.Structure):
+    _fields_ = [("d_field", ctypes.c_void_p), ("ndim", ctypes.c_int), ("shape", ctypes.c_int64 * 3),
+                ("dtype", ctypes.c_int), ("tol", ctypes.c_double), ("tol_mode", ctypes.c_int),
+                ("h_roi_tol", ctypes.POINTER(ctypes.c_double)), ("params", _Params), ("d_out", ctypes.c_void_p),
+                ("out_capacity", ctypes.c_size_t)]
 
 
 _lib = None
@@ -64,6 +71,7 @@ def load():
                               P(ctypes.c_double), P(_Params), vp, sz, P(sz), vp]
     L.bm_stream_info.argtypes = [vp, sz, ctypes.c_int, P(ctypes.c_int), P(i64), P(ctypes.c_int), P(sz)]
     L.bm_decompress.argtypes = [vp, sz, vp, vp]
+    L.bm_compress_batch.argtypes = [ctypes.c_int, P(_BatchItem), P(sz), P(ctypes.c_int), vp]
     L.bm_decompose.argtypes = [vp, ctypes.c_int, P(i64), ctypes.c_int, P(_Params), vp, vp]
     L.bm_recompose.argtypes = [vp, ctypes.c_int, P(i64), ctypes.c_int, P(_Params), vp, vp]
     L.bm_decompose_adjoint.argtypes = [vp, ctypes.c_int, P(i64), ctypes.c_int, P(_Params), vp, vp]
@@ -151,6 +159,55 @@ def compress(field: torch.Tensor, tol: float, mode: str = "rel", roi=None, block
                              ctypes.c_void_p(out.data_ptr()), ctypes.c_size_t(out.numel()), ctypes.byref(nbytes),
                              _stream(stream)))
     return out[: nbytes.value]
+
+
+def compress_batch(fields, tols, mode: str = "rel", rois=None, block=17, levels=2, global_levels=2, chunk=2048,
+                   radius=4096, outs=None, stream=None):
+    """Compress several 3-D CUDA fields in one call (pipelines queued on the
+    library's stream pool, one synchronisation).  ``tols``: one tolerance per
+    field; ``rois``: None or one per-block tolerance map (or None) per field;
+    ``outs``: optional output buffers.  Returns the streams as uint8 views, each
+    identical to :func:`compress` of the same field."""
+    import numpy as np
+    L = load()
+    n = len(fields)
+    if len(tols) != n or (rois is not None and len(rois) != n) or (outs is not None and len(outs) != n):
+        raise ValueError("one tolerance (and ROI map, output) per field")
+    items = (_BatchItem * max(n, 1))()
+    keep = []
+    bufs = []
+    p = _params(block, levels, global_levels, chunk, radius)
+    for i, f in enumerate(fields):
+        _dev_check(f)
+        if f.dim() != 3:
+            raise ValueError("fields must be 3-D")
+        cap = compress_bound(f.shape, f.dtype)
+        o = outs[i] if outs is not None else torch.empty(cap, dtype=torch.uint8, device=f.device)
+        if o.numel() < cap or o.dtype != torch.uint8 or not o.is_cuda:
+            raise ValueError("out must be a CUDA uint8 tensor of at least compress_bound() bytes")
+        bufs.append(o)
+        it = items[i]
+        it.d_field = f.data_ptr()
+        it.ndim = 3
+        for d in range(3):
+            it.shape[d] = int(f.shape[d])
+        it.dtype = _dtype(f.dtype)
+        it.tol = float(tols[i])
+        it.tol_mode = BM_REL if mode == "rel" else BM_ABS
+        r = rois[i] if rois is not None else None
+        if r is not None:
+            r = np.ascontiguousarray(np.asarray(r, dtype=np.float64).ravel())
+            keep.append(r)
+            it.h_roi_tol = r.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        it.params = p
+        it.d_out = o.data_ptr()
+        it.out_capacity = o.numel()
+    sizes = (ctypes.c_size_t * max(n, 1))()
+    status = (ctypes.c_int * max(n, 1))()
+    dev = fields[0].device if n else torch.device("cuda", torch.cuda.current_device())
+    with torch.cuda.device(dev):
+        _check(L.bm_compress_batch(n, items, sizes, status, _stream(stream)))
+    return [bufs[i][: sizes[i]] for i in range(n)]
 
 
 def stream_info(buf: torch.Tensor) -> dict:

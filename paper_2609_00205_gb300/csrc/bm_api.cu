@@ -935,9 +935,23 @@ StreamLayout layout(const PlanHost& h, int ntiers, int chunk) {
   return L;
 }
 
+// Pinned host staging and result of one item of a batched compress.
+struct BatchSlot {
+  unsigned char* h = nullptr;  // Scalars at 0, tiers at 256, block tiers at 256 + 8*256
+  bool raw_now = false;        // the raw copy was chosen on the host
+  unsigned long long raw_total = 0;
+};
+
+bm_status compress_result(const Scalars* hsc, unsigned long long raw_total, size_t* out_bytes) {
+  if (hsc->status & ST_TIMEOUT) return fail(BM_ERR_CUDA, "encoder look-back wait timed out");
+  if (hsc->status & ST_CORRUPT) return fail(BM_ERR_CUDA, "internal error: escape count differs from the histogram");
+  *out_bytes = (hsc->status & ST_RAW) ? (size_t)raw_total : (size_t)hsc->total;
+  return BM_OK;
+}
+
 template <typename T>
 bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, double tol, int rel, const double* roi,
-                     uint8_t* out, size_t cap, size_t* out_bytes, cudaStream_t s) {
+                     uint8_t* out, size_t cap, size_t* out_bytes, cudaStream_t s, BatchSlot* bs = nullptr) {
   PlanDev* P = nullptr;
   if (bm_status st = get_plan(shape, prm.B, prm.K, prm.M, &P)) return st;
   const PlanHost& h = P->h;
@@ -1000,7 +1014,9 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   unsigned char* tickets = cv.take<unsigned char>(256 + 16ull * L.nch);  // ticket, then look-back status words
   unsigned long long* lb_status = reinterpret_cast<unsigned long long*>(tickets + 256);
 
-  unsigned char* hp = reinterpret_cast<unsigned char*>(ws->h);
+  // pinned staging: the stream's own, or the batch item's (items of a batch
+  // share streams, so each needs its own copy until the batch has synchronised)
+  unsigned char* hp = bs ? bs->h : reinterpret_cast<unsigned char*>(ws->h);
   Scalars* hsc = reinterpret_cast<Scalars*>(hp);
   double* htiers = reinterpret_cast<double*>(hp + 256);
   uint8_t* hbt = hp + 256 + 8 * 256;
@@ -1039,6 +1055,11 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     raw_header_kernel<<<1, 32, 0, s>>>(out, f64, h.B, shape[0], shape[1], shape[2], rel, tol, raw_total, sc);
     BM_LAUNCHED();
     BM_CUDA(cudaMemcpyAsync(out + kHeaderBytes, field, (size_t)nel * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    if (bs) {
+      bs->raw_now = true;
+      bs->raw_total = raw_total;
+      return BM_OK;
+    }
     BM_CUDA(cudaStreamSynchronize(s));
     *out_bytes = (size_t)raw_total;
     return BM_OK;
@@ -1113,11 +1134,13 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     BM_CUDA(cudaGetLastError());
     BM_CUDA(cudaMemcpyAsync(hsc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
   }
+  if (bs) {  // the batch reads the result after its single synchronisation
+    bs->raw_now = false;
+    bs->raw_total = raw_total;
+    return BM_OK;
+  }
   BM_CUDA(cudaStreamSynchronize(s));
-  if (hsc->status & ST_TIMEOUT) return fail(BM_ERR_CUDA, "encoder look-back wait timed out");
-  if (hsc->status & ST_CORRUPT) return fail(BM_ERR_CUDA, "internal error: escape count differs from the histogram");
-  *out_bytes = (hsc->status & ST_RAW) ? (size_t)raw_total : (size_t)hsc->total;
-  return BM_OK;
+  return compress_result(hsc, raw_total, out_bytes);
 }
 
 // Parsed and checked header of a stream.
@@ -1403,6 +1426,60 @@ bm_status adjoint_entry(int dir, const int64_t* shape, const Params& prm, T* gfi
   return run_adjoint<T>(*P, dir, gfield, gcoef, cv, s);
 }
 
+// ---------------------------------------------------------------------------
+// Batched compress: the items run on a pool of streams (each with its own
+// workspace), nothing synchronises until every item has been queued, and the
+// results are read from per-item pinned slots afterwards.
+// ---------------------------------------------------------------------------
+constexpr int kBatchStreams = 8;
+struct BatchCtx {
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> joins;
+  cudaEvent_t fork = nullptr;
+  unsigned char* h = nullptr;
+  size_t hbytes = 0;
+};
+std::mutex g_batch_mu;
+std::map<int, BatchCtx> g_batch;
+
+bm_status batch_ctx(size_t hbytes, BatchCtx** out) {
+  int dev = 0;
+  BM_CUDA(cudaGetDevice(&dev));
+  BatchCtx& c = g_batch[dev];
+  if (c.streams.empty()) {
+    for (int i = 0; i < kBatchStreams; ++i) {
+      cudaStream_t st = nullptr;
+      cudaEvent_t ev = nullptr;
+      BM_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+      BM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      c.streams.push_back(st);
+      c.joins.push_back(ev);
+    }
+    BM_CUDA(cudaEventCreateWithFlags(&c.fork, cudaEventDisableTiming));
+  }
+  if (c.hbytes < hbytes) {
+    if (c.h) cudaFreeHost(c.h);
+    c.h = nullptr;
+    c.hbytes = 0;
+    if (cudaMallocHost(&c.h, hbytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(BM_ERR_OOM, "pinned host allocation for the batch failed");
+    }
+    c.hbytes = hbytes;
+  }
+  *out = &c;
+  return BM_OK;
+}
+
+bm_status check_item(const bm_batch_item& it, Params& prm) {
+  if (!it.d_field || !it.d_out) return fail(BM_ERR_ARG, "NULL pointer in a batch item");
+  if (bm_status st = check_shape(it.ndim, it.shape)) return st;
+  if (it.dtype != BM_F32 && it.dtype != BM_F64) return fail(BM_ERR_ARG, "dtype");
+  if (!(it.tol > 0.0) || !std::isfinite(it.tol)) return fail(BM_ERR_ARG, "tolerance must be finite and > 0");
+  if (it.tol_mode != BM_ABS && it.tol_mode != BM_REL) return fail(BM_ERR_ARG, "tol_mode");
+  return check_params(&it.params, prm);
+}
+
 extern "C" {
 
 const char* bm_error_string(bm_status s) {
@@ -1482,6 +1559,72 @@ bm_status bm_compress(const void* d_field, int ndim, const int64_t* shape, bm_dt
     st = compress_t<double>(reinterpret_cast<const double*>(d_field), shape, prm, tol, tol_mode == BM_REL, h_roi_tol,
                             reinterpret_cast<uint8_t*>(d_out), out_capacity, out_bytes, s);
   return st;
+}
+
+bm_status bm_compress_batch(int n, const bm_batch_item* items, size_t* out_bytes, bm_status* item_status,
+                            void* stream) {
+  if (n < 0 || (n > 0 && (!items || !out_bytes))) return fail(BM_ERR_ARG, "NULL pointer argument");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> g(g_timer_mu);
+  std::lock_guard<std::mutex> gb(g_batch_mu);
+  g_timer.begin(s);
+  std::vector<Params> prm((size_t)n);
+  std::vector<size_t> slot_off((size_t)n);
+  std::vector<bm_status> st((size_t)n, BM_OK);
+  size_t hb = 0;
+  for (int i = 0; i < n; ++i) {
+    st[(size_t)i] = check_item(items[i], prm[(size_t)i]);
+    int nb = 1;
+    if (st[(size_t)i] == BM_OK)
+      for (int d = 0; d < 3; ++d) nb *= (int)((items[i].shape[d] + prm[(size_t)i].B - 1) / prm[(size_t)i].B);
+    slot_off[(size_t)i] = hb;
+    hb += (256 + 8 * 256 + (size_t)nb + 255) & ~size_t(255);
+  }
+  BatchCtx* ctx = nullptr;
+  if (bm_status e = batch_ctx(std::max<size_t>(hb, 256), &ctx)) return e;
+  // largest items first, so that each pool stream's workspace is sized once
+  std::vector<int> order((size_t)n);
+  for (int i = 0; i < n; ++i) order[(size_t)i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return nel3(items[a].shape) * (items[a].dtype == BM_F64 ? 2 : 1) >
+           nel3(items[b].shape) * (items[b].dtype == BM_F64 ? 2 : 1);
+  });
+  std::vector<BatchSlot> slot((size_t)n);
+  BM_CUDA(cudaEventRecord(ctx->fork, s));
+  for (cudaStream_t ps : ctx->streams) BM_CUDA(cudaStreamWaitEvent(ps, ctx->fork, 0));
+  int k = 0;
+  for (int i : order) {
+    if (st[(size_t)i] != BM_OK) continue;
+    const bm_batch_item& it = items[i];
+    cudaStream_t ps = ctx->streams[(size_t)(k++ % kBatchStreams)];
+    slot[(size_t)i].h = ctx->h + slot_off[(size_t)i];
+    size_t dummy = 0;
+    if (it.dtype == BM_F32)
+      st[(size_t)i] = compress_t<float>(reinterpret_cast<const float*>(it.d_field), it.shape, prm[(size_t)i], it.tol,
+                                        it.tol_mode == BM_REL, it.h_roi_tol, reinterpret_cast<uint8_t*>(it.d_out),
+                                        it.out_capacity, &dummy, ps, &slot[(size_t)i]);
+    else
+      st[(size_t)i] = compress_t<double>(reinterpret_cast<const double*>(it.d_field), it.shape, prm[(size_t)i], it.tol,
+                                         it.tol_mode == BM_REL, it.h_roi_tol, reinterpret_cast<uint8_t*>(it.d_out),
+                                         it.out_capacity, &dummy, ps, &slot[(size_t)i]);
+  }
+  for (size_t j = 0; j < ctx->streams.size(); ++j) {
+    BM_CUDA(cudaEventRecord(ctx->joins[j], ctx->streams[j]));
+    BM_CUDA(cudaStreamWaitEvent(s, ctx->joins[j], 0));
+  }
+  BM_CUDA(cudaStreamSynchronize(s));
+  bm_status first = BM_OK;
+  for (int i = 0; i < n; ++i) {
+    out_bytes[i] = 0;
+    if (st[(size_t)i] == BM_OK) {
+      const BatchSlot& b = slot[(size_t)i];
+      if (b.raw_now) out_bytes[i] = (size_t)b.raw_total;
+      else st[(size_t)i] = compress_result(reinterpret_cast<const Scalars*>(b.h), b.raw_total, &out_bytes[i]);
+    }
+    if (item_status) item_status[i] = st[(size_t)i];
+    if (first == BM_OK) first = st[(size_t)i];
+  }
+  return first;
 }
 
 bm_status bm_stream_info(const void* in, size_t in_bytes, int in_is_device, int* ndim, int64_t shape[3],

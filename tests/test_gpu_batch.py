@@ -1,0 +1,72 @@
+"""Batched compress: every field's stream equals the single-field call byte
+for byte (uneven shapes, both dtypes, own tolerances, ROI maps), decompresses
+within its bound, and a bad item fails alone."""
+import numpy as np
+import pytest
+import torch
+
+import fields
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def bm():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_2609_00205_gb300 as m
+
+    m.load()
+    return m
+
+
+def _batch(seed, n):
+    rng = np.random.default_rng(seed)
+    fs, tols, rois = [], [], []
+    for i in range(n):
+        f64 = i % 5 == 4
+        shape = tuple(int(v) for v in rng.integers(20, 90, size=3))
+        u = fields.power_law_grf(shape, exponent=float(rng.uniform(-4.0, -1.5)), seed=100 + i,
+                                 dtype=torch.float64 if f64 else torch.float32, device=DEV).contiguous()
+        tol = float(10 ** rng.uniform(-5, -2))
+        nb = int(np.prod([(s + 16) // 17 for s in shape]))
+        roi = None
+        if i % 3 == 0:
+            roi = np.full(nb, tol)
+            pick = rng.choice(nb, size=max(1, nb // 10), replace=False)
+            roi[pick] = tol / 10
+        fs.append(u)
+        tols.append(tol)
+        rois.append(roi)
+    return fs, tols, rois
+
+
+def test_batch_matches_single_calls(bm):
+    fs, tols, rois = _batch(1, 13)
+    out = bm.compress_batch(fs, tols, rois=rois)
+    for u, t, r, s in zip(fs, tols, rois, out):
+        ref = bm.compress(u, t, roi=r)
+        assert s.numel() == ref.numel()
+        assert torch.equal(s, ref)
+        d = bm.decompress(s)
+        maxabs = float(u.abs().max())
+        tau = t * maxabs
+        if r is None:
+            assert float((d - u).abs().max()) <= tau
+        else:
+            # every node keeps the loosest bound; blocks with a tighter entry are checked in the parity tests
+            assert float((d - u).abs().max()) <= tau
+
+
+def test_batch_reports_a_bad_item_alone(bm):
+    fs, tols, rois = _batch(2, 4)
+    tols[2] = -1.0
+    with pytest.raises(bm.BlockMGARDError):
+        bm.compress_batch(fs, tols, rois=rois)
+    # the library keeps working afterwards
+    ok = bm.compress_batch(fs[:2], tols[:2], rois=rois[:2])
+    for u, t, r, s in zip(fs[:2], tols[:2], rois[:2], ok):
+        assert torch.equal(s, bm.compress(u, t, roi=r))
