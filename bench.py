@@ -13,6 +13,7 @@ needed between steps.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
   python bench.py --workload batch64    # 64 uneven fields: batched call vs per-field loop
   python bench.py --workload diff257    # differentiable recompose: forward + backward
+  python bench.py --workload model      # Eq. 1 fit on this GPU, its knee, Alg. 1 choices
 
 Under torchrun (N > 1) every rank compresses its own field (seed + rank): the
 problems are independent, there is no collective on the data path, scaling
@@ -362,6 +363,34 @@ def run_diff257(args):
     print(json.dumps(line))
 
 
+def run_model(args):
+    """Fit the performance model (Eq. 1 for the In-cache Block stage) on this
+    GPU for both dtypes, report the knee (90 % of the saturated throughput)
+    and Alg. 1's choice for the 513^3 workload under a few time budgets."""
+    import torch
+
+    import paper_2609_00205_gb300 as bm
+
+    torch.cuda.set_device(0)
+    bm.load()
+    out = {"metric": "performance model (Eq. 1) and Alg. 1 selection", "workload": "model", "data": "synthetic"}
+    for name, dt in (("f32", torch.float32), ("f64", torch.float64)):
+        m = bm.perf_model_fit(dt, 17)
+        d = m.as_dict()
+        d["knee_blocks_90pct"] = bm.perf_model_knee(m, 0.9)
+        d["tp_peak_gbs"] = m.block_peak_per_ms * 17 ** 3 * (4 if dt == torch.float32 else 8) / 1e6
+        sel = {}
+        for budget in (0.8, 1.2, 2.0, 5.0):
+            try:
+                p, t = bm.select_params(m, SHAPE, budget)
+                sel[str(budget)] = {"params": p, "predicted_ms": t}
+            except bm.BlockMGARDError as e:
+                sel[str(budget)] = {"error": str(e)}
+        d["alg1_513"] = sel
+        out[name] = d
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -373,12 +402,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--edge", type=int, default=513, help="field edge (513 = the workload; smaller for profiling)")
     ap.add_argument("--quick", action="store_true", help="compress steps only (profiling runs)")
-    ap.add_argument("--workload", default="grf513", choices=["grf513", "batch64", "diff257"])
+    ap.add_argument("--workload", default="grf513", choices=["grf513", "batch64", "diff257", "model"])
     args = ap.parse_args()
     if args.workload == "batch64" and args.impl == "gpu":
         return run_batch64(args)
     if args.workload == "diff257" and args.impl == "gpu":
         return run_diff257(args)
+    if args.workload == "model" and args.impl == "gpu":
+        return run_model(args)
     global SHAPE
     SHAPE = (args.edge,) * 3
     if args.impl == "reference":

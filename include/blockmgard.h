@@ -103,6 +103,39 @@ bm_status bm_stream_info(const void* in, size_t in_bytes, int in_is_device, int*
  * the stream bounds and reports through a status word rather than trapping. */
 bm_status bm_decompress(const void* d_in, size_t in_bytes, void* d_field, void* stream);
 
+/* Performance model of the compress pipeline on this GPU (Sec. III-B): the
+ * In-cache Block stage follows Eq. 1 (time of N blocks = 1/Slope +
+ * N/TP_peak, i.e. TP(N) = N / (1/Slope + N/TP_peak)); the global levels, the
+ * histogram and the encoder are straight lines in their size; the codebook and
+ * the remaining small stages are constants.  Times in ms. */
+typedef struct {
+  double block_latency_ms;      /* 1/Slope */
+  double block_peak_per_ms;     /* TP_peak, blocks per ms */
+  double global_ms, global_ms_per_node;       /* per global level */
+  double hist_ms, hist_ms_per_symbol;         /* max of the two */
+  double codebook_ms;
+  double encode_ms, encode_ms_per_symbol;     /* max of the two */
+  double other_ms;
+  int block_nodes, incache_levels;            /* configuration the fit was taken with */
+  bm_dtype dtype;
+} bm_perf_model;
+
+/* Fits the model by compressing synthetic fields of 1^3 .. 22^3 blocks of
+ * block_nodes nodes (default levels) on `stream` with stage timing; allocates
+ * and frees its own buffers (up to ~1.6 GB for FP32, B = 17).  Synchronous. */
+bm_status bm_perf_model_fit(bm_dtype dtype, int block_nodes, bm_perf_model* model, void* stream);
+/* Block count at which Eq. 1 reaches `fraction` (0..1) of TP_peak (the knee). */
+double bm_perf_model_knee(const bm_perf_model* model, double fraction);
+/* Predicted compress time of one field with these parameters. */
+bm_status bm_predict_ms(const bm_perf_model* model, int ndim, const int64_t* shape, const bm_params* params,
+                        double* ms);
+/* Alg. 1: among the (in-cache levels K, global levels M) pairs whose
+ * predicted time is within budget_ms, the largest in (M, -K) (more global
+ * levels first, then fewer in-cache levels); block size as in the model.
+ * BM_ERR_UNSUPPORTED when no pair fits. */
+bm_status bm_select_params(const bm_perf_model* model, int ndim, const int64_t* shape, double budget_ms,
+                           bm_params* out, double* predicted_ms);
+
 /* One field of a batched compress: the arguments of bm_compress for it. */
 typedef struct {
   const void* d_field;

@@ -18,7 +18,8 @@ __all__ = [
     "BM_F32", "BM_F64", "BlockMGARDError", "load", "compress", "compress_batch", "decompress", "decompose", "recompose",
     "coeff_count", "stream_info", "stream_codes", "huffman_encode", "huffman_decode", "compress_bound",
     "set_timing", "stage_times", "stage_timeline", "decompose_adjoint", "recompose_adjoint", "Decompose",
-    "Recompose", "decompose_ad", "recompose_ad", "launch_count", "release_workspace", "library_path",
+    "Recompose", "decompose_ad", "recompose_ad", "PerfModel", "perf_model_fit", "perf_model_knee", "predict_ms",
+    "select_params", "launch_count", "release_workspace", "library_path",
 ]
 
 BM_F32, BM_F64 = 0, 1
@@ -43,6 +44,20 @@ class _BatchItem(ctypes.Structure):
                 ("dtype", ctypes.c_int), ("tol", ctypes.c_double), ("tol_mode", ctypes.c_int),
                 ("h_roi_tol", ctypes.POINTER(ctypes.c_double)), ("params", _Params), ("d_out", ctypes.c_void_p),
                 ("out_capacity", ctypes.c_size_t)]
+
+
+class PerfModel(ctypes.Structure):
+    """Fitted performance model (Eq. 1 for the In-cache Block stage, lines for
+    the rest); see bm_perf_model in include/blockmgard.h."""
+    _fields_ = [("block_latency_ms", ctypes.c_double), ("block_peak_per_ms", ctypes.c_double),
+                ("global_ms", ctypes.c_double), ("global_ms_per_node", ctypes.c_double),
+                ("hist_ms", ctypes.c_double), ("hist_ms_per_symbol", ctypes.c_double),
+                ("codebook_ms", ctypes.c_double), ("encode_ms", ctypes.c_double),
+                ("encode_ms_per_symbol", ctypes.c_double), ("other_ms", ctypes.c_double),
+                ("block_nodes", ctypes.c_int), ("incache_levels", ctypes.c_int), ("dtype", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _lib = None
@@ -72,6 +87,12 @@ def load():
     L.bm_stream_info.argtypes = [vp, sz, ctypes.c_int, P(ctypes.c_int), P(i64), P(ctypes.c_int), P(sz)]
     L.bm_decompress.argtypes = [vp, sz, vp, vp]
     L.bm_compress_batch.argtypes = [ctypes.c_int, P(_BatchItem), P(sz), P(ctypes.c_int), vp]
+    L.bm_perf_model_fit.argtypes = [ctypes.c_int, ctypes.c_int, P(PerfModel), vp]
+    L.bm_perf_model_knee.argtypes = [P(PerfModel), ctypes.c_double]
+    L.bm_perf_model_knee.restype = ctypes.c_double
+    L.bm_predict_ms.argtypes = [P(PerfModel), ctypes.c_int, P(i64), P(_Params), P(ctypes.c_double)]
+    L.bm_select_params.argtypes = [P(PerfModel), ctypes.c_int, P(i64), ctypes.c_double, P(_Params),
+                                   P(ctypes.c_double)]
     L.bm_decompose.argtypes = [vp, ctypes.c_int, P(i64), ctypes.c_int, P(_Params), vp, vp]
     L.bm_recompose.argtypes = [vp, ctypes.c_int, P(i64), ctypes.c_int, P(_Params), vp, vp]
     L.bm_decompose_adjoint.argtypes = [vp, ctypes.c_int, P(i64), ctypes.c_int, P(_Params), vp, vp]
@@ -208,6 +229,35 @@ def compress_batch(fields, tols, mode: str = "rel", rois=None, block=17, levels=
     with torch.cuda.device(dev):
         _check(L.bm_compress_batch(n, items, sizes, status, _stream(stream)))
     return [bufs[i][: sizes[i]] for i in range(n)]
+
+
+def perf_model_fit(dtype=torch.float32, block=17, stream=None) -> PerfModel:
+    """Calibrate the performance model on the current GPU (synchronous)."""
+    m = PerfModel()
+    _check(load().bm_perf_model_fit(_dtype(dtype), int(block), ctypes.byref(m), _stream(stream)))
+    return m
+
+
+def perf_model_knee(model: PerfModel, fraction: float = 0.9) -> float:
+    return float(load().bm_perf_model_knee(ctypes.byref(model), float(fraction)))
+
+
+def predict_ms(model: PerfModel, shape, block=17, levels=2, global_levels=2) -> float:
+    ms = ctypes.c_double(0.0)
+    p = _params(block, levels, global_levels)
+    _check(load().bm_predict_ms(ctypes.byref(model), 3, _shape(shape), ctypes.byref(p), ctypes.byref(ms)))
+    return ms.value
+
+
+def select_params(model: PerfModel, shape, budget_ms: float):
+    """Alg. 1: (block, levels, global_levels) maximising (M, -K) within the
+    time budget; returns (params dict, predicted ms)."""
+    p = _Params()
+    ms = ctypes.c_double(0.0)
+    _check(load().bm_select_params(ctypes.byref(model), 3, _shape(shape), float(budget_ms), ctypes.byref(p),
+                                   ctypes.byref(ms)))
+    return {"block": p.block_nodes, "levels": p.incache_levels,
+            "global_levels": p.global_levels if p.global_levels > 0 else 0}, ms.value
 
 
 def stream_info(buf: torch.Tensor) -> dict:

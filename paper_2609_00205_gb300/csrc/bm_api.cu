@@ -1480,6 +1480,57 @@ bm_status check_item(const bm_batch_item& it, Params& prm) {
   return check_params(&it.params, prm);
 }
 
+// ---------------------------------------------------------------------------
+// Performance model and parameter selection (Sec. III-B, Eq. 1, Alg. 1)
+// ---------------------------------------------------------------------------
+// Seeded synthetic field for the calibration runs: a smooth part plus a
+// small hashed noise (the calibration measures time, not compression).
+template <typename T>
+__global__ void calib_field_kernel(T* u, int64_t n0, int64_t n1, int64_t n2) {
+  const int64_t n = n0 * n1 * n2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = i % n2, t = i / n2, j = t % n1, l = t / n1;
+    unsigned h = (unsigned)i * 2654435761u;
+    h ^= h >> 15;
+    h *= 2246822519u;
+    h ^= h >> 13;
+    const double noise = (double)(h & 0xFFFFFF) / 16777216.0 - 0.5;
+    u[i] = (T)(sin(0.13 * (double)l) * cos(0.07 * (double)j) + 0.5 * sin(0.05 * (double)k) + 0.05 * noise);
+  }
+}
+
+struct CalibPoint {
+  double blocks, block_ms;
+  std::vector<std::pair<double, double>> global;  // (grid nodes, ms) per level
+  double syms, hist_ms, ghist_syms, ghist_ms, cb_ms, enc_ms, other_ms;
+};
+
+// Eq. 1: the time of N blocks is 1/Slope + N / TP_peak (the reciprocal of
+// TP(N) = N / (1/Slope + N/TP_peak), per block); a least-squares line through
+// (N, time) gives both.  Other stages: straight lines in their size.
+static void fit_line(const std::vector<double>& x, const std::vector<double>& y, double& a, double& b) {
+  const double n = (double)x.size();
+  double sx = 0, sy = 0, sxx = 0, sxy = 0;
+  for (size_t i = 0; i < x.size(); ++i) {
+    sx += x[i];
+    sy += y[i];
+    sxx += x[i] * x[i];
+    sxy += x[i] * y[i];
+  }
+  const double den = n * sxx - sx * sx;
+  b = den != 0 ? (n * sxy - sx * sy) / den : 0.0;
+  a = (sy - b * sx) / n;
+  if (b < 0) {  // flat: a constant
+    b = 0;
+    a = sy / n;
+  }
+  if (a < 0) a = 0;
+}
+
+// Coarse-grid shape after one level (Sec. II-B: floor(n/2)+1 nodes, none
+// removed from a dimension of at most two nodes).
+static int64_t coarsen(int64_t n) { return n <= 2 ? n : n / 2 + 1; }
+
 extern "C" {
 
 const char* bm_error_string(bm_status s) {
@@ -1625,6 +1676,189 @@ bm_status bm_compress_batch(int n, const bm_batch_item* items, size_t* out_bytes
     if (first == BM_OK) first = st[(size_t)i];
   }
   return first;
+}
+
+bm_status bm_perf_model_fit(bm_dtype dtype, int block_nodes, bm_perf_model* model, void* stream) {
+  if (!model) return fail(BM_ERR_ARG, "NULL pointer argument");
+  if (dtype != BM_F32 && dtype != BM_F64) return fail(BM_ERR_ARG, "dtype");
+  bm_params bp{};
+  bp.block_nodes = block_nodes;
+  Params prm;
+  if (bm_status st = check_params(&bp, prm)) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t esize = dtype == BM_F64 ? 8 : 4;
+  // fields of 1^3 .. 22^3 blocks (up to ~0.8 GB of FP32 input at B = 17)
+  const int nb_list[] = {1, 2, 3, 4, 6, 8, 10, 12, 14, 16, 19, 22};
+  const int64_t emax = (int64_t)22 * prm.B;
+  const size_t fbytes = (size_t)(emax * emax * emax) * esize;
+  const size_t obytes = kHeaderBytes + fbytes;
+  void* dfield = nullptr;
+  void* dout = nullptr;
+  BM_CUDA(cudaMalloc(&dfield, fbytes));
+  if (cudaMalloc(&dout, obytes) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(dfield);
+    return fail(BM_ERR_OOM, "calibration buffers");
+  }
+  std::vector<CalibPoint> pts;
+  bm_status st = BM_OK;
+  const int prev_timing = g_timing.load();
+  g_timing.store(1);
+  for (int nb : nb_list) {
+    const int64_t e = (int64_t)nb * prm.B;
+    const int64_t shape[3] = {e, e, e};
+    if (dtype == BM_F64) calib_field_kernel<double><<<grid_for(e * e * e, 256), 256, 0, s>>>((double*)dfield, e, e, e);
+    else calib_field_kernel<float><<<grid_for(e * e * e, 256), 256, 0, s>>>((float*)dfield, e, e, e);
+    CalibPoint cp{};
+    for (int rep = 0; rep < 3 && st == BM_OK; ++rep) {  // warm-up, then two timed calls (the second kept)
+      size_t nbytes = 0;
+      {
+        std::lock_guard<std::mutex> g(g_timer_mu);
+        g_timer.begin(s);
+        st = dtype == BM_F64 ? compress_t<double>((const double*)dfield, shape, prm, 1e-3, 1, nullptr,
+                                                   (uint8_t*)dout, obytes, &nbytes, s)
+                             : compress_t<float>((const float*)dfield, shape, prm, 1e-3, 1, nullptr,
+                                                 (uint8_t*)dout, obytes, &nbytes, s);
+        g_timer.collect();
+      }
+      if (st != BM_OK || rep == 0) continue;
+      PlanDev* P = nullptr;
+      if ((st = get_plan(shape, prm.B, prm.K, prm.M, &P)) != BM_OK) break;
+      const GSizes gs = gsizes(P->h);
+      cp = CalibPoint{};
+      cp.blocks = (double)P->h.nblocks;
+      cp.syms = (double)P->h.nblocks * (double)P->h.per_block;
+      cp.ghist_syms = (double)(P->h.n_coeffs - P->h.sym_off[0]);
+      int gl = 0;
+      for (auto& r : g_timer.last) {
+        const std::string name = r.name;
+        if (name == "incache_decompose") cp.block_ms = r.ms;
+        else if (name == "global_decompose") cp.global.push_back({(double)gs.U[(size_t)gl++], (double)r.ms});
+        else if (name == "histogram") cp.hist_ms = r.ms;
+        else if (name == "global_histogram") cp.ghist_ms = r.ms;
+        else if (name == "huffman_codebook") cp.cb_ms = r.ms;
+        else if (name == "huffman_encode") cp.enc_ms = r.ms;
+        else cp.other_ms += r.ms;
+      }
+    }
+    if (st != BM_OK) break;
+    pts.push_back(cp);
+  }
+  g_timing.store(prev_timing);
+  cudaFree(dfield);
+  cudaFree(dout);
+  if (st != BM_OK) return st;
+  std::vector<double> x, y;
+  for (auto& p : pts) { x.push_back(p.blocks); y.push_back(p.block_ms); }
+  double a = 0, b = 0;
+  fit_line(x, y, a, b);
+  model->block_latency_ms = a;                  // 1 / Slope
+  model->block_peak_per_ms = b > 0 ? 1.0 / b : 0.0;  // TP_peak (blocks per ms)
+  x.clear(); y.clear();
+  for (auto& p : pts) for (auto& g : p.global) { x.push_back(g.first); y.push_back(g.second); }
+  fit_line(x, y, model->global_ms, model->global_ms_per_node);
+  x.clear(); y.clear();
+  for (auto& p : pts) { x.push_back(p.syms); y.push_back(p.hist_ms); x.push_back(p.ghist_syms); y.push_back(p.ghist_ms); }
+  fit_line(x, y, model->hist_ms, model->hist_ms_per_symbol);
+  x.clear(); y.clear();
+  for (auto& p : pts) { x.push_back(p.syms + p.ghist_syms); y.push_back(p.enc_ms); }
+  fit_line(x, y, model->encode_ms, model->encode_ms_per_symbol);
+  double cb = 0, other = 0;
+  for (auto& p : pts) { cb += p.cb_ms; other += p.other_ms; }
+  model->codebook_ms = cb / (double)pts.size();
+  model->other_ms = other / (double)pts.size();
+  model->block_nodes = prm.B;
+  model->incache_levels = prm.K;
+  model->dtype = dtype;
+  return BM_OK;
+}
+
+double bm_perf_model_knee(const bm_perf_model* m, double fraction) {
+  // TP(N) / TP_peak = N / (N + N0), N0 = TP_peak / Slope: the fraction is
+  // reached at N = N0 * fraction / (1 - fraction)
+  if (!m || !(fraction > 0.0) || !(fraction < 1.0)) return 0.0;
+  const double n0 = m->block_peak_per_ms * m->block_latency_ms;
+  return n0 * fraction / (1.0 - fraction);
+}
+
+bm_status bm_predict_ms(const bm_perf_model* m, int ndim, const int64_t* shape, const bm_params* params,
+                        double* ms) {
+  if (!m || !ms) return fail(BM_ERR_ARG, "NULL pointer argument");
+  if (bm_status st = check_shape(ndim, shape)) return st;
+  Params prm;
+  if (bm_status st = check_params(params, prm)) return st;
+  PlanDev* P = nullptr;
+  if (bm_status st = get_plan(shape, prm.B, prm.K, prm.M, &P)) return st;
+  const PlanHost& h = P->h;
+  const GSizes gs = gsizes(h);
+  // the in-cache levels (quantisation fused) follow Eq. 1; a model fitted
+  // for K levels is scaled by the share of a block's work the other K keep
+  // (each level's work is ~ its node count)
+  double kscale = 1.0;
+  if (m->incache_levels > 0 && m->incache_levels != prm.K) {
+    auto work = [&](int K) {
+      double w = 0, n = prm.B;
+      for (int l = 0; l < K; ++l) { w += n * n * n; n = (double)coarsen((int64_t)n); }
+      return w;
+    };
+    kscale = work(prm.K) / work(m->incache_levels);
+  }
+  const double nb = (double)h.nblocks;
+  double t = kscale * (m->block_latency_ms + (m->block_peak_per_ms > 0 ? nb / m->block_peak_per_ms : 0.0));
+  for (int l = 0; l < h.M; ++l) t += m->global_ms + m->global_ms_per_node * (double)gs.U[(size_t)l];
+  const double syms = (double)h.n_coeffs;
+  t += std::max(m->hist_ms, m->hist_ms_per_symbol * syms);
+  t += m->codebook_ms;
+  t += std::max(m->encode_ms, m->encode_ms_per_symbol * syms);
+  t += m->other_ms;
+  *ms = t;
+  return BM_OK;
+}
+
+bm_status bm_select_params(const bm_perf_model* m, int ndim, const int64_t* shape, double budget_ms,
+                           bm_params* out, double* predicted_ms) {
+  if (!m || !out) return fail(BM_ERR_ARG, "NULL pointer argument");
+  if (bm_status st = check_shape(ndim, shape)) return st;
+  const int B = m->block_nodes ? m->block_nodes : 17;
+  const int kmax = B == 9 ? 3 : 4;
+  bool found = false;
+  int bestK = 0, bestM = -1;
+  double bestT = 0;
+  for (int K = 1; K <= kmax; ++K) {
+    // block-coarse grid after K levels, then the global levels that still coarsen
+    int64_t mb = B;
+    for (int l = 0; l < K; ++l) mb = coarsen(mb);
+    int64_t g[3];
+    for (int d = 0; d < 3; ++d) g[d] = ((shape[d] + B - 1) / B) * mb;
+    int mmax = 0;
+    while (mmax < 16 && (g[0] > 2 || g[1] > 2 || g[2] > 2)) {
+      for (int d = 0; d < 3; ++d) g[d] = coarsen(g[d]);
+      ++mmax;
+    }
+    for (int M = 0; M <= mmax; ++M) {
+      bm_params p{};
+      p.block_nodes = B;
+      p.incache_levels = K;
+      p.global_levels = M ? M : -1;
+      double t = 0;
+      if (bm_predict_ms(m, ndim, shape, &p, &t) != BM_OK) continue;
+      if (t > budget_ms) continue;
+      // Alg. 1: the feasible pair that is largest in (M, -K)
+      if (!found || M > bestM || (M == bestM && K < bestK)) {
+        found = true;
+        bestK = K;
+        bestM = M;
+        bestT = t;
+      }
+    }
+  }
+  if (!found) return fail(BM_ERR_UNSUPPORTED, "no (levels, global levels) pair meets the time budget");
+  *out = bm_params{};
+  out->block_nodes = B;
+  out->incache_levels = bestK;
+  out->global_levels = bestM ? bestM : -1;
+  if (predicted_ms) *predicted_ms = bestT;
+  return BM_OK;
 }
 
 bm_status bm_stream_info(const void* in, size_t in_bytes, int in_is_device, int* ndim, int64_t shape[3],

@@ -70,3 +70,27 @@ def test_batch_reports_a_bad_item_alone(bm):
     ok = bm.compress_batch(fs[:2], tols[:2], rois=rois[:2])
     for u, t, r, s in zip(fs[:2], tols[:2], rois[:2], ok):
         assert torch.equal(s, bm.compress(u, t, roi=r))
+
+
+def test_perf_model_fit_and_selection(bm):
+    m = bm.perf_model_fit(torch.float32, 17)
+    d = m.as_dict()
+    assert d["block_latency_ms"] > 0 and d["block_peak_per_ms"] > 0
+    assert bm.perf_model_knee(m, 0.9) > 0
+    shape = (160, 150, 140)
+    u = fields.power_law_grf(shape, seed=9, device=DEV).contiguous()
+    pred = bm.predict_ms(m, shape)
+    bm.compress(u, 1e-3)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(5):
+        bm.compress(u, 1e-3)
+    b.record()
+    torch.cuda.synchronize()
+    meas = a.elapsed_time(b) / 5
+    assert pred / 3 < meas < pred * 3, (pred, meas)
+    p, t = bm.select_params(m, shape, 10.0)
+    s = bm.compress(u, 1e-3, **p)
+    d = bm.decompress(s)
+    assert float((d - u).abs().max()) <= 1e-3 * float(u.abs().max())
