@@ -62,6 +62,14 @@ def lib():
                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, P(u8), ctypes.c_uint64,
                                   P(ctypes.c_uint64), P(i64)]
         L.or_decompress.argtypes = [P(u8), ctypes.c_uint64, P(d), P(i64)]
+        ci = ctypes.c_int
+        L.or_plan_r.argtypes = [P(i64), ci, ci, ci, ci, P(i64)]
+        L.or_decompose_r.argtypes = [P(d), P(i64), ci, ci, ci, ci, P(d)]
+        L.or_recompose_r.argtypes = [P(d), P(i64), ci, ci, ci, ci, P(d)]
+        L.or_rounds.argtypes = [P(i64), ci, ci, ci, P(u8), P(i64), P(u8)]
+        L.or_budget_r.argtypes = [P(i64), ci, ci, ci, ci, P(d), ci, d, ci, P(d), P(d)]
+        L.or_compress_r.argtypes = [P(d), P(i64), ci, d, ci, P(d), ci, ci, ci, ci, ci, ci, P(u8), ctypes.c_uint64,
+                                    P(ctypes.c_uint64), P(i64)]
         _lib = L
     return _lib
 
@@ -93,9 +101,9 @@ def level_1d(x):
     return I, Mf, Mc, P
 
 
-def plan(shape, B, K, M):
+def plan(shape, B, K, M, R=1):
     out = np.zeros(11 + max(M, 1), dtype=np.int64)
-    _check(lib().or_plan(_ptr(_shape3(shape), ctypes.c_int64), B, K, M, _ptr(out, ctypes.c_int64)))
+    _check(lib().or_plan_r(_ptr(_shape3(shape), ctypes.c_int64), B, K, M, R, _ptr(out, ctypes.c_int64)))
     return {
         "n_coeffs": int(out[0]), "per_block": int(out[1]), "nblocks": int(out[2]), "m": int(out[3]),
         "gshape": tuple(int(v) for v in out[4:7]), "cshape": tuple(int(v) for v in out[7:10]),
@@ -103,21 +111,47 @@ def plan(shape, B, K, M):
     }
 
 
-def decompose(u, B, K, M):
+def decompose(u, B, K, M, R=1):
     u = np.ascontiguousarray(np.asarray(u, dtype=np.float64))
-    p = plan(u.shape, B, K, M)
+    p = plan(u.shape, B, K, M, R)
     coef = np.zeros(p["n_coeffs"])
     c = ctypes.c_double
-    _check(lib().or_decompose(_ptr(u, c), _ptr(_shape3(u.shape), ctypes.c_int64), B, K, M, _ptr(coef, c)))
+    _check(lib().or_decompose_r(_ptr(u, c), _ptr(_shape3(u.shape), ctypes.c_int64), B, K, M, R, _ptr(coef, c)))
     return coef
 
 
-def recompose(coef, shape, B, K, M):
+def recompose(coef, shape, B, K, M, R=1):
     coef = np.ascontiguousarray(np.asarray(coef, dtype=np.float64))
     u = np.zeros(tuple(shape))
     c = ctypes.c_double
-    _check(lib().or_recompose(_ptr(coef, c), _ptr(_shape3(shape), ctypes.c_int64), B, K, M, _ptr(u, c)))
+    _check(lib().or_recompose_r(_ptr(coef, c), _ptr(_shape3(shape), ctypes.c_int64), B, K, M, R, _ptr(u, c)))
     return u
+
+
+def rounds(shape, B, K, R, tier0=None):
+    """Blocks of every re-blocking round and, given round 0's block tiers,
+    every round's propagated tiers (a list of arrays)."""
+    nb = np.zeros(R, dtype=np.int64)
+    t0 = None if tier0 is None else np.ascontiguousarray(np.asarray(tier0, dtype=np.uint8))
+    out = None
+    if t0 is not None:
+        out = np.zeros(int(sum(plan_rounds_count(shape, B, K, R))), dtype=np.uint8)
+    _check(lib().or_rounds(_ptr(_shape3(shape), ctypes.c_int64), B, K, R,
+                           _ptr(t0, ctypes.c_uint8) if t0 is not None else None, _ptr(nb, ctypes.c_int64),
+                           _ptr(out, ctypes.c_uint8) if out is not None else None))
+    if out is None:
+        return [int(v) for v in nb], None
+    parts, o = [], 0
+    for v in nb:
+        parts.append(out[o:o + int(v)])
+        o += int(v)
+    return [int(v) for v in nb], parts
+
+
+def plan_rounds_count(shape, B, K, R):
+    nb = np.zeros(R, dtype=np.int64)
+    _check(lib().or_rounds(_ptr(_shape3(shape), ctypes.c_int64), B, K, R, None, _ptr(nb, ctypes.c_int64), None))
+    return [int(v) for v in nb]
 
 
 def decompose_matrix(shape, B, K, M):
@@ -175,13 +209,13 @@ def level_constants(shape, B, K, M):
     return out
 
 
-def budget(shape, B, K, M, taus, max_abs, f64):
+def budget(shape, B, K, M, taus, max_abs, f64, R=1):
     taus = np.ascontiguousarray(np.asarray(taus, dtype=np.float64))
     q = np.zeros(len(taus) * K + M + 1)
     meta = np.zeros(2)
     c = ctypes.c_double
-    _check(lib().or_budget(_ptr(_shape3(shape), ctypes.c_int64), B, K, M, _ptr(taus, c), len(taus),
-                           float(max_abs), int(bool(f64)), _ptr(q, c), _ptr(meta, c)))
+    _check(lib().or_budget_r(_ptr(_shape3(shape), ctypes.c_int64), B, K, M, R, _ptr(taus, c), len(taus),
+                             float(max_abs), int(bool(f64)), _ptr(q, c), _ptr(meta, c)))
     return q, float(meta[0]), bool(meta[1])
 
 
@@ -234,14 +268,15 @@ def huffman_decode(section, meta, n, dict_size, chunk):
     return out
 
 
-def compress(u, tol, rel=True, roi=None, B=9, K=1, M=2, chunk=2048, radius=4096, f64=None, want_codes=False):
+def compress(u, tol, rel=True, roi=None, B=9, K=1, M=2, chunk=2048, radius=4096, f64=None, want_codes=False, R=1):
     """Full stream for field u (numpy, float32 or float64).  Returns bytes
     (uint8 array) and, if asked, the integer codes in coefficient order."""
     if f64 is None:
         f64 = np.asarray(u).dtype == np.float64
     u64 = np.ascontiguousarray(np.asarray(u, dtype=np.float64))
-    p = plan(u64.shape, B, K, M)
-    cap = HEADER_BYTES + 8 * u64.size + 16 * p["n_coeffs"] + 2 * p["nblocks"] + 16 * radius + (1 << 16)
+    p = plan(u64.shape, B, K, M, R)
+    cap = HEADER_BYTES + 8 * u64.size + 16 * p["n_coeffs"] + 2 * sum(plan_rounds_count(u64.shape, B, K, R)) \
+        + 16 * radius + (1 << 16)
     out = np.zeros(cap, dtype=np.uint8)
     nbytes = ctypes.c_uint64(0)
     roi_arr = None
@@ -250,10 +285,10 @@ def compress(u, tol, rel=True, roi=None, B=9, K=1, M=2, chunk=2048, radius=4096,
         assert roi_arr.size == p["nblocks"]
     codes = np.zeros(p["n_coeffs"], dtype=np.int64) if want_codes else None
     c = ctypes.c_double
-    rc = lib().or_compress(_ptr(u64, c), _ptr(_shape3(u64.shape), ctypes.c_int64), int(bool(f64)), float(tol),
-                           int(bool(rel)), _ptr(roi_arr, c) if roi_arr is not None else None, B, K, M, chunk,
-                           radius, _ptr(out, ctypes.c_uint8), cap, ctypes.byref(nbytes),
-                           _ptr(codes, ctypes.c_int64) if codes is not None else None)
+    rc = lib().or_compress_r(_ptr(u64, c), _ptr(_shape3(u64.shape), ctypes.c_int64), int(bool(f64)), float(tol),
+                             int(bool(rel)), _ptr(roi_arr, c) if roi_arr is not None else None, B, K, M, R, chunk,
+                             radius, _ptr(out, ctypes.c_uint8), cap, ctypes.byref(nbytes),
+                             _ptr(codes, ctypes.c_int64) if codes is not None else None)
     _check(rc)
     s = out[:nbytes.value].copy()
     return (s, codes) if want_codes else s
@@ -294,5 +329,5 @@ def stream_header(s):
         "off_tiers": u64(128), "off_qtab": u64(136), "off_blocktier": u64(144), "off_chunks": u64(152),
         "off_codebook": u64(160), "off_bits": u64(168), "off_outliers": u64(176), "total": u64(184),
         "codebook_bytes": u32(192), "n_runs": u32(196), "margin": f64(200), "off_chunk_esc": u64(208),
-        "off_splits": u64(216),
+        "off_splits": u64(216), "R": u32(224) + 1,
     }

@@ -270,13 +270,23 @@ size_t level_detail_count(const Level1D* L) {
 }
 
 // ---------------------------------------------------------------------------
-// Hybrid hierarchy plan: K in-cache levels per B^3 block, M global levels.
+// Hybrid hierarchy plan: R rounds of K in-cache levels per B^3 block (round
+// r+1 re-blocks the gathered coarse values of round r, Sec. III-C), then M
+// global levels.
 // ---------------------------------------------------------------------------
-struct Plan {
-  int64_t shape[3];
-  int B, K, M;
+struct Round {
+  int64_t shape[3];  // the round's input grid
   int64_t nb[3];
   int64_t nblocks;
+  size_t off;        // first coefficient of the round
+};
+
+struct Plan {
+  int64_t shape[3];
+  int B, K, M, R = 1;
+  int64_t nb[3];     // round 0
+  int64_t nblocks;   // round 0
+  std::vector<Round> rounds;
   int m;                          // coarse nodes per block dim after K levels
   std::vector<std::vector<double>> block_coords;  // per local level (K+1 entries)
   std::vector<Level1D> local;     // per local level: one 1-D level (same for all dims)
@@ -289,11 +299,11 @@ struct Plan {
   size_t n_coeffs = 0;
 };
 
-Plan make_plan(const int64_t* shape, int B, int K, int M) {
-  if (B < 2 || K < 0 || M < 0) throw std::runtime_error("bad parameters");
+Plan make_plan(const int64_t* shape, int B, int K, int M, int R = 1) {
+  if (B < 2 || K < 0 || M < 0 || R < 1) throw std::runtime_error("bad parameters");
   Plan p;
   for (int d = 0; d < 3; ++d) p.shape[d] = shape[d];
-  p.B = B; p.K = K; p.M = M;
+  p.B = B; p.K = K; p.M = M; p.R = R;
   p.nblocks = 1;
   for (int d = 0; d < 3; ++d) {
     p.nb[d] = (shape[d] + B - 1) / B;
@@ -311,13 +321,36 @@ Plan make_plan(const int64_t* shape, int B, int K, int M) {
     p.block_coords.push_back(xl);
   }
   p.m = (int)xl.size();
-  // Physical coordinates of the gathered block-coarse grid: block offset plus
-  // the local coordinate of the coarse node, in finest-grid index units.
+  // rounds: each re-blocks the previous round's gathered grid (zero fill
+  // beyond its extent)
+  int64_t S[3] = {shape[0], shape[1], shape[2]};
+  size_t off = 0;
+  for (int r = 0; r < R; ++r) {
+    Round rd;
+    rd.nblocks = 1;
+    for (int d = 0; d < 3; ++d) {
+      rd.shape[d] = S[d];
+      rd.nb[d] = (S[d] + B - 1) / B;
+      rd.nblocks *= rd.nb[d];
+    }
+    rd.off = off;
+    off += (size_t)rd.nblocks * p.per_block;
+    p.rounds.push_back(rd);
+    for (int d = 0; d < 3; ++d) S[d] = rd.nb[d] * p.m;
+  }
+  // Coordinates of the gathered grid the global levels start from.  One
+  // round: physical, block offset plus the coarse node's local coordinate, in
+  // finest-grid index units.  Several rounds: index coordinates of the last
+  // round's gathered grid (the paper's re-blocking works in index space).
   std::vector<double> gx[3];
   for (int d = 0; d < 3; ++d) {
-    p.gshape[d] = p.nb[d] * p.m;
-    for (int64_t b = 0; b < p.nb[d]; ++b)
-      for (int j = 0; j < p.m; ++j) gx[d].push_back((double)(b * B) + xl[j]);
+    p.gshape[d] = S[d];
+    if (R == 1) {
+      for (int64_t b = 0; b < p.nb[d]; ++b)
+        for (int j = 0; j < p.m; ++j) gx[d].push_back((double)(b * B) + xl[j]);
+    } else {
+      for (int64_t i = 0; i < S[d]; ++i) gx[d].push_back((double)i);
+    }
   }
   for (int l = 0; l < M; ++l) {
     std::array<Level1D, 3> L3{make_level(gx[0]), make_level(gx[1]), make_level(gx[2])};
@@ -327,29 +360,27 @@ Plan make_plan(const int64_t* shape, int B, int K, int M) {
   }
   for (int d = 0; d < 3; ++d) p.cshape[d] = (int64_t)gx[d].size();
   p.coarsest = (size_t)(p.cshape[0] * p.cshape[1] * p.cshape[2]);
-  p.n_coeffs = (size_t)p.nblocks * p.per_block;
+  p.n_coeffs = off;
   for (size_t c : p.global_counts) p.n_coeffs += c;
   p.n_coeffs += p.coarsest;
   return p;
 }
 
-// Coefficient order: blocks row-major; inside a block levels finest->coarsest,
-// each level's non-coarse nodes row-major; then global levels finest->coarsest;
-// then the coarsest array row-major.
-std::vector<double> decompose(const double* u, const Plan& p) {
-  std::vector<double> coef;
-  coef.reserve(p.n_coeffs);
-  Grid G(p.gshape[0], p.gshape[1], p.gshape[2]);
-  for (int64_t b0 = 0; b0 < p.nb[0]; ++b0)
-    for (int64_t b1 = 0; b1 < p.nb[1]; ++b1)
-      for (int64_t b2 = 0; b2 < p.nb[2]; ++b2) {
+// Coefficient order: round by round, blocks row-major; inside a block levels
+// finest->coarsest, each level's non-coarse nodes row-major; then global
+// levels finest->coarsest; then the coarsest array row-major.
+Grid decompose_round(const Grid& in, const Plan& p, const Round& rd, std::vector<double>& coef) {
+  Grid G(rd.nb[0] * p.m, rd.nb[1] * p.m, rd.nb[2] * p.m);
+  for (int64_t b0 = 0; b0 < rd.nb[0]; ++b0)
+    for (int64_t b1 = 0; b1 < rd.nb[1]; ++b1)
+      for (int64_t b2 = 0; b2 < rd.nb[2]; ++b2) {
         Grid blk(p.B, p.B, p.B);
         for (int i = 0; i < p.B; ++i)
           for (int j = 0; j < p.B; ++j)
             for (int k = 0; k < p.B; ++k) {
               int64_t gi = b0 * p.B + i, gj = b1 * p.B + j, gk = b2 * p.B + k;
-              bool in = gi < p.shape[0] && gj < p.shape[1] && gk < p.shape[2];
-              blk.at(i, j, k) = in ? u[(gi * p.shape[1] + gj) * p.shape[2] + gk] : 0.0;  // zero fill
+              bool inside = gi < rd.shape[0] && gj < rd.shape[1] && gk < rd.shape[2];
+              blk.at(i, j, k) = inside ? in.at(gi, gj, gk) : 0.0;  // zero fill
             }
         for (int l = 0; l < p.K; ++l) {
           Level1D L3[3] = {p.local[l], p.local[l], p.local[l]};
@@ -359,30 +390,30 @@ std::vector<double> decompose(const double* u, const Plan& p) {
           for (int j = 0; j < p.m; ++j)
             for (int k = 0; k < p.m; ++k) G.at(b0 * p.m + i, b1 * p.m + j, b2 * p.m + k) = blk.at(i, j, k);
       }
+  return G;
+}
+
+std::vector<double> decompose(const double* u, const Plan& p) {
+  std::vector<double> coef;
+  coef.reserve(p.n_coeffs);
+  Grid G(p.shape[0], p.shape[1], p.shape[2]);
+  std::copy(u, u + G.v.size(), G.v.begin());
+  for (const Round& rd : p.rounds) G = decompose_round(G, p, rd, coef);
   for (int l = 0; l < p.M; ++l) G = decompose_level(G, p.global[l].data(), coef);
   for (double v : G.v) coef.push_back(v);
   return coef;
 }
 
-std::vector<double> recompose(const double* coef, const Plan& p) {
-  // Coarsest, then global levels coarsest->finest, then the blocks.
-  size_t gstart = (size_t)p.nblocks * p.per_block;
-  std::vector<size_t> gpos(p.M);
-  size_t pos = gstart;
-  for (int l = 0; l < p.M; ++l) { gpos[l] = pos; pos += p.global_counts[l]; }
-  Grid G(p.cshape[0], p.cshape[1], p.cshape[2]);
-  for (size_t t = 0; t < G.v.size(); ++t) G.v[t] = coef[pos + t];
-  for (int l = p.M - 1; l >= 0; --l) {
-    size_t q = gpos[l];
-    G = recompose_level(G, p.global[l].data(), coef, q);
-  }
-  std::vector<double> u((size_t)(p.shape[0] * p.shape[1] * p.shape[2]), 0.0);
+// Inverse of decompose_round: the round's gathered grid G and its
+// coefficients give the round's input grid (in-domain nodes only).
+Grid recompose_round(const Grid& G, const Plan& p, const Round& rd, const double* coef) {
+  Grid out(rd.shape[0], rd.shape[1], rd.shape[2]);
   std::vector<size_t> lpos(p.K);
-  for (int64_t b0 = 0; b0 < p.nb[0]; ++b0)
-    for (int64_t b1 = 0; b1 < p.nb[1]; ++b1)
-      for (int64_t b2 = 0; b2 < p.nb[2]; ++b2) {
-        int64_t bid = (b0 * p.nb[1] + b1) * p.nb[2] + b2;
-        size_t q = (size_t)bid * p.per_block;
+  for (int64_t b0 = 0; b0 < rd.nb[0]; ++b0)
+    for (int64_t b1 = 0; b1 < rd.nb[1]; ++b1)
+      for (int64_t b2 = 0; b2 < rd.nb[2]; ++b2) {
+        int64_t bid = (b0 * rd.nb[1] + b1) * rd.nb[2] + b2;
+        size_t q = rd.off + (size_t)bid * p.per_block;
         for (int l = 0; l < p.K; ++l) {
           lpos[l] = q;
           Level1D L3[3] = {p.local[l], p.local[l], p.local[l]};
@@ -401,11 +432,57 @@ std::vector<double> recompose(const double* coef, const Plan& p) {
           for (int j = 0; j < p.B; ++j)
             for (int k = 0; k < p.B; ++k) {
               int64_t gi = b0 * p.B + i, gj = b1 * p.B + j, gk = b2 * p.B + k;
-              if (gi < p.shape[0] && gj < p.shape[1] && gk < p.shape[2])
-                u[(size_t)((gi * p.shape[1] + gj) * p.shape[2] + gk)] = blk.at(i, j, k);
+              if (gi < rd.shape[0] && gj < rd.shape[1] && gk < rd.shape[2]) out.at(gi, gj, gk) = blk.at(i, j, k);
             }
       }
-  return u;
+  return out;
+}
+
+std::vector<double> recompose(const double* coef, const Plan& p) {
+  // Coarsest, then global levels coarsest->finest, then the rounds last to first.
+  size_t pos = p.rounds.back().off + (size_t)p.rounds.back().nblocks * p.per_block;
+  std::vector<size_t> gpos(p.M);
+  for (int l = 0; l < p.M; ++l) { gpos[l] = pos; pos += p.global_counts[l]; }
+  Grid G(p.cshape[0], p.cshape[1], p.cshape[2]);
+  for (size_t t = 0; t < G.v.size(); ++t) G.v[t] = coef[pos + t];
+  for (int l = p.M - 1; l >= 0; --l) {
+    size_t q = gpos[l];
+    G = recompose_level(G, p.global[l].data(), coef, q);
+  }
+  for (int r = p.R - 1; r >= 0; --r) G = recompose_round(G, p, p.rounds[(size_t)r], coef);
+  return G.v;
+}
+
+// Block tiers of every round (Sec. III-C): a block of round r+1 takes the
+// smallest tolerance (lowest tier) among the round-r blocks whose coarse
+// values it holds.  Empty with a single tier.
+std::vector<std::vector<uint8_t>> round_tiers(const Plan& p, const std::vector<uint8_t>& tier0) {
+  std::vector<std::vector<uint8_t>> t(p.rounds.size());
+  if (tier0.empty()) return t;
+  t[0] = tier0;
+  for (size_t r = 0; r + 1 < p.rounds.size(); ++r) {
+    const Round& a = p.rounds[r];
+    const Round& b = p.rounds[r + 1];
+    t[r + 1].assign((size_t)b.nblocks, 255);
+    for (int64_t j0 = 0; j0 < b.nb[0]; ++j0)
+      for (int64_t j1 = 0; j1 < b.nb[1]; ++j1)
+        for (int64_t j2 = 0; j2 < b.nb[2]; ++j2) {
+          const int64_t j[3] = {j0, j1, j2};
+          int64_t lo[3], hi[3];  // contributing round-r blocks per dimension
+          for (int d = 0; d < 3; ++d) {
+            const int64_t first = j[d] * p.B, last = std::min((j[d] + 1) * p.B, b.shape[d]) - 1;
+            lo[d] = first / p.m;
+            hi[d] = last / p.m;
+          }
+          uint8_t v = 255;
+          for (int64_t i0 = lo[0]; i0 <= hi[0]; ++i0)
+            for (int64_t i1 = lo[1]; i1 <= hi[1]; ++i1)
+              for (int64_t i2 = lo[2]; i2 <= hi[2]; ++i2)
+                v = std::min(v, t[r][(size_t)((i0 * a.nb[1] + i1) * a.nb[2] + i2)]);
+          t[r + 1][(size_t)((j0 * b.nb[1] + j1) * b.nb[2] + j2)] = v;
+        }
+  }
+  return t;
 }
 
 // ---------------------------------------------------------------------------
@@ -488,7 +565,7 @@ double q_of(double tau_p, int N, double A) {
 Budget make_budget(const Plan& p, const std::vector<double>& tau, double max_abs, bool f64) {
   Budget b;
   b.tau = tau;
-  const int N = p.K + p.M;
+  const int N = p.R * p.K + p.M;
   double eps = f64 ? kEps64 : kEps32;
   b.margin = ((kKappa * eps) * (double)(N + 1)) * max_abs;
   std::vector<double> C = level_constants(p);
@@ -534,17 +611,19 @@ QResult quantize(double c, double q, bool f64) {
 
 // Index into the q table of every coefficient, in coefficient order: local
 // levels use the block's tier, global levels and the coarsest array follow.
-std::vector<uint32_t> coeff_q_index(const Plan& p, const std::vector<uint8_t>& block_tier, int ntiers) {
+std::vector<uint32_t> coeff_q_index(const Plan& p, const std::vector<std::vector<uint8_t>>& block_tier,
+                                    int ntiers) {
   std::vector<uint32_t> qi(p.n_coeffs);
   size_t pos = 0;
-  for (int64_t b = 0; b < p.nblocks; ++b) {
-    int tier = block_tier.empty() ? 0 : block_tier[(size_t)b];
-    for (int l = 0; l < p.K; ++l) {
-      Level1D L3[3] = {p.local[l], p.local[l], p.local[l]};
-      size_t cnt = level_detail_count(L3);
-      for (size_t t = 0; t < cnt; ++t) qi[pos++] = (uint32_t)(tier * p.K + l);
+  for (size_t r = 0; r < p.rounds.size(); ++r)
+    for (int64_t b = 0; b < p.rounds[r].nblocks; ++b) {
+      int tier = block_tier[r].empty() ? 0 : block_tier[r][(size_t)b];
+      for (int l = 0; l < p.K; ++l) {
+        Level1D L3[3] = {p.local[l], p.local[l], p.local[l]};
+        size_t cnt = level_detail_count(L3);
+        for (size_t t = 0; t < cnt; ++t) qi[pos++] = (uint32_t)(tier * p.K + l);
+      }
     }
-  }
   for (int l = 0; l < p.M; ++l)
     for (size_t t = 0; t < p.global_counts[l]; ++t) qi[pos++] = (uint32_t)(ntiers * p.K + l);
   for (size_t t = 0; t < p.coarsest; ++t) qi[pos++] = (uint32_t)(ntiers * p.K + p.M);
@@ -771,7 +850,7 @@ bool huffman_decode(const std::vector<uint8_t>& len, const uint32_t* chunk_words
 }
 
 struct CompressOpts {
-  int B = 9, K = 1, M = 2, chunk = 2048, radius = 4096;
+  int B = 9, K = 1, M = 2, chunk = 2048, radius = 4096, R = 1;
 };
 
 thread_local std::string g_err;
@@ -779,7 +858,7 @@ thread_local std::string g_err;
 // Full compression of an FP64 copy of the field (f64 says what the original dtype was).
 std::vector<uint8_t> compress(const double* u, const int64_t* shape, bool f64, double tol, int rel,
                               const double* roi, const CompressOpts& o, std::vector<int64_t>* codes_out) {
-  Plan p = make_plan(shape, o.B, o.K, o.M);
+  Plan p = make_plan(shape, o.B, o.K, o.M, o.R);
   const size_t nel = (size_t)(shape[0] * shape[1] * shape[2]);
   double max_abs = 0.0;
   bool finite = true;
@@ -812,7 +891,7 @@ std::vector<uint8_t> compress(const double* u, const int64_t* shape, bool f64, d
   std::vector<int32_t> out_code;  // codes of the escaped symbols, in stream order
   if (!raw) {
     std::vector<double> coef = decompose(u, p);
-    std::vector<uint32_t> qi = coeff_q_index(p, block_tier, ntiers);
+    std::vector<uint32_t> qi = coeff_q_index(p, round_tiers(p, ntiers > 1 ? block_tier : std::vector<uint8_t>()), ntiers);
     sym.resize(p.n_coeffs);
     if (codes_out) codes_out->resize(p.n_coeffs);
     for (size_t i = 0; i < p.n_coeffs && !raw; ++i) {
@@ -875,6 +954,7 @@ std::vector<uint8_t> compress(const double* u, const int64_t* shape, bool f64, d
   w.put_at<uint32_t>(192, (uint32_t)h.codebook.size());
   w.put_at<uint32_t>(196, h.n_runs);
   w.put_at<double>(200, bud.margin);
+  w.put_at<uint32_t>(224, (uint32_t)(o.R - 1));
   w.put_at<uint64_t>(128, (uint64_t)w.b.size());
   for (double t : tiers) w.put<double>(t);
   w.pad8();
@@ -883,7 +963,8 @@ std::vector<uint8_t> compress(const double* u, const int64_t* shape, bool f64, d
   w.pad8();
   w.put_at<uint64_t>(144, (uint64_t)w.b.size());
   if (ntiers > 1)
-    for (uint8_t t : block_tier) w.put<uint8_t>(t);
+    for (const auto& rt : round_tiers(p, block_tier))
+      for (uint8_t t : rt) w.put<uint8_t>(t);
   w.pad8();
   w.put_at<uint64_t>(152, (uint64_t)w.b.size());
   for (uint32_t c : h.chunk_words) w.put<uint32_t>(c);
@@ -938,16 +1019,21 @@ bool decompress(const uint8_t* s, size_t nbytes, std::vector<double>& u, int64_t
   o.chunk = rd<int32_t>(s, 48);
   o.radius = rd<int32_t>(s, 52);
   int ntiers = rd<int32_t>(s, 56);
-  Plan p = make_plan(shape, o.B, o.K, o.M);
+  o.R = (int)rd<uint32_t>(s, 224) + 1;
+  if (o.R > 16) { g_err = "rounds"; return false; }
+  Plan p = make_plan(shape, o.B, o.K, o.M, o.R);
   uint64_t nsym = rd<uint64_t>(s, 96), nch = rd<uint64_t>(s, 104), nout = rd<uint64_t>(s, 112),
            nwords = rd<uint64_t>(s, 120);
   if (nsym != p.n_coeffs) { g_err = "symbol count"; return false; }
   const double* q = reinterpret_cast<const double*>(s + rd<uint64_t>(s, 136));
   std::vector<double> qv(q, q + (size_t)ntiers * o.K + o.M + 1);
-  std::vector<uint8_t> block_tier;
+  std::vector<std::vector<uint8_t>> block_tier(p.rounds.size());
   if (ntiers > 1) {
     const uint8_t* bt = s + rd<uint64_t>(s, 144);
-    block_tier.assign(bt, bt + p.nblocks);
+    for (size_t r = 0; r < p.rounds.size(); ++r) {
+      block_tier[r].assign(bt, bt + p.rounds[r].nblocks);
+      bt += p.rounds[r].nblocks;
+    }
   }
   std::vector<uint32_t> chunk_words(nch);
   std::memcpy(chunk_words.data(), s + rd<uint64_t>(s, 152), nch * 4);
@@ -1009,9 +1095,9 @@ int or_level_1d(int n, const double* x, double* I, double* Mf, double* Mc, doubl
 // Sizes of the hierarchy: out[0]=n_coeffs, [1]=per_block, [2]=nblocks, [3]=m,
 // [4..6]=gathered grid, [7..9]=coarsest grid, [10]=coarsest count,
 // [11..11+M) = global level counts.
-int or_plan(const int64_t* shape, int B, int K, int M, int64_t* out) {
+int or_plan_r(const int64_t* shape, int B, int K, int M, int R, int64_t* out) {
   try {
-    Plan p = make_plan(shape, B, K, M);
+    Plan p = make_plan(shape, B, K, M, R);
     out[0] = (int64_t)p.n_coeffs;
     out[1] = (int64_t)p.per_block;
     out[2] = p.nblocks;
@@ -1023,22 +1109,51 @@ int or_plan(const int64_t* shape, int B, int K, int M, int64_t* out) {
   } catch (const std::exception& e) { g_err = e.what(); return 1; }
 }
 
-int or_decompose(const double* u, const int64_t* shape, int B, int K, int M, double* coef_out) {
+int or_plan(const int64_t* shape, int B, int K, int M, int64_t* out) { return or_plan_r(shape, B, K, M, 1, out); }
+
+// Blocks of every round (out[r]) and the tiers of every round's blocks
+// propagated from round 0's (tier_out, concatenated; only if tier0 != null).
+int or_rounds(const int64_t* shape, int B, int K, int R, const uint8_t* tier0, int64_t* nblocks_out,
+              uint8_t* tier_out) {
   try {
-    Plan p = make_plan(shape, B, K, M);
+    Plan p = make_plan(shape, B, K, 0, R);
+    for (int r = 0; r < R; ++r) nblocks_out[r] = p.rounds[(size_t)r].nblocks;
+    if (tier0 && tier_out) {
+      std::vector<uint8_t> t0(tier0, tier0 + p.nblocks);
+      size_t o = 0;
+      for (const auto& rt : round_tiers(p, t0)) {
+        std::memcpy(tier_out + o, rt.data(), rt.size());
+        o += rt.size();
+      }
+    }
+    return 0;
+  } catch (const std::exception& e) { g_err = e.what(); return 1; }
+}
+
+int or_decompose_r(const double* u, const int64_t* shape, int B, int K, int M, int R, double* coef_out) {
+  try {
+    Plan p = make_plan(shape, B, K, M, R);
     std::vector<double> c = decompose(u, p);
     std::memcpy(coef_out, c.data(), c.size() * 8);
     return 0;
   } catch (const std::exception& e) { g_err = e.what(); return 1; }
 }
 
-int or_recompose(const double* coef, const int64_t* shape, int B, int K, int M, double* u_out) {
+int or_decompose(const double* u, const int64_t* shape, int B, int K, int M, double* coef_out) {
+  return or_decompose_r(u, shape, B, K, M, 1, coef_out);
+}
+
+int or_recompose_r(const double* coef, const int64_t* shape, int B, int K, int M, int R, double* u_out) {
   try {
-    Plan p = make_plan(shape, B, K, M);
+    Plan p = make_plan(shape, B, K, M, R);
     std::vector<double> u = recompose(coef, p);
     std::memcpy(u_out, u.data(), u.size() * 8);
     return 0;
   } catch (const std::exception& e) { g_err = e.what(); return 1; }
+}
+
+int or_recompose(const double* coef, const int64_t* shape, int B, int K, int M, double* u_out) {
+  return or_recompose_r(coef, shape, B, K, M, 1, u_out);
 }
 
 // Coefficients of one block (its K local levels, in stream order) and its m^3 coarse values.
@@ -1078,10 +1193,10 @@ int or_level_constants(const int64_t* shape, int B, int K, int M, double* out) {
 
 // Quantiser widths for tiers tau[0..ntiers): out = [tier*K + l], M global, coarsest;
 // meta[0] = margin, meta[1] = raw flag.
-int or_budget(const int64_t* shape, int B, int K, int M, const double* tau, int ntiers, double max_abs, int f64,
-              double* q_out, double* meta) {
+int or_budget_r(const int64_t* shape, int B, int K, int M, int R, const double* tau, int ntiers, double max_abs,
+                int f64, double* q_out, double* meta) {
   try {
-    Plan p = make_plan(shape, B, K, M);
+    Plan p = make_plan(shape, B, K, M, R);
     std::vector<double> t(tau, tau + ntiers);
     Budget b = make_budget(p, t, max_abs, f64 != 0);
     std::memcpy(q_out, b.q.data(), b.q.size() * 8);
@@ -1089,6 +1204,11 @@ int or_budget(const int64_t* shape, int B, int K, int M, const double* tau, int 
     meta[1] = b.raw ? 1.0 : 0.0;
     return 0;
   } catch (const std::exception& e) { g_err = e.what(); return 1; }
+}
+
+int or_budget(const int64_t* shape, int B, int K, int M, const double* tau, int ntiers, double max_abs, int f64,
+              double* q_out, double* meta) {
+  return or_budget_r(shape, B, K, M, 1, tau, ntiers, max_abs, f64, q_out, meta);
 }
 
 int64_t or_quantize(double c, double q, int f64, int* overflow) {
@@ -1147,12 +1267,12 @@ int or_huffman_decode(const uint8_t* codebook, uint64_t cb_bytes, uint32_t n_run
 // Compress a field given as FP64 values (dtype_f64 = 1 if the original is FP64).
 // roi may be null (one tolerance per block otherwise). codes_out (optional,
 // n_coeffs entries) receives the integer codes.
-int or_compress(const double* u, const int64_t* shape, int dtype_f64, double tol, int rel, const double* roi, int B,
-                int K, int M, int chunk, int radius, uint8_t* out, uint64_t cap, uint64_t* out_bytes,
-                int64_t* codes_out) {
+int or_compress_r(const double* u, const int64_t* shape, int dtype_f64, double tol, int rel, const double* roi, int B,
+                  int K, int M, int R, int chunk, int radius, uint8_t* out, uint64_t cap, uint64_t* out_bytes,
+                  int64_t* codes_out) {
   try {
     CompressOpts o;
-    o.B = B; o.K = K; o.M = M; o.chunk = chunk; o.radius = radius;
+    o.B = B; o.K = K; o.M = M; o.R = R; o.chunk = chunk; o.radius = radius;
     std::vector<int64_t> codes;
     std::vector<uint8_t> s = compress(u, shape, dtype_f64 != 0, tol, rel, roi, o, codes_out ? &codes : nullptr);
     *out_bytes = s.size();
@@ -1161,6 +1281,12 @@ int or_compress(const double* u, const int64_t* shape, int dtype_f64, double tol
     if (codes_out && !codes.empty()) std::memcpy(codes_out, codes.data(), codes.size() * 8);
     return 0;
   } catch (const std::exception& e) { g_err = e.what(); return 1; }
+}
+
+int or_compress(const double* u, const int64_t* shape, int dtype_f64, double tol, int rel, const double* roi, int B,
+                int K, int M, int chunk, int radius, uint8_t* out, uint64_t cap, uint64_t* out_bytes,
+                int64_t* codes_out) {
+  return or_compress_r(u, shape, dtype_f64, tol, rel, roi, B, K, M, 1, chunk, radius, out, cap, out_bytes, codes_out);
 }
 
 // Decompress into FP64 values u_out (shape from the header); codes_out optional.
