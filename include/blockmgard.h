@@ -65,6 +65,11 @@ typedef struct {
                           (default 2048)                                                 */
   int dict_radius;     /* quantisation codes with |code| < radius become symbols
                           code + radius; others are outliers.  16..4096 (default 4096)   */
+  int rounds;          /* R, 1..8 (0 = 1): re-blocking rounds of K in-cache levels each;
+                          round r+1 re-blocks round r's gathered coarse values and takes
+                          the strictest tolerance among the blocks each new block holds
+                          coarse values of (Sec. III-C).  With R > 1 the global levels use
+                          index coordinates; the adjoint entry points need R = 1.       */
 } bm_params;
 
 /* Upper bound on the stream size for a field of this shape and dtype: the raw

@@ -36,7 +36,7 @@ class BlockMGARDError(RuntimeError):
 
 class _Params(ctypes.Structure):
     _fields_ = [("block_nodes", ctypes.c_int), ("incache_levels", ctypes.c_int), ("global_levels", ctypes.c_int),
-                ("chunk_symbols", ctypes.c_int), ("dict_radius", ctypes.c_int)]
+                ("chunk_symbols", ctypes.c_int), ("dict_radius", ctypes.c_int), ("rounds", ctypes.c_int)]
 
 
 class _BatchItem(ctypes.Structure):
@@ -138,8 +138,9 @@ def _dtype(t):
     raise TypeError("fields must be float32 or float64")
 
 
-def _params(block=17, levels=2, global_levels=2, chunk=2048, radius=4096):
-    return _Params(int(block), int(levels), int(global_levels) if global_levels != 0 else -1, int(chunk), int(radius))
+def _params(block=17, levels=2, global_levels=2, chunk=2048, radius=4096, rounds=1):
+    return _Params(int(block), int(levels), int(global_levels) if global_levels != 0 else -1, int(chunk), int(radius),
+                   int(rounds))
 
 
 def _dev_check(t):
@@ -154,7 +155,7 @@ def compress_bound(shape, dtype=torch.float32) -> int:
 
 
 def compress(field: torch.Tensor, tol: float, mode: str = "rel", roi=None, block=17, levels=2, global_levels=2,
-             chunk=2048, radius=4096, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+             chunk=2048, radius=4096, out: torch.Tensor | None = None, stream=None, rounds=1) -> torch.Tensor:
     """Compress a 3-D float32/float64 CUDA tensor; returns the stream as a
     uint8 CUDA tensor (a view of ``out`` when given).  ``roi``: optional
     per-block tolerances (same mode as ``tol``), row-major over the block grid."""
@@ -173,7 +174,7 @@ def compress(field: torch.Tensor, tol: float, mode: str = "rel", roi=None, block
         r = np.ascontiguousarray(np.asarray(roi, dtype=np.float64).ravel())
         roi_ptr = r.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     nbytes = ctypes.c_size_t(0)
-    p = _params(block, levels, global_levels, chunk, radius)
+    p = _params(block, levels, global_levels, chunk, radius, rounds)
     with torch.cuda.device(field.device):
         _check(L.bm_compress(ctypes.c_void_p(field.data_ptr()), 3, _shape(field.shape), _dtype(field.dtype),
                              float(tol), BM_REL if mode == "rel" else BM_ABS, roi_ptr, ctypes.byref(p),
@@ -183,7 +184,7 @@ def compress(field: torch.Tensor, tol: float, mode: str = "rel", roi=None, block
 
 
 def compress_batch(fields, tols, mode: str = "rel", rois=None, block=17, levels=2, global_levels=2, chunk=2048,
-                   radius=4096, outs=None, stream=None):
+                   radius=4096, outs=None, stream=None, rounds=1):
     """Compress several 3-D CUDA fields in one call (pipelines queued on the
     library's stream pool, one synchronisation).  ``tols``: one tolerance per
     field; ``rois``: None or one per-block tolerance map (or None) per field;
@@ -197,7 +198,7 @@ def compress_batch(fields, tols, mode: str = "rel", rois=None, block=17, levels=
     items = (_BatchItem * max(n, 1))()
     keep = []
     bufs = []
-    p = _params(block, levels, global_levels, chunk, radius)
+    p = _params(block, levels, global_levels, chunk, radius, rounds)
     for i, f in enumerate(fields):
         _dev_check(f)
         if f.dim() != 3:
@@ -290,29 +291,30 @@ def decompress(buf: torch.Tensor, out: torch.Tensor | None = None, stream=None) 
     return out
 
 
-def coeff_count(shape, block=17, levels=2, global_levels=2) -> int:
+def coeff_count(shape, block=17, levels=2, global_levels=2, rounds=1) -> int:
     n = ctypes.c_size_t(0)
-    p = _params(block, levels, global_levels)
+    p = _params(block, levels, global_levels, rounds=rounds)
     _check(load().bm_coeff_count(3, _shape(shape), ctypes.byref(p), ctypes.byref(n)))
     return n.value
 
 
-def decompose(field: torch.Tensor, block=17, levels=2, global_levels=2, stream=None) -> torch.Tensor:
+def decompose(field: torch.Tensor, block=17, levels=2, global_levels=2, stream=None, rounds=1) -> torch.Tensor:
     """Full-precision multilevel coefficients in stream order."""
     _dev_check(field)
-    n = coeff_count(field.shape, block, levels, global_levels)
+    n = coeff_count(field.shape, block, levels, global_levels, rounds)
     out = torch.empty(n, dtype=field.dtype, device=field.device)
-    p = _params(block, levels, global_levels)
+    p = _params(block, levels, global_levels, rounds=rounds)
     with torch.cuda.device(field.device):
         _check(load().bm_decompose(ctypes.c_void_p(field.data_ptr()), 3, _shape(field.shape), _dtype(field.dtype),
                                    ctypes.byref(p), ctypes.c_void_p(out.data_ptr()), _stream(stream)))
     return out
 
 
-def recompose(coeffs: torch.Tensor, shape, block=17, levels=2, global_levels=2, stream=None) -> torch.Tensor:
+def recompose(coeffs: torch.Tensor, shape, block=17, levels=2, global_levels=2, stream=None,
+              rounds=1) -> torch.Tensor:
     _dev_check(coeffs)
     out = torch.empty(tuple(shape), dtype=coeffs.dtype, device=coeffs.device)
-    p = _params(block, levels, global_levels)
+    p = _params(block, levels, global_levels, rounds=rounds)
     with torch.cuda.device(coeffs.device):
         _check(load().bm_recompose(ctypes.c_void_p(coeffs.data_ptr()), 3, _shape(shape), _dtype(coeffs.dtype),
                                    ctypes.byref(p), ctypes.c_void_p(out.data_ptr()), _stream(stream)))

@@ -213,7 +213,7 @@ struct PlanDev {
   std::vector<GLevel<double>> gd;
 };
 std::mutex g_plan_mu;
-std::map<std::tuple<int64_t, int64_t, int64_t, int, int, int>, std::unique_ptr<PlanDev>> g_plans;
+std::map<std::tuple<int64_t, int64_t, int64_t, int, int, int, int>, std::unique_ptr<PlanDev>> g_plans;
 
 template <typename T>
 std::vector<GLevel<T>>& glevels(PlanDev& p);
@@ -303,13 +303,13 @@ bm_status upload_tables(PlanDev& P) {
   return BM_OK;
 }
 
-bm_status get_plan(const int64_t* shape, int B, int K, int M, PlanDev** out) {
+bm_status get_plan(const int64_t* shape, int B, int K, int M, int R, PlanDev** out) {
   std::lock_guard<std::mutex> g(g_plan_mu);
-  auto key = std::make_tuple(shape[0], shape[1], shape[2], B, K, M);
+  auto key = std::make_tuple(shape[0], shape[1], shape[2], B, K, M, R);
   auto it = g_plans.find(key);
   if (it == g_plans.end()) {
     auto p = std::make_unique<PlanDev>();
-    std::string err = make_plan(shape, B, K, M, p->h);
+    std::string err = make_plan(shape, B, K, M, R, p->h);
     if (!err.empty()) return fail(BM_ERR_ARG, err);
     it = g_plans.emplace(key, std::move(p)).first;
   }
@@ -320,7 +320,7 @@ bm_status get_plan(const int64_t* shape, int B, int K, int M, PlanDev** out) {
 // ---------------------------------------------------------------------------
 // Parameters and shapes
 // ---------------------------------------------------------------------------
-struct Params { int B, K, M, chunk, radius; };
+struct Params { int B, K, M, chunk, radius, R; };
 
 bm_status check_params(const bm_params* p, Params& o) {
   o.B = (p && p->block_nodes) ? p->block_nodes : 17;
@@ -329,6 +329,8 @@ bm_status check_params(const bm_params* p, Params& o) {
   if (p && p->global_levels < 0) o.M = 0;
   o.chunk = (p && p->chunk_symbols) ? p->chunk_symbols : 2048;
   o.radius = (p && p->dict_radius) ? p->dict_radius : 4096;
+  o.R = (p && p->rounds) ? p->rounds : 1;
+  if (o.R < 1 || o.R > 8) return fail(BM_ERR_ARG, "rounds must be in [1, 8]");
   if (o.B != 9 && o.B != 17) return fail(BM_ERR_UNSUPPORTED, "block_nodes must be 9 or 17 in this build");
   const int kmax = o.B == 9 ? 3 : 4;
   if (o.K < 1 || o.K > kmax) return fail(BM_ERR_ARG, "incache_levels out of range for this block size");
@@ -405,7 +407,7 @@ __device__ __forceinline__ void maxabs_acc(T x, T& m, bool& bad) {
 struct QtabArgs {
   int enabled;
   const double* tiers;  // relative or absolute, ascending
-  int ntiers, rel, K, M;
+  int ntiers, rel, K, M, R;
   double A[24];
   double kappa, eps;
   double* qd;           // [ntiers*K + M + 1]
@@ -419,7 +421,7 @@ struct QtabArgs {
 __device__ void qtab_compute(const QtabArgs& a) {
   const double max_abs = a.f64 ? __longlong_as_double((long long)a.sc->maxabs_bits)
                                : (double)__uint_as_float((unsigned)a.sc->maxabs_bits);
-  const int N = a.K + a.M;
+  const int N = a.R * a.K + a.M;
   const double t = (double)(N + 1);
   const double margin = __dmul_rn(__dmul_rn(__dmul_rn(a.kappa, a.eps), t), max_abs);
   bool raw = !isfinite(max_abs);
@@ -505,7 +507,7 @@ __global__ void __launch_bounds__(256) maxabs_kernel(const T* __restrict__ u, in
 
 struct HeaderArgs {
   uint8_t* out;
-  int f64, B, K, M, chunk, radius, ntiers, m, rel;
+  int f64, B, K, M, chunk, radius, ntiers, m, rel, R;
   int64_t shape[3];
   int nb[3];
   double tol;
@@ -558,7 +560,8 @@ __global__ void header_kernel(HeaderArgs a) {
   put<double>(o, 200, sc->margin);
   put<uint64_t>(o, 208, sc->off_chunk_esc);
   put<uint64_t>(o, 216, a.off_splits);
-  for (int i = 224; i < kHeaderBytes; ++i) o[i] = 0;
+  put<uint32_t>(o, 224, (uint32_t)(a.R - 1));
+  for (int i = 228; i < kHeaderBytes; ++i) o[i] = 0;
   const unsigned long long cend = sc->off_chunk_esc + (sc->n_outliers ? 4ull * a.n_chunks : 0ull);
   for (unsigned long long i = cend; i < sc->off_outliers; ++i) o[i] = 0;
   const unsigned long long oend = sc->off_outliers + 4ull * sc->n_outliers;
@@ -776,6 +779,19 @@ struct FwdOut {
   Scalars* sc = nullptr;
 };
 
+// Gathered grids of the re-blocking rounds: every round but the last writes
+// its own (carved from the workspace); the last writes the global levels'
+// input.
+template <typename T>
+std::vector<T*> round_grids(const PlanHost& h, Carver& cv, T* last) {
+  std::vector<T*> g;
+  for (size_t r = 0; r < h.rounds.size(); ++r) {
+    const RoundHost& rd = h.rounds[r];
+    g.push_back(r + 1 < h.rounds.size() ? cv.take<T>((size_t)(rd.gshape[0] * rd.gshape[1] * rd.gshape[2])) : last);
+  }
+  return g;
+}
+
 template <typename T>
 bm_status run_decompose(PlanDev& P, const T* field, int mode, const FwdOut<T>& o, Carver& cv, cudaStream_t s,
                         const std::function<bm_status()>& after_block = nullptr) {
@@ -787,18 +803,27 @@ bm_status run_decompose(PlanDev& P, const T* field, int mode, const FwdOut<T>& o
   T* Dbuf = cv.take<T>((size_t)gs.D);
   T* W1 = cv.take<T>((size_t)std::max<int64_t>(gs.W1, 1));
   T* W2 = cv.take<T>((size_t)std::max<int64_t>(gs.W2, 1));
+  std::vector<T*> Gr = round_grids<T>(h, cv, U[0]);
   {
     Stage st("incache_decompose");
-    BlockArgs<T> a{};
-    a.field = const_cast<T*>(field);
-    a.n0 = h.shape[0]; a.n1 = h.shape[1]; a.n2 = h.shape[2];
-    a.nb0 = h.nb[0]; a.nb1 = h.nb[1]; a.nb2 = h.nb[2];
-    a.nblocks = h.nblocks;
-    a.G = U[0];
-    a.g1 = h.gshape[1]; a.g2 = h.gshape[2];
-    a.sym = o.sym; a.esc = o.esc; a.coef = o.coef;
-    a.tier = o.tier; a.rq = o.rq; a.hist = o.hist; a.radius = o.radius; a.sc = o.sc;
-    BM_CUDA(launch_block<T>(0, h.B, h.K, mode, a, s));
+    int64_t toff = 0;
+    for (size_t r = 0; r < h.rounds.size(); ++r) {  // each round blocks the previous round's gathered grid
+      const RoundHost& rd = h.rounds[r];
+      BlockArgs<T> a{};
+      a.field = r == 0 ? const_cast<T*>(field) : Gr[r - 1];
+      a.n0 = rd.shape[0]; a.n1 = rd.shape[1]; a.n2 = rd.shape[2];
+      a.nb0 = rd.nb[0]; a.nb1 = rd.nb[1]; a.nb2 = rd.nb[2];
+      a.nblocks = rd.nblocks;
+      a.G = Gr[r];
+      a.g1 = rd.gshape[1]; a.g2 = rd.gshape[2];
+      a.sym = o.sym ? o.sym + rd.off : nullptr;
+      a.esc = o.esc ? o.esc + rd.off : nullptr;
+      a.coef = o.coef ? o.coef + rd.off : nullptr;
+      a.tier = o.tier ? o.tier + toff : nullptr;
+      a.rq = o.rq; a.hist = o.hist; a.radius = o.radius; a.sc = o.sc;
+      BM_CUDA(launch_block<T>(0, h.B, h.K, mode, a, s));
+      toff += rd.nblocks;
+    }
   }
   if (after_block)
     if (bm_status st = after_block()) return st;
@@ -861,6 +886,7 @@ bm_status run_recompose(PlanDev& P, T* field, int mode, const InvIn<T>& in, Carv
   T* W1 = cv.take<T>((size_t)std::max<int64_t>(gs.W1, 1));
   T* W2 = cv.take<T>((size_t)std::max<int64_t>(gs.W2, 1));
   (void)Dbuf;
+  std::vector<T*> Gr = round_grids<T>(h, cv, U[0]);
   {
     Stage st("coarsest");
     const int64_t cnt = gs.U[h.M];
@@ -889,22 +915,27 @@ bm_status run_recompose(PlanDev& P, T* field, int mode, const InvIn<T>& in, Carv
   }
   {
     Stage st("incache_recompose");
-    BlockArgs<T> a{};
-    a.field = field;
-    a.n0 = h.shape[0]; a.n1 = h.shape[1]; a.n2 = h.shape[2];
-    a.nb0 = h.nb[0]; a.nb1 = h.nb[1]; a.nb2 = h.nb[2];
-    a.nblocks = h.nblocks;
-    a.G = U[0];
-    a.g1 = h.gshape[1]; a.g2 = h.gshape[2];
-    a.sym = const_cast<uint16_t*>(in.sym);
-    a.esc = const_cast<int32_t*>(in.esc);
-    a.coef = const_cast<T*>(in.coef);
-    a.tier = in.tier;
-    a.q = in.q;
-    a.radius = in.radius;
-    a.ntiers = in.ntiers;
-    a.sc = in.sc;
-    BM_CUDA(launch_block<T>(1, h.B, h.K, mode, a, s));
+    std::vector<int64_t> toff(h.rounds.size(), 0);
+    for (size_t r = 1; r < h.rounds.size(); ++r) toff[r] = toff[r - 1] + h.rounds[r - 1].nblocks;
+    for (size_t rr = h.rounds.size(); rr-- > 0;) {  // last round first: each restores its input grid
+      const RoundHost& rd = h.rounds[rr];
+      BlockArgs<T> a{};
+      a.field = rr == 0 ? field : Gr[rr - 1];
+      a.n0 = rd.shape[0]; a.n1 = rd.shape[1]; a.n2 = rd.shape[2];
+      a.nb0 = rd.nb[0]; a.nb1 = rd.nb[1]; a.nb2 = rd.nb[2];
+      a.nblocks = rd.nblocks;
+      a.G = Gr[rr];
+      a.g1 = rd.gshape[1]; a.g2 = rd.gshape[2];
+      a.sym = in.sym ? const_cast<uint16_t*>(in.sym) + rd.off : nullptr;
+      a.esc = in.esc ? const_cast<int32_t*>(in.esc) + rd.off : nullptr;
+      a.coef = in.coef ? const_cast<T*>(in.coef) + rd.off : nullptr;
+      a.tier = in.tier ? in.tier + toff[rr] : nullptr;
+      a.q = in.q;
+      a.radius = in.radius;
+      a.ntiers = in.ntiers;
+      a.sc = in.sc;
+      BM_CUDA(launch_block<T>(1, h.B, h.K, mode, a, s));
+    }
   }
   return BM_OK;
 }
@@ -913,6 +944,8 @@ size_t decompose_scratch(const PlanHost& h, size_t esize) {
   const GSizes gs = gsizes(h);
   size_t b = 0;
   for (int64_t u : gs.U) b += (size_t)u * esize + 256;
+  for (size_t r = 0; r + 1 < h.rounds.size(); ++r)
+    b += (size_t)(h.rounds[r].gshape[0] * h.rounds[r].gshape[1] * h.rounds[r].gshape[2]) * esize + 256;
   b += ((size_t)gs.D + gs.W1 + gs.W2 + 3) * esize + 768;
   return b;
 }
@@ -929,10 +962,42 @@ StreamLayout layout(const PlanHost& h, int ntiers, int chunk) {
   L.off_tiers = kHeaderBytes;
   L.off_qtab = L.off_tiers + pad8(8ull * ntiers);
   L.off_btier = L.off_qtab + pad8(8ull * L.nq);
-  L.off_chunks = L.off_btier + (ntiers > 1 ? pad8((unsigned long long)h.nblocks) : 0ull);
+  L.off_chunks = L.off_btier + (ntiers > 1 ? pad8((unsigned long long)h.nblocks_all) : 0ull);
   L.off_splits = L.off_chunks + pad8(4ull * L.nch);
   L.off_codebook = L.off_splits + pad8(2ull * (kSplits - 1) * L.nch);
   return L;
+}
+
+// Block tiers of the rounds after the first (Sec. III-C), appended to t
+// (which holds round 0's): every round-r block pushes its tier to the
+// round-(r+1) blocks its gathered coarse values fall into, which keep the
+// lowest (the strictest tolerance).
+void propagate_tiers(const PlanHost& h, std::vector<uint8_t>& t) {
+  size_t base = 0;
+  for (size_t r = 0; r + 1 < h.rounds.size(); ++r) {
+    const RoundHost& a = h.rounds[r];
+    const RoundHost& b = h.rounds[r + 1];
+    const size_t nbase = t.size();
+    t.resize(nbase + (size_t)b.nblocks, 255);
+    for (int64_t i0 = 0; i0 < a.nb[0]; ++i0)
+      for (int64_t i1 = 0; i1 < a.nb[1]; ++i1)
+        for (int64_t i2 = 0; i2 < a.nb[2]; ++i2) {
+          const uint8_t v = t[base + (size_t)((i0 * a.nb[1] + i1) * a.nb[2] + i2)];
+          const int64_t i[3] = {i0, i1, i2};
+          int64_t lo[3], hi[3];
+          for (int d = 0; d < 3; ++d) {
+            lo[d] = i[d] * h.m / h.B;
+            hi[d] = ((i[d] + 1) * h.m - 1) / h.B;
+          }
+          for (int64_t j0 = lo[0]; j0 <= hi[0]; ++j0)
+            for (int64_t j1 = lo[1]; j1 <= hi[1]; ++j1)
+              for (int64_t j2 = lo[2]; j2 <= hi[2]; ++j2) {
+                uint8_t& w = t[nbase + (size_t)((j0 * b.nb[1] + j1) * b.nb[2] + j2)];
+                w = std::min(w, v);
+              }
+        }
+    base = nbase;
+  }
 }
 
 // Pinned host staging and result of one item of a batched compress.
@@ -953,7 +1018,7 @@ template <typename T>
 bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, double tol, int rel, const double* roi,
                      uint8_t* out, size_t cap, size_t* out_bytes, cudaStream_t s, BatchSlot* bs = nullptr) {
   PlanDev* P = nullptr;
-  if (bm_status st = get_plan(shape, prm.B, prm.K, prm.M, &P)) return st;
+  if (bm_status st = get_plan(shape, prm.B, prm.K, prm.M, prm.R, &P)) return st;
   const PlanHost& h = P->h;
   if (h.n_coeffs >= (int64_t(1) << 31)) return fail(BM_ERR_UNSUPPORTED, "more than 2^31 - 1 coefficients");
   if (prm.M + prm.K > 24) return fail(BM_ERR_ARG, "too many levels");
@@ -978,6 +1043,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
       btier.resize((size_t)h.nblocks);
       for (int64_t b = 0; b < h.nblocks; ++b)
         btier[(size_t)b] = (uint8_t)(std::lower_bound(tiers.begin(), tiers.end(), bt[(size_t)b]) - tiers.begin());
+      propagate_tiers(h, btier);
     }
   }
   const int ntiers = (int)tiers.size();
@@ -993,11 +1059,11 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   Carver probe;
   carve_all(probe, nullptr);
   probe.take<Scalars>(1); probe.take<unsigned>(dict); probe.take<uint8_t>(dict); probe.take<unsigned>(dict);
-  probe.take<double>(L.nq); probe.take<T>(L.nq); probe.take<double>(ntiers); probe.take<uint8_t>(h.nblocks);
+  probe.take<double>(L.nq); probe.take<T>(L.nq); probe.take<double>(ntiers); probe.take<uint8_t>(h.nblocks_all);
   probe.take<uint16_t>((size_t)h.n_coeffs); probe.take<int32_t>((size_t)h.n_coeffs);
   probe.take<unsigned char>(256 + 16ull * L.nch);
   const size_t need = probe.off + decompose_scratch(h, sizeof(T)) + 4096;
-  const size_t hneed = sizeof(Scalars) + 8 * ntiers + (size_t)h.nblocks + 4096;
+  const size_t hneed = 256 + 8 * 256 + (size_t)h.nblocks_all + 4096;
   Workspace* ws = nullptr;
   if (bm_status st = get_ws(s, need, hneed, &ws)) return st;
   carve_all(cv, reinterpret_cast<unsigned char*>(ws->d));
@@ -1008,7 +1074,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   double* qd = cv.take<double>(L.nq);
   T* rq = cv.take<T>(L.nq);
   double* dtiers = cv.take<double>(ntiers);
-  uint8_t* dbt = cv.take<uint8_t>(h.nblocks);
+  uint8_t* dbt = cv.take<uint8_t>(h.nblocks_all);
   uint16_t* sym = cv.take<uint16_t>((size_t)h.n_coeffs);
   int32_t* esc = cv.take<int32_t>((size_t)h.n_coeffs);
   unsigned char* tickets = cv.take<unsigned char>(256 + 16ull * L.nch);  // ticket, then look-back status words
@@ -1029,10 +1095,10 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     BM_CUDA(cudaMemsetAsync(sc, 0, sizeof(Scalars), s));
     BM_CUDA(cudaMemsetAsync(hist, 0, 4ull * dict, s));
     BM_CUDA(cudaMemcpyAsync(dtiers, htiers, 8 * ntiers, cudaMemcpyHostToDevice, s));
-    if (ntiers > 1) BM_CUDA(cudaMemcpyAsync(dbt, hbt, (size_t)h.nblocks, cudaMemcpyHostToDevice, s));
+    if (ntiers > 1) BM_CUDA(cudaMemcpyAsync(dbt, hbt, (size_t)h.nblocks_all, cudaMemcpyHostToDevice, s));
     if (prefix_fits) {
       BM_CUDA(cudaMemsetAsync(out, 0, L.off_codebook, s));
-      if (ntiers > 1) BM_CUDA(cudaMemcpyAsync(out + L.off_btier, dbt, (size_t)h.nblocks, cudaMemcpyDeviceToDevice, s));
+      if (ntiers > 1) BM_CUDA(cudaMemcpyAsync(out + L.off_btier, dbt, (size_t)h.nblocks_all, cudaMemcpyDeviceToDevice, s));
     }
   }
   const int mgrid = (int)std::min<int64_t>((int64_t)num_sms() * 8, std::max<int64_t>(1, (nel + 4095) / 4096));
@@ -1040,7 +1106,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     Stage st("maxabs");
     QtabArgs qa{};
     qa.enabled = prefix_fits;
-    qa.tiers = dtiers; qa.ntiers = ntiers; qa.rel = rel; qa.K = h.K; qa.M = h.M;
+    qa.tiers = dtiers; qa.ntiers = ntiers; qa.rel = rel; qa.K = h.K; qa.M = h.M; qa.R = h.R;
     for (size_t i = 0; i < h.A.size() && i < 24; ++i) qa.A[i] = h.A[i];
     qa.kappa = 8.0;
     qa.eps = f64 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
@@ -1080,7 +1146,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     }
     {
       Stage st("histogram", hs);
-      const unsigned long long nloc = (unsigned long long)h.nblocks * h.per_block;
+      const unsigned long long nloc = (unsigned long long)h.sym_off[0];  // the symbols of every round
       hist_range_kernel<<<num_sms() * BM_HIST_CTAS, 256, 0, hs>>>(sym, 0, nloc, dict, (unsigned)prm.radius, hist);
       BM_LAUNCHED();
     }
@@ -1121,7 +1187,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     HeaderArgs ha{};
     ha.raw_total = raw_total; ha.capacity = cap;
     ha.out = out; ha.f64 = f64; ha.B = h.B; ha.K = h.K; ha.M = h.M; ha.chunk = prm.chunk; ha.radius = prm.radius;
-    ha.ntiers = ntiers; ha.m = h.m; ha.rel = rel;
+    ha.ntiers = ntiers; ha.m = h.m; ha.rel = rel; ha.R = h.R;
     for (int d = 0; d < 3; ++d) { ha.shape[d] = shape[d]; ha.nb[d] = h.nb[d]; }
     ha.tol = tol; ha.n_symbols = (unsigned long long)h.n_coeffs; ha.n_chunks = L.nch;
     ha.off_tiers = L.off_tiers; ha.off_qtab = L.off_qtab; ha.off_btier = ntiers > 1 ? L.off_btier : L.off_chunks;
@@ -1146,7 +1212,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
 // Parsed and checked header of a stream.
 struct Header {
   bool raw, f64;
-  int B, K, M, chunk, radius, ntiers, m, rel;
+  int B, K, M, chunk, radius, ntiers, m, rel, R;
   int64_t shape[3];
   unsigned long long n_symbols, n_chunks, n_outliers, n_words, off_tiers, off_qtab, off_btier, off_chunks,
       off_codebook, off_bits, off_chunk_esc, off_outliers, total, off_splits;
@@ -1190,6 +1256,8 @@ bm_status parse_header(const unsigned char* hb, size_t in_bytes, Header& H) {
   H.off_chunk_esc = rd<uint64_t>(hb, 208);
   H.off_splits = rd<uint64_t>(hb, 216);
   H.codebook_bytes = rd<uint32_t>(hb, 192); H.n_runs = rd<uint32_t>(hb, 196);
+  H.R = (int)rd<uint32_t>(hb, 224) + 1;
+  if (H.R < 1 || H.R > 8) return fail(BM_ERR_CORRUPT, "rounds");
   if ((H.B != 9 && H.B != 17) || H.K < 1 || H.K > (H.B == 9 ? 3 : 4) || H.M < 0 || H.M > 16 || H.chunk < 64 ||
       H.chunk > 2048 || H.chunk % 32 || H.radius < 16 || H.radius > kMaxDict / 2 || H.ntiers < 1 || H.ntiers > 255)
     return fail(BM_ERR_CORRUPT, "header parameters out of range");
@@ -1287,10 +1355,10 @@ bm_status check_status(Scalars* sc, cudaStream_t s) {
 template <typename T>
 bm_status decompress_t(const uint8_t* in, const Header& H, T* field, cudaStream_t s) {
   PlanDev* P = nullptr;
-  if (bm_status st = get_plan(H.shape, H.B, H.K, H.M, &P)) return fail(BM_ERR_CORRUPT, g_detail);
+  if (bm_status st = get_plan(H.shape, H.B, H.K, H.M, H.R, &P)) return fail(BM_ERR_CORRUPT, g_detail);
   const PlanHost& h = P->h;
   if ((unsigned long long)h.n_coeffs != H.n_symbols || h.m != H.m) return fail(BM_ERR_CORRUPT, "symbol count");
-  if (H.ntiers > 1 && H.off_chunks != H.off_btier + pad8((unsigned long long)h.nblocks))
+  if (H.ntiers > 1 && H.off_chunks != H.off_btier + pad8((unsigned long long)h.nblocks_all))
     return fail(BM_ERR_CORRUPT, "block tier section size");
   const size_t need = decode_scratch(H) + decompose_scratch(h, sizeof(T)) + 8192;
   Workspace* ws = nullptr;
@@ -1415,8 +1483,9 @@ bm_status run_adjoint(PlanDev& P, int dir, T* gfield, T* gcoef, Carver& cv, cuda
 
 template <typename T>
 bm_status adjoint_entry(int dir, const int64_t* shape, const Params& prm, T* gfield, T* gcoef, cudaStream_t s) {
+  if (prm.R != 1) return fail(BM_ERR_UNSUPPORTED, "the adjoint entry points need one round");
   PlanDev* P = nullptr;
-  if (bm_status st = get_plan(shape, prm.B, prm.K, prm.M, &P)) return st;
+  if (bm_status st = get_plan(shape, prm.B, prm.K, prm.M, prm.R, &P)) return st;
   std::lock_guard<std::mutex> g(g_timer_mu);
   g_timer.begin(s);
   Workspace* ws = nullptr;
@@ -1584,7 +1653,7 @@ bm_status bm_coeff_count(int ndim, const int64_t* shape, const bm_params* params
   Params prm;
   if (bm_status st = check_params(params, prm)) return st;
   PlanDev* P = nullptr;
-  if (bm_status st = get_plan(shape, prm.B, prm.K, prm.M, &P)) return st;
+  if (bm_status st = get_plan(shape, prm.B, prm.K, prm.M, prm.R, &P)) return st;
   if (n_coeffs) *n_coeffs = (size_t)P->h.n_coeffs;
   return BM_OK;
 }
@@ -1625,9 +1694,22 @@ bm_status bm_compress_batch(int n, const bm_batch_item* items, size_t* out_bytes
   size_t hb = 0;
   for (int i = 0; i < n; ++i) {
     st[(size_t)i] = check_item(items[i], prm[(size_t)i]);
-    int nb = 1;
-    if (st[(size_t)i] == BM_OK)
-      for (int d = 0; d < 3; ++d) nb *= (int)((items[i].shape[d] + prm[(size_t)i].B - 1) / prm[(size_t)i].B);
+    int64_t nb = 0;  // blocks of every round
+    if (st[(size_t)i] == BM_OK) {
+      const Params& q = prm[(size_t)i];
+      int64_t m = q.B;
+      for (int l = 0; l < q.K; ++l) m = m / 2 + 1;
+      int64_t S[3] = {items[i].shape[0], items[i].shape[1], items[i].shape[2]};
+      for (int r = 0; r < q.R; ++r) {
+        int64_t n = 1;
+        for (int d = 0; d < 3; ++d) {
+          const int64_t b = (S[d] + q.B - 1) / q.B;
+          n *= b;
+          S[d] = b * m;
+        }
+        nb += n;
+      }
+    }
     slot_off[(size_t)i] = hb;
     hb += (256 + 8 * 256 + (size_t)nb + 255) & ~size_t(255);
   }
@@ -1723,7 +1805,7 @@ bm_status bm_perf_model_fit(bm_dtype dtype, int block_nodes, bm_perf_model* mode
       }
       if (st != BM_OK || rep == 0) continue;
       PlanDev* P = nullptr;
-      if ((st = get_plan(shape, prm.B, prm.K, prm.M, &P)) != BM_OK) break;
+      if ((st = get_plan(shape, prm.B, prm.K, prm.M, prm.R, &P)) != BM_OK) break;
       const GSizes gs = gsizes(P->h);
       cp = CalibPoint{};
       cp.blocks = (double)P->h.nblocks;
@@ -1788,7 +1870,7 @@ bm_status bm_predict_ms(const bm_perf_model* m, int ndim, const int64_t* shape, 
   Params prm;
   if (bm_status st = check_params(params, prm)) return st;
   PlanDev* P = nullptr;
-  if (bm_status st = get_plan(shape, prm.B, prm.K, prm.M, &P)) return st;
+  if (bm_status st = get_plan(shape, prm.B, prm.K, prm.M, prm.R, &P)) return st;
   const PlanHost& h = P->h;
   const GSizes gs = gsizes(h);
   // the in-cache levels (quantisation fused) follow Eq. 1; a model fitted
@@ -1899,7 +1981,7 @@ bm_status bm_decompose(const void* d_field, int ndim, const int64_t* shape, bm_d
   Params prm;
   if (bm_status st = check_params(params, prm)) return st;
   PlanDev* P = nullptr;
-  if (bm_status st = get_plan(shape, prm.B, prm.K, prm.M, &P)) return st;
+  if (bm_status st = get_plan(shape, prm.B, prm.K, prm.M, prm.R, &P)) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   std::lock_guard<std::mutex> g(g_timer_mu);
   g_timer.begin(s);
@@ -1925,7 +2007,7 @@ bm_status bm_recompose(const void* d_coeffs, int ndim, const int64_t* shape, bm_
   Params prm;
   if (bm_status st = check_params(params, prm)) return st;
   PlanDev* P = nullptr;
-  if (bm_status st = get_plan(shape, prm.B, prm.K, prm.M, &P)) return st;
+  if (bm_status st = get_plan(shape, prm.B, prm.K, prm.M, prm.R, &P)) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   std::lock_guard<std::mutex> g(g_timer_mu);
   g_timer.begin(s);

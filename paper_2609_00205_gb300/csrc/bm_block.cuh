@@ -351,7 +351,8 @@ __device__ __forceinline__ void store_symbols(uint16_t* __restrict__ dst, const 
     uint32_t* d32 = reinterpret_cast<uint32_t*>(dst);
     for (int i = threadIdx.x; i < PB / 2; i += blockDim.x) d32[i] = s32[i];
   } else {
-    if ((sbase & 1) == 0) {
+    (void)sbase;
+    if ((reinterpret_cast<uintptr_t>(dst) & 3) == 0) {
       const uint32_t* s32 = reinterpret_cast<const uint32_t*>(src);
       uint32_t* d32 = reinterpret_cast<uint32_t*>(dst);
       for (int i = threadIdx.x; i < PB / 2; i += blockDim.x) d32[i] = s32[i];
@@ -546,7 +547,7 @@ __global__ void __launch_bounds__(BlockCfg<T, B, K>::NT_INV, BlockCfg<T, B, K>::
     if (MODE == 0) {
       uint16_t* st = reinterpret_cast<uint16_t*>(stage);
       const uint16_t* src = a.sym + sbase;
-      if ((sbase & 1) == 0) {
+      if ((reinterpret_cast<uintptr_t>(src) & 3) == 0) {
         const uint32_t* s32 = reinterpret_cast<const uint32_t*>(src);
         uint32_t* d32 = reinterpret_cast<uint32_t*>(st);
         for (int i = threadIdx.x; i < Cfg::PB / 2; i += blockDim.x) d32[i] = __ldg(s32 + i);

@@ -182,11 +182,12 @@ double error_constant(const Dim1DHost* D3) {
 
 }  // namespace
 
-std::string make_plan(const int64_t* shape, int B, int K, int M, PlanHost& p) {
+std::string make_plan(const int64_t* shape, int B, int K, int M, int R, PlanHost& p) {
   if (B < 3 || B % 2 == 0) return "block size must be odd and >= 3";
+  if (R < 1) return "at least one round";
   p = PlanHost{};
   for (int d = 0; d < 3; ++d) p.shape[d] = shape[d];
-  p.B = B; p.K = K; p.M = M;
+  p.B = B; p.K = K; p.M = M; p.R = R;
   p.nblocks = 1;
   for (int d = 0; d < 3; ++d) {
     const int64_t nb = (shape[d] + B - 1) / B;
@@ -211,13 +212,40 @@ std::string make_plan(const int64_t* shape, int B, int K, int M, PlanHost& p) {
     xl = nx;
   }
   p.m = (int)xl.size();
+  // re-blocking rounds (Sec. III-C): round r+1 blocks round r's gathered grid
+  int64_t S[3] = {shape[0], shape[1], shape[2]};
+  int64_t pos = 0;
+  p.nblocks_all = 0;
+  for (int r = 0; r < R; ++r) {
+    RoundHost rd{};
+    rd.nblocks = 1;
+    for (int d = 0; d < 3; ++d) {
+      const int64_t nb = (S[d] + B - 1) / B;
+      if (nb > (1 << 30)) return "shape too large";
+      rd.shape[d] = S[d];
+      rd.nb[d] = (int)nb;
+      rd.nblocks *= nb;
+      rd.gshape[d] = nb * p.m;
+    }
+    rd.off = pos;
+    pos += rd.nblocks * p.per_block;
+    p.nblocks_all += rd.nblocks;
+    p.rounds.push_back(rd);
+    for (int d = 0; d < 3; ++d) S[d] = rd.gshape[d];
+  }
+  // coordinates of the global levels' input: physical for one round (block
+  // offset plus the coarse node's in-block coordinate), index coordinates of
+  // the last gathered grid for several
   std::vector<double> gx[3];
   for (int d = 0; d < 3; ++d) {
-    p.gshape[d] = (int64_t)p.nb[d] * p.m;
-    for (int b = 0; b < p.nb[d]; ++b)
-      for (int j = 0; j < p.m; ++j) gx[d].push_back((double)b * B + xl[j]);
+    p.gshape[d] = S[d];
+    if (R == 1) {
+      for (int b = 0; b < p.nb[d]; ++b)
+        for (int j = 0; j < p.m; ++j) gx[d].push_back((double)b * B + xl[j]);
+    } else {
+      for (int64_t i = 0; i < S[d]; ++i) gx[d].push_back((double)i);
+    }
   }
-  int64_t pos = p.nblocks * p.per_block;
   for (int l = 0; l <= M; ++l) {
     for (int d = 0; d < 3; ++d) p.lshape.push_back((int64_t)gx[d].size());
     p.sym_off.push_back(pos);

@@ -22,14 +22,26 @@ struct Dim1DHost {
   std::vector<double> P;       // [c x n] row-major: M_c^{-1} I^T M_f (global levels)
 };
 
-struct PlanHost {
-  int64_t shape[3];
-  int B, K, M;
+// One re-blocking round: B-node blocks over the round's input grid (the field
+// for round 0, the previous round's gathered coarse grid after that).
+struct RoundHost {
+  int64_t shape[3];  // input grid
   int nb[3];
   int64_t nblocks;
+  int64_t off;       // first coefficient of the round
+  int64_t gshape[3]; // gathered coarse grid (nb * m)
+};
+
+struct PlanHost {
+  int64_t shape[3];
+  int B, K, M, R;
+  int nb[3];         // round 0
+  int64_t nblocks;   // round 0
+  std::vector<RoundHost> rounds;
+  int64_t nblocks_all;  // blocks of all rounds
   int m;                 // coarse nodes per block edge after K levels
   int64_t per_block;
-  int64_t gshape[3];     // gathered grid
+  int64_t gshape[3];     // gathered grid of the last round (the global levels' input)
   std::vector<int64_t> lshape;  // [3*(M+1)]: grid of global level l (l = 0 is G), last = coarsest
   std::vector<int64_t> sym_off; // [M+2]: first symbol of global level l; sym_off[M] = coarsest
   int64_t n_coeffs;
@@ -38,6 +50,6 @@ struct PlanHost {
 };
 
 // Builds the plan; returns an empty string on success, else a message.
-std::string make_plan(const int64_t* shape, int B, int K, int M, PlanHost& p);
+std::string make_plan(const int64_t* shape, int B, int K, int M, int R, PlanHost& p);
 
 }  // namespace bm
