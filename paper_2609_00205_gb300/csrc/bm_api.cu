@@ -489,10 +489,21 @@ __global__ void __launch_bounds__(256) maxabs_kernel(const T* __restrict__ u, in
     m = y > m ? y : m;
   }
   bad = __any_sync(0xffffffffu, bad);
+  // one atomic per CTA: the whole grid's atomics go to one address
+  __shared__ T s_m[8];
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
   if ((threadIdx.x & 31) == 0) {
+    s_m[threadIdx.x >> 5] = m;
+    if (bad) s_bad = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = s_m[w] > m ? s_m[w] : m;
     if (sizeof(T) == 4) atomicMax(&sc->maxabs_bits, (unsigned long long)__float_as_uint((float)m));
     else atomicMax(&sc->maxabs_bits, (unsigned long long)__double_as_longlong((double)m));
-    if (bad) atomicOr(&sc->status, ST_RAW);
+    if (s_bad) atomicOr(&sc->status, ST_RAW);
   }
   if (!qa.enabled) return;
   __threadfence();
