@@ -141,6 +141,7 @@ struct Workspace {
   void* d = nullptr;
   size_t dbytes = 0;
   void* h = nullptr;
+  void* hd = nullptr;  // device-side address of h (pinned memory is mapped)
   size_t hbytes = 0;
   int dev = -1;
   // second stream for work that runs beside the caller's stream, joined back
@@ -176,12 +177,19 @@ bm_status get_ws(cudaStream_t s, size_t dbytes, size_t hbytes, Workspace** out) 
     w.dbytes = want;
   }
   if (w.hbytes < hbytes) {
-    if (w.h) { cudaStreamSynchronize(s); cudaFreeHost(w.h); w.h = nullptr; w.hbytes = 0; }
+    if (w.h) { cudaStreamSynchronize(s); cudaFreeHost(w.h); w.h = nullptr; w.hd = nullptr; w.hbytes = 0; }
     size_t want = hbytes + (1 << 16);
     if (cudaMallocHost(&w.h, want) != cudaSuccess) {
       cudaGetLastError();
       w.h = nullptr;
       return fail(BM_ERR_OOM, "pinned host scratch allocation failed");
+    }
+    if (cudaHostGetDevicePointer(&w.hd, w.h, 0) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFreeHost(w.h);
+      w.h = nullptr;
+      w.hd = nullptr;
+      return fail(BM_ERR_CUDA, "pinned host scratch is not mapped into the device address space");
     }
     w.hbytes = want;
   }
@@ -1012,8 +1020,65 @@ void propagate_tiers(const PlanHost& h, std::vector<uint8_t>& t) {
 }
 
 // Pinned host staging and result of one item of a batched compress.
+// Small transfers of a call (zeroed scratch, the tolerance tables from the
+// pinned staging buffer, the scalars and header read back to it) done by one
+// kernel through the host mapping of pinned memory rather than by copy-engine
+// copies or memsets: a call then never waits behind bulk copies that the
+// caller has queued on the copy engines for other data (its next field, its
+// previous stream).  A span with src == nullptr is zero-filled.
+struct Span {
+  void* dst;
+  const void* src;
+  unsigned long long bytes;
+};
+constexpr int kMaxSpans = 8;
+struct SpanArgs {
+  Span r[kMaxSpans];
+  int n;
+};
+
+__global__ void __launch_bounds__(256) spans_kernel(SpanArgs a) {
+  const unsigned long long tid = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned long long nth = (unsigned long long)gridDim.x * blockDim.x;
+  for (int k = 0; k < a.n; ++k) {
+    uint8_t* d = reinterpret_cast<uint8_t*>(a.r[k].dst);
+    const uint8_t* src = reinterpret_cast<const uint8_t*>(a.r[k].src);
+    const unsigned long long n = a.r[k].bytes;
+    const uintptr_t al = reinterpret_cast<uintptr_t>(d) | (src ? reinterpret_cast<uintptr_t>(src) : 0) | (uintptr_t)n;
+    if ((al & 15) == 0) {
+      uint4* d4 = reinterpret_cast<uint4*>(d);
+      const uint4* s4 = reinterpret_cast<const uint4*>(src);
+      for (unsigned long long i = tid; i < n / 16; i += nth) d4[i] = src ? s4[i] : make_uint4(0u, 0u, 0u, 0u);
+    } else if ((al & 3) == 0) {
+      uint32_t* d1 = reinterpret_cast<uint32_t*>(d);
+      const uint32_t* s1 = reinterpret_cast<const uint32_t*>(src);
+      for (unsigned long long i = tid; i < n / 4; i += nth) d1[i] = src ? s1[i] : 0u;
+    } else {
+      for (unsigned long long i = tid; i < n; i += nth) d[i] = src ? src[i] : (uint8_t)0;
+    }
+  }
+  __threadfence_system();  // stores to host memory are visible once the stream has synchronised
+}
+
+struct Spans {
+  SpanArgs a{};
+  void add(void* dst, const void* src, unsigned long long bytes) {
+    if (bytes) a.r[a.n++] = Span{dst, src, bytes};
+  }
+  cudaError_t launch(cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    unsigned long long mx = 0;
+    for (int k = 0; k < a.n; ++k) mx = std::max(mx, a.r[k].bytes);
+    const int grid = (int)std::min<unsigned long long>((unsigned long long)num_sms() * 2, std::max(1ull, (mx + 4095) / 4096));
+    spans_kernel<<<grid, 256, 0, s>>>(a);
+    BM_LAUNCHED();
+    return cudaGetLastError();
+  }
+};
+
 struct BatchSlot {
   unsigned char* h = nullptr;  // Scalars at 0, tiers at 256, block tiers at 256 + 8*256
+  unsigned char* hd = nullptr; // device-side address of h
   bool raw_now = false;        // the raw copy was chosen on the host
   unsigned long long raw_total = 0;
 };
@@ -1094,6 +1159,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   // pinned staging: the stream's own, or the batch item's (items of a batch
   // share streams, so each needs its own copy until the batch has synchronised)
   unsigned char* hp = bs ? bs->h : reinterpret_cast<unsigned char*>(ws->h);
+  unsigned char* hpd = bs ? bs->hd : reinterpret_cast<unsigned char*>(ws->hd);  // its device-side address
   Scalars* hsc = reinterpret_cast<Scalars*>(hp);
   double* htiers = reinterpret_cast<double*>(hp + 256);
   uint8_t* hbt = hp + 256 + 8 * 256;
@@ -1103,14 +1169,25 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   const bool prefix_fits = L.off_codebook <= cap;
   {
     Stage st("setup");
-    BM_CUDA(cudaMemsetAsync(sc, 0, sizeof(Scalars), s));
-    BM_CUDA(cudaMemsetAsync(hist, 0, 4ull * dict, s));
-    BM_CUDA(cudaMemcpyAsync(dtiers, htiers, 8 * ntiers, cudaMemcpyHostToDevice, s));
-    if (ntiers > 1) BM_CUDA(cudaMemcpyAsync(dbt, hbt, (size_t)h.nblocks_all, cudaMemcpyHostToDevice, s));
+    // zeroed scalars, histogram, stream prefix and encoder tickets; the tier
+    // tables read from the pinned staging buffer
+    const unsigned long long nbt = (unsigned long long)h.nblocks_all;
+    Spans sp;
+    sp.add(sc, nullptr, sizeof(Scalars));
+    sp.add(hist, nullptr, 4ull * dict);
+    sp.add(dtiers, hpd + 256, 8ull * ntiers);
+    if (ntiers > 1) sp.add(dbt, hpd + 256 + 8 * 256, nbt);
     if (prefix_fits) {
-      BM_CUDA(cudaMemsetAsync(out, 0, L.off_codebook, s));
-      if (ntiers > 1) BM_CUDA(cudaMemcpyAsync(out + L.off_btier, dbt, (size_t)h.nblocks_all, cudaMemcpyDeviceToDevice, s));
+      if (ntiers > 1) {
+        sp.add(out, nullptr, L.off_btier);
+        sp.add(out + L.off_btier, hpd + 256 + 8 * 256, nbt);
+        sp.add(out + L.off_btier + nbt, nullptr, L.off_codebook - L.off_btier - nbt);
+      } else {
+        sp.add(out, nullptr, L.off_codebook);
+      }
     }
+    sp.add(tickets, nullptr, 256 + 16ull * L.nch);
+    BM_CUDA(sp.launch(s));
   }
   const int mgrid = (int)std::min<int64_t>((int64_t)num_sms() * 8, std::max<int64_t>(1, (nel + 4095) / 4096));
   {
@@ -1182,7 +1259,6 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   }
   {
     Stage st("huffman_encode");
-    BM_CUDA(cudaMemsetAsync(tickets, 0, 256 + 16ull * L.nch, s));
     FusedEncodeArgs ea{};
     ea.sym = sym; ea.esc = esc; ea.n = (unsigned long long)h.n_coeffs; ea.chunk = prm.chunk;
     ea.lens = lens; ea.codes = codes; ea.dict = dict; ea.nch = L.nch;
@@ -1209,7 +1285,9 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
                                                raw_total, sc);
     g_launches.fetch_add(2);
     BM_CUDA(cudaGetLastError());
-    BM_CUDA(cudaMemcpyAsync(hsc, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+    Spans back;
+    back.add(hpd, sc, sizeof(Scalars));
+    BM_CUDA(back.launch(s));
   }
   if (bs) {  // the batch reads the result after its single synchronisation
     bs->raw_now = false;
@@ -1292,7 +1370,9 @@ bm_status read_header(const void* in, size_t in_bytes, bool is_device, cudaStrea
   if (is_device) {
     Workspace* ws = nullptr;
     if (bm_status st = get_ws(s, 1 << 12, 1 << 12, &ws)) return st;
-    BM_CUDA(cudaMemcpyAsync(ws->h, in, kHeaderBytes, cudaMemcpyDeviceToHost, s));
+    Spans sp;
+    sp.add(ws->hd, in, kHeaderBytes);
+    BM_CUDA(sp.launch(s));
     BM_CUDA(cudaStreamSynchronize(s));
     std::memcpy(hb, ws->h, kHeaderBytes);
   } else {
@@ -1310,7 +1390,11 @@ bm_status decode_symbols(const uint8_t* in, const Header& H, Carver& cv, uint16_
   unsigned long long* word_off = cv.take<unsigned long long>(H.n_chunks + 1);
   unsigned long long* esc_off = cv.take<unsigned long long>(H.n_chunks + 1);
   DecodeTables* dt = cv.take<DecodeTables>(1);
-  BM_CUDA(cudaMemsetAsync(sc, 0, sizeof(Scalars), s));
+  {
+    Spans sp;
+    sp.add(sc, nullptr, sizeof(Scalars));
+    BM_CUDA(sp.launch(s));
+  }
   {
     Stage st("huffman_tables");
     word_scan_kernel<<<1, kCbThreads, 0, s>>>(reinterpret_cast<const unsigned*>(in + H.off_chunks), H.n_chunks,
@@ -1356,7 +1440,9 @@ size_t decode_scratch(const Header& H) {
 bm_status check_status(Scalars* sc, cudaStream_t s) {
   Workspace* ws = nullptr;
   if (bm_status st = get_ws(s, 0, 4096, &ws)) return st;
-  BM_CUDA(cudaMemcpyAsync(ws->h, sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+  Spans sp;
+  sp.add(ws->hd, sc, sizeof(Scalars));
+  BM_CUDA(sp.launch(s));
   BM_CUDA(cudaStreamSynchronize(s));
   const Scalars* h = reinterpret_cast<const Scalars*>(ws->h);
   if (h->status & ST_CORRUPT) return fail(BM_ERR_CORRUPT, "stream failed a bound check while decoding");
@@ -1517,6 +1603,7 @@ struct BatchCtx {
   std::vector<cudaEvent_t> joins;
   cudaEvent_t fork = nullptr;
   unsigned char* h = nullptr;
+  unsigned char* hd = nullptr;  // device-side address of h
   size_t hbytes = 0;
 };
 std::mutex g_batch_mu;
@@ -1540,11 +1627,20 @@ bm_status batch_ctx(size_t hbytes, BatchCtx** out) {
   if (c.hbytes < hbytes) {
     if (c.h) cudaFreeHost(c.h);
     c.h = nullptr;
+    c.hd = nullptr;
     c.hbytes = 0;
     if (cudaMallocHost(&c.h, hbytes) != cudaSuccess) {
       cudaGetLastError();
       return fail(BM_ERR_OOM, "pinned host allocation for the batch failed");
     }
+    void* hd = nullptr;
+    if (cudaHostGetDevicePointer(&hd, c.h, 0) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFreeHost(c.h);
+      c.h = nullptr;
+      return fail(BM_ERR_CUDA, "pinned batch buffer is not mapped into the device address space");
+    }
+    c.hd = reinterpret_cast<unsigned char*>(hd);
     c.hbytes = hbytes;
   }
   *out = &c;
@@ -1742,6 +1838,7 @@ bm_status bm_compress_batch(int n, const bm_batch_item* items, size_t* out_bytes
     const bm_batch_item& it = items[i];
     cudaStream_t ps = ctx->streams[(size_t)(k++ % kBatchStreams)];
     slot[(size_t)i].h = ctx->h + slot_off[(size_t)i];
+    slot[(size_t)i].hd = ctx->hd + slot_off[(size_t)i];
     size_t dummy = 0;
     if (it.dtype == BM_F32)
       st[(size_t)i] = compress_t<float>(reinterpret_cast<const float*>(it.d_field), it.shape, prm[(size_t)i], it.tol,
