@@ -655,9 +655,8 @@ __global__ void __launch_bounds__(256) raw_stream_kernel(uint8_t* o, const T* __
 // One block; each warp owns a contiguous segment and walks it 32 counts at a
 // time (coalesced loads, shuffle scan, running carry); the warps' totals are
 // scanned across the block and a second walk writes the offsets.
-__global__ void __launch_bounds__(kCbThreads) word_scan_kernel(const unsigned* chunk_words, unsigned long long nch,
-                                                              unsigned long long* word_off, unsigned long long n_words,
-                                                              Scalars* sc) {
+__device__ __forceinline__ void word_scan_block(const unsigned* chunk_words, unsigned long long nch,
+                                                unsigned long long* word_off, unsigned long long n_words, Scalars* sc) {
   __shared__ unsigned long long wt[32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const unsigned long long seg = (nch + nw - 1) / nw;
@@ -716,6 +715,29 @@ __global__ void __launch_bounds__(kCbThreads) word_scan_kernel(const unsigned* c
     word_off[nch] = total;
     if (total != n_words) atomicOr(&sc->status, ST_CORRUPT);
   }
+}
+
+// The decoder's three table builds in one launch, one CTA each, side by side
+// on different SMs: decode tables from the codebook, word offsets of the
+// chunks, and (when the stream has outliers) their per-chunk offsets.
+struct TablesArgs {
+  const uint8_t* runs;
+  unsigned long long cb_bytes, n_runs;
+  int dict;
+  DecodeTables* dt;
+  const unsigned* chunk_words;
+  const unsigned* chunk_esc;
+  unsigned long long nch, n_words, n_outliers;
+  unsigned long long* word_off;
+  unsigned long long* esc_off;
+  Scalars* sc;
+};
+
+__global__ void __launch_bounds__(kCbThreads) tables_kernel(TablesArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (blockIdx.x == 0) decode_tables_block(a.runs, a.cb_bytes, a.n_runs, a.dict, a.dt, a.sc, smem_raw);
+  else if (blockIdx.x == 1) word_scan_block(a.chunk_words, a.nch, a.word_off, a.n_words, a.sc);
+  else word_scan_block(a.chunk_esc, a.nch, a.esc_off, a.n_outliers, a.sc);
 }
 
 __global__ void zero_tail_kernel(uint8_t* base, Scalars* sc) {
@@ -1397,15 +1419,14 @@ bm_status decode_symbols(const uint8_t* in, const Header& H, Carver& cv, uint16_
   }
   {
     Stage st("huffman_tables");
-    word_scan_kernel<<<1, kCbThreads, 0, s>>>(reinterpret_cast<const unsigned*>(in + H.off_chunks), H.n_chunks,
-                                              word_off, H.n_words, sc);
-    if (H.n_outliers)
-      word_scan_kernel<<<1, kCbThreads, 0, s>>>(reinterpret_cast<const unsigned*>(in + H.off_chunk_esc), H.n_chunks,
-                                                esc_off, H.n_outliers, sc);
-    BM_CUDA(set_smem_once(decode_tables_kernel, (int)sizeof(DtSmem), g_dt_attr));
-    decode_tables_kernel<<<1, kCbThreads, sizeof(DtSmem), s>>>(in + H.off_codebook, H.codebook_bytes, H.n_runs,
-                                                               2 * H.radius, dt, sc);
-    g_launches.fetch_add(H.n_outliers ? 3 : 2);
+    TablesArgs ta{};
+    ta.runs = in + H.off_codebook; ta.cb_bytes = H.codebook_bytes; ta.n_runs = H.n_runs; ta.dict = 2 * H.radius;
+    ta.dt = dt; ta.chunk_words = reinterpret_cast<const unsigned*>(in + H.off_chunks);
+    ta.chunk_esc = reinterpret_cast<const unsigned*>(in + H.off_chunk_esc); ta.nch = H.n_chunks;
+    ta.n_words = H.n_words; ta.n_outliers = H.n_outliers; ta.word_off = word_off; ta.esc_off = esc_off; ta.sc = sc;
+    BM_CUDA(set_smem_once(tables_kernel, (int)sizeof(DtSmem), g_dt_attr));
+    tables_kernel<<<H.n_outliers ? 3 : 2, kCbThreads, sizeof(DtSmem), s>>>(ta);
+    BM_LAUNCHED();
     BM_CUDA(cudaGetLastError());
   }
   {

@@ -891,11 +891,11 @@ struct DtSmem {
   unsigned rfirst[512], rcount[512], roff[512];
 };
 
-// Build decode tables from the stream's codebook runs (one CTA).
-__global__ void __launch_bounds__(kCbThreads) decode_tables_kernel(const uint8_t* runs, unsigned long long nbytes,
-                                                                   unsigned long long n_runs, int dict,
-                                                                   DecodeTables* out, Scalars* sc) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+// Build decode tables from the stream's codebook runs (one CTA of
+// kCbThreads threads, DtSmem in its dynamic shared memory).
+__device__ __forceinline__ void decode_tables_block(const uint8_t* runs, unsigned long long nbytes,
+                                                    unsigned long long n_runs, int dict, DecodeTables* out,
+                                                    Scalars* sc, unsigned char* smem_raw) {
   DtSmem& S = *reinterpret_cast<DtSmem*>(smem_raw);
   __shared__ unsigned s_bad;
   __shared__ unsigned long long s_kr;
