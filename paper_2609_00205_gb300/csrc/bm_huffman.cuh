@@ -66,75 +66,82 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* warp_t
   return before;
 }
 
-// Bitonic sort of 1024*E keys (ascending) by one block of 1024 threads, E
-// consecutive keys per thread in registers: exchanges within a thread need no
-// communication, partners up to 31 threads away are reached by shuffles, and
-// only the longer strides go through shared memory.
-template <typename K, int E, int J>
-__device__ __forceinline__ void sort_stage_regs(K (&v)[E], int t, int k) {
-#pragma unroll
-  for (int e = 0; e < E; ++e)
-    if ((e & J) == 0) {
-      const bool up = ((t * E + e) & k) == 0;
-      const K a = v[e], b = v[e + J];
-      const bool sw = (a > b) == up;
-      v[e] = sw ? b : a;
-      v[e + J] = sw ? a : b;
-    }
-}
+// Per-warp running counts of a counting pass, stored by (digit, warp) with
+// the warp index swizzled by the digit so that the lanes of a warp reading
+// counts of different digits hit different banks.
+__device__ __forceinline__ int wc_idx(unsigned d, int w) { return (int)(d * 32u + ((unsigned)w ^ (d & 31u))); }
 
-template <typename K, int E>
-__device__ void block_sort_regs(K* keys) {
-  constexpr int P = 1024 * E;
-  const int t = threadIdx.x;
-  K v[E];
+// Stable LSD radix sort (8-bit digits) of n <= kMaxDict (key, symbol) pairs by
+// key, one block of kCbThreads threads.  Each pass: every warp ranks its rows
+// of 32 pairs by digit with __match_any_sync, keeping a running count per
+// digit; one block scan over (digit, warp) gives every group its start; the
+// pairs scatter.  As many passes as maxkey has bytes.  Input in (ka, sa);
+// returns 0 when the sorted pairs are in (ka, sa), 1 when in (kb, sb).
+// wcnt: 256 * 32 u32 of scratch.
+__device__ int radix_sort_pairs(unsigned* ka, uint16_t* sa, unsigned* kb, uint16_t* sb, unsigned* wcnt, int n,
+                                unsigned maxkey, unsigned* scan_tmp) {
+  constexpr int RMAX = kMaxDict / kCbThreads;  // rows of 32 per warp at most
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int rows = (n + kCbThreads - 1) / kCbThreads;
+  const int seg = rows * 32;
+  int passes = 1;
+  while (passes < 4 && (maxkey >> (8 * passes)) != 0u) ++passes;
+  int cur = 0;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = 8 * p;
+    const unsigned* kin = cur ? kb : ka;
+    const uint16_t* sin = cur ? sb : sa;
+    unsigned* kout = cur ? ka : kb;
+    uint16_t* sout = cur ? sa : sb;
+    for (int i = threadIdx.x; i < 256 * 32; i += blockDim.x) wcnt[i] = 0u;
+    __syncthreads();
+    unsigned loc[RMAX], dig[RMAX];
 #pragma unroll
-  for (int e = 0; e < E; ++e) v[e] = keys[t * E + e];
-  for (int k = 2; k <= P; k <<= 1)
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      if (j < E) {
-        if (E > 4 && j == 4) sort_stage_regs<K, E, (E > 4 ? 4 : 1)>(v, t, k);
-        else if (E > 2 && j == 2) sort_stage_regs<K, E, (E > 2 ? 2 : 1)>(v, t, k);
-        else sort_stage_regs<K, E, 1>(v, t, k);
-        continue;
-      }
-      const int m = j / E;  // partner thread distance
-      const bool keep_min = (((t & m) == 0) == (((t * E) & k) == 0));
-      if (m < 32) {
+    for (int r = 0; r < RMAX; ++r) {
+      if (r >= rows) break;
+      const int i = wid * seg + r * 32 + lane;
+      const bool ok = i < n;
+      const unsigned d = ok ? (kin[i] >> shift) & 255u : 0u;
+      const unsigned m = __match_any_sync(0xffffffffu, ok ? d : 256u + (unsigned)lane);
+      const unsigned lt = m & ((1u << lane) - 1u);
+      const unsigned base = ok ? wcnt[wc_idx(d, wid)] : 0u;
+      loc[r] = base + (unsigned)__popc(lt);
+      dig[r] = d;
+      __syncwarp();
+      if (ok && lt == 0u) wcnt[wc_idx(d, wid)] = base + (unsigned)__popc(m);
+      __syncwarp();
+    }
+    __syncthreads();
+    // exclusive scan in (digit, warp) order: thread t owns entries 8t .. 8t+7
+    unsigned v[8], sum = 0;
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const K o = __shfl_xor_sync(0xffffffffu, v[e], m);
-          v[e] = keep_min ? (o < v[e] ? o : v[e]) : (o > v[e] ? o : v[e]);
-        }
-      } else {  // element-major in shared memory: neighbouring threads, neighbouring words
-        __syncthreads();
+    for (int j = 0; j < 8; ++j) {
+      const int k = threadIdx.x * 8 + j;
+      v[j] = wcnt[wc_idx((unsigned)k >> 5, k & 31)];
+      sum += v[j];
+    }
+    unsigned pre = block_excl_scan(sum, scan_tmp, nullptr);
 #pragma unroll
-        for (int e = 0; e < E; ++e) keys[e * 1024 + t] = v[e];
-        __syncthreads();
+    for (int j = 0; j < 8; ++j) {
+      const int k = threadIdx.x * 8 + j;
+      wcnt[wc_idx((unsigned)k >> 5, k & 31)] = pre;
+      pre += v[j];
+    }
+    __syncthreads();
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const K o = keys[e * 1024 + (t ^ m)];
-          v[e] = keep_min ? (o < v[e] ? o : v[e]) : (o > v[e] ? o : v[e]);
-        }
+    for (int r = 0; r < RMAX; ++r) {
+      if (r >= rows) break;
+      const int i = wid * seg + r * 32 + lane;
+      if (i < n) {
+        const unsigned dst = wcnt[wc_idx(dig[r], wid)] + loc[r];
+        kout[dst] = kin[i];
+        sout[dst] = sin[i];
       }
     }
-  __syncthreads();
-#pragma unroll
-  for (int e = 0; e < E; ++e) keys[t * E + e] = v[e];
-  __syncthreads();
-}
-
-// Sorts keys[0..P) (P a power of two <= kMaxDict, the array holding at least
-// max(P, 1024) keys); padding up to 1024 uses the largest key value.
-template <typename K>
-__device__ void bitonic_sort(K* keys, int P) {
-  const int Q = P < 1024 ? 1024 : P;
-  for (int i = P + threadIdx.x; i < Q; i += blockDim.x) keys[i] = ~K(0);
-  __syncthreads();
-  if (Q == 1024) block_sort_regs<K, 1>(keys);
-  else if (Q == 2048) block_sort_regs<K, 2>(keys);
-  else if (Q == 4096) block_sort_regs<K, 4>(keys);
-  else block_sort_regs<K, 8>(keys);
+    __syncthreads();
+    cur ^= 1;
+  }
+  return cur;
 }
 
 __device__ __forceinline__ int upper_bound_u32(const unsigned* a, int lo, int hi, unsigned v) {
@@ -152,32 +159,51 @@ __device__ __forceinline__ int lower_bound_u32(const unsigned* a, int lo, int hi
   return lo;
 }
 
-// Canonical tables from a length array len[0..dict) in shared memory.
-// key32 is scratch of >= next_pow2(dict) u32.  Writes canon order into canon.
+// Canonical tables from a length array len[0..dict) in shared memory: the
+// present symbols in (length, symbol) order by one stable counting pass over
+// the lengths (at most kMaxLen): warps rank their rows of 32 symbols as in
+// radix_sort_pairs, warp L-1 scans length L's counts over the warps, and each
+// symbol lands at first_pos[len] + (symbols of its length before it).  key32
+// is scratch of at least (kMaxLen + 1) * 32 u32; canon receives the order.
 __device__ void build_canonical(const uint8_t* len, int dict, unsigned* key32, uint16_t* canon, CanonTables* ct,
                                 unsigned* scan_tmp) {
-  __shared__ unsigned s_n;
+  constexpr int RMAX = kMaxDict / kCbThreads;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned* wcnt = key32;  // (kMaxLen + 1) x 32
   if (threadIdx.x < kMaxLen + 2) ct->count[threadIdx.x] = 0;
+  for (int i = threadIdx.x; i < (kMaxLen + 1) * 32; i += blockDim.x) wcnt[i] = 0u;
   __syncthreads();
-  // compact present symbols as (len << 13 | sym) keys
-  const int per = (dict + blockDim.x - 1) / blockDim.x;
-  const int s0 = threadIdx.x * per;
-  unsigned cnt = 0;
-  for (int s = s0; s < s0 + per && s < dict; ++s) cnt += len[s] ? 1u : 0u;
-  unsigned pos = block_excl_scan(cnt, scan_tmp, &s_n);
-  for (int s = s0; s < s0 + per && s < dict; ++s)
-    if (len[s]) {
-      key32[pos++] = ((unsigned)len[s] << 13) | (unsigned)s;
-      atomicAdd(&ct->count[len[s]], 1u);
+  const int rows = (dict + kCbThreads - 1) / kCbThreads;
+  const int seg = rows * 32;
+  unsigned loc[RMAX];
+#pragma unroll
+  for (int r = 0; r < RMAX; ++r) {
+    if (r >= rows) break;
+    const int s = wid * seg + r * 32 + lane;
+    const unsigned L = s < dict ? len[s] : 0u;
+    const bool ok = L != 0u && L <= (unsigned)kMaxLen;
+    const unsigned m = __match_any_sync(0xffffffffu, ok ? L : 64u + (unsigned)lane);
+    const unsigned lt = m & ((1u << lane) - 1u);
+    const unsigned base = ok ? wcnt[wc_idx(L, wid)] : 0u;
+    loc[r] = base + (unsigned)__popc(lt);
+    __syncwarp();
+    if (ok && lt == 0u) wcnt[wc_idx(L, wid)] = base + (unsigned)__popc(m);
+    __syncwarp();
+  }
+  __syncthreads();
+  if (wid < kMaxLen) {  // length L = wid + 1: exclusive scan of its counts over the warps
+    const unsigned L = (unsigned)wid + 1u;
+    const unsigned c = wcnt[wc_idx(L, lane)];
+    unsigned x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
     }
+    wcnt[wc_idx(L, lane)] = x - c;
+    if (lane == 31) ct->count[L] = x;
+  }
   __syncthreads();
-  const int n = (int)s_n;
-  int P = 1;
-  while (P < n) P <<= 1;
-  for (int i = n + threadIdx.x; i < P; i += blockDim.x) key32[i] = 0xFFFFFFFFu;
-  __syncthreads();
-  bitonic_sort(key32, P);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) canon[i] = (uint16_t)(key32[i] & 8191u);
   if (threadIdx.x == 0) {
     unsigned code = 0, p = 0, maxl = 0;
     ct->count[0] = 0;
@@ -192,8 +218,16 @@ __device__ void build_canonical(const uint8_t* len, int dict, unsigned* key32, u
     for (int L = 1; L <= kMaxLen; ++L)
       ct->limit[L] = ((unsigned long long)ct->first_code[L] + ct->count[L]) << (32 - L);
     ct->limit[kMaxLen + 1] = 1ull << 32;
-    ct->n = (unsigned)n;
+    ct->n = p;
     ct->max_len = maxl;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < RMAX; ++r) {
+    if (r >= rows) break;
+    const int s = wid * seg + r * 32 + lane;
+    const unsigned L = s < dict ? len[s] : 0u;
+    if (L != 0u && L <= (unsigned)kMaxLen) canon[ct->first_pos[L] + wcnt[wc_idx(L, wid)] + loc[r]] = (uint16_t)s;
   }
   __syncthreads();
 }
@@ -228,42 +262,50 @@ struct CbSmem {
 __global__ void __launch_bounds__(kCbThreads) codebook_kernel(CodebookArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CbSmem& S = *reinterpret_cast<CbSmem*>(smem_raw);
-  __shared__ unsigned s_n, s_lp, s_qp, s_qe, s_pl, s_pq, s_leaves, s_rounds, s_maxd, s_total;
+  __shared__ unsigned s_n, s_lp, s_qp, s_qe, s_pl, s_pq, s_leaves, s_rounds, s_maxd, s_total, s_maxk;
   __shared__ unsigned long long s_bits;
   const int dict = a.dict;
   if (threadIdx.x == 0) s_bits = 0;
   uint16_t* merged = reinterpret_cast<uint16_t*>(S.keys);                      // [2*kMaxDict]
   uint16_t* round_end = reinterpret_cast<uint16_t*>(S.keys) + 2 * kMaxDict;    // [kMaxDict]
   for (int shift = 0;; ++shift) {
-    // 1. present symbols as (freq' << 13 | sym) keys
+    // 1. present symbols, in symbol order, as (freq', symbol) pairs
+    unsigned* ka = reinterpret_cast<unsigned*>(S.keys);  // [kMaxDict] keys
+    unsigned* wcnt = ka + kMaxDict;                       // [256 * 32] sort counts
+    uint16_t* sb = reinterpret_cast<uint16_t*>(S.iw);    // [kMaxDict] sort buffer
+    if (threadIdx.x == 0) s_maxk = 0;
     const int per = (dict + blockDim.x - 1) / blockDim.x;
     const int s0 = threadIdx.x * per;
     unsigned cnt = 0;
     for (int s = s0; s < s0 + per && s < dict; ++s) cnt += a.hist[s] ? 1u : 0u;
     unsigned pos = block_excl_scan(cnt, S.scan_tmp, &s_n);
+    unsigned mk = 0;
     for (int s = s0; s < s0 + per && s < dict; ++s) {
       const unsigned f = a.hist[s];
       if (f) {
         const unsigned fs = shift ? max(1u, f >> shift) : f;
-        S.keys[pos++] = ((unsigned long long)fs << 13) | (unsigned long long)s;
+        ka[pos] = fs;
+        S.ls[pos] = (uint16_t)s;
+        ++pos;
+        mk = max(mk, fs);
       }
     }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mk = max(mk, __shfl_xor_sync(0xffffffffu, mk, o));
+    if ((threadIdx.x & 31) == 0 && mk) atomicMax(&s_maxk, mk);
     for (int s = threadIdx.x; s < dict; s += blockDim.x) S.len[s] = 0;
     __syncthreads();
     const int n = (int)s_n;
     if (n <= 1) {
-      if (n == 1 && threadIdx.x == 0) S.len[S.keys[0] & 8191ull] = 1;
+      if (n == 1 && threadIdx.x == 0) S.len[S.ls[0]] = 1;
       __syncthreads();
       break;
     }
-    int P = 1;
-    while (P < n) P <<= 1;
-    for (int i = n + threadIdx.x; i < P; i += blockDim.x) S.keys[i] = ~0ull;
-    __syncthreads();
-    bitonic_sort(S.keys, P);
+    // leaves by ascending weight, ties in symbol order, into (lw, ls)
+    const int which = radix_sort_pairs(ka, S.ls, S.lw, sb, wcnt, n, s_maxk, S.scan_tmp);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      S.lw[i] = (unsigned)(S.keys[i] >> 13);
-      S.ls[i] = (uint16_t)(S.keys[i] & 8191ull);
+      if (which == 0) S.lw[i] = ka[i];
+      else S.ls[i] = sb[i];
     }
     if (threadIdx.x == 0) { s_lp = 0; s_qp = 0; s_qe = 0; s_rounds = 0; s_leaves = 0; }
     __syncthreads();
