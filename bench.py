@@ -558,41 +558,51 @@ def main():
     copy_stream = torch.cuda.Stream(dev)
     h2d_stream = torch.cuda.Stream(dev)
     e2e_steps = max(4, args.steps // 2)
-    d2h = 0
-    barrier()
-    ev0.record(stream)
-    h2d_done = [torch.cuda.Event(), torch.cuda.Event()]
-    used = [torch.cuda.Event(), torch.cuda.Event()]  # last compression that read dev_in[k]
-    d2h_done = [torch.cuda.Event(), torch.cuda.Event()]  # last read-back from bufs2[k]
-    with torch.cuda.stream(h2d_stream):
-        h2d_stream.wait_event(ev0)
-        dev_in[0].copy_(host_in, non_blocking=True)
-        h2d_done[0].record(h2d_stream)
-    for i in range(e2e_steps):
-        k = i % 2
-        if i + 1 < e2e_steps:  # next step's field, once its buffer's last reader is done
-            with torch.cuda.stream(h2d_stream):
-                if i >= 1:
-                    h2d_stream.wait_event(used[1 - k])
-                dev_in[1 - k].copy_(host_in, non_blocking=True)
-                h2d_done[1 - k].record(h2d_stream)
-        stream.wait_event(h2d_done[k])
-        if i >= 2:
-            stream.wait_event(d2h_done[k])  # this step's output buffers have been read back
+
+    def e2e_run(nsteps):
+        """nsteps pipelined steps; returns (event pair, D2H bytes of the last step)."""
         d2h = 0
-        for tol, b, ho in zip(TOLS, bufs2[k], host_out[k]):
-            s = bm.compress(dev_in[k], tol, mode="rel", out=b, **PARAMS)
-            done = torch.cuda.Event()
-            done.record(stream)
-            with torch.cuda.stream(copy_stream):
-                copy_stream.wait_event(done)
-                ho[: s.numel()].copy_(s, non_blocking=True)
-            d2h += s.numel()
-        used[k].record(stream)
-        d2h_done[k].record(copy_stream)
-    stream.wait_stream(copy_stream)  # the timed region ends when every stream is on the host
-    ev1.record(stream)
-    barrier()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h2d_done = [torch.cuda.Event(), torch.cuda.Event()]
+        used = [torch.cuda.Event(), torch.cuda.Event()]  # last compression that read dev_in[k]
+        d2h_done = [torch.cuda.Event(), torch.cuda.Event()]  # last read-back from bufs2[k]
+        with torch.cuda.stream(h2d_stream):
+            h2d_stream.wait_event(e0)
+            dev_in[0].copy_(host_in, non_blocking=True)
+            h2d_done[0].record(h2d_stream)
+        for i in range(nsteps):
+            k = i % 2
+            if i + 1 < nsteps:  # next step's field, once its buffer's last reader is done
+                with torch.cuda.stream(h2d_stream):
+                    if i >= 1:
+                        h2d_stream.wait_event(used[1 - k])
+                    dev_in[1 - k].copy_(host_in, non_blocking=True)
+                    h2d_done[1 - k].record(h2d_stream)
+            stream.wait_event(h2d_done[k])
+            if i >= 2:
+                stream.wait_event(d2h_done[k])  # this step's output buffers have been read back
+            d2h = 0
+            for tol, b, ho in zip(TOLS, bufs2[k], host_out[k]):
+                s = bm.compress(dev_in[k], tol, mode="rel", out=b, **PARAMS)
+                done = torch.cuda.Event()
+                done.record(stream)
+                with torch.cuda.stream(copy_stream):
+                    copy_stream.wait_event(done)
+                    ho[: s.numel()].copy_(s, non_blocking=True)
+                d2h += s.numel()
+            used[k].record(stream)
+            d2h_done[k].record(copy_stream)
+        stream.wait_stream(copy_stream)  # the timed region ends when every stream is on the host
+        e1.record(stream)
+        barrier()
+        return e0, e1, d2h
+
+    # untimed warm-up over both buffer sets: the first transfers from and to
+    # freshly pinned host pages are much slower than the steady state
+    e2e_run(max(2, args.warmup))
+    ev0, ev1, d2h = e2e_run(e2e_steps)
     e2e_ms = ev0.elapsed_time(ev1) / e2e_steps
     e2e = {"value": ws * nbytes * len(TOLS) / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": d2h,
