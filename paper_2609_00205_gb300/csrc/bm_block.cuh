@@ -1,6 +1,7 @@
 // In-cache Block kernels (Sec. III-A, III-D): one CTA keeps a B^3 block in
 // shared memory through K decomposition levels, quantises the coefficients on
-// the spot and writes only symbols (u16) and the block's coarse values.
+// the spot and writes only symbols (u16), the codes of escaping symbols and
+// the block's coarse values.
 //
 // Level structure (Sec. II-B): for a level of N (odd) nodes per dimension
 //   Phase A  lines (i0,i1) along dim 2: coefficients d = u - I(u|C) at every
@@ -49,6 +50,12 @@
 #ifndef BM_INV_MIN_CTAS
 #define BM_INV_MIN_CTAS 4
 #endif
+// BM_INV_CODES: the inverse turns symbols and escapes into int32 codes while
+// loading a block (coalesced escape loads, 4 bytes per staged code) instead of
+// reading each escape's code from the escape array where it is needed.
+#ifndef BM_INV_CODES
+#define BM_INV_CODES 1
+#endif
 
 namespace bm {
 
@@ -89,6 +96,11 @@ constexpr int lvl_offset(int B, int l) {  // first symbol of level l inside a bl
   return l == 0 ? 0 : cube(lvl_n(B, l - 1)) - cube(lvl_n(B, l)) + lvl_offset(B, l - 1);
 }
 
+// Staging of a code in the forward kernel's 16-bit shared-memory array:
+// code + kStageBias, or kStageWide for a code outside [-2^15, 2^15 - 2].
+constexpr int kStageBias = 1 << 15;
+constexpr unsigned kStageWide = 0xFFFFu;
+
 template <typename T, int B, int K>
 struct BlockCfg {
   static constexpr int NT = ((B * B + 31) / 32) * 32;
@@ -111,7 +123,9 @@ struct BlockCfg {
   static constexpr size_t fwd_hist_off = up16(fwd_stage_off + 2 * PB);
   static constexpr size_t fwd_smem = fwd_hist_off + (BM_FWD_HIST ? 4 * kHistWin : 0);
   static constexpr size_t inv_stage_off = up16(sizeof(T) * (A + T1 + T2 + CB0 + CB1));
-  static constexpr size_t inv_smem(int mode) { return inv_stage_off + up16((mode ? sizeof(T) : 2) * PB); }
+  static constexpr size_t inv_smem(int mode) {
+    return inv_stage_off + up16((mode ? sizeof(T) : (BM_INV_CODES ? 4 : 2)) * PB);
+  }
   // CTAs per SM the forward kernel is compiled for: BM_FWD_MIN_CTAS, or as many
   // as the shared memory of an SM holds (228 KB, 1 KB reserved per CTA) when
   // fewer, so the register budget is not cut for residency that cannot happen.
@@ -140,8 +154,7 @@ __device__ __forceinline__ void hist_count(unsigned* hloc, unsigned* hglob, int 
 template <typename T, int N, int MODE>
 __device__ __forceinline__ void level_fwd(T* X, T* __restrict__ T1, T* __restrict__ out, const int lvl_off, const T rq,
                                           uint16_t* stage, int32_t* __restrict__ esc_blk, T* __restrict__ coef_blk,
-                                          unsigned* hloc, unsigned* hglob, const int radius, bool& ovf,
-                                          unsigned& centre) {
+                                          bool& ovf) {
   constexpr int C = (N + 1) / 2;
   const auto& tb = block_tab<T, N>();
   for (int L = threadIdx.x; L < N * N; L += blockDim.x) {
@@ -171,20 +184,19 @@ __device__ __forceinline__ void level_fwd(T* X, T* __restrict__ T1, T* __restric
     const int cc_before = ((i0 + 1) / 2) * C + (f0 ? 0 : (i1 + 1) / 2);
     const int base = lvl_off + L * N - cc_before * C;
     if (MODE == 0) {
-      // symbol code + radius for |code| < radius, else the escape symbol 0
-      // and the code itself at the same position of the escape array (a
-      // predicated store: no memory traffic unless the symbol escapes)
+      // the quantisation codes staged in the block's order as code + 2^15
+      // (store_codes turns them into symbols and escapes when the block is
+      // done); a code outside [-2^15, 2^15 - 2] is staged as 0xFFFF and goes
+      // to the escape array at once (a predicated store, rare)
 #pragma unroll
       for (int k = 0; k < N; ++k) {
         if ((k & 1) || !cc) {
           const int pos = base + (cc ? k / 2 : k);
           const int code = quantize(d[k], rq, ovf);
-          const unsigned u = (unsigned)(code + radius);
-          const bool in = (u - 1u) < (unsigned)(2 * radius - 1);
-          const unsigned sv = in ? u : 0u;
-          stage[pos] = (uint16_t)sv;
-          if (!in) esc_blk[pos] = code;
-          if (BM_FWD_HIST) hist_count(hloc, hglob, radius, sv, centre);
+          const unsigned b = (unsigned)(code + kStageBias);
+          const bool wide = b >= kStageWide;
+          stage[pos] = (uint16_t)(wide ? kStageWide : b);
+          if (wide) esc_blk[pos] = code;
         }
       }
     } else {
@@ -236,13 +248,10 @@ struct LevelBufs {
 template <typename T, int N, int L, int K, int B, int MODE>
 struct FwdLevels {
   __device__ __forceinline__ static void run(const LevelBufs<T>& bufs, T* T1, const T* rq, uint16_t* stage,
-                                             int32_t* esc_blk, T* coef_blk, unsigned* hloc, unsigned* hglob,
-                                             int radius, bool& ovf, unsigned& centre) {
-    level_fwd<T, N, MODE>(bufs(L), T1, bufs(L + 1), lvl_offset(B, L), rq[L], stage, esc_blk, coef_blk, hloc,
-                          hglob, radius, ovf, centre);
+                                             int32_t* esc_blk, T* coef_blk, bool& ovf) {
+    level_fwd<T, N, MODE>(bufs(L), T1, bufs(L + 1), lvl_offset(B, L), rq[L], stage, esc_blk, coef_blk, ovf);
     if constexpr (L + 1 < K)
-      FwdLevels<T, (N + 1) / 2, L + 1, K, B, MODE>::run(bufs, T1, rq, stage, esc_blk, coef_blk, hloc, hglob,
-                                                         radius, ovf, centre);
+      FwdLevels<T, (N + 1) / 2, L + 1, K, B, MODE>::run(bufs, T1, rq, stage, esc_blk, coef_blk, ovf);
   }
 };
 
@@ -339,26 +348,62 @@ __device__ __forceinline__ void store_block(const BlockSpan<T, B>& sp, const T* 
 
 // Copy of n u16 symbols from shared to global memory with the widest aligned
 // stores the per-block offset allows.
+// A block's staged codes -> symbols: code + radius for |code| < radius, else
+// the escape symbol 0 with the code kept at the same position of the escape
+// array.  Consecutive threads take consecutive groups of four codes, so the
+// symbol stores (8 bytes) and the escape stores (the whole 16-byte group
+// whenever one of its codes escapes) are coalesced; escape-array entries at
+// other positions are never read.  A group holding a wide code (already in
+// the escape array) stores its other escapes one by one.
 template <int PB>
-__device__ __forceinline__ void store_symbols(uint16_t* __restrict__ dst, const uint16_t* __restrict__ src,
-                                              int64_t sbase) {
-  if constexpr ((PB % 4) == 0) {
-    const uint2* s2 = reinterpret_cast<const uint2*>(src);
-    uint2* d2 = reinterpret_cast<uint2*>(dst);
-    for (int i = threadIdx.x; i < PB / 4; i += blockDim.x) d2[i] = s2[i];
-  } else if constexpr ((PB % 2) == 0) {
-    const uint32_t* s32 = reinterpret_cast<const uint32_t*>(src);
-    uint32_t* d32 = reinterpret_cast<uint32_t*>(dst);
-    for (int i = threadIdx.x; i < PB / 2; i += blockDim.x) d32[i] = s32[i];
+__device__ __forceinline__ void store_codes(uint16_t* __restrict__ sym, int32_t* __restrict__ esc,
+                                            const uint16_t* __restrict__ st, const int radius, unsigned* hloc,
+                                            unsigned* hglob, unsigned& centre) {
+  const unsigned span = (unsigned)(2 * radius - 1);
+  auto to_sym = [&](unsigned b) {  // b: staged value; wide codes always escape
+    const unsigned u = (unsigned)((int)b - kStageBias + radius);
+    return (b != kStageWide && (u - 1u) < span) ? u : 0u;
+  };
+  bool vec = false;
+  if constexpr (PB % 4 == 0)
+    vec = ((reinterpret_cast<uintptr_t>(sym) & 7) | (reinterpret_cast<uintptr_t>(esc) & 15)) == 0;
+  if (vec) {
+    const uint2* s2 = reinterpret_cast<const uint2*>(st);
+    uint2* d2 = reinterpret_cast<uint2*>(sym);
+    int4* e4 = reinterpret_cast<int4*>(esc);
+    for (int i = threadIdx.x; i < PB / 4; i += blockDim.x) {
+      const uint2 w = s2[i];
+      const unsigned b[4] = {w.x & 0xFFFFu, w.x >> 16, w.y & 0xFFFFu, w.y >> 16};
+      unsigned a[4];
+      bool any_esc = false, any_wide = false;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        a[j] = to_sym(b[j]);
+        any_esc |= a[j] == 0u;
+        any_wide |= b[j] == kStageWide;
+      }
+      d2[i] = make_uint2(a[0] | (a[1] << 16), a[2] | (a[3] << 16));
+      if (any_esc) {
+        if (!any_wide) {
+          e4[i] = make_int4((int)b[0] - kStageBias, (int)b[1] - kStageBias, (int)b[2] - kStageBias,
+                            (int)b[3] - kStageBias);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (a[j] == 0u && b[j] != kStageWide) esc[4 * i + j] = (int)b[j] - kStageBias;
+        }
+      }
+      if (BM_FWD_HIST)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) hist_count(hloc, hglob, radius, a[j], centre);
+    }
   } else {
-    (void)sbase;
-    if ((reinterpret_cast<uintptr_t>(dst) & 3) == 0) {
-      const uint32_t* s32 = reinterpret_cast<const uint32_t*>(src);
-      uint32_t* d32 = reinterpret_cast<uint32_t*>(dst);
-      for (int i = threadIdx.x; i < PB / 2; i += blockDim.x) d32[i] = s32[i];
-      if (threadIdx.x == 0) dst[PB - 1] = src[PB - 1];
-    } else {
-      for (int i = threadIdx.x; i < PB; i += blockDim.x) dst[i] = src[i];
+    for (int i = threadIdx.x; i < PB; i += blockDim.x) {
+      const unsigned b = st[i];
+      const unsigned a = to_sym(b);
+      sym[i] = (uint16_t)a;
+      if (!a && b != kStageWide) esc[i] = (int)b - kStageBias;
+      if (BM_FWD_HIST) hist_count(hloc, hglob, radius, a, centre);
     }
   }
 }
@@ -407,7 +452,7 @@ __global__ void __launch_bounds__(BlockCfg<T, B, K>::NT_FWD, BlockCfg<T, B, K>::
     const int64_t sbase = b * (int64_t)Cfg::PB;
     LevelBufs<T> bufs{Abuf + (BM_FWD_DOUBLE_BUFFER ? buf : 0) * Cfg::A, cb0, cb1};
     FwdLevels<T, B, 0, K, B, MODE>::run(bufs, T1, rq, stage, a.esc + (MODE == 0 ? sbase : 0),
-                                        a.coef + (MODE == 1 ? sbase : 0), hloc, a.hist, a.radius, ovf, centre);
+                                        a.coef + (MODE == 1 ? sbase : 0), ovf);
     // block coarse values -> gathered grid G
     {
       constexpr int M = Cfg::M;
@@ -418,7 +463,7 @@ __global__ void __launch_bounds__(BlockCfg<T, B, K>::NT_FWD, BlockCfg<T, B, K>::
         g[((int64_t)j0 * a.g1 + j1) * a.g2 + j2] = cf[e];
       }
     }
-    if (MODE == 0) store_symbols<Cfg::PB>(a.sym + sbase, stage, sbase);
+    if (MODE == 0) store_codes<Cfg::PB>(a.sym + sbase, a.esc + sbase, stage, a.radius, hloc, a.hist, centre);
     __syncthreads();
     buf ^= 1;
   }
@@ -434,6 +479,36 @@ __global__ void __launch_bounds__(BlockCfg<T, B, K>::NT_FWD, BlockCfg<T, B, K>::
     for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) {
       const unsigned v = hloc[i];
       if (v && lo + i >= 0 && lo + i < 2 * a.radius) atomicAdd(a.hist + lo + i, v);
+    }
+  }
+}
+
+// Symbols and escapes of a block -> int32 codes in shared memory (the inverse
+// of store_codes): consecutive threads take consecutive groups of four, and a
+// group with an escape symbol loads its four escape-array entries as one
+// coalesced 16-byte load.
+template <int PB>
+__device__ __forceinline__ void load_codes(const uint16_t* __restrict__ sym, const int32_t* __restrict__ esc,
+                                           int32_t* __restrict__ st, const int radius) {
+  bool vec = false;
+  if constexpr (PB % 4 == 0)
+    vec = ((reinterpret_cast<uintptr_t>(sym) & 7) | (reinterpret_cast<uintptr_t>(esc) & 15)) == 0;
+  if (vec) {
+    const uint2* s2 = reinterpret_cast<const uint2*>(sym);
+    const int4* e4 = reinterpret_cast<const int4*>(esc);
+    int4* d4 = reinterpret_cast<int4*>(st);
+    for (int i = threadIdx.x; i < PB / 4; i += blockDim.x) {
+      const uint2 w = __ldg(s2 + i);
+      const int a0 = (int)(w.x & 0xFFFFu), a1 = (int)(w.x >> 16), a2 = (int)(w.y & 0xFFFFu), a3 = (int)(w.y >> 16);
+      int4 c = make_int4(0, 0, 0, 0);
+      if (!(a0 && a1 && a2 && a3)) c = __ldg(e4 + i);
+      d4[i] = make_int4(a0 ? a0 - radius : c.x, a1 ? a1 - radius : c.y, a2 ? a2 - radius : c.z,
+                        a3 ? a3 - radius : c.w);
+    }
+  } else {
+    for (int i = threadIdx.x; i < PB; i += blockDim.x) {
+      const int a = (int)sym[i];
+      st[i] = a ? a - radius : esc[i];
     }
   }
 }
@@ -461,8 +536,12 @@ __device__ __forceinline__ void level_inv(T* __restrict__ X, T* __restrict__ T1,
       if ((k & 1) || !cc) {
         const int pos = base + (cc ? k / 2 : k);
         if (MODE == 0) {
+#if BM_INV_CODES
+          const int code = reinterpret_cast<const int32_t*>(stage)[pos];
+#else
           const unsigned s = reinterpret_cast<const uint16_t*>(stage)[pos];
           const int code = s ? (int)s - radius : esc_blk[pos];
+#endif
           v = dequant(code, q);
         } else {
           v = reinterpret_cast<const T*>(stage)[pos];
@@ -545,6 +624,9 @@ __global__ void __launch_bounds__(BlockCfg<T, B, K>::NT_INV, BlockCfg<T, B, K>::
     const BlockCoord bc(b, a.nb1, a.nb2);
     const int64_t sbase = b * (int64_t)Cfg::PB;
     if (MODE == 0) {
+#if BM_INV_CODES
+      load_codes<Cfg::PB>(a.sym + sbase, a.esc + sbase, reinterpret_cast<int32_t*>(stage), a.radius);
+#else
       uint16_t* st = reinterpret_cast<uint16_t*>(stage);
       const uint16_t* src = a.sym + sbase;
       if ((reinterpret_cast<uintptr_t>(src) & 3) == 0) {
@@ -555,6 +637,7 @@ __global__ void __launch_bounds__(BlockCfg<T, B, K>::NT_INV, BlockCfg<T, B, K>::
       } else {
         for (int i = threadIdx.x; i < Cfg::PB; i += blockDim.x) st[i] = src[i];
       }
+#endif
     } else {
       T* st = reinterpret_cast<T*>(stage);
       for (int i = threadIdx.x; i < Cfg::PB; i += blockDim.x) st[i] = a.coef[sbase + i];
