@@ -79,19 +79,13 @@ def test_recompose_matches_oracle(bm, case):
     assert np.abs(g.astype(np.float64) - u).max() <= 8 * _coef_tol(u)
 
 
-@pytest.mark.parametrize("tol", [1e-2, 1e-4])
-@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_compress_parity(bm, case, tol):
-    name, shape, dt, B, K, M = case
-    u = _field(name, shape, dt)
-    f64 = dt == np.float64
-    roi = None
-    if name.startswith("roi"):
-        mask = fields.gradient_roi(u, B)
-        roi = np.where(mask, tol * 1e-2, tol)
+def _check_compress_parity(bm, u, tol, mode, B, K, M, roi=None):
+    shape = u.shape
+    f64 = u.dtype == np.float64
+    rel = mode == "rel"
     t = torch.from_numpy(u).to(DEV)
-    sg = bm.compress(t, tol, mode="rel", roi=roi, block=B, levels=K, global_levels=M).cpu().numpy()
-    so, co = oracle.compress(u, tol, rel=True, roi=roi, B=B, K=K, M=M, want_codes=True)
+    sg = bm.compress(t, tol, mode=mode, roi=roi, block=B, levels=K, global_levels=M).cpu().numpy()
+    so, co = oracle.compress(u, tol, rel=rel, roi=roi, B=B, K=K, M=M, want_codes=True)
     hg, ho = oracle.stream_header(sg), oracle.stream_header(so)
     assert hg["raw"] == ho["raw"]
     # the L-inf bound at every node of every region (GPU decode of the GPU stream)
@@ -100,7 +94,7 @@ def test_compress_parity(bm, case, tol):
     assert np.all(np.abs(d - u) <= tau)
     if hg["raw"]:
         np.testing.assert_array_equal(sg, so)
-        return
+        return None
     for k in ["K", "M", "chunk", "radius", "n_tiers", "m", "nb", "n_symbols", "n_chunks", "max_abs", "margin",
               "off_tiers", "off_qtab", "off_blocktier", "off_chunks"]:
         assert hg[k] == ho[k], k
@@ -117,6 +111,41 @@ def test_compress_parity(bm, case, tol):
         np.testing.assert_array_equal(sg, so)  # whole stream bit-exact
     if f64:
         assert nflip <= 2
+    return np.asarray(co)
+
+
+@pytest.mark.parametrize("tol", [1e-2, 1e-4])
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_compress_parity(bm, case, tol):
+    name, shape, dt, B, K, M = case
+    u = _field(name, shape, dt)
+    roi = None
+    if name.startswith("roi"):
+        mask = fields.gradient_roi(u, B)
+        roi = np.where(mask, tol * 1e-2, tol)
+    _check_compress_parity(bm, u, tol, "rel", B, K, M, roi=roi)
+
+
+def _smooth_with_spikes(shape, dtype):
+    """A smooth field with a few large spikes: small codes almost everywhere,
+    escapes near the spikes, and codes beyond 16 bits at the spikes."""
+    i, j, k = np.meshgrid(*[np.arange(n, dtype=np.float64) for n in shape], indexing="ij")
+    u = np.sin(0.05 * i) * np.cos(0.04 * j) + 0.5 * np.sin(0.03 * k)
+    rng = np.random.default_rng(5)
+    idx = rng.integers(0, u.size, 30)
+    u.ravel()[idx] += rng.choice([-1.0, 1.0], 30) * 3.0
+    return np.ascontiguousarray(u.astype(dtype))
+
+
+@pytest.mark.parametrize("dt,B,K,M", [(np.float32, 17, 2, 2), (np.float32, 9, 3, 1), (np.float64, 9, 2, 2)])
+def test_wide_code_parity(bm, dt, B, K, M):
+    """Escapes in groups with and without codes beyond 16 bits (the block
+    kernels stage codes in 16 bits and send wider ones straight to the escape
+    array), against the oracle."""
+    u = _smooth_with_spikes((40, 37, 45), dt)
+    co = _check_compress_parity(bm, u, 1e-4, "abs", B, K, M)
+    assert co is not None
+    assert int((np.abs(co) >= 32767).sum()) > 0 and int(((np.abs(co) >= 4096) & (np.abs(co) < 32767)).sum()) > 0
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
