@@ -151,6 +151,24 @@ __device__ __forceinline__ int upper_bound_u32(const unsigned* a, int lo, int hi
   }
   return lo;
 }
+// upper_bound by the 32 lanes of a warp (all lanes call it with the same
+// arguments and get the same result): each step probes the last element of 32
+// equal segments and keeps the first segment whose last element exceeds v.
+__device__ __forceinline__ int warp_upper_bound_u32(const unsigned* a, int lo, int hi, unsigned v) {
+  const int lane = threadIdx.x & 31;
+  while (hi - lo > 32) {
+    const int step = (hi - lo + 31) / 32;
+    const int p = min(lo + (lane + 1) * step, hi) - 1;
+    const unsigned m = __ballot_sync(0xffffffffu, a[p] > v);
+    if (m == 0u) return hi;
+    const int f = __ffs(m) - 1;
+    const int nlo = lo + f * step;
+    hi = min(nlo + step, hi);
+    lo = nlo;
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, lane < hi - lo && a[lo + lane] > v);
+  return m ? lo + __ffs(m) - 1 : hi;
+}
 __device__ __forceinline__ int lower_bound_u32(const unsigned* a, int lo, int hi, unsigned v) {
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
@@ -309,21 +327,37 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(CodebookArgs a) {
     }
     if (threadIdx.x == 0) { s_lp = 0; s_qp = 0; s_qe = 0; s_rounds = 0; s_leaves = 0; }
     __syncthreads();
-    // 2. parallel rounds of the two-queue construction
-    while (s_qe < (unsigned)(n - 1)) {
-      if (threadIdx.x == 0) {
+    // 2. parallel rounds of the two-queue construction.  Warp 0 folds the
+    // previous round into the queue state and picks this round's pairs: all
+    // nodes of weight <= X (X = the two smallest weights summed), found by
+    // warp-wide searches of both sorted queues.
+    int np_prev = 0;
+    while (true) {
+      if (threadIdx.x < 32) {
+        if (threadIdx.x == 0 && np_prev) {
+          s_lp += s_leaves;
+          s_qp += 2 * np_prev - s_leaves;
+          s_qe += np_prev;
+          round_end[s_rounds++] = (uint16_t)s_qe;
+          s_leaves = 0;
+        }
+        __syncwarp();
         unsigned lp = s_lp, qp = s_qp;
         const unsigned qe = s_qe;
-        unsigned w[2];
-        for (int t = 0; t < 2; ++t) {
-          if (lp < (unsigned)n && (qp >= qe || S.lw[lp] <= S.iw[qp])) w[t] = S.lw[lp++];
-          else w[t] = S.iw[qp++];
+        if (qe < (unsigned)(n - 1)) {
+          unsigned w[2];
+          for (int t = 0; t < 2; ++t) {
+            if (lp < (unsigned)n && (qp >= qe || S.lw[lp] <= S.iw[qp])) w[t] = S.lw[lp++];
+            else w[t] = S.iw[qp++];
+          }
+          const unsigned X = w[0] + w[1];
+          const int pl = warp_upper_bound_u32(S.lw, (int)s_lp, n, X) - (int)s_lp;
+          const int pq = warp_upper_bound_u32(S.iw, (int)s_qp, (int)qe, X) - (int)s_qp;
+          if (threadIdx.x == 0) { s_pl = (unsigned)pl; s_pq = (unsigned)pq; }
         }
-        const unsigned X = w[0] + w[1];
-        s_pl = (unsigned)upper_bound_u32(S.lw, s_lp, n, X) - s_lp;
-        s_pq = (unsigned)upper_bound_u32(S.iw, s_qp, qe, X) - s_qp;
       }
       __syncthreads();
+      if (s_qe >= (unsigned)(n - 1)) break;
       const int lp = s_lp, qp = s_qp, qe = s_qe, pl = s_pl, pq = s_pq;
       const int npairs = (pl + pq) >> 1;
       for (int e = threadIdx.x; e < pl + pq; e += blockDim.x) {
@@ -351,14 +385,7 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(CodebookArgs a) {
         leaves += (x < n) + (y < n);
       }
       if (leaves) atomicAdd(&s_leaves, leaves);
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        s_lp += s_leaves;
-        s_qp += 2 * npairs - s_leaves;
-        s_qe += npairs;
-        round_end[s_rounds++] = (uint16_t)s_qe;
-        s_leaves = 0;
-      }
+      np_prev = npairs;
       __syncthreads();
     }
     // 3. depths, rounds in reverse (a parent is always created in a later round)
