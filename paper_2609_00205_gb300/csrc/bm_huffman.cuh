@@ -968,27 +968,47 @@ __device__ __forceinline__ void decode_tables_block(const uint8_t* runs, unsigne
   DtSmem& S = *reinterpret_cast<DtSmem*>(smem_raw);
   __shared__ unsigned s_bad;
   __shared__ unsigned long long s_kr;
+  __shared__ unsigned s_total;
   if (threadIdx.x == 0) { s_bad = 0; s_kr = 0; }
   for (int s = threadIdx.x; s < dict; s += blockDim.x) S.len[s] = 0;
+  // the codebook section is walked serially: read it from shared memory when
+  // it fits in the key scratch (free until build_canonical)
+  const uint8_t* rbase = runs;
+  if (nbytes <= sizeof(S.key32) && (reinterpret_cast<uintptr_t>(runs) & 3) == 0) {
+    const unsigned* src = reinterpret_cast<const unsigned*>(runs);
+    const unsigned nw = (unsigned)(nbytes / 4);
+    for (unsigned i = threadIdx.x; i < nw; i += blockDim.x) S.key32[i] = src[i];
+    uint8_t* kb = reinterpret_cast<uint8_t*>(S.key32);
+    for (unsigned i = 4 * nw + threadIdx.x; i < (unsigned)nbytes; i += blockDim.x) kb[i] = runs[i];
+    rbase = kb;
+  }
   __syncthreads();
-  // walk the run headers (serial over runs, parallel over each run's bytes)
+  // walk the run headers (serial, 512 at a time), then every thread copies
+  // lengths of the batch (rcount holds each run's first index in the batch)
   unsigned long long off = 0;
   for (unsigned long long rb = 0; rb < n_runs; rb += 512) {
     const int nb = (int)min(512ull, n_runs - rb);
     if (threadIdx.x == 0) {
+      unsigned tot = 0;
       for (int q = 0; q < nb; ++q) {
         if (off + 8 > nbytes) { s_bad = 1; break; }
-        const unsigned first = *reinterpret_cast<const unsigned*>(runs + off);
-        const unsigned cnt = *reinterpret_cast<const unsigned*>(runs + off + 4);
+        const unsigned first = *reinterpret_cast<const unsigned*>(rbase + off);
+        const unsigned cnt = *reinterpret_cast<const unsigned*>(rbase + off + 4);
         if ((unsigned long long)first + cnt > (unsigned long long)dict || off + 8 + cnt > nbytes) { s_bad = 1; break; }
-        S.rfirst[q] = first; S.rcount[q] = cnt; S.roff[q] = (unsigned)off;
+        S.rfirst[q] = first; S.rcount[q] = tot; S.roff[q] = (unsigned)off;
+        tot += cnt;
         off += 8ull + ((cnt + 3u) & ~3u);
       }
+      s_total = tot;
     }
     __syncthreads();
     if (s_bad) break;
-    for (int q = 0; q < nb; ++q)
-      for (unsigned t = threadIdx.x; t < S.rcount[q]; t += blockDim.x) S.len[S.rfirst[q] + t] = runs[S.roff[q] + 8 + t];
+    const unsigned tot = s_total;
+    for (unsigned e = threadIdx.x; e < tot; e += blockDim.x) {
+      const int q = upper_bound_u32(S.rcount, 0, nb, e) - 1;
+      const unsigned t = e - S.rcount[q];
+      S.len[S.rfirst[q] + t] = rbase[S.roff[q] + 8 + t];
+    }
     __syncthreads();
   }
   // Kraft sum (exact, in units of 2^-32) and the length bound
