@@ -1235,22 +1235,42 @@ __global__ void __launch_bounds__(256) escape_fixup_kernel(const uint16_t* sym, 
       continue;
     }
     unsigned long long e = e0 + (x - ne);
-    while (m) {
-      int idx[4];
-      int k = 0;
+    if (vec && (reinterpret_cast<uintptr_t>(esc + s0) & 15) == 0) {
+      // groups of four positions: one 16-byte store for each group holding an
+      // escape (entries of the other positions are never read)
+      int4* e4 = reinterpret_cast<int4*>(esc + s0);
+      for (int g = 0; g < per / 4 && m; ++g) {
+        const unsigned bits = (unsigned)(m >> (4 * g)) & 15u;
+        if (!bits) continue;
+        int v[4];
+        unsigned r = 0;
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        idx[t] = m ? __ffsll((long long)m) - 1 : -1;
-        m &= m ? m - 1 : 0ull;
-        k += idx[t] >= 0;
+        for (int t = 0; t < 4; ++t) {
+          const bool on = (bits >> t) & 1u;
+          v[t] = on ? __ldg(ocode + e + r) : 0;
+          r += on;
+        }
+        e4[g] = make_int4(v[0], v[1], v[2], v[3]);
+        e += r;
       }
-      int32_t v[4];
+    } else {
+      while (m) {
+        int idx[4];
+        int k = 0;
 #pragma unroll
-      for (int t = 0; t < 4; ++t) v[t] = idx[t] >= 0 ? __ldg(ocode + e + t) : 0;
+        for (int t = 0; t < 4; ++t) {
+          idx[t] = m ? __ffsll((long long)m) - 1 : -1;
+          m &= m ? m - 1 : 0ull;
+          k += idx[t] >= 0;
+        }
+        int32_t v[4];
 #pragma unroll
-      for (int t = 0; t < 4; ++t)
-        if (idx[t] >= 0) esc[s0 + idx[t]] = v[t];
-      e += k;
+        for (int t = 0; t < 4; ++t) v[t] = idx[t] >= 0 ? __ldg(ocode + e + t) : 0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (idx[t] >= 0) esc[s0 + idx[t]] = v[t];
+        e += k;
+      }
     }
   }
 }
