@@ -18,7 +18,11 @@
  *     per CUDA stream and released by bm_release_workspace().
  *   - `stream` is a cudaStream_t passed as void* (0 = legacy default stream).
  *     All device work is ordered on that stream.  Calls that return sizes
- *     (bm_compress) synchronise the stream before returning.
+ *     (bm_compress) synchronise the stream before returning.  A call's own
+ *     small transfers (tolerance tables, status block, stream header) are done
+ *     by a kernel through the device mapping of the library's pinned staging
+ *     memory, not by copy-engine copies, so a call does not wait behind bulk
+ *     copies the caller has queued on other streams.
  *   - Fields are 3-D, row-major (C order) with shape[2] varying fastest, each
  *     extent >= 2.  dtype: BM_F32 or BM_F64.
  *   - Every call returns a bm_status.  On failure a readable message is
