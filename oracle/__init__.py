@@ -36,8 +36,12 @@ def build(force: bool = False) -> str:
 def lib():
     global _lib
     if _lib is None:
-        build()
-        L = ctypes.CDLL(_LIB)
+        # OR_LIBRARY: a build of a modified oracle source (the planted-mistake
+        # tests run the pins against such builds); otherwise the in-tree build
+        path = os.environ.get("OR_LIBRARY")
+        if not path:
+            path = build()
+        L = ctypes.CDLL(path)
         P = ctypes.POINTER
         d, i64, u8 = ctypes.c_double, ctypes.c_int64, ctypes.c_uint8
         L.or_last_error.restype = ctypes.c_char_p
