@@ -114,6 +114,25 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(x, dev):
+    """The largest of a per-rank time over all ranks of the process group (x
+    itself without one): whole-job throughput divides the units of every rank
+    by the slowest rank's time."""
+    import torch
+
+    if torch.distributed.is_available() and torch.distributed.is_initialized() and \
+            torch.distributed.get_world_size() > 1:
+        t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t)
+    return float(x)
+
+
+def whole_job_gbs(ws, bytes_per_rank, ms_max):
+    """Weak-scaling aggregate: every rank's bytes over the slowest rank's time."""
+    return ws * bytes_per_rank / (ms_max * 1e-3) / 1e9
+
+
 def run_reference(args):
     """CPU oracle (FP64 C++, one thread) on a bounded sample of the workload."""
     import numpy as np
@@ -486,11 +505,8 @@ def main():
             for name, ms in st:
                 stage_ms.setdefault(name, []).append(ms)
     bm.set_timing(False)
-    if ws > 1:
-        t = torch.tensor([comp_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        comp_ms = float(t)
-    value = ws * nbytes * len(TOLS) / (comp_ms * 1e-3) / 1e9
+    comp_ms = max_over_ranks(comp_ms, dev)
+    value = whole_job_gbs(ws, nbytes * len(TOLS), comp_ms)
 
     if args.quick:
         if rank == 0:
@@ -512,8 +528,8 @@ def main():
             bm.decompress(s, out=out_field)
     ev1.record(stream)
     barrier()
-    decomp_ms = ev0.elapsed_time(ev1) / args.steps
-    decomp_gbs = ws * nbytes * len(TOLS) / (decomp_ms * 1e-3) / 1e9
+    decomp_ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dev)
+    decomp_gbs = whole_job_gbs(ws, nbytes * len(TOLS), decomp_ms)
     dstage = {}
     bm.set_timing(True)
     for _ in range(max(2, args.steps // 4)):
@@ -603,8 +619,8 @@ def main():
     # freshly pinned host pages are much slower than the steady state
     e2e_run(max(2, args.warmup))
     ev0, ev1, d2h = e2e_run(e2e_steps)
-    e2e_ms = ev0.elapsed_time(ev1) / e2e_steps
-    e2e = {"value": ws * nbytes * len(TOLS) / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
+    e2e_ms = max_over_ranks(ev0.elapsed_time(ev1) / e2e_steps, dev)
+    e2e = {"value": whole_job_gbs(ws, nbytes * len(TOLS), e2e_ms), "unit": "GB/s",
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": d2h,
            "pipelining": "step i+1's H2D and step i's D2H overlap the compressions (two buffer sets)"}
 
