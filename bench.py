@@ -14,6 +14,7 @@ needed between steps.
   python bench.py --workload batch64    # 64 uneven fields: batched call vs per-field loop
   python bench.py --workload diff257    # differentiable recompose: forward + backward
   python bench.py --workload model      # Eq. 1 fit on this GPU, its knee, Alg. 1 choices
+  python bench.py --workload roi385     # ROI error control: CR vs uniform 1e-5, L-inf per region
 
 Under torchrun (N > 1) every rank compresses its own field (seed + rank): the
 problems are independent, there is no collective on the data path, scaling
@@ -386,6 +387,75 @@ def run_diff257(args):
     print(json.dumps(line))
 
 
+def region_errors(d, u, block_mask, block):
+    """Max |d - u| over the nodes of ROI blocks and over the other nodes (block
+    mask: one bool per block of ``block`` nodes per dimension, row-major)."""
+    import numpy as np
+
+    m = np.asarray(block_mask, dtype=bool)
+    for ax in range(3):
+        m = np.repeat(m, block, axis=ax)
+    m = m[: u.shape[0], : u.shape[1], : u.shape[2]]
+    e = np.abs(np.asarray(d, dtype=np.float64) - np.asarray(u, dtype=np.float64))
+    return (float(e[m].max()) if m.any() else 0.0), (float(e[~m].max()) if (~m).any() else 0.0)
+
+
+def run_roi385(args):
+    """ROI error control on the FP64 385x385x257 field (smooth k^-3 background,
+    12 tanh fronts, 6 vortex tubes): ROI = blocks whose max |grad u| exceeds
+    the 95th percentile of |grad u|, ROI tolerance 1e-5 and background 1e-2
+    (relative to max|u|), B = 9, K = 2, M = 2.  Reports the compression ratio
+    against the same field at a uniform 1e-5, the L-inf error of each region
+    against its tolerance, and compress / decompress GB/s of both streams."""
+    import numpy as np
+    import torch
+
+    import fields
+    import paper_2609_00205_gb300 as bm
+
+    dev = torch.device("cuda", 0)
+    shape, B = (385, 385, 257), 9
+    params = dict(block=B, levels=2, global_levels=2)
+    u = fields.roi_field(shape, seed=3, device=dev).contiguous()
+    un = u.cpu().numpy()
+    mask = fields.gradient_roi(un, B)
+    roi = np.where(mask, 1e-5, 1e-2).ravel()
+    maxabs = float(np.abs(un).max())
+    nbytes = u.numel() * u.element_size()
+    out = torch.empty_like(u)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / args.steps
+
+    res = {}
+    for name, tol, r in (("roi", 1e-2, roi), ("uniform_1e-5", 1e-5, None)):
+        s = bm.compress(u, tol, mode="rel", roi=r, **params)
+        c_ms = timed(lambda: bm.compress(u, tol, mode="rel", roi=r, **params))
+        d_ms = timed(lambda: bm.decompress(s, out=out))
+        d = bm.decompress(s, out=out).cpu().numpy()
+        e_roi, e_bg = region_errors(d, un, mask, B)
+        t_bg = tol * maxabs if r is not None else 1e-5 * maxabs
+        res[name] = {"cr": nbytes / s.numel(), "compress_gbs": nbytes / c_ms / 1e6, "decompress_gbs": nbytes / d_ms / 1e6,
+                     "max_err_roi": e_roi, "tol_roi": 1e-5 * maxabs, "max_err_background": e_bg, "tol_background": t_bg,
+                     "bound_ok": e_roi <= 1e-5 * maxabs and e_bg <= t_bg}
+    line = {"metric": "ROI error control: CR with ROI vs uniform 1e-5, L-inf per region (385x385x257 FP64)",
+            "workload": "roi385", "value": res["roi"]["cr"] / res["uniform_1e-5"]["cr"], "unit": "x CR",
+            "higher_is_better": True, "roi_blocks": int(mask.sum()), "blocks": int(mask.size),
+            "steps": args.steps, "warmup": args.warmup, "params": params, "dtype": "f64", "data": "synthetic",
+            "streams": res}
+    print(json.dumps(line))
+
+
 def run_model(args):
     """Fit the performance model (Eq. 1 for the In-cache Block stage) on this
     GPU for both dtypes, report the knee (90 % of the saturated throughput)
@@ -425,7 +495,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--edge", type=int, default=513, help="field edge (513 = the workload; smaller for profiling)")
     ap.add_argument("--quick", action="store_true", help="compress steps only (profiling runs)")
-    ap.add_argument("--workload", default="grf513", choices=["grf513", "batch64", "diff257", "model"])
+    ap.add_argument("--workload", default="grf513", choices=["grf513", "batch64", "diff257", "model", "roi385"])
     args = ap.parse_args()
     if args.workload == "batch64" and args.impl == "gpu":
         return run_batch64(args)
@@ -433,6 +503,8 @@ def main():
         return run_diff257(args)
     if args.workload == "model" and args.impl == "gpu":
         return run_model(args)
+    if args.workload == "roi385" and args.impl == "gpu":
+        return run_roi385(args)
     global SHAPE
     SHAPE = (args.edge,) * 3
     if args.impl == "reference":
