@@ -129,6 +129,18 @@ def max_over_ranks(x, dev):
     return float(x)
 
 
+def pipeline_roofline(field_bytes, n_symbols, stream_bytes, g_bytes, ms_per_call, peak):
+    """Planned HBM traffic of one compress call over the whole pipeline, its
+    rate and its fraction of the peak: the field read twice (max|u| and the
+    block kernel), the 16-bit symbols written once and read twice (histogram,
+    encoder), the block-coarse values G written and read once, the stream
+    written once."""
+    alg = 2 * field_bytes + 3 * 2 * n_symbols + 2 * g_bytes + stream_bytes
+    achieved = alg / (ms_per_call * 1e-3) / 1e9
+    return {"alg_bytes_per_call": alg, "ms_per_call": ms_per_call, "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak}
+
+
 def whole_job_gbs(ws, bytes_per_rank, ms_max):
     """Weak-scaling aggregate: every rank's bytes over the slowest rank's time."""
     return ws * bytes_per_rank / (ms_max * 1e-3) / 1e9
@@ -707,6 +719,12 @@ def main():
     achieved = alg_bytes / (k_ms * 1e-3) / 1e9
     traffic = _profiled_traffic()
     stage_avg = {k: statistics.mean(v) for k, v in stage_ms.items()}
+    try:  # whole-pipeline planned traffic (mean stream size over the tolerances)
+        pipe = pipeline_roofline(nbytes, bm.coeff_count(SHAPE, **PARAMS),
+                                 statistics.mean(nbytes / checks[t]["cr"] for t in TOLS), 4 * g_vals,
+                                 comp_ms / len(TOLS), peak)
+    except Exception as e:  # a reporting extra: never lose the bench line over it
+        pipe = {"error": str(e)}
 
     if rank == 0:
         line = {
@@ -723,6 +741,7 @@ def main():
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
                          "ms_per_launch": k_ms},
+            "pipeline_roofline": pipe,
             "stage_ms": stage_avg,
             "e2e": e2e,
             "gpu_launches": launches,
