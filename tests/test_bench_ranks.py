@@ -72,3 +72,21 @@ def test_reference_arm_under_torchrun_prints_once():
     line = json.loads(lines[0])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_profiled_traffic_follows_the_kernel_sources(tmp_path, monkeypatch):
+    """The DRAM traffic recorded under profiles/ is reported only while the
+    block-kernel sources still hash to the digest recorded with it."""
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    digest = bench.kernel_source_digest()
+    (prof / "block_fwd_grf513.md").write_text(
+        "- traffic_bytes_per_launch: 123456\n- kernel_source_sha256: `%s`\n" % digest)
+    src = tmp_path / "paper_2609_00205_gb300" / "csrc"
+    src.mkdir(parents=True)
+    for rel in bench.BLOCK_KERNEL_SOURCES:
+        (tmp_path / rel).write_bytes(open(os.path.join(ROOT, rel), "rb").read())
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._profiled_traffic() == 123456.0
+    (tmp_path / bench.BLOCK_KERNEL_SOURCES[0]).write_text("// changed\n")
+    assert bench._profiled_traffic() is None
