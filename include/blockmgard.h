@@ -218,19 +218,25 @@ bm_status bm_huffman_encode(const uint16_t* d_symbols, uint64_t n, int dict_size
 
 /* Allocation-free variant of bm_huffman_encode (this entry point has no
  * counterpart in the paper).  Same arguments, same output bytes, but it calls
- * no cudaMalloc/cudaFree and no allocating library routine, for callers that
- * cannot allocate device memory: code running while a stream is being
- * captured into a CUDA graph, or a process whose device memory is entirely
- * owned by another allocator.  Its scratch is one static device array of
- * 1 MiB per GPU that loads this library, held until the process exits; it
- * limits a call to at most 16384 chunks (n <= 16384 * chunk_symbols), larger
- * requests return BM_ERR_ARG.  The first call on a device looks up the
- * array's device address (with that device current); make that first call
- * before any stream capture.  Every call shares the array and it keeps the
+ * no cudaMalloc/cudaFree and no allocating library routine.  It is meant for
+ * callers that cannot allocate device memory: a process whose device memory
+ * is entirely reserved by another allocator (a framework's caching pool that
+ * took the whole GPU up front), or a latency-critical loop that cannot accept
+ * the device-wide synchronisation a cudaMalloc or cudaFree may imply.
+ * Its scratch is one static device array of 1 MiB per GPU that loads this
+ * library, held until the process exits; it limits a call to at most 16384
+ * chunks (n <= 16384 * chunk_symbols), larger requests return BM_ERR_ARG.
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it for the life of the process; the cached
+ * address does not survive cudaDeviceReset, so do not call this entry point
+ * after resetting a device.  Every call shares the array and it keeps the
  * last call's contents (the call clears what must start at zero), so calls
  * whose GPU work overlaps in time (different streams, different host
- * threads) race and must be serialised by the caller.  Synchronises the
- * stream. */
+ * threads) race and must be serialised by the caller.
+ * The call ends by copying its status to the host and synchronising the
+ * stream, so it must not be issued on a stream that is being captured into a
+ * CUDA graph: on a capturing stream it returns BM_ERR_ARG before enqueuing
+ * anything. */
 bm_status bm_huffman_encode_noalloc(const uint16_t* d_symbols, uint64_t n, int dict_size, int chunk_symbols,
                                     void* d_out, size_t out_capacity, uint64_t sizes_out[5], void* stream);
 

@@ -1839,13 +1839,13 @@ bm_status bm_compress_batch(int n, const bm_batch_item* items, size_t* out_bytes
       for (int l = 0; l < q.K; ++l) m = m / 2 + 1;
       int64_t S[3] = {items[i].shape[0], items[i].shape[1], items[i].shape[2]};
       for (int r = 0; r < q.R; ++r) {
-        int64_t n = 1;
+        int64_t nb_round = 1;
         for (int d = 0; d < 3; ++d) {
           const int64_t b = (S[d] + q.B - 1) / q.B;
-          n *= b;
+          nb_round *= b;
           S[d] = b * m;
         }
-        nb += n;
+        nb += nb_round;
       }
     }
     slot_off[(size_t)i] = hb;
@@ -2402,6 +2402,12 @@ extern "C" bm_status bm_huffman_encode_noalloc(const uint16_t* d_symbols, uint64
   const unsigned long long off_cb = off_sp + pad8(2ull * (kSplits - 1) * nch);
   if (off_cb > out_capacity) return fail(BM_ERR_CAPACITY, "capacity below the chunk table");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // the call ends with a device-to-host copy and a stream synchronisation,
+  // neither of which a capturing stream allows
+  cudaStreamCaptureStatus cap_st = cudaStreamCaptureStatusNone;
+  BM_CUDA(cudaStreamIsCapturing(s, &cap_st));
+  if (cap_st != cudaStreamCaptureStatusNone)
+    return fail(BM_ERR_ARG, "the stream is being captured: this call synchronises and cannot be captured");
   void* base = nullptr;
   if (bm_status st = noalloc_scratch(&base)) return st;
   Carver cv;
