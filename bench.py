@@ -130,15 +130,54 @@ def max_over_ranks(x, dev):
 
 
 def pipeline_roofline(field_bytes, n_symbols, stream_bytes, g_bytes, ms_per_call, peak):
-    """Planned HBM traffic of one compress call over the whole pipeline, its
-    rate and its fraction of the peak: the field read twice (max|u| and the
-    block kernel), the 16-bit symbols written once and read twice (histogram,
-    encoder), the block-coarse values G written and read once, the stream
-    written once."""
-    alg = 2 * field_bytes + 3 * 2 * n_symbols + 2 * g_bytes + stream_bytes
-    achieved = alg / (ms_per_call * 1e-3) / 1e9
-    return {"alg_bytes_per_call": alg, "ms_per_call": ms_per_call, "achieved": achieved, "peak": peak,
-            "unit": "GB/s", "frac": achieved / peak}
+    """Whole compress call against the HBM peak.  Algorithmic bytes, as the
+    method defines them per input element: the field read once (s) and the
+    stream written once (s/CR).  Beside them the planned traffic of this
+    pipeline: the field read twice (max|u| and the block kernel), the 16-bit
+    symbols written once and read twice (histogram, encoder), the
+    block-coarse values G written and read once, the stream written once."""
+    alg = field_bytes + stream_bytes
+    planned = 2 * field_bytes + 3 * 2 * n_symbols + 2 * g_bytes + stream_bytes
+    sec = ms_per_call * 1e-3
+    return {"alg_bytes_per_call": alg, "ms_per_call": ms_per_call, "achieved": alg / sec / 1e9, "peak": peak,
+            "unit": "GB/s", "frac": alg / sec / 1e9 / peak, "planned_bytes_per_call": planned,
+            "planned_frac": planned / sec / 1e9 / peak}
+
+
+def block_flops(B, K):
+    """Floating-point operations of the In-cache Block decomposition of one
+    block (interpolation, coefficients, the three restriction passes with the
+    five-point band and both Thomas recurrences, the coarse correction and
+    the quantiser's multiply-add), counted per level of N = B, (B+1)/2, ...
+    nodes with C = (N+1)/2 coarse nodes:
+      phase A, N^2 lines: 4C (coarse average) + N (differences) + 2(N-C)
+               (odd-node interpolation) + 15C (band 10C, Thomas 5C)
+      phase B, N C lines: 15C;  phase C, C^2 lines: 15C + C (correction)
+      quantiser: 2 per coefficient (N^3 - C^3)."""
+    n, total = B, 0
+    for _ in range(K):
+        c = (n + 1) // 2
+        total += n * n * (4 * c + n + 2 * (n - c) + 15 * c) + n * c * 15 * c + c * c * 16 * c + 2 * (n ** 3 - c ** 3)
+        n = c
+    return total
+
+
+def fp64_peak_tflops(dev):
+    """Measured FP64 rate of this GPU: a cuBLAS DGEMM (4096^3, best of 3)."""
+    import torch
+
+    a = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    b = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    torch.matmul(a, b)
+    best = float("inf")
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        best = min(best, e0.elapsed_time(e1))
+    return 2.0 * 4096 ** 3 / (best * 1e-3) / 1e12
 
 
 def whole_job_gbs(ws, bytes_per_rank, ms_max):
@@ -222,18 +261,162 @@ def _profiled_traffic():
         return None
 
 
-def cpu_baseline(u_np, edge):
+def _cpu_model():
+    """Host CPU model name (lscpu, else /proc/cpuinfo), for the baseline record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part")):
+                    return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def _oracle_worker(sub, barrier, queue):
+    """One host core: the oracle on its own sample at every tolerance (the
+    workers start together at a barrier; each reports its own wall time)."""
     import oracle
 
-    sub = u_np[:edge, :edge, :edge].copy()
     oracle.build()
+    barrier.wait()
     t0 = time.perf_counter()
     for tol in TOLS:
         oracle.compress(sub, tol, rel=True, B=PARAMS["block"], K=PARAMS["levels"], M=PARAMS["global_levels"])
+    queue.put(time.perf_counter() - t0)
+
+
+def _oracle_all_cores(u_np, edge, procs):
+    """The oracle as it stands (single-threaded code) on every host core at
+    once: `procs` processes, each compressing its own edge^3 sample of the
+    field at the four tolerances; throughput = all bytes / the slowest."""
+    import multiprocessing as mp
+
+    import numpy as np
+
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(procs)
+    queue = ctx.Queue()
+    n = u_np.shape[0]
+    offs = [((i * 97) % max(1, n - edge + 1), (i * 61) % max(1, n - edge + 1)) for i in range(procs)]
+    ps = [ctx.Process(target=_oracle_worker, args=(np.ascontiguousarray(u_np[a:a + edge, b:b + edge, :edge]),
+                                                     barrier, queue)) for a, b in offs]
+    for p in ps:
+        p.start()
+    times = [queue.get(timeout=600) for _ in ps]
+    for p in ps:
+        p.join(timeout=60)
+    return procs * edge ** 3 * u_np.itemsize * len(TOLS) / max(times) / 1e9, max(times)
+
+
+def _profiled_pipeline():
+    """Measured DRAM bytes of every kernel of one compress call (ncu, summary
+    under profiles/) over their summed duration, as a fraction of the peak;
+    None when absent."""
+    prof = os.path.join(ROOT, "profiles", "pipeline_dram_grf385.md")
+    if not os.path.exists(prof):
+        return None
+    vals = {}
+    with open(prof) as f:
+        for line in f:
+            if ":" in line and line.lstrip("- ").split(":")[0].strip() in ("pipeline_dram_bytes", "pipeline_kernel_ms",
+                                                                          "pipeline_dram_frac", "kernel_source_sha256"):
+                k, v = line.lstrip("- ").split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+    try:
+        return {"dram_bytes": float(vals["pipeline_dram_bytes"]), "kernel_ms": float(vals["pipeline_kernel_ms"]),
+                "frac": float(vals["pipeline_dram_frac"]), "source": "profiles/pipeline_dram_grf385.md",
+                "current": vals.get("kernel_source_sha256") == pipeline_source_digest()}
+    except (KeyError, ValueError):
+        return None
+
+
+def pipeline_source_digest():
+    """sha256 over every CUDA source of the library (staleness check of the
+    whole-pipeline DRAM record)."""
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2609_00205_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()
+
+
+def cpu_baseline(u_np, edge, dev):
+    """The CPU oracle timed on the host: one thread on an edge^3 corner, then
+    every host core at once (one process per core, each on its own edge^3
+    sample).  The one-thread run also gives the oracle's codes of the corner,
+    against which the GPU's codes of the same corner are compared: flips
+    within and outside the 1e-6 relative window of a bin edge, per tolerance."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2609_00205_gb300 as bm
+
+    sub = np.ascontiguousarray(u_np[:edge, :edge, :edge])
+    B, K, M = PARAMS["block"], PARAMS["levels"], PARAMS["global_levels"]
+    oracle.build()
+    t0 = time.perf_counter()
+    res = {}
+    for tol in TOLS:
+        res[tol] = oracle.compress(sub, tol, rel=True, B=B, K=K, M=M, want_codes=True)
     dt = time.perf_counter() - t0
-    return {"value": sub.nbytes * len(TOLS) / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": "%dx%dx%d corner of the same field, compressed at the %d tolerances (%.1f s)"
-                      % (edge, edge, edge, len(TOLS), dt)}
+    one = sub.nbytes * len(TOLS) / dt / 1e9
+    # flips of the GPU's codes on the same corner
+    flips = {}
+    coef = oracle.decompose(sub.astype(np.float64), B, K, M)
+    t = torch.from_numpy(sub).to(dev)
+    for tol in TOLS:
+        so, co = res[tol]
+        sg = bm.compress(t, tol, mode="rel", **PARAMS)
+        if oracle.stream_header(so)["raw"] or oracle.stream_header(sg.cpu().numpy())["raw"]:
+            flips[str(tol)] = {"raw": True}
+            continue
+        cg = bm.stream_codes(sg).cpu().numpy().astype(np.int64)
+        hq = oracle.stream_header(so)
+        q = np.asarray(so[hq["off_qtab"]:hq["off_qtab"] + 8 * (K + M + 1)]).view(np.float64)
+        p = oracle.plan(sub.shape, B, K, M)
+        counts, n = [], B
+        for _ in range(K):
+            c = n // 2 + 1
+            counts.append(n ** 3 - c ** 3)
+            n = c
+        qc = [np.tile(np.concatenate([np.full(c, q[l]) for l, c in enumerate(counts)]), p["nblocks"])]
+        for l, c in enumerate(p["global_counts"]):
+            qc.append(np.full(c, q[K + l]))
+        qc.append(np.full(p["coarsest"], q[K + M]))
+        qc = np.concatenate(qc)
+        d = np.flatnonzero(cg != co)
+        lo = np.minimum(cg[d], co[d])
+        dist = np.abs(coef[d] - (lo + 0.5) * qc[d])
+        win = (np.abs(cg[d] - co[d]) == 1) & (dist <= 1e-6 * np.maximum(np.abs(coef[d]), qc[d]))
+        flips[str(tol)] = {"flips": int(d.size), "within_1e-6": int(win.sum()), "outside_1e-6": int((~win).sum()),
+                           "codes": int(cg.size)}
+    procs = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    try:
+        allc, allc_s = _oracle_all_cores(u_np, edge, procs)
+    except Exception as e:  # a reporting extra: keep the one-thread figure
+        allc, allc_s, procs = None, None, 1
+        print("all-core oracle leg failed: %s" % e, file=sys.stderr)
+    cpu = _cpu_model()
+    out = {"value": allc if allc else one, "unit": "GB/s", "cores": procs if allc else 1, "kind": "oracle",
+           "cpu_model": cpu,
+           "sample": ("%d processes (one per host core), each the oracle on its own %dx%dx%d sample of the same "
+                      "field at the %d tolerances (%.1f s); one thread on the %dx%dx%d corner: %.4f GB/s (%.1f s)"
+                      % (procs, edge, edge, edge, len(TOLS), allc_s or 0.0, edge, edge, edge, one, dt)),
+           "single_thread_value": one,
+           "flips_on_sample": flips}
+    return out
 
 
 def _batch64_fields(dev):
@@ -412,20 +595,21 @@ def region_errors(d, u, block_mask, block):
     return (float(e[m].max()) if m.any() else 0.0), (float(e[~m].max()) if (~m).any() else 0.0)
 
 
-def run_roi385(args):
+def roi385_measure(dev, steps, warmup):
     """ROI error control on the FP64 385x385x257 field (smooth k^-3 background,
     12 tanh fronts, 6 vortex tubes): ROI = blocks whose max |grad u| exceeds
     the 95th percentile of |grad u|, ROI tolerance 1e-5 and background 1e-2
-    (relative to max|u|), B = 9, K = 2, M = 2.  Reports the compression ratio
-    against the same field at a uniform 1e-5, the L-inf error of each region
-    against its tolerance, and compress / decompress GB/s of both streams."""
+    (relative to max|u|), B = 9, K = 2, M = 2.  The compression ratio against
+    the same field at a uniform 1e-5, the L-inf error of each region against
+    its tolerance, compress / decompress GB/s of both streams (CUDA events over
+    `steps` calls each), and the FP64 block kernel against the measured FP64
+    rate (its arithmetic, not HBM, bounds it on this GPU)."""
     import numpy as np
     import torch
 
     import fields
     import paper_2609_00205_gb300 as bm
 
-    dev = torch.device("cuda", 0)
     shape, B = (385, 385, 257), 9
     params = dict(block=B, levels=2, global_levels=2)
     u = fields.roi_field(shape, seed=3, device=dev).contiguous()
@@ -436,35 +620,65 @@ def run_roi385(args):
     nbytes = u.numel() * u.element_size()
     out = torch.empty_like(u)
     stream = torch.cuda.current_stream(dev)
+    cap = bm.compress_bound(shape, torch.float64)
+    obuf = torch.empty(cap, dtype=torch.uint8, device=dev)
 
     def timed(fn):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             fn()
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             fn()
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        return e0.elapsed_time(e1) / args.steps
+        return e0.elapsed_time(e1) / steps
 
     res = {}
     for name, tol, r in (("roi", 1e-2, roi), ("uniform_1e-5", 1e-5, None)):
-        s = bm.compress(u, tol, mode="rel", roi=r, **params)
-        c_ms = timed(lambda: bm.compress(u, tol, mode="rel", roi=r, **params))
+        s = bm.compress(u, tol, mode="rel", roi=r, **params).clone()
+        c_ms = timed(lambda: bm.compress(u, tol, mode="rel", roi=r, out=obuf, **params))
         d_ms = timed(lambda: bm.decompress(s, out=out))
+        bm.set_timing(True)
+        bm.compress(u, tol, mode="rel", roi=r, out=obuf, **params)
+        cst = dict(bm.stage_times())
+        bm.decompress(s, out=out)
+        dst = dict(bm.stage_times())
+        bm.set_timing(False)
         d = bm.decompress(s, out=out).cpu().numpy()
         e_roi, e_bg = region_errors(d, un, mask, B)
         t_bg = tol * maxabs if r is not None else 1e-5 * maxabs
-        res[name] = {"cr": nbytes / s.numel(), "compress_gbs": nbytes / c_ms / 1e6, "decompress_gbs": nbytes / d_ms / 1e6,
-                     "max_err_roi": e_roi, "tol_roi": 1e-5 * maxabs, "max_err_background": e_bg, "tol_background": t_bg,
-                     "bound_ok": e_roi <= 1e-5 * maxabs and e_bg <= t_bg}
+        res[name] = {"cr": nbytes / s.numel(), "stream_bytes": int(s.numel()), "compress_ms": c_ms,
+                     "decompress_ms": d_ms, "compress_gbs": nbytes / c_ms / 1e6, "decompress_gbs": nbytes / d_ms / 1e6,
+                     "max_err_roi": e_roi, "tol_roi": 1e-5 * maxabs, "max_err_background": e_bg,
+                     "tol_background": t_bg, "bound_ok": e_roi <= 1e-5 * maxabs and e_bg <= t_bg,
+                     "compress_stage_ms": cst, "decompress_stage_ms": dst}
+    nblocks = int(mask.size)
+    flops = nblocks * block_flops(B, params["levels"])
+    k_ms = res["roi"]["compress_stage_ms"].get("incache_decompose", float("nan"))
+    fp64 = fp64_peak_tflops(dev)
+    return {"workload": "roi385_f64_b9k2m2", "shape": list(shape), "dtype": "f64", "params": params,
+            "cr_ratio_roi_vs_uniform": res["roi"]["cr"] / res["uniform_1e-5"]["cr"], "roi_blocks": int(mask.sum()),
+            "blocks": nblocks, "steps": steps, "warmup": warmup, "streams": res,
+            "roofline": {"bound": "fp64_alu", "kernel": "block_fwd_kernel<double,9,2,0> (incache_decompose)",
+                         "flops_per_launch": flops, "ms_per_launch": k_ms,
+                         "achieved": flops / (k_ms * 1e-3) / 1e12, "peak": fp64, "unit": "TFLOP/s",
+                         "frac": flops / (k_ms * 1e-3) / 1e12 / fp64,
+                         "peak_kind": "measured (cuBLAS DGEMM 4096^3 on this GPU); nominal 1.25 TFLOP/s",
+                         "hbm_frac": nbytes / (k_ms * 1e-3) / 1e9 / _peaks()[0]}}
+
+
+def run_roi385(args):
+    """The ROI workload alone (one JSON line)."""
+    import torch
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    r = roi385_measure(dev, max(20, args.steps), args.warmup)
     line = {"metric": "ROI error control: CR with ROI vs uniform 1e-5, L-inf per region (385x385x257 FP64)",
-            "workload": "roi385", "value": res["roi"]["cr"] / res["uniform_1e-5"]["cr"], "unit": "x CR",
-            "higher_is_better": True, "roi_blocks": int(mask.sum()), "blocks": int(mask.size),
-            "steps": args.steps, "warmup": args.warmup, "params": params, "dtype": "f64", "data": "synthetic",
-            "streams": res}
+            "workload": "roi385", "value": r["cr_ratio_roi_vs_uniform"], "unit": "x CR", "higher_is_better": True,
+            "data": "synthetic", **r}
     print(json.dumps(line))
 
 
@@ -505,6 +719,7 @@ def main():
     ap.add_argument("--ref-edge", type=int, default=102)
     ap.add_argument("--cpu-edge", type=int, default=221)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-roi", action="store_true", help="skip the FP64 ROI workload in the main line")
     ap.add_argument("--edge", type=int, default=513, help="field edge (513 = the workload; smaller for profiling)")
     ap.add_argument("--quick", action="store_true", help="compress steps only (profiling runs)")
     ap.add_argument("--workload", default="grf513", choices=["grf513", "batch64", "diff257", "model", "roi385"])
@@ -708,23 +923,53 @@ def main():
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": d2h,
            "pipelining": "step i+1's H2D and step i's D2H overlap the compressions (two buffer sets)"}
 
-    # roofline of the dominant kernel (fused In-cache Block decompose + quantise)
+    # roofline of the dominant kernel (fused In-cache Block decompose +
+    # quantise): algorithmic bytes of the step it performs, per input element
+    # the field read once, plus the block-coarse values G it hands to the
+    # global levels; the 16-bit symbols it writes for the entropy stage are
+    # this pipeline's planned traffic and reported beside it
     peak, peak_kind = _peaks()
     k_ms = statistics.mean(stage_ms.get("incache_decompose", [float("nan")]))
     nb = [-(-n // PARAMS["block"]) for n in SHAPE]
     nblocks = nb[0] * nb[1] * nb[2]
     per_block = 17 ** 3 - 9 ** 3 + 9 ** 3 - 5 ** 3   # coefficients of the two in-cache levels
     g_vals = nblocks * 5 ** 3                          # block-coarse values handed to the global levels
-    alg_bytes = nbytes + 2 * nblocks * per_block + 4 * g_vals
+    alg_bytes = nbytes + 4 * g_vals
+    planned_bytes = nbytes + 2 * nblocks * per_block + 4 * g_vals
     achieved = alg_bytes / (k_ms * 1e-3) / 1e9
     traffic = _profiled_traffic()
     stage_avg = {k: statistics.mean(v) for k, v in stage_ms.items()}
-    try:  # whole-pipeline planned traffic (mean stream size over the tolerances)
-        pipe = pipeline_roofline(nbytes, bm.coeff_count(SHAPE, **PARAMS),
-                                 statistics.mean(nbytes / checks[t]["cr"] for t in TOLS), 4 * g_vals,
+    mean_stream = statistics.mean(nbytes / checks[t]["cr"] for t in TOLS)
+    try:  # whole compress call: field read once + stream written once
+        pipe = pipeline_roofline(nbytes, bm.coeff_count(SHAPE, **PARAMS), mean_stream, 4 * g_vals,
                                  comp_ms / len(TOLS), peak)
+        pipe["dram_measured"] = _profiled_pipeline()
     except Exception as e:  # a reporting extra: never lose the bench line over it
         pipe = {"error": str(e)}
+    # decompress: the inverse block kernel (reads G, writes the field), the
+    # decoder (reads the stream) and the whole call (stream + field)
+    dstage_avg = {k: statistics.mean(v) for k, v in dstage.items()}
+    inv_ms = dstage_avg.get("incache_recompose", float("nan"))
+    dec_ms = dstage_avg.get("huffman_decode", float("nan"))
+    dcall_ms = decomp_ms / len(TOLS)
+    dec_roof = {
+        "bound": "hbm", "peak": peak, "unit": "GB/s", "peak_kind": peak_kind,
+        "block_inv_kernel": {"alg_bytes_per_launch": nbytes + 4 * g_vals, "ms_per_launch": inv_ms,
+                             "achieved": (nbytes + 4 * g_vals) / (inv_ms * 1e-3) / 1e9,
+                             "frac": (nbytes + 4 * g_vals) / (inv_ms * 1e-3) / 1e9 / peak},
+        "decode_kernel": {"alg_bytes_per_launch": mean_stream, "ms_per_launch": dec_ms,
+                          "achieved": mean_stream / (dec_ms * 1e-3) / 1e9,
+                          "frac": mean_stream / (dec_ms * 1e-3) / 1e9 / peak},
+        "call": {"alg_bytes_per_call": nbytes + mean_stream, "ms_per_call": dcall_ms,
+                 "achieved": (nbytes + mean_stream) / (dcall_ms * 1e-3) / 1e9,
+                 "frac": (nbytes + mean_stream) / (dcall_ms * 1e-3) / 1e9 / peak},
+    }
+    roi = None
+    if not args.no_roi:
+        try:
+            roi = roi385_measure(dev, max(20, args.steps), args.warmup)
+        except Exception as e:  # a reporting extra: never lose the bench line over it
+            roi = {"error": str(e)}
 
     if rank == 0:
         line = {
@@ -740,15 +985,19 @@ def main():
             "roofline": {"bound": "hbm", "kernel": "block_fwd_kernel<float,17,2,0> (incache_decompose)",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
-                         "ms_per_launch": k_ms},
+                         "planned_bytes_per_launch": planned_bytes,
+                         "planned_frac": planned_bytes / (k_ms * 1e-3) / 1e9 / peak, "ms_per_launch": k_ms},
             "pipeline_roofline": pipe,
+            "input_rate_frac": value / ws / peak,
+            "decompress_roofline": dec_roof,
+            "roi385": roi,
             "stage_ms": stage_avg,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,
         }
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(u.cpu().numpy(), args.cpu_edge)
+            line["cpu_baseline"] = cpu_baseline(u.cpu().numpy(), args.cpu_edge, dev)
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()

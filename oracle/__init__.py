@@ -55,6 +55,7 @@ def lib():
                                 ctypes.c_int, P(d), P(d)]
         L.or_quantize.argtypes = [d, d, ctypes.c_int, P(ctypes.c_int)]
         L.or_quantize.restype = i64
+        L.or_quantize_array.argtypes = [P(d), P(d), i64, ctypes.c_int, P(i64), P(u8)]
         L.or_huffman_lengths.argtypes = [P(ctypes.c_uint64), ctypes.c_int, P(u8)]
         L.or_canonical_codes.argtypes = [P(u8), ctypes.c_int, P(ctypes.c_uint32)]
         L.or_huffman_encode.argtypes = [P(ctypes.c_uint16), ctypes.c_uint64, ctypes.c_int, ctypes.c_int, P(u8),
@@ -227,6 +228,18 @@ def quantize(c, q, f64):
     ov = ctypes.c_int(0)
     code = lib().or_quantize(float(c), float(q), int(bool(f64)), ctypes.byref(ov))
     return int(code), bool(ov.value)
+
+
+def quantize_array(c, q, f64):
+    """The quantiser over arrays of coefficients and bin widths: (codes,
+    overflow flags)."""
+    c = np.ascontiguousarray(np.asarray(c, dtype=np.float64))
+    q = np.ascontiguousarray(np.broadcast_to(np.asarray(q, dtype=np.float64), c.shape))
+    codes = np.zeros(c.size, dtype=np.int64)
+    ovf = np.zeros(c.size, dtype=np.uint8)
+    _check(lib().or_quantize_array(_ptr(c, ctypes.c_double), _ptr(q, ctypes.c_double), c.size, int(bool(f64)),
+                                   _ptr(codes, ctypes.c_int64), _ptr(ovf, ctypes.c_uint8)))
+    return codes.reshape(c.shape), ovf.astype(bool).reshape(c.shape)
 
 
 def huffman_lengths(freq):

@@ -1217,6 +1217,17 @@ int64_t or_quantize(double c, double q, int f64, int* overflow) {
   return r.code;
 }
 
+// The quantiser applied element by element (codes of given coefficients and
+// bin widths; overflowing entries are reported through their own flag).
+int or_quantize_array(const double* c, const double* q, int64_t n, int f64, int64_t* code_out, uint8_t* ovf_out) {
+  for (int64_t i = 0; i < n; ++i) {
+    QResult r = quantize(c[i], q[i], f64 != 0);
+    code_out[i] = r.code;
+    ovf_out[i] = r.overflow ? 1 : 0;
+  }
+  return 0;
+}
+
 int or_huffman_lengths(const uint64_t* freq, int nsym, uint8_t* len_out) {
   std::vector<uint64_t> f(freq, freq + nsym);
   std::vector<uint8_t> l = huffman_lengths(f);

@@ -7,6 +7,8 @@ import torch
 
 import fields
 
+from _util import check_stream_parity
+
 pytestmark = pytest.mark.gpu
 
 DEV = "cuda:0"
@@ -59,6 +61,32 @@ def test_batch_matches_single_calls(bm):
         else:
             # every node keeps the loosest bound; blocks with a tighter entry are checked in the parity tests
             assert float((d - u).abs().max()) <= tau
+
+
+def test_batch_matches_oracle(bm):
+    """Every item of a batch against the oracle's stream of the same field:
+    uneven shapes, both dtypes, their own tolerances, ROI maps on some items
+    (each ROI block checked against its own tau_i), codes with explained
+    flips only and the hard gate."""
+    import fields as F
+
+    specs = [((37, 52, 29), np.float32, 3e-3, True), ((61, 40, 45), np.float32, 1e-4, False),
+             ((33, 35, 31), np.float64, 1e-5, True), ((20, 70, 24), np.float64, 2e-2, False),
+             ((90, 21, 40), np.float32, 1e-2, True)]
+    B, K, M = 17, 2, 2
+    us, ts, rois = [], [], []
+    for i, (shape, dt, tol, with_roi) in enumerate(specs):
+        u = np.ascontiguousarray(F.power_law_grf(shape, exponent=-2.5 - 0.3 * i, seed=300 + i).numpy().astype(dt))
+        roi = None
+        if with_roi:
+            roi = np.where(F.gradient_roi(u, B), tol / 10, tol).ravel()
+        us.append(u)
+        ts.append(tol)
+        rois.append(roi)
+    out = bm.compress_batch([torch.from_numpy(u).to(DEV) for u in us], ts, rois=rois, block=B, levels=K,
+                            global_levels=M)
+    for i, (u, tol, roi, s) in enumerate(zip(us, ts, rois, out)):
+        check_stream_parity(bm, u, s.cpu().numpy(), tol, "rel", B, K, M, roi=roi, label="batch_item%d" % i, dev=DEV)
 
 
 def test_batch_reports_a_bad_item_alone(bm):

@@ -10,7 +10,7 @@ import torch
 import fields
 import oracle
 
-from _util import classify_flips, per_block_tau
+from _util import flip_counts, hard_gate, per_block_tau, record
 
 pytestmark = pytest.mark.gpu
 
@@ -110,9 +110,15 @@ def test_compress_parity_with_rounds(bm, case, tol):
     np.testing.assert_array_equal(sg[ho["off_tiers"]:ho["off_chunks"]], so[ho["off_tiers"]:ho["off_chunks"]])
     cg = bm.stream_codes(torch.from_numpy(sg).to(DEV)).cpu().numpy()
     coef = oracle.decompose(u.astype(np.float64), B, K, M, R)
-    nflip, nwin, bad = classify_flips(cg, co, coef, _q_per_coeff(so, shape, B, K, M, R), _coef_tol(u))
-    assert bad == 0, (nflip, nwin, bad)
-    if nflip == 0:
+    q = _q_per_coeff(so, shape, B, K, M, R)
+    fc = flip_counts(cg, co, coef, q, _coef_tol(u))
+    cgpu = bm.decompose(torch.from_numpy(u).to(DEV), B, K, M, rounds=R).cpu().numpy()
+    gate = hard_gate(cg, cgpu, q, dt == np.float64)
+    record(test="compress_parity_rounds", label=name, shape=list(shape), dtype=str(u.dtype), B=B, K=K, M=M, R=R,
+           tol=tol, hard_gate_mismatches=gate, **fc)
+    assert gate == 0, gate
+    assert fc["unexplained"] == 0, fc
+    if fc["flips"] == 0:
         np.testing.assert_array_equal(sg, so)
 
 

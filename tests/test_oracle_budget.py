@@ -155,6 +155,30 @@ def test_quantizer_is_round_half_up(f64):
     assert np.all(np.abs(got[near] - want[near]) <= 1)
 
 
+@pytest.mark.parametrize("f64", [False, True])
+def test_quantizer_array_is_round_half_up(f64):
+    """The element-wise quantiser: floor(c/q + 1/2) away from bin edges (the
+    rounding decision in the field's precision may differ by one bin only
+    next to an edge), per-element widths, overflow flags for huge and NaN
+    values."""
+    rng = np.random.default_rng(12)
+    c = rng.normal(0, 3.0, 30000)
+    q = 10.0 ** rng.uniform(-4, -1, c.size)
+    if not f64:
+        c = c.astype(np.float32).astype(np.float64)
+    exact = c / q + 0.5
+    rel = 1e-6 if not f64 else 1e-13
+    near = np.abs(exact - np.rint(exact)) < rel * np.maximum(1, np.abs(exact))
+    big = np.abs(exact) >= 2.0 ** 30
+    codes, ovf = oracle.quantize_array(c, q, f64)
+    ok = ~near & ~big
+    assert np.all(codes[ok] == np.floor(exact[ok]))
+    assert np.all(np.abs(codes[near & ~big] - np.floor(exact[near & ~big])) <= 1)
+    assert np.all(ovf == big)
+    _, ov = oracle.quantize_array(np.array([np.nan, 2.0 ** 40, -(2.0 ** 40), 0.0]), 1.0, f64)
+    assert list(ov) == [True, True, True, False]
+
+
 def test_bound_holds_end_to_end_with_roi():
     """Per-region L-inf: ROI blocks at tau 1e-5, background 1e-2 (relative)."""
     u = fields.roi_field((40, 37, 29), seed=4).numpy()
