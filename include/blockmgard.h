@@ -67,8 +67,8 @@ typedef struct {
                           -1 selects 0)                                                  */
   int chunk_symbols;   /* Huffman chunk length in symbols, multiple of 32, 64..2048
                           (default 2048)                                                 */
-  int dict_radius;     /* quantisation codes with |code| < radius become symbols
-                          code + radius; others are outliers.  16..4096 (default 4096)   */
+  int dict_radius;     /* quantisation codes with |code| < radius become 16-bit symbols
+                          code + radius; others are outliers.  16..32768 (default 32768) */
   int rounds;          /* R, 1..8 (0 = 1): re-blocking rounds of K in-cache levels each;
                           round r+1 re-blocks round r's gathered coarse values and takes
                           the strictest tolerance among the blocks each new block holds
@@ -208,7 +208,7 @@ bm_status bm_stream_codes(const void* d_in, size_t in_bytes, int32_t* d_codes, v
 
 /* Stand-alone Huffman stage (Sec. III-B lossless stage; cuSZ-style chunked
  * coding, "deflate" = concatenation of chunk codes): encodes n uint16 symbols
- * (each < dict_size, dict_size <= 8192; n < 2^31) into the section layout used inside
+ * (each < dict_size, dict_size <= 65536; n < 2^31) into the section layout used inside
  * streams: u32 chunk word counts | u16 split offsets (bit offsets of the
  * eighths 1..7 of every chunk) | codebook runs | u32 code words, each part
  * padded to 8 bytes.  chunk_symbols: multiple of 32 in [64, 2048].  sizes_out[0..4] = codebook bytes, runs, chunks, words,

@@ -285,7 +285,7 @@ def huffman_decode(section, meta, n, dict_size, chunk):
     return out
 
 
-def compress(u, tol, rel=True, roi=None, B=9, K=1, M=2, chunk=2048, radius=4096, f64=None, want_codes=False, R=1):
+def compress(u, tol, rel=True, roi=None, B=9, K=1, M=2, chunk=2048, radius=32768, f64=None, want_codes=False, R=1):
     """Full stream for field u (numpy, float32 or float64).  Returns bytes
     (uint8 array) and, if asked, the integer codes in coefficient order."""
     if f64 is None:

@@ -850,7 +850,7 @@ bool huffman_decode(const std::vector<uint8_t>& len, const uint32_t* chunk_words
 }
 
 struct CompressOpts {
-  int B = 9, K = 1, M = 2, chunk = 2048, radius = 4096, R = 1;
+  int B = 9, K = 1, M = 2, chunk = 2048, radius = 32768, R = 1;
 };
 
 thread_local std::string g_err;

@@ -138,7 +138,7 @@ def _dtype(t):
     raise TypeError("fields must be float32 or float64")
 
 
-def _params(block=17, levels=2, global_levels=2, chunk=2048, radius=4096, rounds=1):
+def _params(block=17, levels=2, global_levels=2, chunk=2048, radius=32768, rounds=1):
     return _Params(int(block), int(levels), int(global_levels) if global_levels != 0 else -1, int(chunk), int(radius),
                    int(rounds))
 
@@ -155,7 +155,7 @@ def compress_bound(shape, dtype=torch.float32) -> int:
 
 
 def compress(field: torch.Tensor, tol: float, mode: str = "rel", roi=None, block=17, levels=2, global_levels=2,
-             chunk=2048, radius=4096, out: torch.Tensor | None = None, stream=None, rounds=1) -> torch.Tensor:
+             chunk=2048, radius=32768, out: torch.Tensor | None = None, stream=None, rounds=1) -> torch.Tensor:
     """Compress a 3-D float32/float64 CUDA tensor; returns the stream as a
     uint8 CUDA tensor (a view of ``out`` when given).  ``roi``: optional
     per-block tolerances (same mode as ``tol``), row-major over the block grid."""
@@ -184,7 +184,7 @@ def compress(field: torch.Tensor, tol: float, mode: str = "rel", roi=None, block
 
 
 def compress_batch(fields, tols, mode: str = "rel", rois=None, block=17, levels=2, global_levels=2, chunk=2048,
-                   radius=4096, outs=None, stream=None, rounds=1):
+                   radius=32768, outs=None, stream=None, rounds=1):
     """Compress several 3-D CUDA fields in one call (pipelines queued on the
     library's stream pool, one synchronisation).  ``tols``: one tolerance per
     field; ``rois``: None or one per-block tolerance map (or None) per field;

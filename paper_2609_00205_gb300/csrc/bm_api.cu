@@ -336,7 +336,7 @@ bm_status check_params(const bm_params* p, Params& o) {
   o.M = (p && p->global_levels) ? p->global_levels : 2;
   if (p && p->global_levels < 0) o.M = 0;
   o.chunk = (p && p->chunk_symbols) ? p->chunk_symbols : 2048;
-  o.radius = (p && p->dict_radius) ? p->dict_radius : 4096;
+  o.radius = (p && p->dict_radius) ? p->dict_radius : kMaxDict / 2;
   o.R = (p && p->rounds) ? p->rounds : 1;
   if (o.R < 1 || o.R > 8) return fail(BM_ERR_ARG, "rounds must be in [1, 8]");
   if (o.B != 9 && o.B != 17) return fail(BM_ERR_UNSUPPORTED, "block_nodes must be 9 or 17 in this build");
@@ -344,7 +344,7 @@ bm_status check_params(const bm_params* p, Params& o) {
   if (o.K < 1 || o.K > kmax) return fail(BM_ERR_ARG, "incache_levels out of range for this block size");
   if (o.M > 16) return fail(BM_ERR_ARG, "global_levels too large");
   if (o.chunk < 64 || o.chunk > 2048 || o.chunk % 32) return fail(BM_ERR_ARG, "chunk_symbols must be a multiple of 32 in [64, 2048]");
-  if (o.radius < 16 || o.radius > kMaxDict / 2) return fail(BM_ERR_ARG, "dict_radius must be in [16, 4096]");
+  if (o.radius < 16 || o.radius > kMaxDict / 2) return fail(BM_ERR_ARG, "dict_radius must be in [16, 32768]");
   return BM_OK;
 }
 
@@ -1167,6 +1167,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   Carver probe;
   carve_all(probe, nullptr);
   probe.take<Scalars>(1); probe.take<unsigned>(dict); probe.take<uint8_t>(dict); probe.take<unsigned>(dict);
+  probe.take<unsigned char>(cb_big_bytes());
   probe.take<double>(L.nq); probe.take<T>(L.nq); probe.take<double>(ntiers); probe.take<uint8_t>(h.nblocks_all);
   probe.take<uint16_t>((size_t)h.n_coeffs); probe.take<int32_t>((size_t)h.n_coeffs);
   probe.take<unsigned char>(256 + 16ull * L.nch);
@@ -1179,6 +1180,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   unsigned* hist = cv.take<unsigned>(dict);
   uint8_t* lens = cv.take<uint8_t>(dict);
   unsigned* codes = cv.take<unsigned>(dict);
+  unsigned char* cb_big = cv.take<unsigned char>(cb_big_bytes());
   double* qd = cv.take<double>(L.nq);
   T* rq = cv.take<T>(L.nq);
   double* dtiers = cv.take<double>(ntiers);
@@ -1283,7 +1285,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   {
     Stage st("huffman_codebook");
     CodebookArgs ca{hist, dict, lens, codes, prefix_fits ? out : nullptr, L.off_codebook, cap, sc, 1, L.nch,
-                    raw_total};
+                    raw_total, cb_big};
     BM_CUDA(set_smem_once(codebook_kernel, (int)sizeof(CbSmem), g_cb_attr));
     codebook_kernel<<<1, kCbThreads, sizeof(CbSmem), s>>>(ca);
     BM_LAUNCHED();
@@ -1298,8 +1300,9 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     ea.chunk_words = reinterpret_cast<unsigned*>(out + L.off_chunks);
     ea.splits = reinterpret_cast<uint16_t*>(out + L.off_splits);
     ea.out = out; ea.capacity = cap; ea.sc = sc;
-    encode_fused_kernel<8, false><<<grid_for((int64_t)L.nch * 32, 256, 4), 256, 0, s>>>(ea);
-    BM_LAUNCHED();
+    encode_fused_kernel<8, false, false><<<grid_for((int64_t)L.nch * 32, 256, 4), 256, 0, s>>>(ea);
+    encode_fused_kernel<8, false, true><<<grid_for((int64_t)L.nch * 32, 256, 4), 256, 0, s>>>(ea);
+    g_launches.fetch_add(2);
   }
   {
     Stage st("finish");
@@ -2221,7 +2224,7 @@ bm_status bm_huffman_encode(const uint16_t* d_symbols, uint64_t n, int dict_size
                             size_t out_capacity, uint64_t sizes_out[5], void* stream) {
   if (!d_symbols || !d_out || !sizes_out) return fail(BM_ERR_ARG, "NULL pointer argument");
   if (n == 0 || n >= (uint64_t(1) << 31)) return fail(BM_ERR_ARG, "symbol count must be in [1, 2^31)");
-  if (dict_size < 2 || dict_size > kMaxDict) return fail(BM_ERR_ARG, "dict_size must be in [2, 8192]");
+  if (dict_size < 2 || dict_size > kMaxDict) return fail(BM_ERR_ARG, "dict_size must be in [2, 65536]");
   if (chunk_symbols < 64 || chunk_symbols > 2048 || chunk_symbols % 32) return fail(BM_ERR_ARG, "chunk_symbols");
   if (reinterpret_cast<uintptr_t>(d_out) % 8) return fail(BM_ERR_ARG, "output pointer must be 8-byte aligned");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -2234,6 +2237,7 @@ bm_status bm_huffman_encode(const uint16_t* d_symbols, uint64_t n, int dict_size
   Carver probe;
   probe.take<Scalars>(1); probe.take<unsigned>(dict_size); probe.take<uint8_t>(dict_size);
   probe.take<unsigned>(dict_size); probe.take<unsigned>(nch); probe.take<unsigned char>(256 + 16ull * nch);
+  probe.take<unsigned char>(cb_big_bytes());
   Workspace* ws = nullptr;
   if (bm_status st = get_ws(s, probe.off + 4096, 4096, &ws)) return st;
   Carver cv;
@@ -2243,6 +2247,7 @@ bm_status bm_huffman_encode(const uint16_t* d_symbols, uint64_t n, int dict_size
   uint8_t* lens = cv.take<uint8_t>(dict_size);
   unsigned* codes = cv.take<unsigned>(dict_size);
   unsigned char* tickets = cv.take<unsigned char>(256 + 16ull * nch);
+  unsigned char* cb_big = cv.take<unsigned char>(cb_big_bytes());
   uint8_t* out = reinterpret_cast<uint8_t*>(d_out);
   BM_CUDA(cudaMemsetAsync(sc, 0, sizeof(Scalars), s));
   BM_CUDA(cudaMemsetAsync(hist, 0, 4ull * dict_size, s));
@@ -2250,12 +2255,12 @@ bm_status bm_huffman_encode(const uint16_t* d_symbols, uint64_t n, int dict_size
   BM_CUDA(cudaMemsetAsync(tickets, 0, 256 + 16ull * nch, s));
   {
     Stage st("huffman_histogram");
-    hist_kernel<<<grid_for((int64_t)n, 256, 4), 256, 4 * dict_size, s>>>(d_symbols, n, dict_size, hist, sc);
+    hist_kernel<<<grid_for((int64_t)n, 256, 4), 256, 0, s>>>(d_symbols, n, dict_size, hist, sc);
     BM_LAUNCHED();
   }
   {
     Stage st("huffman_codebook");
-    CodebookArgs ca{hist, dict_size, lens, codes, out, off_cb, out_capacity, sc, 0, nch, ~0ull};
+    CodebookArgs ca{hist, dict_size, lens, codes, out, off_cb, out_capacity, sc, 0, nch, ~0ull, cb_big};
     BM_CUDA(set_smem_once(codebook_kernel, (int)sizeof(CbSmem), g_cb_attr));
     codebook_kernel<<<1, kCbThreads, sizeof(CbSmem), s>>>(ca);
     BM_LAUNCHED();
@@ -2269,7 +2274,7 @@ bm_status bm_huffman_encode(const uint16_t* d_symbols, uint64_t n, int dict_size
     ea.chunk_words = reinterpret_cast<unsigned*>(out); ea.out = out;
     ea.splits = reinterpret_cast<uint16_t*>(out + off_sp);
     ea.capacity = out_capacity; ea.sc = sc;
-    encode_fused_kernel<8, true><<<grid_for((int64_t)nch * 32, 256, 4), 256, 0, s>>>(ea);
+    encode_fused_kernel<8, true, true><<<grid_for((int64_t)nch * 32, 256, 4), 256, 0, s>>>(ea);
     encode_finish_kernel<<<1, 32, 0, s>>>(~0ull, out_capacity, sc);
     zero_tail_kernel<<<1, 32, 0, s>>>(out, sc);
     g_launches.fetch_add(3);
@@ -2292,7 +2297,7 @@ bm_status bm_huffman_encode(const uint16_t* d_symbols, uint64_t n, int dict_size
 bm_status bm_huffman_decode(const void* d_section, const uint64_t sizes[5], uint64_t n, int dict_size,
                             int chunk_symbols, uint16_t* d_symbols, void* stream) {
   if (!d_section || !sizes || !d_symbols) return fail(BM_ERR_ARG, "NULL pointer argument");
-  if (dict_size < 2 || dict_size > kMaxDict) return fail(BM_ERR_ARG, "dict_size must be in [2, 8192]");
+  if (dict_size < 2 || dict_size > kMaxDict) return fail(BM_ERR_ARG, "dict_size must be in [2, 65536]");
   if (chunk_symbols < 64 || chunk_symbols > 2048 || chunk_symbols % 32) return fail(BM_ERR_ARG, "chunk_symbols");
   if (reinterpret_cast<uintptr_t>(d_section) % 8) return fail(BM_ERR_ARG, "section pointer must be 8-byte aligned");
   const unsigned long long nch = (n + chunk_symbols - 1) / chunk_symbols;
@@ -2359,6 +2364,7 @@ namespace {
 // the process, shared by every call.
 constexpr size_t kNoAllocBytes = size_t(1) << 20;     // 1 MiB
 constexpr unsigned long long kNoAllocMaxChunks = 16384;
+constexpr int kNoAllocMaxDict = 8192;  // at most this many present symbols: the codebook stays in shared memory
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 std::mutex g_noalloc_mu;
@@ -2392,7 +2398,7 @@ extern "C" bm_status bm_huffman_encode_noalloc(const uint16_t* d_symbols, uint64
                                                void* d_out, size_t out_capacity, uint64_t sizes_out[5], void* stream) {
   if (!d_symbols || !d_out || !sizes_out) return fail(BM_ERR_ARG, "NULL pointer argument");
   if (n == 0 || n >= (uint64_t(1) << 31)) return fail(BM_ERR_ARG, "symbol count must be in [1, 2^31)");
-  if (dict_size < 2 || dict_size > kMaxDict) return fail(BM_ERR_ARG, "dict_size must be in [2, 8192]");
+  if (dict_size < 2 || dict_size > kNoAllocMaxDict) return fail(BM_ERR_ARG, "dict_size must be in [2, 8192]");
   if (chunk_symbols < 64 || chunk_symbols > 2048 || chunk_symbols % 32) return fail(BM_ERR_ARG, "chunk_symbols");
   if (reinterpret_cast<uintptr_t>(d_out) % 8) return fail(BM_ERR_ARG, "output pointer must be 8-byte aligned");
   const unsigned long long nch = (n + chunk_symbols - 1) / chunk_symbols;
@@ -2424,8 +2430,8 @@ extern "C" bm_status bm_huffman_encode_noalloc(const uint16_t* d_symbols, uint64
   BM_CUDA(cudaMemsetAsync(hist, 0, 4ull * dict_size, s));
   BM_CUDA(cudaMemsetAsync(tickets, 0, 256 + 16ull * nch, s));
   BM_CUDA(cudaMemsetAsync(out, 0, off_cb, s));
-  hist_kernel<<<grid_for((int64_t)n, 256, 4), 256, 4 * dict_size, s>>>(d_symbols, n, dict_size, hist, sc);
-  CodebookArgs ca{hist, dict_size, lens, codes, out, off_cb, out_capacity, sc, 0, nch, ~0ull};
+  hist_kernel<<<grid_for((int64_t)n, 256, 4), 256, 0, s>>>(d_symbols, n, dict_size, hist, sc);
+  CodebookArgs ca{hist, dict_size, lens, codes, out, off_cb, out_capacity, sc, 0, nch, ~0ull, nullptr};
   BM_CUDA(set_smem_once(codebook_kernel, (int)sizeof(CbSmem), g_cb_attr));
   codebook_kernel<<<1, kCbThreads, sizeof(CbSmem), s>>>(ca);
   FusedEncodeArgs ea{};
@@ -2435,7 +2441,7 @@ extern "C" bm_status bm_huffman_encode_noalloc(const uint16_t* d_symbols, uint64
   ea.chunk_words = reinterpret_cast<unsigned*>(out); ea.out = out;
   ea.splits = reinterpret_cast<uint16_t*>(out + off_sp);
   ea.capacity = out_capacity; ea.sc = sc;
-  encode_fused_kernel<8, true><<<grid_for((int64_t)nch * 32, 256, 4), 256, 0, s>>>(ea);
+  encode_fused_kernel<8, true, true><<<grid_for((int64_t)nch * 32, 256, 4), 256, 0, s>>>(ea);
   encode_finish_kernel<<<1, 32, 0, s>>>(~0ull, out_capacity, sc);
   zero_tail_kernel<<<1, 32, 0, s>>>(out, sc);
   g_launches.fetch_add(6);

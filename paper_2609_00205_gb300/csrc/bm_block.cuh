@@ -97,8 +97,11 @@ constexpr int lvl_offset(int B, int l) {  // first symbol of level l inside a bl
 }
 
 // Staging of a code in the forward kernel's 16-bit shared-memory array:
-// code + kStageBias, or kStageWide for a code outside [-2^15, 2^15 - 2].
-constexpr int kStageBias = 1 << 15;
+// code + kStageBias, or kStageWide for a code outside [-(2^15 - 1), 2^15 - 1].
+// Every staged code has |code| < 2^15, so it becomes a symbol for any radius
+// up to 2^15 (the largest dictionary: code 2^15 - 1 is symbol 2^16 - 1); a
+// wide code has |code| >= 2^15 and always escapes.
+constexpr int kStageBias = (1 << 15) - 1;
 constexpr unsigned kStageWide = 0xFFFFu;
 
 template <typename T, int B, int K>
@@ -135,9 +138,10 @@ struct BlockCfg {
   static constexpr int INV_MIN_CTAS = inv_fit < 1 ? 1 : (inv_fit < BM_INV_MIN_CTAS ? inv_fit : BM_INV_MIN_CTAS);
 };
 
-// Histogram of one CTA: the whole dictionary in shared memory; the centre
-// symbol (code 0, most of the symbols at loose tolerances) is counted in a
-// register per thread and added once at the end.
+// Histogram of one CTA: a window of kHistWin symbols around the centre in
+// shared memory, global atomics outside it; the centre symbol (code 0, most
+// of the symbols at loose tolerances) is counted in a register per thread and
+// added once at the end.
 __device__ __forceinline__ void hist_count(unsigned* hloc, unsigned* hglob, int radius, unsigned s, unsigned& centre) {
   if (s == (unsigned)radius) {
     ++centre;
@@ -184,10 +188,10 @@ __device__ __forceinline__ void level_fwd(T* X, T* __restrict__ T1, T* __restric
     const int cc_before = ((i0 + 1) / 2) * C + (f0 ? 0 : (i1 + 1) / 2);
     const int base = lvl_off + L * N - cc_before * C;
     if (MODE == 0) {
-      // the quantisation codes staged in the block's order as code + 2^15
+      // the quantisation codes staged in the block's order as code + 2^15 - 1
       // (store_codes turns them into symbols and escapes when the block is
-      // done); a code outside [-2^15, 2^15 - 2] is staged as 0xFFFF and goes
-      // to the escape array at once (a predicated store, rare)
+      // done); a code outside [-(2^15 - 1), 2^15 - 1] is staged as 0xFFFF and
+      // goes to the escape array at once (a predicated store, rare)
 #pragma unroll
       for (int k = 0; k < N; ++k) {
         if ((k & 1) || !cc) {

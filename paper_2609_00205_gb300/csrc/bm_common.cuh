@@ -19,7 +19,7 @@ enum : unsigned {
 
 constexpr int kHeaderBytes = 256;
 constexpr uint32_t kMagic = 0x31474D42u;  // "BMG1"
-constexpr int kMaxDict = 8192;           // symbols (2 * radius)
+constexpr int kMaxDict = 65536;          // symbols (2 * radius): 16-bit symbols
 constexpr int kMaxLen = 32;              // longest Huffman code
 
 __host__ __device__ inline uint64_t pad8(uint64_t x) { return (x + 7) & ~uint64_t(7); }
@@ -42,6 +42,8 @@ struct Scalars {
   unsigned long long max_len;
   unsigned long long esc_seen;     // escapes the encoder met (must equal n_outliers)
   unsigned maxabs_done;            // CTAs of the max|u| pass that have finished
+  unsigned enc_lo;                 // first symbol of the encoder's shared-memory code window
+  unsigned enc_full;               // 1: every present symbol lies in that window
   unsigned pad1;
 };
 
@@ -167,9 +169,12 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int NLEFT>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NLEFT)); }
 
-// Histogram bins kept in shared memory by every kernel that produces
-// symbols: the whole dictionary, so no symbol goes to a global atomic before
-// the per-CTA flush (a single hot global bin serialises on one L2 slice).
-constexpr int kHistWin = kMaxDict;
+// Histogram bins kept in shared memory by the kernels that count symbols: a
+// window of kHistWin symbols centred on the dictionary's middle (code 0), so
+// the frequent symbols never go to a global atomic before the per-CTA flush
+// (a single hot global bin serialises on one L2 slice); symbols outside the
+// window (large codes, spread thinly over the dictionary) are counted with
+// global atomics.  A dictionary of at most kHistWin symbols lies wholly in it.
+constexpr int kHistWin = 8192;
 
 }  // namespace bm

@@ -17,6 +17,9 @@ namespace bm {
 
 constexpr int kCbThreads = 1024;
 constexpr int kLutBits = 14;
+// Entries of the code table the encoder keeps in shared memory (a window of
+// the dictionary; symbols outside it are looked up in the global table).
+constexpr int kEncWin = 8192;
 // Every chunk is split into eight equal runs; the stream stores the bit
 // offsets of runs 1..7 so that eight decoders can work on one chunk.
 constexpr int kSplits = 8;
@@ -35,6 +38,10 @@ struct DecodeTables {
   CanonTables ct;
   alignas(16) unsigned lut[1 << kLutBits];  // sym | len << 16 for codes of <= kLutBits bits, 0 otherwise
   uint16_t canon[kMaxDict];     // symbols in canonical order
+  // construction arrays for more present symbols than shared memory holds
+  uint8_t big_clen[kMaxDict];
+  uint16_t big_csym[kMaxDict];
+  uint16_t big_canon[kMaxDict];
 };
 
 // ---------------------------------------------------------------------------
@@ -71,16 +78,18 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* warp_t
 // counts of different digits hit different banks.
 __device__ __forceinline__ int wc_idx(unsigned d, int w) { return (int)(d * 32u + ((unsigned)w ^ (d & 31u))); }
 
-// Stable LSD radix sort (8-bit digits) of n <= kMaxDict (key, symbol) pairs by
-// key, one block of kCbThreads threads.  Each pass: every warp ranks its rows
-// of 32 pairs by digit with __match_any_sync, keeping a running count per
-// digit; one block scan over (digit, warp) gives every group its start; the
-// pairs scatter.  As many passes as maxkey has bytes.  Input in (ka, sa);
-// returns 0 when the sorted pairs are in (ka, sa), 1 when in (kb, sb).
-// wcnt: 256 * 32 u32 of scratch.
+// Stable LSD radix sort (8-bit digits) of n <= kMaxDict (key, payload) pairs
+// by key, one block of kCbThreads threads.  Warp w owns the contiguous rows
+// w*rows .. w*rows+rows-1 of 32 pairs, so (warp, row, lane) is index order.
+// Each pass: a counting walk (every warp ranks its rows by digit with
+// __match_any_sync, keeping a running count per (digit, warp)), one block
+// scan over (digit, warp) for every group's start, and a scatter walk over
+// the same rows in the same order that recomputes each pair's rank (so no
+// per-row state is kept in registers and n is not limited by them).  As many
+// passes as maxkey has bytes.  Input in (ka, sa); returns 0 when the sorted
+// pairs are in (ka, sa), 1 when in (kb, sb).  wcnt: 256 * 32 u32 of scratch.
 __device__ int radix_sort_pairs(unsigned* ka, uint16_t* sa, unsigned* kb, uint16_t* sb, unsigned* wcnt, int n,
                                 unsigned maxkey, unsigned* scan_tmp) {
-  constexpr int RMAX = kMaxDict / kCbThreads;  // rows of 32 per warp at most
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int rows = (n + kCbThreads - 1) / kCbThreads;
   const int seg = rows * 32;
@@ -95,20 +104,12 @@ __device__ int radix_sort_pairs(unsigned* ka, uint16_t* sa, unsigned* kb, uint16
     uint16_t* sout = cur ? sa : sb;
     for (int i = threadIdx.x; i < 256 * 32; i += blockDim.x) wcnt[i] = 0u;
     __syncthreads();
-    unsigned loc[RMAX], dig[RMAX];
-#pragma unroll
-    for (int r = 0; r < RMAX; ++r) {
-      if (r >= rows) break;
+    for (int r = 0; r < rows; ++r) {  // counting walk
       const int i = wid * seg + r * 32 + lane;
       const bool ok = i < n;
       const unsigned d = ok ? (kin[i] >> shift) & 255u : 0u;
       const unsigned m = __match_any_sync(0xffffffffu, ok ? d : 256u + (unsigned)lane);
-      const unsigned lt = m & ((1u << lane) - 1u);
-      const unsigned base = ok ? wcnt[wc_idx(d, wid)] : 0u;
-      loc[r] = base + (unsigned)__popc(lt);
-      dig[r] = d;
-      __syncwarp();
-      if (ok && lt == 0u) wcnt[wc_idx(d, wid)] = base + (unsigned)__popc(m);
+      if (ok && (m & ((1u << lane) - 1u)) == 0u) wcnt[wc_idx(d, wid)] += (unsigned)__popc(m);
       __syncwarp();
     }
     __syncthreads();
@@ -128,15 +129,22 @@ __device__ int radix_sort_pairs(unsigned* ka, uint16_t* sa, unsigned* kb, uint16
       pre += v[j];
     }
     __syncthreads();
-#pragma unroll
-    for (int r = 0; r < RMAX; ++r) {
-      if (r >= rows) break;
+    for (int r = 0; r < rows; ++r) {  // scatter walk
       const int i = wid * seg + r * 32 + lane;
-      if (i < n) {
-        const unsigned dst = wcnt[wc_idx(dig[r], wid)] + loc[r];
-        kout[dst] = kin[i];
+      const bool ok = i < n;
+      const unsigned key = ok ? kin[i] : 0u;
+      const unsigned d = (key >> shift) & 255u;
+      const unsigned m = __match_any_sync(0xffffffffu, ok ? d : 256u + (unsigned)lane);
+      const unsigned lt = m & ((1u << lane) - 1u);
+      const unsigned base = ok ? wcnt[wc_idx(d, wid)] : 0u;
+      if (ok) {
+        const unsigned dst = base + (unsigned)__popc(lt);
+        kout[dst] = key;
         sout[dst] = sin[i];
       }
+      __syncwarp();
+      if (ok && lt == 0u) wcnt[wc_idx(d, wid)] = base + (unsigned)__popc(m);
+      __syncwarp();
     }
     __syncthreads();
     cur ^= 1;
@@ -177,35 +185,26 @@ __device__ __forceinline__ int lower_bound_u32(const unsigned* a, int lo, int hi
   return lo;
 }
 
-// Canonical tables from a length array len[0..dict) in shared memory: the
-// present symbols in (length, symbol) order by one stable counting pass over
-// the lengths (at most kMaxLen): warps rank their rows of 32 symbols as in
-// radix_sort_pairs, warp L-1 scans length L's counts over the warps, and each
-// symbol lands at first_pos[len] + (symbols of its length before it).  key32
-// is scratch of at least (kMaxLen + 1) * 32 u32; canon receives the order.
-__device__ void build_canonical(const uint8_t* len, int dict, unsigned* key32, uint16_t* canon, CanonTables* ct,
-                                unsigned* scan_tmp) {
-  constexpr int RMAX = kMaxDict / kCbThreads;
+// Canonical-code tables from the code lengths of the n present symbols held
+// in symbol order (len[i]: length of the i-th present symbol): canon[] gets
+// the indices i in (length, symbol) order, by one stable counting pass over
+// the lengths (at most kMaxLen): warps rank their rows of 32 as in
+// radix_sort_pairs (counting walk, scan, ranking walk), warp L-1 scans length
+// L's counts over the warps, and each index lands at first_pos[len] + (indices
+// of its length before it).  wcnt is scratch of at least (kMaxLen + 1) * 32 u32.
+__device__ void build_canonical(const uint8_t* len, int n, unsigned* wcnt, uint16_t* canon, CanonTables* ct) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  unsigned* wcnt = key32;  // (kMaxLen + 1) x 32
   if (threadIdx.x < kMaxLen + 2) ct->count[threadIdx.x] = 0;
   for (int i = threadIdx.x; i < (kMaxLen + 1) * 32; i += blockDim.x) wcnt[i] = 0u;
   __syncthreads();
-  const int rows = (dict + kCbThreads - 1) / kCbThreads;
+  const int rows = (n + kCbThreads - 1) / kCbThreads;
   const int seg = rows * 32;
-  unsigned loc[RMAX];
-#pragma unroll
-  for (int r = 0; r < RMAX; ++r) {
-    if (r >= rows) break;
-    const int s = wid * seg + r * 32 + lane;
-    const unsigned L = s < dict ? len[s] : 0u;
+  for (int r = 0; r < rows; ++r) {
+    const int i = wid * seg + r * 32 + lane;
+    const unsigned L = i < n ? len[i] : 0u;
     const bool ok = L != 0u && L <= (unsigned)kMaxLen;
     const unsigned m = __match_any_sync(0xffffffffu, ok ? L : 64u + (unsigned)lane);
-    const unsigned lt = m & ((1u << lane) - 1u);
-    const unsigned base = ok ? wcnt[wc_idx(L, wid)] : 0u;
-    loc[r] = base + (unsigned)__popc(lt);
-    __syncwarp();
-    if (ok && lt == 0u) wcnt[wc_idx(L, wid)] = base + (unsigned)__popc(m);
+    if (ok && (m & ((1u << lane) - 1u)) == 0u) wcnt[wc_idx(L, wid)] += (unsigned)__popc(m);
     __syncwarp();
   }
   __syncthreads();
@@ -240,12 +239,17 @@ __device__ void build_canonical(const uint8_t* len, int dict, unsigned* key32, u
     ct->max_len = maxl;
   }
   __syncthreads();
-#pragma unroll
-  for (int r = 0; r < RMAX; ++r) {
-    if (r >= rows) break;
-    const int s = wid * seg + r * 32 + lane;
-    const unsigned L = s < dict ? len[s] : 0u;
-    if (L != 0u && L <= (unsigned)kMaxLen) canon[ct->first_pos[L] + wcnt[wc_idx(L, wid)] + loc[r]] = (uint16_t)s;
+  for (int r = 0; r < rows; ++r) {
+    const int i = wid * seg + r * 32 + lane;
+    const unsigned L = i < n ? len[i] : 0u;
+    const bool ok = L != 0u && L <= (unsigned)kMaxLen;
+    const unsigned m = __match_any_sync(0xffffffffu, ok ? L : 64u + (unsigned)lane);
+    const unsigned lt = m & ((1u << lane) - 1u);
+    const unsigned base = ok ? wcnt[wc_idx(L, wid)] : 0u;
+    if (ok) canon[ct->first_pos[L] + base + (unsigned)__popc(lt)] = (uint16_t)i;
+    __syncwarp();
+    if (ok && lt == 0u) wcnt[wc_idx(L, wid)] = base + (unsigned)__popc(m);
+    __syncwarp();
   }
   __syncthreads();
 }
@@ -262,69 +266,138 @@ struct CodebookArgs {
   int esc_mode;                  // symbol 0 is the escape of an outlier code
   unsigned long long nch;        // chunks
   unsigned long long raw_total;  // size of the raw stream (~0: no raw fallback)
+  unsigned char* big;            // global scratch for more than kCbSmemSyms present symbols (cb_big_bytes())
 };
 
-// Shared memory of the codebook kernel (dynamic).
+// Present symbols the codebook keeps in shared memory; more use global
+// scratch (L2-resident) with the same code.
+constexpr int kCbSmemSyms = 8192;
+
+// Arrays of the codebook construction over the n present symbols, indexed by
+// their rank in symbol order ("compact index"); node ids of the Huffman tree
+// are leaves 0..n-1 (sorted order) and internal nodes n.. (creation order).
+template <typename IdT>
+struct CbArrays {
+  uint16_t* csym;      // [n] symbol of compact index
+  uint8_t* clen;       // [n] code length of compact index
+  unsigned* ka;        // [n] sort keys -> sorted leaf weights (lw)
+  uint16_t* sa;        // [n] compact indices -> sorted leaf order (ls)
+  unsigned* kb;        // [n] sort buffer (aliases iw in shared memory)
+  uint16_t* sb;        // [n] sort buffer (aliases parent in shared memory)
+  unsigned* iw;        // [n] internal weights
+  IdT* parent;         // [2n]
+  uint8_t* depth;      // [2n]
+  unsigned* wcnt;      // [256*32] sort counts (aliases merged + round_end in shared memory)
+  IdT* merged;         // [n] a round's consumed nodes in merged order
+  IdT* round_end;      // [n] internal nodes created up to the end of each round
+  uint16_t* canon;     // [n] compact indices in canonical order (aliases iw)
+  unsigned* run_start; // [n] compact index of each run's first symbol (aliases ka)
+  unsigned* run_end;   // [n] one past its last (aliases iw, after the canonical codes are out)
+  unsigned* run_off;   // [n] byte offset of the run in the codebook section (aliases wcnt)
+};
+
+// Shared-memory layout for at most kCbSmemSyms present symbols (16-bit ids).
 struct CbSmem {
-  unsigned long long keys[kMaxDict];  // sort keys; later merged order / round ends
-  unsigned lw[kMaxDict];              // leaf weights (sorted)
-  unsigned iw[kMaxDict];              // internal weights (creation order)
-  uint16_t ls[kMaxDict];              // leaf symbols
-  uint16_t parent[2 * kMaxDict];
-  uint8_t depth[2 * kMaxDict];
-  uint8_t len[kMaxDict];
+  unsigned ka[kCbSmemSyms];                 // 32 KB
+  unsigned iw[kCbSmemSyms];                 // 32 KB (sort: kb; later canon)
+  unsigned wcnt[256 * 32];                  // 32 KB (rounds: merged u16[N] + round_end u16[N])
+  uint16_t parent[2 * kCbSmemSyms];         // 32 KB (sort: sb)
+  uint8_t depth[2 * kCbSmemSyms];           // 16 KB
+  uint16_t sa[kCbSmemSyms];                 // 16 KB
+  uint16_t csym[kCbSmemSyms];               // 16 KB
+  uint8_t clen[kCbSmemSyms];                //  8 KB
   unsigned scan_tmp[64];
   CanonTables ct;
 };
+static_assert(sizeof(CbSmem) <= 227 * 1024, "codebook shared memory");
+static_assert(256 * 32 >= kCbSmemSyms, "run offsets over the sort counts");
 
-__global__ void __launch_bounds__(kCbThreads) codebook_kernel(CodebookArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  CbSmem& S = *reinterpret_cast<CbSmem*>(smem_raw);
-  __shared__ unsigned s_n, s_lp, s_qp, s_qe, s_pl, s_pq, s_leaves, s_rounds, s_maxd, s_total, s_maxk;
-  __shared__ unsigned long long s_bits;
-  const int dict = a.dict;
-  if (threadIdx.x == 0) s_bits = 0;
-  uint16_t* merged = reinterpret_cast<uint16_t*>(S.keys);                      // [2*kMaxDict]
-  uint16_t* round_end = reinterpret_cast<uint16_t*>(S.keys) + 2 * kMaxDict;    // [kMaxDict]
+// Global scratch of the large variant: n <= kMaxDict present symbols, 32-bit ids.
+__host__ __device__ constexpr size_t cb_big_bytes() {
+  return (size_t)kMaxDict * (2 + 1 + 4 + 2 + 4 + 2 + 4 + 4 * 2 + 2 + 4 + 4 + 2) + 3 * 4 * ((size_t)kMaxDict + 1) +
+         256 * 32 * 4 + 16 * 256;
+}
+
+__device__ __forceinline__ CbArrays<uint16_t> cb_small(CbSmem& S) {
+  CbArrays<uint16_t> v;
+  v.csym = S.csym; v.clen = S.clen; v.ka = S.ka; v.sa = S.sa;
+  v.kb = S.iw; v.sb = S.parent; v.iw = S.iw; v.parent = S.parent; v.depth = S.depth;
+  v.wcnt = S.wcnt;
+  v.merged = reinterpret_cast<uint16_t*>(S.wcnt);
+  v.round_end = reinterpret_cast<uint16_t*>(S.wcnt) + kCbSmemSyms;
+  v.canon = reinterpret_cast<uint16_t*>(S.iw);
+  v.run_start = S.ka;
+  v.run_end = S.iw;
+  v.run_off = S.wcnt;
+  return v;
+}
+
+__device__ __forceinline__ CbArrays<unsigned> cb_big(unsigned char* g) {
+  auto take = [&](size_t bytes) {
+    unsigned char* p = g;
+    g += (bytes + 255) & ~size_t(255);
+    return p;
+  };
+  const size_t N = kMaxDict;
+  CbArrays<unsigned> v;
+  v.csym = reinterpret_cast<uint16_t*>(take(2 * N));
+  v.clen = take(N);
+  v.ka = reinterpret_cast<unsigned*>(take(4 * N));
+  v.sa = reinterpret_cast<uint16_t*>(take(2 * N));
+  v.kb = reinterpret_cast<unsigned*>(take(4 * N));
+  v.sb = reinterpret_cast<uint16_t*>(take(2 * N));
+  v.iw = reinterpret_cast<unsigned*>(take(4 * N));
+  v.parent = reinterpret_cast<unsigned*>(take(4 * 2 * N));
+  v.depth = take(2 * N);
+  v.merged = reinterpret_cast<unsigned*>(take(4 * N));
+  v.round_end = reinterpret_cast<unsigned*>(take(4 * N));
+  v.canon = reinterpret_cast<uint16_t*>(take(2 * N));
+  v.run_start = reinterpret_cast<unsigned*>(take(4 * N));
+  v.run_end = reinterpret_cast<unsigned*>(take(4 * N));
+  v.run_off = reinterpret_cast<unsigned*>(take(4 * N));
+  v.wcnt = reinterpret_cast<unsigned*>(take(256 * 32 * 4));
+  return v;
+}
+
+// The codebook over the compact arrays V (n present symbols, already in
+// V.csym): Huffman lengths into V.clen.  The lengths are those of the
+// sequential two-queue construction; lengths above kMaxLen are avoided by
+// re-running on max(1, f >> t), t = 1, 2, ...
+template <typename IdT>
+__device__ void codebook_lengths(const CodebookArgs& a, CbArrays<IdT> V, int n, unsigned* scan_tmp) {
+  __shared__ unsigned s_lp, s_qp, s_qe, s_pl, s_pq, s_leaves, s_rounds, s_maxd, s_maxk;
+  if (n <= 1) {
+    if (n == 1 && threadIdx.x == 0) V.clen[0] = 1;
+    __syncthreads();
+    return;
+  }
   for (int shift = 0;; ++shift) {
-    // 1. present symbols, in symbol order, as (freq', symbol) pairs
-    unsigned* ka = reinterpret_cast<unsigned*>(S.keys);  // [kMaxDict] keys
-    unsigned* wcnt = ka + kMaxDict;                       // [256 * 32] sort counts
-    uint16_t* sb = reinterpret_cast<uint16_t*>(S.iw);    // [kMaxDict] sort buffer
+    // 1. (freq', compact index) pairs in symbol order
     if (threadIdx.x == 0) s_maxk = 0;
-    const int per = (dict + blockDim.x - 1) / blockDim.x;
-    const int s0 = threadIdx.x * per;
-    unsigned cnt = 0;
-    for (int s = s0; s < s0 + per && s < dict; ++s) cnt += a.hist[s] ? 1u : 0u;
-    unsigned pos = block_excl_scan(cnt, S.scan_tmp, &s_n);
+    __syncthreads();
     unsigned mk = 0;
-    for (int s = s0; s < s0 + per && s < dict; ++s) {
-      const unsigned f = a.hist[s];
-      if (f) {
-        const unsigned fs = shift ? max(1u, f >> shift) : f;
-        ka[pos] = fs;
-        S.ls[pos] = (uint16_t)s;
-        ++pos;
-        mk = max(mk, fs);
-      }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const unsigned f = a.hist[V.csym[i]];
+      const unsigned fs = shift ? max(1u, f >> shift) : f;
+      V.ka[i] = fs;
+      V.sa[i] = (uint16_t)i;
+      V.clen[i] = 0;
+      mk = max(mk, fs);
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) mk = max(mk, __shfl_xor_sync(0xffffffffu, mk, o));
     if ((threadIdx.x & 31) == 0 && mk) atomicMax(&s_maxk, mk);
-    for (int s = threadIdx.x; s < dict; s += blockDim.x) S.len[s] = 0;
     __syncthreads();
-    const int n = (int)s_n;
-    if (n <= 1) {
-      if (n == 1 && threadIdx.x == 0) S.len[S.ls[0]] = 1;
-      __syncthreads();
-      break;
+    // leaves by ascending weight, ties in symbol order, into (ka, sa) = (lw, ls)
+    const int which = radix_sort_pairs(V.ka, V.sa, V.kb, V.sb, V.wcnt, n, s_maxk, scan_tmp);
+    if (which) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        V.ka[i] = V.kb[i];
+        V.sa[i] = V.sb[i];
+      }
     }
-    // leaves by ascending weight, ties in symbol order, into (lw, ls)
-    const int which = radix_sort_pairs(ka, S.ls, S.lw, sb, wcnt, n, s_maxk, S.scan_tmp);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      if (which == 0) S.lw[i] = ka[i];
-      else S.ls[i] = sb[i];
-    }
+    const unsigned* lw = V.ka;
+    const uint16_t* ls = V.sa;
     if (threadIdx.x == 0) { s_lp = 0; s_qp = 0; s_qe = 0; s_rounds = 0; s_leaves = 0; }
     __syncthreads();
     // 2. parallel rounds of the two-queue construction.  Warp 0 folds the
@@ -338,7 +411,7 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(CodebookArgs a) {
           s_lp += s_leaves;
           s_qp += 2 * np_prev - s_leaves;
           s_qe += np_prev;
-          round_end[s_rounds++] = (uint16_t)s_qe;
+          V.round_end[s_rounds++] = (IdT)s_qe;
           s_leaves = 0;
         }
         __syncwarp();
@@ -347,12 +420,12 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(CodebookArgs a) {
         if (qe < (unsigned)(n - 1)) {
           unsigned w[2];
           for (int t = 0; t < 2; ++t) {
-            if (lp < (unsigned)n && (qp >= qe || S.lw[lp] <= S.iw[qp])) w[t] = S.lw[lp++];
-            else w[t] = S.iw[qp++];
+            if (lp < (unsigned)n && (qp >= qe || lw[lp] <= V.iw[qp])) w[t] = lw[lp++];
+            else w[t] = V.iw[qp++];
           }
           const unsigned X = w[0] + w[1];
-          const int pl = warp_upper_bound_u32(S.lw, (int)s_lp, n, X) - (int)s_lp;
-          const int pq = warp_upper_bound_u32(S.iw, (int)s_qp, (int)qe, X) - (int)s_qp;
+          const int pl = warp_upper_bound_u32(lw, (int)s_lp, n, X) - (int)s_lp;
+          const int pq = warp_upper_bound_u32(V.iw, (int)s_qp, (int)qe, X) - (int)s_qp;
           if (threadIdx.x == 0) { s_pl = (unsigned)pl; s_pq = (unsigned)pq; }
         }
       }
@@ -364,24 +437,24 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(CodebookArgs a) {
         int rank, id;
         if (e < pl) {
           const int i = lp + e;
-          rank = e + (lower_bound_u32(S.iw, qp, qp + pq, S.lw[i]) - qp);
+          rank = e + (lower_bound_u32(V.iw, qp, qp + pq, lw[i]) - qp);
           id = i;
         } else {
           const int j = qp + (e - pl);
-          rank = (e - pl) + (upper_bound_u32(S.lw, lp, lp + pl, S.iw[j]) - lp);
+          rank = (e - pl) + (upper_bound_u32(lw, lp, lp + pl, V.iw[j]) - lp);
           id = n + j;
         }
-        if (rank < 2 * npairs) merged[rank] = (uint16_t)id;
+        if (rank < 2 * npairs) V.merged[rank] = (IdT)id;
       }
       __syncthreads();
       unsigned leaves = 0;
       for (int k = threadIdx.x; k < npairs; k += blockDim.x) {
-        const int x = merged[2 * k], y = merged[2 * k + 1];
-        const unsigned wx = x < n ? S.lw[x] : S.iw[x - n];
-        const unsigned wy = y < n ? S.lw[y] : S.iw[y - n];
-        S.iw[qe + k] = wx + wy;
-        S.parent[x] = (uint16_t)(n + qe + k);
-        S.parent[y] = (uint16_t)(n + qe + k);
+        const int x = (int)V.merged[2 * k], y = (int)V.merged[2 * k + 1];
+        const unsigned wx = x < n ? lw[x] : V.iw[x - n];
+        const unsigned wy = y < n ? lw[y] : V.iw[y - n];
+        V.iw[qe + k] = wx + wy;
+        V.parent[x] = (IdT)(n + qe + k);
+        V.parent[y] = (IdT)(n + qe + k);
         leaves += (x < n) + (y < n);
       }
       if (leaves) atomicAdd(&s_leaves, leaves);
@@ -390,20 +463,20 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(CodebookArgs a) {
     }
     // 3. depths, rounds in reverse (a parent is always created in a later round)
     const int root = 2 * n - 2;
-    if (threadIdx.x == 0) { S.depth[root] = 0; s_maxd = 0; }
+    if (threadIdx.x == 0) { V.depth[root] = 0; s_maxd = 0; }
     __syncthreads();
     for (int r = (int)s_rounds - 1; r >= 0; --r) {
-      const int jb = r ? round_end[r - 1] : 0, je = round_end[r];
+      const int jb = r ? (int)V.round_end[r - 1] : 0, je = (int)V.round_end[r];
       for (int j = jb + threadIdx.x; j < je; j += blockDim.x) {
         const int v = n + j;
-        if (v != root) S.depth[v] = S.depth[S.parent[v]] + 1;
+        if (v != root) V.depth[v] = V.depth[V.parent[v]] + 1;
       }
       __syncthreads();
     }
     unsigned md = 0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const unsigned d = S.depth[S.parent[i]] + 1u;
-      S.len[S.ls[i]] = (uint8_t)min(d, 255u);
+      const unsigned d = V.depth[V.parent[i]] + 1u;
+      V.clen[ls[i]] = (uint8_t)min(d, 255u);
       md = max(md, d);
     }
     if (md) atomicMax(&s_maxd, md);
@@ -411,42 +484,45 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(CodebookArgs a) {
     if (s_maxd <= (unsigned)kMaxLen) break;
     __syncthreads();
   }
-  // 4. canonical codes
-  unsigned* key32 = reinterpret_cast<unsigned*>(S.lw);  // lw/iw no longer needed
-  uint16_t* canon = reinterpret_cast<uint16_t*>(S.iw);
-  build_canonical(S.len, dict, key32, canon, &S.ct, S.scan_tmp);
-  for (int i = threadIdx.x; i < (int)S.ct.n; i += blockDim.x) {
-    const int s = canon[i];
-    const int L = S.len[s];
-    a.codes[s] = S.ct.first_code[L] + (unsigned)(i - (int)S.ct.first_pos[L]);
+}
+
+// Canonical codes, the lookup tables of the encoder, the codebook section of
+// the stream and the offsets of the sections after it, from the lengths.
+template <typename IdT>
+__device__ void codebook_emit(const CodebookArgs& a, CbArrays<IdT> V, int n, unsigned* scan_tmp, CanonTables* ct) {
+  __shared__ unsigned s_total, s_nruns;
+  __shared__ unsigned long long s_bits;
+  if (threadIdx.x == 0) s_bits = 0;
+  // 4. canonical codes (wcnt of the counting pass in the free weight array)
+  build_canonical(V.clen, n, V.ka, V.canon, ct);
+  for (int i = threadIdx.x; i < (int)ct->n; i += blockDim.x) {
+    const int ci = V.canon[i];
+    const int L = V.clen[ci];
+    a.codes[V.csym[ci]] = ct->first_code[L] + (unsigned)(i - (int)ct->first_pos[L]);
   }
-  for (int s = threadIdx.x; s < dict; s += blockDim.x) {
-    a.lens[s] = S.len[s];
-    if (!S.len[s]) a.codes[s] = 0;
-  }
-  // 5. codebook runs {u32 first, u32 count, u8 len[count], pad to 4}
-  unsigned* run_start = reinterpret_cast<unsigned*>(S.keys);            // [kMaxDict/2+1]
-  unsigned* run_end = run_start + (kMaxDict / 2 + 1);                    // one past the last symbol
-  unsigned* run_off = run_end + (kMaxDict / 2 + 1);
-  const int per = (dict + blockDim.x - 1) / blockDim.x;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a.lens[V.csym[i]] = V.clen[i];
+  // 5. codebook runs {u32 first, u32 count, u8 len[count], pad to 4}: a run
+  // starts at every present symbol whose predecessor is absent
+  unsigned* run_start = V.run_start;
+  unsigned* run_end = V.run_end;
+  unsigned* run_off = V.run_off;
+  const int per = (n + blockDim.x - 1) / blockDim.x;
   const int s0 = threadIdx.x * per;
-  auto is_start = [&](int s) { return S.len[s] && (s == 0 || !S.len[s - 1]); };
-  auto is_end = [&](int s) { return S.len[s] && (s == dict - 1 || !S.len[s + 1]); };
-  unsigned nst = 0, nen = 0;
-  for (int s = s0; s < s0 + per && s < dict; ++s) { nst += is_start(s); nen += is_end(s); }
-  unsigned r = block_excl_scan(nst, S.scan_tmp, &s_n);
-  for (int s = s0; s < s0 + per && s < dict; ++s)
-    if (is_start(s)) run_start[r++] = (unsigned)s;
-  unsigned r2 = block_excl_scan(nen, S.scan_tmp, nullptr);
-  for (int s = s0; s < s0 + per && s < dict; ++s)
-    if (is_end(s)) run_end[r2++] = (unsigned)s + 1u;
+  auto is_start = [&](int i) { return i == 0 || V.csym[i] != V.csym[i - 1] + 1; };
+  unsigned nst = 0;
+  for (int i = s0; i < s0 + per && i < n; ++i) nst += is_start(i);
+  unsigned r = block_excl_scan(nst, scan_tmp, &s_nruns);
+  for (int i = s0; i < s0 + per && i < n; ++i)
+    if (is_start(i)) run_start[r++] = (unsigned)i;
   __syncthreads();
-  const int nruns = (int)s_n;
+  const int nruns = (int)s_nruns;
+  for (int q = threadIdx.x; q < nruns; q += blockDim.x) run_end[q] = q + 1 < nruns ? run_start[q + 1] : (unsigned)n;
+  __syncthreads();
   unsigned my_bytes = 0;
   const int rper = (nruns + blockDim.x - 1) / blockDim.x;
   const int r0 = threadIdx.x * rper;
   for (int q = r0; q < r0 + rper && q < nruns; ++q) my_bytes += 8u + (((run_end[q] - run_start[q]) + 3u) & ~3u);
-  unsigned off = block_excl_scan(my_bytes, S.scan_tmp, &s_total);
+  unsigned off = block_excl_scan(my_bytes, scan_tmp, &s_total);
   for (int q = r0; q < r0 + rper && q < nruns; ++q) {
     run_off[q] = off;
     off += 8u + (((run_end[q] - run_start[q]) + 3u) & ~3u);
@@ -458,15 +534,14 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(CodebookArgs a) {
     for (int q = threadIdx.x; q < nruns; q += blockDim.x) {
       const unsigned first = run_start[q], cntq = run_end[q] - first;
       uint8_t* p = a.out + a.off + run_off[q];
-      *reinterpret_cast<unsigned*>(p) = first;
+      *reinterpret_cast<unsigned*>(p) = (unsigned)V.csym[first];
       *reinterpret_cast<unsigned*>(p + 4) = cntq;
       for (unsigned t = cntq; t < ((cntq + 3u) & ~3u); ++t) p[8 + t] = 0;
     }
-    // length bytes: symbol s of run q goes to run_off[q] + 8 + (s - first)
-    for (int s = threadIdx.x; s < dict; s += blockDim.x) {
-      if (!S.len[s]) continue;
-      const int q = upper_bound_u32(run_start, 0, nruns, (unsigned)s) - 1;
-      a.out[a.off + run_off[q] + 8 + (s - run_start[q])] = S.len[s];
+    // length bytes: compact index i of run q goes to run_off[q] + 8 + (i - run_start[q])
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int q = upper_bound_u32(run_start, 0, nruns, (unsigned)i) - 1;
+      a.out[a.off + run_off[q] + 8 + (i - run_start[q])] = V.clen[i];
     }
     if (threadIdx.x == 0)
       for (unsigned long long t = total; t < pad8(total); ++t) a.out[a.off + t] = 0;
@@ -475,7 +550,7 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(CodebookArgs a) {
   // the bitstream) and a lower bound on its size: the bitstream holds exactly
   // sum_s f_s len_s bits plus the padding of each chunk to whole words
   unsigned long long my_bits = 0;
-  for (int s = threadIdx.x; s < dict; s += blockDim.x) my_bits += (unsigned long long)a.hist[s] * S.len[s];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) my_bits += (unsigned long long)a.hist[V.csym[i]] * V.clen[i];
 #pragma unroll
   for (int o = 16; o; o >>= 1) my_bits += __shfl_xor_sync(0xffffffffu, my_bits, o);
   if ((threadIdx.x & 31) == 0 && my_bits) atomicAdd(&s_bits, my_bits);
@@ -484,7 +559,18 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(CodebookArgs a) {
     Scalars* sc = a.sc;
     sc->codebook_bytes = total;
     sc->n_runs = (unsigned long long)nruns;
-    sc->max_len = S.ct.max_len;
+    sc->max_len = ct->max_len;
+    // the encoder's shared-memory window of the code table: every present
+    // symbol when they span at most kEncWin symbols, else centred on the
+    // dictionary's middle (code 0); symbols outside it are looked up in memory
+    const unsigned smin = n ? V.csym[0] : 0u, smax = n ? V.csym[n - 1] : 0u;
+    if (smax - smin < (unsigned)kEncWin) {
+      sc->enc_lo = a.dict <= kEncWin ? 0u : min(smin, (unsigned)(a.dict - kEncWin));
+      sc->enc_full = 1;
+    } else {
+      sc->enc_lo = (unsigned)max(0, min(a.dict / 2 - kEncWin / 2, a.dict - kEncWin));
+      sc->enc_full = 0;
+    }
     if (a.out && !fits) atomicOr(&sc->status, ST_CAPACITY | ST_RAW);
     const unsigned long long nout = a.esc_mode ? (unsigned long long)a.hist[0] : 0ull;
     const unsigned long long off_ce = a.off + pad8(total);
@@ -502,30 +588,70 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(CodebookArgs a) {
   }
 }
 
-// Histogram of a symbol array (stand-alone Huffman entry point).
-__global__ void hist_kernel(const uint16_t* __restrict__ sym, unsigned long long n, int dict, unsigned* hist,
-                            Scalars* sc) {
-  extern __shared__ unsigned hs[];
-  for (int i = threadIdx.x; i < dict; i += blockDim.x) hs[i] = 0;
+__global__ void __launch_bounds__(kCbThreads) codebook_kernel(CodebookArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CbSmem& S = *reinterpret_cast<CbSmem*>(smem_raw);
+  __shared__ unsigned s_n;
+  const int dict = a.dict;
+  // 0. every dictionary entry starts without a code
+  for (int s = threadIdx.x; s < dict; s += blockDim.x) {
+    a.lens[s] = 0;
+    a.codes[s] = 0;
+  }
+  // present symbols, in symbol order, compacted (each thread a contiguous slice)
+  const int per = (dict + blockDim.x - 1) / blockDim.x;
+  const int s0 = threadIdx.x * per;
+  unsigned cnt = 0;
+  for (int s = s0; s < s0 + per && s < dict; ++s) cnt += a.hist[s] ? 1u : 0u;
+  unsigned pos = block_excl_scan(cnt, S.scan_tmp, &s_n);
+  const int n = (int)s_n;
+  const bool small = n <= kCbSmemSyms;
+  uint16_t* csym = small ? S.csym : cb_big(a.big).csym;
+  for (int s = s0; s < s0 + per && s < dict; ++s)
+    if (a.hist[s]) csym[pos++] = (uint16_t)s;
+  __syncthreads();
+  if (small) {
+    const CbArrays<uint16_t> V = cb_small(S);
+    codebook_lengths<uint16_t>(a, V, n, S.scan_tmp);
+    codebook_emit<uint16_t>(a, V, n, S.scan_tmp, &S.ct);
+  } else {
+    const CbArrays<unsigned> V = cb_big(a.big);
+    codebook_lengths<unsigned>(a, V, n, S.scan_tmp);
+    codebook_emit<unsigned>(a, V, n, S.scan_tmp, &S.ct);
+  }
+}
+
+// Histogram of a symbol array (stand-alone Huffman entry point): a shared
+// window of kHistWin bins around the dictionary's middle, global atomics
+// outside it; symbols not below dict are flagged.
+__global__ void __launch_bounds__(256) hist_kernel(const uint16_t* __restrict__ sym, unsigned long long n, int dict,
+                                                   unsigned* hist, Scalars* sc) {
+  __shared__ unsigned hs[kHistWin];
+  const int lo = max(0, min(dict / 2 - kHistWin / 2, dict - kHistWin));
+  const int w = min(dict, kHistWin);
+  for (int i = threadIdx.x; i < w; i += blockDim.x) hs[i] = 0;
   __syncthreads();
   bool bad = false;
   for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
        i += (unsigned long long)gridDim.x * blockDim.x) {
     const unsigned s = sym[i];
-    if (s < (unsigned)dict) atomicAdd(hs + s, 1u);
+    const unsigned k = s - (unsigned)lo;
+    if (k < (unsigned)w) atomicAdd(hs + k, 1u);
+    else if (s < (unsigned)dict) atomicAdd(hist + s, 1u);
     else bad = true;
   }
   if (bad) atomicOr(&sc->status, ST_CORRUPT);
   __syncthreads();
-  for (int i = threadIdx.x; i < dict; i += blockDim.x)
-    if (hs[i]) atomicAdd(hist + i, hs[i]);
+  for (int i = threadIdx.x; i < w; i += blockDim.x)
+    if (hs[i]) atomicAdd(hist + lo + i, hs[i]);
 }
 
 // Histogram of a symbol range [s0, s1) with 16-byte loads.  Build-time choice
 // BM_HIST_METHOD: 1 = the centre symbol (code 0) counted in a register, the
 // rest with shared atomics; 7 = the seven symbols around the centre in
 // registers; 0 = equal symbols of a warp instruction merged first
-// (__match_any_sync), one shared atomic per distinct symbol.
+// (__match_any_sync), one shared atomic per distinct symbol.  Shared bins
+// cover kHistWin symbols around the centre; the rest go to global atomics.
 #ifndef BM_HIST_METHOD
 #define BM_HIST_METHOD 1
 #endif
@@ -535,24 +661,31 @@ __global__ void hist_kernel(const uint16_t* __restrict__ sym, unsigned long long
 __global__ void __launch_bounds__(256) hist_range_kernel(const uint16_t* __restrict__ sym, unsigned long long s0,
                                                          unsigned long long s1, int dict, unsigned centre_sym,
                                                          unsigned* hist) {
-  __shared__ unsigned hs[kMaxDict];
-  for (int i = threadIdx.x; i < dict; i += blockDim.x) hs[i] = 0;
+  __shared__ unsigned hs[kHistWin];
+  const unsigned wlo = (unsigned)max(0, min((int)centre_sym - kHistWin / 2, dict - kHistWin));
+  const unsigned wn = (unsigned)min(dict, kHistWin);
+  for (int i = threadIdx.x; i < (int)wn; i += blockDim.x) hs[i] = 0;
   __syncthreads();
   constexpr int NC = BM_HIST_METHOD == 7 ? 7 : 1;
   unsigned cnt[NC];
 #pragma unroll
   for (int j = 0; j < NC; ++j) cnt[j] = 0;
   const unsigned lo = centre_sym - (NC / 2);
+  auto bin = [&](unsigned s, unsigned c) {
+    const unsigned k = s - wlo;
+    if (k < wn) atomicAdd(hs + k, c);
+    else if (s < (unsigned)dict) atomicAdd(hist + s, c);
+  };
   auto count = [&](unsigned s) {
     if (BM_HIST_METHOD == 0) {
       const unsigned m = __match_any_sync(__activemask(), s);
-      if ((unsigned)(threadIdx.x & 31) == (unsigned)(__ffs(m) - 1) && s < (unsigned)dict) atomicAdd(hs + s, __popc(m));
+      if ((unsigned)(threadIdx.x & 31) == (unsigned)(__ffs(m) - 1)) bin(s, __popc(m));
       return;
     }
     const unsigned d = s - lo;
 #pragma unroll
     for (int j = 0; j < NC; ++j) cnt[j] += d == (unsigned)j;
-    if (d >= (unsigned)NC && s < (unsigned)dict) atomicAdd(hs + s, 1u);
+    if (d >= (unsigned)NC) bin(s, 1u);
   };
   const unsigned long long a0 = min(s1, (s0 + 7) & ~7ull);  // 16-byte aligned start
   const unsigned long long tid = blockIdx.x * 256ull + threadIdx.x, nth = gridDim.x * 256ull;
@@ -582,11 +715,11 @@ __global__ void __launch_bounds__(256) hist_range_kernel(const uint16_t* __restr
     unsigned c = cnt[j];
 #pragma unroll
     for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if (BM_HIST_METHOD != 0 && (threadIdx.x & 31) == 0 && c && lo + j < (unsigned)dict) atomicAdd(hs + lo + j, c);
+    if (BM_HIST_METHOD != 0 && (threadIdx.x & 31) == 0 && c) bin(lo + j, c);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < dict; i += blockDim.x)
-    if (hs[i]) atomicAdd(hist + i, hs[i]);
+  for (int i = threadIdx.x; i < (int)wn; i += blockDim.x)
+    if (hs[i]) atomicAdd(hist + wlo + i, hs[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -634,29 +767,51 @@ __device__ __forceinline__ unsigned sym_of(const uint4* q, int i) {
   return (i & 1) ? (w >> 16) : (w & 0xFFFFu);
 }
 
-// Codes of a symbol: (code, length) from one packed word (code | len << 26)
-// when every code has at most 26 bits, else from two tables.
-template <bool PACKED>
-__device__ __forceinline__ void code_of(const unsigned* codes, const uint8_t* lens, unsigned s, unsigned& c,
-                                        unsigned& L) {
-  const unsigned cw = codes[s];
-  if (PACKED) { c = cw & 0x3FFFFFFu; L = cw >> 26; }
-  else { c = cw; L = lens[s]; }
+// The encoder's code table: a window of kEncWin entries in shared memory
+// (sc: code, or code | len << 26 when every code has at most 26 bits; sl:
+// length) starting at symbol `lo`, and the whole table in global memory for
+// symbols outside the window (WIN = true; with WIN = false every symbol is
+// known to lie in the window).
+struct EncTab {
+  const unsigned* sc;
+  const uint8_t* sl;
+  unsigned lo;
+  const unsigned* gc;
+  const uint8_t* gl;
+};
+
+template <bool PACKED, bool WIN>
+__device__ __forceinline__ void code_of(const EncTab& t, unsigned s, unsigned& c, unsigned& L) {
+  const unsigned k = s - t.lo;
+  if (!WIN || k < (unsigned)kEncWin) {
+    const unsigned cw = t.sc[k];
+    if (PACKED) { c = cw & 0x3FFFFFFu; L = cw >> 26; }
+    else { c = cw; L = t.sl[k]; }
+  } else {
+    c = __ldg(t.gc + s);
+    L = __ldg(t.gl + s);
+  }
+}
+template <bool PACKED, bool WIN>
+__device__ __forceinline__ unsigned len_of(const EncTab& t, unsigned s) {
+  const unsigned k = s - t.lo;
+  if (!WIN || k < (unsigned)kEncWin) return PACKED ? (t.sc[k] >> 26) : (unsigned)t.sl[k];
+  return __ldg(t.gl + s);
 }
 
 // Bits and escape mask of a lane's vector slice (G groups held in registers).
 // CLAMP: symbols may be out of the dictionary (caller-supplied) and are
 // clamped; the compressor's own symbols are in range by construction.
-template <bool PACKED, bool CLAMP, int GC>
-__device__ __forceinline__ void slice_bits(const uint4* q, int G, unsigned dmax, const unsigned* codes,
-                                           const uint8_t* lens, unsigned& bits, unsigned long long& emask) {
+template <bool PACKED, bool WIN, bool CLAMP, int GC>
+__device__ __forceinline__ void slice_bits(const uint4* q, int G, unsigned dmax, const EncTab& tab, unsigned& bits,
+                                           unsigned long long& emask) {
   bits = 0;
   unsigned nz = 0;
 #pragma unroll
   for (int i = 0; i < 8 * kEncGroups; ++i) {
     if ((i >> 3) < (GC ? GC : G)) {
       const unsigned s = CLAMP ? min(sym_of(q, i), dmax) : sym_of(q, i);
-      bits += PACKED ? (codes[s] >> 26) : (unsigned)lens[s];
+      bits += len_of<PACKED, WIN>(tab, s);
       nz += s == 0;
     }
   }
@@ -675,10 +830,10 @@ __device__ __forceinline__ void slice_bits(const uint4* q, int G, unsigned dmax,
 // word is stored through `wp` as soon as it fills.  The lane's first word may
 // start with the previous lane's last bits: it is stored with zeros there and
 // the previous lane ORs its bits in afterwards.
-template <bool PACKED, bool CLAMP, int GC>
-__device__ __forceinline__ void slice_pack(const uint4* q, int G, unsigned dmax, const unsigned* codes,
-                                           const uint8_t* lens, unsigned* wp, unsigned nb,
-                                           unsigned long long& acc_out, unsigned& nb_out, unsigned*& wp_out) {
+template <bool PACKED, bool WIN, bool CLAMP, int GC>
+__device__ __forceinline__ void slice_pack(const uint4* q, int G, unsigned dmax, const EncTab& tab, unsigned* wp,
+                                           unsigned nb, unsigned long long& acc_out, unsigned& nb_out,
+                                           unsigned*& wp_out) {
   // acc = hi:lo; packed codes have at most 26 bits, so the shifts stay below
   // 32 and each is one funnel shift (and a plain shift of the low word)
   unsigned hi = 0, lo = 0;
@@ -687,7 +842,7 @@ __device__ __forceinline__ void slice_pack(const uint4* q, int G, unsigned dmax,
     if ((i >> 3) < (GC ? GC : G)) {
       const unsigned s = CLAMP ? min(sym_of(q, i), dmax) : sym_of(q, i);
       unsigned c, L;
-      code_of<PACKED>(codes, lens, s, c, L);
+      code_of<PACKED, WIN>(tab, s, c, L);
       if (PACKED) {
         hi = __funnelshift_l(lo, hi, L);
         lo = (lo << L) | c;
@@ -708,6 +863,23 @@ __device__ __forceinline__ void slice_pack(const uint4* q, int G, unsigned dmax,
   wp_out = wp;
 }
 
+// One of the four instantiations of a slice function, picked at run time
+// (packed codes, full default-size slices); WIN is the kernel's.
+#define BM_ENC_DISPATCH(FN, ...)                                                        \
+  do {                                                                                  \
+    if (G == kEncGroups) {                                                              \
+      if (packed) FN<true, WIN, CLAMP, kEncGroups>(__VA_ARGS__);                         \
+      else FN<false, WIN, CLAMP, kEncGroups>(__VA_ARGS__);                               \
+    } else {                                                                            \
+      if (packed) FN<true, WIN, CLAMP, 0>(__VA_ARGS__);                                  \
+      else FN<false, WIN, CLAMP, 0>(__VA_ARGS__);                                        \
+    }                                                                                   \
+  } while (0)
+
+// Two instantiations per symbol source: WIN = false when the codebook found
+// every present symbol inside the shared-memory window (sc->enc_full), WIN =
+// true otherwise (lookups outside the window go to the global table).  Both
+// are launched; the one that does not match returns at once.
 // Warps take chunks in ticket order.  A warp codes its chunk's bit count from
 // the symbols it holds in registers, publishes the chunk's (words, escapes)
 // aggregate, walks back over its predecessors until one has published an
@@ -715,19 +887,27 @@ __device__ __forceinline__ void slice_pack(const uint4* q, int G, unsigned dmax,
 // packs its codes at the now known word offset.  Each lane stores its full
 // words; a word shared by two lanes is completed by an atomic OR of the
 // earlier lane's last bits.
-template <int WARPS, bool CLAMP>
+template <int WARPS, bool CLAMP, bool WIN>
 __global__ void __launch_bounds__(WARPS * 32, 4) encode_fused_kernel(FusedEncodeArgs a) {
-  __shared__ uint8_t lens[kMaxDict];
-  __shared__ unsigned codes[kMaxDict];
+  __shared__ uint8_t lens[kEncWin];
+  __shared__ unsigned codes[kEncWin];
   Scalars* sc = a.sc;
   if (sc->skip) return;  // the stream is already known to be a raw copy
+  // caller-supplied symbols (CLAMP) may be absent from the table: they always
+  // take the variant with the global fallback
+  if (CLAMP ? !WIN : (WIN == (sc->enc_full != 0))) return;
   // codes of at most 26 bits are packed with their length into one word
-  // (code | len << 26): one shared-memory lookup per symbol
+  // (code | len << 26): one shared-memory lookup per symbol in the window
   const bool packed = sc->max_len <= 26;
-  for (int i = threadIdx.x; i < a.dict; i += blockDim.x) {
-    lens[i] = a.lens[i];
-    codes[i] = packed ? (a.codes[i] | ((unsigned)a.lens[i] << 26)) : a.codes[i];
+  const unsigned wlo = sc->enc_lo;
+  for (int i = threadIdx.x; i < kEncWin; i += blockDim.x) {
+    const unsigned s = wlo + (unsigned)i;
+    const unsigned L = s < (unsigned)a.dict ? a.lens[s] : 0u;
+    const unsigned c = s < (unsigned)a.dict ? a.codes[s] : 0u;
+    lens[i] = (uint8_t)L;
+    codes[i] = packed ? (c | (L << 26)) : c;
   }
+  const EncTab tab{codes, lens, wlo, a.codes, a.lens};
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const unsigned dmax = (unsigned)(a.dict - 1);
@@ -762,18 +942,12 @@ __global__ void __launch_bounds__(WARPS * 32, 4) encode_fused_kernel(FusedEncode
 #pragma unroll
       for (int g = 0; g < kEncGroups; ++g) q[g] = g < G ? __ldg(p + g) : make_uint4(0, 0, 0, 0);
       // G is 8 at the default chunk of 2048 symbols: a fully unrolled slice
-      if (G == kEncGroups) {
-        if (packed) slice_bits<true, CLAMP, kEncGroups>(q, G, dmax, codes, lens, bits, emask);
-        else slice_bits<false, CLAMP, kEncGroups>(q, G, dmax, codes, lens, bits, emask);
-      } else {
-        if (packed) slice_bits<true, CLAMP, 0>(q, G, dmax, codes, lens, bits, emask);
-        else slice_bits<false, CLAMP, 0>(q, G, dmax, codes, lens, bits, emask);
-      }
+      BM_ENC_DISPATCH(slice_bits, q, G, dmax, tab, bits, emask);
       nesc = __popcll(emask);
     } else {
       for (int t = 0; t < cnt; ++t) {
         const unsigned s = CLAMP ? min((unsigned)a.sym[s0 + t], dmax) : (unsigned)a.sym[s0 + t];
-        bits += lens[s];
+        bits += len_of<false, true>(tab, s);
         nesc += s == 0;
       }
     }
@@ -893,13 +1067,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) encode_fused_kernel(FusedEncode
       unsigned* wp;
       unsigned* const w0 = words + head_idx;
       const unsigned nb0 = bit0 & 31u;
-      if (G == kEncGroups) {
-        if (packed) slice_pack<true, CLAMP, kEncGroups>(q, G, dmax, codes, lens, w0, nb0, acc, nb, wp);
-        else slice_pack<false, CLAMP, kEncGroups>(q, G, dmax, codes, lens, w0, nb0, acc, nb, wp);
-      } else {
-        if (packed) slice_pack<true, CLAMP, 0>(q, G, dmax, codes, lens, w0, nb0, acc, nb, wp);
-        else slice_pack<false, CLAMP, 0>(q, G, dmax, codes, lens, w0, nb0, acc, nb, wp);
-      }
+      BM_ENC_DISPATCH(slice_pack, q, G, dmax, tab, w0, nb0, acc, nb, wp);
       // every lane holds >= 32 bits, so the word of its last bits is the next
       // lane's first word (already stored, zeros in these bits); the last
       // lane's last word is its own
@@ -917,8 +1085,10 @@ __global__ void __launch_bounds__(WARPS * 32, 4) encode_fused_kernel(FusedEncode
       bool pending_head = head_partial;
       for (int t = 0; t < cnt; ++t) {
         const unsigned s = CLAMP ? min((unsigned)a.sym[s0 + t], dmax) : (unsigned)a.sym[s0 + t];
-        const unsigned L = lens[s];
-        acc = (acc << L) | (packed ? (codes[s] & 0x3FFFFFFu) : codes[s]);
+        unsigned c, L;
+        if (packed) code_of<true, true>(tab, s, c, L);
+        else code_of<false, true>(tab, s, c, L);
+        acc = (acc << L) | c;
         nb += L;
         if (nb >= 32u) {
           nb -= 32u;
@@ -951,26 +1121,40 @@ __global__ void encode_finish_kernel(unsigned long long raw_total, unsigned long
 // ---------------------------------------------------------------------------
 // Decoding
 // ---------------------------------------------------------------------------
+// Present symbols the decoder-table builder keeps in shared memory; more use
+// the global arrays of DecodeTables.
+constexpr int kDtSmemSyms = 8192;
+
 struct DtSmem {
-  uint8_t len[kMaxDict];
-  unsigned key32[kMaxDict];
-  uint16_t canon[kMaxDict];
+  uint8_t clen[kDtSmemSyms];    // code length of each present symbol (symbol order)
+  uint16_t csym[kDtSmemSyms];   // its symbol
+  uint16_t canon[kDtSmemSyms];  // present-symbol indices in canonical order
+  unsigned key32[kDtSmemSyms];  // the codebook section (when it fits), then counting scratch
   unsigned scan_tmp[64];
   CanonTables ct;
   unsigned rfirst[512], rcount[512], roff[512];
 };
 
 // Build decode tables from the stream's codebook runs (one CTA of
-// kCbThreads threads, DtSmem in its dynamic shared memory).
+// kCbThreads threads, DtSmem in its dynamic shared memory).  The runs list
+// the present symbols in symbol order: run q's t-th symbol is present symbol
+// (symbols of the runs before q) + t.
 __device__ __forceinline__ void decode_tables_block(const uint8_t* runs, unsigned long long nbytes,
                                                     unsigned long long n_runs, int dict, DecodeTables* out,
                                                     Scalars* sc, unsigned char* smem_raw) {
   DtSmem& S = *reinterpret_cast<DtSmem*>(smem_raw);
   __shared__ unsigned s_bad;
   __shared__ unsigned long long s_kr;
-  __shared__ unsigned s_total;
-  if (threadIdx.x == 0) { s_bad = 0; s_kr = 0; }
-  for (int s = threadIdx.x; s < dict; s += blockDim.x) S.len[s] = 0;
+  __shared__ unsigned s_total, s_n;
+  if (threadIdx.x == 0) { s_bad = 0; s_kr = 0; s_n = 0; }
+  // every present symbol takes at least one length byte after its run's
+  // 8-byte header: this bounds their count and picks the arrays
+  const unsigned long long nbound = nbytes > 8ull * n_runs ? nbytes - 8ull * n_runs : 0ull;
+  const bool small = nbound <= (unsigned long long)kDtSmemSyms;
+  const unsigned cap = small ? (unsigned)kDtSmemSyms : (unsigned)kMaxDict;
+  uint8_t* clen = small ? S.clen : out->big_clen;
+  uint16_t* csym = small ? S.csym : out->big_csym;
+  uint16_t* canon = small ? S.canon : out->big_canon;
   // the codebook section is walked serially: read it from shared memory when
   // it fits in the key scratch (free until build_canonical)
   const uint8_t* rbase = runs;
@@ -984,8 +1168,10 @@ __device__ __forceinline__ void decode_tables_block(const uint8_t* runs, unsigne
   }
   __syncthreads();
   // walk the run headers (serial, 512 at a time), then every thread copies
-  // lengths of the batch (rcount holds each run's first index in the batch)
+  // lengths and symbols of the batch (rcount holds each run's first index in
+  // the batch)
   unsigned long long off = 0;
+  unsigned prev_end = 0;  // runs must be ascending and must not overlap
   for (unsigned long long rb = 0; rb < n_runs; rb += 512) {
     const int nb = (int)min(512ull, n_runs - rb);
     if (threadIdx.x == 0) {
@@ -994,27 +1180,36 @@ __device__ __forceinline__ void decode_tables_block(const uint8_t* runs, unsigne
         if (off + 8 > nbytes) { s_bad = 1; break; }
         const unsigned first = *reinterpret_cast<const unsigned*>(rbase + off);
         const unsigned cnt = *reinterpret_cast<const unsigned*>(rbase + off + 4);
-        if ((unsigned long long)first + cnt > (unsigned long long)dict || off + 8 + cnt > nbytes) { s_bad = 1; break; }
+        if ((unsigned long long)first + cnt > (unsigned long long)dict || off + 8 + cnt > nbytes ||
+            (rb + q > 0 && first < prev_end) || (unsigned long long)s_n + tot + cnt > cap) {
+          s_bad = 1;
+          break;
+        }
         S.rfirst[q] = first; S.rcount[q] = tot; S.roff[q] = (unsigned)off;
         tot += cnt;
+        prev_end = first + cnt;
         off += 8ull + ((cnt + 3u) & ~3u);
       }
       s_total = tot;
     }
     __syncthreads();
     if (s_bad) break;
-    const unsigned tot = s_total;
+    const unsigned tot = s_total, base = s_n;
     for (unsigned e = threadIdx.x; e < tot; e += blockDim.x) {
       const int q = upper_bound_u32(S.rcount, 0, nb, e) - 1;
       const unsigned t = e - S.rcount[q];
-      S.len[S.rfirst[q] + t] = rbase[S.roff[q] + 8 + t];
+      clen[base + e] = rbase[S.roff[q] + 8 + t];
+      csym[base + e] = (uint16_t)(S.rfirst[q] + t);
     }
     __syncthreads();
+    if (threadIdx.x == 0) s_n = base + tot;
+    __syncthreads();
   }
+  const int n = (int)s_n;
   // Kraft sum (exact, in units of 2^-32) and the length bound
   unsigned long long kr = 0;
-  for (int s = threadIdx.x; s < dict; s += blockDim.x) {
-    const unsigned L = S.len[s];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const unsigned L = clen[i];
     if (L > (unsigned)kMaxLen) s_bad = 1;
     else if (L) kr += 1ull << (32 - L);
   }
@@ -1028,8 +1223,8 @@ __device__ __forceinline__ void decode_tables_block(const uint8_t* runs, unsigne
     if (threadIdx.x == 0) atomicOr(&sc->status, ST_CORRUPT);
     return;
   }
-  build_canonical(S.len, dict, S.key32, S.canon, &S.ct, S.scan_tmp);
-  for (int i = threadIdx.x; i < (int)S.ct.n; i += blockDim.x) out->canon[i] = S.canon[i];
+  build_canonical(clen, n, S.key32, canon, &S.ct);
+  for (int i = threadIdx.x; i < (int)S.ct.n; i += blockDim.x) out->canon[i] = csym[canon[i]];
   __syncthreads();
   // every LUT entry from its own bits: the length is the first whose
   // left-justified limit lies above them (canonical order), the symbol that
@@ -1041,7 +1236,7 @@ __device__ __forceinline__ void decode_tables_block(const uint8_t* runs, unsigne
     unsigned e = 0;
     if (L <= (unsigned)kLutBits) {
       const unsigned idx = S.ct.first_pos[L] + (((unsigned)peek >> (32 - L)) - S.ct.first_code[L]);
-      if (idx < S.ct.n) e = (unsigned)S.canon[idx] | (L << 16);
+      if (idx < S.ct.n) e = (unsigned)csym[canon[idx]] | (L << 16);
     }
     out->lut[p] = e;
   }

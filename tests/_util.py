@@ -105,7 +105,7 @@ def coef_tol(u):
     return (1e-5 if u.dtype == np.float32 else 1e-12) * float(np.abs(u).max())
 
 
-def check_stream_parity(bm, u, sg, tol, mode, B, K, M, roi=None, label="", dev="cuda:0"):
+def check_stream_parity(bm, u, sg, tol, mode, B, K, M, roi=None, label="", dev="cuda:0", radius=32768):
     """A GPU stream sg of field u against the oracle's stream of the same
     field and arguments: raw decision, the L-inf bound at every node of every
     region (GPU decode), header fields and the tier / q tables bit-exact,
@@ -117,7 +117,7 @@ def check_stream_parity(bm, u, sg, tol, mode, B, K, M, roi=None, label="", dev="
 
     shape = u.shape
     f64 = u.dtype == np.float64
-    so, co = oracle.compress(u, tol, rel=(mode == "rel"), roi=roi, B=B, K=K, M=M, want_codes=True)
+    so, co = oracle.compress(u, tol, rel=(mode == "rel"), roi=roi, B=B, K=K, M=M, radius=radius, want_codes=True)
     hg, ho = oracle.stream_header(sg), oracle.stream_header(so)
     assert hg["raw"] == ho["raw"]
     d = bm.decompress(torch.from_numpy(sg).to(dev)).cpu().numpy().astype(np.float64)
@@ -142,7 +142,8 @@ def check_stream_parity(bm, u, sg, tol, mode, B, K, M, roi=None, label="", dev="
     gate = hard_gate(cg, cgpu, q, f64)
     worst = float((err / np.maximum(tau, np.finfo(np.float64).tiny)).max())
     record(test="compress_parity", label=label, shape=list(shape), dtype=str(u.dtype), B=B, K=K, M=M, tol=tol,
-           mode=mode, n_tiers=ho["n_tiers"], hard_gate_mismatches=gate, max_err_over_tau=worst,
+           mode=mode, radius=radius, n_tiers=ho["n_tiers"], n_outliers=ho["n_outliers"],
+           hard_gate_mismatches=gate, max_err_over_tau=worst,
            cr=float(u.nbytes) / sg.size, **fc)
     assert gate == 0, gate
     assert fc["unexplained"] == 0, fc

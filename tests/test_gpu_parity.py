@@ -85,10 +85,10 @@ def test_recompose_matches_oracle(bm, case):
     assert np.abs(g.astype(np.float64) - u).max() <= 8 * _coef_tol(u)
 
 
-def _check_compress_parity(bm, u, tol, mode, B, K, M, roi=None, label=""):
+def _check_compress_parity(bm, u, tol, mode, B, K, M, roi=None, label="", radius=32768):
     t = torch.from_numpy(u).to(DEV)
-    sg = bm.compress(t, tol, mode=mode, roi=roi, block=B, levels=K, global_levels=M).cpu().numpy()
-    return check_stream_parity(bm, u, sg, tol, mode, B, K, M, roi=roi, label=label, dev=DEV)
+    sg = bm.compress(t, tol, mode=mode, roi=roi, block=B, levels=K, global_levels=M, radius=radius).cpu().numpy()
+    return check_stream_parity(bm, u, sg, tol, mode, B, K, M, roi=roi, label=label, dev=DEV, radius=radius)
 
 
 @pytest.mark.parametrize("tol", [1e-2, 1e-4])
@@ -114,15 +114,46 @@ def _smooth_with_spikes(shape, dtype):
     return np.ascontiguousarray(u.astype(dtype))
 
 
+@pytest.mark.parametrize("radius", [4096, 32768])
 @pytest.mark.parametrize("dt,B,K,M", [(np.float32, 17, 2, 2), (np.float32, 9, 3, 1), (np.float64, 9, 2, 2)])
-def test_wide_code_parity(bm, dt, B, K, M):
+def test_wide_code_parity(bm, dt, B, K, M, radius):
     """Escapes in groups with and without codes beyond 16 bits (the block
     kernels stage codes in 16 bits and send wider ones straight to the escape
-    array), against the oracle."""
+    array), against the oracle, with a small dictionary (escapes below 2^15)
+    and the full 16-bit one."""
     u = _smooth_with_spikes((40, 37, 45), dt)
-    co = _check_compress_parity(bm, u, 1e-4, "abs", B, K, M, label="spikes")
+    co = _check_compress_parity(bm, u, 1e-4, "abs", B, K, M, label="spikes_r%d" % radius, radius=radius)
     assert co is not None
-    assert int((np.abs(co) >= 32767).sum()) > 0 and int(((np.abs(co) >= 4096) & (np.abs(co) < 32767)).sum()) > 0
+    assert int((np.abs(co) >= 32768).sum()) > 0
+    assert int(((np.abs(co) >= radius) & (np.abs(co) < 32767)).sum()) > 0 or radius == 32768
+    assert int(((np.abs(co) >= 4096) & (np.abs(co) < 32767)).sum()) > 0
+
+
+@pytest.mark.parametrize("radius", [4096, 32768])
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+def test_codes_at_the_dictionary_edge(bm, dt, radius):
+    """Codes exactly at and around the largest 16-bit symbol: isolated spikes
+    on level-one detail nodes (all coarse neighbours zero, so the coefficient
+    is the spike itself) sized to give codes of +-(2^15 - 2) .. +-(2^15 + 1)
+    and far beyond; the stream must match the oracle's (code 2^15 - 1 is
+    symbol 2^16 - 1 with the full dictionary, code 2^15 escapes)."""
+    B, K, M = 9, 1, 0
+    shape = (36, 27, 27)
+    tol = 1e-3
+    u = np.zeros(shape, dtype=np.float64)
+    targets = [32766, 32767, 32768, 32769, -32766, -32767, -32768, -32769, 40000, -100000, 5, -7]
+    # the widths depend on max|u| through the round-off margin: iterate to the fixed point
+    q, _, _ = oracle.budget(shape, B, K, M, [tol], 1.0, dt == np.float64)
+    for _ in range(5):
+        q, _, _ = oracle.budget(shape, B, K, M, [tol], float(dt(100000 * q[0])), dt == np.float64)
+    for i, code in enumerate(targets):  # node (1,1,1) of block i along dims 0..2
+        b0, b1 = divmod(i, 3)
+        u[9 * b0 + 1, 9 * b1 + 1, 1] = code * q[0]
+    u = np.ascontiguousarray(u.astype(dt))
+    co = _check_compress_parity(bm, u, tol, "abs", B, K, M, label="edge_r%d" % radius, radius=radius)
+    assert co is not None
+    for code in targets:
+        assert code in set(int(c) for c in co), code
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
@@ -143,6 +174,11 @@ def test_gpu_decodes_oracle_stream(bm, case):
 @pytest.mark.parametrize("scale,esc,chunk,dict_size", [
     (0.3, 0.0, 2048, 8192), (5.0, 0.001, 1024, 8192), (300.0, 0.01, 1536, 8192), (0.0, 0.0, 64, 64),
     (40.0, 0.0, 256, 1024), (2000.0, 0.0, 2048, 8192),
+    # the full 16-bit dictionary: present symbols within the encoder's window
+    # and the shared-memory codebook, spread over more than the window, and so
+    # many that the codebook and decoder tables take global scratch
+    (200.0, 0.002, 2048, 65536), (1500.0, 0.0, 1024, 65536), (6000.0, 0.001, 2048, 65536),
+    (30000.0, 0.0, 512, 65536),
 ])
 def test_huffman_bit_exact(bm, scale, esc, chunk, dict_size):
     sym = fields.laplace_symbols(300_007, dict_size // 2, scale, seed=17, escape_rate=esc)
