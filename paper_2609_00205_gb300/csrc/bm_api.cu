@@ -377,7 +377,7 @@ GSizes gsizes(const PlanHost& h) {
 }
 
 // cudaFuncAttributeMaxDynamicSharedMemorySize set once per device for a kernel.
-std::atomic<unsigned> g_cb_attr{0}, g_dt_attr{0}, g_dec_attr{0};
+std::atomic<unsigned> g_cb_attr{0}, g_dt_attr{0}, g_dec_attr{0}, g_encw_attr{0}, g_encc_attr{0};
 template <class F>
 cudaError_t set_smem_once(F* fn, int bytes, std::atomic<unsigned>& done) {
   int dev = 0;
@@ -390,11 +390,46 @@ cudaError_t set_smem_once(F* fn, int bytes, std::atomic<unsigned>& done) {
   return e;
 }
 
+// Preferred shared-memory carveout 0 (the most L1) for a kernel that keeps
+// a table in L1 rather than in shared memory, once per device.
+template <class F>
+cudaError_t prefer_l1_once(F* fn, std::atomic<unsigned>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned bit = 1u << (dev & 31);
+  if (done.load() & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  if (e == cudaSuccess) done.fetch_or(bit);
+  return e;
+}
+
 int grid_for(int64_t work, int threads, int per_sm = 8) {
   int64_t g = (work + threads - 1) / threads;
   const int64_t cap = (int64_t)num_sms() * per_sm;
   if (g > cap) g = cap;
   return (int)std::max<int64_t>(g, 1);
+}
+
+// Histogram of symbols [s0, s1) into hist (zeroed by the caller): with
+// `ctas` CTAs of the small-window kernel when the dictionary fits its window,
+// else one wide-window CTA per SM (at most `ctas`).  With `check`, symbols
+// not below dict are flagged in sc.
+std::atomic<unsigned> g_hw_attr{0};
+cudaError_t launch_hist(const uint16_t* sym, unsigned long long s0, unsigned long long s1, int dict, unsigned centre,
+                        unsigned* hist, Scalars* sc, bool check, int ctas, cudaStream_t s) {
+  if (dict <= kHistWin) {
+    if (check) hist_kernel<<<ctas, 256, 0, s>>>(sym + s0, s1 - s0, dict, hist, sc);
+    else hist_range_kernel<<<ctas, 256, 0, s>>>(sym, s0, s1, dict, centre, hist);
+  } else {
+    const int smem = 4 * hist_wide_bins(dict);
+    const cudaError_t e = set_smem_once(hist_wide_kernel, 4 * kHistWideMax, g_hw_attr);
+    if (e != cudaSuccess) return e;
+    const int grid = std::max(1, std::min(ctas, num_sms()));
+    hist_wide_kernel<<<grid, kHistWideThreads, smem, s>>>(sym, s0, s1, dict, centre, hist, check ? sc : nullptr);
+  }
+  g_launches.fetch_add(1);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -907,9 +942,7 @@ bm_status run_decompose(PlanDev& P, const T* field, int mode, const FwdOut<T>& o
     Stage st("global_histogram");
     const unsigned long long s0 = (unsigned long long)h.sym_off[0], s1 = (unsigned long long)h.n_coeffs;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(num_sms(), (int64_t)(s1 - s0) / 16384));
-    hist_range_kernel<<<grid, 256, 0, s>>>(o.sym, s0, s1, 2 * o.radius, (unsigned)o.radius, o.hist);
-    BM_LAUNCHED();
-    BM_CUDA(cudaGetLastError());
+    BM_CUDA(launch_hist(o.sym, s0, s1, 2 * o.radius, (unsigned)o.radius, o.hist, o.sc, false, grid, s));
   }
   return BM_OK;
 }
@@ -1167,7 +1200,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   Carver probe;
   carve_all(probe, nullptr);
   probe.take<Scalars>(1); probe.take<unsigned>(dict); probe.take<uint8_t>(dict); probe.take<unsigned>(dict);
-  probe.take<unsigned char>(cb_big_bytes());
+  probe.take<unsigned char>(cb_big_bytes()); probe.take<unsigned>(dict);
   probe.take<double>(L.nq); probe.take<T>(L.nq); probe.take<double>(ntiers); probe.take<uint8_t>(h.nblocks_all);
   probe.take<uint16_t>((size_t)h.n_coeffs); probe.take<int32_t>((size_t)h.n_coeffs);
   probe.take<unsigned char>(256 + 16ull * L.nch);
@@ -1181,6 +1214,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   uint8_t* lens = cv.take<uint8_t>(dict);
   unsigned* codes = cv.take<unsigned>(dict);
   unsigned char* cb_big = cv.take<unsigned char>(cb_big_bytes());
+  unsigned* packed = cv.take<unsigned>(dict);
   double* qd = cv.take<double>(L.nq);
   T* rq = cv.take<T>(L.nq);
   double* dtiers = cv.take<double>(ntiers);
@@ -1269,8 +1303,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     {
       Stage st("histogram", hs);
       const unsigned long long nloc = (unsigned long long)h.sym_off[0];  // the symbols of every round
-      hist_range_kernel<<<num_sms() * BM_HIST_CTAS, 256, 0, hs>>>(sym, 0, nloc, dict, (unsigned)prm.radius, hist);
-      BM_LAUNCHED();
+      BM_CUDA(launch_hist(sym, 0, nloc, dict, (unsigned)prm.radius, hist, sc, false, num_sms() * BM_HIST_CTAS, hs));
     }
     if (BM_HIST_OVERLAP) BM_CUDA(cudaEventRecord(ws->ev_join, ws->aux));
     return BM_OK;
@@ -1285,7 +1318,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   {
     Stage st("huffman_codebook");
     CodebookArgs ca{hist, dict, lens, codes, prefix_fits ? out : nullptr, L.off_codebook, cap, sc, 1, L.nch,
-                    raw_total, cb_big};
+                    raw_total, cb_big, packed};
     BM_CUDA(set_smem_once(codebook_kernel, (int)sizeof(CbSmem), g_cb_attr));
     codebook_kernel<<<1, kCbThreads, sizeof(CbSmem), s>>>(ca);
     BM_LAUNCHED();
@@ -1295,12 +1328,13 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     Stage st("huffman_encode");
     FusedEncodeArgs ea{};
     ea.sym = sym; ea.esc = esc; ea.n = (unsigned long long)h.n_coeffs; ea.chunk = prm.chunk;
-    ea.lens = lens; ea.codes = codes; ea.dict = dict; ea.nch = L.nch;
+    ea.lens = lens; ea.codes = codes; ea.packed = packed; ea.dict = dict; ea.nch = L.nch;
     ea.ticket = reinterpret_cast<unsigned*>(tickets); ea.st = lb_status;
     ea.chunk_words = reinterpret_cast<unsigned*>(out + L.off_chunks);
     ea.splits = reinterpret_cast<uint16_t*>(out + L.off_splits);
     ea.out = out; ea.capacity = cap; ea.sc = sc;
-    encode_fused_kernel<8, false, false><<<grid_for((int64_t)L.nch * 32, 256, 4), 256, 0, s>>>(ea);
+    BM_CUDA(prefer_l1_once(encode_fused_kernel<8, false, true>, g_encw_attr));
+    encode_fused_kernel<8, false, false><<<grid_for((int64_t)L.nch * 32, 256, 4), 256, enc_smem<false>(), s>>>(ea);
     encode_fused_kernel<8, false, true><<<grid_for((int64_t)L.nch * 32, 256, 4), 256, 0, s>>>(ea);
     g_launches.fetch_add(2);
   }
@@ -2237,7 +2271,7 @@ bm_status bm_huffman_encode(const uint16_t* d_symbols, uint64_t n, int dict_size
   Carver probe;
   probe.take<Scalars>(1); probe.take<unsigned>(dict_size); probe.take<uint8_t>(dict_size);
   probe.take<unsigned>(dict_size); probe.take<unsigned>(nch); probe.take<unsigned char>(256 + 16ull * nch);
-  probe.take<unsigned char>(cb_big_bytes());
+  probe.take<unsigned char>(cb_big_bytes()); probe.take<unsigned>(dict_size);
   Workspace* ws = nullptr;
   if (bm_status st = get_ws(s, probe.off + 4096, 4096, &ws)) return st;
   Carver cv;
@@ -2248,6 +2282,7 @@ bm_status bm_huffman_encode(const uint16_t* d_symbols, uint64_t n, int dict_size
   unsigned* codes = cv.take<unsigned>(dict_size);
   unsigned char* tickets = cv.take<unsigned char>(256 + 16ull * nch);
   unsigned char* cb_big = cv.take<unsigned char>(cb_big_bytes());
+  unsigned* packed = cv.take<unsigned>(dict_size);
   uint8_t* out = reinterpret_cast<uint8_t*>(d_out);
   BM_CUDA(cudaMemsetAsync(sc, 0, sizeof(Scalars), s));
   BM_CUDA(cudaMemsetAsync(hist, 0, 4ull * dict_size, s));
@@ -2255,12 +2290,12 @@ bm_status bm_huffman_encode(const uint16_t* d_symbols, uint64_t n, int dict_size
   BM_CUDA(cudaMemsetAsync(tickets, 0, 256 + 16ull * nch, s));
   {
     Stage st("huffman_histogram");
-    hist_kernel<<<grid_for((int64_t)n, 256, 4), 256, 0, s>>>(d_symbols, n, dict_size, hist, sc);
-    BM_LAUNCHED();
+    BM_CUDA(launch_hist(d_symbols, 0, n, dict_size, (unsigned)(dict_size / 2), hist, sc, true,
+                        grid_for((int64_t)n, 256, 4), s));
   }
   {
     Stage st("huffman_codebook");
-    CodebookArgs ca{hist, dict_size, lens, codes, out, off_cb, out_capacity, sc, 0, nch, ~0ull, cb_big};
+    CodebookArgs ca{hist, dict_size, lens, codes, out, off_cb, out_capacity, sc, 0, nch, ~0ull, cb_big, packed};
     BM_CUDA(set_smem_once(codebook_kernel, (int)sizeof(CbSmem), g_cb_attr));
     codebook_kernel<<<1, kCbThreads, sizeof(CbSmem), s>>>(ca);
     BM_LAUNCHED();
@@ -2274,7 +2309,13 @@ bm_status bm_huffman_encode(const uint16_t* d_symbols, uint64_t n, int dict_size
     ea.chunk_words = reinterpret_cast<unsigned*>(out); ea.out = out;
     ea.splits = reinterpret_cast<uint16_t*>(out + off_sp);
     ea.capacity = out_capacity; ea.sc = sc;
-    encode_fused_kernel<8, true, true><<<grid_for((int64_t)nch * 32, 256, 4), 256, 0, s>>>(ea);
+    ea.packed = packed;
+    if (dict_size <= kEncWin) {
+      encode_fused_kernel<8, true, false><<<grid_for((int64_t)nch * 32, 256, 4), 256, enc_smem<false>(), s>>>(ea);
+    } else {
+      BM_CUDA(prefer_l1_once(encode_fused_kernel<8, true, true>, g_encc_attr));
+      encode_fused_kernel<8, true, true><<<grid_for((int64_t)nch * 32, 256, 4), 256, 0, s>>>(ea);
+    }
     encode_finish_kernel<<<1, 32, 0, s>>>(~0ull, out_capacity, sc);
     zero_tail_kernel<<<1, 32, 0, s>>>(out, sc);
     g_launches.fetch_add(3);
@@ -2441,7 +2482,7 @@ extern "C" bm_status bm_huffman_encode_noalloc(const uint16_t* d_symbols, uint64
   ea.chunk_words = reinterpret_cast<unsigned*>(out); ea.out = out;
   ea.splits = reinterpret_cast<uint16_t*>(out + off_sp);
   ea.capacity = out_capacity; ea.sc = sc;
-  encode_fused_kernel<8, true, true><<<grid_for((int64_t)nch * 32, 256, 4), 256, 0, s>>>(ea);
+  encode_fused_kernel<8, true, false><<<grid_for((int64_t)nch * 32, 256, 4), 256, enc_smem<false>(), s>>>(ea);
   encode_finish_kernel<<<1, 32, 0, s>>>(~0ull, out_capacity, sc);
   zero_tail_kernel<<<1, 32, 0, s>>>(out, sc);
   g_launches.fetch_add(6);

@@ -20,6 +20,10 @@ constexpr int kLutBits = 14;
 // Entries of the code table the encoder keeps in shared memory (a window of
 // the dictionary; symbols outside it are looked up in the global table).
 constexpr int kEncWin = 8192;
+// Shared memory of the encoder: the window's codes and lengths; the variant
+// for wide code distributions (GLOB) keeps no table in shared memory.
+template <bool GLOB>
+__host__ __device__ constexpr size_t enc_smem() { return GLOB ? 0 : (size_t)kEncWin * 5; }
 // Every chunk is split into eight equal runs; the stream stores the bit
 // offsets of runs 1..7 so that eight decoders can work on one chunk.
 constexpr int kSplits = 8;
@@ -73,6 +77,31 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned v, unsigned* warp_t
   return before;
 }
 
+// Exclusive scan over the warps of a block of one count per warp (every lane
+// of a warp passes the same value); returns the sum of the warps before this
+// one to every lane, and the total in *total.  scan_tmp: 32 u32.
+__device__ __forceinline__ unsigned warp_excl_scan_block(unsigned v, unsigned* scan_tmp, unsigned* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) scan_tmp[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    const unsigned c = lane < nw ? scan_tmp[lane] : 0u;
+    unsigned x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane < nw) scan_tmp[lane] = x - c;
+    if (lane == 31 && total) *total = x;
+  }
+  __syncthreads();
+  const unsigned r = scan_tmp[wid];
+  __syncthreads();
+  return r;
+}
+
 // Per-warp running counts of a counting pass, stored by (digit, warp) with
 // the warp index swizzled by the digit so that the lanes of a warp reading
 // counts of different digits hit different banks.
@@ -104,13 +133,23 @@ __device__ int radix_sort_pairs(unsigned* ka, uint16_t* sa, unsigned* kb, uint16
     uint16_t* sout = cur ? sa : sb;
     for (int i = threadIdx.x; i < 256 * 32; i += blockDim.x) wcnt[i] = 0u;
     __syncthreads();
-    for (int r = 0; r < rows; ++r) {  // counting walk
-      const int i = wid * seg + r * 32 + lane;
-      const bool ok = i < n;
-      const unsigned d = ok ? (kin[i] >> shift) & 255u : 0u;
-      const unsigned m = __match_any_sync(0xffffffffu, ok ? d : 256u + (unsigned)lane);
-      if (ok && (m & ((1u << lane) - 1u)) == 0u) wcnt[wc_idx(d, wid)] += (unsigned)__popc(m);
-      __syncwarp();
+    for (int r0 = 0; r0 < rows; r0 += 8) {  // counting walk, eight rows' keys loaded ahead
+      unsigned kk[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int i = wid * seg + (r0 + t) * 32 + lane;
+        kk[t] = (r0 + t < rows && i < n) ? kin[i] : 0u;
+      }
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        if (r0 + t >= rows) break;
+        const int i = wid * seg + (r0 + t) * 32 + lane;
+        const bool ok = i < n;
+        const unsigned d = (kk[t] >> shift) & 255u;
+        const unsigned m = __match_any_sync(0xffffffffu, ok ? d : 256u + (unsigned)lane);
+        if (ok && (m & ((1u << lane) - 1u)) == 0u) wcnt[wc_idx(d, wid)] += (unsigned)__popc(m);
+        __syncwarp();
+      }
     }
     __syncthreads();
     // exclusive scan in (digit, warp) order: thread t owns entries 8t .. 8t+7
@@ -129,22 +168,34 @@ __device__ int radix_sort_pairs(unsigned* ka, uint16_t* sa, unsigned* kb, uint16
       pre += v[j];
     }
     __syncthreads();
-    for (int r = 0; r < rows; ++r) {  // scatter walk
-      const int i = wid * seg + r * 32 + lane;
-      const bool ok = i < n;
-      const unsigned key = ok ? kin[i] : 0u;
-      const unsigned d = (key >> shift) & 255u;
-      const unsigned m = __match_any_sync(0xffffffffu, ok ? d : 256u + (unsigned)lane);
-      const unsigned lt = m & ((1u << lane) - 1u);
-      const unsigned base = ok ? wcnt[wc_idx(d, wid)] : 0u;
-      if (ok) {
-        const unsigned dst = base + (unsigned)__popc(lt);
-        kout[dst] = key;
-        sout[dst] = sin[i];
+    for (int r0 = 0; r0 < rows; r0 += 8) {  // scatter walk, eight rows loaded ahead
+      unsigned kk[8];
+      uint16_t pp[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int i = wid * seg + (r0 + t) * 32 + lane;
+        const bool ok = r0 + t < rows && i < n;
+        kk[t] = ok ? kin[i] : 0u;
+        pp[t] = ok ? sin[i] : (uint16_t)0;
       }
-      __syncwarp();
-      if (ok && lt == 0u) wcnt[wc_idx(d, wid)] = base + (unsigned)__popc(m);
-      __syncwarp();
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        if (r0 + t >= rows) break;
+        const int i = wid * seg + (r0 + t) * 32 + lane;
+        const bool ok = i < n;
+        const unsigned d = (kk[t] >> shift) & 255u;
+        const unsigned m = __match_any_sync(0xffffffffu, ok ? d : 256u + (unsigned)lane);
+        const unsigned lt = m & ((1u << lane) - 1u);
+        const unsigned base = ok ? wcnt[wc_idx(d, wid)] : 0u;
+        if (ok) {
+          const unsigned dst = base + (unsigned)__popc(lt);
+          kout[dst] = kk[t];
+          sout[dst] = pp[t];
+        }
+        __syncwarp();
+        if (ok && lt == 0u) wcnt[wc_idx(d, wid)] = base + (unsigned)__popc(m);
+        __syncwarp();
+      }
     }
     __syncthreads();
     cur ^= 1;
@@ -177,6 +228,28 @@ __device__ __forceinline__ int warp_upper_bound_u32(const unsigned* a, int lo, i
   const unsigned m = __ballot_sync(0xffffffffu, lane < hi - lo && a[lo + lane] > v);
   return m ? lo + __ffs(m) - 1 : hi;
 }
+// Merge path split by the 32 lanes of a warp: the number of A elements among
+// the first d of merge(A[0..na), B[0..nb)) when A's element goes first on
+// equal weight, i.e. the first i in [max(0, d - nb), min(d, na)] with
+// A[i] > B[d - 1 - i] (a 32-ary search: each step probes 32 equal segments).
+__device__ __forceinline__ int warp_merge_split(const unsigned* A, int na, const unsigned* B, int nb, int d) {
+  const int lane = threadIdx.x & 31;
+  int lo = max(0, d - nb), hi = min(d, na);
+  auto after = [&](int i) { return A[i] > B[d - 1 - i]; };  // A[i] is not among the first d
+  while (hi - lo > 32) {
+    const int step = (hi - lo + 31) / 32;
+    const int p = min(lo + (lane + 1) * step, hi) - 1;
+    const unsigned m = __ballot_sync(0xffffffffu, after(p));
+    if (m == 0u) return hi;
+    const int f = __ffs(m) - 1;
+    const int nlo = lo + f * step;
+    hi = min(nlo + step, hi);
+    lo = nlo;
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, lane < hi - lo && after(lo + lane));
+  return m ? lo + __ffs(m) - 1 : hi;
+}
+
 __device__ __forceinline__ int lower_bound_u32(const unsigned* a, int lo, int hi, unsigned v) {
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
@@ -199,13 +272,22 @@ __device__ void build_canonical(const uint8_t* len, int n, unsigned* wcnt, uint1
   __syncthreads();
   const int rows = (n + kCbThreads - 1) / kCbThreads;
   const int seg = rows * 32;
-  for (int r = 0; r < rows; ++r) {
-    const int i = wid * seg + r * 32 + lane;
-    const unsigned L = i < n ? len[i] : 0u;
-    const bool ok = L != 0u && L <= (unsigned)kMaxLen;
-    const unsigned m = __match_any_sync(0xffffffffu, ok ? L : 64u + (unsigned)lane);
-    if (ok && (m & ((1u << lane) - 1u)) == 0u) wcnt[wc_idx(L, wid)] += (unsigned)__popc(m);
-    __syncwarp();
+  for (int r0 = 0; r0 < rows; r0 += 8) {
+    unsigned ll[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int i = wid * seg + (r0 + t) * 32 + lane;
+      ll[t] = (r0 + t < rows && i < n) ? len[i] : 0u;
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      if (r0 + t >= rows) break;
+      const unsigned L = ll[t];
+      const bool ok = L != 0u && L <= (unsigned)kMaxLen;
+      const unsigned m = __match_any_sync(0xffffffffu, ok ? L : 64u + (unsigned)lane);
+      if (ok && (m & ((1u << lane) - 1u)) == 0u) wcnt[wc_idx(L, wid)] += (unsigned)__popc(m);
+      __syncwarp();
+    }
   }
   __syncthreads();
   if (wid < kMaxLen) {  // length L = wid + 1: exclusive scan of its counts over the warps
@@ -239,17 +321,27 @@ __device__ void build_canonical(const uint8_t* len, int n, unsigned* wcnt, uint1
     ct->max_len = maxl;
   }
   __syncthreads();
-  for (int r = 0; r < rows; ++r) {
-    const int i = wid * seg + r * 32 + lane;
-    const unsigned L = i < n ? len[i] : 0u;
-    const bool ok = L != 0u && L <= (unsigned)kMaxLen;
-    const unsigned m = __match_any_sync(0xffffffffu, ok ? L : 64u + (unsigned)lane);
-    const unsigned lt = m & ((1u << lane) - 1u);
-    const unsigned base = ok ? wcnt[wc_idx(L, wid)] : 0u;
-    if (ok) canon[ct->first_pos[L] + base + (unsigned)__popc(lt)] = (uint16_t)i;
-    __syncwarp();
-    if (ok && lt == 0u) wcnt[wc_idx(L, wid)] = base + (unsigned)__popc(m);
-    __syncwarp();
+  for (int r0 = 0; r0 < rows; r0 += 8) {
+    unsigned ll[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int i = wid * seg + (r0 + t) * 32 + lane;
+      ll[t] = (r0 + t < rows && i < n) ? len[i] : 0u;
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      if (r0 + t >= rows) break;
+      const int i = wid * seg + (r0 + t) * 32 + lane;
+      const unsigned L = ll[t];
+      const bool ok = L != 0u && L <= (unsigned)kMaxLen;
+      const unsigned m = __match_any_sync(0xffffffffu, ok ? L : 64u + (unsigned)lane);
+      const unsigned lt = m & ((1u << lane) - 1u);
+      const unsigned base = ok ? wcnt[wc_idx(L, wid)] : 0u;
+      if (ok) canon[ct->first_pos[L] + base + (unsigned)__popc(lt)] = (uint16_t)i;
+      __syncwarp();
+      if (ok && lt == 0u) wcnt[wc_idx(L, wid)] = base + (unsigned)__popc(m);
+      __syncwarp();
+    }
   }
   __syncthreads();
 }
@@ -267,6 +359,7 @@ struct CodebookArgs {
   unsigned long long nch;        // chunks
   unsigned long long raw_total;  // size of the raw stream (~0: no raw fallback)
   unsigned char* big;            // global scratch for more than kCbSmemSyms present symbols (cb_big_bytes())
+  unsigned* packed;              // [dict] out (nullable): code | len << 26 when every code has at most 26 bits
 };
 
 // Present symbols the codebook keeps in shared memory; more use global
@@ -287,8 +380,7 @@ struct CbArrays {
   unsigned* iw;        // [n] internal weights
   IdT* parent;         // [2n]
   uint8_t* depth;      // [2n]
-  unsigned* wcnt;      // [256*32] sort counts (aliases merged + round_end in shared memory)
-  IdT* merged;         // [n] a round's consumed nodes in merged order
+  unsigned* wcnt;      // [256*32] sort counts (aliases round_end in shared memory)
   IdT* round_end;      // [n] internal nodes created up to the end of each round
   uint16_t* canon;     // [n] compact indices in canonical order (aliases iw)
   unsigned* run_start; // [n] compact index of each run's first symbol (aliases ka)
@@ -298,9 +390,9 @@ struct CbArrays {
 
 // Shared-memory layout for at most kCbSmemSyms present symbols (16-bit ids).
 struct CbSmem {
-  unsigned ka[kCbSmemSyms];                 // 32 KB
-  unsigned iw[kCbSmemSyms];                 // 32 KB (sort: kb; later canon)
-  unsigned wcnt[256 * 32];                  // 32 KB (rounds: merged u16[N] + round_end u16[N])
+  unsigned ka[kCbSmemSyms];                 // 32 KB  } global-scratch variant: a tile of the
+  unsigned iw[kCbSmemSyms];                 // 32 KB  } two queues (sort: kb; later canon)
+  unsigned wcnt[256 * 32];                  // 32 KB (rounds: round_end u16[N])
   uint16_t parent[2 * kCbSmemSyms];         // 32 KB (sort: sb)
   uint8_t depth[2 * kCbSmemSyms];           // 16 KB
   uint16_t sa[kCbSmemSyms];                 // 16 KB
@@ -314,8 +406,7 @@ static_assert(256 * 32 >= kCbSmemSyms, "run offsets over the sort counts");
 
 // Global scratch of the large variant: n <= kMaxDict present symbols, 32-bit ids.
 __host__ __device__ constexpr size_t cb_big_bytes() {
-  return (size_t)kMaxDict * (2 + 1 + 4 + 2 + 4 + 2 + 4 + 4 * 2 + 2 + 4 + 4 + 2) + 3 * 4 * ((size_t)kMaxDict + 1) +
-         256 * 32 * 4 + 16 * 256;
+  return (size_t)kMaxDict * (2 + 1 + 4 + 2 + 4 + 2 + 4 + 4 * 2 + 2 + 4 + 2) + 3 * 4 * (size_t)kMaxDict + 16 * 256;
 }
 
 __device__ __forceinline__ CbArrays<uint16_t> cb_small(CbSmem& S) {
@@ -323,8 +414,7 @@ __device__ __forceinline__ CbArrays<uint16_t> cb_small(CbSmem& S) {
   v.csym = S.csym; v.clen = S.clen; v.ka = S.ka; v.sa = S.sa;
   v.kb = S.iw; v.sb = S.parent; v.iw = S.iw; v.parent = S.parent; v.depth = S.depth;
   v.wcnt = S.wcnt;
-  v.merged = reinterpret_cast<uint16_t*>(S.wcnt);
-  v.round_end = reinterpret_cast<uint16_t*>(S.wcnt) + kCbSmemSyms;
+  v.round_end = reinterpret_cast<uint16_t*>(S.wcnt);
   v.canon = reinterpret_cast<uint16_t*>(S.iw);
   v.run_start = S.ka;
   v.run_end = S.iw;
@@ -332,7 +422,7 @@ __device__ __forceinline__ CbArrays<uint16_t> cb_small(CbSmem& S) {
   return v;
 }
 
-__device__ __forceinline__ CbArrays<unsigned> cb_big(unsigned char* g) {
+__device__ __forceinline__ CbArrays<unsigned> cb_big(unsigned char* g, unsigned* smem_wcnt) {
   auto take = [&](size_t bytes) {
     unsigned char* p = g;
     g += (bytes + 255) & ~size_t(255);
@@ -349,13 +439,12 @@ __device__ __forceinline__ CbArrays<unsigned> cb_big(unsigned char* g) {
   v.iw = reinterpret_cast<unsigned*>(take(4 * N));
   v.parent = reinterpret_cast<unsigned*>(take(4 * 2 * N));
   v.depth = take(2 * N);
-  v.merged = reinterpret_cast<unsigned*>(take(4 * N));
   v.round_end = reinterpret_cast<unsigned*>(take(4 * N));
   v.canon = reinterpret_cast<uint16_t*>(take(2 * N));
   v.run_start = reinterpret_cast<unsigned*>(take(4 * N));
   v.run_end = reinterpret_cast<unsigned*>(take(4 * N));
   v.run_off = reinterpret_cast<unsigned*>(take(4 * N));
-  v.wcnt = reinterpret_cast<unsigned*>(take(256 * 32 * 4));
+  v.wcnt = smem_wcnt;  // the counting passes stay in shared memory
   return v;
 }
 
@@ -363,9 +452,42 @@ __device__ __forceinline__ CbArrays<unsigned> cb_big(unsigned char* g) {
 // V.csym): Huffman lengths into V.clen.  The lengths are those of the
 // sequential two-queue construction; lengths above kMaxLen are avoided by
 // re-running on max(1, f >> t), t = 1, 2, ...
+// Ranks of a round's merged order handled per shared-memory tile by the
+// global-scratch variant.
+constexpr int kCbTile = 8192;
+static_assert(kCbTile == kCbSmemSyms, "a tile of each queue fills ka, then iw (adjacent)");
+
+// Pairs of the ranks [d0, d1) of merge(A[0..na), B[0..nb)) (A first on equal
+// weight), d0 even, whose first i0 = split(d0) ranks came from A: appends
+// the pairs' weights to iw at qe + rank/2 and sets the parents.  Ids: A[i] is
+// node aid0 + i, B[j] is node bid0 + j.
 template <typename IdT>
-__device__ void codebook_lengths(const CodebookArgs& a, CbArrays<IdT> V, int n, unsigned* scan_tmp) {
+__device__ __forceinline__ unsigned merge_pairs(const unsigned* A, int na, const unsigned* B, int nb, int d0, int d1,
+                                                int i, int aid0, int bid0, int qe, int rank0, unsigned* iw,
+                                                IdT* parent, int n) {
+  unsigned leaves = 0;
+  int j = d0 - i;
+  for (int d = d0; d < d1; d += 2) {
+    int id[2];
+    unsigned w[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      if (i < na && (j >= nb || A[i] <= B[j])) { w[t] = A[i]; id[t] = aid0 + i; ++i; ++leaves; }
+      else { w[t] = B[j]; id[t] = bid0 + j; ++j; }
+    }
+    const int k = (rank0 + d) >> 1;
+    iw[qe + k] = w[0] + w[1];
+    parent[id[0]] = (IdT)(n + qe + k);
+    parent[id[1]] = (IdT)(n + qe + k);
+  }
+  return leaves;
+}
+
+template <typename IdT>
+__device__ void codebook_lengths(const CodebookArgs& a, CbArrays<IdT> V, int n, unsigned* scan_tmp,
+                                 unsigned* stage) {
   __shared__ unsigned s_lp, s_qp, s_qe, s_pl, s_pq, s_leaves, s_rounds, s_maxd, s_maxk;
+  __shared__ int s_split;
   if (n <= 1) {
     if (n == 1 && threadIdx.x == 0) V.clen[0] = 1;
     __syncthreads();
@@ -406,15 +528,17 @@ __device__ void codebook_lengths(const CodebookArgs& a, CbArrays<IdT> V, int n, 
     // warp-wide searches of both sorted queues.
     int np_prev = 0;
     while (true) {
-      if (threadIdx.x < 32) {
-        if (threadIdx.x == 0 && np_prev) {
-          s_lp += s_leaves;
-          s_qp += 2 * np_prev - s_leaves;
-          s_qe += np_prev;
-          V.round_end[s_rounds++] = (IdT)s_qe;
-          s_leaves = 0;
-        }
-        __syncwarp();
+      if (threadIdx.x == 0 && np_prev) {
+        s_lp += s_leaves;
+        s_qp += 2 * np_prev - s_leaves;
+        s_qe += np_prev;
+        V.round_end[s_rounds++] = (IdT)s_qe;
+        s_leaves = 0;
+      }
+      __syncthreads();
+      // warps 0 and 1 find, side by side, how many leaves and how many
+      // internal nodes weigh at most X (both compute X)
+      if (threadIdx.x < 64) {
         unsigned lp = s_lp, qp = s_qp;
         const unsigned qe = s_qe;
         if (qe < (unsigned)(n - 1)) {
@@ -424,38 +548,67 @@ __device__ void codebook_lengths(const CodebookArgs& a, CbArrays<IdT> V, int n, 
             else w[t] = V.iw[qp++];
           }
           const unsigned X = w[0] + w[1];
-          const int pl = warp_upper_bound_u32(lw, (int)s_lp, n, X) - (int)s_lp;
-          const int pq = warp_upper_bound_u32(V.iw, (int)s_qp, (int)qe, X) - (int)s_qp;
-          if (threadIdx.x == 0) { s_pl = (unsigned)pl; s_pq = (unsigned)pq; }
+          if (threadIdx.x < 32) {
+            const int pl = warp_upper_bound_u32(lw, (int)s_lp, n, X) - (int)s_lp;
+            if (threadIdx.x == 0) s_pl = (unsigned)pl;
+          } else {
+            const int pq = warp_upper_bound_u32(V.iw, (int)s_qp, (int)qe, X) - (int)s_qp;
+            if (threadIdx.x == 32) s_pq = (unsigned)pq;
+          }
         }
       }
       __syncthreads();
       if (s_qe >= (unsigned)(n - 1)) break;
       const int lp = s_lp, qp = s_qp, qe = s_qe, pl = s_pl, pq = s_pq;
       const int npairs = (pl + pq) >> 1;
-      for (int e = threadIdx.x; e < pl + pq; e += blockDim.x) {
-        int rank, id;
-        if (e < pl) {
-          const int i = lp + e;
-          rank = e + (lower_bound_u32(V.iw, qp, qp + pq, lw[i]) - qp);
-          id = i;
-        } else {
-          const int j = qp + (e - pl);
-          rank = (e - pl) + (upper_bound_u32(lw, lp, lp + pl, V.iw[j]) - lp);
-          id = n + j;
-        }
-        if (rank < 2 * npairs) V.merged[rank] = (IdT)id;
-      }
-      __syncthreads();
+      // the first 2*npairs nodes of the merged order (leaf first on equal
+      // weight) pair up in order.  Merge path: thread t takes the ranks
+      // [d0, d1) (d0 even), finds how many of the first d0 are leaves by one
+      // binary search, then walks its ranks sequentially and forms its pairs.
+      const unsigned* A = lw + lp;
+      const unsigned* Bq = V.iw + qp;
+      const int T = 2 * npairs;
       unsigned leaves = 0;
-      for (int k = threadIdx.x; k < npairs; k += blockDim.x) {
-        const int x = (int)V.merged[2 * k], y = (int)V.merged[2 * k + 1];
-        const unsigned wx = x < n ? lw[x] : V.iw[x - n];
-        const unsigned wy = y < n ? lw[y] : V.iw[y - n];
-        V.iw[qe + k] = wx + wy;
-        V.parent[x] = (IdT)(n + qe + k);
-        V.parent[y] = (IdT)(n + qe + k);
-        leaves += (x < n) + (y < n);
+      if (stage == nullptr) {  // arrays in shared memory: one split per thread
+        const int seg = 2 * ((npairs + (int)blockDim.x - 1) / (int)blockDim.x);
+        const int d0 = min(T, (int)threadIdx.x * seg), d1 = min(T, d0 + seg);
+        if (d0 < d1) {
+          int lo = max(0, d0 - pq), hi = min(d0, pl);
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (A[mid] <= Bq[d0 - 1 - mid]) lo = mid + 1; else hi = mid;
+          }
+          leaves = merge_pairs<IdT>(A, pl, Bq, pq, d0, d1, lo, lp, n + qp, qe, 0, V.iw, V.parent, n);
+        }
+      } else {  // arrays in global memory: tiles of kCbTile ranks staged in shared memory
+        unsigned* sA = stage;
+        unsigned* sB = stage + kCbTile;
+        int ia = 0;
+        for (int tb = 0; tb < T; tb += kCbTile) {
+          const int te = min(T, tb + kCbTile);
+          if (threadIdx.x < 32) {
+            const int ib = warp_merge_split(A, pl, Bq, pq, te);
+            if (threadIdx.x == 0) s_split = ib;
+          }
+          __syncthreads();
+          const int ib = s_split, ja = tb - ia, jb = te - ib;
+          for (int k = threadIdx.x; k < ib - ia; k += blockDim.x) sA[k] = A[ia + k];
+          for (int k = threadIdx.x; k < jb - ja; k += blockDim.x) sB[k] = Bq[ja + k];
+          __syncthreads();
+          const int tl = te - tb, na = ib - ia, nb = jb - ja;
+          const int seg = 2 * ((tl / 2 + (int)blockDim.x - 1) / (int)blockDim.x);
+          const int d0 = min(tl, (int)threadIdx.x * seg), d1 = min(tl, d0 + seg);
+          if (d0 < d1) {
+            int lo = max(0, d0 - nb), hi = min(d0, na);
+            while (lo < hi) {
+              const int mid = (lo + hi) >> 1;
+              if (sA[mid] <= sB[d0 - 1 - mid]) lo = mid + 1; else hi = mid;
+            }
+            leaves += merge_pairs<IdT>(sA, na, sB, nb, d0, d1, lo, lp + ia, n + qp + ja, qe, tb, V.iw, V.parent, n);
+          }
+          ia = ib;
+          __syncthreads();
+        }
       }
       if (leaves) atomicAdd(&s_leaves, leaves);
       np_prev = npairs;
@@ -493,37 +646,54 @@ __device__ void codebook_emit(const CodebookArgs& a, CbArrays<IdT> V, int n, uns
   __shared__ unsigned s_total, s_nruns;
   __shared__ unsigned long long s_bits;
   if (threadIdx.x == 0) s_bits = 0;
-  // 4. canonical codes (wcnt of the counting pass in the free weight array)
-  build_canonical(V.clen, n, V.ka, V.canon, ct);
+  // 4. canonical codes (the counting pass in the sort counts' shared memory)
+  build_canonical(V.clen, n, V.wcnt, V.canon, ct);
+  const bool pk = a.packed && ct->max_len <= 26;
   for (int i = threadIdx.x; i < (int)ct->n; i += blockDim.x) {
     const int ci = V.canon[i];
-    const int L = V.clen[ci];
-    a.codes[V.csym[ci]] = ct->first_code[L] + (unsigned)(i - (int)ct->first_pos[L]);
+    const unsigned L = V.clen[ci];
+    const unsigned c = ct->first_code[L] + (unsigned)(i - (int)ct->first_pos[L]);
+    const unsigned sy = V.csym[ci];
+    a.codes[sy] = c;
+    if (pk) a.packed[sy] = c | (L << 26);
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) a.lens[V.csym[i]] = V.clen[i];
   // 5. codebook runs {u32 first, u32 count, u8 len[count], pad to 4}: a run
-  // starts at every present symbol whose predecessor is absent
+  // starts at every present symbol whose predecessor is absent.  Warp w walks
+  // its contiguous rows of 32 compact indices (coalesced loads): run starts
+  // by ballot, one scan over the warps, then each start's run index.
   unsigned* run_start = V.run_start;
   unsigned* run_end = V.run_end;
   unsigned* run_off = V.run_off;
-  const int per = (n + blockDim.x - 1) / blockDim.x;
-  const int s0 = threadIdx.x * per;
-  auto is_start = [&](int i) { return i == 0 || V.csym[i] != V.csym[i - 1] + 1; };
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int rows = (n + 31) / 32, rpw = (rows + nwarps - 1) / nwarps;
+  const int r0 = wid * rpw, r1 = min(rows, r0 + rpw);
+  auto start_mask = [&](int r) {
+    const int i = r * 32 + lane;
+    const bool st = i < n && (i == 0 || V.csym[i] != V.csym[i - 1] + 1);
+    return __ballot_sync(0xffffffffu, st);
+  };
   unsigned nst = 0;
-  for (int i = s0; i < s0 + per && i < n; ++i) nst += is_start(i);
-  unsigned r = block_excl_scan(nst, scan_tmp, &s_nruns);
-  for (int i = s0; i < s0 + per && i < n; ++i)
-    if (is_start(i)) run_start[r++] = (unsigned)i;
+  for (int r = r0; r < r1; ++r) nst += (unsigned)__popc(start_mask(r));
+  const unsigned rbase = warp_excl_scan_block(nst, scan_tmp, &s_nruns);
+  {
+    unsigned q = rbase;
+    for (int r = r0; r < r1; ++r) {
+      const unsigned m = start_mask(r);
+      if ((m >> lane) & 1u) run_start[q + (unsigned)__popc(m & ((1u << lane) - 1u))] = (unsigned)(r * 32 + lane);
+      q += (unsigned)__popc(m);
+    }
+  }
   __syncthreads();
   const int nruns = (int)s_nruns;
   for (int q = threadIdx.x; q < nruns; q += blockDim.x) run_end[q] = q + 1 < nruns ? run_start[q + 1] : (unsigned)n;
   __syncthreads();
   unsigned my_bytes = 0;
   const int rper = (nruns + blockDim.x - 1) / blockDim.x;
-  const int r0 = threadIdx.x * rper;
-  for (int q = r0; q < r0 + rper && q < nruns; ++q) my_bytes += 8u + (((run_end[q] - run_start[q]) + 3u) & ~3u);
+  const int q0 = threadIdx.x * rper;
+  for (int q = q0; q < q0 + rper && q < nruns; ++q) my_bytes += 8u + (((run_end[q] - run_start[q]) + 3u) & ~3u);
   unsigned off = block_excl_scan(my_bytes, scan_tmp, &s_total);
-  for (int q = r0; q < r0 + rper && q < nruns; ++q) {
+  for (int q = q0; q < q0 + rper && q < nruns; ++q) {
     run_off[q] = off;
     off += 8u + (((run_end[q] - run_start[q]) + 3u) & ~3u);
   }
@@ -538,10 +708,17 @@ __device__ void codebook_emit(const CodebookArgs& a, CbArrays<IdT> V, int n, uns
       *reinterpret_cast<unsigned*>(p + 4) = cntq;
       for (unsigned t = cntq; t < ((cntq + 3u) & ~3u); ++t) p[8 + t] = 0;
     }
-    // length bytes: compact index i of run q goes to run_off[q] + 8 + (i - run_start[q])
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const int q = upper_bound_u32(run_start, 0, nruns, (unsigned)i) - 1;
-      a.out[a.off + run_off[q] + 8 + (i - run_start[q])] = V.clen[i];
+    // length bytes: compact index i of run q goes to run_off[q] + 8 + (i -
+    // run_start[q]), q = (run starts up to i) - 1, from the same row walk
+    unsigned q = rbase;
+    for (int r = r0; r < r1; ++r) {
+      const unsigned m = start_mask(r);
+      const int i = r * 32 + lane;
+      if (i < n) {
+        const unsigned qi = q + (unsigned)__popc(m & ((2u << lane) - 1u)) - 1u;
+        a.out[a.off + run_off[qi] + 8 + (i - run_start[qi])] = V.clen[i];
+      }
+      q += (unsigned)__popc(m);
     }
     if (threadIdx.x == 0)
       for (unsigned long long t = total; t < pad8(total); ++t) a.out[a.off + t] = 0;
@@ -568,7 +745,7 @@ __device__ void codebook_emit(const CodebookArgs& a, CbArrays<IdT> V, int n, uns
       sc->enc_lo = a.dict <= kEncWin ? 0u : min(smin, (unsigned)(a.dict - kEncWin));
       sc->enc_full = 1;
     } else {
-      sc->enc_lo = (unsigned)max(0, min(a.dict / 2 - kEncWin / 2, a.dict - kEncWin));
+      sc->enc_lo = 0;
       sc->enc_full = 0;
     }
     if (a.out && !fits) atomicOr(&sc->status, ST_CAPACITY | ST_RAW);
@@ -597,26 +774,66 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(CodebookArgs a) {
   for (int s = threadIdx.x; s < dict; s += blockDim.x) {
     a.lens[s] = 0;
     a.codes[s] = 0;
+    if (a.packed) a.packed[s] = 0;
   }
-  // present symbols, in symbol order, compacted (each thread a contiguous slice)
-  const int per = (dict + blockDim.x - 1) / blockDim.x;
-  const int s0 = threadIdx.x * per;
+  // present symbols, in symbol order, compacted: warp w walks its contiguous
+  // rows of 32 symbols (coalesced loads, eight rows in flight), counting by
+  // ballot; one scan over the warps; a second walk writes each present
+  // symbol at its warp's offset plus its rank in the row
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int rows = (dict + 31) / 32, rpw = (rows + nwarps - 1) / nwarps;
+  const int r0 = wid * rpw, r1 = min(rows, r0 + rpw);
   unsigned cnt = 0;
-  for (int s = s0; s < s0 + per && s < dict; ++s) cnt += a.hist[s] ? 1u : 0u;
-  unsigned pos = block_excl_scan(cnt, S.scan_tmp, &s_n);
+  for (int r = r0; r < r1; r += 8) {
+    unsigned f[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int s = (r + k) * 32 + lane;
+      f[k] = (r + k < r1 && s < dict) ? a.hist[s] : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) cnt += (unsigned)__popc(__ballot_sync(0xffffffffu, f[k] != 0u));
+  }
+  if (lane == 0) S.scan_tmp[32 + wid] = cnt;
+  __syncthreads();
+  if (wid == 0) {
+    const unsigned c = lane < nwarps ? S.scan_tmp[32 + lane] : 0u;
+    unsigned x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane < nwarps) S.scan_tmp[lane] = x - c;
+    if (lane == 31) s_n = x;
+  }
+  __syncthreads();
   const int n = (int)s_n;
   const bool small = n <= kCbSmemSyms;
-  uint16_t* csym = small ? S.csym : cb_big(a.big).csym;
-  for (int s = s0; s < s0 + per && s < dict; ++s)
-    if (a.hist[s]) csym[pos++] = (uint16_t)s;
+  uint16_t* csym = small ? S.csym : cb_big(a.big, S.wcnt).csym;
+  unsigned pos = S.scan_tmp[wid];
+  for (int r = r0; r < r1; r += 8) {
+    unsigned f[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int s = (r + k) * 32 + lane;
+      f[k] = (r + k < r1 && s < dict) ? a.hist[s] : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const unsigned m = __ballot_sync(0xffffffffu, f[k] != 0u);
+      if (f[k]) csym[pos + (unsigned)__popc(m & ((1u << lane) - 1u))] = (uint16_t)((r + k) * 32 + lane);
+      pos += (unsigned)__popc(m);
+    }
+  }
   __syncthreads();
   if (small) {
     const CbArrays<uint16_t> V = cb_small(S);
-    codebook_lengths<uint16_t>(a, V, n, S.scan_tmp);
+    codebook_lengths<uint16_t>(a, V, n, S.scan_tmp, nullptr);
     codebook_emit<uint16_t>(a, V, n, S.scan_tmp, &S.ct);
   } else {
-    const CbArrays<unsigned> V = cb_big(a.big);
-    codebook_lengths<unsigned>(a, V, n, S.scan_tmp);
+    const CbArrays<unsigned> V = cb_big(a.big, S.wcnt);
+    codebook_lengths<unsigned>(a, V, n, S.scan_tmp, S.ka);  // S.ka and S.iw (adjacent) stage the tiles
     codebook_emit<unsigned>(a, V, n, S.scan_tmp, &S.ct);
   }
 }
@@ -670,6 +887,7 @@ __global__ void __launch_bounds__(256) hist_range_kernel(const uint16_t* __restr
   unsigned cnt[NC];
 #pragma unroll
   for (int j = 0; j < NC; ++j) cnt[j] = 0;
+  unsigned n_esc = 0;  // the escape symbol 0: outside the window for large dictionaries, and frequent
   const unsigned lo = centre_sym - (NC / 2);
   auto bin = [&](unsigned s, unsigned c) {
     const unsigned k = s - wlo;
@@ -685,7 +903,8 @@ __global__ void __launch_bounds__(256) hist_range_kernel(const uint16_t* __restr
     const unsigned d = s - lo;
 #pragma unroll
     for (int j = 0; j < NC; ++j) cnt[j] += d == (unsigned)j;
-    if (d >= (unsigned)NC) bin(s, 1u);
+    n_esc += s == 0u;
+    if (d >= (unsigned)NC && s != 0u) bin(s, 1u);
   };
   const unsigned long long a0 = min(s1, (s0 + 7) & ~7ull);  // 16-byte aligned start
   const unsigned long long tid = blockIdx.x * 256ull + threadIdx.x, nth = gridDim.x * 256ull;
@@ -717,9 +936,85 @@ __global__ void __launch_bounds__(256) hist_range_kernel(const uint16_t* __restr
     for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if (BM_HIST_METHOD != 0 && (threadIdx.x & 31) == 0 && c) bin(lo + j, c);
   }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) n_esc += __shfl_xor_sync(0xffffffffu, n_esc, o);
+  if ((threadIdx.x & 31) == 0 && n_esc) bin(0u, n_esc);
   __syncthreads();
   for (int i = threadIdx.x; i < (int)wn; i += blockDim.x)
     if (hs[i]) atomicAdd(hist + wlo + i, hs[i]);
+}
+
+// Histogram of a symbol range [s0, s1) for dictionaries larger than the
+// small window: one CTA of kHistWideThreads threads per SM keeps a private
+// window of hist_wide_bins(dict) bins centred on the centre symbol (as much
+// of the dictionary as fits in shared memory: at most kHistWideMax bins) and
+// counts with shared atomics; symbols outside it (thin tails of very wide
+// code distributions) go to global atomics; the centre and the escape symbol
+// 0 are counted in registers.  Symbols not below dict are flagged (sc, when
+// given).  Measured on GB300 faster than spreading the whole dictionary over
+// a thread-block cluster in distributed shared memory (remote reductions on
+// the frequent bins serialise at their owner).
+constexpr int kHistWideThreads = 1024;
+constexpr int kHistWideMax = 49152;
+__host__ __device__ constexpr int hist_wide_bins(int dict) { return dict < kHistWideMax ? dict : kHistWideMax; }
+
+__global__ void __launch_bounds__(kHistWideThreads)
+    hist_wide_kernel(const uint16_t* __restrict__ sym, unsigned long long s0, unsigned long long s1, int dict,
+                     unsigned centre_sym, unsigned* hist, Scalars* sc) {
+  extern __shared__ __align__(16) unsigned hw[];
+  const int W = hist_wide_bins(dict);
+  const unsigned wlo = (unsigned)max(0, min((int)centre_sym - W / 2, dict - W));
+  for (int i = threadIdx.x; i < W; i += blockDim.x) hw[i] = 0;
+  __syncthreads();
+  unsigned n_centre = 0, n_esc = 0;
+  bool bad = false;
+  auto count = [&](unsigned s) {
+    n_centre += s == centre_sym;
+    n_esc += s == 0u;
+    if (s == centre_sym || s == 0u) return;
+    const unsigned k = s - wlo;
+    if (k < (unsigned)W) atomicAdd(hw + k, 1u);
+    else if (s < (unsigned)dict) atomicAdd(hist + s, 1u);
+    else bad = true;
+  };
+  const unsigned long long a0 = min(s1, (s0 + 7) & ~7ull);  // 16-byte aligned start
+  const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+  const unsigned long long nth = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = s0 + tid; i < a0; i += nth) count(sym[i]);
+  const unsigned long long nv = (s1 - a0) / 8;
+  const uint4* pv = reinterpret_cast<const uint4*>(sym + a0);
+  constexpr int NF = 4;
+  for (unsigned long long v = tid; v < nv; v += NF * nth) {
+    uint4 q[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const unsigned long long vf = v + f * nth;
+      q[f] = vf < nv ? __ldg(pv + vf) : make_uint4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      if (v + f * nth >= nv) break;
+      const unsigned w4[4] = {q[f].x, q[f].y, q[f].z, q[f].w};
+#pragma unroll
+      for (int h = 0; h < 4; ++h) { count(w4[h] & 0xFFFFu); count(w4[h] >> 16); }
+    }
+  }
+  for (unsigned long long i = a0 + nv * 8 + tid; i < s1; i += nth) count(sym[i]);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    n_centre += __shfl_xor_sync(0xffffffffu, n_centre, o);
+    n_esc += __shfl_xor_sync(0xffffffffu, n_esc, o);
+  }
+  if ((threadIdx.x & 31) == 0) {  // the window always holds the centre (it is centred on it, or holds all)
+    if (n_centre) atomicAdd(hw + (centre_sym - wlo), n_centre);
+    if (n_esc) atomicAdd(hist, n_esc);
+  }
+  if (bad && sc) atomicOr(&sc->status, ST_CORRUPT);
+  __syncthreads();
+  for (int i = threadIdx.x; i < W; i += blockDim.x) {
+    const unsigned v = hw[i];
+    if (v) atomicAdd(hist + wlo + i, v);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -743,6 +1038,7 @@ struct FusedEncodeArgs {
   int chunk;                     // multiple of 32
   const uint8_t* lens;
   const unsigned* codes;
+  const unsigned* packed;        // code | len << 26 per symbol (written by the codebook), or null
   int dict;
   unsigned long long nch;
   unsigned* ticket;              // zeroed before launch
@@ -767,36 +1063,55 @@ __device__ __forceinline__ unsigned sym_of(const uint4* q, int i) {
   return (i & 1) ? (w >> 16) : (w & 0xFFFFu);
 }
 
-// The encoder's code table: a window of kEncWin entries in shared memory
-// (sc: code, or code | len << 26 when every code has at most 26 bits; sl:
-// length) starting at symbol `lo`, and the whole table in global memory for
-// symbols outside the window (WIN = true; with WIN = false every symbol is
-// known to lie in the window).
+// The encoder's code table: with GLOB = false, a window of kEncWin entries
+// in shared memory (sc: code, or code | len << 26 when every code has at most
+// 26 bits; sl: length) starting at symbol `lo` that holds every symbol met;
+// with GLOB = true (code distributions wider than the window) the whole table
+// in global memory, read through L1 (gp: packed entries, or gc / gl), and the
+// escape symbol 0's entry in registers.
 struct EncTab {
   const unsigned* sc;
   const uint8_t* sl;
   unsigned lo;
   const unsigned* gc;
   const uint8_t* gl;
+  const unsigned* gp;
+  unsigned c0, l0;  // code and length of symbol 0
 };
 
-template <bool PACKED, bool WIN>
+template <bool PACKED, bool GLOB>
 __device__ __forceinline__ void code_of(const EncTab& t, unsigned s, unsigned& c, unsigned& L) {
-  const unsigned k = s - t.lo;
-  if (!WIN || k < (unsigned)kEncWin) {
+  if (!GLOB) {
+    const unsigned k = s - t.lo;
     const unsigned cw = t.sc[k];
     if (PACKED) { c = cw & 0x3FFFFFFu; L = cw >> 26; }
     else { c = cw; L = t.sl[k]; }
+  } else if (s == 0u) {
+    c = t.c0;
+    L = t.l0;
+  } else if (PACKED) {
+    const unsigned cw = __ldg(t.gp + s);
+    c = cw & 0x3FFFFFFu;
+    L = cw >> 26;
   } else {
     c = __ldg(t.gc + s);
     L = __ldg(t.gl + s);
   }
 }
-template <bool PACKED, bool WIN>
+template <bool PACKED, bool GLOB>
 __device__ __forceinline__ unsigned len_of(const EncTab& t, unsigned s) {
-  const unsigned k = s - t.lo;
-  if (!WIN || k < (unsigned)kEncWin) return PACKED ? (t.sc[k] >> 26) : (unsigned)t.sl[k];
-  return __ldg(t.gl + s);
+  if (!GLOB) return PACKED ? (t.sc[s - t.lo] >> 26) : (unsigned)t.sl[s - t.lo];
+  if (s == 0u) return t.l0;
+  return PACKED ? (__ldg(t.gp + s) >> 26) : (unsigned)__ldg(t.gl + s);
+}
+
+// Symbols of a slice, streamed past L1 (the global code table of the GLOB
+// variant keeps L1 to itself).
+__device__ __forceinline__ uint4 ld_stream(const uint4* p) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+  return v;
 }
 
 // Bits and escape mask of a lane's vector slice (G groups held in registers).
@@ -876,10 +1191,11 @@ __device__ __forceinline__ void slice_pack(const uint4* q, int G, unsigned dmax,
     }                                                                                   \
   } while (0)
 
-// Two instantiations per symbol source: WIN = false when the codebook found
-// every present symbol inside the shared-memory window (sc->enc_full), WIN =
-// true otherwise (lookups outside the window go to the global table).  Both
-// are launched; the one that does not match returns at once.
+// Two instantiations per symbol source: WIN = false when every symbol met
+// lies in the shared-memory window, WIN = true (the GLOB table) otherwise.
+// For the compressor's own symbols (CLAMP = false) the codebook decided
+// (sc->enc_full) and both are launched, the one that does not match returning
+// at once; for caller-supplied symbols the host picks by dictionary size.
 // Warps take chunks in ticket order.  A warp codes its chunk's bit count from
 // the symbols it holds in registers, publishes the chunk's (words, escapes)
 // aggregate, walks back over its predecessors until one has published an
@@ -889,25 +1205,25 @@ __device__ __forceinline__ void slice_pack(const uint4* q, int G, unsigned dmax,
 // earlier lane's last bits.
 template <int WARPS, bool CLAMP, bool WIN>
 __global__ void __launch_bounds__(WARPS * 32, 4) encode_fused_kernel(FusedEncodeArgs a) {
-  __shared__ uint8_t lens[kEncWin];
-  __shared__ unsigned codes[kEncWin];
+  extern __shared__ __align__(16) unsigned char enc_smem_raw[];
+  constexpr int WN = WIN ? 0 : kEncWin;
+  unsigned* codes = reinterpret_cast<unsigned*>(enc_smem_raw);           // [WN]
+  uint8_t* lens = enc_smem_raw + 4 * WN;                                  // [WN]
   Scalars* sc = a.sc;
   if (sc->skip) return;  // the stream is already known to be a raw copy
-  // caller-supplied symbols (CLAMP) may be absent from the table: they always
-  // take the variant with the global fallback
-  if (CLAMP ? !WIN : (WIN == (sc->enc_full != 0))) return;
+  if (!CLAMP && WIN == (sc->enc_full != 0)) return;
   // codes of at most 26 bits are packed with their length into one word
   // (code | len << 26): one shared-memory lookup per symbol in the window
-  const bool packed = sc->max_len <= 26;
+  const bool packed = sc->max_len <= 26 && (!WIN || a.packed != nullptr);
   const unsigned wlo = sc->enc_lo;
-  for (int i = threadIdx.x; i < kEncWin; i += blockDim.x) {
+  for (int i = threadIdx.x; i < WN; i += blockDim.x) {
     const unsigned s = wlo + (unsigned)i;
     const unsigned L = s < (unsigned)a.dict ? a.lens[s] : 0u;
     const unsigned c = s < (unsigned)a.dict ? a.codes[s] : 0u;
     lens[i] = (uint8_t)L;
     codes[i] = packed ? (c | (L << 26)) : c;
   }
-  const EncTab tab{codes, lens, wlo, a.codes, a.lens};
+  const EncTab tab{codes, lens, wlo, a.codes, a.lens, a.packed, a.codes[0], a.lens[0]};
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const unsigned dmax = (unsigned)(a.dict - 1);
@@ -932,7 +1248,8 @@ __global__ void __launch_bounds__(WARPS * 32, 4) encode_fused_kernel(FusedEncode
     // vector slices: whole groups of 8 symbols, 16-byte aligned, every lane
     // full with at least 32 symbols (so at least 32 bits: a word never has
     // more than two owners)
-    const bool warp_vec = __all_sync(0xffffffffu, (per & 7) == 0 && per >= 32 && cnt == per && (s0 & 7ull) == 0);
+    const bool warp_vec = __all_sync(0xffffffffu, (per & 7) == 0 && per >= 32 && cnt == per && (s0 & 7ull) == 0 &&
+                                                      (reinterpret_cast<uintptr_t>(a.sym) & 15) == 0);
     uint4 q[kEncGroups];
     // pass 1: bits and escapes of the slice
     unsigned bits = 0, nesc = 0;
@@ -940,14 +1257,15 @@ __global__ void __launch_bounds__(WARPS * 32, 4) encode_fused_kernel(FusedEncode
     if (warp_vec) {
       const uint4* p = reinterpret_cast<const uint4*>(a.sym + s0);
 #pragma unroll
-      for (int g = 0; g < kEncGroups; ++g) q[g] = g < G ? __ldg(p + g) : make_uint4(0, 0, 0, 0);
+      for (int g = 0; g < kEncGroups; ++g)
+        q[g] = g < G ? (WIN ? ld_stream(p + g) : __ldg(p + g)) : make_uint4(0, 0, 0, 0);
       // G is 8 at the default chunk of 2048 symbols: a fully unrolled slice
       BM_ENC_DISPATCH(slice_bits, q, G, dmax, tab, bits, emask);
       nesc = __popcll(emask);
     } else {
       for (int t = 0; t < cnt; ++t) {
         const unsigned s = CLAMP ? min((unsigned)a.sym[s0 + t], dmax) : (unsigned)a.sym[s0 + t];
-        bits += len_of<false, true>(tab, s);
+        bits += len_of<false, WIN>(tab, s);
         nesc += s == 0;
       }
     }
@@ -1086,8 +1404,8 @@ __global__ void __launch_bounds__(WARPS * 32, 4) encode_fused_kernel(FusedEncode
       for (int t = 0; t < cnt; ++t) {
         const unsigned s = CLAMP ? min((unsigned)a.sym[s0 + t], dmax) : (unsigned)a.sym[s0 + t];
         unsigned c, L;
-        if (packed) code_of<true, true>(tab, s, c, L);
-        else code_of<false, true>(tab, s, c, L);
+        if (packed) code_of<true, WIN>(tab, s, c, L);
+        else code_of<false, WIN>(tab, s, c, L);
         acc = (acc << L) | c;
         nb += L;
         if (nb >= 32u) {
