@@ -75,6 +75,8 @@ def lib():
         L.or_budget_r.argtypes = [P(i64), ci, ci, ci, ci, P(d), ci, d, ci, P(d), P(d)]
         L.or_compress_r.argtypes = [P(d), P(i64), ci, d, ci, P(d), ci, ci, ci, ci, ci, ci, P(u8), ctypes.c_uint64,
                                     P(ctypes.c_uint64), P(i64)]
+        L.or_compress_nd.argtypes = [P(d), P(i64), ci, ci, d, ci, P(d), ci, ci, ci, ci, ci, ci, P(u8),
+                                     ctypes.c_uint64, P(ctypes.c_uint64), P(i64)]
         _lib = L
     return _lib
 
@@ -89,7 +91,12 @@ def _check(rc):
 
 
 def _shape3(shape):
-    return np.ascontiguousarray(np.array(list(shape), dtype=np.int64))
+    """A shape of 1..3 dimensions as a 3-D shape with leading extents of 1 (the
+    missing dimensions are neither blocked nor coarsened)."""
+    s = [int(v) for v in shape]
+    if not 1 <= len(s) <= 3:
+        raise ValueError("fields have 1, 2 or 3 dimensions")
+    return np.ascontiguousarray(np.array([1] * (3 - len(s)) + s, dtype=np.int64))
 
 
 # ---------------------------------------------------------------------------
@@ -302,10 +309,10 @@ def compress(u, tol, rel=True, roi=None, B=9, K=1, M=2, chunk=2048, radius=32768
         assert roi_arr.size == p["nblocks"]
     codes = np.zeros(p["n_coeffs"], dtype=np.int64) if want_codes else None
     c = ctypes.c_double
-    rc = lib().or_compress_r(_ptr(u64, c), _ptr(_shape3(u64.shape), ctypes.c_int64), int(bool(f64)), float(tol),
-                             int(bool(rel)), _ptr(roi_arr, c) if roi_arr is not None else None, B, K, M, R, chunk,
-                             radius, _ptr(out, ctypes.c_uint8), cap, ctypes.byref(nbytes),
-                             _ptr(codes, ctypes.c_int64) if codes is not None else None)
+    rc = lib().or_compress_nd(_ptr(u64, c), _ptr(_shape3(u64.shape), ctypes.c_int64), u64.ndim, int(bool(f64)),
+                              float(tol), int(bool(rel)), _ptr(roi_arr, c) if roi_arr is not None else None, B, K, M,
+                              R, chunk, radius, _ptr(out, ctypes.c_uint8), cap, ctypes.byref(nbytes),
+                              _ptr(codes, ctypes.c_int64) if codes is not None else None)
     _check(rc)
     s = out[:nbytes.value].copy()
     return (s, codes) if want_codes else s
@@ -314,13 +321,15 @@ def compress(u, tol, rel=True, roi=None, B=9, K=1, M=2, chunk=2048, radius=32768
 def decompress(stream, want_codes=False):
     s = np.ascontiguousarray(np.asarray(stream, dtype=np.uint8))
     info = stream_header(s)
-    u = np.zeros(info["shape"])
+    u = np.zeros(info["shape"])  # the 3-D shape; reshaped to the field's own dimensions below
     codes = None
     if want_codes and not info["raw"]:
         codes = np.zeros(int(info["n_symbols"]), dtype=np.int64)
     _check(lib().or_decompress(_ptr(s, ctypes.c_uint8), s.size, _ptr(u, ctypes.c_double),
                                _ptr(codes, ctypes.c_int64) if codes is not None else None))
     u = u.astype(np.float64 if info["f64"] else np.float32)
+    nd = info["ndim"] if 1 <= info["ndim"] <= 3 else 3
+    u = u.reshape(info["shape"][3 - nd:])
     return (u, codes) if want_codes else u
 
 

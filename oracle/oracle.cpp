@@ -284,12 +284,15 @@ struct Round {
 struct Plan {
   int64_t shape[3];
   int B, K, M, R = 1;
+  int Bd[3];         // block edge per dimension: B, or 1 for a dimension of extent 1
+  int md[3];         // coarse nodes per block edge after K levels, per dimension
   int64_t nb[3];     // round 0
   int64_t nblocks;   // round 0
   std::vector<Round> rounds;
-  int m;                          // coarse nodes per block dim after K levels
-  std::vector<std::vector<double>> block_coords;  // per local level (K+1 entries)
-  std::vector<Level1D> local;     // per local level: one 1-D level (same for all dims)
+  int m;                          // coarse nodes per block dim after K levels (B-node dimensions)
+  std::vector<std::vector<double>> block_coords;  // per local level (K+1 entries), B-node dimensions
+  std::vector<Level1D> local;     // per local level: the 1-D level of a B-node dimension
+  std::vector<std::array<Level1D, 3>> local3;     // per local level, per dimension (identity where Bd = 1)
   std::vector<std::array<Level1D, 3>> global;     // per global level
   size_t per_block = 0;           // coefficients per block
   std::vector<size_t> global_counts;
@@ -304,23 +307,34 @@ Plan make_plan(const int64_t* shape, int B, int K, int M, int R = 1) {
   Plan p;
   for (int d = 0; d < 3; ++d) p.shape[d] = shape[d];
   p.B = B; p.K = K; p.M = M; p.R = R;
+  // A dimension of extent 1 (the missing dimensions of a 1-D or 2-D field) is
+  // neither blocked nor coarsened: its blocks are one node thick and its level
+  // operators are the identity of one node.
+  for (int d = 0; d < 3; ++d) {
+    if (shape[d] < 1) throw std::runtime_error("bad shape");
+    p.Bd[d] = shape[d] == 1 ? 1 : B;
+  }
   p.nblocks = 1;
   for (int d = 0; d < 3; ++d) {
-    p.nb[d] = (shape[d] + B - 1) / B;
+    p.nb[d] = (shape[d] + p.Bd[d] - 1) / p.Bd[d];
     p.nblocks *= p.nb[d];
   }
   std::vector<double> xl(B);
   for (int j = 0; j < B; ++j) xl[j] = j;  // block-local coordinates x_j = j
   p.block_coords.push_back(xl);
+  const Level1D one = make_level(std::vector<double>{0.0});
   for (int l = 0; l < K; ++l) {
     Level1D L = make_level(xl);
     p.local.push_back(L);
-    Level1D L3[3] = {L, L, L};
-    p.per_block += level_detail_count(L3);
+    std::array<Level1D, 3> L3;
+    for (int d = 0; d < 3; ++d) L3[d] = p.Bd[d] == 1 ? one : L;
+    p.per_block += level_detail_count(L3.data());
+    p.local3.push_back(L3);
     xl = L.xc;
     p.block_coords.push_back(xl);
   }
   p.m = (int)xl.size();
+  for (int d = 0; d < 3; ++d) p.md[d] = p.Bd[d] == 1 ? 1 : p.m;
   // rounds: each re-blocks the previous round's gathered grid (zero fill
   // beyond its extent)
   int64_t S[3] = {shape[0], shape[1], shape[2]};
@@ -330,13 +344,13 @@ Plan make_plan(const int64_t* shape, int B, int K, int M, int R = 1) {
     rd.nblocks = 1;
     for (int d = 0; d < 3; ++d) {
       rd.shape[d] = S[d];
-      rd.nb[d] = (S[d] + B - 1) / B;
+      rd.nb[d] = (S[d] + p.Bd[d] - 1) / p.Bd[d];
       rd.nblocks *= rd.nb[d];
     }
     rd.off = off;
     off += (size_t)rd.nblocks * p.per_block;
     p.rounds.push_back(rd);
-    for (int d = 0; d < 3; ++d) S[d] = rd.nb[d] * p.m;
+    for (int d = 0; d < 3; ++d) S[d] = rd.nb[d] * p.md[d];
   }
   // Coordinates of the gathered grid the global levels start from.  One
   // round: physical, block offset plus the coarse node's local coordinate, in
@@ -347,7 +361,7 @@ Plan make_plan(const int64_t* shape, int B, int K, int M, int R = 1) {
     p.gshape[d] = S[d];
     if (R == 1) {
       for (int64_t b = 0; b < p.nb[d]; ++b)
-        for (int j = 0; j < p.m; ++j) gx[d].push_back((double)(b * B) + xl[j]);
+        for (int j = 0; j < p.md[d]; ++j) gx[d].push_back((double)(b * p.Bd[d]) + (p.Bd[d] == 1 ? 0.0 : xl[j]));
     } else {
       for (int64_t i = 0; i < S[d]; ++i) gx[d].push_back((double)i);
     }
@@ -370,25 +384,25 @@ Plan make_plan(const int64_t* shape, int B, int K, int M, int R = 1) {
 // finest->coarsest, each level's non-coarse nodes row-major; then global
 // levels finest->coarsest; then the coarsest array row-major.
 Grid decompose_round(const Grid& in, const Plan& p, const Round& rd, std::vector<double>& coef) {
-  Grid G(rd.nb[0] * p.m, rd.nb[1] * p.m, rd.nb[2] * p.m);
+  const int* Bd = p.Bd;
+  const int* md = p.md;
+  Grid G(rd.nb[0] * md[0], rd.nb[1] * md[1], rd.nb[2] * md[2]);
   for (int64_t b0 = 0; b0 < rd.nb[0]; ++b0)
     for (int64_t b1 = 0; b1 < rd.nb[1]; ++b1)
       for (int64_t b2 = 0; b2 < rd.nb[2]; ++b2) {
-        Grid blk(p.B, p.B, p.B);
-        for (int i = 0; i < p.B; ++i)
-          for (int j = 0; j < p.B; ++j)
-            for (int k = 0; k < p.B; ++k) {
-              int64_t gi = b0 * p.B + i, gj = b1 * p.B + j, gk = b2 * p.B + k;
+        Grid blk(Bd[0], Bd[1], Bd[2]);
+        for (int i = 0; i < Bd[0]; ++i)
+          for (int j = 0; j < Bd[1]; ++j)
+            for (int k = 0; k < Bd[2]; ++k) {
+              int64_t gi = b0 * Bd[0] + i, gj = b1 * Bd[1] + j, gk = b2 * Bd[2] + k;
               bool inside = gi < rd.shape[0] && gj < rd.shape[1] && gk < rd.shape[2];
               blk.at(i, j, k) = inside ? in.at(gi, gj, gk) : 0.0;  // zero fill
             }
-        for (int l = 0; l < p.K; ++l) {
-          Level1D L3[3] = {p.local[l], p.local[l], p.local[l]};
-          blk = decompose_level(blk, L3, coef);
-        }
-        for (int i = 0; i < p.m; ++i)
-          for (int j = 0; j < p.m; ++j)
-            for (int k = 0; k < p.m; ++k) G.at(b0 * p.m + i, b1 * p.m + j, b2 * p.m + k) = blk.at(i, j, k);
+        for (int l = 0; l < p.K; ++l) blk = decompose_level(blk, p.local3[l].data(), coef);
+        for (int i = 0; i < md[0]; ++i)
+          for (int j = 0; j < md[1]; ++j)
+            for (int k = 0; k < md[2]; ++k)
+              G.at(b0 * md[0] + i, b1 * md[1] + j, b2 * md[2] + k) = blk.at(i, j, k);
       }
   return G;
 }
@@ -414,24 +428,24 @@ Grid recompose_round(const Grid& G, const Plan& p, const Round& rd, const double
       for (int64_t b2 = 0; b2 < rd.nb[2]; ++b2) {
         int64_t bid = (b0 * rd.nb[1] + b1) * rd.nb[2] + b2;
         size_t q = rd.off + (size_t)bid * p.per_block;
+        const int* Bd = p.Bd;
+        const int* md = p.md;
         for (int l = 0; l < p.K; ++l) {
           lpos[l] = q;
-          Level1D L3[3] = {p.local[l], p.local[l], p.local[l]};
-          q += level_detail_count(L3);
+          q += level_detail_count(p.local3[l].data());
         }
-        Grid blk(p.m, p.m, p.m);
-        for (int i = 0; i < p.m; ++i)
-          for (int j = 0; j < p.m; ++j)
-            for (int k = 0; k < p.m; ++k) blk.at(i, j, k) = G.at(b0 * p.m + i, b1 * p.m + j, b2 * p.m + k);
+        Grid blk(md[0], md[1], md[2]);
+        for (int i = 0; i < md[0]; ++i)
+          for (int j = 0; j < md[1]; ++j)
+            for (int k = 0; k < md[2]; ++k) blk.at(i, j, k) = G.at(b0 * md[0] + i, b1 * md[1] + j, b2 * md[2] + k);
         for (int l = p.K - 1; l >= 0; --l) {
-          Level1D L3[3] = {p.local[l], p.local[l], p.local[l]};
           size_t r = lpos[l];
-          blk = recompose_level(blk, L3, coef, r);
+          blk = recompose_level(blk, p.local3[l].data(), coef, r);
         }
-        for (int i = 0; i < p.B; ++i)
-          for (int j = 0; j < p.B; ++j)
-            for (int k = 0; k < p.B; ++k) {
-              int64_t gi = b0 * p.B + i, gj = b1 * p.B + j, gk = b2 * p.B + k;
+        for (int i = 0; i < Bd[0]; ++i)
+          for (int j = 0; j < Bd[1]; ++j)
+            for (int k = 0; k < Bd[2]; ++k) {
+              int64_t gi = b0 * Bd[0] + i, gj = b1 * Bd[1] + j, gk = b2 * Bd[2] + k;
               if (gi < rd.shape[0] && gj < rd.shape[1] && gk < rd.shape[2]) out.at(gi, gj, gk) = blk.at(i, j, k);
             }
       }
@@ -470,9 +484,9 @@ std::vector<std::vector<uint8_t>> round_tiers(const Plan& p, const std::vector<u
           const int64_t j[3] = {j0, j1, j2};
           int64_t lo[3], hi[3];  // contributing round-r blocks per dimension
           for (int d = 0; d < 3; ++d) {
-            const int64_t first = j[d] * p.B, last = std::min((j[d] + 1) * p.B, b.shape[d]) - 1;
-            lo[d] = first / p.m;
-            hi[d] = last / p.m;
+            const int64_t first = j[d] * p.Bd[d], last = std::min((j[d] + 1) * p.Bd[d], b.shape[d]) - 1;
+            lo[d] = first / p.md[d];
+            hi[d] = last / p.md[d];
           }
           uint8_t v = 255;
           for (int64_t i0 = lo[0]; i0 <= hi[0]; ++i0)
@@ -535,10 +549,7 @@ double level_error_constant(const Level1D* L) {
 
 std::vector<double> level_constants(const Plan& p) {  // local 1..K then global 1..M
   std::vector<double> C;
-  for (int l = 0; l < p.K; ++l) {
-    Level1D L3[3] = {p.local[l], p.local[l], p.local[l]};
-    C.push_back(round_constant(level_error_constant(L3)));
-  }
+  for (int l = 0; l < p.K; ++l) C.push_back(round_constant(level_error_constant(p.local3[l].data())));
   for (int l = 0; l < p.M; ++l) C.push_back(round_constant(level_error_constant(p.global[l].data())));
   return C;
 }
@@ -619,8 +630,7 @@ std::vector<uint32_t> coeff_q_index(const Plan& p, const std::vector<std::vector
     for (int64_t b = 0; b < p.rounds[r].nblocks; ++b) {
       int tier = block_tier[r].empty() ? 0 : block_tier[r][(size_t)b];
       for (int l = 0; l < p.K; ++l) {
-        Level1D L3[3] = {p.local[l], p.local[l], p.local[l]};
-        size_t cnt = level_detail_count(L3);
+        size_t cnt = level_detail_count(p.local3[l].data());
         for (size_t t = 0; t < cnt; ++t) qi[pos++] = (uint32_t)(tier * p.K + l);
       }
     }
@@ -851,6 +861,7 @@ bool huffman_decode(const std::vector<uint8_t>& len, const uint32_t* chunk_words
 
 struct CompressOpts {
   int B = 9, K = 1, M = 2, chunk = 2048, radius = 32768, R = 1;
+  int ndim = 3;  // dimensions of the caller's field (the shape holds it with leading extents of 1)
 };
 
 thread_local std::string g_err;
@@ -911,7 +922,7 @@ std::vector<uint8_t> compress(const double* u, const int64_t* shape, bool f64, d
   w.b.assign(kHeader, 0);
   w.put_at<uint32_t>(0, kMagic);
   w.put_at<uint16_t>(4, 1);
-  w.put_at<int32_t>(8, 3);
+  w.put_at<int32_t>(8, o.ndim);
   w.put_at<int32_t>(12, o.B);
   for (int d = 0; d < 3; ++d) w.put_at<int64_t>(16 + 8 * d, shape[d]);
   w.put_at<double>(80, max_abs);
@@ -922,7 +933,7 @@ std::vector<uint8_t> compress(const double* u, const int64_t* shape, bool f64, d
     w.put_at<uint32_t>(0, kMagic);
     w.put_at<uint16_t>(4, 1);
     w.put_at<uint16_t>(6, (uint16_t)(1 | (f64 ? 2 : 0)));
-    w.put_at<int32_t>(8, 3);
+    w.put_at<int32_t>(8, o.ndim);
     w.put_at<int32_t>(12, o.B);
     for (int d = 0; d < 3; ++d) w.put_at<int64_t>(16 + 8 * d, shape[d]);
     w.put_at<int32_t>(76, rel);
@@ -1278,6 +1289,27 @@ int or_huffman_decode(const uint8_t* codebook, uint64_t cb_bytes, uint32_t n_run
 // Compress a field given as FP64 values (dtype_f64 = 1 if the original is FP64).
 // roi may be null (one tolerance per block otherwise). codes_out (optional,
 // n_coeffs entries) receives the integer codes.
+// The same for a field of ndim (1..3) dimensions, held in `shape` as a 3-D
+// shape with leading extents of 1; the header records ndim.
+int or_compress_nd(const double* u, const int64_t* shape, int ndim, int dtype_f64, double tol, int rel,
+                   const double* roi, int B, int K, int M, int R, int chunk, int radius, uint8_t* out, uint64_t cap,
+                   uint64_t* out_bytes, int64_t* codes_out) {
+  try {
+    if (ndim < 1 || ndim > 3) throw std::runtime_error("ndim must be 1, 2 or 3");
+    for (int d = 0; d < 3 - ndim; ++d)
+      if (shape[d] != 1) throw std::runtime_error("leading extents of a field with fewer than 3 dimensions must be 1");
+    CompressOpts o;
+    o.B = B; o.K = K; o.M = M; o.R = R; o.chunk = chunk; o.radius = radius; o.ndim = ndim;
+    std::vector<int64_t> codes;
+    std::vector<uint8_t> s = compress(u, shape, dtype_f64 != 0, tol, rel, roi, o, codes_out ? &codes : nullptr);
+    *out_bytes = s.size();
+    if (s.size() > cap) { g_err = "capacity"; return 2; }
+    std::memcpy(out, s.data(), s.size());
+    if (codes_out && !codes.empty()) std::memcpy(codes_out, codes.data(), codes.size() * 8);
+    return 0;
+  } catch (const std::exception& e) { g_err = e.what(); return 1; }
+}
+
 int or_compress_r(const double* u, const int64_t* shape, int dtype_f64, double tol, int rel, const double* roi, int B,
                   int K, int M, int R, int chunk, int radius, uint8_t* out, uint64_t cap, uint64_t* out_bytes,
                   int64_t* codes_out) {
