@@ -23,8 +23,12 @@
  *     by a kernel through the device mapping of the library's pinned staging
  *     memory, not by copy-engine copies, so a call does not wait behind bulk
  *     copies the caller has queued on other streams.
- *   - Fields are 3-D, row-major (C order) with shape[2] varying fastest, each
- *     extent >= 2.  dtype: BM_F32 or BM_F64.
+ *   - Fields have ndim = 1, 2 or 3 dimensions, row-major (C order) with the
+ *     last extent varying fastest; `shape` holds ndim extents, each >= 1, at
+ *     least two values in all.  A field is handled as 3-D with leading extents
+ *     of 1, and a dimension of extent 1 is neither blocked nor coarsened (its
+ *     blocks are one node thick), so a 1-D or 2-D field gets the 1-D or 2-D
+ *     transform.  dtype: BM_F32 or BM_F64.
  *   - Every call returns a bm_status.  On failure a readable message is
  *     available from bm_last_error_detail() (thread-local); no output buffer
  *     is guaranteed to hold meaningful data.  Invalid arguments are rejected
@@ -73,7 +77,8 @@ typedef struct {
                           round r+1 re-blocks round r's gathered coarse values and takes
                           the strictest tolerance among the blocks each new block holds
                           coarse values of (Sec. III-C).  With R > 1 the global levels use
-                          index coordinates; the adjoint entry points need R = 1.       */
+                          index coordinates; the adjoint entry points need R = 1.  R > 1
+                          needs a 3-D field without extents of 1.                       */
 } bm_params;
 
 /* Upper bound on the stream size for a field of this shape and dtype: the raw
@@ -84,9 +89,9 @@ size_t bm_compress_bound(int ndim, const int64_t* shape, bm_dtype dtype);
  *   d_field     device pointer to the field, shape[0]*shape[1]*shape[2] values
  *               of `dtype`, row-major.
  *   tol         error tolerance (> 0, finite); absolute or relative (tol_mode).
- *   h_roi_tol   optional host array with one tolerance per block of B^3 nodes,
- *               row-major over the block grid ceil(shape[d]/B); same mode as
- *               tol.  Block i's tolerance is min(tol, h_roi_tol[i]) (Sec. III-C
+ *   h_roi_tol   optional host array with one tolerance per block (B nodes along
+ *               every dimension of extent > 1), row-major over the block grid
+ *               ceil(shape[d]/B); same mode as tol.  Block i's tolerance is min(tol, h_roi_tol[i]) (Sec. III-C
  *               block-wise tolerance assignment).  NULL = uniform.  At most 255
  *               distinct values.
  *   d_out       device buffer for the stream; out_capacity bytes (use
@@ -101,7 +106,8 @@ bm_status bm_compress(const void* d_field, int ndim, const int64_t* shape, bm_dt
                       size_t out_capacity, size_t* out_bytes, void* stream);
 
 /* Header of a stream (the first 256 bytes, host or device memory: set
- * `in_is_device`).  Any output pointer may be NULL. */
+ * `in_is_device`).  Any output pointer may be NULL; shape receives the
+ * field's ndim extents (unused entries 0). */
 bm_status bm_stream_info(const void* in, size_t in_bytes, int in_is_device, int* ndim, int64_t shape[3],
                          bm_dtype* dtype, size_t* n_coeffs);
 
@@ -192,8 +198,9 @@ bm_status bm_recompose(const void* d_coeffs, int ndim, const int64_t* shape, bm_
  * written; nodes outside the domain of a padded block have no field entry
  * and receive nothing).  bm_recompose_adjoint: d_field_grad (read) ->
  * d_coeff_grad (n_coeffs, written).  Same dtype, parameters and errors as
- * bm_decompose; both run asynchronously on `stream` and allocate nothing
- * beyond the cached workspace. */
+ * bm_decompose, except that they need a 3-D field without extents of 1
+ * (BM_ERR_UNSUPPORTED otherwise); both run asynchronously on `stream` and
+ * allocate nothing beyond the cached workspace. */
 bm_status bm_decompose_adjoint(const void* d_coeff_grad, int ndim, const int64_t* shape, bm_dtype dtype,
                                const bm_params* params, void* d_field_grad, void* stream);
 bm_status bm_recompose_adjoint(const void* d_field_grad, int ndim, const int64_t* shape, bm_dtype dtype,

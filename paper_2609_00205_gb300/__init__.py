@@ -127,7 +127,11 @@ def _stream(stream):
 
 
 def _shape(shape):
-    return (ctypes.c_int64 * 3)(*[int(v) for v in shape])
+    """Extents of a field of 1..3 dimensions (a C array of 3; unused entries 0)."""
+    s = [int(v) for v in shape]
+    if not 1 <= len(s) <= 3:
+        raise ValueError("fields have 1, 2 or 3 dimensions")
+    return (ctypes.c_int64 * 3)(*(s + [0] * (3 - len(s))))
 
 
 def _dtype(t):
@@ -151,7 +155,7 @@ def _dev_check(t):
 
 
 def compress_bound(shape, dtype=torch.float32) -> int:
-    return int(load().bm_compress_bound(3, _shape(shape), _dtype(dtype)))
+    return int(load().bm_compress_bound(len(shape), _shape(shape), _dtype(dtype)))
 
 
 def compress(field: torch.Tensor, tol: float, mode: str = "rel", roi=None, block=17, levels=2, global_levels=2,
@@ -160,8 +164,8 @@ def compress(field: torch.Tensor, tol: float, mode: str = "rel", roi=None, block
     uint8 CUDA tensor (a view of ``out`` when given).  ``roi``: optional
     per-block tolerances (same mode as ``tol``), row-major over the block grid."""
     _dev_check(field)
-    if field.dim() != 3:
-        raise ValueError("fields must be 3-D")
+    if not 1 <= field.dim() <= 3:
+        raise ValueError("fields have 1, 2 or 3 dimensions")
     L = load()
     cap = compress_bound(field.shape, field.dtype)
     if out is None:
@@ -176,7 +180,7 @@ def compress(field: torch.Tensor, tol: float, mode: str = "rel", roi=None, block
     nbytes = ctypes.c_size_t(0)
     p = _params(block, levels, global_levels, chunk, radius, rounds)
     with torch.cuda.device(field.device):
-        _check(L.bm_compress(ctypes.c_void_p(field.data_ptr()), 3, _shape(field.shape), _dtype(field.dtype),
+        _check(L.bm_compress(ctypes.c_void_p(field.data_ptr()), field.dim(), _shape(field.shape), _dtype(field.dtype),
                              float(tol), BM_REL if mode == "rel" else BM_ABS, roi_ptr, ctypes.byref(p),
                              ctypes.c_void_p(out.data_ptr()), ctypes.c_size_t(out.numel()), ctypes.byref(nbytes),
                              _stream(stream)))
@@ -201,8 +205,8 @@ def compress_batch(fields, tols, mode: str = "rel", rois=None, block=17, levels=
     p = _params(block, levels, global_levels, chunk, radius, rounds)
     for i, f in enumerate(fields):
         _dev_check(f)
-        if f.dim() != 3:
-            raise ValueError("fields must be 3-D")
+        if not 1 <= f.dim() <= 3:
+            raise ValueError("fields have 1, 2 or 3 dimensions")
         cap = compress_bound(f.shape, f.dtype)
         o = outs[i] if outs is not None else torch.empty(cap, dtype=torch.uint8, device=f.device)
         if o.numel() < cap or o.dtype != torch.uint8 or not o.is_cuda:
@@ -210,9 +214,9 @@ def compress_batch(fields, tols, mode: str = "rel", rois=None, block=17, levels=
         bufs.append(o)
         it = items[i]
         it.d_field = f.data_ptr()
-        it.ndim = 3
+        it.ndim = f.dim()
         for d in range(3):
-            it.shape[d] = int(f.shape[d])
+            it.shape[d] = int(f.shape[d]) if d < f.dim() else 0
         it.dtype = _dtype(f.dtype)
         it.tol = float(tols[i])
         it.tol_mode = BM_REL if mode == "rel" else BM_ABS
@@ -275,7 +279,7 @@ def stream_info(buf: torch.Tensor) -> dict:
         b = buf.contiguous()
         _check(L.bm_stream_info(ctypes.c_void_p(b.data_ptr()), b.numel(), 0, ctypes.byref(nd), shp, ctypes.byref(dt),
                                 ctypes.byref(nc)))
-    return {"shape": tuple(shp), "dtype": torch.float64 if dt.value == BM_F64 else torch.float32,
+    return {"shape": tuple(shp[: nd.value]), "dtype": torch.float64 if dt.value == BM_F64 else torch.float32,
             "n_coeffs": nc.value}
 
 
@@ -294,7 +298,7 @@ def decompress(buf: torch.Tensor, out: torch.Tensor | None = None, stream=None) 
 def coeff_count(shape, block=17, levels=2, global_levels=2, rounds=1) -> int:
     n = ctypes.c_size_t(0)
     p = _params(block, levels, global_levels, rounds=rounds)
-    _check(load().bm_coeff_count(3, _shape(shape), ctypes.byref(p), ctypes.byref(n)))
+    _check(load().bm_coeff_count(len(shape), _shape(shape), ctypes.byref(p), ctypes.byref(n)))
     return n.value
 
 
@@ -305,7 +309,7 @@ def decompose(field: torch.Tensor, block=17, levels=2, global_levels=2, stream=N
     out = torch.empty(n, dtype=field.dtype, device=field.device)
     p = _params(block, levels, global_levels, rounds=rounds)
     with torch.cuda.device(field.device):
-        _check(load().bm_decompose(ctypes.c_void_p(field.data_ptr()), 3, _shape(field.shape), _dtype(field.dtype),
+        _check(load().bm_decompose(ctypes.c_void_p(field.data_ptr()), field.dim(), _shape(field.shape), _dtype(field.dtype),
                                    ctypes.byref(p), ctypes.c_void_p(out.data_ptr()), _stream(stream)))
     return out
 
@@ -316,7 +320,7 @@ def recompose(coeffs: torch.Tensor, shape, block=17, levels=2, global_levels=2, 
     out = torch.empty(tuple(shape), dtype=coeffs.dtype, device=coeffs.device)
     p = _params(block, levels, global_levels, rounds=rounds)
     with torch.cuda.device(coeffs.device):
-        _check(load().bm_recompose(ctypes.c_void_p(coeffs.data_ptr()), 3, _shape(shape), _dtype(coeffs.dtype),
+        _check(load().bm_recompose(ctypes.c_void_p(coeffs.data_ptr()), len(shape), _shape(shape), _dtype(coeffs.dtype),
                                    ctypes.byref(p), ctypes.c_void_p(out.data_ptr()), _stream(stream)))
     return out
 
@@ -331,7 +335,7 @@ def decompose_adjoint(coeff_grad: torch.Tensor, shape, block=17, levels=2, globa
     out = torch.empty(tuple(shape), dtype=coeff_grad.dtype, device=coeff_grad.device)
     p = _params(block, levels, global_levels)
     with torch.cuda.device(coeff_grad.device):
-        _check(load().bm_decompose_adjoint(ctypes.c_void_p(coeff_grad.data_ptr()), 3, _shape(shape),
+        _check(load().bm_decompose_adjoint(ctypes.c_void_p(coeff_grad.data_ptr()), len(shape), _shape(shape),
                                            _dtype(coeff_grad.dtype), ctypes.byref(p), ctypes.c_void_p(out.data_ptr()),
                                            _stream(stream)))
     return out
@@ -341,13 +345,11 @@ def recompose_adjoint(field_grad: torch.Tensor, block=17, levels=2, global_level
     """Transpose of :func:`recompose` applied to field gradients: the gradient
     with respect to the coefficients (stream order)."""
     _dev_check(field_grad)
-    if field_grad.dim() != 3:
-        raise ValueError("fields must be 3-D")
     n = coeff_count(field_grad.shape, block, levels, global_levels)
     out = torch.empty(n, dtype=field_grad.dtype, device=field_grad.device)
     p = _params(block, levels, global_levels)
     with torch.cuda.device(field_grad.device):
-        _check(load().bm_recompose_adjoint(ctypes.c_void_p(field_grad.data_ptr()), 3, _shape(field_grad.shape),
+        _check(load().bm_recompose_adjoint(ctypes.c_void_p(field_grad.data_ptr()), field_grad.dim(), _shape(field_grad.shape),
                                            _dtype(field_grad.dtype), ctypes.byref(p), ctypes.c_void_p(out.data_ptr()),
                                            _stream(stream)))
     return out

@@ -385,8 +385,8 @@ __global__ void gl_adj_gather(GLevel<T> L, const T* __restrict__ g, const T* __r
     const int i2 = (int)(idx % n2);
     const int64_t q = idx / n2;
     const int i1 = (int)(q % n1), i0 = (int)(q / n1);
-    if (all_coarse(L.d[0].isc, L.d[1].isc, L.d[2].isc, i0, i1, i2)) continue;
-    coef[L.sym_off + nc_rank(L, i0, i1, i2, idx)] = g[idx] - t[idx];
+    if (all_coarse(L, i0, i1, i2)) continue;
+    coef[nc_pos(L, i0, i1, i2, idx)] = g[idx] - t[idx];
   }
 }
 

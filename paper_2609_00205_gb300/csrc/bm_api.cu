@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <functional>
 #include <cmath>
@@ -219,6 +220,8 @@ struct PlanDev {
   int dev[2] = {-1, -1};
   std::vector<GLevel<float>> gf;
   std::vector<GLevel<double>> gd;
+  std::vector<GLevel<float>> rf;   // in-cache levels on the block-major grid (fields with an extent of 1)
+  std::vector<GLevel<double>> rd;
 };
 std::mutex g_plan_mu;
 std::map<std::tuple<int64_t, int64_t, int64_t, int, int, int, int>, std::unique_ptr<PlanDev>> g_plans;
@@ -229,6 +232,12 @@ template <>
 std::vector<GLevel<float>>& glevels<float>(PlanDev& p) { return p.gf; }
 template <>
 std::vector<GLevel<double>>& glevels<double>(PlanDev& p) { return p.gd; }
+template <typename T>
+std::vector<GLevel<T>>& rlevels(PlanDev& p);
+template <>
+std::vector<GLevel<float>>& rlevels<float>(PlanDev& p) { return p.rf; }
+template <>
+std::vector<GLevel<double>>& rlevels<double>(PlanDev& p) { return p.rd; }
 
 template <typename T>
 bm_status upload_tables(PlanDev& P) {
@@ -246,8 +255,18 @@ bm_status upload_tables(PlanDev& P) {
   };
   struct Offs { size_t cidx, jlo, jhi, wl, wr, cb, isc, proj, f0, band, tm, tib, tsup, md, mo; };
   std::vector<Offs> offs;
+  // every tabulated dimension: the global levels' three, then the two in-block
+  // axes of each in-cache level of the block-major grid
+  std::vector<const Dim1DHost*> dims;
   for (auto& L3 : P.h.glev)
-    for (auto& D : L3) {
+    for (auto& D : L3) dims.push_back(&D);
+  for (auto& rl : P.h.rlev) {
+    dims.push_back(&rl.da);
+    dims.push_back(&rl.db);
+  }
+  for (const Dim1DHost* Dp : dims) {
+    const Dim1DHost& D = *Dp;
+    {
       auto cvt = [](const std::vector<double>& v) {
         std::vector<T> o(v.size());
         for (size_t i = 0; i < v.size(); ++i) o[i] = (T)v[i];
@@ -273,6 +292,7 @@ bm_status upload_tables(PlanDev& P) {
       o.mo = put(mo.data(), mo.size() * sizeof(T));
       offs.push_back(o);
     }
+  }
   if (P.dtab[di]) { cudaFree(P.dtab[di]); P.dtab[di] = nullptr; }
   if (!img.empty()) {
     BM_CUDA(cudaMalloc(&P.dtab[di], img.size()));
@@ -282,12 +302,8 @@ bm_status upload_tables(PlanDev& P) {
   auto& G = glevels<T>(P);
   G.clear();
   const unsigned char* base = reinterpret_cast<const unsigned char*>(P.dtab[di]);
-  for (int l = 0; l < P.h.M; ++l) {
-    GLevel<T> L;
-    for (int d = 0; d < 3; ++d) {
-      const Offs& o = offs[l * 3 + d];
-      const Dim1DHost& D = P.h.glev[l][d];
-      GDim<T>& g = L.d[d];
+  auto fill = [&](GDim<T>& g, const Offs& o, const Dim1DHost& D) {
+    {
       g.n = D.n; g.c = D.c;
       g.cidx = reinterpret_cast<const int*>(base + o.cidx);
       g.jlo = reinterpret_cast<const int*>(base + o.jlo);
@@ -304,9 +320,29 @@ bm_status upload_tables(PlanDev& P) {
       g.tsup = reinterpret_cast<const T*>(base + o.tsup);
       g.md = reinterpret_cast<const T*>(base + o.md);
       g.mo = reinterpret_cast<const T*>(base + o.mo);
+      g.ident = 0;
     }
+  };
+  for (int l = 0; l < P.h.M; ++l) {
+    GLevel<T> L{};
+    for (int d = 0; d < 3; ++d) fill(L.d[d], offs[(size_t)(l * 3 + d)], P.h.glev[l][d]);
     L.sym_off = P.h.sym_off[l];
+    L.blk_extra = 0;
     G.push_back(L);
+  }
+  auto& RL = rlevels<T>(P);
+  RL.clear();
+  size_t k = (size_t)P.h.M * 3;
+  for (const RLevelHost& rl : P.h.rlev) {
+    GLevel<T> L{};
+    L.d[0].n = L.d[0].c = (int)rl.nblk;
+    L.d[0].ident = 1;
+    fill(L.d[1], offs[k], rl.da);
+    fill(L.d[2], offs[k + 1], rl.db);
+    k += 2;
+    L.sym_off = rl.off;
+    L.blk_extra = rl.blk_extra;
+    RL.push_back(L);
   }
   return BM_OK;
 }
@@ -328,7 +364,7 @@ bm_status get_plan(const int64_t* shape, int B, int K, int M, int R, PlanDev** o
 // ---------------------------------------------------------------------------
 // Parameters and shapes
 // ---------------------------------------------------------------------------
-struct Params { int B, K, M, chunk, radius, R; };
+struct Params { int B, K, M, chunk, radius, R, ndim = 3; };
 
 bm_status check_params(const bm_params* p, Params& o) {
   o.B = (p && p->block_nodes) ? p->block_nodes : 17;
@@ -348,20 +384,31 @@ bm_status check_params(const bm_params* p, Params& o) {
   return BM_OK;
 }
 
-bm_status check_shape(int ndim, const int64_t* shape) {
-  if (ndim != 3) return fail(ndim >= 1 && ndim <= 3 ? BM_ERR_UNSUPPORTED : BM_ERR_ARG, "only 3-D fields are supported");
+// A field of ndim (1..3) dimensions as a 3-D shape with leading extents of 1
+// (a dimension of extent 1 is neither blocked nor coarsened); at least two
+// values.
+bm_status norm_shape(int ndim, const int64_t* shape, int64_t s3[3]) {
+  if (ndim < 1 || ndim > 3) return fail(BM_ERR_ARG, "ndim must be 1, 2 or 3");
   if (!shape) return fail(BM_ERR_ARG, "shape is NULL");
-  for (int d = 0; d < 3; ++d)
-    if (shape[d] < 2 || shape[d] > (int64_t(1) << 31)) return fail(BM_ERR_ARG, "every extent must be in [2, 2^31]");
+  int64_t total = 1;
+  for (int d = 0; d < 3; ++d) {
+    s3[d] = d < 3 - ndim ? 1 : shape[d - (3 - ndim)];
+    if (s3[d] < 1 || s3[d] > (int64_t(1) << 31)) return fail(BM_ERR_ARG, "every extent must be in [1, 2^31]");
+    total *= s3[d];
+  }
+  if (total < 2) return fail(BM_ERR_ARG, "a field needs at least two values");
   return BM_OK;
 }
 
 int64_t nel3(const int64_t* s) { return s[0] * s[1] * s[2]; }
 
-// Sizes of the global-level scratch arrays (elements): U[l] per level, D, W1, W2.
+// Sizes of the global-level scratch arrays (elements): U[l] per level, D, W1,
+// W2; for a field with an extent of 1, RB[l] (l = 0..K) the block-major grids
+// of its in-cache levels (the same D, W1, W2 serve their passes).
 struct GSizes {
   std::vector<int64_t> U;
   int64_t D = 0, W1 = 0, W2 = 0;
+  std::vector<int64_t> RB;
 };
 GSizes gsizes(const PlanHost& h) {
   GSizes g;
@@ -373,7 +420,35 @@ GSizes gsizes(const PlanHost& h) {
     g.W1 = std::max(g.W1, n0 * n1 * c2);
     g.W2 = std::max(g.W2, std::max(n0 * c1 * c2, c0 * c1 * c2));
   }
+  if (h.reduced) {
+    for (const RLevelHost& rl : h.rlev) {
+      g.RB.push_back(rl.nblk * rl.da.n * rl.db.n);
+      g.W1 = std::max(g.W1, rl.nblk * rl.da.n * rl.db.c);
+      g.W2 = std::max(g.W2, rl.nblk * rl.da.c * rl.db.c);
+    }
+    const RLevelHost& last = h.rlev.back();
+    g.RB.push_back(last.nblk * last.da.c * last.db.c);
+    g.D = std::max(g.D, g.RB[0]);
+  }
   return g;
+}
+
+// Between a grid and its block-major tiles (reblock_kernel): the field and
+// the blocks of round 0, or the gathered grid G and the blocks' coarse values.
+Reblock reblock_of(const PlanHost& h, bool coarse) {
+  Reblock R{};
+  for (int d = 0; d < 3; ++d) {
+    R.g[d] = coarse ? h.gshape[d] : h.shape[d];
+    R.e[d] = coarse ? h.md[d] : h.Bd[d];
+    R.nb[d] = h.nb[d];
+  }
+  R.ax[0] = h.ax[0];
+  R.ax[1] = h.ax[1];
+  const int edge = coarse ? h.m : h.B;
+  R.E1 = h.ax[0] < 0 ? 1 : edge;
+  R.E2 = edge;
+  R.nblk = h.nblocks;
+  return R;
 }
 
 // cudaFuncAttributeMaxDynamicSharedMemorySize set once per device for a kernel.
@@ -571,7 +646,7 @@ __global__ void __launch_bounds__(256) maxabs_kernel(const T* __restrict__ u, in
 
 struct HeaderArgs {
   uint8_t* out;
-  int f64, B, K, M, chunk, radius, ntiers, m, rel, R;
+  int f64, B, K, M, chunk, radius, ntiers, m, rel, R, ndim;
   int64_t shape[3];
   int nb[3];
   double tol;
@@ -594,7 +669,7 @@ __global__ void header_kernel(HeaderArgs a) {
   put<uint32_t>(o, 0, kMagic);
   put<uint16_t>(o, 4, 1);
   put<uint16_t>(o, 6, (uint16_t)(a.f64 ? 2 : 0));
-  put<int32_t>(o, 8, 3);
+  put<int32_t>(o, 8, a.ndim);
   put<int32_t>(o, 12, a.B);
   for (int d = 0; d < 3; ++d) put<int64_t>(o, 16 + 8 * d, a.shape[d]);
   put<int32_t>(o, 40, a.K);
@@ -635,13 +710,13 @@ __global__ void header_kernel(HeaderArgs a) {
 }
 
 __global__ void raw_header_kernel(uint8_t* o, int f64, int B, int64_t s0, int64_t s1, int64_t s2, int rel, double tol,
-                                  unsigned long long total, Scalars* sc) {
+                                  unsigned long long total, Scalars* sc, int ndim) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   for (int i = 0; i < kHeaderBytes; ++i) o[i] = 0;
   put<uint32_t>(o, 0, kMagic);
   put<uint16_t>(o, 4, 1);
   put<uint16_t>(o, 6, (uint16_t)(1 | (f64 ? 2 : 0)));
-  put<int32_t>(o, 8, 3);
+  put<int32_t>(o, 8, ndim);
   put<int32_t>(o, 12, B);
   put<int64_t>(o, 16, s0);
   put<int64_t>(o, 24, s1);
@@ -661,14 +736,14 @@ __global__ void raw_header_kernel(uint8_t* o, int f64, int B, int64_t s0, int64_
 template <typename T>
 __global__ void __launch_bounds__(256) raw_stream_kernel(uint8_t* o, const T* __restrict__ field, int64_t nel, int f64,
                                                          int B, int64_t s0, int64_t s1, int64_t s2, int rel, double tol,
-                                                         unsigned long long total, Scalars* sc) {
+                                                         unsigned long long total, Scalars* sc, int ndim) {
   if (!(sc->status & ST_RAW)) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     for (int i = 0; i < kHeaderBytes; ++i) o[i] = 0;
     put<uint32_t>(o, 0, kMagic);
     put<uint16_t>(o, 4, 1);
     put<uint16_t>(o, 6, (uint16_t)(1 | (f64 ? 2 : 0)));
-    put<int32_t>(o, 8, 3);
+    put<int32_t>(o, 8, ndim);
     put<int32_t>(o, 12, B);
     put<int64_t>(o, 16, s0);
     put<int64_t>(o, 24, s1);
@@ -890,7 +965,32 @@ bm_status run_decompose(PlanDev& P, const T* field, int mode, const FwdOut<T>& o
   T* W1 = cv.take<T>((size_t)std::max<int64_t>(gs.W1, 1));
   T* W2 = cv.take<T>((size_t)std::max<int64_t>(gs.W2, 1));
   std::vector<T*> Gr = round_grids<T>(h, cv, U[0]);
-  {
+  if (h.reduced) {  // a field with an extent of 1: in-cache levels on the block-major grid
+    Stage st("incache_decompose");
+    std::vector<T*> RB;
+    for (int64_t n : gs.RB) RB.push_back(cv.take<T>((size_t)n));
+    const Reblock rf = reblock_of(h, false), rc = reblock_of(h, true);
+    reblock_kernel<T, 0><<<grid_for(gs.RB[0], 256), 256, 0, s>>>(rf, const_cast<T*>(field), RB[0]);
+    auto& RL = rlevels<T>(P);
+    for (int l = 0; l < h.K; ++l) {
+      const GLevel<T>& L = RL[(size_t)l];
+      const int64_t rows = (int64_t)L.d[0].n * L.d[1].n;
+      const T* rq = o.rq ? o.rq + l : nullptr;
+      if (mode == 0)
+        gl_fwd_detail<T, 0><<<grid_for(rows * 32, 256, 8), 256, 0, s>>>(L, RB[l], Dbuf, o.sym, o.esc, o.coef, rq, o.radius,
+                                                                       o.sc, o.tier, h.K);
+      else
+        gl_fwd_detail<T, 1><<<grid_for(rows * 32, 256, 8), 256, 0, s>>>(L, RB[l], Dbuf, o.sym, o.esc, o.coef, rq, o.radius,
+                                                                       o.sc, nullptr, 0);
+      BM_CUDA((launch_apply<T, 2, 0>(L, Dbuf, W1, nullptr, s)));
+      BM_CUDA((launch_apply<T, 1, 0>(L, W1, W2, nullptr, s)));
+      gl_ident0<T, 1><<<grid_for(gs.RB[(size_t)l + 1], 256), 256, 0, s>>>(L, W2, RB[(size_t)l + 1], RB[l]);
+      g_launches.fetch_add(4);
+    }
+    reblock_kernel<T, 1><<<grid_for(gs.RB.back(), 256), 256, 0, s>>>(rc, Gr[0], RB.back());
+    g_launches.fetch_add(2);
+    BM_CUDA(cudaGetLastError());
+  } else {
     Stage st("incache_decompose");
     int64_t toff = 0;
     for (size_t r = 0; r < h.rounds.size(); ++r) {  // each round blocks the previous round's gathered grid
@@ -997,7 +1097,33 @@ bm_status run_recompose(PlanDev& P, T* field, int mode, const InvIn<T>& in, Carv
     g_launches.fetch_add(5);
     BM_CUDA(cudaGetLastError());
   }
-  {
+  if (h.reduced) {
+    Stage st("incache_recompose");
+    std::vector<T*> RB;
+    for (int64_t n : gs.RB) RB.push_back(cv.take<T>((size_t)n));
+    const Reblock rf = reblock_of(h, false), rc = reblock_of(h, true);
+    reblock_kernel<T, 0><<<grid_for(gs.RB.back(), 256), 256, 0, s>>>(rc, Gr[0], RB.back());
+    auto& RL = rlevels<T>(P);
+    T* Cn = Dbuf;
+    for (int l = h.K - 1; l >= 0; --l) {
+      const GLevel<T>& L = RL[(size_t)l];
+      const double* q = in.q ? in.q + l : nullptr;
+      const int64_t nn = gs.RB[(size_t)l];
+      if (mode == 0)
+        gl_inv_dequant<T, 0><<<grid_for(nn, 256), 256, 0, s>>>(L, in.sym, in.esc, in.coef, q, in.radius, RB[l], in.tier,
+                                                                h.K, in.ntiers, in.sc);
+      else
+        gl_inv_dequant<T, 1><<<grid_for(nn, 256), 256, 0, s>>>(L, in.sym, in.esc, in.coef, q, in.radius, RB[l]);
+      BM_CUDA((launch_apply<T, 2, 0>(L, RB[l], W1, nullptr, s)));
+      BM_CUDA((launch_apply<T, 1, 0>(L, W1, W2, nullptr, s)));
+      gl_ident0<T, 2><<<grid_for(gs.RB[(size_t)l + 1], 256), 256, 0, s>>>(L, W2, Cn, RB[(size_t)l + 1]);
+      gl_inv_interp<T><<<grid_for(nn, 256), 256, 0, s>>>(L, Cn, RB[l]);
+      g_launches.fetch_add(5);
+    }
+    reblock_kernel<T, 1><<<grid_for(gs.RB[0], 256), 256, 0, s>>>(rf, field, RB[0]);
+    g_launches.fetch_add(2);
+    BM_CUDA(cudaGetLastError());
+  } else {
     Stage st("incache_recompose");
     std::vector<int64_t> toff(h.rounds.size(), 0);
     for (size_t r = 1; r < h.rounds.size(); ++r) toff[r] = toff[r - 1] + h.rounds[r - 1].nblocks;
@@ -1028,6 +1154,7 @@ size_t decompose_scratch(const PlanHost& h, size_t esize) {
   const GSizes gs = gsizes(h);
   size_t b = 0;
   for (int64_t u : gs.U) b += (size_t)u * esize + 256;
+  for (int64_t u : gs.RB) b += (size_t)u * esize + 256;
   for (size_t r = 0; r + 1 < h.rounds.size(); ++r)
     b += (size_t)(h.rounds[r].gshape[0] * h.rounds[r].gshape[1] * h.rounds[r].gshape[2]) * esize + 256;
   b += ((size_t)gs.D + gs.W1 + gs.W2 + 3) * esize + 768;
@@ -1274,7 +1401,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     BM_CUDA(cudaGetLastError());
   }
   if (!prefix_fits) {  // not even the tables fit: the raw copy is the stream
-    raw_header_kernel<<<1, 32, 0, s>>>(out, f64, h.B, shape[0], shape[1], shape[2], rel, tol, raw_total, sc);
+    raw_header_kernel<<<1, 32, 0, s>>>(out, f64, h.B, shape[0], shape[1], shape[2], rel, tol, raw_total, sc, prm.ndim);
     BM_LAUNCHED();
     BM_CUDA(cudaMemcpyAsync(out + kHeaderBytes, field, (size_t)nel * sizeof(T), cudaMemcpyDeviceToDevice, s));
     if (bs) {
@@ -1343,7 +1470,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     HeaderArgs ha{};
     ha.raw_total = raw_total; ha.capacity = cap;
     ha.out = out; ha.f64 = f64; ha.B = h.B; ha.K = h.K; ha.M = h.M; ha.chunk = prm.chunk; ha.radius = prm.radius;
-    ha.ntiers = ntiers; ha.m = h.m; ha.rel = rel; ha.R = h.R;
+    ha.ntiers = ntiers; ha.m = h.m; ha.rel = rel; ha.R = h.R; ha.ndim = prm.ndim;
     for (int d = 0; d < 3; ++d) { ha.shape[d] = shape[d]; ha.nb[d] = h.nb[d]; }
     ha.tol = tol; ha.n_symbols = (unsigned long long)h.n_coeffs; ha.n_chunks = L.nch;
     ha.off_tiers = L.off_tiers; ha.off_qtab = L.off_qtab; ha.off_btier = ntiers > 1 ? L.off_btier : L.off_chunks;
@@ -1351,7 +1478,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     header_kernel<<<1, 32, 0, s>>>(ha);
     // a raw fallback is written on the device in the same pass (no second host round trip)
     raw_stream_kernel<T><<<mgrid, 256, 0, s>>>(out, field, nel, f64, h.B, shape[0], shape[1], shape[2], rel, tol,
-                                               raw_total, sc);
+                                               raw_total, sc, prm.ndim);
     g_launches.fetch_add(2);
     BM_CUDA(cudaGetLastError());
     Spans back;
@@ -1370,7 +1497,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
 // Parsed and checked header of a stream.
 struct Header {
   bool raw, f64;
-  int B, K, M, chunk, radius, ntiers, m, rel, R;
+  int B, K, M, chunk, radius, ntiers, m, rel, R, ndim;
   int64_t shape[3];
   unsigned long long n_symbols, n_chunks, n_outliers, n_words, off_tiers, off_qtab, off_btier, off_chunks,
       off_codebook, off_bits, off_chunk_esc, off_outliers, total, off_splits;
@@ -1391,11 +1518,13 @@ bm_status parse_header(const unsigned char* hb, size_t in_bytes, Header& H) {
   const uint16_t flags = rd<uint16_t>(hb, 6);
   H.raw = flags & 1;
   H.f64 = flags & 2;
-  if (rd<int32_t>(hb, 8) != 3) return fail(BM_ERR_CORRUPT, "ndim");
+  H.ndim = rd<int32_t>(hb, 8);
+  if (H.ndim < 1 || H.ndim > 3) return fail(BM_ERR_CORRUPT, "ndim");
   H.B = rd<int32_t>(hb, 12);
   for (int d = 0; d < 3; ++d) {
     H.shape[d] = rd<int64_t>(hb, 16 + 8 * d);
-    if (H.shape[d] < 2 || H.shape[d] > (int64_t(1) << 31)) return fail(BM_ERR_CORRUPT, "shape");
+    if (H.shape[d] < 1 || H.shape[d] > (int64_t(1) << 31) || (d < 3 - H.ndim && H.shape[d] != 1))
+      return fail(BM_ERR_CORRUPT, "shape");
   }
   H.total = rd<uint64_t>(hb, 184);
   if (H.total != in_bytes) return fail(BM_ERR_CORRUPT, "stream length does not match its header");
@@ -1651,6 +1780,7 @@ bm_status adjoint_entry(int dir, const int64_t* shape, const Params& prm, T* gfi
   if (prm.R != 1) return fail(BM_ERR_UNSUPPORTED, "the adjoint entry points need one round");
   PlanDev* P = nullptr;
   if (bm_status st = get_plan(shape, prm.B, prm.K, prm.M, prm.R, &P)) return st;
+  if (P->h.reduced) return fail(BM_ERR_UNSUPPORTED, "the adjoint entry points need a 3-D field without extents of 1");
   std::lock_guard<std::mutex> g(g_timer_mu);
   g_timer.begin(s);
   Workspace* ws = nullptr;
@@ -1715,13 +1845,15 @@ bm_status batch_ctx(size_t hbytes, BatchCtx** out) {
   return BM_OK;
 }
 
-bm_status check_item(const bm_batch_item& it, Params& prm) {
+bm_status check_item(const bm_batch_item& it, Params& prm, int64_t s3[3]) {
   if (!it.d_field || !it.d_out) return fail(BM_ERR_ARG, "NULL pointer in a batch item");
-  if (bm_status st = check_shape(it.ndim, it.shape)) return st;
+  if (bm_status st = norm_shape(it.ndim, it.shape, s3)) return st;
   if (it.dtype != BM_F32 && it.dtype != BM_F64) return fail(BM_ERR_ARG, "dtype");
   if (!(it.tol > 0.0) || !std::isfinite(it.tol)) return fail(BM_ERR_ARG, "tolerance must be finite and > 0");
   if (it.tol_mode != BM_ABS && it.tol_mode != BM_REL) return fail(BM_ERR_ARG, "tol_mode");
-  return check_params(&it.params, prm);
+  if (bm_status st = check_params(&it.params, prm)) return st;
+  prm.ndim = it.ndim;
+  return BM_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -1817,14 +1949,15 @@ int bm_stage_times(const char** names, float* ms, int max_stages) {
 }
 
 size_t bm_compress_bound(int ndim, const int64_t* shape, bm_dtype dtype) {
-  if (ndim != 3 || !shape) return 0;
-  for (int d = 0; d < 3; ++d)
-    if (shape[d] < 2 || shape[d] > (int64_t(1) << 31)) return 0;
-  return (size_t)kHeaderBytes + (size_t)nel3(shape) * (dtype == BM_F64 ? 8 : 4);
+  int64_t s3[3];
+  if (norm_shape(ndim, shape, s3) != BM_OK) return 0;
+  return (size_t)kHeaderBytes + (size_t)nel3(s3) * (dtype == BM_F64 ? 8 : 4);
 }
 
 bm_status bm_coeff_count(int ndim, const int64_t* shape, const bm_params* params, size_t* n_coeffs) {
-  if (bm_status st = check_shape(ndim, shape)) return st;
+  int64_t s3_[3];
+  if (bm_status st = norm_shape(ndim, shape, s3_)) return st;
+  shape = s3_;
   Params prm;
   if (bm_status st = check_params(params, prm)) return st;
   PlanDev* P = nullptr;
@@ -1837,12 +1970,15 @@ bm_status bm_compress(const void* d_field, int ndim, const int64_t* shape, bm_dt
                       bm_tol_mode tol_mode, const double* h_roi_tol, const bm_params* params, void* d_out,
                       size_t out_capacity, size_t* out_bytes, void* stream) {
   if (!d_field || !d_out || !out_bytes) return fail(BM_ERR_ARG, "NULL pointer argument");
-  if (bm_status st = check_shape(ndim, shape)) return st;
+  int64_t s3_[3];
+  if (bm_status st = norm_shape(ndim, shape, s3_)) return st;
+  shape = s3_;
   if (dtype != BM_F32 && dtype != BM_F64) return fail(BM_ERR_ARG, "dtype");
   if (!(tol > 0.0) || !std::isfinite(tol)) return fail(BM_ERR_ARG, "tolerance must be finite and > 0");
   if (tol_mode != BM_ABS && tol_mode != BM_REL) return fail(BM_ERR_ARG, "tol_mode");
   Params prm;
   if (bm_status st = check_params(params, prm)) return st;
+  prm.ndim = ndim;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   std::lock_guard<std::mutex> g(g_timer_mu);
   g_timer.begin(s);
@@ -1866,15 +2002,17 @@ bm_status bm_compress_batch(int n, const bm_batch_item* items, size_t* out_bytes
   std::vector<Params> prm((size_t)n);
   std::vector<size_t> slot_off((size_t)n);
   std::vector<bm_status> st((size_t)n, BM_OK);
+  std::vector<std::array<int64_t, 3>> shp((size_t)n);
   size_t hb = 0;
   for (int i = 0; i < n; ++i) {
-    st[(size_t)i] = check_item(items[i], prm[(size_t)i]);
+    st[(size_t)i] = check_item(items[i], prm[(size_t)i], shp[(size_t)i].data());
     int64_t nb = 0;  // blocks of every round
     if (st[(size_t)i] == BM_OK) {
       const Params& q = prm[(size_t)i];
       int64_t m = q.B;
       for (int l = 0; l < q.K; ++l) m = m / 2 + 1;
-      int64_t S[3] = {items[i].shape[0], items[i].shape[1], items[i].shape[2]};
+      const int64_t* s3 = shp[(size_t)i].data();
+      int64_t S[3] = {s3[0], s3[1], s3[2]};
       for (int r = 0; r < q.R; ++r) {
         int64_t nb_round = 1;
         for (int d = 0; d < 3; ++d) {
@@ -1894,8 +2032,8 @@ bm_status bm_compress_batch(int n, const bm_batch_item* items, size_t* out_bytes
   std::vector<int> order((size_t)n);
   for (int i = 0; i < n; ++i) order[(size_t)i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-    return nel3(items[a].shape) * (items[a].dtype == BM_F64 ? 2 : 1) >
-           nel3(items[b].shape) * (items[b].dtype == BM_F64 ? 2 : 1);
+    return nel3(shp[(size_t)a].data()) * (items[a].dtype == BM_F64 ? 2 : 1) >
+           nel3(shp[(size_t)b].data()) * (items[b].dtype == BM_F64 ? 2 : 1);
   });
   std::vector<BatchSlot> slot((size_t)n);
   BM_CUDA(cudaEventRecord(ctx->fork, s));
@@ -1909,11 +2047,11 @@ bm_status bm_compress_batch(int n, const bm_batch_item* items, size_t* out_bytes
     slot[(size_t)i].hd = ctx->hd + slot_off[(size_t)i];
     size_t dummy = 0;
     if (it.dtype == BM_F32)
-      st[(size_t)i] = compress_t<float>(reinterpret_cast<const float*>(it.d_field), it.shape, prm[(size_t)i], it.tol,
+      st[(size_t)i] = compress_t<float>(reinterpret_cast<const float*>(it.d_field), shp[(size_t)i].data(), prm[(size_t)i], it.tol,
                                         it.tol_mode == BM_REL, it.h_roi_tol, reinterpret_cast<uint8_t*>(it.d_out),
                                         it.out_capacity, &dummy, ps, &slot[(size_t)i]);
     else
-      st[(size_t)i] = compress_t<double>(reinterpret_cast<const double*>(it.d_field), it.shape, prm[(size_t)i], it.tol,
+      st[(size_t)i] = compress_t<double>(reinterpret_cast<const double*>(it.d_field), shp[(size_t)i].data(), prm[(size_t)i], it.tol,
                                          it.tol_mode == BM_REL, it.h_roi_tol, reinterpret_cast<uint8_t*>(it.d_out),
                                          it.out_capacity, &dummy, ps, &slot[(size_t)i]);
   }
@@ -2042,7 +2180,9 @@ double bm_perf_model_knee(const bm_perf_model* m, double fraction) {
 bm_status bm_predict_ms(const bm_perf_model* m, int ndim, const int64_t* shape, const bm_params* params,
                         double* ms) {
   if (!m || !ms) return fail(BM_ERR_ARG, "NULL pointer argument");
-  if (bm_status st = check_shape(ndim, shape)) return st;
+  int64_t s3_[3];
+  if (bm_status st = norm_shape(ndim, shape, s3_)) return st;
+  shape = s3_;
   Params prm;
   if (bm_status st = check_params(params, prm)) return st;
   PlanDev* P = nullptr;
@@ -2076,7 +2216,9 @@ bm_status bm_predict_ms(const bm_perf_model* m, int ndim, const int64_t* shape, 
 bm_status bm_select_params(const bm_perf_model* m, int ndim, const int64_t* shape, double budget_ms,
                            bm_params* out, double* predicted_ms) {
   if (!m || !out) return fail(BM_ERR_ARG, "NULL pointer argument");
-  if (bm_status st = check_shape(ndim, shape)) return st;
+  int64_t s3_[3];
+  if (bm_status st = norm_shape(ndim, shape, s3_)) return st;
+  shape = s3_;
   const int B = m->block_nodes ? m->block_nodes : 17;
   const int kmax = B == 9 ? 3 : 4;
   bool found = false;
@@ -2124,8 +2266,11 @@ bm_status bm_stream_info(const void* in, size_t in_bytes, int in_is_device, int*
   if (!in) return fail(BM_ERR_ARG, "NULL stream");
   Header H{};
   if (bm_status st = read_header(in, in_bytes, in_is_device != 0, nullptr, H)) return st;
-  if (ndim) *ndim = 3;
-  if (shape) for (int d = 0; d < 3; ++d) shape[d] = H.shape[d];
+  if (ndim) *ndim = H.ndim;
+  if (shape) {  // the field's own extents first; unused entries 0
+    for (int d = 0; d < 3; ++d) shape[d] = 0;
+    for (int d = 0; d < H.ndim; ++d) shape[d] = H.shape[3 - H.ndim + d];
+  }
   if (dtype) *dtype = H.f64 ? BM_F64 : BM_F32;
   if (n_coeffs) *n_coeffs = H.raw ? 0 : (size_t)H.n_symbols;
   return BM_OK;
@@ -2153,7 +2298,9 @@ bm_status bm_decompress(const void* d_in, size_t in_bytes, void* d_field, void* 
 bm_status bm_decompose(const void* d_field, int ndim, const int64_t* shape, bm_dtype dtype, const bm_params* params,
                        void* d_coeffs, void* stream) {
   if (!d_field || !d_coeffs) return fail(BM_ERR_ARG, "NULL pointer argument");
-  if (bm_status st = check_shape(ndim, shape)) return st;
+  int64_t s3_[3];
+  if (bm_status st = norm_shape(ndim, shape, s3_)) return st;
+  shape = s3_;
   Params prm;
   if (bm_status st = check_params(params, prm)) return st;
   PlanDev* P = nullptr;
@@ -2179,7 +2326,9 @@ bm_status bm_decompose(const void* d_field, int ndim, const int64_t* shape, bm_d
 bm_status bm_recompose(const void* d_coeffs, int ndim, const int64_t* shape, bm_dtype dtype, const bm_params* params,
                        void* d_field, void* stream) {
   if (!d_field || !d_coeffs) return fail(BM_ERR_ARG, "NULL pointer argument");
-  if (bm_status st = check_shape(ndim, shape)) return st;
+  int64_t s3_[3];
+  if (bm_status st = norm_shape(ndim, shape, s3_)) return st;
+  shape = s3_;
   Params prm;
   if (bm_status st = check_params(params, prm)) return st;
   PlanDev* P = nullptr;
@@ -2205,7 +2354,9 @@ bm_status bm_recompose(const void* d_coeffs, int ndim, const int64_t* shape, bm_
 bm_status bm_decompose_adjoint(const void* d_coeff_grad, int ndim, const int64_t* shape, bm_dtype dtype,
                                const bm_params* params, void* d_field_grad, void* stream) {
   if (!d_coeff_grad || !d_field_grad) return fail(BM_ERR_ARG, "NULL pointer argument");
-  if (bm_status st = check_shape(ndim, shape)) return st;
+  int64_t s3_[3];
+  if (bm_status st = norm_shape(ndim, shape, s3_)) return st;
+  shape = s3_;
   Params prm;
   if (bm_status st = check_params(params, prm)) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -2219,7 +2370,9 @@ bm_status bm_decompose_adjoint(const void* d_coeff_grad, int ndim, const int64_t
 bm_status bm_recompose_adjoint(const void* d_field_grad, int ndim, const int64_t* shape, bm_dtype dtype,
                                const bm_params* params, void* d_coeff_grad, void* stream) {
   if (!d_coeff_grad || !d_field_grad) return fail(BM_ERR_ARG, "NULL pointer argument");
-  if (bm_status st = check_shape(ndim, shape)) return st;
+  int64_t s3_[3];
+  if (bm_status st = norm_shape(ndim, shape, s3_)) return st;
+  shape = s3_;
   Params prm;
   if (bm_status st = check_params(params, prm)) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -30,28 +30,43 @@ struct GDim {
   const T* tsup;
   const T* md;          // [n] diagonal of M_f
   const T* mo;          // [n] mo[i] = M_f(i, i+1)
+  int ident;            // 1: the identity of n nodes (c = n); the tables above are not used
 };
+
+// Index tables of a dimension, the identity's computed in place.
+template <typename T> __device__ __forceinline__ int g_cidx(const GDim<T>& D, int i) { return D.ident ? i : D.cidx[i]; }
+template <typename T> __device__ __forceinline__ int g_jlo(const GDim<T>& D, int i) { return D.ident ? i : D.jlo[i]; }
+template <typename T> __device__ __forceinline__ int g_jhi(const GDim<T>& D, int i) { return D.ident ? i : D.jhi[i]; }
+template <typename T> __device__ __forceinline__ T g_wl(const GDim<T>& D, int i) { return D.ident ? T(1) : D.wl[i]; }
+template <typename T> __device__ __forceinline__ T g_wr(const GDim<T>& D, int i) { return D.ident ? T(0) : D.wr[i]; }
+template <typename T> __device__ __forceinline__ int g_cb(const GDim<T>& D, int i) { return D.ident ? i : D.cb[i]; }
+template <typename T> __device__ __forceinline__ bool g_isc(const GDim<T>& D, int i) { return D.ident || D.isc[i]; }
 
 template <typename T>
 struct GLevel {
   GDim<T> d[3];
-  int64_t sym_off;  // first symbol of the level in the stream order
+  int64_t sym_off;    // first symbol of the level in the stream order
+  int64_t blk_extra;  // added per index of dimension 0: 0 for global levels; for the in-cache levels
+                      // of the block-major grid, the symbols of a block's other levels (block-major order)
 };
 
-__device__ __forceinline__ bool all_coarse(const uint8_t* a, const uint8_t* b, const uint8_t* c, int i0, int i1,
-                                           int i2) {
-  return a[i0] && b[i1] && c[i2];
+template <typename T>
+__device__ __forceinline__ bool all_coarse(const GLevel<T>& L, int i0, int i1, int i2) {
+  return g_isc(L.d[0], i0) && g_isc(L.d[1], i1) && g_isc(L.d[2], i2);
 }
 
+// Stream position of the coefficient at (i0, i1, i2), flat index `flat`:
+// its rank among the level's non-coarse nodes (row-major) plus the level's
+// offset and, per index of dimension 0, blk_extra.
 template <typename T>
-__device__ __forceinline__ int64_t nc_rank(const GLevel<T>& L, int i0, int i1, int i2, int64_t flat) {
+__device__ __forceinline__ int64_t nc_pos(const GLevel<T>& L, int i0, int i1, int i2, int64_t flat) {
   const int64_t c1 = L.d[1].c, c2 = L.d[2].c;
-  int64_t before = (int64_t)L.d[0].cb[i0] * c1 * c2;
-  if (L.d[0].isc[i0]) {
-    before += (int64_t)L.d[1].cb[i1] * c2;
-    if (L.d[1].isc[i1]) before += L.d[2].cb[i2];
+  int64_t before = (int64_t)g_cb(L.d[0], i0) * c1 * c2;
+  if (g_isc(L.d[0], i0)) {
+    before += (int64_t)g_cb(L.d[1], i1) * c2;
+    if (g_isc(L.d[1], i1)) before += g_cb(L.d[2], i2);
   }
-  return flat - before;
+  return L.sym_off + flat - before + (int64_t)i0 * L.blk_extra;
 }
 
 // Coefficients of one global level: D = U - I(U|C) at every node (0 at
@@ -60,43 +75,47 @@ __device__ __forceinline__ int64_t nc_rank(const GLevel<T>& L, int i0, int i1, i
 // (mode 1) at their stream position.  One warp
 // per grid row (i0, i1): the row's interpolation sources, weights and stream
 // offset are computed once, the lanes walk i2.
+// With tier != null (the in-cache levels of the block-major grid), the
+// quantiser width of row (i0, i1) is rq_ptr[tier[i0] * tstride] (the block's
+// ROI tier); otherwise rq_ptr[0].
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) gl_fwd_detail(GLevel<T> L, const T* __restrict__ U, T* __restrict__ Dfull,
                                                      uint16_t* sym, int32_t* esc, T* coef, const T* rq_ptr,
-                                                     int radius, Scalars* sc) {
+                                                     int radius, Scalars* sc, const uint8_t* tier = nullptr,
+                                                     int tstride = 0) {
   const GDim<T>&D0 = L.d[0], &D1 = L.d[1], &D2 = L.d[2];
   const int n1 = D1.n, n2 = D2.n;
   const int64_t rows = (int64_t)D0.n * n1, c12 = (int64_t)D1.c * D2.c;
-  const T rq = MODE == 0 ? *rq_ptr : T(0);
   const unsigned dict = 2u * (unsigned)radius;
   bool ovf = false;
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows; row += nwarps) {
     const int i0 = (int)(row / n1), i1 = (int)(row - (int64_t)i0 * n1);
-    const int a0 = D0.cidx[D0.jlo[i0]], b0 = D0.cidx[D0.jhi[i0]];
-    const int a1 = D1.cidx[D1.jlo[i1]], b1 = D1.cidx[D1.jhi[i1]];
-    const T wl0 = D0.wl[i0], wr0 = D0.wr[i0], wl1 = D1.wl[i1], wr1 = D1.wr[i1];
+    const T rq = MODE == 0 ? rq_ptr[tier ? (int)tier[i0] * tstride : 0] : T(0);
+    const int a0 = g_cidx(D0, g_jlo(D0, i0)), b0 = g_cidx(D0, g_jhi(D0, i0));
+    const int a1 = g_cidx(D1, g_jlo(D1, i1)), b1 = g_cidx(D1, g_jhi(D1, i1));
+    const T wl0 = g_wl(D0, i0), wr0 = g_wr(D0, i0), wl1 = g_wl(D1, i1), wr1 = g_wr(D1, i1);
     const T* r00 = U + ((int64_t)a0 * n1 + a1) * n2;
     const T* r01 = U + ((int64_t)a0 * n1 + b1) * n2;
     const T* r10 = U + ((int64_t)b0 * n1 + a1) * n2;
     const T* r11 = U + ((int64_t)b0 * n1 + b1) * n2;
-    const bool cc01 = D0.isc[i0] && D1.isc[i1];  // the row holds all-coarse nodes
+    const bool cc01 = g_isc(D0, i0) && g_isc(D1, i1);  // the row holds all-coarse nodes
     // stream rank of the row's first node: flat index minus the all-coarse nodes before it
-    int64_t before = (int64_t)D0.cb[i0] * c12;
-    if (D0.isc[i0]) before += (int64_t)D1.cb[i1] * D2.c;
-    const int64_t rbase = L.sym_off + row * n2 - before;
+    int64_t before = (int64_t)g_cb(D0, i0) * c12;
+    if (g_isc(D0, i0)) before += (int64_t)g_cb(D1, i1) * D2.c;
+    const int64_t rbase = L.sym_off + row * n2 - before + (int64_t)i0 * L.blk_extra;
     for (int i2 = lane; i2 < n2; i2 += 32) {
-      const int a2 = D2.cidx[D2.jlo[i2]], b2 = D2.cidx[D2.jhi[i2]];
-      const T wl2 = D2.wl[i2], wr2 = D2.wr[i2];
+      const int a2 = g_cidx(D2, g_jlo(D2, i2)), b2 = g_cidx(D2, g_jhi(D2, i2));
+      const T wl2 = g_wl(D2, i2), wr2 = g_wr(D2, i2);
       const T ta = fma(wl1, fma(wl2, r00[a2], wr2 * r00[b2]), wr1 * fma(wl2, r01[a2], wr2 * r01[b2]));
       const T tb = fma(wl1, fma(wl2, r10[a2], wr2 * r10[b2]), wr1 * fma(wl2, r11[a2], wr2 * r11[b2]));
       const T e = fma(wl0, ta, wr0 * tb);
       const int64_t idx = row * n2 + i2;
       const T dv = U[idx] - e;
       Dfull[idx] = dv;
-      if (cc01 && D2.isc[i2]) continue;  // all-coarse node: no coefficient
-      const int64_t pos = rbase + i2 - (cc01 ? D2.cb[i2] : 0);
+      if (cc01 && g_isc(D2, i2)) continue;  // all-coarse node: no coefficient
+      const int64_t pos = rbase + i2 - (cc01 ? g_cb(D2, i2) : 0);
       if (MODE == 0) {
         const int code = quantize(dv, rq, ovf);
         const unsigned u = (unsigned)(code + radius);
@@ -361,13 +380,77 @@ __global__ void __launch_bounds__(256) gl_line(GLevel<T> L, ApplyShape S, const 
   }
 }
 
+// The restriction pass along an identity dimension 0 (the block index of
+// the block-major grid): z = in, elementwise, with FINAL as for gl_apply
+// (1: out = U|C + z; 2: out = U - z; 0: out = z).  in, out: (n0, c1, c2).
+template <typename T, int FINAL>
+__global__ void __launch_bounds__(256) gl_ident0(GLevel<T> L, const T* __restrict__ in, T* __restrict__ out,
+                                                 const T* __restrict__ U) {
+  const int n0 = L.d[0].n, c1 = L.d[1].c, c2 = L.d[2].c, n1 = L.d[1].n, n2 = L.d[2].n;
+  const int64_t total = (int64_t)n0 * c1 * c2;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total; o += (int64_t)gridDim.x * blockDim.x) {
+    const T z = in[o];
+    if (FINAL == 1) {
+      const int j2 = (int)(o % c2);
+      const int64_t t = o / c2;
+      const int j1 = (int)(t % c1);
+      const int i0 = (int)(t / c1);
+      out[o] = U[((int64_t)i0 * n1 + g_cidx(L.d[1], j1)) * n2 + g_cidx(L.d[2], j2)] + z;
+    } else if (FINAL == 2) {
+      out[o] = U[o] - z;
+    } else {
+      out[o] = z;
+    }
+  }
+}
+
+// Between a grid and its blocks in block-major order: block b (row-major
+// over the block grid nb) of edges e[3] (1 along dimensions of extent 1) is
+// stored as a contiguous E1 x E2 tile, its axes the grid dimensions ax[0] and
+// ax[1] (ax[0] = -1: E1 = 1).  DIR 0 gathers (nodes outside the grid read as
+// zero), DIR 1 scatters the nodes inside the grid.
+struct Reblock {
+  int64_t g[3];   // grid shape
+  int e[3];       // block edge per dimension
+  int nb[3];      // blocks per dimension
+  int ax[2];      // grid dimension of tile axis 1 and 2 (-1: none)
+  int E1, E2;     // tile extents
+  int64_t nblk;
+};
+
+template <typename T, int DIR>
+__global__ void __launch_bounds__(256) reblock_kernel(Reblock R, T* __restrict__ grid, T* __restrict__ blocked) {
+  const int64_t total = R.nblk * R.E1 * R.E2;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int k2 = (int)(idx % R.E2);
+    const int64_t t = idx / R.E2;
+    const int k1 = (int)(t % R.E1);
+    const int64_t b = t / R.E1;
+    const int b2 = (int)(b % R.nb[2]);
+    const int64_t t2 = b / R.nb[2];
+    const int b1 = (int)(t2 % R.nb[1]);
+    const int b0 = (int)(t2 / R.nb[1]);
+    int64_t c[3] = {(int64_t)b0 * R.e[0], (int64_t)b1 * R.e[1], (int64_t)b2 * R.e[2]};
+    if (R.ax[0] >= 0) c[R.ax[0]] += k1;
+    c[R.ax[1]] += k2;
+    const bool in = c[0] < R.g[0] && c[1] < R.g[1] && c[2] < R.g[2];
+    const int64_t gi = (c[0] * R.g[1] + c[1]) * R.g[2] + c[2];
+    if (DIR == 0) blocked[idx] = in ? grid[gi] : T(0);
+    else if (in) grid[gi] = blocked[idx];
+  }
+}
+
 // Inverse: dequantised coefficients into a full grid (0 at all-coarse nodes).
+// With tier != null (the in-cache levels of the block-major grid), the
+// quantiser width of the nodes with index i0 is q_ptr[tier[i0] * tstride];
+// the tier byte is range-checked against ntiers (a corrupt stream flags sc).
 template <typename T, int MODE>
 __global__ void gl_inv_dequant(GLevel<T> L, const uint16_t* __restrict__ sym, const int32_t* __restrict__ esc,
-                               const T* __restrict__ coef, const double* q_ptr, int radius, T* __restrict__ Dfull) {
+                               const T* __restrict__ coef, const double* q_ptr, int radius, T* __restrict__ Dfull,
+                               const uint8_t* tier = nullptr, int tstride = 0, int ntiers = 1, Scalars* sc = nullptr) {
   const int n0 = L.d[0].n, n1 = L.d[1].n, n2 = L.d[2].n;
   const int64_t total = (int64_t)n0 * n1 * n2;
-  const T q = MODE == 0 ? (T)*q_ptr : T(0);
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int i2 = (int)(idx % n2);
@@ -375,8 +458,14 @@ __global__ void gl_inv_dequant(GLevel<T> L, const uint16_t* __restrict__ sym, co
     const int i1 = (int)(t % n1);
     const int i0 = (int)(t / n1);
     T v = T(0);
-    if (!all_coarse(L.d[0].isc, L.d[1].isc, L.d[2].isc, i0, i1, i2)) {
-      const int64_t pos = L.sym_off + nc_rank(L, i0, i1, i2, idx);
+    if (!all_coarse(L, i0, i1, i2)) {
+      const int64_t pos = nc_pos(L, i0, i1, i2, idx);
+      int tr = tier ? (int)tier[i0] : 0;
+      if (tr >= ntiers) {
+        if (sc) atomicOr(&sc->status, ST_CORRUPT);
+        tr = 0;
+      }
+      const T q = MODE == 0 ? (T)q_ptr[tr * tstride] : T(0);
       if (MODE == 0) {
         const unsigned s = sym[pos];
         const int code = s ? (int)s - radius : esc[pos];
@@ -401,12 +490,12 @@ __global__ void gl_inv_interp(GLevel<T> L, const T* __restrict__ Uc, T* __restri
     const int64_t t = idx / n2;
     const int i1 = (int)(t % n1);
     const int i0 = (int)(t / n1);
-    const int a0 = L.d[0].jlo[i0], b0 = L.d[0].jhi[i0];
-    const int a1 = L.d[1].jlo[i1], b1 = L.d[1].jhi[i1];
-    const int a2 = L.d[2].jlo[i2], b2 = L.d[2].jhi[i2];
-    const T wl0 = L.d[0].wl[i0], wr0 = L.d[0].wr[i0];
-    const T wl1 = L.d[1].wl[i1], wr1 = L.d[1].wr[i1];
-    const T wl2 = L.d[2].wl[i2], wr2 = L.d[2].wr[i2];
+    const int a0 = g_jlo(L.d[0], i0), b0 = g_jhi(L.d[0], i0);
+    const int a1 = g_jlo(L.d[1], i1), b1 = g_jhi(L.d[1], i1);
+    const int a2 = g_jlo(L.d[2], i2), b2 = g_jhi(L.d[2], i2);
+    const T wl0 = g_wl(L.d[0], i0), wr0 = g_wr(L.d[0], i0);
+    const T wl1 = g_wl(L.d[1], i1), wr1 = g_wr(L.d[1], i1);
+    const T wl2 = g_wl(L.d[2], i2), wr2 = g_wr(L.d[2], i2);
     auto s = [&](int x0, int x1) {
       const T* row = Uc + ((int64_t)x0 * c1 + x1) * c2;
       return fma(wl2, row[a2], wr2 * row[b2]);

@@ -188,9 +188,24 @@ std::string make_plan(const int64_t* shape, int B, int K, int M, int R, PlanHost
   p = PlanHost{};
   for (int d = 0; d < 3; ++d) p.shape[d] = shape[d];
   p.B = B; p.K = K; p.M = M; p.R = R;
+  // a dimension of extent 1 (the missing dimensions of a 1-D or 2-D field)
+  // is neither blocked nor coarsened
+  int nonunit = 0;
+  for (int d = 0; d < 3; ++d) {
+    if (shape[d] < 1) return "every extent must be at least 1";
+    p.Bd[d] = shape[d] == 1 ? 1 : B;
+    if (shape[d] > 1) {
+      if (nonunit < 2) p.ax[nonunit] = d;
+      ++nonunit;
+    }
+  }
+  if (nonunit == 0) return "a field needs at least two values";
+  p.reduced = nonunit < 3;
+  if (p.reduced && nonunit == 1) { p.ax[1] = p.ax[0]; p.ax[0] = -1; }
+  if (p.reduced && R > 1) return "re-blocking rounds need a 3-D field without extents of 1";
   p.nblocks = 1;
   for (int d = 0; d < 3; ++d) {
-    const int64_t nb = (shape[d] + B - 1) / B;
+    const int64_t nb = (shape[d] + p.Bd[d] - 1) / p.Bd[d];
     if (nb > (1 << 30)) return "shape too large";
     p.nb[d] = (int)nb;
     p.nblocks *= nb;
@@ -199,19 +214,43 @@ std::string make_plan(const int64_t* shape, int B, int K, int M, int R, PlanHost
   std::vector<double> xl(B);
   for (int j = 0; j < B; ++j) xl[j] = j;
   p.per_block = 0;
+  const Dim1DHost one = make_dim(std::vector<double>{0.0});
+  std::vector<int64_t> lvl_cnt;
+  std::vector<Dim1DHost> lvl_dim;
   for (int l = 0; l < K; ++l) {
     const int n = (int)xl.size();
     if (n < 3) return "too many in-cache levels for this block size";
     std::vector<int> ci = coarse_of(n);
-    p.per_block += (int64_t)n * n * n - (int64_t)ci.size() * ci.size() * ci.size();
+    int64_t nn = 1, cc = 1;
+    for (int d = 0; d < 3; ++d) {
+      nn *= p.Bd[d] == 1 ? 1 : n;
+      cc *= p.Bd[d] == 1 ? 1 : (int64_t)ci.size();
+    }
+    lvl_cnt.push_back(nn - cc);
+    p.per_block += nn - cc;
     Dim1DHost D = make_dim(xl);
-    const Dim1DHost D3[3] = {D, D, D};
+    const Dim1DHost D3[3] = {p.Bd[0] == 1 ? one : D, p.Bd[1] == 1 ? one : D, p.Bd[2] == 1 ? one : D};
     p.A.push_back(error_constant(D3));
+    lvl_dim.push_back(D);
     std::vector<double> nx;
     for (int j : ci) nx.push_back(xl[j]);
     xl = nx;
   }
   p.m = (int)xl.size();
+  for (int d = 0; d < 3; ++d) p.md[d] = p.Bd[d] == 1 ? 1 : p.m;
+  if (p.reduced) {
+    int64_t off = 0;
+    for (int l = 0; l < K; ++l) {
+      RLevelHost rl;
+      rl.nblk = p.nblocks;
+      rl.da = p.ax[0] < 0 ? one : lvl_dim[(size_t)l];
+      rl.db = lvl_dim[(size_t)l];
+      rl.off = off;
+      rl.blk_extra = p.per_block - lvl_cnt[(size_t)l];
+      off += lvl_cnt[(size_t)l];
+      p.rlev.push_back(rl);
+    }
+  }
   // re-blocking rounds (Sec. III-C): round r+1 blocks round r's gathered grid
   int64_t S[3] = {shape[0], shape[1], shape[2]};
   int64_t pos = 0;
@@ -220,12 +259,12 @@ std::string make_plan(const int64_t* shape, int B, int K, int M, int R, PlanHost
     RoundHost rd{};
     rd.nblocks = 1;
     for (int d = 0; d < 3; ++d) {
-      const int64_t nb = (S[d] + B - 1) / B;
+      const int64_t nb = (S[d] + p.Bd[d] - 1) / p.Bd[d];
       if (nb > (1 << 30)) return "shape too large";
       rd.shape[d] = S[d];
       rd.nb[d] = (int)nb;
       rd.nblocks *= nb;
-      rd.gshape[d] = nb * p.m;
+      rd.gshape[d] = nb * p.md[d];
     }
     rd.off = pos;
     pos += rd.nblocks * p.per_block;
@@ -241,7 +280,7 @@ std::string make_plan(const int64_t* shape, int B, int K, int M, int R, PlanHost
     p.gshape[d] = S[d];
     if (R == 1) {
       for (int b = 0; b < p.nb[d]; ++b)
-        for (int j = 0; j < p.m; ++j) gx[d].push_back((double)b * B + xl[j]);
+        for (int j = 0; j < p.md[d]; ++j) gx[d].push_back((double)b * p.Bd[d] + (p.Bd[d] == 1 ? 0.0 : xl[j]));
     } else {
       for (int64_t i = 0; i < S[d]; ++i) gx[d].push_back((double)i);
     }
@@ -252,7 +291,6 @@ std::string make_plan(const int64_t* shape, int B, int K, int M, int R, PlanHost
     if (l == M) break;
     std::vector<Dim1DHost> L3;
     for (int d = 0; d < 3; ++d) {
-      if (gx[d].size() < 2) return "global level on a dimension with fewer than 2 nodes";
       L3.push_back(make_dim(gx[d]));
       L3.back().P = projection(L3.back());
     }

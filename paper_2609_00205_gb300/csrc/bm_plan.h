@@ -32,9 +32,25 @@ struct RoundHost {
   int64_t gshape[3]; // gathered coarse grid (nb * m)
 };
 
+// One in-cache level of a field with a dimension of extent 1, run on the
+// block-major grid (block, a, b): the block index is an identity dimension
+// (not tabulated), a and b the block's two remaining axes (a has one node for
+// a 1-D field).
+struct RLevelHost {
+  int64_t nblk;                 // blocks (identity dimension)
+  Dim1DHost da, db;             // the level's operators along the in-block axes
+  int64_t off;                  // first symbol of the level inside block 0
+  int64_t blk_extra;            // per block: symbols of the other levels (block-major order)
+};
+
 struct PlanHost {
   int64_t shape[3];
   int B, K, M, R;
+  int Bd[3];         // block edge per dimension: B, or 1 for a dimension of extent 1
+  int md[3];         // coarse nodes per block edge after K levels, per dimension
+  bool reduced = false;         // some dimension has extent 1: in-cache levels on the block-major grid
+  int ax[2] = {-1, -1};         // field dimensions of the block-major grid's axes a and b (-1: one node)
+  std::vector<RLevelHost> rlev; // [K] (reduced only)
   int nb[3];         // round 0
   int64_t nblocks;   // round 0
   std::vector<RoundHost> rounds;

@@ -5,11 +5,22 @@ import numpy as np
 import oracle
 
 
-def local_counts(B, K):
+def block_edges(shape3, B):
+    """Block edge per dimension of a 3-D shape: B, or 1 along an extent of 1."""
+    return [1 if n == 1 else B for n in shape3]
+
+
+def local_counts(B, K, shape3=(2, 2, 2)):
+    """Coefficients of each in-cache level inside one block (a dimension of
+    extent 1 is neither blocked nor coarsened)."""
     out, n = [], B
     for _ in range(K):
         c = n // 2 + 1
-        out.append(n ** 3 - c ** 3)
+        nn = cc = 1
+        for e in shape3:
+            nn *= 1 if e == 1 else n
+            cc *= 1 if e == 1 else c
+        out.append(nn - cc)
         n = c
     return out
 
@@ -26,7 +37,7 @@ def q_per_coeff(stream):
         tier = np.asarray(stream[h["off_blocktier"]:h["off_blocktier"] + p["nblocks"]]).astype(np.int64)
     else:
         tier = np.zeros(p["nblocks"], dtype=np.int64)
-    lc = local_counts(B, K)
+    lc = local_counts(B, K, h["shape"])
     per_level = np.concatenate([np.full(c, l) for l, c in enumerate(lc)]) if K else np.zeros(0, np.int64)
     local = q[(tier[:, None] * K + per_level[None, :]).ravel()]
     parts = [local]
@@ -85,7 +96,8 @@ def hard_gate(codes_gpu, coef_gpu, q, f64):
 
 
 def per_block_tau(stream, shape, B):
-    """Absolute tolerance of every node, from the stream's tiers and block tiers."""
+    """Absolute tolerance of every node, from the stream's tiers and block
+    tiers, in the field's own shape."""
     h = oracle.stream_header(stream)
     nt = h["n_tiers"]
     tiers = np.asarray(stream[h["off_tiers"]:h["off_tiers"] + 8 * nt]).view(np.float64)
@@ -94,9 +106,11 @@ def per_block_tau(stream, shape, B):
         tier = np.asarray(stream[h["off_blocktier"]:h["off_blocktier"] + int(np.prod(nb))]).astype(np.int64)
     else:
         tier = np.zeros(int(np.prod(nb)), dtype=np.int64)
+    s3 = h["shape"]
     t = tiers[tier].reshape(nb)
-    t = np.repeat(np.repeat(np.repeat(t, B, 0), B, 1), B, 2)
-    return t[: shape[0], : shape[1], : shape[2]]
+    for ax, e in enumerate(block_edges(s3, B)):
+        t = np.repeat(t, e, ax)
+    return t[: s3[0], : s3[1], : s3[2]].reshape(shape)
 
 
 def coef_tol(u):

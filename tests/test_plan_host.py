@@ -15,7 +15,9 @@ import pytest
 import oracle
 
 SHAPES = [(2, 3, 2), (9, 9, 9), (10, 9, 8), (17, 17, 17), (18, 35, 52), (40, 37, 45), (65, 65, 65),
-          (33, 5, 70), (129, 17, 3), (100, 101, 102)]
+          (33, 5, 70), (129, 17, 3), (100, 101, 102),
+          # 1-D and 2-D fields and explicit extents of 1
+          (500,), (3,), (120, 91), (2, 3), (40, 1, 23), (1, 1, 300), (300, 1, 1)]
 PARAMS = [(9, k, m) for k in (1, 2, 3) for m in (0, 1, 2, 3)] + [(17, k, m) for k in (1, 2, 3, 4) for m in (0, 1, 2)]
 
 
