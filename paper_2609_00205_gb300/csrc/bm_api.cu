@@ -222,6 +222,8 @@ struct PlanDev {
   std::vector<GLevel<double>> gd;
   std::vector<GLevel<float>> rf;   // in-cache levels on the block-major grid (fields with an extent of 1)
   std::vector<GLevel<double>> rd;
+  std::vector<std::vector<GLevel<float>>> xf;   // [round][level] blocked levels (no fused block kernel)
+  std::vector<std::vector<GLevel<double>>> xd;
 };
 std::mutex g_plan_mu;
 std::map<std::tuple<int64_t, int64_t, int64_t, int, int, int, int>, std::unique_ptr<PlanDev>> g_plans;
@@ -232,6 +234,12 @@ template <>
 std::vector<GLevel<float>>& glevels<float>(PlanDev& p) { return p.gf; }
 template <>
 std::vector<GLevel<double>>& glevels<double>(PlanDev& p) { return p.gd; }
+template <typename T>
+std::vector<std::vector<GLevel<T>>>& xlevels(PlanDev& p);
+template <>
+std::vector<std::vector<GLevel<float>>>& xlevels<float>(PlanDev& p) { return p.xf; }
+template <>
+std::vector<std::vector<GLevel<double>>>& xlevels<double>(PlanDev& p) { return p.xd; }
 template <typename T>
 std::vector<GLevel<T>>& rlevels(PlanDev& p);
 template <>
@@ -264,6 +272,9 @@ bm_status upload_tables(PlanDev& P) {
     dims.push_back(&rl.da);
     dims.push_back(&rl.db);
   }
+  for (auto& rlv : P.h.xlev)
+    for (auto& X : rlv)
+      for (int d = 0; d < 3; ++d) dims.push_back(&X.d[d]);
   for (const Dim1DHost* Dp : dims) {
     const Dim1DHost& D = *Dp;
     {
@@ -344,6 +355,26 @@ bm_status upload_tables(PlanDev& P) {
     L.blk_extra = rl.blk_extra;
     RL.push_back(L);
   }
+  auto& XL = xlevels<T>(P);
+  XL.clear();
+  for (auto& rlv : P.h.xlev) {
+    std::vector<GLevel<T>> lv;
+    for (auto& X : rlv) {
+      GLevel<T> L{};
+      for (int d = 0; d < 3; ++d) {
+        fill(L.d[d], offs[k++], X.d[d]);
+        L.be[d] = X.e[d];
+        L.bce[d] = X.ce[d];
+        L.bnb[d] = X.nb[d];
+      }
+      L.sym_off = X.sym_off;
+      L.blk_extra = 0;
+      L.bmode = 1;
+      L.bpb = P.h.per_block;
+      lv.push_back(L);
+    }
+    XL.push_back(lv);
+  }
   return BM_OK;
 }
 
@@ -375,8 +406,9 @@ bm_status check_params(const bm_params* p, Params& o) {
   o.radius = (p && p->dict_radius) ? p->dict_radius : kMaxDict / 2;
   o.R = (p && p->rounds) ? p->rounds : 1;
   if (o.R < 1 || o.R > 8) return fail(BM_ERR_ARG, "rounds must be in [1, 8]");
-  if (o.B != 9 && o.B != 17) return fail(BM_ERR_UNSUPPORTED, "block_nodes must be 9 or 17 in this build");
-  const int kmax = o.B == 9 ? 3 : 4;
+  if (o.B < 3 || o.B > 64) return fail(BM_ERR_ARG, "block_nodes must be in [3, 64]");
+  int kmax = 0;  // levels while a block edge still has at least 3 nodes
+  for (int n = o.B; n >= 3; n = n / 2 + 1) ++kmax;
   if (o.K < 1 || o.K > kmax) return fail(BM_ERR_ARG, "incache_levels out of range for this block size");
   if (o.M > 16) return fail(BM_ERR_ARG, "global_levels too large");
   if (o.chunk < 64 || o.chunk > 2048 || o.chunk % 32) return fail(BM_ERR_ARG, "chunk_symbols must be a multiple of 32 in [64, 2048]");
@@ -409,6 +441,7 @@ struct GSizes {
   std::vector<int64_t> U;
   int64_t D = 0, W1 = 0, W2 = 0;
   std::vector<int64_t> RB;
+  std::vector<int64_t> XP;  // padded grids of the blocked levels 0..K-1 (no fused block kernel)
 };
 GSizes gsizes(const PlanHost& h) {
   GSizes g;
@@ -419,6 +452,21 @@ GSizes gsizes(const PlanHost& h) {
     const int64_t c0 = h.lshape[3 * l + 3], c1 = h.lshape[3 * l + 4], c2 = h.lshape[3 * l + 5];
     g.W1 = std::max(g.W1, n0 * n1 * c2);
     g.W2 = std::max(g.W2, std::max(n0 * c1 * c2, c0 * c1 * c2));
+  }
+  if (h.generic) {  // padded grids of every level, sized for the largest round
+    for (int l = 0; l < h.K; ++l) {
+      int64_t big = 0;
+      for (const auto& rlv : h.xlev) {
+        const XLevelHost& X = rlv[(size_t)l];
+        const int64_t n0 = X.shape[0], n1 = X.shape[1], n2 = X.shape[2];
+        const int64_t c0 = X.d[0].c, c1 = X.d[1].c, c2 = X.d[2].c;
+        big = std::max(big, n0 * n1 * n2);
+        g.W1 = std::max(g.W1, n0 * n1 * c2);
+        g.W2 = std::max(g.W2, std::max(n0 * c1 * c2, c0 * c1 * c2));
+      }
+      g.XP.push_back(big);
+      g.D = std::max(g.D, big);
+    }
   }
   if (h.reduced) {
     for (const RLevelHost& rl : h.rlev) {
@@ -990,6 +1038,40 @@ bm_status run_decompose(PlanDev& P, const T* field, int mode, const FwdOut<T>& o
     reblock_kernel<T, 1><<<grid_for(gs.RB.back(), 256), 256, 0, s>>>(rc, Gr[0], RB.back());
     g_launches.fetch_add(2);
     BM_CUDA(cudaGetLastError());
+  } else if (h.generic) {  // no fused block kernel: blocked levels on each round's padded grid
+    Stage st("incache_decompose");
+    std::vector<T*> XP;
+    for (int64_t n : gs.XP) XP.push_back(cv.take<T>((size_t)n));
+    int64_t toff = 0;
+    for (size_t r = 0; r < h.rounds.size(); ++r) {
+      const RoundHost& rd = h.rounds[r];
+      const auto& XL = xlevels<T>(P)[r];
+      const XLevelHost& X0 = h.xlev[r][0];
+      const T* in = r == 0 ? field : Gr[r - 1];
+      const int64_t npad = X0.shape[0] * X0.shape[1] * X0.shape[2];
+      pad_kernel<T, 0><<<grid_for(npad, 256), 256, 0, s>>>(in, XP[0], rd.shape[0], rd.shape[1], rd.shape[2],
+                                                           X0.shape[0], X0.shape[1], X0.shape[2]);
+      g_launches.fetch_add(1);
+      const uint8_t* tier = o.tier ? o.tier + toff : nullptr;
+      for (int l = 0; l < h.K; ++l) {
+        const GLevel<T>& L = XL[(size_t)l];
+        T* next = l + 1 < h.K ? XP[(size_t)l + 1] : Gr[r];
+        const int64_t rows = (int64_t)L.d[0].n * L.d[1].n;
+        const T* rq = o.rq ? o.rq + l : nullptr;
+        if (mode == 0)
+          gl_fwd_detail<T, 0><<<grid_for(rows * 32, 256, 8), 256, 0, s>>>(L, XP[(size_t)l], Dbuf, o.sym, o.esc,
+                                                                         o.coef, rq, o.radius, o.sc, tier, h.K);
+        else
+          gl_fwd_detail<T, 1><<<grid_for(rows * 32, 256, 8), 256, 0, s>>>(L, XP[(size_t)l], Dbuf, o.sym, o.esc, o.coef,
+                                                                         rq, o.radius, o.sc, nullptr, 0);
+        BM_CUDA((launch_apply<T, 2, 0>(L, Dbuf, W1, nullptr, s)));
+        BM_CUDA((launch_apply<T, 1, 0>(L, W1, W2, nullptr, s)));
+        BM_CUDA((launch_apply<T, 0, 1>(L, W2, next, XP[(size_t)l], s)));
+        g_launches.fetch_add(4);
+      }
+      toff += rd.nblocks;
+    }
+    BM_CUDA(cudaGetLastError());
   } else {
     Stage st("incache_decompose");
     int64_t toff = 0;
@@ -1123,6 +1205,41 @@ bm_status run_recompose(PlanDev& P, T* field, int mode, const InvIn<T>& in, Carv
     reblock_kernel<T, 1><<<grid_for(gs.RB[0], 256), 256, 0, s>>>(rf, field, RB[0]);
     g_launches.fetch_add(2);
     BM_CUDA(cudaGetLastError());
+  } else if (h.generic) {
+    Stage st("incache_recompose");
+    std::vector<T*> XP;
+    for (int64_t n : gs.XP) XP.push_back(cv.take<T>((size_t)n));
+    std::vector<int64_t> toff(h.rounds.size(), 0);
+    for (size_t r = 1; r < h.rounds.size(); ++r) toff[r] = toff[r - 1] + h.rounds[r - 1].nblocks;
+    T* Cn = Dbuf;
+    for (size_t rr = h.rounds.size(); rr-- > 0;) {  // last round first: each restores its input grid
+      const RoundHost& rd = h.rounds[rr];
+      const auto& XL = xlevels<T>(P)[rr];
+      const XLevelHost& X0 = h.xlev[rr][0];
+      const uint8_t* tier = in.tier ? in.tier + toff[rr] : nullptr;
+      for (int l = h.K - 1; l >= 0; --l) {
+        const GLevel<T>& L = XL[(size_t)l];
+        T* coarse = l + 1 < h.K ? XP[(size_t)l + 1] : Gr[rr];
+        const double* q = in.q ? in.q + l : nullptr;
+        const int64_t nn = (int64_t)L.d[0].n * L.d[1].n * L.d[2].n;
+        if (mode == 0)
+          gl_inv_dequant<T, 0><<<grid_for(nn, 256), 256, 0, s>>>(L, in.sym, in.esc, in.coef, q, in.radius,
+                                                                  XP[(size_t)l], tier, h.K, in.ntiers, in.sc);
+        else
+          gl_inv_dequant<T, 1><<<grid_for(nn, 256), 256, 0, s>>>(L, in.sym, in.esc, in.coef, q, in.radius,
+                                                                  XP[(size_t)l]);
+        BM_CUDA((launch_apply<T, 2, 0>(L, XP[(size_t)l], W1, nullptr, s)));
+        BM_CUDA((launch_apply<T, 1, 0>(L, W1, W2, nullptr, s)));
+        BM_CUDA((launch_apply<T, 0, 2>(L, W2, Cn, coarse, s)));
+        gl_inv_interp<T><<<grid_for(nn, 256), 256, 0, s>>>(L, Cn, XP[(size_t)l]);
+        g_launches.fetch_add(5);
+      }
+      T* out = rr == 0 ? field : Gr[rr - 1];
+      pad_kernel<T, 1><<<grid_for(rd.shape[0] * rd.shape[1] * rd.shape[2], 256), 256, 0, s>>>(
+          XP[0], out, rd.shape[0], rd.shape[1], rd.shape[2], X0.shape[0], X0.shape[1], X0.shape[2]);
+      g_launches.fetch_add(1);
+    }
+    BM_CUDA(cudaGetLastError());
   } else {
     Stage st("incache_recompose");
     std::vector<int64_t> toff(h.rounds.size(), 0);
@@ -1155,6 +1272,7 @@ size_t decompose_scratch(const PlanHost& h, size_t esize) {
   size_t b = 0;
   for (int64_t u : gs.U) b += (size_t)u * esize + 256;
   for (int64_t u : gs.RB) b += (size_t)u * esize + 256;
+  for (int64_t u : gs.XP) b += (size_t)u * esize + 256;
   for (size_t r = 0; r + 1 < h.rounds.size(); ++r)
     b += (size_t)(h.rounds[r].gshape[0] * h.rounds[r].gshape[1] * h.rounds[r].gshape[2]) * esize + 256;
   b += ((size_t)gs.D + gs.W1 + gs.W2 + 3) * esize + 768;
@@ -1545,7 +1663,9 @@ bm_status parse_header(const unsigned char* hb, size_t in_bytes, Header& H) {
   H.codebook_bytes = rd<uint32_t>(hb, 192); H.n_runs = rd<uint32_t>(hb, 196);
   H.R = (int)rd<uint32_t>(hb, 224) + 1;
   if (H.R < 1 || H.R > 8) return fail(BM_ERR_CORRUPT, "rounds");
-  if ((H.B != 9 && H.B != 17) || H.K < 1 || H.K > (H.B == 9 ? 3 : 4) || H.M < 0 || H.M > 16 || H.chunk < 64 ||
+  int kmax = 0;  // levels while a block edge still has at least 3 nodes
+  for (int n = H.B; n >= 3 && n <= 64; n = n / 2 + 1) ++kmax;
+  if (H.B < 3 || H.B > 64 || H.K < 1 || H.K > kmax || H.M < 0 || H.M > 16 || H.chunk < 64 ||
       H.chunk > 2048 || H.chunk % 32 || H.radius < 16 || H.radius > kMaxDict / 2 || H.ntiers < 1 || H.ntiers > 255)
     return fail(BM_ERR_CORRUPT, "header parameters out of range");
   const unsigned long long nq = (unsigned long long)H.ntiers * H.K + H.M + 1;
@@ -1781,6 +1901,7 @@ bm_status adjoint_entry(int dir, const int64_t* shape, const Params& prm, T* gfi
   PlanDev* P = nullptr;
   if (bm_status st = get_plan(shape, prm.B, prm.K, prm.M, prm.R, &P)) return st;
   if (P->h.reduced) return fail(BM_ERR_UNSUPPORTED, "the adjoint entry points need a 3-D field without extents of 1");
+  if (P->h.generic) return fail(BM_ERR_UNSUPPORTED, "the adjoint entry points need block_nodes 9 or 17");
   std::lock_guard<std::mutex> g(g_timer_mu);
   g_timer.begin(s);
   Workspace* ws = nullptr;

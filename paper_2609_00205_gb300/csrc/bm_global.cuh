@@ -48,7 +48,41 @@ struct GLevel {
   int64_t sym_off;    // first symbol of the level in the stream order
   int64_t blk_extra;  // added per index of dimension 0: 0 for global levels; for the in-cache levels
                       // of the block-major grid, the symbols of a block's other levels (block-major order)
+  // Blocked levels (the in-cache levels of the padded grid of a round's
+  // blocks, block-diagonal operators): coefficients are stored block by
+  // block, bpb symbols per block, each block's level row-major over its own
+  // non-coarse nodes; be / bce: a block's extent and coarse count per
+  // dimension, bnb: blocks per dimension.  bmode = 0 otherwise.
+  int bmode;
+  int be[3], bce[3], bnb[3];
+  int64_t bpb;
 };
+
+// Block (row-major over the block grid) of a node of a blocked level.
+template <typename T>
+__device__ __forceinline__ int64_t blk_of(const GLevel<T>& L, int i0, int i1, int i2) {
+  return ((int64_t)(i0 / L.be[0]) * L.bnb[1] + i1 / L.be[1]) * L.bnb[2] + i2 / L.be[2];
+}
+
+// Stream position of a non-coarse node of a blocked level.
+template <typename T>
+__device__ __forceinline__ int64_t blk_pos(const GLevel<T>& L, int i0, int i1, int i2) {
+  const int b0 = i0 / L.be[0], b1 = i1 / L.be[1], b2 = i2 / L.be[2];
+  const int k0 = i0 - b0 * L.be[0], k1 = i1 - b1 * L.be[1], k2 = i2 - b2 * L.be[2];
+  // coarse nodes of the block before the node: from the line tables, whose
+  // coarse counts run over the whole padded line
+  const int64_t c0 = L.d[0].cb[i0] - (int64_t)b0 * L.bce[0];
+  const int64_t c1 = L.d[1].cb[i1] - (int64_t)b1 * L.bce[1];
+  const int64_t c2 = L.d[2].cb[i2] - (int64_t)b2 * L.bce[2];
+  int64_t before = c0 * L.bce[1] * L.bce[2];
+  if (L.d[0].isc[i0]) {
+    before += c1 * L.bce[2];
+    if (L.d[1].isc[i1]) before += c2;
+  }
+  const int64_t flat = ((int64_t)k0 * L.be[1] + k1) * L.be[2] + k2;
+  const int64_t b = ((int64_t)b0 * L.bnb[1] + b1) * L.bnb[2] + b2;
+  return L.sym_off + b * L.bpb + flat - before;
+}
 
 template <typename T>
 __device__ __forceinline__ bool all_coarse(const GLevel<T>& L, int i0, int i1, int i2) {
@@ -60,6 +94,7 @@ __device__ __forceinline__ bool all_coarse(const GLevel<T>& L, int i0, int i1, i
 // offset and, per index of dimension 0, blk_extra.
 template <typename T>
 __device__ __forceinline__ int64_t nc_pos(const GLevel<T>& L, int i0, int i1, int i2, int64_t flat) {
+  if (L.bmode) return blk_pos(L, i0, i1, i2);
   const int64_t c1 = L.d[1].c, c2 = L.d[2].c;
   int64_t before = (int64_t)g_cb(L.d[0], i0) * c1 * c2;
   if (g_isc(L.d[0], i0)) {
@@ -92,7 +127,7 @@ __global__ void __launch_bounds__(256) gl_fwd_detail(GLevel<T> L, const T* __res
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows; row += nwarps) {
     const int i0 = (int)(row / n1), i1 = (int)(row - (int64_t)i0 * n1);
-    const T rq = MODE == 0 ? rq_ptr[tier ? (int)tier[i0] * tstride : 0] : T(0);
+    const T rq_row = MODE == 0 && !L.bmode ? rq_ptr[tier ? (int)tier[i0] * tstride : 0] : T(0);
     const int a0 = g_cidx(D0, g_jlo(D0, i0)), b0 = g_cidx(D0, g_jhi(D0, i0));
     const int a1 = g_cidx(D1, g_jlo(D1, i1)), b1 = g_cidx(D1, g_jhi(D1, i1));
     const T wl0 = g_wl(D0, i0), wr0 = g_wr(D0, i0), wl1 = g_wl(D1, i1), wr1 = g_wr(D1, i1);
@@ -115,7 +150,14 @@ __global__ void __launch_bounds__(256) gl_fwd_detail(GLevel<T> L, const T* __res
       const T dv = U[idx] - e;
       Dfull[idx] = dv;
       if (cc01 && g_isc(D2, i2)) continue;  // all-coarse node: no coefficient
-      const int64_t pos = rbase + i2 - (cc01 ? g_cb(D2, i2) : 0);
+      int64_t pos;
+      T rq = rq_row;
+      if (L.bmode) {  // block-major order; the block's ROI tier
+        pos = blk_pos(L, i0, i1, i2);
+        if (MODE == 0) rq = rq_ptr[tier ? (int)tier[blk_of(L, i0, i1, i2)] * tstride : 0];
+      } else {
+        pos = rbase + i2 - (cc01 ? g_cb(D2, i2) : 0);
+      }
       if (MODE == 0) {
         const int code = quantize(dv, rq, ovf);
         const unsigned u = (unsigned)(code + radius);
@@ -441,6 +483,22 @@ __global__ void __launch_bounds__(256) reblock_kernel(Reblock R, T* __restrict__
   }
 }
 
+// Between a grid of shape S and its zero-padded copy of shape P (P >= S per
+// dimension, the padding at the high end): DIR 0 pads (dst = padded),
+// DIR 1 crops (dst = the grid).
+template <typename T, int DIR>
+__global__ void __launch_bounds__(256) pad_kernel(const T* __restrict__ src, T* __restrict__ dst, int64_t s0,
+                                                  int64_t s1, int64_t s2, int64_t p0, int64_t p1, int64_t p2) {
+  const int64_t total = DIR == 0 ? p0 * p1 * p2 : s0 * s1 * s2;
+  const int64_t n1 = DIR == 0 ? p1 : s1, n2 = DIR == 0 ? p2 : s2;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i2 = idx % n2, t = idx / n2, i1 = t % n1, i0 = t / n1;
+    if (DIR == 0) dst[idx] = (i0 < s0 && i1 < s1 && i2 < s2) ? src[(i0 * s1 + i1) * s2 + i2] : T(0);
+    else dst[idx] = src[(i0 * p1 + i1) * p2 + i2];
+  }
+}
+
 // Inverse: dequantised coefficients into a full grid (0 at all-coarse nodes).
 // With tier != null (the in-cache levels of the block-major grid), the
 // quantiser width of the nodes with index i0 is q_ptr[tier[i0] * tstride];
@@ -460,7 +518,7 @@ __global__ void gl_inv_dequant(GLevel<T> L, const uint16_t* __restrict__ sym, co
     T v = T(0);
     if (!all_coarse(L, i0, i1, i2)) {
       const int64_t pos = nc_pos(L, i0, i1, i2, idx);
-      int tr = tier ? (int)tier[i0] : 0;
+      int tr = tier ? (int)tier[L.bmode ? blk_of(L, i0, i1, i2) : (int64_t)i0] : 0;
       if (tr >= ntiers) {
         if (sc) atomicOr(&sc->status, ST_CORRUPT);
         tr = 0;

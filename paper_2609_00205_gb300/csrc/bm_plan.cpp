@@ -102,6 +102,42 @@ Dim1DHost make_dim(const std::vector<double>& x) {
   return D;
 }
 
+// nb copies of the level on block-local coordinates xs side by side, with
+// no coupling between them: every index table shifted by the segment, the
+// band rows kept inside their segment (make_dim zeroes columns beyond it),
+// and the Thomas factors restarting at each segment (tm = 0 at its first
+// coarse node, tsup = 0 at its last), so one solve along the whole line is
+// nb independent solves.
+Dim1DHost make_blocked_dim(int nb, const std::vector<double>& xs) {
+  const Dim1DHost S = make_dim(xs);
+  Dim1DHost D;
+  const int n = S.n, c = S.c;
+  D.n = nb * n;
+  D.c = nb * c;
+  for (int b = 0; b < nb; ++b) {
+    for (int i = 0; i < n; ++i) {
+      D.x.push_back((double)b * (xs.back() + 1.0) + xs[(size_t)i]);
+      D.jlo.push_back(b * c + S.jlo[(size_t)i]);
+      D.jhi.push_back(b * c + S.jhi[(size_t)i]);
+      D.cb.push_back(b * c + S.cb[(size_t)i]);
+      D.isc.push_back(S.isc[(size_t)i]);
+      D.wl.push_back(S.wl[(size_t)i]);
+      D.wr.push_back(S.wr[(size_t)i]);
+      D.md.push_back(S.md[(size_t)i]);
+      D.mo.push_back(S.mo[(size_t)i]);  // 0 at the segment's last node
+    }
+    for (int J = 0; J < c; ++J) {
+      D.cidx.push_back(b * n + S.cidx[(size_t)J]);
+      D.f0.push_back(b * n + S.f0[(size_t)J]);
+      for (int m = 0; m < 5; ++m) D.band.push_back(S.band[5 * (size_t)J + m]);
+      D.tm.push_back(S.tm[(size_t)J]);    // 0 at the segment's first coarse node
+      D.tib.push_back(S.tib[(size_t)J]);
+      D.tsup.push_back(S.tsup[(size_t)J]);  // 0 at its last
+    }
+  }
+  return D;
+}
+
 // P = M_c^{-1} I^T M_f as a dense c x n matrix, column by column (Thomas).
 std::vector<double> projection(const Dim1DHost& D) {
   std::vector<double> P((size_t)D.c * D.n, 0.0);
@@ -183,7 +219,7 @@ double error_constant(const Dim1DHost* D3) {
 }  // namespace
 
 std::string make_plan(const int64_t* shape, int B, int K, int M, int R, PlanHost& p) {
-  if (B < 3 || B % 2 == 0) return "block size must be odd and >= 3";
+  if (B < 3 || B > 64) return "block size must be in [3, 64]";
   if (R < 1) return "at least one round";
   p = PlanHost{};
   for (int d = 0; d < 3; ++d) p.shape[d] = shape[d];
@@ -271,6 +307,40 @@ std::string make_plan(const int64_t* shape, int B, int K, int M, int R, PlanHost
     p.nblocks_all += rd.nblocks;
     p.rounds.push_back(rd);
     for (int d = 0; d < 3; ++d) S[d] = rd.gshape[d];
+  }
+  // block sizes without a fused kernel: per round and level, the padded grid
+  // and its block-diagonal operators
+  p.generic = !p.reduced && !fused_block(B);
+  if (p.generic) {
+    std::vector<std::vector<double>> xs;  // block coordinates per level (K + 1)
+    std::vector<double> x0(B);
+    for (int j = 0; j < B; ++j) x0[j] = j;
+    xs.push_back(x0);
+    for (int l = 0; l < K; ++l) {
+      std::vector<double> nx;
+      for (int j : coarse_of((int)xs.back().size())) nx.push_back(xs.back()[(size_t)j]);
+      xs.push_back(nx);
+    }
+    for (const RoundHost& rd : p.rounds) {
+      std::vector<XLevelHost> lv;
+      int64_t off = rd.off;
+      for (int l = 0; l < K; ++l) {
+        XLevelHost X;
+        const int e = (int)xs[(size_t)l].size(), ce = (int)xs[(size_t)l + 1].size();
+        for (int d = 0; d < 3; ++d) {
+          X.e[d] = e;
+          X.ce[d] = ce;
+          X.nb[d] = rd.nb[d];
+          X.shape[d] = (int64_t)rd.nb[d] * e;
+          X.d[d] = make_blocked_dim(rd.nb[d], xs[(size_t)l]);
+          if (X.d[d].c > 544) X.d[d].P = projection(X.d[d]);  // lines longer than the scan kernel takes
+        }
+        X.sym_off = off;
+        off += (int64_t)e * e * e - (int64_t)ce * ce * ce;
+        lv.push_back(X);
+      }
+      p.xlev.push_back(lv);
+    }
   }
   // coordinates of the global levels' input: physical for one round (block
   // offset plus the coarse node's in-block coordinate), index coordinates of

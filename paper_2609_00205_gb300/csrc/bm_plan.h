@@ -43,9 +43,23 @@ struct RLevelHost {
   int64_t blk_extra;            // per block: symbols of the other levels (block-major order)
 };
 
+// One in-cache level of one round of a field whose block size has no fused
+// block kernel, run on the zero-padded grid of the round's blocks: along
+// every dimension the level operator is block-diagonal (nb segments of the
+// block-local level), which makes the whole-grid passes the blockwise
+// transform; the coarse part after the last level is the gathered grid.
+struct XLevelHost {
+  int64_t shape[3];             // padded grid of the level (nb * block extent of the level)
+  Dim1DHost d[3];               // block-diagonal operators
+  int e[3], ce[3], nb[3];       // per dimension: block extent, its coarse count, blocks
+  int64_t sym_off;              // first symbol of the level inside the round's first block
+};
+
 struct PlanHost {
   int64_t shape[3];
   int B, K, M, R;
+  bool generic = false;         // no fused block kernel for B: in-cache levels as padded whole-grid passes
+  std::vector<std::vector<XLevelHost>> xlev;  // [round][level] (generic only)
   int Bd[3];         // block edge per dimension: B, or 1 for a dimension of extent 1
   int md[3];         // coarse nodes per block edge after K levels, per dimension
   bool reduced = false;         // some dimension has extent 1: in-cache levels on the block-major grid
@@ -64,6 +78,9 @@ struct PlanHost {
   std::vector<std::vector<Dim1DHost>> glev;  // [M][3]
   std::vector<double> A;  // level error constants: local 1..K then global 1..M (rounded)
 };
+
+// Whether the fused In-cache Block kernels exist for a block size.
+inline bool fused_block(int B) { return B == 9 || B == 17; }
 
 // Builds the plan; returns an empty string on success, else a message.
 std::string make_plan(const int64_t* shape, int B, int K, int M, int R, PlanHost& p);

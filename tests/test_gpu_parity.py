@@ -34,6 +34,12 @@ CASES = [
     # path of the global levels), along dimension 0 and along dimension 2
     ("long0_b9k1m1", (2000, 6, 5), np.float32, 9, 1, 1),
     ("long2_f64_b9k1m1", (5, 6, 2000), np.float64, 9, 1, 1),
+    # block sizes without a fused block kernel (the paper's 8-node blocks,
+    # 16 and 33 nodes): the in-cache levels as blocked whole-grid passes
+    ("grf_b8k3m1", (40, 37, 45), np.float32, 8, 3, 1),
+    ("roi_f64_b8k1m2", (47, 41, 33), np.float64, 8, 1, 2),
+    ("grf_b16k2m2", (70, 61, 53), np.float32, 16, 2, 2),
+    ("grf_b33k2m1", (70, 40, 66), np.float32, 33, 2, 1),
 ]
 
 
@@ -291,7 +297,13 @@ def test_invalid_arguments(bm):
         bm.compress(t, -1.0)
     assert e.value.status == 1
     with pytest.raises(bm.BlockMGARDError) as e:
-        bm.compress(t, 1e-3, block=8)
+        bm.compress(t, 1e-3, block=2)
+    assert e.value.status == 1
+    with pytest.raises(bm.BlockMGARDError) as e:
+        bm.compress(t, 1e-3, block=65)
+    assert e.value.status == 1
+    with pytest.raises(bm.BlockMGARDError) as e:
+        bm.recompose_adjoint(t, block=8, levels=1, global_levels=1)
     assert e.value.status == 5
     with pytest.raises(bm.BlockMGARDError):
         bm.compress(t, 1e-3, block=9, levels=4)

@@ -22,6 +22,9 @@ CASES = [
     ("grf_b9k1m0r3", (52, 35, 70), np.float32, 9, 1, 0, 3),
     ("grf_b17k1m1r2", (70, 61, 53), np.float32, 17, 1, 1, 2),
     ("roi_f64_b9k2m1r2", (47, 41, 33), np.float64, 9, 2, 1, 2),
+    # the paper's schedule: 8-node blocks, one level per round, three rounds
+    ("grf_b8k1m1r3", (60, 45, 52), np.float32, 8, 1, 1, 3),
+    ("roi_f64_b8k1m0r3", (47, 41, 33), np.float64, 8, 1, 0, 3),
 ]
 
 

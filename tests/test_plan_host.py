@@ -18,7 +18,8 @@ SHAPES = [(2, 3, 2), (9, 9, 9), (10, 9, 8), (17, 17, 17), (18, 35, 52), (40, 37,
           (33, 5, 70), (129, 17, 3), (100, 101, 102),
           # 1-D and 2-D fields and explicit extents of 1
           (500,), (3,), (120, 91), (2, 3), (40, 1, 23), (1, 1, 300), (300, 1, 1)]
-PARAMS = [(9, k, m) for k in (1, 2, 3) for m in (0, 1, 2, 3)] + [(17, k, m) for k in (1, 2, 3, 4) for m in (0, 1, 2)]
+PARAMS = [(9, k, m) for k in (1, 2, 3) for m in (0, 1, 2, 3)] + [(17, k, m) for k in (1, 2, 3, 4) for m in (0, 1, 2)] \
+    + [(8, k, m) for k in (1, 2, 3) for m in (0, 2)] + [(16, k, m) for k in (1, 3) for m in (0, 1)] + [(5, 1, 1), (33, 2, 1)]
 
 
 @pytest.fixture(scope="module")
@@ -47,7 +48,8 @@ def test_coefficient_counts_match_the_oracle(bm, B, K, M):
 
 @pytest.mark.parametrize("R", [2, 3])
 def test_coefficient_counts_match_the_oracle_with_rounds(bm, R):
-    for shape, (B, K, M) in itertools.product(SHAPES[2:8], [(9, 1, 1), (9, 1, 2), (17, 1, 1), (9, 2, 0)]):
+    for shape, (B, K, M) in itertools.product(SHAPES[2:8], [(9, 1, 1), (9, 1, 2), (17, 1, 1), (9, 2, 0), (8, 1, 1),
+                                                           (16, 2, 0)]):
         try:
             want = oracle.plan(shape, B, K, M, R)["n_coeffs"]
         except Exception:
