@@ -1394,7 +1394,7 @@ struct BatchSlot {
 };
 
 bm_status compress_result(const Scalars* hsc, unsigned long long raw_total, size_t* out_bytes) {
-  if (hsc->status & ST_TIMEOUT) return fail(BM_ERR_CUDA, "encoder look-back wait timed out");
+  if (hsc->status & ST_TIMEOUT) return fail(BM_ERR_CUDA, "a bounded device wait timed out (block staging or encoder look-back)");
   if (hsc->status & ST_CORRUPT) return fail(BM_ERR_CUDA, "internal error: escape count differs from the histogram");
   *out_bytes = (hsc->status & ST_RAW) ? (size_t)raw_total : (size_t)hsc->total;
   return BM_OK;
