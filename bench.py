@@ -461,6 +461,15 @@ def _roi_maps(fs, block):
 
 
 def run_batch64(args):
+    """The batched workload alone, as its own JSON line."""
+    import torch
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    print(json.dumps(batch64_measure(dev, args.steps, args.warmup)))
+
+
+def batch64_measure(dev, steps, warmup):
     """Batched compress of 64 fields vs the per-field loop (same fields,
     tolerances, ROI maps and parameters); the block size and in-cache levels
     are picked by timing each candidate on the batch."""
@@ -468,8 +477,6 @@ def run_batch64(args):
 
     import paper_2609_00205_gb300 as bm
 
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
     bm.load()
     fs = _batch64_fields(dev)
     tols = [t for _, t in fs]
@@ -508,11 +515,11 @@ def run_batch64(args):
         tune.append((timed(batch, p, rois, 2)[0], p))
     best = min(tune, key=lambda z: z[0])[1]
     rois = _roi_maps(fs, best["block"])
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batch(best, rois)
         loop(best, rois)
-    b_ms, b_wall = timed(batch, best, rois, args.steps)
-    l_ms, l_wall = timed(loop, best, rois, args.steps)
+    b_ms, b_wall = timed(batch, best, rois, steps)
+    l_ms, l_wall = timed(loop, best, rois, steps)
     res = batch(best, rois)
     ref = loop(best, rois)
     same = all(torch.equal(x, y) for x, y in zip(res, ref))
@@ -521,11 +528,16 @@ def run_batch64(args):
             "value": nbytes / b_ms / 1e6, "unit": "GB/s", "higher_is_better": True,
             "ms_per_batch": b_ms, "wall_ms_per_batch": b_wall, "loop_ms": l_ms, "loop_wall_ms": l_wall,
             "speedup_vs_loop": l_ms / b_ms, "identical_streams": same, "cr": cr, "input_bytes": nbytes,
-            "params": best, "tuning_ms": [[round(t, 3), p] for t, p in tune], "steps": args.steps,
-            "warmup": args.warmup, "data": "synthetic",
+            "params": best, "tuning_ms": [[round(t, 3), p] for t, p in tune], "steps": steps,
+            "warmup": warmup, "data": "synthetic",
             "fields": "24 planar FP32 sides U[100,2049], 32 3-D FP32 sides U[33,257], "
-                      "8 3-D FP64 129^3; tolerances log-uniform [1e-5,1e-2], ROI 10% of blocks at 10x tighter"}
-    print(json.dumps(line))
+                      "8 3-D FP64 129^3; tolerances log-uniform [1e-5,1e-2], ROI 10% of blocks at 10x tighter",
+            "path": "3-D fields with B in {9, 17}: max|u|, quantiser tables and In-cache Block stage in one "
+                    "persistent launch per (dtype, B, K) draining a device work queue; other stages and fields "
+                    "on the library's stream pool"}
+    del fs, us, outs
+    torch.cuda.empty_cache()
+    return line
 
 
 def run_diff257(args):
@@ -722,6 +734,7 @@ def main():
     ap.add_argument("--cpu-edge", type=int, default=221)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-roi", action="store_true", help="skip the FP64 ROI workload in the main line")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-field batched workload in the main line")
     ap.add_argument("--edge", type=int, default=513, help="field edge (513 = the workload; smaller for profiling)")
     ap.add_argument("--quick", action="store_true", help="compress steps only (profiling runs)")
     ap.add_argument("--workload", default="grf513", choices=["grf513", "batch64", "diff257", "model", "roi385"])
@@ -972,6 +985,12 @@ def main():
             roi = roi385_measure(dev, max(20, args.steps), args.warmup)
         except Exception as e:  # a reporting extra: never lose the bench line over it
             roi = {"error": str(e)}
+    b64 = None
+    if not args.no_batch:
+        try:
+            b64 = batch64_measure(dev, 10, max(2, args.warmup))
+        except Exception as e:  # a reporting extra: never lose the bench line over it
+            b64 = {"error": str(e)}
 
     if rank == 0:
         line = {
@@ -993,6 +1012,7 @@ def main():
             "input_rate_frac": value / ws / peak,
             "decompress_roofline": dec_roof,
             "roi385": roi,
+            "batch64": b64,
             "stage_ms": stage_avg,
             "e2e": e2e,
             "gpu_launches": launches,

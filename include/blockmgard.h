@@ -165,12 +165,20 @@ typedef struct {
   size_t out_capacity;
 } bm_batch_item;
 
-/* Compresses n independent fields (Sec. III-D: many fields per launch
- * sequence).  The fields' pipelines are queued on a pool of the library's
- * streams, forked from and joined back into `stream`, without any host
- * synchronisation until all are queued; then one synchronisation and the
- * per-field sizes in out_bytes[i] (host array of n).  Each field gives the
- * same stream, byte for byte, as bm_compress with the same arguments.
+/* Compresses n independent fields (Sec. III-B throughput model, Sec. III-D:
+ * many fields per launch).  Every 3-D field (no extent of 1) with B in
+ * {9, 17} and one round has its max|u| pass, quantiser table and In-cache
+ * Block stage done by one persistent kernel launch per (dtype, B, K), whose
+ * CTAs take work items (slices of max|u|, then single blocks) from a
+ * device-side queue spanning all those fields; a block waits, with a bounded
+ * wait (status BM_ERR_CUDA if it ever ran out), for its field's quantiser
+ * table.  The other stages, and whole pipelines of the other fields, are
+ * queued on a pool of the library's streams, forked from and joined back
+ * into `stream`, without any host synchronisation until all are queued; then
+ * one synchronisation and the per-field sizes in out_bytes[i] (host array of
+ * n).  Each field gives the same stream, byte for byte, as bm_compress with
+ * the same arguments.  Device scratch for the batched fields (their symbols,
+ * escape codes and levels at once) is kept by the library between calls.
  * item_status (host array of n, nullable) receives each field's status; the
  * return value is the first non-OK status, or BM_OK.  Buffers are owned by
  * the caller; fields and outputs must not overlap. */

@@ -188,17 +188,23 @@ def compress(field: torch.Tensor, tol: float, mode: str = "rel", roi=None, block
 
 
 def compress_batch(fields, tols, mode: str = "rel", rois=None, block=17, levels=2, global_levels=2, chunk=2048,
-                   radius=32768, outs=None, stream=None, rounds=1):
-    """Compress several 3-D CUDA fields in one call (pipelines queued on the
-    library's stream pool, one synchronisation).  ``tols``: one tolerance per
+                   radius=32768, outs=None, stream=None, rounds=1, params=None):
+    """Compress several CUDA fields (1-3 dims) in one call: the In-cache Block
+    stage of every 3-D field with B in {9, 17} and one round runs in one
+    persistent launch per (dtype, B, K), the rest of each pipeline on the
+    library's stream pool, one synchronisation.  ``tols``: one tolerance per
     field; ``rois``: None or one per-block tolerance map (or None) per field;
-    ``outs``: optional output buffers.  Returns the streams as uint8 views, each
-    identical to :func:`compress` of the same field."""
+    ``outs``: optional output buffers; ``params``: None or one dict per field
+    (keys block, levels, global_levels, chunk, radius, rounds) overriding the
+    shared keyword arguments.  Returns the streams as uint8 views, each
+    identical to :func:`compress` of the same field and parameters."""
     import numpy as np
     L = load()
     n = len(fields)
-    if len(tols) != n or (rois is not None and len(rois) != n) or (outs is not None and len(outs) != n):
-        raise ValueError("one tolerance (and ROI map, output) per field")
+    if (len(tols) != n or (rois is not None and len(rois) != n) or (outs is not None and len(outs) != n)
+            or (params is not None and len(params) != n)):
+        raise ValueError("one tolerance (and ROI map, output, parameter set) per field")
+    shared = dict(block=block, levels=levels, global_levels=global_levels, chunk=chunk, radius=radius, rounds=rounds)
     items = (_BatchItem * max(n, 1))()
     keep = []
     bufs = []
@@ -225,7 +231,11 @@ def compress_batch(fields, tols, mode: str = "rel", rois=None, block=17, levels=
             r = np.ascontiguousarray(np.asarray(r, dtype=np.float64).ravel())
             keep.append(r)
             it.h_roi_tol = r.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-        it.params = p
+        if params is not None and params[i]:
+            q = dict(shared, **params[i])
+            it.params = _params(q["block"], q["levels"], q["global_levels"], q["chunk"], q["radius"], q["rounds"])
+        else:
+            it.params = p
         it.d_out = o.data_ptr()
         it.out_capacity = o.numel()
     sizes = (ctypes.c_size_t * max(n, 1))()

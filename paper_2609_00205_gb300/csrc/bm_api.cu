@@ -22,12 +22,18 @@
 #include "bm_huffman.cuh"
 #include "bm_internal.h"
 #include "bm_plan.h"
+#include "bm_qtab.cuh"
 
 #ifndef BM_FWD_HIST
 #define BM_FWD_HIST 0
 #endif
 // The block region's histogram: on a second stream beside the global levels
 // (BM_HIST_OVERLAP) with BM_HIST_CTAS CTAs per SM.
+// BM_BATCH_GRAPHS: a batched compress met a second time with the same
+// arguments is captured as a CUDA graph, and replayed from then on.
+#ifndef BM_BATCH_GRAPHS
+#define BM_BATCH_GRAPHS 1
+#endif
 #ifndef BM_HIST_OVERLAP
 #define BM_HIST_OVERLAP 1
 #endif
@@ -44,6 +50,9 @@ namespace {
 thread_local std::string g_detail;
 std::atomic<uint64_t> g_launches{0};
 std::atomic<int> g_timing{0};
+// bumped whenever library scratch is (re)allocated: captured batch graphs
+// holding older addresses are discarded
+std::atomic<uint64_t> g_alloc_gen{0};
 
 struct StageTimer {
   struct Rec { const char* name; cudaEvent_t a, b; cudaStream_t s; };
@@ -170,6 +179,7 @@ bm_status get_ws(cudaStream_t s, size_t dbytes, size_t hbytes, Workspace** out) 
   if (w.dbytes < dbytes) {
     if (w.d) { cudaStreamSynchronize(s); cudaFree(w.d); w.d = nullptr; w.dbytes = 0; }
     size_t want = dbytes + dbytes / 8 + (1 << 20);
+    g_alloc_gen.fetch_add(1);
     if (cudaMalloc(&w.d, want) != cudaSuccess) {
       cudaGetLastError();
       w.d = nullptr;
@@ -180,6 +190,7 @@ bm_status get_ws(cudaStream_t s, size_t dbytes, size_t hbytes, Workspace** out) 
   if (w.hbytes < hbytes) {
     if (w.h) { cudaStreamSynchronize(s); cudaFreeHost(w.h); w.h = nullptr; w.hd = nullptr; w.hbytes = 0; }
     size_t want = hbytes + (1 << 16);
+    g_alloc_gen.fetch_add(1);
     if (cudaMallocHost(&w.h, want) != cudaSuccess) {
       cudaGetLastError();
       w.h = nullptr;
@@ -560,61 +571,6 @@ cudaError_t launch_hist(const uint16_t* sym, unsigned long long s0, unsigned lon
 // ---------------------------------------------------------------------------
 // Small kernels of the API layer
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ void maxabs_acc(T x, T& m, bool& bad) {
-  const T v = fabs(x);
-  bad |= !(v < T(INFINITY));  // NaN or infinity: the stream will be raw
-  m = v > m ? v : m;          // NaN never compares greater: ignored; infinity kept
-}
-
-// Quantiser widths of every (tier, level), in IEEE double arithmetic without
-// contraction: tau' = tau - margin, margin = kappa eps (N+1) max|u|;
-// q_level = 2 tau'/((N+1) A_level), q_coarsest = 2 tau_g'/(N+1).
-struct QtabArgs {
-  int enabled;
-  const double* tiers;  // relative or absolute, ascending
-  int ntiers, rel, K, M, R;
-  double A[24];
-  double kappa, eps;
-  double* qd;           // [ntiers*K + M + 1]
-  void* rq;             // same count, field dtype
-  int f64;
-  uint8_t* out;         // stream (tiers + qtab sections) or null
-  unsigned long long off_tiers, off_qtab;
-  Scalars* sc;
-};
-
-__device__ void qtab_compute(const QtabArgs& a) {
-  const double max_abs = a.f64 ? __longlong_as_double((long long)a.sc->maxabs_bits)
-                               : (double)__uint_as_float((unsigned)a.sc->maxabs_bits);
-  const int N = a.R * a.K + a.M;
-  const double t = (double)(N + 1);
-  const double margin = __dmul_rn(__dmul_rn(__dmul_rn(a.kappa, a.eps), t), max_abs);
-  bool raw = !isfinite(max_abs);
-  double taug = INFINITY;
-  const int nq = a.ntiers * a.K + a.M + 1;
-  for (int i = 0; i < a.ntiers; ++i) {
-    const double tau = a.rel ? __dmul_rn(a.tiers[i], max_abs) : a.tiers[i];
-    if (a.out) reinterpret_cast<double*>(a.out + a.off_tiers)[i] = tau;
-    const double taup = __dsub_rn(tau, margin);
-    if (!(taup > __dmul_rn(0.5, tau))) raw = true;
-    taug = fmin(taug, taup);
-    for (int l = 0; l < a.K; ++l)
-      a.qd[i * a.K + l] = __dmul_rn(2.0, __ddiv_rn(taup, __dmul_rn(t, a.A[l])));
-  }
-  for (int l = 0; l < a.M; ++l) a.qd[a.ntiers * a.K + l] = __dmul_rn(2.0, __ddiv_rn(taug, __dmul_rn(t, a.A[a.K + l])));
-  a.qd[nq - 1] = __dmul_rn(2.0, __ddiv_rn(taug, t));
-  for (int i = 0; i < nq; ++i) {
-    const double r = __ddiv_rn(1.0, a.qd[i]);
-    if (a.f64) reinterpret_cast<double*>(a.rq)[i] = r;
-    else reinterpret_cast<float*>(a.rq)[i] = __double2float_rn(r);
-    if (a.out) reinterpret_cast<double*>(a.out + a.off_qtab)[i] = a.qd[i];
-  }
-  a.sc->max_abs = max_abs;
-  a.sc->margin = margin;
-  if (raw) atomicOr(&a.sc->status, ST_RAW);
-}
-
 // Loads in flight per thread and CTAs per SM of the max|u| pass (the fastest
 // measured on GB300 at 513^3 FP32: 0.101 ms, against 0.115 ms with 4 and 8).
 #ifndef BM_MAXABS_INFLIGHT
@@ -1001,9 +957,15 @@ std::vector<T*> round_grids(const PlanHost& h, Carver& cv, T* last) {
   return g;
 }
 
+// What run_decompose does with the fused In-cache Block stage: launch it,
+// only record its arguments (and return before any launch), or skip it (the
+// batched forward kernel ran it).
+enum class Incache { Run, Record, Skip };
+
 template <typename T>
 bm_status run_decompose(PlanDev& P, const T* field, int mode, const FwdOut<T>& o, Carver& cv, cudaStream_t s,
-                        const std::function<bm_status()>& after_block = nullptr) {
+                        const std::function<bm_status()>& after_block = nullptr, Incache ic = Incache::Run,
+                        BlockArgs<T>* rec = nullptr) {
   const PlanHost& h = P.h;
   if (bm_status st = upload_tables<T>(P)) return st;
   const GSizes gs = gsizes(h);
@@ -1072,7 +1034,7 @@ bm_status run_decompose(PlanDev& P, const T* field, int mode, const FwdOut<T>& o
       toff += rd.nblocks;
     }
     BM_CUDA(cudaGetLastError());
-  } else {
+  } else if (ic != Incache::Skip) {
     Stage st("incache_decompose");
     int64_t toff = 0;
     for (size_t r = 0; r < h.rounds.size(); ++r) {  // each round blocks the previous round's gathered grid
@@ -1089,6 +1051,10 @@ bm_status run_decompose(PlanDev& P, const T* field, int mode, const FwdOut<T>& o
       a.coef = o.coef ? o.coef + rd.off : nullptr;
       a.tier = o.tier ? o.tier + toff : nullptr;
       a.rq = o.rq; a.hist = o.hist; a.radius = o.radius; a.sc = o.sc;
+      if (ic == Incache::Record) {
+        if (rec) *rec = a;
+        return BM_OK;
+      }
       BM_CUDA(launch_block<T>(0, h.B, h.K, mode, a, s));
       toff += rd.nblocks;
     }
@@ -1386,17 +1352,72 @@ struct Spans {
   }
 };
 
+// Phases of one batch item: the whole pipeline on a pool stream, or (items
+// whose in-cache levels run in the batched forward kernel) a size query, the
+// part before the block stage (recording the kernel's arguments) and the
+// part after it.
+enum BatchPhase { kWhole = 0, kQuery = 1, kPrepare = 2, kFinish = 3 };
+
 struct BatchSlot {
   unsigned char* h = nullptr;  // Scalars at 0, tiers at 256, block tiers at 256 + 8*256
   unsigned char* hd = nullptr; // device-side address of h
   bool raw_now = false;        // the raw copy was chosen on the host
   unsigned long long raw_total = 0;
+  int phase = kWhole;
+  std::vector<double> tiers;         // kPrepare -> kFinish: the item's tolerance tiers
+  std::vector<uint8_t> btier;        // and block tiers
+  bool batched = false;              // kQuery: the item can take the batched kernel
+  size_t need = 0;                   // kQuery: device scratch of the item
+  unsigned char* scratch = nullptr;  // kPrepare / kFinish: the item's own scratch
+  BlockArgs<float> af{};             // kPrepare: recorded block arguments (FP32 / FP64)
+  BlockArgs<double> ad{};
+  QtabArgs qa{};                     // kPrepare: recorded quantiser-table arguments
 };
 
 bm_status compress_result(const Scalars* hsc, unsigned long long raw_total, size_t* out_bytes) {
   if (hsc->status & ST_TIMEOUT) return fail(BM_ERR_CUDA, "a bounded device wait timed out (block staging or encoder look-back)");
   if (hsc->status & ST_CORRUPT) return fail(BM_ERR_CUDA, "internal error: escape count differs from the histogram");
   *out_bytes = (hsc->status & ST_RAW) ? (size_t)raw_total : (size_t)hsc->total;
+  return BM_OK;
+}
+
+// Tolerance tiers of a call (Sec. III-C): the distinct values of
+// min(tol, roi_b) over the blocks, ascending, and each block's tier (empty
+// with a single tier), then propagated through the rounds.  Distinct values
+// are collected with a cache of the last one (neighbouring blocks mostly
+// share it), so a map of N blocks and t tiers costs O(N log t).
+bm_status make_tiers(const PlanHost& h, double tol, const double* roi, std::vector<double>& tiers,
+                     std::vector<uint8_t>& btier) {
+  tiers.assign(1, tol);
+  btier.clear();
+  if (!roi) return BM_OK;
+  tiers.clear();
+  double last = -1.0;
+  for (int64_t b = 0; b < h.nblocks; ++b) {
+    if (!(roi[b] > 0.0) || !std::isfinite(roi[b])) return fail(BM_ERR_ARG, "ROI tolerances must be finite and > 0");
+    const double v = std::min(tol, roi[b]);
+    if (v == last) continue;
+    last = v;
+    if (std::find(tiers.begin(), tiers.end(), v) == tiers.end()) {
+      if (tiers.size() == 255) return fail(BM_ERR_ARG, "more than 255 distinct tolerances");
+      tiers.push_back(v);
+    }
+  }
+  std::sort(tiers.begin(), tiers.end());
+  if (tiers.size() > 1) {
+    btier.resize((size_t)h.nblocks);
+    double lv = -1.0;
+    uint8_t lt = 0;
+    for (int64_t b = 0; b < h.nblocks; ++b) {
+      const double v = std::min(tol, roi[b]);
+      if (v != lv) {
+        lv = v;
+        lt = (uint8_t)(std::lower_bound(tiers.begin(), tiers.end(), v) - tiers.begin());
+      }
+      btier[(size_t)b] = lt;
+    }
+    propagate_tiers(h, btier);
+  }
   return BM_OK;
 }
 
@@ -1412,27 +1433,17 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   const int64_t nel = nel3(shape);
   const unsigned long long raw_total = kHeaderBytes + (unsigned long long)nel * sizeof(T);
   if (cap < raw_total) return fail(BM_ERR_CAPACITY, "out_capacity below bm_compress_bound()");
-  // tiers: distinct min(tol, roi_i) values, ascending (one tier without a ROI map)
-  std::vector<double> tiers{tol};
-  std::vector<uint8_t> btier;
-  if (roi) {
-    std::vector<double> bt((size_t)h.nblocks, tol);
-    for (int64_t b = 0; b < h.nblocks; ++b) {
-      if (!(roi[b] > 0.0) || !std::isfinite(roi[b])) return fail(BM_ERR_ARG, "ROI tolerances must be finite and > 0");
-      bt[(size_t)b] = std::min(tol, roi[b]);
-    }
-    tiers = bt;
-    std::sort(tiers.begin(), tiers.end());
-    tiers.erase(std::unique(tiers.begin(), tiers.end()), tiers.end());
-    if (tiers.size() > 255) return fail(BM_ERR_ARG, "more than 255 distinct tolerances");
-    if (tiers.size() > 1) {
-      btier.resize((size_t)h.nblocks);
-      for (int64_t b = 0; b < h.nblocks; ++b)
-        btier[(size_t)b] = (uint8_t)(std::lower_bound(tiers.begin(), tiers.end(), bt[(size_t)b]) - tiers.begin());
-      propagate_tiers(h, btier);
-    }
-  }
-  const int ntiers = (int)tiers.size();
+  // tiers: distinct min(tol, roi_i) values, ascending (one tier without a ROI
+  // map); a batch item keeps them from its first phase to its last, and its
+  // size query takes the largest table (255 tiers) instead
+  const int phase = bs ? bs->phase : kWhole;
+  std::vector<double> tiers_own;
+  std::vector<uint8_t> btier_own;
+  std::vector<double>& tiers = phase == kWhole ? tiers_own : bs->tiers;
+  std::vector<uint8_t>& btier = phase == kWhole ? btier_own : bs->btier;
+  if (phase == kWhole || phase == kPrepare)
+    if (bm_status st = make_tiers(h, tol, roi, tiers, btier)) return st;
+  const int ntiers = phase == kQuery ? (roi ? 255 : 1) : (int)tiers.size();
   const StreamLayout L = layout(h, ntiers, prm.chunk);
   const int dict = 2 * prm.radius;
 
@@ -1451,9 +1462,19 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   probe.take<unsigned char>(256 + 16ull * L.nch);
   const size_t need = probe.off + decompose_scratch(h, sizeof(T)) + 4096;
   const size_t hneed = 256 + 8 * 256 + (size_t)h.nblocks_all + 4096;
+  if (phase == kQuery) {
+    bs->need = need;
+    bs->batched = h.R == 1 && !h.reduced && !h.generic && fused_block(h.B) && h.K <= 4;
+    return BM_OK;
+  }
   Workspace* ws = nullptr;
-  if (bm_status st = get_ws(s, need, hneed, &ws)) return st;
-  carve_all(cv, reinterpret_cast<unsigned char*>(ws->d));
+  if (phase == kWhole) {
+    if (bm_status st = get_ws(s, need, hneed, &ws)) return st;
+    carve_all(cv, reinterpret_cast<unsigned char*>(ws->d));
+  } else {
+    carve_all(cv, bs->scratch);
+    if (phase == kFinish && bs->raw_now) return BM_OK;
+  }
   Scalars* sc = cv.take<Scalars>(1);
   unsigned* hist = cv.take<unsigned>(dict);
   uint8_t* lens = cv.take<uint8_t>(dict);
@@ -1480,7 +1501,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   if (ntiers > 1) std::memcpy(hbt, btier.data(), btier.size());
 
   const bool prefix_fits = L.off_codebook <= cap;
-  {
+  if (phase != kFinish) {
     Stage st("setup");
     // zeroed scalars, histogram, stream prefix and encoder tickets; the tier
     // tables read from the pinned staging buffer
@@ -1503,7 +1524,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     BM_CUDA(sp.launch(s));
   }
   const int mgrid = (int)std::min<int64_t>((int64_t)num_sms() * BM_MAXABS_CTAS, std::max<int64_t>(1, (nel + 4095) / 4096));
-  {
+  if (phase != kFinish) {
     Stage st("maxabs");
     QtabArgs qa{};
     qa.enabled = prefix_fits;
@@ -1514,11 +1535,15 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     qa.qd = qd; qa.rq = rq; qa.f64 = f64;
     qa.out = prefix_fits ? out : nullptr;
     qa.off_tiers = L.off_tiers; qa.off_qtab = L.off_qtab; qa.sc = sc;
-    maxabs_kernel<T><<<mgrid, 256, 0, s>>>(field, nel, sc, qa);
-    BM_LAUNCHED();
-    BM_CUDA(cudaGetLastError());
+    if (phase == kPrepare) {
+      bs->qa = qa;  // max|u| and the table are items of the batched kernel
+    } else {
+      maxabs_kernel<T><<<mgrid, 256, 0, s>>>(field, nel, sc, qa);
+      BM_LAUNCHED();
+      BM_CUDA(cudaGetLastError());
+    }
   }
-  if (!prefix_fits) {  // not even the tables fit: the raw copy is the stream
+  if (!prefix_fits && phase != kFinish) {  // not even the tables fit: the raw copy is the stream
     raw_header_kernel<<<1, 32, 0, s>>>(out, f64, h.B, shape[0], shape[1], shape[2], rel, tol, raw_total, sc, prm.ndim);
     BM_LAUNCHED();
     BM_CUDA(cudaMemcpyAsync(out + kHeaderBytes, field, (size_t)nel * sizeof(T), cudaMemcpyDeviceToDevice, s));
@@ -1536,10 +1561,13 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   fo.ntiers = ntiers; fo.radius = prm.radius; fo.sc = sc;
   // the block kernel does not count its symbols: their histogram is taken on
   // a second stream while the global levels run on the call's stream
+  // (the batched kernel never counts: its items take the separate pass on
+  // the item's own stream)
   auto block_hist = [&]() -> bm_status {
-    if (BM_FWD_HIST) return BM_OK;
+    if (BM_FWD_HIST && phase == kWhole) return BM_OK;
     cudaStream_t hs = s;
-    if (BM_HIST_OVERLAP) {
+    const bool overlap = BM_HIST_OVERLAP && phase == kWhole;
+    if (overlap) {
       if (bm_status st = ensure_aux(ws)) return st;
       BM_CUDA(cudaEventRecord(ws->ev_fork, s));
       BM_CUDA(cudaStreamWaitEvent(ws->aux, ws->ev_fork, 0));
@@ -1550,14 +1578,19 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
       const unsigned long long nloc = (unsigned long long)h.sym_off[0];  // the symbols of every round
       BM_CUDA(launch_hist(sym, 0, nloc, dict, (unsigned)prm.radius, hist, sc, false, num_sms() * BM_HIST_CTAS, hs));
     }
-    if (BM_HIST_OVERLAP) BM_CUDA(cudaEventRecord(ws->ev_join, ws->aux));
+    if (overlap) BM_CUDA(cudaEventRecord(ws->ev_join, ws->aux));
     return BM_OK;
   };
+  if (phase == kPrepare) {  // record the block arguments; the rest follows the batched kernel
+    BlockArgs<T>* rec = reinterpret_cast<BlockArgs<T>*>(f64 ? (void*)&bs->ad : (void*)&bs->af);
+    return run_decompose<T>(*P, field, 0, fo, cv, s, nullptr, Incache::Record, rec);
+  }
   {
-    const bm_status st = run_decompose<T>(*P, field, 0, fo, cv, s, block_hist);
+    const bm_status st = run_decompose<T>(*P, field, 0, fo, cv, s, block_hist,
+                                          phase == kFinish ? Incache::Skip : Incache::Run);
     // join the second stream before anything else (also on errors: no work
     // of this call may outlive it)
-    if (!BM_FWD_HIST && BM_HIST_OVERLAP && ws->aux) BM_CUDA(cudaStreamWaitEvent(s, ws->ev_join, 0));
+    if (phase == kWhole && !BM_FWD_HIST && BM_HIST_OVERLAP && ws->aux) BM_CUDA(cudaStreamWaitEvent(s, ws->ev_join, 0));
     if (st) return st;
   }
   {
@@ -1916,15 +1949,53 @@ bm_status adjoint_entry(int dir, const int64_t* shape, const Params& prm, T* gfi
 // workspace), nothing synchronises until every item has been queued, and the
 // results are read from per-item pinned slots afterwards.
 // ---------------------------------------------------------------------------
-constexpr int kBatchStreams = 8;
+// pool streams of a batch: the first half takes whole pipelines, the second
+// half the stages after the batched forward kernel
+constexpr int kBatchStreams = 16;
+// A batch captured as a CUDA graph: replayed while the call's arguments (the
+// key: every item's pointers, shape, dtype, tolerance, parameters and ROI
+// map) and the library's scratch addresses (g_alloc_gen) stay the same.
+struct BatchGraph {
+  std::vector<unsigned char> key;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<unsigned char> hstage;  // the pinned staging the graph reads (tiers, descriptors)
+  std::vector<unsigned char> raw_now;
+  std::vector<unsigned long long> raw_total;
+  uint64_t gen = 0;
+  uint64_t used = 0;
+};
+
 struct BatchCtx {
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> joins;
   cudaEvent_t fork = nullptr;
+  cudaEvent_t forks[2] = {nullptr, nullptr};  // the two halves of the pool
   unsigned char* h = nullptr;
   unsigned char* hd = nullptr;  // device-side address of h
   size_t hbytes = 0;
+  unsigned char* d = nullptr;   // device scratch of the items of the batched kernel
+  size_t dbytes = 0;
+  cudaStream_t cap = nullptr;   // the stream a batch is captured on
+  std::vector<BatchGraph> graphs;
+  std::vector<std::vector<unsigned char>> seen;  // keys met once (captured when met again)
+  uint64_t clock = 0;
 };
+
+// Device scratch of a batch, grown (never shrunk) under the batch lock; the
+// previous batch has synchronised, so nothing uses the old buffer.
+bm_status batch_scratch(BatchCtx* c, size_t bytes) {
+  if (c->dbytes >= bytes) return BM_OK;
+  g_alloc_gen.fetch_add(1);
+  if (c->d) cudaFree(c->d);
+  c->d = nullptr;
+  c->dbytes = 0;
+  if (cudaMalloc(&c->d, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(BM_ERR_OOM, "device scratch of the batch");
+  }
+  c->dbytes = bytes;
+  return BM_OK;
+}
 std::mutex g_batch_mu;
 std::map<int, BatchCtx> g_batch;
 
@@ -1942,8 +2013,10 @@ bm_status batch_ctx(size_t hbytes, BatchCtx** out) {
       c.joins.push_back(ev);
     }
     BM_CUDA(cudaEventCreateWithFlags(&c.fork, cudaEventDisableTiming));
+    for (cudaEvent_t& e : c.forks) BM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
   if (c.hbytes < hbytes) {
+    g_alloc_gen.fetch_add(1);
     if (c.h) cudaFreeHost(c.h);
     c.h = nullptr;
     c.hd = nullptr;
@@ -2027,6 +2100,104 @@ static void fit_line(const std::vector<double>& x, const std::vector<double>& y,
 // Coarse-grid shape after one level (Sec. II-B: floor(n/2)+1 nodes, none
 // removed from a dimension of at most two nodes).
 static int64_t coarsen(int64_t n) { return n <= 2 ? n : n / 2 + 1; }
+
+namespace {
+
+// One group of the batched forward kernel: items sharing dtype, B and K.
+struct BatchGroup {
+  bool f64;
+  int B, K;
+  std::vector<int> items;
+};
+
+template <typename T>
+BlockArgs<T>& slot_args(BatchSlot& b) {
+  return *reinterpret_cast<BlockArgs<T>*>(sizeof(T) == 8 ? (void*)&b.ad : (void*)&b.af);
+}
+
+// Descriptors of one group in pinned memory (at *hoff), copied to the device
+// scratch (at *doff) and the batched kernel launched on s.
+template <typename T>
+bm_status launch_group(const BatchGroup& g, std::vector<BatchSlot>& slot, const std::vector<std::array<int64_t, 3>>& shp,
+                       BatchCtx* ctx, size_t* hoff, size_t* doff, cudaStream_t s) {
+  const size_t nf = g.items.size();
+  const size_t bytes = nf * sizeof(BatchField<T>);
+  BatchField<T>* hf = reinterpret_cast<BatchField<T>*>(ctx->h + *hoff);
+  unsigned long long* dticket = reinterpret_cast<unsigned long long*>(ctx->d + *doff);
+  BatchField<T>* df = reinterpret_cast<BatchField<T>*>(ctx->d + *doff + 256);
+  unsigned long long nmax = 0, nblk = 0;
+  for (size_t j = 0; j < nf; ++j) {
+    BatchSlot& b = slot[(size_t)g.items[j]];
+    BatchField<T>& f = hf[j];
+    f.a = slot_args<T>(b);
+    f.qa = b.qa;
+    f.nel = nel3(shp[(size_t)g.items[j]].data());
+    f.max0 = nmax;
+    nmax += (unsigned long long)((f.nel + kBatchMaxChunk - 1) / kBatchMaxChunk);
+  }
+  for (size_t j = 0; j < nf; ++j) {
+    hf[j].blk0 = nmax + nblk;
+    nblk += (unsigned long long)hf[j].a.nblocks;
+  }
+  BatchQueue q{};
+  q.ticket = dticket;
+  q.n_max = nmax;
+  q.n_all = nmax + nblk;
+  q.nfields = (int)nf;
+  BM_CUDA(cudaMemsetAsync(dticket, 0, sizeof(unsigned long long), s));
+  BM_CUDA(cudaMemcpyAsync(df, hf, bytes, cudaMemcpyHostToDevice, s));
+  cudaError_t e;
+  if (sizeof(T) == 8)
+    e = g.B == 9 ? launch_block_batch_f64_b9(g.K, reinterpret_cast<const BatchField<double>*>(df), q, s, num_sms())
+                 : launch_block_batch_f64_b17(g.K, reinterpret_cast<const BatchField<double>*>(df), q, s, num_sms());
+  else
+    e = g.B == 9 ? launch_block_batch_f32_b9(g.K, reinterpret_cast<const BatchField<float>*>(df), q, s, num_sms())
+                 : launch_block_batch_f32_b17(g.K, reinterpret_cast<const BatchField<float>*>(df), q, s, num_sms());
+  BM_CUDA(e);
+  BM_LAUNCHED();
+  *hoff += (bytes + 255) & ~size_t(255);
+  *doff += 256 + ((bytes + 255) & ~size_t(255));
+  return BM_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// Key of a batch call: the items' bytes with their ROI maps, the device and
+// the block grid limit.
+std::vector<unsigned char> batch_key(int n, const bm_batch_item* items, const std::vector<std::array<int64_t, 3>>& shp,
+                                     const std::vector<int64_t>& nroi) {
+  std::vector<unsigned char> k;
+  auto put = [&](const void* p, size_t b) {
+    const unsigned char* c = reinterpret_cast<const unsigned char*>(p);
+    k.insert(k.end(), c, c + b);
+  };
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int cap = g_block_grid_cap.load();
+  put(&dev, sizeof dev);
+  put(&cap, sizeof cap);
+  put(&n, sizeof n);
+  for (int i = 0; i < n; ++i) {
+    const bm_batch_item& it = items[i];
+    put(&it.d_field, sizeof it.d_field);
+    put(&it.ndim, sizeof it.ndim);
+    put(shp[(size_t)i].data(), 3 * sizeof(int64_t));
+    put(&it.dtype, sizeof it.dtype);
+    put(&it.tol, sizeof it.tol);
+    put(&it.tol_mode, sizeof it.tol_mode);
+    put(&it.params, sizeof it.params);
+    put(&it.d_out, sizeof it.d_out);
+    put(&it.out_capacity, sizeof it.out_capacity);
+    const int64_t nr = it.h_roi_tol ? nroi[(size_t)i] : -1;
+    put(&nr, sizeof nr);
+    if (nr > 0) put(it.h_roi_tol, (size_t)nr * sizeof(double));
+  }
+  return k;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -2124,6 +2295,7 @@ bm_status bm_compress_batch(int n, const bm_batch_item* items, size_t* out_bytes
   std::vector<size_t> slot_off((size_t)n);
   std::vector<bm_status> st((size_t)n, BM_OK);
   std::vector<std::array<int64_t, 3>> shp((size_t)n);
+  std::vector<int64_t> nroi((size_t)n, 0);  // entries of each item's ROI map (first-round blocks)
   size_t hb = 0;
   for (int i = 0; i < n; ++i) {
     st[(size_t)i] = check_item(items[i], prm[(size_t)i], shp[(size_t)i].data());
@@ -2142,57 +2314,242 @@ bm_status bm_compress_batch(int n, const bm_batch_item* items, size_t* out_bytes
           S[d] = b * m;
         }
         nb += nb_round;
+        if (r == 0) nroi[(size_t)i] = nb_round;
       }
     }
     slot_off[(size_t)i] = hb;
     hb += (256 + 8 * 256 + (size_t)nb + 255) & ~size_t(255);
   }
+  const size_t hdesc = hb;  // then the batched kernel's descriptors
+  hb += (size_t)n * sizeof(BatchField<double>) + 32 * 256;
   BatchCtx* ctx = nullptr;
   if (bm_status e = batch_ctx(std::max<size_t>(hb, 256), &ctx)) return e;
-  // largest items first, so that each pool stream's workspace is sized once
-  std::vector<int> order((size_t)n);
-  for (int i = 0; i < n; ++i) order[(size_t)i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-    return nel3(shp[(size_t)a].data()) * (items[a].dtype == BM_F64 ? 2 : 1) >
-           nel3(shp[(size_t)b].data()) * (items[b].dtype == BM_F64 ? 2 : 1);
-  });
+  bool all_ok = true;
+  for (int i = 0; i < n; ++i) all_ok = all_ok && st[(size_t)i] == BM_OK;
+  const bool graphs_on = all_ok && n > 0 && !g_timing.load() && BM_BATCH_GRAPHS;
+  std::vector<unsigned char> key;
+  if (graphs_on) key = batch_key(n, items, shp, nroi);
+  auto finish = [&](const std::vector<BatchSlot>& slot) -> bm_status {
+    BM_CUDA(cudaStreamSynchronize(s));
+    bm_status first = BM_OK;
+    for (int i = 0; i < n; ++i) {
+      out_bytes[i] = 0;
+      if (st[(size_t)i] == BM_OK) {
+        const BatchSlot& b = slot[(size_t)i];
+        if (b.raw_now) out_bytes[i] = (size_t)b.raw_total;
+        else st[(size_t)i] = compress_result(reinterpret_cast<const Scalars*>(b.h), b.raw_total, &out_bytes[i]);
+      }
+      if (item_status) item_status[i] = st[(size_t)i];
+      if (first == BM_OK) first = st[(size_t)i];
+    }
+    return first;
+  };
   std::vector<BatchSlot> slot((size_t)n);
-  BM_CUDA(cudaEventRecord(ctx->fork, s));
-  for (cudaStream_t ps : ctx->streams) BM_CUDA(cudaStreamWaitEvent(ps, ctx->fork, 0));
-  int k = 0;
-  for (int i : order) {
-    if (st[(size_t)i] != BM_OK) continue;
-    const bm_batch_item& it = items[i];
-    cudaStream_t ps = ctx->streams[(size_t)(k++ % kBatchStreams)];
+  for (int i = 0; i < n; ++i) {
     slot[(size_t)i].h = ctx->h + slot_off[(size_t)i];
     slot[(size_t)i].hd = ctx->hd + slot_off[(size_t)i];
-    size_t dummy = 0;
-    if (it.dtype == BM_F32)
-      st[(size_t)i] = compress_t<float>(reinterpret_cast<const float*>(it.d_field), shp[(size_t)i].data(), prm[(size_t)i], it.tol,
-                                        it.tol_mode == BM_REL, it.h_roi_tol, reinterpret_cast<uint8_t*>(it.d_out),
-                                        it.out_capacity, &dummy, ps, &slot[(size_t)i]);
-    else
-      st[(size_t)i] = compress_t<double>(reinterpret_cast<const double*>(it.d_field), shp[(size_t)i].data(), prm[(size_t)i], it.tol,
-                                         it.tol_mode == BM_REL, it.h_roi_tol, reinterpret_cast<uint8_t*>(it.d_out),
-                                         it.out_capacity, &dummy, ps, &slot[(size_t)i]);
   }
-  for (size_t j = 0; j < ctx->streams.size(); ++j) {
-    BM_CUDA(cudaEventRecord(ctx->joins[j], ctx->streams[j]));
-    BM_CUDA(cudaStreamWaitEvent(s, ctx->joins[j], 0));
-  }
-  BM_CUDA(cudaStreamSynchronize(s));
-  bm_status first = BM_OK;
-  for (int i = 0; i < n; ++i) {
-    out_bytes[i] = 0;
-    if (st[(size_t)i] == BM_OK) {
-      const BatchSlot& b = slot[(size_t)i];
-      if (b.raw_now) out_bytes[i] = (size_t)b.raw_total;
-      else st[(size_t)i] = compress_result(reinterpret_cast<const Scalars*>(b.h), b.raw_total, &out_bytes[i]);
+  // a captured graph of this very call: restore its staging and replay it
+  if (graphs_on) {
+    for (BatchGraph& gph : ctx->graphs) {
+      if (gph.key != key) continue;
+      if (gph.gen != g_alloc_gen.load()) break;
+      std::memcpy(ctx->h, gph.hstage.data(), gph.hstage.size());
+      BM_CUDA(cudaGraphLaunch(gph.exec, s));
+      gph.used = ++ctx->clock;
+      for (int i = 0; i < n; ++i) {
+        slot[(size_t)i].raw_now = gph.raw_now[(size_t)i] != 0;
+        slot[(size_t)i].raw_total = gph.raw_total[(size_t)i];
+      }
+      return finish(slot);
     }
-    if (item_status) item_status[i] = st[(size_t)i];
-    if (first == BM_OK) first = st[(size_t)i];
   }
-  return first;
+  // the work of the call, enqueued on stream q (the call's stream, or the
+  // capture stream)
+  auto enqueue = [&](cudaStream_t q) -> bm_status {
+    // which items take the batched forward kernel, and their scratch
+    size_t dneed = 0;
+    std::vector<size_t> doff((size_t)n, 0);
+    std::vector<BatchGroup> groups;
+    for (int i = 0; i < n; ++i) {
+      if (st[(size_t)i] != BM_OK) continue;
+      const bm_batch_item& it = items[i];
+      BatchSlot& b = slot[(size_t)i];
+      b.phase = kQuery;
+      size_t dummy = 0;
+      st[(size_t)i] = it.dtype == BM_F32
+                          ? compress_t<float>(reinterpret_cast<const float*>(it.d_field), shp[(size_t)i].data(),
+                                              prm[(size_t)i], it.tol, it.tol_mode == BM_REL, it.h_roi_tol,
+                                              reinterpret_cast<uint8_t*>(it.d_out), it.out_capacity, &dummy, q, &b)
+                          : compress_t<double>(reinterpret_cast<const double*>(it.d_field), shp[(size_t)i].data(),
+                                               prm[(size_t)i], it.tol, it.tol_mode == BM_REL, it.h_roi_tol,
+                                               reinterpret_cast<uint8_t*>(it.d_out), it.out_capacity, &dummy, q, &b);
+      b.phase = kWhole;
+      if (st[(size_t)i] != BM_OK || !b.batched) continue;
+      doff[(size_t)i] = dneed;
+      dneed += (b.need + 255) & ~size_t(255);
+      const bool f64 = it.dtype == BM_F64;
+      const int B = prm[(size_t)i].B, K = prm[(size_t)i].K;
+      auto gi = std::find_if(groups.begin(), groups.end(),
+                             [&](const BatchGroup& x) { return x.f64 == f64 && x.B == B && x.K == K; });
+      if (gi == groups.end()) {
+        groups.push_back(BatchGroup{f64, B, K, {}});
+        gi = groups.end() - 1;
+      }
+      gi->items.push_back(i);
+    }
+    const size_t ddesc = dneed;
+    if (!groups.empty()) {
+      dneed += (size_t)n * sizeof(BatchField<double>) + groups.size() * 512 + 256;
+      if (bm_status e = batch_scratch(ctx, dneed)) return e;
+      for (const BatchGroup& gr : groups)
+        for (int i : gr.items) {
+          slot[(size_t)i].phase = kPrepare;
+          slot[(size_t)i].scratch = ctx->d + doff[(size_t)i];
+        }
+    }
+    // largest items first, so that each pool stream's workspace is sized once
+    std::vector<int> order((size_t)n);
+    for (int i = 0; i < n; ++i) order[(size_t)i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      return nel3(shp[(size_t)a].data()) * (items[a].dtype == BM_F64 ? 2 : 1) >
+             nel3(shp[(size_t)b].data()) * (items[b].dtype == BM_F64 ? 2 : 1);
+    });
+    constexpr int kHalf = kBatchStreams / 2;
+    // items of one phase, round robin over pool streams [first, first + kHalf)
+    auto run_items = [&](int want_phase, int first) {
+      int k = 0;
+      for (int i : order) {
+        if (st[(size_t)i] != BM_OK) continue;
+        BatchSlot& b = slot[(size_t)i];
+        if (b.phase != want_phase) continue;
+        const bm_batch_item& it = items[i];
+        cudaStream_t ps = want_phase == kPrepare ? q : ctx->streams[(size_t)(first + k++ % kHalf)];
+        size_t dummy = 0;
+        if (it.dtype == BM_F32)
+          st[(size_t)i] = compress_t<float>(reinterpret_cast<const float*>(it.d_field), shp[(size_t)i].data(),
+                                            prm[(size_t)i], it.tol, it.tol_mode == BM_REL, it.h_roi_tol,
+                                            reinterpret_cast<uint8_t*>(it.d_out), it.out_capacity, &dummy, ps, &b);
+        else
+          st[(size_t)i] = compress_t<double>(reinterpret_cast<const double*>(it.d_field), shp[(size_t)i].data(),
+                                             prm[(size_t)i], it.tol, it.tol_mode == BM_REL, it.h_roi_tol,
+                                             reinterpret_cast<uint8_t*>(it.d_out), it.out_capacity, &dummy, ps, &b);
+      }
+    };
+    auto fork = [&](int first) -> bm_status {
+      BM_CUDA(cudaEventRecord(ctx->forks[(size_t)(first / kHalf)], q));
+      for (int j = first; j < first + kHalf; ++j)
+        BM_CUDA(cudaStreamWaitEvent(ctx->streams[(size_t)j], ctx->forks[(size_t)(first / kHalf)], 0));
+      return BM_OK;
+    };
+    // 1. the batched items' setup (one small launch each) on q
+    run_items(kPrepare, 0);
+    // 2. the other items' whole pipelines on the first half of the pool,
+    //    beside the batched kernel
+    if (bm_status e = fork(0)) return e;
+    run_items(kWhole, 0);
+    // 3. the batched forward kernel, one launch per (dtype, B, K), on q
+    bool any = false;
+    if (!groups.empty()) {
+      size_t ho = hdesc, dof = ddesc;
+      for (BatchGroup& gr : groups) {
+        std::vector<int> live;
+        for (int i : gr.items)
+          if (st[(size_t)i] == BM_OK && !slot[(size_t)i].raw_now) live.push_back(i);
+        for (int i : gr.items) slot[(size_t)i].phase = kFinish;
+        gr.items = live;
+        if (gr.items.empty()) continue;
+        any = true;
+        const bm_status e = gr.f64 ? launch_group<double>(gr, slot, shp, ctx, &ho, &dof, q)
+                                   : launch_group<float>(gr, slot, shp, ctx, &ho, &dof, q);
+        if (e) return e;
+      }
+    }
+    // 4. the batched items' remaining stages on the second half
+    if (any || !groups.empty()) {
+      if (bm_status e = fork(kHalf)) return e;
+      run_items(kFinish, kHalf);
+    }
+    // 5. every pool stream back into q
+    for (size_t j = 0; j < ctx->streams.size(); ++j) {
+      BM_CUDA(cudaEventRecord(ctx->joins[j], ctx->streams[j]));
+      BM_CUDA(cudaStreamWaitEvent(q, ctx->joins[j], 0));
+    }
+    return BM_OK;
+  };
+  // capture the call when its key was met before (scratch is sized by then)
+  bool capture = false;
+  if (graphs_on) {
+    auto it = std::find(ctx->seen.begin(), ctx->seen.end(), key);
+    if (it != ctx->seen.end()) {
+      capture = true;
+      ctx->seen.erase(it);
+    } else {
+      ctx->seen.push_back(key);
+      if (ctx->seen.size() > 8) ctx->seen.erase(ctx->seen.begin());
+    }
+  }
+  if (capture) {
+    if (!ctx->cap) BM_CUDA(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
+    const uint64_t gen0 = g_alloc_gen.load();
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool ok = cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    bm_status e = BM_OK;
+    if (ok) {
+      e = enqueue(ctx->cap);
+      ok = cudaStreamEndCapture(ctx->cap, &graph) == cudaSuccess && e == BM_OK && graph;
+      ok = ok && g_alloc_gen.load() == gen0;
+      for (int i = 0; i < n && ok; ++i) ok = st[(size_t)i] == BM_OK;
+      ok = ok && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (ok) {
+      BatchGraph gph;
+      gph.key = std::move(key);
+      gph.exec = exec;
+      gph.hstage.assign(ctx->h, ctx->h + hb);
+      gph.gen = gen0;
+      gph.used = ++ctx->clock;
+      for (int i = 0; i < n; ++i) {
+        gph.raw_now.push_back(slot[(size_t)i].raw_now ? 1 : 0);
+        gph.raw_total.push_back(slot[(size_t)i].raw_total);
+      }
+      if (ctx->graphs.size() >= 4) {  // least recently used out
+        auto lru = std::min_element(ctx->graphs.begin(), ctx->graphs.end(),
+                                    [](const BatchGraph& a, const BatchGraph& b) { return a.used < b.used; });
+        cudaGraphExecDestroy(lru->exec);
+        ctx->graphs.erase(lru);
+      }
+      ctx->graphs.push_back(std::move(gph));
+      BM_CUDA(cudaGraphLaunch(exec, s));
+      return finish(slot);
+    }
+    // the capture failed: clear its errors and run the call directly
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaGetLastError();
+    for (int i = 0; i < n; ++i) {
+      st[(size_t)i] = BM_OK;
+      BatchSlot fresh;
+      fresh.h = slot[(size_t)i].h;
+      fresh.hd = slot[(size_t)i].hd;
+      slot[(size_t)i] = fresh;
+    }
+  }
+  // graphs holding stale scratch addresses are of no further use
+  for (size_t j = 0; j < ctx->graphs.size();) {
+    if (ctx->graphs[j].gen != g_alloc_gen.load()) {
+      cudaGraphExecDestroy(ctx->graphs[j].exec);
+      ctx->graphs.erase(ctx->graphs.begin() + (long)j);
+    } else {
+      ++j;
+    }
+  }
+  if (bm_status e = enqueue(s)) {
+    cudaStreamSynchronize(s);
+    return e;
+  }
+  return finish(slot);
 }
 
 bm_status bm_perf_model_fit(bm_dtype dtype, int block_nodes, bm_perf_model* model, void* stream) {

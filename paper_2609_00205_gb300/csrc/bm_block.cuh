@@ -19,11 +19,11 @@
 
 #include "bm_common.cuh"
 #include "bm_internal.h"
+#include "bm_qtab.cuh"
 
 // Build-time choices of the forward kernel: whether it keeps the symbol
 // histogram itself (BM_FWD_HIST; otherwise a separate pass counts the
-// symbols), prefetches the next block into a second buffer
-// (BM_FWD_DOUBLE_BUFFER), its threads per CTA (BM_FWD_THREADS; 0 = one per
+// symbols), its threads per CTA (BM_FWD_THREADS; 0 = one per
 // line of the first pass, B^2 rounded up to whole warps) and the CTAs per SM
 // it is compiled for (BM_FWD_MIN_CTAS, capped by what shared memory holds);
 // BM_INV_THREADS and BM_INV_MIN_CTAS are the last two for the inverse.  The
@@ -34,9 +34,6 @@
 // waits overlap the others' work.
 #ifndef BM_FWD_HIST
 #define BM_FWD_HIST 0
-#endif
-#ifndef BM_FWD_DOUBLE_BUFFER
-#define BM_FWD_DOUBLE_BUFFER 0
 #endif
 #ifndef BM_FWD_MIN_CTAS
 #define BM_FWD_MIN_CTAS 4
@@ -132,11 +129,10 @@ struct BlockCfg {
   static constexpr int CB1 = C2 * C2 * C2;
   static constexpr int PB = per_block_count(B, K);
   static constexpr int M = lvl_n(B, K);
-  static constexpr int NBUF = BM_FWD_DOUBLE_BUFFER ? 2 : 1;
   // byte offsets: the symbol staging area and the histogram start on 16-byte
   // boundaries (the staging area is copied out with 8-byte vectors)
   static constexpr size_t up16(size_t x) { return (x + 15) / 16 * 16; }
-  static constexpr size_t fwd_stage_off = up16(sizeof(T) * (NBUF * A + T1 + CB0 + CB1));  // T2 overlays A
+  static constexpr size_t fwd_stage_off = up16(sizeof(T) * (A + T1 + CB0 + CB1));  // T2 overlays A
   static constexpr size_t fwd_hist_off = up16(fwd_stage_off + 2 * PB);
   static constexpr size_t fwd_hist_end = fwd_hist_off + (BM_FWD_HIST ? 4 * kHistWin : 0);
   // bulk staging: B^2 row slots of RP bytes (a row of B elements starting
@@ -145,13 +141,13 @@ struct BlockCfg {
   // staging area; after the histogram when the kernel keeps one), then the
   // copies' mbarrier
   static constexpr int RP = (int)((B * sizeof(T) + 16 - sizeof(T) + 15) / 16 * 16);
-  static constexpr size_t fwd_stg_off = BM_FWD_HIST ? up16(fwd_hist_end) : up16(sizeof(T) * NBUF * A);
+  static constexpr size_t fwd_stg_off = BM_FWD_HIST ? up16(fwd_hist_end) : up16(sizeof(T) * A);
   // used unless the slots would cut the CTAs an SM holds (228 KB, 1 KB
   // reserved per CTA) below 16: FP64 with B = 17 keeps the element-wise copy
   static constexpr size_t fwd_stg_end = fwd_stg_off + (size_t)B * B * RP;
   static constexpr size_t fwd_bar_off = up16(fwd_stg_end > fwd_hist_end ? fwd_stg_end : fwd_hist_end);
   static constexpr int fit_of(size_t bytes) { return (int)((228u * 1024u) / (bytes + 1024u)); }
-  static constexpr bool BULK = BM_FWD_BULK && !BM_FWD_DOUBLE_BUFFER &&
+  static constexpr bool BULK = BM_FWD_BULK &&
                                (fit_of(fwd_bar_off + 16) >= fit_of(fwd_hist_end) || fit_of(fwd_bar_off + 16) >= 16);
   static constexpr size_t fwd_smem = BULK ? fwd_bar_off + 16 : fwd_hist_end;
   static constexpr size_t inv_stage_off = up16(sizeof(T) * (A + T1 + T2 + CB0 + CB1));
@@ -520,104 +516,258 @@ __device__ __forceinline__ void store_codes(uint16_t* __restrict__ sym, int32_t*
   }
 }
 
-// Forward: persistent CTAs walk the blocks; the next block is prefetched with
-// cp.async (zero fill outside the domain) while the current one is processed.
-template <typename T, int B, int K, int MODE>
-__global__ void __launch_bounds__(BlockCfg<T, B, K>::NT_FWD, BlockCfg<T, B, K>::FWD_MIN_CTAS)
-    block_fwd_kernel(BlockArgs<T> a) {
-  using Cfg = BlockCfg<T, B, K>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Abuf = reinterpret_cast<T*>(smem_raw);
-  T* T1 = Abuf + Cfg::NBUF * Cfg::A;
-  T* cb0 = T1 + Cfg::T1;
-  T* cb1 = cb0 + Cfg::CB0;
-  uint16_t* stage = reinterpret_cast<uint16_t*>(smem_raw + Cfg::fwd_stage_off);
-  unsigned* hloc = reinterpret_cast<unsigned*>(smem_raw + Cfg::fwd_hist_off);
+// Shared memory of the forward kernels.
+template <typename T, int B, int K>
+struct FwdSmem {
+  T* A;            // the block (B^3), then T2 over it
+  T* T1;           // first-pass results (B^2 C)
+  T* cb0;          // coarse values of odd levels (C^3)
+  T* cb1;          // coarse values of even levels
+  uint16_t* stage;  // the block's staged codes
+  unsigned* hloc;  // histogram window (BM_FWD_HIST)
+  uint64_t* bar;   // bulk-copy barrier (BM_FWD_BULK)
+  unsigned char* stg;  // bulk-copy row slots
+  __device__ __forceinline__ explicit FwdSmem(unsigned char* raw) {
+    using Cfg = BlockCfg<T, B, K>;
+    A = reinterpret_cast<T*>(raw);
+    T1 = A + Cfg::A;
+    cb0 = T1 + Cfg::T1;
+    cb1 = cb0 + Cfg::CB0;
+    stage = reinterpret_cast<uint16_t*>(raw + Cfg::fwd_stage_off);
+    hloc = reinterpret_cast<unsigned*>(raw + Cfg::fwd_hist_off);
+    bar = reinterpret_cast<uint64_t*>(raw + Cfg::fwd_bar_off);
+    stg = raw + Cfg::fwd_stg_off;
+  }
+};
 
-  if (MODE == 0 && BM_FWD_HIST)
-    for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) hloc[i] = 0;
-  bool ovf = false;
-  unsigned centre = 0;
-  auto span = [&](int64_t bi) { return BlockSpan<const T, B>(a.field, a.n0, a.n1, a.n2, BlockCoord(bi, a.nb1, a.nb2)); };
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + Cfg::fwd_bar_off);
-  unsigned char* stg = smem_raw + Cfg::fwd_stg_off;
-  unsigned phase = 0;
-  if (Cfg::BULK) {
+template <typename T, int B, int K>
+__device__ __forceinline__ void fwd_init(const FwdSmem<T, B, K>& S) {
+  if (BlockCfg<T, B, K>::BULK) {
     if (threadIdx.x == 0) {
-      mbar_init(bar, Cfg::NT_FWD);
+      mbar_init(S.bar, BlockCfg<T, B, K>::NT_FWD);
       mbar_fence_init();
     }
     __syncthreads();
   }
-  int64_t b = blockIdx.x;
-  int buf = 0;
-  if (BM_FWD_DOUBLE_BUFFER && b < a.nblocks) issue_block_load<T, B>(Abuf, a.field, span(b), a.n1, a.n2);
-  cp_async_commit();
-  auto interior = [&](const BlockSpan<const T, B>& sp) { return (sp.lim0 == B) & (sp.lim1 == B) & (sp.lim2 == B); };
-  for (; b < a.nblocks; b += gridDim.x) {
-    const BlockCoord bc(b, a.nb1, a.nb2);
-    if (BM_FWD_DOUBLE_BUFFER) {
-      const int64_t nx = b + gridDim.x;
-      if (nx < a.nblocks) issue_block_load<T, B>(Abuf + (buf ^ 1) * Cfg::A, a.field, span(nx), a.n1, a.n2);
-      cp_async_commit();
-      cp_async_wait<1>();
-      __syncthreads();
-    } else {
-      const BlockSpan<const T, B> sp(a.field, a.n0, a.n1, a.n2, bc);
-      if (Cfg::BULK && interior(sp)) {
-        const int64_t s0 = a.n1 * a.n2;
-        issue_block_bulk<T, B, K>(stg, bar, sp.base, s0, a.n2);
-        const bool late = !mbar_wait_bounded(bar, phase);
-        compact_block_rows<T, B, K>(Abuf, stg, sp.base, s0, a.n2);
-        if (__syncthreads_or(late)) {  // the copies never completed: report, drain (bounded), stop
-          if (threadIdx.x == 0 && a.sc) atomicOr(&a.sc->status, ST_TIMEOUT);
-          mbar_wait_bounded(bar, phase);
-          return;
-        }
-        phase ^= 1u;
-      } else {
-        issue_block_load<T, B>(Abuf, a.field, sp, a.n1, a.n2);
-        cp_async_commit();
-        cp_async_wait<0>();
-        __syncthreads();
-      }
-    }
+}
 
-    T rq[K];
-    const int tier = a.tier ? a.tier[b] : 0;
-#pragma unroll
-    for (int l = 0; l < K; ++l) rq[l] = MODE == 0 ? a.rq[tier * K + l] : T(0);
-    const int64_t sbase = b * (int64_t)Cfg::PB;
-    LevelBufs<T> bufs{Abuf + (BM_FWD_DOUBLE_BUFFER ? buf : 0) * Cfg::A, cb0, cb1};
-    FwdLevels<T, B, 0, K, B, MODE>::run(bufs, T1, rq, stage, a.esc + (MODE == 0 ? sbase : 0),
-                                        a.coef + (MODE == 1 ? sbase : 0), ovf);
-    // block coarse values -> gathered grid G
-    {
-      constexpr int M = Cfg::M;
-      const T* cf = bufs(K);
-      T* g = a.G + (((int64_t)bc.b0 * M) * a.g1 + (int64_t)bc.b1 * M) * a.g2 + (int64_t)bc.b2 * M;
-      for (int e = threadIdx.x; e < M * M * M; e += blockDim.x) {
-        const int j0 = e / (M * M), r = e - j0 * M * M, j1 = r / M, j2 = r - j1 * M;
-        g[((int64_t)j0 * a.g1 + j1) * a.g2 + j2] = cf[e];
-      }
+// One block of the forward pass: staged into shared memory (zero filled
+// outside the domain), K levels with the codes quantised on the spot, the
+// block's coarse values to the gathered grid G, its symbols and escapes out.
+// The quantiser table is read around L1 (the batched kernel writes it in the
+// same launch).  Returns false when the block's bulk copies never completed:
+// the status is set and the CTA must stop.
+template <typename T, int B, int K, int MODE>
+__device__ __forceinline__ bool fwd_block(const BlockArgs<T>& a, int64_t b, const FwdSmem<T, B, K>& S,
+                                          unsigned& phase, bool& ovf, unsigned& centre) {
+  using Cfg = BlockCfg<T, B, K>;
+  const BlockCoord bc(b, a.nb1, a.nb2);
+  const BlockSpan<const T, B> sp(a.field, a.n0, a.n1, a.n2, bc);
+  if (Cfg::BULK && (sp.lim0 == B) & (sp.lim1 == B) & (sp.lim2 == B)) {
+    const int64_t s0 = a.n1 * a.n2;
+    issue_block_bulk<T, B, K>(S.stg, S.bar, sp.base, s0, a.n2);
+    const bool late = !mbar_wait_bounded(S.bar, phase);
+    compact_block_rows<T, B, K>(S.A, S.stg, sp.base, s0, a.n2);
+    if (__syncthreads_or(late)) {  // the copies never completed: report, drain (bounded), stop
+      if (threadIdx.x == 0 && a.sc) atomicOr(&a.sc->status, ST_TIMEOUT);
+      mbar_wait_bounded(S.bar, phase);
+      return false;
     }
-    if (MODE == 0) store_codes<Cfg::PB>(a.sym + sbase, a.esc + sbase, stage, a.radius, hloc, a.hist, centre);
-    if (Cfg::BULK) fence_proxy_async_smem();  // the next block's bulk copies overwrite what was read here
+    phase ^= 1u;
+  } else {
+    issue_block_load<T, B>(S.A, a.field, sp, a.n1, a.n2);
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
-    buf ^= 1;
   }
-  cp_async_wait<0>();
-  if (MODE == 0 && !BM_FWD_HIST && ovf) atomicOr(&a.sc->status, ST_OVERFLOW);
+  T rq[K];
+  const int tier = a.tier ? a.tier[b] : 0;
+#pragma unroll
+  for (int l = 0; l < K; ++l) rq[l] = MODE == 0 ? __ldcg(a.rq + tier * K + l) : T(0);
+  const int64_t sbase = b * (int64_t)Cfg::PB;
+  const LevelBufs<T> bufs{S.A, S.cb0, S.cb1};
+  FwdLevels<T, B, 0, K, B, MODE>::run(bufs, S.T1, rq, S.stage, a.esc + (MODE == 0 ? sbase : 0),
+                                      a.coef + (MODE == 1 ? sbase : 0), ovf);
+  {  // block coarse values -> gathered grid G
+    constexpr int M = Cfg::M;
+    const T* cf = bufs(K);
+    T* g = a.G + (((int64_t)bc.b0 * M) * a.g1 + (int64_t)bc.b1 * M) * a.g2 + (int64_t)bc.b2 * M;
+    for (int e = threadIdx.x; e < M * M * M; e += blockDim.x) {
+      const int j0 = e / (M * M), r = e - j0 * M * M, j1 = r / M, j2 = r - j1 * M;
+      g[((int64_t)j0 * a.g1 + j1) * a.g2 + j2] = cf[e];
+    }
+  }
+  if (MODE == 0) store_codes<Cfg::PB>(a.sym + sbase, a.esc + sbase, S.stage, a.radius, S.hloc, a.hist, centre);
+  if (Cfg::BULK) fence_proxy_async_smem();  // the next block's bulk copies overwrite what was read here
+  __syncthreads();
+  return true;
+}
+
+// Forward: persistent CTAs walk the blocks of one field.  (A variant that
+// prefetched the next block into a second buffer with element-wise cp.async
+// cost more than it hid: twice the block array per CTA.)
+template <typename T, int B, int K, int MODE>
+__global__ void __launch_bounds__(BlockCfg<T, B, K>::NT_FWD, BlockCfg<T, B, K>::FWD_MIN_CTAS)
+    block_fwd_kernel(BlockArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const FwdSmem<T, B, K> S(smem_raw);
+  if (MODE == 0 && BM_FWD_HIST)
+    for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) S.hloc[i] = 0;
+  fwd_init(S);
+  bool ovf = false;
+  unsigned centre = 0, phase = 0;
+  for (int64_t b = blockIdx.x; b < a.nblocks; b += gridDim.x)
+    if (!fwd_block<T, B, K, MODE>(a, b, S, phase, ovf, centre)) return;
+  if (MODE == 0 && ovf) atomicOr(&a.sc->status, ST_OVERFLOW);
   if (MODE == 0 && BM_FWD_HIST) {
-    if (ovf) atomicOr(&a.sc->status, ST_OVERFLOW);
 #pragma unroll
     for (int o = 16; o; o >>= 1) centre += __shfl_xor_sync(0xffffffffu, centre, o);
-    if ((threadIdx.x & 31) == 0 && centre) atomicAdd(hloc + (kHistWin / 2), centre);
+    if ((threadIdx.x & 31) == 0 && centre) atomicAdd(S.hloc + (kHistWin / 2), centre);
     __syncthreads();
     const int lo = a.radius - kHistWin / 2;
     for (int i = threadIdx.x; i < kHistWin; i += blockDim.x) {
-      const unsigned v = hloc[i];
+      const unsigned v = S.hloc[i];
       if (v && lo + i >= 0 && lo + i < 2 * a.radius) atomicAdd(a.hist + lo + i, v);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Batched forward (Sec. III-B / III-D: many fields per launch): one persistent
+// launch drains a device-side queue of work items spanning every field of a
+// batch that shares (dtype, B, K).  Items are taken in ticket order from one
+// global counter: first the max|u| items of every field (a slice of
+// kBatchMaxChunk elements each), then one item per block.  The CTA that
+// finishes a field's last max|u| item computes that field's quantiser table
+// and raises its ready flag; a CTA taking a block of the field waits for the
+// flag (bounded, acquire).  Every max|u| item holds a lower ticket than every
+// block item and is done by a running CTA without waiting, so the wait ends.
+// ---------------------------------------------------------------------------
+constexpr int64_t kBatchMaxChunk = 65536;
+
+template <typename T>
+struct BatchField {
+  BlockArgs<T> a;             // the field's block arguments (MODE 0)
+  QtabArgs qa;                // its quantiser table (qa.sc: the field's scalars)
+  int64_t nel;                // elements of the field
+  unsigned long long max0;    // first max|u| ticket
+  unsigned long long blk0;    // first block ticket
+};
+
+struct BatchQueue {
+  unsigned long long* ticket;  // zeroed before the launch
+  unsigned long long n_max;    // max|u| items of all fields (tickets [0, n_max))
+  unsigned long long n_all;    // all items
+  int nfields;
+};
+
+// Field of ticket t: the last field whose first ticket (of the item's kind)
+// is <= t (binary search over the descriptors, one thread).
+template <typename T>
+__device__ __forceinline__ int batch_field_of(const BatchField<T>* f, int n, unsigned long long t, bool blk) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const unsigned long long v = blk ? __ldg(&f[mid].blk0) : __ldg(&f[mid].max0);
+    if (v <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// max|u| of elements [lo, hi) of u, 16-byte loads over the aligned middle.
+template <typename T>
+__device__ __forceinline__ void maxabs_slice(const T* __restrict__ u, int64_t lo, int64_t hi, T& m, bool& bad) {
+  constexpr int V = 16 / sizeof(T);
+  const uintptr_t pa = reinterpret_cast<uintptr_t>(u + lo);
+  int64_t h = (int64_t)(((16 - (pa & 15)) & 15) / sizeof(T));
+  if (h > hi - lo) h = hi - lo;
+  const int64_t nv = (hi - lo - h) / V;
+  const uint4* pv = reinterpret_cast<const uint4*>(u + lo + h);
+  for (int64_t i = threadIdx.x; i < nv; i += blockDim.x) {
+    const uint4 q = __ldg(pv + i);
+    const T* t = reinterpret_cast<const T*>(&q);
+#pragma unroll
+    for (int j = 0; j < V; ++j) maxabs_acc(t[j], m, bad);
+  }
+  for (int64_t i = threadIdx.x; i < h; i += blockDim.x) maxabs_acc(u[lo + i], m, bad);
+  for (int64_t i = lo + h + nv * V + threadIdx.x; i < hi; i += blockDim.x) maxabs_acc(u[i], m, bad);
+}
+
+template <typename T, int B, int K>
+__global__ void __launch_bounds__(BlockCfg<T, B, K>::NT_FWD, BlockCfg<T, B, K>::FWD_MIN_CTAS)
+    block_fwd_batch_kernel(const BatchField<T>* __restrict__ fields, BatchQueue q) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const FwdSmem<T, B, K> S(smem_raw);
+  __shared__ unsigned long long s_t;
+  __shared__ int s_ok;
+  __shared__ T s_m[32];
+  __shared__ int s_bad;
+  fwd_init(S);
+  unsigned phase = 0, centre = 0;
+  while (true) {
+    if (threadIdx.x == 0) s_t = atomicAdd(q.ticket, 1ull);
+    __syncthreads();
+    const unsigned long long t = s_t;
+    if (t >= q.n_all) break;
+    if (t < q.n_max) {  // a slice of max|u|
+      const int f = batch_field_of(fields, q.nfields, t, false);
+      const BatchField<T>& F = fields[f];
+      const int64_t lo = (int64_t)(t - F.max0) * kBatchMaxChunk;
+      const int64_t hi = lo + kBatchMaxChunk < F.nel ? lo + kBatchMaxChunk : F.nel;
+      T m = T(0);
+      bool bad = false;
+      maxabs_slice(F.a.field, lo, hi, m, bad);
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        const T y = __shfl_xor_sync(0xffffffffu, m, o);
+        m = y > m ? y : m;
+      }
+      bad = __any_sync(0xffffffffu, bad);
+      if (threadIdx.x == 0) s_bad = 0;
+      __syncthreads();
+      if ((threadIdx.x & 31) == 0) {
+        s_m[threadIdx.x >> 5] = m;
+        if (bad) s_bad = 1;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = s_m[w] > m ? s_m[w] : m;
+        Scalars* sc = F.qa.sc;
+        if (sizeof(T) == 4) atomicMax(&sc->maxabs_bits, (unsigned long long)__float_as_uint((float)m));
+        else atomicMax(&sc->maxabs_bits, (unsigned long long)__double_as_longlong((double)m));
+        if (s_bad) atomicOr(&sc->status, ST_RAW);
+        __threadfence();
+        const unsigned n_items = (unsigned)((F.nel + kBatchMaxChunk - 1) / kBatchMaxChunk);
+        if (atomicAdd(&sc->maxabs_done, 1u) == n_items - 1) {  // the field's last slice: its table
+          __threadfence();
+          qtab_compute(F.qa);
+          __threadfence();
+          asm volatile("st.release.gpu.global.u32 [%0], %1;\n" ::"l"(&sc->qready), "r"(1u) : "memory");
+        }
+      }
+      __syncthreads();
+    } else {  // one block
+      const int f = batch_field_of(fields, q.nfields, t, true);
+      const BatchField<T>& F = fields[f];
+      if (threadIdx.x == 0) {
+        const unsigned* flag = &F.qa.sc->qready;
+        unsigned v = 0;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(flag) : "memory");
+        if (!v) {
+          const long long t0 = clock64();
+          do {
+            __nanosleep(256);
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(flag) : "memory");
+          } while (!v && clock64() - t0 < (1ll << 31));
+        }
+        s_ok = v != 0;
+        if (!v) atomicOr(&F.qa.sc->status, ST_TIMEOUT);
+      }
+      __syncthreads();
+      if (!s_ok) continue;  // the field's table never came: reported, block skipped
+      bool ovf = false;
+      if (!fwd_block<T, B, K, 0>(F.a, (int64_t)(t - F.blk0), S, phase, ovf, centre)) return;
+      if (ovf) atomicOr(&F.a.sc->status, ST_OVERFLOW);
     }
   }
 }

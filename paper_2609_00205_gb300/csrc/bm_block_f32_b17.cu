@@ -14,4 +14,9 @@ cudaError_t launch_block_f32_b17(int dir, int K, int mode, const BlockArgs<float
   }
 }
 
+cudaError_t launch_block_batch_f32_b17(int K, const BatchField<float>* fields, const BatchQueue& q, cudaStream_t s,
+                                    int nsm) {
+  return launch_batch_k<float, 17>(K, fields, q, s, nsm);
+}
+
 }  // namespace bm

@@ -13,4 +13,9 @@ cudaError_t launch_block_f32_b9(int dir, int K, int mode, const BlockArgs<float>
   }
 }
 
+cudaError_t launch_block_batch_f32_b9(int K, const BatchField<float>* fields, const BatchQueue& q, cudaStream_t s,
+                                    int nsm) {
+  return launch_batch_k<float, 9>(K, fields, q, s, nsm);
+}
+
 }  // namespace bm

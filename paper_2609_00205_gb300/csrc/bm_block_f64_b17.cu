@@ -14,4 +14,9 @@ cudaError_t launch_block_f64_b17(int dir, int K, int mode, const BlockArgs<doubl
   }
 }
 
+cudaError_t launch_block_batch_f64_b17(int K, const BatchField<double>* fields, const BatchQueue& q, cudaStream_t s,
+                                    int nsm) {
+  return launch_batch_k<double, 17>(K, fields, q, s, nsm);
+}
+
 }  // namespace bm

@@ -13,4 +13,9 @@ cudaError_t launch_block_f64_b9(int dir, int K, int mode, const BlockArgs<double
   }
 }
 
+cudaError_t launch_block_batch_f64_b9(int K, const BatchField<double>* fields, const BatchQueue& q, cudaStream_t s,
+                                    int nsm) {
+  return launch_batch_k<double, 9>(K, fields, q, s, nsm);
+}
+
 }  // namespace bm

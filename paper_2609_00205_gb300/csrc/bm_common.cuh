@@ -44,7 +44,7 @@ struct Scalars {
   unsigned maxabs_done;            // CTAs of the max|u| pass that have finished
   unsigned enc_lo;                 // first symbol of the encoder's shared-memory code window
   unsigned enc_full;               // 1: every present symbol lies in that window
-  unsigned pad1;
+  unsigned qready;                 // batched forward kernel: 1 once the quantiser table is written
 };
 
 // ---------------------------------------------------------------------------

@@ -41,6 +41,20 @@ cudaError_t launch_block_f64_b9(int dir, int K, int mode, const BlockArgs<double
 cudaError_t launch_block_f64_b17(int dir, int K, int mode, const BlockArgs<double>& a, cudaStream_t s, int nsm,
                                  int max_grid);
 
+// Batched forward In-cache Block kernel (max|u|, quantiser tables and the
+// blocks of every field of a batch sharing dtype, B and K; mode 0).
+template <typename T>
+struct BatchField;
+struct BatchQueue;
+cudaError_t launch_block_batch_f32_b9(int K, const BatchField<float>* fields, const BatchQueue& q, cudaStream_t s,
+                                      int nsm);
+cudaError_t launch_block_batch_f32_b17(int K, const BatchField<float>* fields, const BatchQueue& q, cudaStream_t s,
+                                       int nsm);
+cudaError_t launch_block_batch_f64_b9(int K, const BatchField<double>* fields, const BatchQueue& q, cudaStream_t s,
+                                      int nsm);
+cudaError_t launch_block_batch_f64_b17(int K, const BatchField<double>* fields, const BatchQueue& q, cudaStream_t s,
+                                       int nsm);
+
 // Transposed In-cache Block levels: dir 0 = transposed decomposition
 // (coefficient and block-coarse gradients -> field gradients), dir 1 =
 // transposed recomposition (field gradients -> coefficient and block-coarse

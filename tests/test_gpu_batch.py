@@ -122,3 +122,72 @@ def test_perf_model_fit_and_selection(bm):
     s = bm.compress(u, 1e-3, **p)
     d = bm.decompress(s)
     assert float((d - u).abs().max()) <= 1e-3 * float(u.abs().max())
+
+
+def test_batched_kernel_groups_and_fallbacks(bm):
+    """A batch mixing every kind of item: groups of the persistent forward
+    kernel (FP32 B17 K2, FP32 B9 K1, FP64 B9 K2 with a ROI map, FP64 B17 K1,
+    a field of ~7 M elements spanning many max|u| slices), and items that keep
+    their own pipeline (a planar field, B = 8, two rounds), a field with a NaN
+    (raw stream) and one with an infinity; every stream equals the single
+    call's byte for byte, and two items match the oracle."""
+    rng = np.random.default_rng(7)
+    specs = [
+        ((200, 190, 180), torch.float32, dict(block=17, levels=2, global_levels=2), 1e-3),
+        ((45, 38, 52), torch.float32, dict(block=17, levels=2, global_levels=2), 1e-4),
+        ((30, 70, 41), torch.float32, dict(block=17, levels=2, global_levels=1), 1e-2),
+        ((40, 33, 29), torch.float32, dict(block=9, levels=1, global_levels=1), 5e-3),
+        ((27, 30, 36), torch.float32, dict(block=9, levels=1, global_levels=2), 1e-5),
+        ((41, 37, 33), torch.float64, dict(block=9, levels=2, global_levels=2), 1e-4),
+        ((25, 31, 29), torch.float64, dict(block=9, levels=2, global_levels=2), 2e-3),
+        ((35, 18, 40), torch.float64, dict(block=17, levels=1, global_levels=1), 1e-6),
+        ((300, 257), torch.float32, dict(block=17, levels=2, global_levels=2), 1e-3),
+        ((40, 37, 45), torch.float32, dict(block=8, levels=2, global_levels=1), 1e-3),
+        ((70, 61, 53), torch.float32, dict(block=17, levels=2, global_levels=1, rounds=2), 1e-3),
+        ((33, 34, 35), torch.float32, dict(block=17, levels=2, global_levels=2), 1e-3),
+        ((34, 35, 36), torch.float32, dict(block=17, levels=2, global_levels=2), 1e-3),
+    ]
+    fs, tols, rois, params = [], [], [], []
+    for i, (shape, dt, p, tol) in enumerate(specs):
+        u = fields.power_law_grf(shape, exponent=-3.0, seed=500 + i, dtype=dt, device=DEV).contiguous()
+        fs.append(u)
+        tols.append(tol)
+        params.append(p)
+        roi = None
+        if i == 5:
+            nb = int(np.prod([(s + p["block"] - 1) // p["block"] for s in shape]))
+            roi = np.full(nb, tol)
+            roi[rng.choice(nb, size=max(1, nb // 8), replace=False)] = tol / 10
+        rois.append(roi)
+    fs[11].view(-1)[12345] = float("nan")
+    fs[12].view(-1)[777] = float("inf")
+    out = bm.compress_batch(fs, tols, rois=rois, params=params)
+    for i, (u, t, r, p, s) in enumerate(zip(fs, tols, rois, params, out)):
+        ref = bm.compress(u, t, roi=r, **p)
+        assert torch.equal(s, ref), i
+    for i in (1, 5):
+        u = fs[i].cpu().numpy()
+        p = params[i]
+        check_stream_parity(bm, u, out[i].cpu().numpy(), tols[i], "rel", p["block"], p["levels"], p["global_levels"],
+                            roi=rois[i], label="batched_kernel_item%d" % i, dev=DEV)
+    # the same batch again: the second call is captured as a CUDA graph, the
+    # third and fourth replay it (tickets and flags start afresh each time)
+    for _ in range(3):
+        again = bm.compress_batch(fs, tols, rois=rois, params=params)
+        for a, b in zip(out, again):
+            assert torch.equal(a, b)
+    # new field values under the same arguments: the replayed graph reads them
+    for u in fs[:11]:
+        u.mul_(0.5).add_(0.25)
+    out2 = bm.compress_batch(fs, tols, rois=rois, params=params)
+    for i, (u, t, r, p, s) in enumerate(zip(fs, tols, rois, params, out2)):
+        assert torch.equal(s, bm.compress(u, t, roi=r, **p)), i
+    # other arguments (a tolerance, a ROI entry): not the captured graph
+    tols2 = list(tols)
+    tols2[3] = 2e-3
+    rois2 = [None if r is None else r.copy() for r in rois]
+    rois2[5][0] = tols[5] / 100
+    for _ in range(3):
+        out3 = bm.compress_batch(fs, tols2, rois=rois2, params=params)
+        for i, (u, t, r, p, s) in enumerate(zip(fs, tols2, rois2, params, out3)):
+            assert torch.equal(s, bm.compress(u, t, roi=r, **p)), i
