@@ -545,6 +545,23 @@ int grid_for(int64_t work, int threads, int per_sm = 8) {
   return (int)std::max<int64_t>(g, 1);
 }
 
+// CTAs of the decoder an SM holds (its lookup table, threads and registers),
+// once per device.
+int dec_per_sm() {
+  static std::atomic<int> cached[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return 1;
+  int v = cached[dev].load();
+  if (v <= 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, decode_kernel, kDecThreads, kDecSmem) != cudaSuccess || v < 1) {
+      cudaGetLastError();
+      v = 1;
+    }
+    cached[dev].store(v);
+  }
+  return v;
+}
+
 // Histogram of symbols [s0, s1) into hist (zeroed by the caller): with
 // `ctas` CTAs of the small-window kernel when the dictionary fits its window,
 // else one wide-window CTA per SM (at most `ctas`).  With `check`, symbols
@@ -1766,7 +1783,7 @@ bm_status decode_symbols(const uint8_t* in, const Header& H, Carver& cv, uint16_
     da.splits = reinterpret_cast<const uint16_t*>(in + H.off_splits);
     da.tab = dt; da.sym = sym; da.sc = sc;
     BM_CUDA(set_smem_once(decode_kernel, (int)kDecSmem, g_dec_attr));
-    decode_kernel<<<grid_for((int64_t)H.n_chunks * kSplits, kDecThreads, 3), kDecThreads, kDecSmem, s>>>(da);
+    decode_kernel<<<grid_for((int64_t)H.n_chunks * kSplits, kDecThreads, dec_per_sm()), kDecThreads, kDecSmem, s>>>(da);
     BM_LAUNCHED();
     if (stream_mode && H.n_outliers) {
       escape_fixup_kernel<<<grid_for((int64_t)H.n_chunks * 32, 256, 8), 256, 0, s>>>(

@@ -40,7 +40,10 @@ struct CanonTables {
 
 struct DecodeTables {
   CanonTables ct;
-  alignas(16) unsigned lut[1 << kLutBits];  // sym | len << 16 for codes of <= kLutBits bits, 0 otherwise
+  // sym | len << 16 for codes of <= kLutBits bits; for a prefix of longer
+  // codes, L0 << 16 with L0 > kLutBits the length of the prefix's first code
+  // (kMaxLen + 1: no code has the prefix)
+  alignas(16) unsigned lut[1 << kLutBits];
   uint16_t canon[kMaxDict];     // symbols in canonical order
   // construction arrays for more present symbols than shared memory holds
   uint8_t big_clen[kMaxDict];
@@ -1546,15 +1549,16 @@ __device__ __forceinline__ void decode_tables_block(const uint8_t* runs, unsigne
   __syncthreads();
   // every LUT entry from its own bits: the length is the first whose
   // left-justified limit lies above them (canonical order), the symbol that
-  // code's canonical rank
+  // code's canonical rank; a prefix of longer codes keeps the length of its
+  // first code, where the decoder's search for the length starts
   for (int p = threadIdx.x; p < (1 << kLutBits); p += blockDim.x) {
     const unsigned long long peek = (unsigned long long)p << (32 - kLutBits);
     unsigned L = 1;
-    while (L <= (unsigned)kLutBits && peek >= S.ct.limit[L]) ++L;
-    unsigned e = 0;
+    while (L <= (unsigned)kMaxLen && peek >= S.ct.limit[L]) ++L;
+    unsigned e = L << 16;
     if (L <= (unsigned)kLutBits) {
       const unsigned idx = S.ct.first_pos[L] + (((unsigned)peek >> (32 - L)) - S.ct.first_code[L]);
-      if (idx < S.ct.n) e = (unsigned)csym[canon[idx]] | (L << 16);
+      e = idx < S.ct.n ? ((unsigned)csym[canon[idx]] | (L << 16)) : ((unsigned)(kMaxLen + 1) << 16);
     }
     out->lut[p] = e;
   }
@@ -1576,13 +1580,22 @@ struct DecodeArgs {
 
 // One thread per run (an eighth of a chunk): table-driven canonical decoding
 // with a 64-bit window refilled a word at a time from registers loaded ahead
-// in 16-byte groups, sixteen symbols per step stored as one 32-byte sector.  Codes of at most
-// kLutBits bits (nearly all) take one shared-memory lookup; longer ones walk
-// the left-justified limits.  A run must end exactly where the next one
+// in 16-byte groups, sixteen symbols per step stored as one 32-byte sector.
+// Codes of at most kLutBits bits take one shared-memory lookup; for a longer
+// one the lookup gives the length of the first code of its prefix, from
+// which the left-justified limits are walked (one or two steps).  A run must end exactly where the next one
 // starts (the last run of a chunk within the chunk); reading past the chunk
 // reads zeros and shows in that check.  Persistent CTAs: the tables are
 // staged once per CTA.
-constexpr int kDecThreads = 256;
+// Threads per decoder CTA: the lookup table (64 KB) is staged once per CTA,
+// so larger CTAs keep more warps per SM on one table.  On GB300 (513^3 FP32
+// streams, 1e-2 .. 1e-5) 512 took 0.399 / 0.501 / 0.723 / 1.186 ms against
+// 0.451 / 0.566 / 0.749 / 1.189 with 256 and 0.682 / 0.903 / 1.180 / 1.586
+// with 128.
+#ifndef BM_DEC_THREADS
+#define BM_DEC_THREADS 512
+#endif
+constexpr int kDecThreads = BM_DEC_THREADS;
 constexpr size_t kDecSmem = sizeof(unsigned) * (1u << kLutBits) + sizeof(unsigned long long) * (kMaxLen + 2) +
                             2 * sizeof(unsigned) * (kMaxLen + 2);
 
@@ -1649,37 +1662,41 @@ __global__ void __launch_bounds__(kDecThreads) decode_kernel(DecodeArgs a) {
     unsigned nwords = 2;  // words entered into the window
     bool bad = false;
     auto one = [&]() -> unsigned {
-      if (nbits <= 32) {
-        buf |= (unsigned long long)c0 << (32 - nbits);
-        nbits += 32;
-        ++nwords;
-        c0 = c1;
-        c1 = c2;
-        c2 = c3;
-        if (--cl == 0) {
-          c0 = n.x;
-          c1 = n.y;
-          c2 = n.z;
-          c3 = n.w;
-          n = ld4(gq);
-          gq += 4;
-          cl = 4;
-        }
+      // a word into the window when 32 bits or fewer are left: selects, so
+      // that lanes refilling at different symbols do not diverge; only the
+      // reload of the queue (every fourth word) branches
+      const bool need = nbits <= 32;
+      const int sh = need ? 32 - nbits : 0;
+      buf |= need ? (unsigned long long)c0 << sh : 0ull;
+      nbits += need ? 32 : 0;
+      nwords += need ? 1u : 0u;
+      c0 = need ? c1 : c0;
+      c1 = need ? c2 : c1;
+      c2 = need ? c3 : c2;
+      cl -= need ? 1 : 0;
+      if (cl == 0) {
+        c0 = n.x;
+        c1 = n.y;
+        c2 = n.z;
+        c3 = n.w;
+        n = ld4(gq);
+        gq += 4;
+        cl = 4;
       }
       const unsigned peek = (unsigned)(buf >> 32);
       unsigned e = lut[peek >> (32 - kLutBits)];
-      if (e == 0u) {  // a code longer than kLutBits bits
-        unsigned L = kLutBits + 1;
+      unsigned L = e >> 16;
+      if (L > (unsigned)kLutBits) {  // a longer code: its length from its prefix's first on
         while (L <= (unsigned)kMaxLen && (unsigned long long)peek >= limit[L]) ++L;
         const unsigned idx = L <= (unsigned)kMaxLen ? fpos[L] + ((peek >> (32 - L)) - fcode[L]) : nsym;
         if (idx >= nsym) {
           bad = true;
-          e = 1u << 16;
+          L = 1;
+          e = 0;
         } else {
-          e = (unsigned)canon[idx] | (L << 16);
+          e = (unsigned)canon[idx];
         }
       }
-      const unsigned L = e >> 16;
       buf <<= L;
       nbits -= (int)L;
       return e & 0xFFFFu;
