@@ -1628,10 +1628,11 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     ea.chunk_words = reinterpret_cast<unsigned*>(out + L.off_chunks);
     ea.splits = reinterpret_cast<uint16_t*>(out + L.off_splits);
     ea.out = out; ea.capacity = cap; ea.sc = sc;
-    BM_CUDA(prefer_l1_once(encode_fused_kernel<8, false, true>, g_encw_attr));
-    encode_fused_kernel<8, false, false><<<grid_for((int64_t)L.nch * 32, 256, 4), 256, enc_smem<false>(), s>>>(ea);
-    encode_fused_kernel<8, false, true><<<grid_for((int64_t)L.nch * 32, 256, 4), 256, 0, s>>>(ea);
-    g_launches.fetch_add(2);
+    BM_CUDA(prefer_l1_once(encode_fused_kernel<8, false, 2>, g_encw_attr));
+    encode_fused_kernel<8, false, 0><<<grid_for((int64_t)L.nch * 32, 256, 4), 256, enc_smem<0>(), s>>>(ea);
+    encode_fused_kernel<8, false, 1><<<grid_for((int64_t)L.nch * 32, 256, 4), 256, enc_smem<1>(), s>>>(ea);
+    encode_fused_kernel<8, false, 2><<<grid_for((int64_t)L.nch * 32, 256, 4), 256, 0, s>>>(ea);
+    g_launches.fetch_add(3);
   }
   {
     Stage st("finish");
@@ -2959,10 +2960,10 @@ bm_status bm_huffman_encode(const uint16_t* d_symbols, uint64_t n, int dict_size
     ea.capacity = out_capacity; ea.sc = sc;
     ea.packed = packed;
     if (dict_size <= kEncWin) {
-      encode_fused_kernel<8, true, false><<<grid_for((int64_t)nch * 32, 256, 4), 256, enc_smem<false>(), s>>>(ea);
+      encode_fused_kernel<8, true, 0><<<grid_for((int64_t)nch * 32, 256, 4), 256, enc_smem<0>(), s>>>(ea);
     } else {
-      BM_CUDA(prefer_l1_once(encode_fused_kernel<8, true, true>, g_encc_attr));
-      encode_fused_kernel<8, true, true><<<grid_for((int64_t)nch * 32, 256, 4), 256, 0, s>>>(ea);
+      BM_CUDA(prefer_l1_once(encode_fused_kernel<8, true, 2>, g_encc_attr));
+      encode_fused_kernel<8, true, 2><<<grid_for((int64_t)nch * 32, 256, 4), 256, 0, s>>>(ea);
     }
     encode_finish_kernel<<<1, 32, 0, s>>>(~0ull, out_capacity, sc);
     zero_tail_kernel<<<1, 32, 0, s>>>(out, sc);
@@ -3130,7 +3131,7 @@ extern "C" bm_status bm_huffman_encode_noalloc(const uint16_t* d_symbols, uint64
   ea.chunk_words = reinterpret_cast<unsigned*>(out); ea.out = out;
   ea.splits = reinterpret_cast<uint16_t*>(out + off_sp);
   ea.capacity = out_capacity; ea.sc = sc;
-  encode_fused_kernel<8, true, false><<<grid_for((int64_t)nch * 32, 256, 4), 256, enc_smem<false>(), s>>>(ea);
+  encode_fused_kernel<8, true, 0><<<grid_for((int64_t)nch * 32, 256, 4), 256, enc_smem<0>(), s>>>(ea);
   encode_finish_kernel<<<1, 32, 0, s>>>(~0ull, out_capacity, sc);
   zero_tail_kernel<<<1, 32, 0, s>>>(out, sc);
   g_launches.fetch_add(6);

@@ -43,7 +43,7 @@ struct Scalars {
   unsigned long long esc_seen;     // escapes the encoder met (must equal n_outliers)
   unsigned maxabs_done;            // CTAs of the max|u| pass that have finished
   unsigned enc_lo;                 // first symbol of the encoder's shared-memory code window
-  unsigned enc_full;               // 1: every present symbol lies in that window
+  unsigned enc_mode;               // the encoder's table: 0 window, 1 window + global table, 2 global table
   unsigned qready;                 // batched forward kernel: 1 once the quantiser table is written
 };
 

@@ -20,10 +20,23 @@ constexpr int kLutBits = 14;
 // Entries of the code table the encoder keeps in shared memory (a window of
 // the dictionary; symbols outside it are looked up in the global table).
 constexpr int kEncWin = 8192;
+// The window variant with global look-ups beside it is taken while its
+// window (and the escape symbol's registers) serve at least BM_ENC_WIN_PCT
+// percent of a call's symbols and fewer than BM_ENC_ESC_PCT percent escape.
+// When escapes dominate, the other symbols are the far tails spread over the
+// whole dictionary, and the global-table variant, which leaves all of L1 to
+// the table, was faster on GB300 (513^3, 1e-5: 1.11 against 1.47 ms); at 1e-3
+// and 1e-4 the window variant was (0.47 against 0.56 ms, 0.89 against 0.99).
+#ifndef BM_ENC_WIN_PCT
+#define BM_ENC_WIN_PCT 50
+#endif
+#ifndef BM_ENC_ESC_PCT
+#define BM_ENC_ESC_PCT 20
+#endif
 // Shared memory of the encoder: the window's codes and lengths; the variant
 // for wide code distributions (GLOB) keeps no table in shared memory.
-template <bool GLOB>
-__host__ __device__ constexpr size_t enc_smem() { return GLOB ? 0 : (size_t)kEncWin * 5; }
+template <int TAB>
+__host__ __device__ constexpr size_t enc_smem() { return TAB == 2 ? 0 : (size_t)kEncWin * 5; }
 // Every chunk is split into eight equal runs; the stream stores the bit
 // offsets of runs 1..7 so that eight decoders can work on one chunk.
 constexpr int kSplits = 8;
@@ -647,8 +660,8 @@ __device__ void codebook_lengths(const CodebookArgs& a, CbArrays<IdT> V, int n, 
 template <typename IdT>
 __device__ void codebook_emit(const CodebookArgs& a, CbArrays<IdT> V, int n, unsigned* scan_tmp, CanonTables* ct) {
   __shared__ unsigned s_total, s_nruns;
-  __shared__ unsigned long long s_bits;
-  if (threadIdx.x == 0) s_bits = 0;
+  __shared__ unsigned long long s_bits, s_all, s_win;
+  if (threadIdx.x == 0) { s_bits = 0; s_all = 0; s_win = 0; }
   // 4. canonical codes (the counting pass in the sort counts' shared memory)
   build_canonical(V.clen, n, V.wcnt, V.canon, ct);
   const bool pk = a.packed && ct->max_len <= 26;
@@ -729,11 +742,29 @@ __device__ void codebook_emit(const CodebookArgs& a, CbArrays<IdT> V, int n, uns
   // 6. layout of the rest of the stream (escape counts, outlier codes, then
   // the bitstream) and a lower bound on its size: the bitstream holds exactly
   // sum_s f_s len_s bits plus the padding of each chunk to whole words
-  unsigned long long my_bits = 0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) my_bits += (unsigned long long)a.hist[V.csym[i]] * V.clen[i];
+  // (and the symbols met that the encoder's window centred on code 0, or the
+  // escape symbol's registers, serve)
+  const unsigned wlo_c =
+      a.dict <= kEncWin ? 0u : (unsigned)min(max(a.dict / 2 - kEncWin / 2, 0), a.dict - kEncWin);
+  unsigned long long my_bits = 0, my_all = 0, my_win = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const unsigned sy = V.csym[i];
+    const unsigned long long f = a.hist[sy];
+    my_bits += f * V.clen[i];
+    my_all += f;
+    if (sy - wlo_c < (unsigned)kEncWin || sy == 0u) my_win += f;
+  }
 #pragma unroll
-  for (int o = 16; o; o >>= 1) my_bits += __shfl_xor_sync(0xffffffffu, my_bits, o);
-  if ((threadIdx.x & 31) == 0 && my_bits) atomicAdd(&s_bits, my_bits);
+  for (int o = 16; o; o >>= 1) {
+    my_bits += __shfl_xor_sync(0xffffffffu, my_bits, o);
+    my_all += __shfl_xor_sync(0xffffffffu, my_all, o);
+    my_win += __shfl_xor_sync(0xffffffffu, my_win, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (my_bits) atomicAdd(&s_bits, my_bits);
+    if (my_all) atomicAdd(&s_all, my_all);
+    if (my_win) atomicAdd(&s_win, my_win);
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     Scalars* sc = a.sc;
@@ -741,15 +772,22 @@ __device__ void codebook_emit(const CodebookArgs& a, CbArrays<IdT> V, int n, uns
     sc->n_runs = (unsigned long long)nruns;
     sc->max_len = ct->max_len;
     // the encoder's shared-memory window of the code table: every present
-    // symbol when they span at most kEncWin symbols, else centred on the
-    // dictionary's middle (code 0); symbols outside it are looked up in memory
+    // symbol when they span at most kEncWin symbols; else centred on the
+    // dictionary's middle (code 0) while it and the escape symbol serve at
+    // least BM_ENC_WIN_PCT percent of the symbols met and escapes are fewer
+    // than BM_ENC_ESC_PCT percent (the rest looked up in the global table);
+    // else no window (the global-table variant, with all of L1 for the table)
     const unsigned smin = n ? V.csym[0] : 0u, smax = n ? V.csym[n - 1] : 0u;
     if (smax - smin < (unsigned)kEncWin) {
       sc->enc_lo = a.dict <= kEncWin ? 0u : min(smin, (unsigned)(a.dict - kEncWin));
-      sc->enc_full = 1;
+      sc->enc_mode = 0;
+    } else if (s_win * 100ull >= (unsigned long long)BM_ENC_WIN_PCT * s_all &&
+               (unsigned long long)a.hist[0] * 100ull < (unsigned long long)BM_ENC_ESC_PCT * s_all) {
+      sc->enc_lo = wlo_c;
+      sc->enc_mode = 1;
     } else {
       sc->enc_lo = 0;
-      sc->enc_full = 0;
+      sc->enc_mode = 2;
     }
     if (a.out && !fits) atomicOr(&sc->status, ST_CAPACITY | ST_RAW);
     const unsigned long long nout = a.esc_mode ? (unsigned long long)a.hist[0] : 0ull;
@@ -1068,10 +1106,11 @@ __device__ __forceinline__ unsigned sym_of(const uint4* q, int i) {
 
 // The encoder's code table: with GLOB = false, a window of kEncWin entries
 // in shared memory (sc: code, or code | len << 26 when every code has at most
-// 26 bits; sl: length) starting at symbol `lo` that holds every symbol met;
-// with GLOB = true (code distributions wider than the window) the whole table
-// in global memory, read through L1 (gp: packed entries, or gc / gl), and the
-// escape symbol 0's entry in registers.
+// 26 bits; sl: length) starting at symbol `lo`, symbols outside it looked up
+// in the global table; with GLOB = true (code distributions whose mass lies
+// mostly outside any window) the whole table in global memory, read through
+// L1 (gp: packed entries, or gc / gl).  Either way the escape symbol 0's
+// entry is in registers.
 struct EncTab {
   const unsigned* sc;
   const uint8_t* sl;
@@ -1082,17 +1121,24 @@ struct EncTab {
   unsigned c0, l0;  // code and length of symbol 0
 };
 
-template <bool PACKED, bool GLOB>
+// Table of a lookup: TAB 0 = the shared-memory window only (it holds every
+// symbol met), 1 = the window with the global table for symbols outside it,
+// 2 = the global table only.
+template <bool PACKED, int TAB>
 __device__ __forceinline__ void code_of(const EncTab& t, unsigned s, unsigned& c, unsigned& L) {
-  if (!GLOB) {
+  if (TAB < 2) {
     const unsigned k = s - t.lo;
-    const unsigned cw = t.sc[k];
-    if (PACKED) { c = cw & 0x3FFFFFFu; L = cw >> 26; }
-    else { c = cw; L = t.sl[k]; }
-  } else if (s == 0u) {
+    if (TAB == 0 || k < (unsigned)kEncWin) {
+      const unsigned cw = t.sc[k];
+      if (PACKED) { c = cw & 0x3FFFFFFu; L = cw >> 26; }
+      else { c = cw; L = t.sl[k]; }
+      return;
+    }
+  }
+  if (s == 0u) {
     c = t.c0;
     L = t.l0;
-  } else if (PACKED) {
+  } else if (PACKED && t.gp) {
     const unsigned cw = __ldg(t.gp + s);
     c = cw & 0x3FFFFFFu;
     L = cw >> 26;
@@ -1101,11 +1147,14 @@ __device__ __forceinline__ void code_of(const EncTab& t, unsigned s, unsigned& c
     L = __ldg(t.gl + s);
   }
 }
-template <bool PACKED, bool GLOB>
+template <bool PACKED, int TAB>
 __device__ __forceinline__ unsigned len_of(const EncTab& t, unsigned s) {
-  if (!GLOB) return PACKED ? (t.sc[s - t.lo] >> 26) : (unsigned)t.sl[s - t.lo];
+  if (TAB < 2) {
+    const unsigned k = s - t.lo;
+    if (TAB == 0 || k < (unsigned)kEncWin) return PACKED ? (t.sc[k] >> 26) : (unsigned)t.sl[k];
+  }
   if (s == 0u) return t.l0;
-  return PACKED ? (__ldg(t.gp + s) >> 26) : (unsigned)__ldg(t.gl + s);
+  return (PACKED && t.gp) ? (__ldg(t.gp + s) >> 26) : (unsigned)__ldg(t.gl + s);
 }
 
 // Symbols of a slice, streamed past L1 (the global code table of the GLOB
@@ -1120,7 +1169,7 @@ __device__ __forceinline__ uint4 ld_stream(const uint4* p) {
 // Bits and escape mask of a lane's vector slice (G groups held in registers).
 // CLAMP: symbols may be out of the dictionary (caller-supplied) and are
 // clamped; the compressor's own symbols are in range by construction.
-template <bool PACKED, bool WIN, bool CLAMP, int GC>
+template <bool PACKED, int TAB, bool CLAMP, int GC>
 __device__ __forceinline__ void slice_bits(const uint4* q, int G, unsigned dmax, const EncTab& tab, unsigned& bits,
                                            unsigned long long& emask) {
   bits = 0;
@@ -1129,7 +1178,7 @@ __device__ __forceinline__ void slice_bits(const uint4* q, int G, unsigned dmax,
   for (int i = 0; i < 8 * kEncGroups; ++i) {
     if ((i >> 3) < (GC ? GC : G)) {
       const unsigned s = CLAMP ? min(sym_of(q, i), dmax) : sym_of(q, i);
-      bits += len_of<PACKED, WIN>(tab, s);
+      bits += len_of<PACKED, TAB>(tab, s);
       nz += s == 0;
     }
   }
@@ -1148,7 +1197,7 @@ __device__ __forceinline__ void slice_bits(const uint4* q, int G, unsigned dmax,
 // word is stored through `wp` as soon as it fills.  The lane's first word may
 // start with the previous lane's last bits: it is stored with zeros there and
 // the previous lane ORs its bits in afterwards.
-template <bool PACKED, bool WIN, bool CLAMP, int GC>
+template <bool PACKED, int TAB, bool CLAMP, int GC>
 __device__ __forceinline__ void slice_pack(const uint4* q, int G, unsigned dmax, const EncTab& tab, unsigned* wp,
                                            unsigned nb, unsigned long long& acc_out, unsigned& nb_out,
                                            unsigned*& wp_out) {
@@ -1160,7 +1209,7 @@ __device__ __forceinline__ void slice_pack(const uint4* q, int G, unsigned dmax,
     if ((i >> 3) < (GC ? GC : G)) {
       const unsigned s = CLAMP ? min(sym_of(q, i), dmax) : sym_of(q, i);
       unsigned c, L;
-      code_of<PACKED, WIN>(tab, s, c, L);
+      code_of<PACKED, TAB>(tab, s, c, L);
       if (PACKED) {
         hi = __funnelshift_l(lo, hi, L);
         lo = (lo << L) | c;
@@ -1182,22 +1231,23 @@ __device__ __forceinline__ void slice_pack(const uint4* q, int G, unsigned dmax,
 }
 
 // One of the four instantiations of a slice function, picked at run time
-// (packed codes, full default-size slices); WIN is the kernel's.
+// (packed codes, full default-size slices); TAB is the kernel's.
 #define BM_ENC_DISPATCH(FN, ...)                                                        \
   do {                                                                                  \
     if (G == kEncGroups) {                                                              \
-      if (packed) FN<true, WIN, CLAMP, kEncGroups>(__VA_ARGS__);                         \
-      else FN<false, WIN, CLAMP, kEncGroups>(__VA_ARGS__);                               \
+      if (packed) FN<true, TAB, CLAMP, kEncGroups>(__VA_ARGS__);                         \
+      else FN<false, TAB, CLAMP, kEncGroups>(__VA_ARGS__);                               \
     } else {                                                                            \
-      if (packed) FN<true, WIN, CLAMP, 0>(__VA_ARGS__);                                  \
-      else FN<false, WIN, CLAMP, 0>(__VA_ARGS__);                                        \
+      if (packed) FN<true, TAB, CLAMP, 0>(__VA_ARGS__);                                  \
+      else FN<false, TAB, CLAMP, 0>(__VA_ARGS__);                                        \
     }                                                                                   \
   } while (0)
 
-// Two instantiations per symbol source: WIN = false when every symbol met
-// lies in the shared-memory window, WIN = true (the GLOB table) otherwise.
+// Three instantiations per symbol source: TAB = 0 when every symbol met lies
+// in the shared-memory window, 1 when the window serves most of them and the
+// global table the rest, 2 (the global table only) otherwise.
 // For the compressor's own symbols (CLAMP = false) the codebook decided
-// (sc->enc_full) and both are launched, the one that does not match returning
+// (sc->enc_mode) and all three are launched, the ones that do not match returning
 // at once; for caller-supplied symbols the host picks by dictionary size.
 // Warps take chunks in ticket order.  A warp codes its chunk's bit count from
 // the symbols it holds in registers, publishes the chunk's (words, escapes)
@@ -1206,18 +1256,18 @@ __device__ __forceinline__ void slice_pack(const uint4* q, int G, unsigned dmax,
 // packs its codes at the now known word offset.  Each lane stores its full
 // words; a word shared by two lanes is completed by an atomic OR of the
 // earlier lane's last bits.
-template <int WARPS, bool CLAMP, bool WIN>
+template <int WARPS, bool CLAMP, int TAB>
 __global__ void __launch_bounds__(WARPS * 32, 4) encode_fused_kernel(FusedEncodeArgs a) {
   extern __shared__ __align__(16) unsigned char enc_smem_raw[];
-  constexpr int WN = WIN ? 0 : kEncWin;
+  constexpr int WN = TAB == 2 ? 0 : kEncWin;
   unsigned* codes = reinterpret_cast<unsigned*>(enc_smem_raw);           // [WN]
   uint8_t* lens = enc_smem_raw + 4 * WN;                                  // [WN]
   Scalars* sc = a.sc;
   if (sc->skip) return;  // the stream is already known to be a raw copy
-  if (!CLAMP && WIN == (sc->enc_full != 0)) return;
+  if (!CLAMP && (unsigned)TAB != sc->enc_mode) return;
   // codes of at most 26 bits are packed with their length into one word
   // (code | len << 26): one shared-memory lookup per symbol in the window
-  const bool packed = sc->max_len <= 26 && (!WIN || a.packed != nullptr);
+  const bool packed = sc->max_len <= 26 && (TAB != 2 || a.packed != nullptr);
   const unsigned wlo = sc->enc_lo;
   for (int i = threadIdx.x; i < WN; i += blockDim.x) {
     const unsigned s = wlo + (unsigned)i;
@@ -1261,14 +1311,14 @@ __global__ void __launch_bounds__(WARPS * 32, 4) encode_fused_kernel(FusedEncode
       const uint4* p = reinterpret_cast<const uint4*>(a.sym + s0);
 #pragma unroll
       for (int g = 0; g < kEncGroups; ++g)
-        q[g] = g < G ? (WIN ? ld_stream(p + g) : __ldg(p + g)) : make_uint4(0, 0, 0, 0);
+        q[g] = g < G ? (TAB == 2 ? ld_stream(p + g) : __ldg(p + g)) : make_uint4(0, 0, 0, 0);
       // G is 8 at the default chunk of 2048 symbols: a fully unrolled slice
       BM_ENC_DISPATCH(slice_bits, q, G, dmax, tab, bits, emask);
       nesc = __popcll(emask);
     } else {
       for (int t = 0; t < cnt; ++t) {
         const unsigned s = CLAMP ? min((unsigned)a.sym[s0 + t], dmax) : (unsigned)a.sym[s0 + t];
-        bits += len_of<false, WIN>(tab, s);
+        bits += len_of<false, TAB>(tab, s);
         nesc += s == 0;
       }
     }
@@ -1407,8 +1457,8 @@ __global__ void __launch_bounds__(WARPS * 32, 4) encode_fused_kernel(FusedEncode
       for (int t = 0; t < cnt; ++t) {
         const unsigned s = CLAMP ? min((unsigned)a.sym[s0 + t], dmax) : (unsigned)a.sym[s0 + t];
         unsigned c, L;
-        if (packed) code_of<true, WIN>(tab, s, c, L);
-        else code_of<false, WIN>(tab, s, c, L);
+        if (packed) code_of<true, TAB>(tab, s, c, L);
+        else code_of<false, TAB>(tab, s, c, L);
         acc = (acc << L) | c;
         nb += L;
         if (nb >= 32u) {
