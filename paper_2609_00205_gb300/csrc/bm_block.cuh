@@ -183,7 +183,7 @@ __device__ __forceinline__ void hist_count(unsigned* hloc, unsigned* hglob, int 
 template <typename T, int N, int MODE>
 __device__ __forceinline__ void level_fwd(T* X, T* __restrict__ T1, T* __restrict__ out, const int lvl_off, const T rq,
                                           uint16_t* stage, int32_t* __restrict__ esc_blk, T* __restrict__ coef_blk,
-                                          bool& ovf) {
+                                          bool& ovf, const bool full) {
   constexpr int C = (N + 1) / 2;
   const auto& tb = block_tab<T, N>();
   for (int L = threadIdx.x; L < N * N; L += blockDim.x) {
@@ -216,7 +216,10 @@ __device__ __forceinline__ void level_fwd(T* X, T* __restrict__ T1, T* __restric
       // the quantisation codes staged in the block's order as code + 2^15 - 1
       // (store_codes turns them into symbols and escapes when the block is
       // done); a code outside [-(2^15 - 1), 2^15 - 1] is staged as 0xFFFF and
-      // goes to the escape array at once (a predicated store, rare)
+      // goes to the escape array at once (a predicated store).  With the full
+      // dictionary (`full`: radius 2^15) those wide codes are exactly the
+      // escapes, so the staged value is the symbol itself: code + 2^15, or 0
+      const unsigned sadd = full ? 1u : 0u, swide = full ? 0u : kStageWide;
 #pragma unroll
       for (int k = 0; k < N; ++k) {
         if ((k & 1) || !cc) {
@@ -224,7 +227,7 @@ __device__ __forceinline__ void level_fwd(T* X, T* __restrict__ T1, T* __restric
           const int code = quantize(d[k], rq, ovf);
           const unsigned b = (unsigned)(code + kStageBias);
           const bool wide = b >= kStageWide;
-          stage[pos] = (uint16_t)(wide ? kStageWide : b);
+          stage[pos] = (uint16_t)(wide ? swide : b + sadd);
           if (wide) esc_blk[pos] = code;
         }
       }
@@ -277,10 +280,10 @@ struct LevelBufs {
 template <typename T, int N, int L, int K, int B, int MODE>
 struct FwdLevels {
   __device__ __forceinline__ static void run(const LevelBufs<T>& bufs, T* T1, const T* rq, uint16_t* stage,
-                                             int32_t* esc_blk, T* coef_blk, bool& ovf) {
-    level_fwd<T, N, MODE>(bufs(L), T1, bufs(L + 1), lvl_offset(B, L), rq[L], stage, esc_blk, coef_blk, ovf);
+                                             int32_t* esc_blk, T* coef_blk, bool& ovf, const bool full) {
+    level_fwd<T, N, MODE>(bufs(L), T1, bufs(L + 1), lvl_offset(B, L), rq[L], stage, esc_blk, coef_blk, ovf, full);
     if constexpr (L + 1 < K)
-      FwdLevels<T, (N + 1) / 2, L + 1, K, B, MODE>::run(bufs, T1, rq, stage, esc_blk, coef_blk, ovf);
+      FwdLevels<T, (N + 1) / 2, L + 1, K, B, MODE>::run(bufs, T1, rq, stage, esc_blk, coef_blk, ovf, full);
   }
 };
 
@@ -516,6 +519,20 @@ __device__ __forceinline__ void store_codes(uint16_t* __restrict__ sym, int32_t*
   }
 }
 
+// A block's staged symbols (full dictionary: escapes are already in the
+// escape array) to global memory: 8-byte vectors when the block's first
+// symbol is 8-byte aligned.
+template <int PB>
+__device__ __forceinline__ void copy_symbols(uint16_t* __restrict__ sym, const uint16_t* __restrict__ st) {
+  if (PB % 4 == 0 && (reinterpret_cast<uintptr_t>(sym) & 7) == 0) {
+    const uint2* s2 = reinterpret_cast<const uint2*>(st);
+    uint2* d2 = reinterpret_cast<uint2*>(sym);
+    for (int i = threadIdx.x; i < PB / 4; i += blockDim.x) d2[i] = s2[i];
+  } else {
+    for (int i = threadIdx.x; i < PB; i += blockDim.x) sym[i] = st[i];
+  }
+}
+
 // Shared memory of the forward kernels.
 template <typename T, int B, int K>
 struct FwdSmem {
@@ -586,8 +603,9 @@ __device__ __forceinline__ bool fwd_block(const BlockArgs<T>& a, int64_t b, cons
   for (int l = 0; l < K; ++l) rq[l] = MODE == 0 ? __ldcg(a.rq + tier * K + l) : T(0);
   const int64_t sbase = b * (int64_t)Cfg::PB;
   const LevelBufs<T> bufs{S.A, S.cb0, S.cb1};
+  const bool full = MODE == 0 && a.radius == (1 << 15) && !BM_FWD_HIST;
   FwdLevels<T, B, 0, K, B, MODE>::run(bufs, S.T1, rq, S.stage, a.esc + (MODE == 0 ? sbase : 0),
-                                      a.coef + (MODE == 1 ? sbase : 0), ovf);
+                                      a.coef + (MODE == 1 ? sbase : 0), ovf, full);
   {  // block coarse values -> gathered grid G
     constexpr int M = Cfg::M;
     const T* cf = bufs(K);
@@ -597,7 +615,10 @@ __device__ __forceinline__ bool fwd_block(const BlockArgs<T>& a, int64_t b, cons
       g[((int64_t)j0 * a.g1 + j1) * a.g2 + j2] = cf[e];
     }
   }
-  if (MODE == 0) store_codes<Cfg::PB>(a.sym + sbase, a.esc + sbase, S.stage, a.radius, S.hloc, a.hist, centre);
+  if (MODE == 0) {
+    if (full) copy_symbols<Cfg::PB>(a.sym + sbase, S.stage);
+    else store_codes<Cfg::PB>(a.sym + sbase, a.esc + sbase, S.stage, a.radius, S.hloc, a.hist, centre);
+  }
   if (Cfg::BULK) fence_proxy_async_smem();  // the next block's bulk copies overwrite what was read here
   __syncthreads();
   return true;
