@@ -219,7 +219,13 @@ __device__ __forceinline__ void level_fwd(T* X, T* __restrict__ T1, T* __restric
       // goes to the escape array at once (a predicated store).  With the full
       // dictionary (`full`: radius 2^15) those wide codes are exactly the
       // escapes, so the staged value is the symbol itself: code + 2^15, or 0
+      // A line with a wide code writes every code of the line to the escape
+      // array (entries at other positions are never read): the lines of a
+      // warp are consecutive positions, so its stores fill whole sectors
+      // instead of leaving partly written ones to be merged from DRAM.
       const unsigned sadd = full ? 1u : 0u, swide = full ? 0u : kStageWide;
+      int codes[N];
+      bool anyw = false;
 #pragma unroll
       for (int k = 0; k < N; ++k) {
         if ((k & 1) || !cc) {
@@ -228,8 +234,14 @@ __device__ __forceinline__ void level_fwd(T* X, T* __restrict__ T1, T* __restric
           const unsigned b = (unsigned)(code + kStageBias);
           const bool wide = b >= kStageWide;
           stage[pos] = (uint16_t)(wide ? swide : b + sadd);
-          if (wide) esc_blk[pos] = code;
+          codes[k] = code;
+          anyw |= wide;
         }
+      }
+      if (anyw) {
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+          if ((k & 1) || !cc) esc_blk[base + (cc ? k / 2 : k)] = codes[k];
       }
     } else {
 #pragma unroll
