@@ -514,13 +514,26 @@ __device__ void codebook_lengths(const CodebookArgs& a, CbArrays<IdT> V, int n, 
     if (threadIdx.x == 0) s_maxk = 0;
     __syncthreads();
     unsigned mk = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const unsigned f = a.hist[V.csym[i]];
-      const unsigned fs = shift ? max(1u, f >> shift) : f;
-      V.ka[i] = fs;
-      V.sa[i] = (uint16_t)i;
-      V.clen[i] = 0;
-      mk = max(mk, fs);
+    for (int i0 = threadIdx.x; i0 < n; i0 += 8 * blockDim.x) {  // eight loads in flight
+      unsigned sy[8], f[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int i = i0 + t * (int)blockDim.x;
+        sy[t] = i < n ? (unsigned)V.csym[i] : 0u;
+      }
+#pragma unroll
+      for (int t = 0; t < 8; ++t) f[t] = i0 + t * (int)blockDim.x < n ? a.hist[sy[t]] : 0u;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int i = i0 + t * (int)blockDim.x;
+        if (i < n) {
+          const unsigned fs = shift ? max(1u, f[t] >> shift) : f[t];
+          V.ka[i] = fs;
+          V.sa[i] = (uint16_t)i;
+          V.clen[i] = 0;
+          mk = max(mk, fs);
+        }
+      }
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) mk = max(mk, __shfl_xor_sync(0xffffffffu, mk, o));
@@ -643,10 +656,22 @@ __device__ void codebook_lengths(const CodebookArgs& a, CbArrays<IdT> V, int n, 
       __syncthreads();
     }
     unsigned md = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const unsigned d = V.depth[V.parent[i]] + 1u;
-      V.clen[ls[i]] = (uint8_t)min(d, 255u);
-      md = max(md, d);
+    for (int i0 = threadIdx.x; i0 < n; i0 += 8 * blockDim.x) {  // eight loads in flight
+      unsigned pa[8], li[8], dd[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int i = i0 + t * (int)blockDim.x;
+        pa[t] = i < n ? (unsigned)V.parent[i] : 0u;
+        li[t] = i < n ? (unsigned)ls[i] : 0u;
+      }
+#pragma unroll
+      for (int t = 0; t < 8; ++t) dd[t] = i0 + t * (int)blockDim.x < n ? (unsigned)V.depth[pa[t]] + 1u : 0u;
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+        if (i0 + t * (int)blockDim.x < n) {
+          V.clen[li[t]] = (uint8_t)min(dd[t], 255u);
+          md = max(md, dd[t]);
+        }
     }
     if (md) atomicMax(&s_maxd, md);
     __syncthreads();
@@ -665,15 +690,31 @@ __device__ void codebook_emit(const CodebookArgs& a, CbArrays<IdT> V, int n, uns
   // 4. canonical codes (the counting pass in the sort counts' shared memory)
   build_canonical(V.clen, n, V.wcnt, V.canon, ct);
   const bool pk = a.packed && ct->max_len <= 26;
-  for (int i = threadIdx.x; i < (int)ct->n; i += blockDim.x) {
-    const int ci = V.canon[i];
-    const unsigned L = V.clen[ci];
-    const unsigned c = ct->first_code[L] + (unsigned)(i - (int)ct->first_pos[L]);
-    const unsigned sy = V.csym[ci];
-    a.codes[sy] = c;
-    if (pk) a.packed[sy] = c | (L << 26);
+  const int nc = (int)ct->n;
+  for (int i0 = threadIdx.x; i0 < nc; i0 += 8 * blockDim.x) {  // eight loads in flight
+    unsigned ci[8], L[8], sy[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int i = i0 + t * (int)blockDim.x;
+      ci[t] = i < nc ? (unsigned)V.canon[i] : 0u;
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const bool ok = i0 + t * (int)blockDim.x < nc;
+      L[t] = ok ? (unsigned)V.clen[ci[t]] : 0u;
+      sy[t] = ok ? (unsigned)V.csym[ci[t]] : 0u;
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int i = i0 + t * (int)blockDim.x;
+      if (i < nc) {
+        const unsigned c = ct->first_code[L[t]] + (unsigned)(i - (int)ct->first_pos[L[t]]);
+        a.codes[sy[t]] = c;
+        if (pk) a.packed[sy[t]] = c | (L[t] << 26);
+        a.lens[sy[t]] = (uint8_t)L[t];
+      }
+    }
   }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) a.lens[V.csym[i]] = V.clen[i];
   // 5. codebook runs {u32 first, u32 count, u8 len[count], pad to 4}: a run
   // starts at every present symbol whose predecessor is absent.  Warp w walks
   // its contiguous rows of 32 compact indices (coalesced loads): run starts
@@ -684,20 +725,41 @@ __device__ void codebook_emit(const CodebookArgs& a, CbArrays<IdT> V, int n, uns
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int rows = (n + 31) / 32, rpw = (rows + nwarps - 1) / nwarps;
   const int r0 = wid * rpw, r1 = min(rows, r0 + rpw);
-  auto start_mask = [&](int r) {
-    const int i = r * 32 + lane;
-    const bool st = i < n && (i == 0 || V.csym[i] != V.csym[i - 1] + 1);
-    return __ballot_sync(0xffffffffu, st);
+  // run-start masks of eight rows at once (sixteen loads in flight)
+  auto start_masks = [&](int r, unsigned (&m)[8]) {
+    unsigned c[8], p[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int i = (r + t) * 32 + lane;
+      const bool ok = r + t < r1 && i < n;
+      c[t] = ok ? (unsigned)V.csym[i] : 0u;
+      p[t] = ok && i > 0 ? (unsigned)V.csym[i - 1] : 0u;
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int i = (r + t) * 32 + lane;
+      m[t] = __ballot_sync(0xffffffffu, r + t < r1 && i < n && (i == 0 || c[t] != p[t] + 1u));
+    }
   };
   unsigned nst = 0;
-  for (int r = r0; r < r1; ++r) nst += (unsigned)__popc(start_mask(r));
+  for (int r = r0; r < r1; r += 8) {
+    unsigned m[8];
+    start_masks(r, m);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) nst += (unsigned)__popc(m[t]);
+  }
   const unsigned rbase = warp_excl_scan_block(nst, scan_tmp, &s_nruns);
   {
     unsigned q = rbase;
-    for (int r = r0; r < r1; ++r) {
-      const unsigned m = start_mask(r);
-      if ((m >> lane) & 1u) run_start[q + (unsigned)__popc(m & ((1u << lane) - 1u))] = (unsigned)(r * 32 + lane);
-      q += (unsigned)__popc(m);
+    for (int r = r0; r < r1; r += 8) {
+      unsigned m[8];
+      start_masks(r, m);
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        if ((m[t] >> lane) & 1u)
+          run_start[q + (unsigned)__popc(m[t] & ((1u << lane) - 1u))] = (unsigned)((r + t) * 32 + lane);
+        q += (unsigned)__popc(m[t]);
+      }
     }
   }
   __syncthreads();
@@ -727,14 +789,27 @@ __device__ void codebook_emit(const CodebookArgs& a, CbArrays<IdT> V, int n, uns
     // length bytes: compact index i of run q goes to run_off[q] + 8 + (i -
     // run_start[q]), q = (run starts up to i) - 1, from the same row walk
     unsigned q = rbase;
-    for (int r = r0; r < r1; ++r) {
-      const unsigned m = start_mask(r);
-      const int i = r * 32 + lane;
-      if (i < n) {
-        const unsigned qi = q + (unsigned)__popc(m & ((2u << lane) - 1u)) - 1u;
-        a.out[a.off + run_off[qi] + 8 + (i - run_start[qi])] = V.clen[i];
+    for (int r = r0; r < r1; r += 8) {
+      unsigned m[8], qi[8], ro[8], rs[8], cl[8];
+      start_masks(r, m);
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        qi[t] = q + (unsigned)__popc(m[t] & ((2u << lane) - 1u)) - 1u;
+        q += (unsigned)__popc(m[t]);
       }
-      q += (unsigned)__popc(m);
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int i = (r + t) * 32 + lane;
+        const bool ok = r + t < r1 && i < n;
+        ro[t] = ok ? run_off[qi[t]] : 0u;
+        rs[t] = ok ? run_start[qi[t]] : 0u;
+        cl[t] = ok ? (unsigned)V.clen[i] : 0u;
+      }
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int i = (r + t) * 32 + lane;
+        if (r + t < r1 && i < n) a.out[a.off + ro[t] + 8 + (i - rs[t])] = (uint8_t)cl[t];
+      }
     }
     if (threadIdx.x == 0)
       for (unsigned long long t = total; t < pad8(total); ++t) a.out[a.off + t] = 0;
@@ -747,12 +822,23 @@ __device__ void codebook_emit(const CodebookArgs& a, CbArrays<IdT> V, int n, uns
   const unsigned wlo_c =
       a.dict <= kEncWin ? 0u : (unsigned)min(max(a.dict / 2 - kEncWin / 2, 0), a.dict - kEncWin);
   unsigned long long my_bits = 0, my_all = 0, my_win = 0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const unsigned sy = V.csym[i];
-    const unsigned long long f = a.hist[sy];
-    my_bits += f * V.clen[i];
-    my_all += f;
-    if (sy - wlo_c < (unsigned)kEncWin || sy == 0u) my_win += f;
+  for (int i0 = threadIdx.x; i0 < n; i0 += 8 * blockDim.x) {  // eight loads in flight
+    unsigned sy[8], cl[8], f[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int i = i0 + t * (int)blockDim.x;
+      sy[t] = i < n ? (unsigned)V.csym[i] : 0u;
+      cl[t] = i < n ? (unsigned)V.clen[i] : 0u;
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) f[t] = i0 + t * (int)blockDim.x < n ? a.hist[sy[t]] : 0u;
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+      if (i0 + t * (int)blockDim.x < n) {
+        my_bits += (unsigned long long)f[t] * cl[t];
+        my_all += f[t];
+        if (sy[t] - wlo_c < (unsigned)kEncWin || sy[t] == 0u) my_win += f[t];
+      }
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
