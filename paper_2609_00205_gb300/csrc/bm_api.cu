@@ -34,6 +34,16 @@
 #ifndef BM_BATCH_GRAPHS
 #define BM_BATCH_GRAPHS 1
 #endif
+// Percentage of the SMs the block symbols' wide-window histogram takes (the
+// rest run the global levels beside it: one of its CTAs holds most of an SM's
+// shared memory, so on every SM it takes, the global levels' kernels wait).
+// On GB300 at 513^3 a compress call took 1.276 / 1.526 / 2.384 / 2.848 ms
+// (1e-2 .. 1e-5) with 66 against 1.335 / 1.577 / 2.432 / 2.934 with 100,
+// 1.316 / 1.556 / 2.419 / 2.932 with 50 and 1.320 / 1.560 / 2.426 / 2.883
+// with 80.
+#ifndef BM_HIST_WIDE_PCT
+#define BM_HIST_WIDE_PCT 66
+#endif
 #ifndef BM_HIST_OVERLAP
 #define BM_HIST_OVERLAP 1
 #endif
@@ -1593,7 +1603,10 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     {
       Stage st("histogram", hs);
       const unsigned long long nloc = (unsigned long long)h.sym_off[0];  // the symbols of every round
-      BM_CUDA(launch_hist(sym, 0, nloc, dict, (unsigned)prm.radius, hist, sc, false, num_sms() * BM_HIST_CTAS, hs));
+      // the wide-window kernel holds most of an SM's shared memory: a share of
+      // the SMs is left to the global levels running beside it
+      const int hctas = dict > kHistWin ? std::max(1, num_sms() * BM_HIST_WIDE_PCT / 100) : num_sms() * BM_HIST_CTAS;
+      BM_CUDA(launch_hist(sym, 0, nloc, dict, (unsigned)prm.radius, hist, sc, false, hctas, hs));
     }
     if (overlap) BM_CUDA(cudaEventRecord(ws->ev_join, ws->aux));
     return BM_OK;
