@@ -579,6 +579,23 @@ def run_diff257(args):
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / args.steps
     peak = torch.cuda.max_memory_allocated(dev) - base
+    # the same loss on a leaf tensor of the field's shape (no decomposition):
+    # its autograd graph alone, for comparison with the peak above
+    x0 = u.clone()
+
+    def loss_only():
+        x = x0.clone().requires_grad_(True)
+        loss = ((x - target) ** 2).sum() + 0.1 * sum((torch.diff(x, dim=d) ** 2).sum() for d in range(3))
+        loss.backward()
+        return x.grad
+
+    loss_only()
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats(dev)
+    base2 = torch.cuda.memory_allocated(dev)
+    loss_only()
+    torch.cuda.synchronize()
+    loss_peak = torch.cuda.max_memory_allocated(dev) - base2
     # the operator pair alone: recompose + its adjoint
     gx = torch.randn(shape, generator=g).to(dev)
     a.record()
@@ -590,7 +607,11 @@ def run_diff257(args):
     op_ms = a.elapsed_time(b) / args.steps
     line = {"metric": "differentiable recompose, forward + backward ms (257^3 FP32)", "workload": "diff257",
             "value": ms, "unit": "ms", "higher_is_better": False, "recompose_plus_adjoint_ms": op_ms,
-            "peak_extra_bytes": peak, "field_bytes": u.numel() * 4, "steps": args.steps, "warmup": args.warmup,
+            "peak_extra_bytes": peak, "loss_only_peak_extra_bytes": loss_peak, "field_bytes": u.numel() * 4,
+            "coeff_bytes": c0.numel() * 4, "steps": args.steps, "warmup": args.warmup,
+            "peak_note": "torch allocations of the step; the library's operators save nothing for backward, and "
+                         "the peak is the loss's own autograd tensors (loss_only_peak_extra_bytes, the same loss "
+                         "on a leaf tensor) plus the coefficient tensor and its gradient",
             "params": PARAMS, "data": "synthetic",
             "saved_for_backward": "nothing (linear operators: the adjoint needs only the incoming gradient)"}
     print(json.dumps(line))
