@@ -541,6 +541,14 @@ def batch64_measure(dev, steps, warmup):
 
 
 def run_diff257(args):
+    """The differentiable workload alone, as its own JSON line."""
+    import torch
+
+    torch.cuda.set_device(0)
+    print(json.dumps(diff257_measure(torch.device("cuda", 0), args.steps, args.warmup)))
+
+
+def diff257_measure(dev, steps, warmup):
     """Differentiable recomposition on a 257^3 FP32 GRF: loss =
     ||recompose(c) - target||^2 + 0.1 ||grad_x recompose(c)||^2, forward and
     backward timed with CUDA events; the operators are linear, so their
@@ -550,8 +558,6 @@ def run_diff257(args):
     import fields
     import paper_2609_00205_gb300 as bm
 
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
     bm.load()
     shape = (257, 257, 257)
     u = fields.power_law_grf(shape, seed=7, dtype=torch.float32, device=dev).contiguous()
@@ -566,18 +572,18 @@ def run_diff257(args):
         loss.backward()
         return c.grad
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     torch.cuda.reset_peak_memory_stats(dev)
     base = torch.cuda.memory_allocated(dev)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
     b.record()
     torch.cuda.synchronize()
-    ms = a.elapsed_time(b) / args.steps
+    ms = a.elapsed_time(b) / steps
     peak = torch.cuda.max_memory_allocated(dev) - base
     # the same loss on a leaf tensor of the field's shape (no decomposition):
     # its autograd graph alone, for comparison with the peak above
@@ -599,22 +605,22 @@ def run_diff257(args):
     # the operator pair alone: recompose + its adjoint
     gx = torch.randn(shape, generator=g).to(dev)
     a.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         bm.recompose(c0, shape, **PARAMS)
         bm.recompose_adjoint(gx, **PARAMS)
     b.record()
     torch.cuda.synchronize()
-    op_ms = a.elapsed_time(b) / args.steps
+    op_ms = a.elapsed_time(b) / steps
     line = {"metric": "differentiable recompose, forward + backward ms (257^3 FP32)", "workload": "diff257",
             "value": ms, "unit": "ms", "higher_is_better": False, "recompose_plus_adjoint_ms": op_ms,
             "peak_extra_bytes": peak, "loss_only_peak_extra_bytes": loss_peak, "field_bytes": u.numel() * 4,
-            "coeff_bytes": c0.numel() * 4, "steps": args.steps, "warmup": args.warmup,
+            "coeff_bytes": c0.numel() * 4, "steps": steps, "warmup": warmup,
             "peak_note": "torch allocations of the step; the library's operators save nothing for backward, and "
                          "the peak is the loss's own autograd tensors (loss_only_peak_extra_bytes, the same loss "
                          "on a leaf tensor) plus the coefficient tensor and its gradient",
             "params": PARAMS, "data": "synthetic",
             "saved_for_backward": "nothing (linear operators: the adjoint needs only the incoming gradient)"}
-    print(json.dumps(line))
+    return line
 
 
 def region_errors(d, u, block_mask, block):
@@ -718,14 +724,20 @@ def run_roi385(args):
 
 
 def run_model(args):
+    """The performance-model workload alone, as its own JSON line."""
+    import torch
+
+    torch.cuda.set_device(0)
+    print(json.dumps(model_measure()))
+
+
+def model_measure():
     """Fit the performance model (Eq. 1 for the In-cache Block stage) on this
     GPU for both dtypes, report the knee (90 % of the saturated throughput)
     and Alg. 1's choice for the 513^3 workload under a few time budgets."""
+    import paper_2609_00205_gb300 as bm
     import torch
 
-    import paper_2609_00205_gb300 as bm
-
-    torch.cuda.set_device(0)
     bm.load()
     out = {"metric": "performance model (Eq. 1) and Alg. 1 selection", "workload": "model", "data": "synthetic"}
     for name, dt in (("f32", torch.float32), ("f64", torch.float64)):
@@ -742,7 +754,7 @@ def run_model(args):
                 sel[str(budget)] = {"error": str(e)}
         d["alg1_513"] = sel
         out[name] = d
-    print(json.dumps(out))
+    return out
 
 
 def main():
@@ -756,6 +768,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-roi", action="store_true", help="skip the FP64 ROI workload in the main line")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-field batched workload in the main line")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the differentiable and performance-model workloads in the main line")
     ap.add_argument("--edge", type=int, default=513, help="field edge (513 = the workload; smaller for profiling)")
     ap.add_argument("--quick", action="store_true", help="compress steps only (profiling runs)")
     ap.add_argument("--workload", default="grf513", choices=["grf513", "batch64", "diff257", "model", "roi385"])
@@ -1012,6 +1026,16 @@ def main():
             b64 = batch64_measure(dev, 10, max(2, args.warmup))
         except Exception as e:  # a reporting extra: never lose the bench line over it
             b64 = {"error": str(e)}
+    diff = model = None
+    if not args.no_extras and not args.quick:
+        try:
+            diff = diff257_measure(dev, 10, 3)
+        except Exception as e:  # a reporting extra: never lose the bench line over it
+            diff = {"error": str(e)}
+        try:
+            model = model_measure()
+        except Exception as e:
+            model = {"error": str(e)}
 
     if rank == 0:
         line = {
@@ -1034,6 +1058,8 @@ def main():
             "decompress_roofline": dec_roof,
             "roi385": roi,
             "batch64": b64,
+            "diff257": diff,
+            "model": model,
             "stage_ms": stage_avg,
             "e2e": e2e,
             "gpu_launches": launches,
