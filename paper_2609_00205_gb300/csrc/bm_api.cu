@@ -521,7 +521,7 @@ Reblock reblock_of(const PlanHost& h, bool coarse) {
 }
 
 // cudaFuncAttributeMaxDynamicSharedMemorySize set once per device for a kernel.
-std::atomic<unsigned> g_cb_attr{0}, g_dt_attr{0}, g_dec_attr{0}, g_encw_attr{0}, g_encc_attr{0};
+std::atomic<unsigned> g_cb_attr{0}, g_dt_attr{0}, g_dec_attr{0}, g_encw_attr{0}, g_encc_attr{0}, g_cbb_attr{0};
 template <class F>
 cudaError_t set_smem_once(F* fn, int bytes, std::atomic<unsigned>& done) {
   int dev = 0;
@@ -1383,7 +1383,7 @@ struct Spans {
 // whose in-cache levels run in the batched forward kernel) a size query, the
 // part before the block stage (recording the kernel's arguments) and the
 // part after it.
-enum BatchPhase { kWhole = 0, kQuery = 1, kPrepare = 2, kFinish = 3 };
+enum BatchPhase { kWhole = 0, kQuery = 1, kPrepare = 2, kFinishA = 3, kFinishB = 4 };
 
 struct BatchSlot {
   unsigned char* h = nullptr;  // Scalars at 0, tiers at 256, block tiers at 256 + 8*256
@@ -1391,14 +1391,16 @@ struct BatchSlot {
   bool raw_now = false;        // the raw copy was chosen on the host
   unsigned long long raw_total = 0;
   int phase = kWhole;
-  std::vector<double> tiers;         // kPrepare -> kFinish: the item's tolerance tiers
+  std::vector<double> tiers;         // kPrepare -> kFinishB: the item's tolerance tiers
   std::vector<uint8_t> btier;        // and block tiers
   bool batched = false;              // kQuery: the item can take the batched kernel
   size_t need = 0;                   // kQuery: device scratch of the item
-  unsigned char* scratch = nullptr;  // kPrepare / kFinish: the item's own scratch
+  unsigned char* scratch = nullptr;  // kPrepare .. kFinishB: the item's own scratch
   BlockArgs<float> af{};             // kPrepare: recorded block arguments (FP32 / FP64)
   BlockArgs<double> ad{};
   QtabArgs qa{};                     // kPrepare: recorded quantiser-table arguments
+  CodebookArgs cb{};                 // kFinishA: recorded codebook arguments (the batch builds them at once)
+  bool cb_ready = false;
 };
 
 bm_status compress_result(const Scalars* hsc, unsigned long long raw_total, size_t* out_bytes) {
@@ -1500,7 +1502,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     carve_all(cv, reinterpret_cast<unsigned char*>(ws->d));
   } else {
     carve_all(cv, bs->scratch);
-    if (phase == kFinish && bs->raw_now) return BM_OK;
+    if ((phase == kFinishA || phase == kFinishB) && bs->raw_now) return BM_OK;
   }
   Scalars* sc = cv.take<Scalars>(1);
   unsigned* hist = cv.take<unsigned>(dict);
@@ -1528,7 +1530,8 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
   if (ntiers > 1) std::memcpy(hbt, btier.data(), btier.size());
 
   const bool prefix_fits = L.off_codebook <= cap;
-  if (phase != kFinish) {
+  const bool after_block = phase == kFinishA || phase == kFinishB;
+  if (!after_block) {
     Stage st("setup");
     // zeroed scalars, histogram, stream prefix and encoder tickets; the tier
     // tables read from the pinned staging buffer
@@ -1551,7 +1554,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     BM_CUDA(sp.launch(s));
   }
   const int mgrid = (int)std::min<int64_t>((int64_t)num_sms() * BM_MAXABS_CTAS, std::max<int64_t>(1, (nel + 4095) / 4096));
-  if (phase != kFinish) {
+  if (!after_block) {
     Stage st("maxabs");
     QtabArgs qa{};
     qa.enabled = prefix_fits;
@@ -1570,7 +1573,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
       BM_CUDA(cudaGetLastError());
     }
   }
-  if (!prefix_fits && phase != kFinish) {  // not even the tables fit: the raw copy is the stream
+  if (!prefix_fits && !after_block) {  // not even the tables fit: the raw copy is the stream
     raw_header_kernel<<<1, 32, 0, s>>>(out, f64, h.B, shape[0], shape[1], shape[2], rel, tol, raw_total, sc, prm.ndim);
     BM_LAUNCHED();
     BM_CUDA(cudaMemcpyAsync(out + kHeaderBytes, field, (size_t)nel * sizeof(T), cudaMemcpyDeviceToDevice, s));
@@ -1615,9 +1618,9 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     BlockArgs<T>* rec = reinterpret_cast<BlockArgs<T>*>(f64 ? (void*)&bs->ad : (void*)&bs->af);
     return run_decompose<T>(*P, field, 0, fo, cv, s, nullptr, Incache::Record, rec);
   }
-  {
+  if (phase != kFinishB) {
     const bm_status st = run_decompose<T>(*P, field, 0, fo, cv, s, block_hist,
-                                          phase == kFinish ? Incache::Skip : Incache::Run);
+                                          phase == kFinishA ? Incache::Skip : Incache::Run);
     // join the second stream before anything else (also on errors: no work
     // of this call may outlive it)
     if (phase == kWhole && !BM_FWD_HIST && BM_HIST_OVERLAP && ws->aux) BM_CUDA(cudaStreamWaitEvent(s, ws->ev_join, 0));
@@ -1627,10 +1630,17 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     Stage st("huffman_codebook");
     CodebookArgs ca{hist, dict, lens, codes, prefix_fits ? out : nullptr, L.off_codebook, cap, sc, 1, L.nch,
                     raw_total, cb_big, packed};
-    BM_CUDA(set_smem_once(codebook_kernel, (int)sizeof(CbSmem), g_cb_attr));
-    codebook_kernel<<<1, kCbThreads, sizeof(CbSmem), s>>>(ca);
-    BM_LAUNCHED();
-    BM_CUDA(cudaGetLastError());
+    if (phase == kFinishA) {  // the batch builds every item's codebook in one launch
+      bs->cb = ca;
+      bs->cb_ready = true;
+      return BM_OK;
+    }
+    if (phase != kFinishB) {
+      BM_CUDA(set_smem_once(codebook_kernel, (int)sizeof(CbSmem), g_cb_attr));
+      codebook_kernel<<<1, kCbThreads, sizeof(CbSmem), s>>>(ca);
+      BM_LAUNCHED();
+      BM_CUDA(cudaGetLastError());
+    }
   }
   {
     Stage st("huffman_encode");
@@ -2353,6 +2363,8 @@ bm_status bm_compress_batch(int n, const bm_batch_item* items, size_t* out_bytes
   }
   const size_t hdesc = hb;  // then the batched kernel's descriptors
   hb += (size_t)n * sizeof(BatchField<double>) + 32 * 256;
+  const size_t hcb = hb;  // then the batched codebook's
+  hb += (size_t)n * sizeof(CodebookArgs) + 256;
   BatchCtx* ctx = nullptr;
   if (bm_status e = batch_ctx(std::max<size_t>(hb, 256), &ctx)) return e;
   bool all_ok = true;
@@ -2432,6 +2444,7 @@ bm_status bm_compress_batch(int n, const bm_batch_item* items, size_t* out_bytes
     const size_t ddesc = dneed;
     if (!groups.empty()) {
       dneed += (size_t)n * sizeof(BatchField<double>) + groups.size() * 512 + 256;
+      dneed += (size_t)n * sizeof(CodebookArgs) + 256;
       if (bm_status e = batch_scratch(ctx, dneed)) return e;
       for (const BatchGroup& gr : groups)
         for (int i : gr.items) {
@@ -2487,7 +2500,7 @@ bm_status bm_compress_batch(int n, const bm_batch_item* items, size_t* out_bytes
         std::vector<int> live;
         for (int i : gr.items)
           if (st[(size_t)i] == BM_OK && !slot[(size_t)i].raw_now) live.push_back(i);
-        for (int i : gr.items) slot[(size_t)i].phase = kFinish;
+        for (int i : gr.items) slot[(size_t)i].phase = kFinishA;
         gr.items = live;
         if (gr.items.empty()) continue;
         any = true;
@@ -2496,10 +2509,34 @@ bm_status bm_compress_batch(int n, const bm_batch_item* items, size_t* out_bytes
         if (e) return e;
       }
     }
-    // 4. the batched items' remaining stages on the second half
+    // 4. the batched items' histograms and global levels on the second half,
+    //    their codebooks in one launch (one CTA each) on q, then their
+    //    encoders and headers on the second half again
     if (any || !groups.empty()) {
       if (bm_status e = fork(kHalf)) return e;
-      run_items(kFinish, kHalf);
+      run_items(kFinishA, kHalf);
+      for (int j = kHalf; j < kBatchStreams; ++j) {
+        BM_CUDA(cudaEventRecord(ctx->joins[(size_t)j], ctx->streams[(size_t)j]));
+        BM_CUDA(cudaStreamWaitEvent(q, ctx->joins[(size_t)j], 0));
+      }
+      CodebookArgs* hc = reinterpret_cast<CodebookArgs*>(ctx->h + hcb);
+      int ncb = 0;
+      for (int i : order)
+        if (st[(size_t)i] == BM_OK && slot[(size_t)i].phase == kFinishA && slot[(size_t)i].cb_ready)
+          hc[ncb++] = slot[(size_t)i].cb;
+      if (ncb) {
+        const size_t dcb = ddesc + (size_t)n * sizeof(BatchField<double>) + groups.size() * 512 + 256;
+        CodebookArgs* dc = reinterpret_cast<CodebookArgs*>(ctx->d + dcb);
+        BM_CUDA(cudaMemcpyAsync(dc, hc, (size_t)ncb * sizeof(CodebookArgs), cudaMemcpyHostToDevice, q));
+        BM_CUDA(set_smem_once(codebook_batch_kernel, (int)sizeof(CbSmem), g_cbb_attr));
+        codebook_batch_kernel<<<(unsigned)ncb, kCbThreads, sizeof(CbSmem), q>>>(dc);
+        BM_LAUNCHED();
+        BM_CUDA(cudaGetLastError());
+      }
+      for (int i : order)
+        if (slot[(size_t)i].phase == kFinishA) slot[(size_t)i].phase = kFinishB;
+      if (bm_status e = fork(kHalf)) return e;
+      run_items(kFinishB, kHalf);
     }
     // 5. every pool stream back into q
     for (size_t j = 0; j < ctx->streams.size(); ++j) {

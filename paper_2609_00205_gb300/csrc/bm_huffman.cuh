@@ -892,7 +892,8 @@ __device__ void codebook_emit(const CodebookArgs& a, CbArrays<IdT> V, int n, uns
   }
 }
 
-__global__ void __launch_bounds__(kCbThreads) codebook_kernel(CodebookArgs a) {
+// The codebook of one compress call, built by one CTA (the whole block).
+__device__ void codebook_block(const CodebookArgs& a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CbSmem& S = *reinterpret_cast<CbSmem*>(smem_raw);
   __shared__ unsigned s_n;
@@ -963,6 +964,14 @@ __global__ void __launch_bounds__(kCbThreads) codebook_kernel(CodebookArgs a) {
     codebook_lengths<unsigned>(a, V, n, S.scan_tmp, S.ka);  // S.ka and S.iw (adjacent) stage the tiles
     codebook_emit<unsigned>(a, V, n, S.scan_tmp, &S.ct);
   }
+}
+
+__global__ void __launch_bounds__(kCbThreads) codebook_kernel(CodebookArgs a) { codebook_block(a); }
+
+// The codebooks of several compress calls (a batch), one CTA each.
+__global__ void __launch_bounds__(kCbThreads) codebook_batch_kernel(const CodebookArgs* __restrict__ args) {
+  const CodebookArgs a = args[blockIdx.x];
+  codebook_block(a);
 }
 
 // Histogram of a symbol array (stand-alone Huffman entry point): a shared
