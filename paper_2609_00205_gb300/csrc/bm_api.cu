@@ -29,6 +29,11 @@
 #endif
 // The block region's histogram: on a second stream beside the global levels
 // (BM_HIST_OVERLAP) with BM_HIST_CTAS CTAs per SM.
+// BM_CB_PRESORT: a compress call's codebook starts with the multi-CTA
+// clearing, compaction and sort of cb_presort_kernel.
+#ifndef BM_CB_PRESORT
+#define BM_CB_PRESORT 1
+#endif
 // BM_BATCH_GRAPHS: a batched compress met a second time with the same
 // arguments is captured as a CUDA graph, and replayed from then on.
 #ifndef BM_BATCH_GRAPHS
@@ -1636,6 +1641,15 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
       return BM_OK;
     }
     if (phase != kFinishB) {
+      // the table clearing, compaction and (for wide distributions) the
+      // sort run on kPreCtas CTAs first; the tree itself is one CTA's work
+      ca.presorted = BM_CB_PRESORT;
+      if (BM_CB_PRESORT) {
+        void* kargs[] = {(void*)&ca};
+        BM_CUDA(cudaLaunchCooperativeKernel((const void*)cb_presort_kernel, dim3(kPreCtas), dim3(kPreThreads), kargs,
+                                            0, s));
+        BM_LAUNCHED();
+      }
       BM_CUDA(set_smem_once(codebook_kernel, (int)sizeof(CbSmem), g_cb_attr));
       codebook_kernel<<<1, kCbThreads, sizeof(CbSmem), s>>>(ca);
       BM_LAUNCHED();

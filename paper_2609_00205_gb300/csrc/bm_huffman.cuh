@@ -11,6 +11,8 @@
 // weigh >= X and lose ties), so all those pairs are formed at once.
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "bm_common.cuh"
 
 namespace bm {
@@ -376,6 +378,8 @@ struct CodebookArgs {
   unsigned long long raw_total;  // size of the raw stream (~0: no raw fallback)
   unsigned char* big;            // global scratch for more than kCbSmemSyms present symbols (cb_big_bytes())
   unsigned* packed;              // [dict] out (nullable): code | len << 26 when every code has at most 26 bits
+  int presorted;                 // cb_presort_kernel ran: tables cleared, symbols compacted into the
+                                 // global arrays and, above kCbSmemSyms of them, sorted
 };
 
 // Present symbols the codebook keeps in shared memory; more use global
@@ -421,8 +425,16 @@ static_assert(sizeof(CbSmem) <= 227 * 1024, "codebook shared memory");
 static_assert(256 * 32 >= kCbSmemSyms, "run offsets over the sort counts");
 
 // Global scratch of the large variant: n <= kMaxDict present symbols, 32-bit ids.
+constexpr int kPreCtas = 64;  // CTAs of cb_presort_kernel
+// Counts of the multi-CTA presort, after the arrays in the global scratch.
+struct CbPre {
+  unsigned n, maxk, passes, pad;
+  unsigned cnt[kPreCtas];          // present symbols of each CTA's dictionary segment
+  unsigned dcnt[kPreCtas * 256];   // per (CTA, digit) keys of the current pass
+};
 __host__ __device__ constexpr size_t cb_big_bytes() {
-  return (size_t)kMaxDict * (2 + 1 + 4 + 2 + 4 + 2 + 4 + 4 * 2 + 2 + 4 + 2) + 3 * 4 * (size_t)kMaxDict + 16 * 256;
+  return (size_t)kMaxDict * (2 + 1 + 4 + 2 + 4 + 2 + 4 + 4 * 2 + 2 + 4 + 2) + 3 * 4 * (size_t)kMaxDict + 16 * 256 +
+         sizeof(CbPre) + 256;
 }
 
 __device__ __forceinline__ CbArrays<uint16_t> cb_small(CbSmem& S) {
@@ -463,6 +475,14 @@ __device__ __forceinline__ CbArrays<unsigned> cb_big(unsigned char* g, unsigned*
   v.wcnt = smem_wcnt;  // the counting passes stay in shared memory
   return v;
 }
+// The presort's counts: after the arrays of cb_big.
+__device__ __forceinline__ CbPre* cb_pre(unsigned char* g) {
+  const size_t N = kMaxDict;
+  size_t off = 0;
+  const size_t parts[] = {2 * N, N, 4 * N, 2 * N, 4 * N, 2 * N, 4 * N, 8 * N, 2 * N, 4 * N, 2 * N, 4 * N, 4 * N, 4 * N};
+  for (size_t b : parts) off += (b + 255) & ~size_t(255);
+  return reinterpret_cast<CbPre*>(g + off);
+}
 
 // The codebook over the compact arrays V (n present symbols, already in
 // V.csym): Huffman lengths into V.clen.  The lengths are those of the
@@ -501,7 +521,7 @@ __device__ __forceinline__ unsigned merge_pairs(const unsigned* A, int na, const
 
 template <typename IdT>
 __device__ void codebook_lengths(const CodebookArgs& a, CbArrays<IdT> V, int n, unsigned* scan_tmp,
-                                 unsigned* stage) {
+                                 unsigned* stage, int pre_passes = -1) {
   __shared__ unsigned s_lp, s_qp, s_qe, s_pl, s_pq, s_leaves, s_rounds, s_maxd, s_maxk;
   __shared__ int s_split;
   if (n <= 1) {
@@ -510,9 +530,19 @@ __device__ void codebook_lengths(const CodebookArgs& a, CbArrays<IdT> V, int n, 
     return;
   }
   for (int shift = 0;; ++shift) {
+    const bool presorted = shift == 0 && pre_passes > 0;  // pairs sorted by cb_presort_kernel
+    if (presorted && (pre_passes & 1)) {  // the sorted pairs are in (kb, sb)
+      unsigned* tk = V.ka;
+      V.ka = V.kb;
+      V.kb = tk;
+      uint16_t* ts = V.sa;
+      V.sa = V.sb;
+      V.sb = ts;
+    }
     // 1. (freq', compact index) pairs in symbol order
     if (threadIdx.x == 0) s_maxk = 0;
     __syncthreads();
+    if (!presorted) {
     unsigned mk = 0;
     for (int i0 = threadIdx.x; i0 < n; i0 += 8 * blockDim.x) {  // eight loads in flight
       unsigned sy[8], f[8];
@@ -547,6 +577,7 @@ __device__ void codebook_lengths(const CodebookArgs& a, CbArrays<IdT> V, int n, 
         V.sa[i] = V.sb[i];
       }
     }
+    }  // !presorted
     const unsigned* lw = V.ka;
     const uint16_t* ls = V.sa;
     if (threadIdx.x == 0) { s_lp = 0; s_qp = 0; s_qe = 0; s_rounds = 0; s_leaves = 0; }
@@ -892,12 +923,179 @@ __device__ void codebook_emit(const CodebookArgs& a, CbArrays<IdT> V, int n, uns
   }
 }
 
+// Multi-CTA start of the codebook for wide code distributions: one
+// cooperative launch of kPreCtas CTAs with grid-wide barriers between the
+// phases.  It clears the code tables, compacts the present symbols (symbol
+// order) into the global arrays with their frequencies as keys, the compact
+// index as payload and zero lengths, and, when more than kCbSmemSyms symbols
+// are present, sorts the pairs by key, stably, with 8-bit LSD passes: each
+// CTA owns a contiguous segment of the pairs; a pass counts the segment's
+// digits, and after the barrier thread d of each CTA walks its segment (staged
+// in shared memory) in order and places the keys of digit d at the digit's
+// global offset (all keys of smaller digits, then those of digit d in the
+// CTAs before), so equal keys keep their order.  The sorted pairs are in
+// (ka, sa) after an even number of passes and in (kb, sb) after an odd one
+// (CbPre::passes; 0 when the codebook kernel sorts in shared memory itself).
+constexpr int kPreThreads = 256;
+constexpr int kPreSeg = kMaxDict / kPreCtas;  // pairs per CTA at most
+__global__ void __launch_bounds__(kPreThreads) cb_presort_kernel(CodebookArgs a) {
+  cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+  CbPre* pre = cb_pre(a.big);
+  const CbArrays<unsigned> V = cb_big(a.big, nullptr);
+  const int dict = a.dict, c = blockIdx.x, G = gridDim.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __shared__ unsigned s_red[kPreThreads / 32];
+  __shared__ unsigned s_scan[kPreThreads];
+  __shared__ unsigned s_dc[256];
+  __shared__ unsigned s_key[kPreSeg];
+  __shared__ uint16_t s_val[kPreSeg];
+  __shared__ unsigned s_base, s_n, s_maxk;
+  auto block_sum = [&](unsigned v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) s_red[wid] = v;
+    __syncthreads();
+    unsigned t = 0;
+    for (int w = 0; w < kPreThreads / 32; ++w) t += s_red[w];
+    return t;
+  };
+  auto block_excl = [&](unsigned v, unsigned* total) {  // exclusive scan over the block's threads
+    s_scan[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < kPreThreads; o <<= 1) {
+      const unsigned y = threadIdx.x >= (unsigned)o ? s_scan[threadIdx.x - o] : 0u;
+      __syncthreads();
+      s_scan[threadIdx.x] += y;
+      __syncthreads();
+    }
+    const unsigned incl = s_scan[threadIdx.x];
+    if (total) *total = s_scan[kPreThreads - 1];
+    __syncthreads();
+    return incl - v;
+  };
+  // 0. tables cleared; present symbols of this CTA's dictionary segment counted
+  for (int s = c * kPreThreads + threadIdx.x; s < dict; s += G * kPreThreads) {
+    a.lens[s] = 0;
+    a.codes[s] = 0;
+    if (a.packed) a.packed[s] = 0;
+  }
+  const int dseg = (dict + G - 1) / G, d0 = min(dict, c * dseg), d1 = min(dict, d0 + dseg);
+  unsigned my = 0;
+  for (int s = d0 + threadIdx.x; s < d1; s += kPreThreads) my += a.hist[s] != 0u;
+  const unsigned cnt = block_sum(my);
+  if (threadIdx.x == 0) {
+    pre->cnt[c] = cnt;
+    if (c == 0) pre->maxk = 0;
+  }
+  grid.sync();
+  // 1. compaction in symbol order: (frequency, compact index) pairs
+  if (threadIdx.x == 0) {
+    unsigned b = 0, t = 0;
+    for (int k = 0; k < G; ++k) {
+      const unsigned v = pre->cnt[k];
+      if (k < c) b += v;
+      t += v;
+    }
+    s_base = b;
+    s_n = t;
+  }
+  __syncthreads();
+  unsigned pos = s_base, mk = 0;
+  for (int s0 = d0; s0 < d1; s0 += kPreThreads) {
+    const int s = s0 + threadIdx.x;
+    const unsigned f = s < d1 ? a.hist[s] : 0u;
+    unsigned tot = 0;
+    const unsigned r = block_excl(f != 0u ? 1u : 0u, &tot);
+    if (f) {
+      const unsigned i = pos + r;
+      V.csym[i] = (uint16_t)s;
+      V.clen[i] = 0;
+      V.ka[i] = f;
+      V.sa[i] = (uint16_t)i;
+      mk = max(mk, f);
+    }
+    pos += tot;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) mk = max(mk, __shfl_xor_sync(0xffffffffu, mk, o));
+  if (lane == 0 && mk) atomicMax(&pre->maxk, mk);
+  if (c == 0 && threadIdx.x == 0) pre->n = s_n;
+  grid.sync();
+  const int n = (int)s_n;
+  if (threadIdx.x == 0) s_maxk = pre->maxk;
+  __syncthreads();
+  int passes = 0;
+  if (n > kCbSmemSyms) {
+    passes = 1;
+    while (passes < 4 && (s_maxk >> (8 * passes)) != 0u) ++passes;
+  }
+  if (c == 0 && threadIdx.x == 0) pre->passes = (unsigned)passes;
+  const int pseg = (n + G - 1) / G, p0 = min(n, c * pseg), p1 = min(n, p0 + pseg);
+  for (int p = 0; p < passes; ++p) {
+    const int shift = 8 * p;
+    const unsigned* kin = (p & 1) ? V.kb : V.ka;
+    const uint16_t* sin = (p & 1) ? V.sb : V.sa;
+    unsigned* kout = (p & 1) ? V.ka : V.kb;
+    uint16_t* sout = (p & 1) ? V.sa : V.sb;
+    // the segment staged, its digits counted
+    s_dc[threadIdx.x] = 0u;
+    __syncthreads();
+    for (int i = p0 + threadIdx.x; i < p1; i += kPreThreads) {
+      const unsigned k = kin[i];
+      s_key[i - p0] = k;
+      s_val[i - p0] = sin[i];
+      atomicAdd(&s_dc[(k >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    pre->dcnt[c * 256 + threadIdx.x] = s_dc[threadIdx.x];
+    grid.sync();
+    // offsets of digit d (thread d): keys of smaller digits, then of digit d
+    // in the CTAs before this one
+    const unsigned d = threadIdx.x;
+    unsigned col = 0, part = 0;
+    for (int k = 0; k < G; ++k) {
+      const unsigned v = pre->dcnt[k * 256 + d];
+      if (k < c) part += v;
+      col += v;
+    }
+    unsigned off = block_excl(col, nullptr) + part;
+    for (int i = 0; i < p1 - p0; ++i) {
+      const unsigned k = s_key[i];
+      if (((k >> shift) & 255u) == d) {
+        kout[off] = k;
+        sout[off] = s_val[i];
+        ++off;
+      }
+    }
+    grid.sync();
+  }
+}
+
 // The codebook of one compress call, built by one CTA (the whole block).
 __device__ void codebook_block(const CodebookArgs& a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CbSmem& S = *reinterpret_cast<CbSmem*>(smem_raw);
   __shared__ unsigned s_n;
   const int dict = a.dict;
+  if (a.presorted) {  // cb_presort_kernel cleared the tables and compacted the symbols
+    const CbPre* pre = cb_pre(a.big);
+    const int n = (int)pre->n;
+    const int passes = (int)pre->passes;
+    if (n <= kCbSmemSyms) {
+      const uint16_t* gsym = cb_big(a.big, S.wcnt).csym;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) S.csym[i] = gsym[i];
+      __syncthreads();
+      const CbArrays<uint16_t> V = cb_small(S);
+      codebook_lengths<uint16_t>(a, V, n, S.scan_tmp, nullptr);
+      codebook_emit<uint16_t>(a, V, n, S.scan_tmp, &S.ct);
+    } else {
+      const CbArrays<unsigned> V = cb_big(a.big, S.wcnt);
+      codebook_lengths<unsigned>(a, V, n, S.scan_tmp, S.ka, passes);
+      codebook_emit<unsigned>(a, V, n, S.scan_tmp, &S.ct);
+    }
+    return;
+  }
   // 0. every dictionary entry starts without a code
   for (int s = threadIdx.x; s < dict; s += blockDim.x) {
     a.lens[s] = 0;
