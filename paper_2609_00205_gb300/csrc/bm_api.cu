@@ -30,7 +30,8 @@
 // The block region's histogram: on a second stream beside the global levels
 // (BM_HIST_OVERLAP) with BM_HIST_CTAS CTAs per SM.
 // BM_CB_PRESORT: a compress call's codebook starts with the multi-CTA
-// clearing, compaction and sort of cb_presort_kernel.
+// clearing, compaction and sort of cb_presort_kernel and, above 8192 present
+// symbols, ends with the multi-CTA emission of cb_emit_kernel.
 #ifndef BM_CB_PRESORT
 #define BM_CB_PRESORT 1
 #endif
@@ -1654,6 +1655,12 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
       codebook_kernel<<<1, kCbThreads, sizeof(CbSmem), s>>>(ca);
       BM_LAUNCHED();
       BM_CUDA(cudaGetLastError());
+      if (BM_CB_PRESORT) {  // above 8192 present symbols the codes are emitted on kPreCtas CTAs
+        void* kargs[] = {(void*)&ca};
+        BM_CUDA(cudaLaunchCooperativeKernel((const void*)cb_emit_kernel, dim3(kPreCtas), dim3(kPreThreads), kargs, 0,
+                                            s));
+        BM_LAUNCHED();
+      }
     }
   }
   {

@@ -276,6 +276,26 @@ __device__ __forceinline__ int lower_bound_u32(const unsigned* a, int lo, int hi
   return lo;
 }
 
+// First codes, first positions, left-justified limits, the symbol count and
+// the longest length of canonical codes from the count of codes of each
+// length (ct->count[1..kMaxLen], count[kMaxLen + 1] = 0); one thread.
+__device__ inline void canon_from_counts(CanonTables* ct) {
+  unsigned code = 0, p = 0, maxl = 0;
+  ct->count[0] = 0;
+  for (int L = 1; L <= kMaxLen + 1; ++L) {
+    code = (code + (L > 1 ? ct->count[L - 1] : 0u)) << 1;
+    if (L == 1) code = 0;
+    ct->first_code[L] = code;
+    ct->first_pos[L] = p;
+    p += ct->count[L];
+    if (ct->count[L]) maxl = L;
+  }
+  for (int L = 1; L <= kMaxLen; ++L) ct->limit[L] = ((unsigned long long)ct->first_code[L] + ct->count[L]) << (32 - L);
+  ct->limit[kMaxLen + 1] = 1ull << 32;
+  ct->n = p;
+  ct->max_len = maxl;
+}
+
 // Canonical-code tables from the code lengths of the n present symbols held
 // in symbol order (len[i]: length of the i-th present symbol): canon[] gets
 // the indices i in (length, symbol) order, by one stable counting pass over
@@ -321,23 +341,7 @@ __device__ void build_canonical(const uint8_t* len, int n, unsigned* wcnt, uint1
     if (lane == 31) ct->count[L] = x;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned code = 0, p = 0, maxl = 0;
-    ct->count[0] = 0;
-    for (int L = 1; L <= kMaxLen + 1; ++L) {
-      code = (code + (L > 1 ? ct->count[L - 1] : 0u)) << 1;
-      if (L == 1) code = 0;
-      ct->first_code[L] = code;
-      ct->first_pos[L] = p;
-      p += ct->count[L];
-      if (ct->count[L]) maxl = L;
-    }
-    for (int L = 1; L <= kMaxLen; ++L)
-      ct->limit[L] = ((unsigned long long)ct->first_code[L] + ct->count[L]) << (32 - L);
-    ct->limit[kMaxLen + 1] = 1ull << 32;
-    ct->n = p;
-    ct->max_len = maxl;
-  }
+  if (threadIdx.x == 0) canon_from_counts(ct);
   __syncthreads();
   for (int r0 = 0; r0 < rows; r0 += 8) {
     unsigned ll[8];
@@ -430,7 +434,10 @@ constexpr int kPreCtas = 64;  // CTAs of cb_presort_kernel
 struct CbPre {
   unsigned n, maxk, passes, pad;
   unsigned cnt[kPreCtas];          // present symbols of each CTA's dictionary segment
-  unsigned dcnt[kPreCtas * 256];   // per (CTA, digit) keys of the current pass
+  unsigned dcnt[kPreCtas * 256];   // per (CTA, digit) keys of the current pass; then per (CTA, length) codes
+  unsigned rcnt[kPreCtas];         // run starts of each CTA's segment of compact indices
+  unsigned bsum[kPreCtas];         // codebook-section bytes of each CTA's runs
+  unsigned long long bits, all, win;  // sums of f len, f, f served by the encoder's window
 };
 __host__ __device__ constexpr size_t cb_big_bytes() {
   return (size_t)kMaxDict * (2 + 1 + 4 + 2 + 4 + 2 + 4 + 4 * 2 + 2 + 4 + 2) + 3 * 4 * (size_t)kMaxDict + 16 * 256 +
@@ -711,6 +718,55 @@ __device__ void codebook_lengths(const CodebookArgs& a, CbArrays<IdT> V, int n, 
   }
 }
 
+// The codebook's decisions (one thread): section sizes and offsets, the
+// encoder's table and window, the lower bound on the stream size and the
+// raw-copy decision.  smin / smax: the smallest and largest present symbol;
+// bits, all, win: sum of f_s len_s, of f_s, and of f_s over the symbols the
+// encoder's centred window (or the escape registers) serves.
+__device__ inline void codebook_decide(const CodebookArgs& a, unsigned smin, unsigned smax, unsigned long long total,
+                                       int nruns, unsigned max_len, unsigned long long bits, unsigned long long all,
+                                       unsigned long long win, bool fits) {
+  const unsigned wlo_c =
+      a.dict <= kEncWin ? 0u : (unsigned)min(max(a.dict / 2 - kEncWin / 2, 0), a.dict - kEncWin);
+  {
+    Scalars* sc = a.sc;
+    sc->codebook_bytes = total;
+    sc->n_runs = (unsigned long long)nruns;
+    sc->max_len = max_len;
+    // the encoder's shared-memory window of the code table: every present
+    // symbol when they span at most kEncWin symbols; else centred on the
+    // dictionary's middle (code 0) while it and the escape symbol serve at
+    // least BM_ENC_WIN_PCT percent of the symbols met and escapes are fewer
+    // than BM_ENC_ESC_PCT percent (the rest looked up in the global table);
+    // else no window (the global-table variant, with all of L1 for the table)
+    if (smax - smin < (unsigned)kEncWin) {
+      sc->enc_lo = a.dict <= kEncWin ? 0u : min(smin, (unsigned)(a.dict - kEncWin));
+      sc->enc_mode = 0;
+    } else if (win * 100ull >= (unsigned long long)BM_ENC_WIN_PCT * all &&
+               (unsigned long long)a.hist[0] * 100ull < (unsigned long long)BM_ENC_ESC_PCT * all) {
+      sc->enc_lo = wlo_c;
+      sc->enc_mode = 1;
+    } else {
+      sc->enc_lo = 0;
+      sc->enc_mode = 2;
+    }
+    if (a.out && !fits) atomicOr(&sc->status, ST_CAPACITY | ST_RAW);
+    const unsigned long long nout = a.esc_mode ? (unsigned long long)a.hist[0] : 0ull;
+    const unsigned long long off_ce = a.off + pad8(total);
+    const unsigned long long off_out = off_ce + (nout ? pad8(4ull * a.nch) : 0ull);
+    const unsigned long long off_bits = off_out + pad8(4ull * nout);
+    const unsigned long long min_total = off_bits + pad8(4ull * ((bits + 31ull) / 32ull));
+    sc->n_outliers = nout;
+    sc->off_chunk_esc = off_ce;
+    sc->off_outliers = off_out;
+    sc->off_bits = off_bits;
+    // a quantisation overflow, a size bound at or above the raw copy, or sections
+    // that do not fit all make the stream a raw copy: skip the encoder
+    if ((sc->status & ST_OVERFLOW) || min_total >= a.raw_total || off_bits > a.capacity) atomicOr(&sc->status, ST_RAW);
+    sc->skip = (sc->status & ST_RAW) ? 1u : 0u;
+  }
+}
+
 // Canonical codes, the lookup tables of the encoder, the codebook section of
 // the stream and the offsets of the sections after it, from the lengths.
 template <typename IdT>
@@ -883,44 +939,9 @@ __device__ void codebook_emit(const CodebookArgs& a, CbArrays<IdT> V, int n, uns
     if (my_win) atomicAdd(&s_win, my_win);
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    Scalars* sc = a.sc;
-    sc->codebook_bytes = total;
-    sc->n_runs = (unsigned long long)nruns;
-    sc->max_len = ct->max_len;
-    // the encoder's shared-memory window of the code table: every present
-    // symbol when they span at most kEncWin symbols; else centred on the
-    // dictionary's middle (code 0) while it and the escape symbol serve at
-    // least BM_ENC_WIN_PCT percent of the symbols met and escapes are fewer
-    // than BM_ENC_ESC_PCT percent (the rest looked up in the global table);
-    // else no window (the global-table variant, with all of L1 for the table)
-    const unsigned smin = n ? V.csym[0] : 0u, smax = n ? V.csym[n - 1] : 0u;
-    if (smax - smin < (unsigned)kEncWin) {
-      sc->enc_lo = a.dict <= kEncWin ? 0u : min(smin, (unsigned)(a.dict - kEncWin));
-      sc->enc_mode = 0;
-    } else if (s_win * 100ull >= (unsigned long long)BM_ENC_WIN_PCT * s_all &&
-               (unsigned long long)a.hist[0] * 100ull < (unsigned long long)BM_ENC_ESC_PCT * s_all) {
-      sc->enc_lo = wlo_c;
-      sc->enc_mode = 1;
-    } else {
-      sc->enc_lo = 0;
-      sc->enc_mode = 2;
-    }
-    if (a.out && !fits) atomicOr(&sc->status, ST_CAPACITY | ST_RAW);
-    const unsigned long long nout = a.esc_mode ? (unsigned long long)a.hist[0] : 0ull;
-    const unsigned long long off_ce = a.off + pad8(total);
-    const unsigned long long off_out = off_ce + (nout ? pad8(4ull * a.nch) : 0ull);
-    const unsigned long long off_bits = off_out + pad8(4ull * nout);
-    const unsigned long long min_total = off_bits + pad8(4ull * ((s_bits + 31ull) / 32ull));
-    sc->n_outliers = nout;
-    sc->off_chunk_esc = off_ce;
-    sc->off_outliers = off_out;
-    sc->off_bits = off_bits;
-    // a quantisation overflow, a size bound at or above the raw copy, or sections
-    // that do not fit all make the stream a raw copy: skip the encoder
-    if ((sc->status & ST_OVERFLOW) || min_total >= a.raw_total || off_bits > a.capacity) atomicOr(&sc->status, ST_RAW);
-    sc->skip = (sc->status & ST_RAW) ? 1u : 0u;
-  }
+  if (threadIdx.x == 0)
+    codebook_decide(a, n ? V.csym[0] : 0u, n ? V.csym[n - 1] : 0u, total, nruns, ct->max_len, s_bits, s_all, s_win,
+                    fits);
 }
 
 // Multi-CTA start of the codebook for wide code distributions: one
@@ -986,7 +1007,12 @@ __global__ void __launch_bounds__(kPreThreads) cb_presort_kernel(CodebookArgs a)
   const unsigned cnt = block_sum(my);
   if (threadIdx.x == 0) {
     pre->cnt[c] = cnt;
-    if (c == 0) pre->maxk = 0;
+    if (c == 0) {
+      pre->maxk = 0;
+      pre->bits = 0;
+      pre->all = 0;
+      pre->win = 0;
+    }
   }
   grid.sync();
   // 1. compaction in symbol order: (frequency, compact index) pairs
@@ -1072,6 +1098,226 @@ __global__ void __launch_bounds__(kPreThreads) cb_presort_kernel(CodebookArgs a)
   }
 }
 
+// Multi-CTA end of the codebook for wide code distributions (after the one-CTA
+// tree, above kCbSmemSyms present symbols; cooperative launch of kPreCtas
+// CTAs, grid-wide barriers between the phases): what codebook_emit does, each
+// CTA over its segment of compact indices.  Canonical order: per-(CTA,
+// length) counts, then thread L of each CTA places its segment's indices of
+// length L in order (symbol order within a length).  Runs of consecutive
+// present symbols: per-CTA start counts give each start's run index; the
+// runs' section bytes are summed per CTA for their offsets.  The sums of the
+// size bound and of the encoder's window go to global atomics; CTA 0 makes
+// the decisions.
+__global__ void __launch_bounds__(kPreThreads) cb_emit_kernel(CodebookArgs a) {
+  cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+  CbPre* pre = cb_pre(a.big);
+  const CbArrays<unsigned> V = cb_big(a.big, nullptr);
+  const int n = (int)pre->n;
+  if (n <= kCbSmemSyms) return;  // the one-CTA kernel emitted everything (the same for every CTA)
+  const int c = blockIdx.x, G = gridDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  __shared__ uint8_t s_len[kPreSeg];
+  __shared__ uint16_t s_sym[kPreSeg];
+  __shared__ unsigned s_lc[kMaxLen + 2];
+  __shared__ unsigned s_scan[kPreThreads];
+  __shared__ unsigned s_red[kPreThreads / 32];
+  __shared__ unsigned long long s_r64[3][kPreThreads / 32];
+  __shared__ CanonTables s_ct;
+  __shared__ unsigned s_prev, s_rbase, s_nruns, s_boff, s_total;
+  auto block_excl = [&](unsigned v, unsigned* total) {
+    s_scan[tid] = v;
+    __syncthreads();
+    for (int o = 1; o < kPreThreads; o <<= 1) {
+      const unsigned y = tid >= o ? s_scan[tid - o] : 0u;
+      __syncthreads();
+      s_scan[tid] += y;
+      __syncthreads();
+    }
+    const unsigned incl = s_scan[tid];
+    if (total) *total = s_scan[kPreThreads - 1];
+    __syncthreads();
+    return incl - v;
+  };
+  const int pseg = (n + G - 1) / G, e0 = min(n, c * pseg), e1 = min(n, e0 + pseg), m = e1 - e0;
+  // E0: the segment staged; its length counts, run starts and size sums
+  if (tid < kMaxLen + 2) s_lc[tid] = 0u;
+  if (tid == 0) s_prev = e0 > 0 ? (unsigned)V.csym[e0 - 1] : 0u;
+  __syncthreads();
+  const unsigned wlo_c =
+      a.dict <= kEncWin ? 0u : (unsigned)min(max(a.dict / 2 - kEncWin / 2, 0), a.dict - kEncWin);
+  unsigned long long my_bits = 0, my_all = 0, my_win = 0;
+  for (int i = tid; i < m; i += kPreThreads) {
+    const unsigned L = V.clen[e0 + i], sy = V.csym[e0 + i];
+    s_len[i] = (uint8_t)L;
+    s_sym[i] = (uint16_t)sy;
+    if (L >= 1u && L <= (unsigned)kMaxLen) atomicAdd(&s_lc[L], 1u);
+    const unsigned long long f = a.hist[sy];
+    my_bits += f * L;
+    my_all += f;
+    if (sy - wlo_c < (unsigned)kEncWin || sy == 0u) my_win += f;
+  }
+  __syncthreads();
+  auto is_start = [&](int i) {  // i: index within the segment
+    return e0 + i == 0 || (unsigned)s_sym[i] != (i ? (unsigned)s_sym[i - 1] : s_prev) + 1u;
+  };
+  unsigned my_st = 0;
+  for (int i = tid; i < m; i += kPreThreads) my_st += is_start(i);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    my_bits += __shfl_xor_sync(0xffffffffu, my_bits, o);
+    my_all += __shfl_xor_sync(0xffffffffu, my_all, o);
+    my_win += __shfl_xor_sync(0xffffffffu, my_win, o);
+    my_st += __shfl_xor_sync(0xffffffffu, my_st, o);
+  }
+  if (lane == 0) {
+    s_r64[0][wid] = my_bits;
+    s_r64[1][wid] = my_all;
+    s_r64[2][wid] = my_win;
+    s_red[wid] = my_st;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long b = 0, al = 0, w = 0;
+    unsigned st = 0;
+    for (int k = 0; k < kPreThreads / 32; ++k) {
+      b += s_r64[0][k];
+      al += s_r64[1][k];
+      w += s_r64[2][k];
+      st += s_red[k];
+    }
+    atomicAdd(&pre->bits, b);
+    atomicAdd(&pre->all, al);
+    atomicAdd(&pre->win, w);
+    pre->rcnt[c] = st;
+  }
+  if (tid < kMaxLen + 2) pre->dcnt[c * 256 + tid] = s_lc[tid];
+  grid.sync();
+  // E1: canonical tables (every CTA, the same), this segment's canonical
+  // positions; run bases
+  unsigned part = 0;
+  if (tid <= kMaxLen + 1) {
+    unsigned tot = 0;
+    for (int k = 0; k < G; ++k) {
+      const unsigned v = pre->dcnt[k * 256 + tid];
+      if (k < c) part += v;
+      tot += v;
+    }
+    s_ct.count[tid] = tid == 0 || tid == kMaxLen + 1 ? 0u : tot;
+  }
+  if (tid == 0) {
+    unsigned rb = 0, rt = 0;
+    for (int k = 0; k < G; ++k) {
+      const unsigned v = pre->rcnt[k];
+      if (k < c) rb += v;
+      rt += v;
+    }
+    s_rbase = rb;
+    s_nruns = rt;
+  }
+  __syncthreads();
+  if (tid == 0) canon_from_counts(&s_ct);
+  __syncthreads();
+  if (tid >= 1 && tid <= kMaxLen) {
+    unsigned pos = s_ct.first_pos[tid] + part;
+    for (int i = 0; i < m; ++i)
+      if (s_len[i] == (unsigned)tid) V.canon[pos++] = (uint16_t)(e0 + i);
+  }
+  const int nruns = (int)s_nruns;
+  {  // run starts of the segment at their run indices
+    unsigned q = s_rbase;
+    for (int i0 = 0; i0 < m; i0 += kPreThreads) {
+      const int i = i0 + tid;
+      const bool st = i < m && is_start(i);
+      unsigned tot = 0;
+      const unsigned r = block_excl(st ? 1u : 0u, &tot);
+      if (st) V.run_start[q + r] = (unsigned)(e0 + i);
+      q += tot;
+    }
+  }
+  grid.sync();
+  // E2: code tables over the canonical order; section bytes of this CTA's runs
+  const bool pk = a.packed && s_ct.max_len <= 26;
+  for (int i = c * kPreThreads + tid; i < n; i += G * kPreThreads) {
+    const unsigned ci = V.canon[i];
+    const unsigned L = V.clen[ci];
+    const unsigned cd = s_ct.first_code[L] + (unsigned)(i - (int)s_ct.first_pos[L]);
+    const unsigned sy = V.csym[ci];
+    a.codes[sy] = cd;
+    if (pk) a.packed[sy] = cd | (L << 26);
+    a.lens[sy] = (uint8_t)L;
+  }
+  const int rq = (nruns + G - 1) / G, q0 = min(nruns, c * rq), q1 = min(nruns, q0 + rq);
+  unsigned my_b = 0;
+  for (int q = q0 + tid; q < q1; q += kPreThreads) {
+    const unsigned st = V.run_start[q], en = q + 1 < nruns ? V.run_start[q + 1] : (unsigned)n;
+    V.run_end[q] = en;
+    my_b += 8u + (((en - st) + 3u) & ~3u);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) my_b += __shfl_xor_sync(0xffffffffu, my_b, o);
+  if (lane == 0) s_red[wid] = my_b;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned t = 0;
+    for (int k = 0; k < kPreThreads / 32; ++k) t += s_red[k];
+    pre->bsum[c] = t;
+  }
+  grid.sync();
+  // E3: run offsets and headers
+  if (tid == 0) {
+    unsigned b = 0, t = 0;
+    for (int k = 0; k < G; ++k) {
+      const unsigned v = pre->bsum[k];
+      if (k < c) b += v;
+      t += v;
+    }
+    s_boff = b;
+    s_total = t;
+  }
+  __syncthreads();
+  const unsigned long long total = s_total;
+  const bool fits = a.out && a.off + pad8(total) <= a.capacity;
+  {
+    unsigned off = s_boff;
+    for (int qb = q0; qb < q1; qb += kPreThreads) {
+      const int q = qb + tid;
+      const unsigned st = q < q1 ? V.run_start[q] : 0u, en = q < q1 ? V.run_end[q] : 0u;
+      const unsigned bq = q < q1 ? 8u + (((en - st) + 3u) & ~3u) : 0u;
+      unsigned tot = 0;
+      const unsigned r = block_excl(bq, &tot);
+      if (q < q1) {
+        V.run_off[q] = off + r;
+        if (fits) {
+          uint8_t* p = a.out + a.off + off + r;
+          *reinterpret_cast<unsigned*>(p) = (unsigned)V.csym[st];
+          *reinterpret_cast<unsigned*>(p + 4) = en - st;
+          for (unsigned t = en - st; t < (((en - st) + 3u) & ~3u); ++t) p[8 + t] = 0;
+        }
+      }
+      off += tot;
+    }
+  }
+  grid.sync();
+  // E4: the length bytes, each at its run's offset; CTA 0's decisions
+  if (fits) {
+    unsigned q = s_rbase;  // run index of the next start
+    for (int i0 = 0; i0 < m; i0 += kPreThreads) {
+      const int i = i0 + tid;
+      const bool st = i < m && is_start(i);
+      unsigned tot = 0;
+      const unsigned r = block_excl(st ? 1u : 0u, &tot);
+      if (i < m) {
+        const unsigned qi = q + r + (st ? 1u : 0u) - 1u;  // starts up to and including i, minus one
+        a.out[a.off + V.run_off[qi] + 8 + ((unsigned)(e0 + i) - V.run_start[qi])] = s_len[i];
+      }
+      q += tot;
+    }
+    if (c == 0 && tid == 0)
+      for (unsigned long long t = total; t < pad8(total); ++t) a.out[a.off + t] = 0;
+  }
+  if (c == 0 && tid == 0)
+    codebook_decide(a, V.csym[0], V.csym[n - 1], total, nruns, s_ct.max_len, pre->bits, pre->all, pre->win, fits);
+}
+
 // The codebook of one compress call, built by one CTA (the whole block).
 __device__ void codebook_block(const CodebookArgs& a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1089,10 +1335,9 @@ __device__ void codebook_block(const CodebookArgs& a) {
       const CbArrays<uint16_t> V = cb_small(S);
       codebook_lengths<uint16_t>(a, V, n, S.scan_tmp, nullptr);
       codebook_emit<uint16_t>(a, V, n, S.scan_tmp, &S.ct);
-    } else {
+    } else {  // the tree here; cb_emit_kernel emits the codes on many CTAs afterwards
       const CbArrays<unsigned> V = cb_big(a.big, S.wcnt);
       codebook_lengths<unsigned>(a, V, n, S.scan_tmp, S.ka, passes);
-      codebook_emit<unsigned>(a, V, n, S.scan_tmp, &S.ct);
     }
     return;
   }
