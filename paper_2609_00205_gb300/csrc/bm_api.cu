@@ -1644,8 +1644,11 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     if (phase != kFinishB) {
       // the table clearing, compaction and (for wide distributions) the
       // sort run on kPreCtas CTAs first; the tree itself is one CTA's work
-      ca.presorted = BM_CB_PRESORT;
-      if (BM_CB_PRESORT) {
+      // (single calls only: a batch runs many codebooks side by side, and is
+      // captured as a graph)
+      const bool coop = BM_CB_PRESORT && bs == nullptr;
+      ca.presorted = coop ? 1 : 0;
+      if (coop) {
         void* kargs[] = {(void*)&ca};
         BM_CUDA(cudaLaunchCooperativeKernel((const void*)cb_presort_kernel, dim3(kPreCtas), dim3(kPreThreads), kargs,
                                             0, s));
@@ -1655,7 +1658,7 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
       codebook_kernel<<<1, kCbThreads, sizeof(CbSmem), s>>>(ca);
       BM_LAUNCHED();
       BM_CUDA(cudaGetLastError());
-      if (BM_CB_PRESORT) {  // above 8192 present symbols the codes are emitted on kPreCtas CTAs
+      if (coop) {  // above 8192 present symbols the codes are emitted on kPreCtas CTAs
         void* kargs[] = {(void*)&ca};
         BM_CUDA(cudaLaunchCooperativeKernel((const void*)cb_emit_kernel, dim3(kPreCtas), dim3(kPreThreads), kargs, 0,
                                             s));
