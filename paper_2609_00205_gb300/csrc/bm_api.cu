@@ -528,6 +528,7 @@ Reblock reblock_of(const PlanHost& h, bool coarse) {
 
 // cudaFuncAttributeMaxDynamicSharedMemorySize set once per device for a kernel.
 std::atomic<unsigned> g_cb_attr{0}, g_dt_attr{0}, g_dec_attr{0}, g_encw_attr{0}, g_encc_attr{0}, g_cbb_attr{0};
+std::atomic<unsigned> g_enc1_attr{0}, g_enc3_attr{0};
 template <class F>
 cudaError_t set_smem_once(F* fn, int bytes, std::atomic<unsigned>& done) {
   int dev = 0;
@@ -1675,11 +1676,25 @@ bm_status compress_t(const T* field, const int64_t* shape, const Params& prm, do
     ea.chunk_words = reinterpret_cast<unsigned*>(out + L.off_chunks);
     ea.splits = reinterpret_cast<uint16_t*>(out + L.off_splits);
     ea.out = out; ea.capacity = cap; ea.sc = sc;
+    // the codebook picked one of four variants (the others return at once):
+    // every symbol in a small window, four CTAs of eight warps per SM; every
+    // symbol in the large window, or the large window with global look-ups
+    // beside it, one CTA of kEncWarps warps per SM; the global table, four
+    // CTAs of eight warps per SM
+    constexpr int ew = kEncWarps * 32;
+    const int eg = grid_for((int64_t)L.nch * 32, ew, 32 / kEncWarps);
+    BM_CUDA(set_smem_once(encode_fused_kernel<kEncWarps, false, 3>, (int)enc_smem<0>(kEncWin), g_enc3_attr));
+    BM_CUDA(set_smem_once(encode_fused_kernel<kEncWarps, false, 1>, (int)enc_smem<1>(kEncWin), g_enc1_attr));
     BM_CUDA(prefer_l1_once(encode_fused_kernel<8, false, 2>, g_encw_attr));
-    encode_fused_kernel<8, false, 0><<<grid_for((int64_t)L.nch * 32, 256, 4), 256, enc_smem<0>(), s>>>(ea);
-    encode_fused_kernel<8, false, 1><<<grid_for((int64_t)L.nch * 32, 256, 4), 256, enc_smem<1>(), s>>>(ea);
+    FusedEncodeArgs e0 = ea, e1 = ea;
+    e0.win = kEncWinSmall;
+    e1.win = kEncWin;
+    encode_fused_kernel<8, false, 0>
+        <<<grid_for((int64_t)L.nch * 32, 256, 4), 256, enc_smem<0>(kEncWinSmall), s>>>(e0);
+    encode_fused_kernel<kEncWarps, false, 3><<<eg, ew, enc_smem<0>(kEncWin), s>>>(e1);
+    encode_fused_kernel<kEncWarps, false, 1><<<eg, ew, enc_smem<1>(kEncWin), s>>>(e1);
     encode_fused_kernel<8, false, 2><<<grid_for((int64_t)L.nch * 32, 256, 4), 256, 0, s>>>(ea);
-    g_launches.fetch_add(3);
+    g_launches.fetch_add(4);
   }
   {
     Stage st("finish");
@@ -3033,8 +3048,10 @@ bm_status bm_huffman_encode(const uint16_t* d_symbols, uint64_t n, int dict_size
     ea.splits = reinterpret_cast<uint16_t*>(out + off_sp);
     ea.capacity = out_capacity; ea.sc = sc;
     ea.packed = packed;
-    if (dict_size <= kEncWin) {
-      encode_fused_kernel<8, true, 0><<<grid_for((int64_t)nch * 32, 256, 4), 256, enc_smem<0>(), s>>>(ea);
+    ea.win = kEncWinSmall;
+    if (dict_size <= kEncWinSmall) {
+      encode_fused_kernel<8, true, 0>
+          <<<grid_for((int64_t)nch * 32, 256, 4), 256, enc_smem<0>(kEncWinSmall), s>>>(ea);
     } else {
       BM_CUDA(prefer_l1_once(encode_fused_kernel<8, true, 2>, g_encc_attr));
       encode_fused_kernel<8, true, 2><<<grid_for((int64_t)nch * 32, 256, 4), 256, 0, s>>>(ea);
@@ -3129,6 +3146,7 @@ namespace {
 constexpr size_t kNoAllocBytes = size_t(1) << 20;     // 1 MiB
 constexpr unsigned long long kNoAllocMaxChunks = 16384;
 constexpr int kNoAllocMaxDict = 8192;  // at most this many present symbols: the codebook stays in shared memory
+static_assert(kNoAllocMaxDict <= kEncWinSmall, "the encoder's window must hold the whole dictionary");
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 std::mutex g_noalloc_mu;
@@ -3187,6 +3205,7 @@ extern "C" bm_status bm_huffman_encode_noalloc(const uint16_t* d_symbols, uint64
   uint8_t* lens = cv.take<uint8_t>(dict_size);
   unsigned* codes = cv.take<unsigned>(dict_size);
   unsigned char* tickets = cv.take<unsigned char>(256 + 16ull * nch);
+  unsigned* packed = cv.take<unsigned>(dict_size);
   if (cv.off > kNoAllocBytes) return fail(BM_ERR_ARG, "request does not fit the static scratch");
   uint8_t* out = reinterpret_cast<uint8_t*>(d_out);
   // the array keeps the previous call's contents: clear what must start at zero
@@ -3195,7 +3214,7 @@ extern "C" bm_status bm_huffman_encode_noalloc(const uint16_t* d_symbols, uint64
   BM_CUDA(cudaMemsetAsync(tickets, 0, 256 + 16ull * nch, s));
   BM_CUDA(cudaMemsetAsync(out, 0, off_cb, s));
   hist_kernel<<<grid_for((int64_t)n, 256, 4), 256, 0, s>>>(d_symbols, n, dict_size, hist, sc);
-  CodebookArgs ca{hist, dict_size, lens, codes, out, off_cb, out_capacity, sc, 0, nch, ~0ull, nullptr};
+  CodebookArgs ca{hist, dict_size, lens, codes, out, off_cb, out_capacity, sc, 0, nch, ~0ull, nullptr, packed};
   BM_CUDA(set_smem_once(codebook_kernel, (int)sizeof(CbSmem), g_cb_attr));
   codebook_kernel<<<1, kCbThreads, sizeof(CbSmem), s>>>(ca);
   FusedEncodeArgs ea{};
@@ -3205,7 +3224,9 @@ extern "C" bm_status bm_huffman_encode_noalloc(const uint16_t* d_symbols, uint64
   ea.chunk_words = reinterpret_cast<unsigned*>(out); ea.out = out;
   ea.splits = reinterpret_cast<uint16_t*>(out + off_sp);
   ea.capacity = out_capacity; ea.sc = sc;
-  encode_fused_kernel<8, true, 0><<<grid_for((int64_t)nch * 32, 256, 4), 256, enc_smem<0>(), s>>>(ea);
+  ea.packed = packed;
+  ea.win = kEncWinSmall;  // dict_size <= kNoAllocMaxDict = kEncWinSmall: every symbol in the window
+  encode_fused_kernel<8, true, 0><<<grid_for((int64_t)nch * 32, 256, 4), 256, enc_smem<0>(kEncWinSmall), s>>>(ea);
   encode_finish_kernel<<<1, 32, 0, s>>>(~0ull, out_capacity, sc);
   zero_tail_kernel<<<1, 32, 0, s>>>(out, sc);
   g_launches.fetch_add(6);

@@ -43,8 +43,10 @@ struct Scalars {
   unsigned long long esc_seen;     // escapes the encoder met (must equal n_outliers)
   unsigned maxabs_done;            // CTAs of the max|u| pass that have finished
   unsigned enc_lo;                 // first symbol of the encoder's shared-memory code window
-  unsigned enc_mode;               // the encoder's table: 0 window, 1 window + global table, 2 global table
+  unsigned enc_mode;               // the encoder's table: 0 small window, 3 large window, 1 large window + global
+                                   // table, 2 global table
   unsigned qready;                 // batched forward kernel: 1 once the quantiser table is written
+  unsigned enc_n;                  // entries of the encoder's window that a met symbol can reach
 };
 
 // ---------------------------------------------------------------------------

@@ -20,25 +20,46 @@ namespace bm {
 constexpr int kCbThreads = 1024;
 constexpr int kLutBits = 14;
 // Entries of the code table the encoder keeps in shared memory (a window of
-// the dictionary; symbols outside it are looked up in the global table).
-constexpr int kEncWin = 8192;
+// the dictionary), 4 bytes each.  When every present symbol lies within
+// kEncWinSmall consecutive symbols, the window holds them all in CTAs of
+// eight warps, four per SM (the rest of the SM's shared memory stays L1 for
+// the symbol loads in flight).  Otherwise the window of the variant with
+// global look-ups beside it has kEncWin entries in one CTA of kEncWarps warps
+// per SM: 57,344 entries (224 KB) serve all but the far tails of a
+// 65,536-symbol dictionary.  The encoder of caller-supplied symbols keeps
+// kEncWinSmall entries.
+#ifndef BM_ENC_WIN
+#define BM_ENC_WIN 57344
+#endif
+constexpr int kEncWin = BM_ENC_WIN;
+constexpr int kEncWarps = kEncWin > 8192 ? 32 : 8;
+constexpr int kEncWinSmall = 8192;
 // The window variant with global look-ups beside it is taken while its
 // window (and the escape symbol's registers) serve at least BM_ENC_WIN_PCT
 // percent of a call's symbols and fewer than BM_ENC_ESC_PCT percent escape.
 // When escapes dominate, the other symbols are the far tails spread over the
 // whole dictionary, and the global-table variant, which leaves all of L1 to
-// the table, was faster on GB300 (513^3, 1e-5: 1.11 against 1.47 ms); at 1e-3
-// and 1e-4 the window variant was (0.47 against 0.56 ms, 0.89 against 0.99).
+// the table, was faster on GB300 (513^3 GRF, 1e-5, 56 % escapes: 1.08 against
+// 1.68 ms for the large window); at 1e-4 (no symbol spans fewer than 57,344)
+// the large window took 0.52 ms, against 0.84 for the 8,192-entry one.
 #ifndef BM_ENC_WIN_PCT
 #define BM_ENC_WIN_PCT 50
 #endif
 #ifndef BM_ENC_ESC_PCT
 #define BM_ENC_ESC_PCT 20
 #endif
-// Shared memory of the encoder: the window's codes and lengths; the variant
-// for wide code distributions (GLOB) keeps no table in shared memory.
+// The encoder's table entry of a symbol: its code in the low kPackBits bits
+// and its length above them.  A code longer than kPackBits bits (a few
+// symbols of singleton counts in fields of 10^8 symbols and more) keeps only
+// its length there, and the encoder reads the code from the full code table.
+constexpr unsigned kPackBits = 26;
+__host__ __device__ constexpr unsigned enc_entry(unsigned code, unsigned len) {
+  return (len <= kPackBits ? code : 0u) | (len << kPackBits);
+}
+// Shared memory of the encoder with a window of `win` entries; the variant
+// for wide code distributions keeps no table in shared memory.
 template <int TAB>
-__host__ __device__ constexpr size_t enc_smem() { return TAB == 2 ? 0 : (size_t)kEncWin * 5; }
+__host__ __device__ constexpr size_t enc_smem(int win = kEncWin) { return TAB == 2 ? 0 : (size_t)win * 4; }
 // Every chunk is split into eight equal runs; the stream stores the bit
 // offsets of runs 1..7 so that eight decoders can work on one chunk.
 constexpr int kSplits = 8;
@@ -381,7 +402,7 @@ struct CodebookArgs {
   unsigned long long nch;        // chunks
   unsigned long long raw_total;  // size of the raw stream (~0: no raw fallback)
   unsigned char* big;            // global scratch for more than kCbSmemSyms present symbols (cb_big_bytes())
-  unsigned* packed;              // [dict] out (nullable): code | len << 26 when every code has at most 26 bits
+  unsigned* packed;              // [dict] out (nullable): the encoder's entries, enc_entry(code, len)
   int presorted;                 // cb_presort_kernel ran: tables cleared, symbols compacted into the
                                  // global arrays and, above kCbSmemSyms of them, sorted
 };
@@ -734,14 +755,20 @@ __device__ inline void codebook_decide(const CodebookArgs& a, unsigned smin, uns
     sc->n_runs = (unsigned long long)nruns;
     sc->max_len = max_len;
     // the encoder's shared-memory window of the code table: every present
-    // symbol when they span at most kEncWin symbols; else centred on the
-    // dictionary's middle (code 0) while it and the escape symbol serve at
-    // least BM_ENC_WIN_PCT percent of the symbols met and escapes are fewer
-    // than BM_ENC_ESC_PCT percent (the rest looked up in the global table);
-    // else no window (the global-table variant, with all of L1 for the table)
-    if (smax - smin < (unsigned)kEncWin) {
-      sc->enc_lo = a.dict <= kEncWin ? 0u : min(smin, (unsigned)(a.dict - kEncWin));
+    // symbol when they span at most kEncWinSmall symbols, or at most kEncWin
+    // (a larger window in a larger CTA); else kEncWin entries centred on the dictionary's middle (code 0) while they and the
+    // escape symbol serve at least BM_ENC_WIN_PCT percent of the symbols met
+    // and escapes are fewer than BM_ENC_ESC_PCT percent (the rest looked up
+    // in the global table); else no window (the global-table variant, with
+    // all of L1 for the table)
+    unsigned wn = kEncWin;
+    if (smax - smin < (unsigned)kEncWinSmall) {
+      sc->enc_lo = a.dict <= kEncWinSmall ? 0u : min(smin, (unsigned)(a.dict - kEncWinSmall));
       sc->enc_mode = 0;
+      wn = kEncWinSmall;
+    } else if (smax - smin < (unsigned)kEncWin) {
+      sc->enc_lo = a.dict <= kEncWin ? 0u : min(smin, (unsigned)(a.dict - kEncWin));
+      sc->enc_mode = 3;
     } else if (win * 100ull >= (unsigned long long)BM_ENC_WIN_PCT * all &&
                (unsigned long long)a.hist[0] * 100ull < (unsigned long long)BM_ENC_ESC_PCT * all) {
       sc->enc_lo = wlo_c;
@@ -750,6 +777,8 @@ __device__ inline void codebook_decide(const CodebookArgs& a, unsigned smin, uns
       sc->enc_lo = 0;
       sc->enc_mode = 2;
     }
+    // the window's entries above the largest present symbol are never read
+    sc->enc_n = smax >= sc->enc_lo ? min(wn, smax + 1u - sc->enc_lo) : 0u;
     if (a.out && !fits) atomicOr(&sc->status, ST_CAPACITY | ST_RAW);
     const unsigned long long nout = a.esc_mode ? (unsigned long long)a.hist[0] : 0ull;
     const unsigned long long off_ce = a.off + pad8(total);
@@ -776,7 +805,7 @@ __device__ void codebook_emit(const CodebookArgs& a, CbArrays<IdT> V, int n, uns
   if (threadIdx.x == 0) { s_bits = 0; s_all = 0; s_win = 0; }
   // 4. canonical codes (the counting pass in the sort counts' shared memory)
   build_canonical(V.clen, n, V.wcnt, V.canon, ct);
-  const bool pk = a.packed && ct->max_len <= 26;
+  const bool pk = a.packed != nullptr;
   const int nc = (int)ct->n;
   for (int i0 = threadIdx.x; i0 < nc; i0 += 8 * blockDim.x) {  // eight loads in flight
     unsigned ci[8], L[8], sy[8];
@@ -797,7 +826,7 @@ __device__ void codebook_emit(const CodebookArgs& a, CbArrays<IdT> V, int n, uns
       if (i < nc) {
         const unsigned c = ct->first_code[L[t]] + (unsigned)(i - (int)ct->first_pos[L[t]]);
         a.codes[sy[t]] = c;
-        if (pk) a.packed[sy[t]] = c | (L[t] << 26);
+        if (pk) a.packed[sy[t]] = enc_entry(c, L[t]);
         a.lens[sy[t]] = (uint8_t)L[t];
       }
     }
@@ -1235,14 +1264,14 @@ __global__ void __launch_bounds__(kPreThreads) cb_emit_kernel(CodebookArgs a) {
   }
   grid.sync();
   // E2: code tables over the canonical order; section bytes of this CTA's runs
-  const bool pk = a.packed && s_ct.max_len <= 26;
+  const bool pk = a.packed != nullptr;
   for (int i = c * kPreThreads + tid; i < n; i += G * kPreThreads) {
     const unsigned ci = V.canon[i];
     const unsigned L = V.clen[ci];
     const unsigned cd = s_ct.first_code[L] + (unsigned)(i - (int)s_ct.first_pos[L]);
     const unsigned sy = V.csym[ci];
     a.codes[sy] = cd;
-    if (pk) a.packed[sy] = cd | (L << 26);
+    if (pk) a.packed[sy] = enc_entry(cd, L);
     a.lens[sy] = (uint8_t)L;
   }
   const int rq = (nruns + G - 1) / G, q0 = min(nruns, c * rq), q1 = min(nruns, q0 + rq);
@@ -1617,7 +1646,7 @@ struct FusedEncodeArgs {
   int chunk;                     // multiple of 32
   const uint8_t* lens;
   const unsigned* codes;
-  const unsigned* packed;        // code | len << 26 per symbol (written by the codebook), or null
+  const unsigned* packed;        // [dict] enc_entry(code, len) per symbol (written by the codebook)
   int dict;
   unsigned long long nch;
   unsigned* ticket;              // zeroed before launch
@@ -1627,6 +1656,7 @@ struct FusedEncodeArgs {
   uint8_t* out;                  // stream base; the codebook kernel put the section offsets in sc
   unsigned long long capacity;
   Scalars* sc;
+  int win;                       // entries of the shared-memory window (dynamic shared memory: 4 per entry)
 };
 
 __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
@@ -1642,58 +1672,62 @@ __device__ __forceinline__ unsigned sym_of(const uint4* q, int i) {
   return (i & 1) ? (w >> 16) : (w & 0xFFFFu);
 }
 
-// The encoder's code table: with GLOB = false, a window of kEncWin entries
-// in shared memory (sc: code, or code | len << 26 when every code has at most
-// 26 bits; sl: length) starting at symbol `lo`, symbols outside it looked up
-// in the global table; with GLOB = true (code distributions whose mass lies
-// mostly outside any window) the whole table in global memory, read through
-// L1 (gp: packed entries, or gc / gl).  Either way the escape symbol 0's
-// entry is in registers.
+// The encoder's code table, entries enc_entry(code, len): a window of
+// `wn` entries in shared memory (sc) starting at symbol `lo`, and the
+// whole table in global memory (gp), read through L1; gc holds the full codes
+// of the rare codes longer than kPackBits bits.  The escape symbol 0's code
+// and length are in registers.
 struct EncTab {
   const unsigned* sc;
-  const uint8_t* sl;
-  unsigned lo;
+  unsigned lo, wn;  // first symbol and entries of the window
   const unsigned* gc;
-  const uint8_t* gl;
   const unsigned* gp;
   unsigned c0, l0;  // code and length of symbol 0
 };
 
+// A global load issued only where `pred` holds (a predicated instruction,
+// not a branch: the warp does not diverge); v keeps its value elsewhere.
+__device__ __forceinline__ unsigned ld_nc_if(const unsigned* p, bool pred, unsigned v) {
+  asm("{\n .reg .pred q;\n setp.ne.u32 q, %2, 0;\n @q ld.global.nc.u32 %0, [%1];\n}\n"
+      : "+r"(v)
+      : "l"(p), "r"((unsigned)pred));
+  return v;
+}
 // Table of a lookup: TAB 0 = the shared-memory window only (it holds every
 // symbol met), 1 = the window with the global table for symbols outside it,
 // 2 = the global table only.
-template <bool PACKED, int TAB>
+template <int TAB>
+__device__ __forceinline__ unsigned entry_of(const EncTab& t, unsigned s) {
+  if (TAB == 0) return t.sc[s - t.lo];
+  if (TAB == 1) {  // the window's entry, or (rare) the global table's by a predicated load
+    const unsigned k = s - t.lo;
+    const bool in = k < t.wn;
+    const unsigned ew = t.sc[in ? k : 0u];
+    const unsigned eg = ld_nc_if(t.gp + s, !in && s != 0u, enc_entry(t.c0, t.l0));
+    return in ? ew : eg;
+  }
+  return s == 0u ? enc_entry(t.c0, t.l0) : __ldg(t.gp + s);
+}
+template <int TAB>
 __device__ __forceinline__ void code_of(const EncTab& t, unsigned s, unsigned& c, unsigned& L) {
-  if (TAB < 2) {
-    const unsigned k = s - t.lo;
-    if (TAB == 0 || k < (unsigned)kEncWin) {
-      const unsigned cw = t.sc[k];
-      if (PACKED) { c = cw & 0x3FFFFFFu; L = cw >> 26; }
-      else { c = cw; L = t.sl[k]; }
-      return;
-    }
-  }
-  if (s == 0u) {
-    c = t.c0;
-    L = t.l0;
-  } else if (PACKED && t.gp) {
-    const unsigned cw = __ldg(t.gp + s);
-    c = cw & 0x3FFFFFFu;
-    L = cw >> 26;
-  } else {
-    c = __ldg(t.gc + s);
-    L = __ldg(t.gl + s);
-  }
+  const unsigned e = entry_of<TAB>(t, s);
+  c = e & ((1u << kPackBits) - 1u);
+  L = e >> kPackBits;
+  if (L > kPackBits) c = s == 0u ? t.c0 : __ldg(t.gc + s);  // a long code (rare)
 }
-template <bool PACKED, int TAB>
+// Without long codes in the warp's slices: the entry alone.
+template <int TAB>
+__device__ __forceinline__ void code_of_short(const EncTab& t, unsigned s, unsigned& c, unsigned& L) {
+  const unsigned e = entry_of<TAB>(t, s);
+  c = e & ((1u << kPackBits) - 1u);
+  L = e >> kPackBits;
+}
+template <int TAB>
 __device__ __forceinline__ unsigned len_of(const EncTab& t, unsigned s) {
-  if (TAB < 2) {
-    const unsigned k = s - t.lo;
-    if (TAB == 0 || k < (unsigned)kEncWin) return PACKED ? (t.sc[k] >> 26) : (unsigned)t.sl[k];
-  }
-  if (s == 0u) return t.l0;
-  return (PACKED && t.gp) ? (__ldg(t.gp + s) >> 26) : (unsigned)__ldg(t.gl + s);
+  return entry_of<TAB>(t, s) >> kPackBits;
 }
+// An entry at or above this one has a code longer than kPackBits bits.
+constexpr unsigned kLongEntry = (kPackBits + 1u) << kPackBits;
 
 // Symbols of a slice, streamed past L1 (the global code table of the GLOB
 // variant keeps L1 to itself).
@@ -1704,19 +1738,23 @@ __device__ __forceinline__ uint4 ld_stream(const uint4* p) {
   return v;
 }
 
-// Bits and escape mask of a lane's vector slice (G groups held in registers).
-// CLAMP: symbols may be out of the dictionary (caller-supplied) and are
-// clamped; the compressor's own symbols are in range by construction.
-template <bool PACKED, int TAB, bool CLAMP, int GC>
+// Bits, escape mask and largest table entry of a lane's vector slice (G
+// groups held in registers).  CLAMP: symbols may be out of the dictionary
+// (caller-supplied) and are clamped; the compressor's own symbols are in
+// range by construction.
+template <int TAB, bool CLAMP, int GC>
 __device__ __forceinline__ void slice_bits(const uint4* q, int G, unsigned dmax, const EncTab& tab, unsigned& bits,
-                                           unsigned long long& emask) {
+                                           unsigned long long& emask, unsigned& emax) {
   bits = 0;
+  emax = 0;
   unsigned nz = 0;
 #pragma unroll
   for (int i = 0; i < 8 * kEncGroups; ++i) {
     if ((i >> 3) < (GC ? GC : G)) {
       const unsigned s = CLAMP ? min(sym_of(q, i), dmax) : sym_of(q, i);
-      bits += len_of<PACKED, TAB>(tab, s);
+      const unsigned e = entry_of<TAB>(tab, s);
+      bits += e >> kPackBits;
+      emax = max(emax, e);
       nz += s == 0;
     }
   }
@@ -1735,27 +1773,24 @@ __device__ __forceinline__ void slice_bits(const uint4* q, int G, unsigned dmax,
 // word is stored through `wp` as soon as it fills.  The lane's first word may
 // start with the previous lane's last bits: it is stored with zeros there and
 // the previous lane ORs its bits in afterwards.
-template <bool PACKED, int TAB, bool CLAMP, int GC>
+template <int TAB, bool CLAMP, int GC, bool LONG>
 __device__ __forceinline__ void slice_pack(const uint4* q, int G, unsigned dmax, const EncTab& tab, unsigned* wp,
                                            unsigned nb, unsigned long long& acc_out, unsigned& nb_out,
                                            unsigned*& wp_out) {
-  // acc = hi:lo; packed codes have at most 26 bits, so the shifts stay below
-  // 32 and each is one funnel shift (and a plain shift of the low word)
+  // acc = hi:lo holds at most 31 pending bits, so a code of up to 32 bits
+  // fits; each shift is one clamped funnel shift (a shift by 32 moves the
+  // whole low word up).  LONG: the warp's slices hold codes longer than
+// kPackBits bits, read from the full code table.
   unsigned hi = 0, lo = 0;
 #pragma unroll
   for (int i = 0; i < 8 * kEncGroups; ++i) {
     if ((i >> 3) < (GC ? GC : G)) {
       const unsigned s = CLAMP ? min(sym_of(q, i), dmax) : sym_of(q, i);
       unsigned c, L;
-      code_of<PACKED, TAB>(tab, s, c, L);
-      if (PACKED) {
-        hi = __funnelshift_l(lo, hi, L);
-        lo = (lo << L) | c;
-      } else {
-        const unsigned long long acc = ((((unsigned long long)hi << 32) | lo) << L) | c;
-        hi = (unsigned)(acc >> 32);
-        lo = (unsigned)acc;
-      }
+      if (LONG) code_of<TAB>(tab, s, c, L);
+      else code_of_short<TAB>(tab, s, c, L);
+      hi = __funnelshift_lc(lo, hi, L);
+      lo = __funnelshift_lc(0u, lo, L) | c;
       nb += L;
       if (nb >= 32u) {
         nb -= 32u;
@@ -1768,24 +1803,31 @@ __device__ __forceinline__ void slice_pack(const uint4* q, int G, unsigned dmax,
   wp_out = wp;
 }
 
-// One of the four instantiations of a slice function, picked at run time
-// (packed codes, full default-size slices); TAB is the kernel's.
-#define BM_ENC_DISPATCH(FN, ...)                                                        \
-  do {                                                                                  \
-    if (G == kEncGroups) {                                                              \
-      if (packed) FN<true, TAB, CLAMP, kEncGroups>(__VA_ARGS__);                         \
-      else FN<false, TAB, CLAMP, kEncGroups>(__VA_ARGS__);                               \
-    } else {                                                                            \
-      if (packed) FN<true, TAB, CLAMP, 0>(__VA_ARGS__);                                  \
-      else FN<false, TAB, CLAMP, 0>(__VA_ARGS__);                                        \
-    }                                                                                   \
+// The instantiation of a slice function picked at run time (full
+// default-size slices or not; for packing, long codes in the warp or not);
+// TAB is the kernel's.
+#define BM_ENC_DISPATCH(FN, ...)                                  \
+  do {                                                            \
+    if (G == kEncGroups) FN<TAB, CLAMP, kEncGroups>(__VA_ARGS__); \
+    else FN<TAB, CLAMP, 0>(__VA_ARGS__);                          \
+  } while (0)
+#define BM_ENC_DISPATCH_PACK(FN, ...)                                                  \
+  do {                                                                                 \
+    if (G == kEncGroups) {                                                             \
+      if (wlong) FN<TAB, CLAMP, kEncGroups, true>(__VA_ARGS__);                        \
+      else FN<TAB, CLAMP, kEncGroups, false>(__VA_ARGS__);                             \
+    } else {                                                                           \
+      if (wlong) FN<TAB, CLAMP, 0, true>(__VA_ARGS__);                                 \
+      else FN<TAB, CLAMP, 0, false>(__VA_ARGS__);                                      \
+    }                                                                                  \
   } while (0)
 
-// Three instantiations per symbol source: TAB = 0 when every symbol met lies
-// in the shared-memory window, 1 when the window serves most of them and the
-// global table the rest, 2 (the global table only) otherwise.
-// For the compressor's own symbols (CLAMP = false) the codebook decided
-// (sc->enc_mode) and all three are launched, the ones that do not match returning
+// The codebook's choice of table (sc->enc_mode, the kernel's MODE): 0 when
+// every symbol met lies in a window of kEncWinSmall entries, 3 when they all
+// lie in one of kEncWin entries, 1 when that window serves most of them and
+// the global table the rest, 2 (the global table only) otherwise; modes 0 and
+// 3 look up the window alone (TAB 0).  For the compressor's own symbols
+// (CLAMP = false) all four are launched, the ones that do not match returning
 // at once; for caller-supplied symbols the host picks by dictionary size.
 // Warps take chunks in ticket order.  A warp codes its chunk's bit count from
 // the symbols it holds in registers, publishes the chunk's (words, escapes)
@@ -1794,27 +1836,23 @@ __device__ __forceinline__ void slice_pack(const uint4* q, int G, unsigned dmax,
 // packs its codes at the now known word offset.  Each lane stores its full
 // words; a word shared by two lanes is completed by an atomic OR of the
 // earlier lane's last bits.
-template <int WARPS, bool CLAMP, int TAB>
-__global__ void __launch_bounds__(WARPS * 32, 4) encode_fused_kernel(FusedEncodeArgs a) {
+template <int WARPS, bool CLAMP, int MODE>
+__global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) encode_fused_kernel(FusedEncodeArgs a) {
+  constexpr int TAB = MODE == 3 ? 0 : MODE;
   extern __shared__ __align__(16) unsigned char enc_smem_raw[];
-  constexpr int WN = TAB == 2 ? 0 : kEncWin;
-  unsigned* codes = reinterpret_cast<unsigned*>(enc_smem_raw);           // [WN]
-  uint8_t* lens = enc_smem_raw + 4 * WN;                                  // [WN]
+  const int WN = TAB == 2 ? 0 : a.win;
+  unsigned* ent = reinterpret_cast<unsigned*>(enc_smem_raw);  // [WN] the window's entries
   Scalars* sc = a.sc;
   if (sc->skip) return;  // the stream is already known to be a raw copy
-  if (!CLAMP && (unsigned)TAB != sc->enc_mode) return;
-  // codes of at most 26 bits are packed with their length into one word
-  // (code | len << 26): one shared-memory lookup per symbol in the window
-  const bool packed = sc->max_len <= 26 && (TAB != 2 || a.packed != nullptr);
+  if (!CLAMP && (unsigned)MODE != sc->enc_mode) return;
   const unsigned wlo = sc->enc_lo;
-  for (int i = threadIdx.x; i < WN; i += blockDim.x) {
+  // the compressor's symbols lie below enc_lo + enc_n: the rest is never read
+  const int nfill = CLAMP ? WN : min(WN, (int)sc->enc_n);
+  for (int i = threadIdx.x; i < nfill; i += blockDim.x) {
     const unsigned s = wlo + (unsigned)i;
-    const unsigned L = s < (unsigned)a.dict ? a.lens[s] : 0u;
-    const unsigned c = s < (unsigned)a.dict ? a.codes[s] : 0u;
-    lens[i] = (uint8_t)L;
-    codes[i] = packed ? (c | (L << 26)) : c;
+    ent[i] = s < (unsigned)a.dict ? a.packed[s] : 0u;
   }
-  const EncTab tab{codes, lens, wlo, a.codes, a.lens, a.packed, a.codes[0], a.lens[0]};
+  const EncTab tab{ent, wlo, (unsigned)WN, a.codes, a.packed, a.codes[0], a.lens[0]};
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const unsigned dmax = (unsigned)(a.dict - 1);
@@ -1843,7 +1881,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) encode_fused_kernel(FusedEncode
                                                       (reinterpret_cast<uintptr_t>(a.sym) & 15) == 0);
     uint4 q[kEncGroups];
     // pass 1: bits and escapes of the slice
-    unsigned bits = 0, nesc = 0;
+    unsigned bits = 0, nesc = 0, emax = 0;
     unsigned long long emask = 0;
     if (warp_vec) {
       const uint4* p = reinterpret_cast<const uint4*>(a.sym + s0);
@@ -1851,12 +1889,12 @@ __global__ void __launch_bounds__(WARPS * 32, 4) encode_fused_kernel(FusedEncode
       for (int g = 0; g < kEncGroups; ++g)
         q[g] = g < G ? (TAB == 2 ? ld_stream(p + g) : __ldg(p + g)) : make_uint4(0, 0, 0, 0);
       // G is 8 at the default chunk of 2048 symbols: a fully unrolled slice
-      BM_ENC_DISPATCH(slice_bits, q, G, dmax, tab, bits, emask);
+      BM_ENC_DISPATCH(slice_bits, q, G, dmax, tab, bits, emask, emax);
       nesc = __popcll(emask);
     } else {
       for (int t = 0; t < cnt; ++t) {
         const unsigned s = CLAMP ? min((unsigned)a.sym[s0 + t], dmax) : (unsigned)a.sym[s0 + t];
-        bits += len_of<false, TAB>(tab, s);
+        bits += len_of<TAB>(tab, s);
         nesc += s == 0;
       }
     }
@@ -1976,7 +2014,8 @@ __global__ void __launch_bounds__(WARPS * 32, 4) encode_fused_kernel(FusedEncode
       unsigned* wp;
       unsigned* const w0 = words + head_idx;
       const unsigned nb0 = bit0 & 31u;
-      BM_ENC_DISPATCH(slice_pack, q, G, dmax, tab, w0, nb0, acc, nb, wp);
+      const bool wlong = __any_sync(0xffffffffu, emax >= kLongEntry);
+      BM_ENC_DISPATCH_PACK(slice_pack, q, G, dmax, tab, w0, nb0, acc, nb, wp);
       // every lane holds >= 32 bits, so the word of its last bits is the next
       // lane's first word (already stored, zeros in these bits); the last
       // lane's last word is its own
@@ -1995,8 +2034,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) encode_fused_kernel(FusedEncode
       for (int t = 0; t < cnt; ++t) {
         const unsigned s = CLAMP ? min((unsigned)a.sym[s0 + t], dmax) : (unsigned)a.sym[s0 + t];
         unsigned c, L;
-        if (packed) code_of<true, TAB>(tab, s, c, L);
-        else code_of<false, TAB>(tab, s, c, L);
+        code_of<TAB>(tab, s, c, L);
         acc = (acc << L) | c;
         nb += L;
         if (nb >= 32u) {

@@ -197,6 +197,67 @@ def test_huffman_bit_exact(bm, scale, esc, chunk, dict_size):
     np.testing.assert_array_equal(back, sym)
 
 
+@pytest.mark.parametrize("dict_size,chunk", [(64, 2048), (65536, 1024)])
+def test_huffman_codes_up_to_32_bits(bm, dict_size, chunk):
+    """Fibonacci counts (1, 1, 2, 3, 5, ...) over 33 symbols make the most
+    skewed Huffman tree: codes of 1 to 32 bits.  The encoder keeps a code of
+    at most 26 bits and its length in one table word; the longer ones (the
+    seven rarest symbols here, a 32-bit code among them) come from the full
+    code table.  A 64-symbol dictionary takes the shared-memory table, the
+    16-bit one the global table; 9,227,464 symbols in shuffled order end in a
+    ragged chunk."""
+    fib = [1, 1]
+    while len(fib) < 33:
+        fib.append(fib[-1] + fib[-2])
+    rng = np.random.default_rng(5)
+    present = rng.choice(np.arange(dict_size), size=33, replace=False)
+    sym = np.repeat(present, fib).astype(np.uint16)
+    rng.shuffle(sym)
+    f = np.bincount(sym, minlength=dict_size)
+    L = oracle.huffman_lengths(f)
+    assert L.max() == 32 and (L > 26).sum() == 7
+    so, mo = oracle.huffman_encode(sym, dict_size, chunk)
+    t = torch.from_numpy(sym.view(np.int16)).to(DEV)
+    sg, mg = bm.huffman_encode(t, dict_size, chunk)
+    assert mg == mo
+    np.testing.assert_array_equal(sg.cpu().numpy(), so)
+    back = bm.huffman_decode(sg, mg, sym.size, dict_size, chunk).cpu().numpy().view(np.uint16)
+    np.testing.assert_array_equal(back, sym)
+
+
+def _table_mode(codes, radius=32768):
+    """The encoder's table for a call's codes, by the rule its codebook
+    applies: 0 when the present symbols span fewer than 8192, 3 fewer than
+    57344, 1 when the 57344 symbols centred on code 0 (and the escape symbol)
+    hold at least half of them and escapes fewer than a fifth, else 2."""
+    sym = np.where(np.abs(codes) < radius, codes + radius, 0)
+    f = np.bincount(sym.astype(np.int64), minlength=2 * radius)
+    present = np.flatnonzero(f)
+    span = present.max() - present.min()
+    lo = radius - 57344 // 2
+    win = f[lo:lo + 57344].sum() + f[0]
+    if span < 8192:
+        return 0
+    if span < 57344:
+        return 3
+    return 1 if 2 * win >= f.sum() and 5 * f[0] < f.sum() else 2
+
+
+@pytest.mark.parametrize("tol,mode", [(1e-2, 0), (1e-3, 3), (1e-4, 1), (1e-5, 2)])
+def test_encoder_table_modes(bm, tol, mode):
+    """One compress call per table of the encoder: the same GRF at four
+    tolerances spans about 2,100 symbols (the small shared-memory window),
+    21,000 (the large window), the whole dictionary with 1 % of the symbols
+    outside the large window (looked up in the global table) and 2 % escapes,
+    and the whole dictionary with two thirds escapes (the global table)."""
+    shape = (40, 44, 48)
+    u = fields.power_law_grf(shape, seed=7, dtype=torch.float32).numpy()
+    _, codes = oracle.compress(u, tol, rel=True, B=9, K=2, M=2, want_codes=True)
+    assert _table_mode(codes) == mode
+    sg = bm.compress(torch.from_numpy(u).to(DEV), tol, block=9, levels=2, global_levels=2).cpu().numpy()
+    check_stream_parity(bm, u, sg, tol, "rel", 9, 2, 2, label=f"encoder_mode{mode}")
+
+
 def test_huffman_single_symbol(bm):
     sym = np.full(5000, 77, dtype=np.uint16)
     so, mo = oracle.huffman_encode(sym, 128, 256)
