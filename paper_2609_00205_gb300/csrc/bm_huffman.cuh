@@ -1975,7 +1975,26 @@ __global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) encode_fused_kernel(Fu
     }
     // outlier codes of the slice, in stream order
     unsigned long long epos = pe + (xe - nesc);
-    if (a.esc && nesc) {
+    if (a.esc && warp_vec && (per & 31) == 0 && tot_esc * 8u >= (unsigned)a.chunk) {
+      // many escapes: the warp copies them together, 32 consecutive symbols of
+      // one lane's slice at a time (that lane's escape mask, broadcast), so
+      // the loads of the escaped codes and the stores of the outliers are
+      // coalesced rather than one line per lane
+      unsigned long long ep = pe;
+      for (int l = 0; l < 32; ++l) {
+        const unsigned long long ml = __shfl_sync(0xffffffffu, emask, l);
+        const unsigned long long sl = cb + (unsigned long long)l * per;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const unsigned m = (unsigned)(ml >> (32 * h));
+          if (32 * h < per && m) {
+            const unsigned r = __popc(m & ((1u << lane) - 1u));
+            if (((m >> lane) & 1u) && ep + r < n_out) ocode[ep + r] = __ldg(a.esc + sl + 32 * h + lane);
+            ep += __popc(m);
+          }
+        }
+      }
+    } else if (a.esc && nesc) {
       if (warp_vec) {
         unsigned long long m = emask;
         while (m) {
