@@ -267,6 +267,42 @@ __device__ __forceinline__ int warp_upper_bound_u32(const unsigned* a, int lo, i
   const unsigned m = __ballot_sync(0xffffffffu, lane < hi - lo && a[lo + lane] > v);
   return m ? lo + __ffs(m) - 1 : hi;
 }
+// upper_bound over the sorted a[lo, hi) by the 32 lanes of a warp, with
+// samples smp[k] = a[64 k + 63] in shared memory for the blocks k < nfull (a
+// last block shorter than 64 elements, if any, follows them unsampled): a
+// 32-ary search of the samples finds the block that holds the bound, then one
+// coalesced read of that block (the search's only global round trip).
+__device__ __forceinline__ int warp_upper_bound_sampled(const unsigned* a, const unsigned* smp, int lo, int hi,
+                                                        int nfull, unsigned v) {
+  const int lane = threadIdx.x & 31;
+  if (lo >= hi) return hi;
+  int klo = lo >> 6, khi = nfull;  // the first block in [klo, khi) whose sample exceeds v, else khi
+  while (khi - klo > 32) {
+    const int step = (khi - klo + 31) / 32;
+    const int p = min(klo + (lane + 1) * step, khi) - 1;
+    const unsigned m = __ballot_sync(0xffffffffu, smp[p] > v);
+    if (m == 0u) {
+      klo = khi;
+      break;
+    }
+    const int f = __ffs(m) - 1;
+    const int nlo = klo + f * step;
+    khi = min(nlo + step, khi);
+    klo = nlo;
+  }
+  if (klo < khi) {
+    const unsigned m = __ballot_sync(0xffffffffu, lane < khi - klo && smp[klo + lane] > v);
+    klo = m ? klo + __ffs(m) - 1 : khi;
+  }
+  const int b0 = max(lo, klo << 6), b1 = min(hi, (klo << 6) + 64);
+  if (b0 >= b1) return hi;
+  const int i0 = b0 + lane, i1 = b0 + 32 + lane;
+  const unsigned x0 = i0 < b1 ? a[i0] : 0u, x1 = i1 < b1 ? a[i1] : 0u;
+  const unsigned m0 = __ballot_sync(0xffffffffu, i0 < b1 && x0 > v);
+  if (m0) return b0 + __ffs(m0) - 1;
+  const unsigned m1 = __ballot_sync(0xffffffffu, i1 < b1 && x1 > v);
+  return m1 ? b0 + 32 + __ffs(m1) - 1 : hi;
+}
 // Merge path split by the 32 lanes of a warp: the number of A elements among
 // the first d of merge(A[0..na), B[0..nb)) when A's element goes first on
 // equal weight, i.e. the first i in [max(0, d - nb), min(d, na)] with
@@ -449,6 +485,27 @@ struct CbSmem {
 static_assert(sizeof(CbSmem) <= 227 * 1024, "codebook shared memory");
 static_assert(256 * 32 >= kCbSmemSyms, "run offsets over the sort counts");
 
+// Shared memory of the global-scratch variant's rounds, in the arrays only
+// the shared-memory variant uses: the samples of its two queues (samp, in
+// parent), and per tile of merged ranks the new parent of each leaf and
+// internal node taken (pa, pb: tile-relative pair index, in depth and sa)
+// and the weights of the new nodes (wk, in csym), so that the global arrays
+// are written with coalesced stores.
+struct CbTileScratch {
+  unsigned* samp;
+  uint16_t* pa;
+  uint16_t* pb;
+  unsigned* wk;
+};
+static_assert(sizeof(CbSmem::parent) >= 2 * (kMaxDict / 64) * sizeof(unsigned), "queue samples");
+static_assert(sizeof(CbSmem::depth) >= kCbSmemSyms * sizeof(uint16_t) && sizeof(CbSmem::sa) >= kCbSmemSyms * 2 &&
+                  sizeof(CbSmem::csym) >= kCbSmemSyms / 2 * sizeof(unsigned),
+              "tile scratch");
+__device__ __forceinline__ CbTileScratch cb_tile_scratch(CbSmem& S) {
+  return {reinterpret_cast<unsigned*>(S.parent), reinterpret_cast<uint16_t*>(S.depth), S.sa,
+          reinterpret_cast<unsigned*>(S.csym)};
+}
+
 // Global scratch of the large variant: n <= kMaxDict present symbols, 32-bit ids.
 constexpr int kPreCtas = 64;  // CTAs of cb_presort_kernel
 // Counts of the multi-CTA presort, after the arrays in the global scratch.
@@ -546,10 +603,32 @@ __device__ __forceinline__ unsigned merge_pairs(const unsigned* A, int na, const
   }
   return leaves;
 }
+// The same pairs within one tile, their results in shared memory: pa[i] /
+// pb[j], the tile-relative index of the new parent of A[i] / B[j]; wk[k], the
+// weight of the tile's k-th new node.
+__device__ __forceinline__ unsigned merge_pairs_tile(const unsigned* A, int na, const unsigned* B, int nb, int d0,
+                                                     int d1, int i, uint16_t* pa, uint16_t* pb, unsigned* wk) {
+  unsigned leaves = 0;
+  int j = d0 - i;
+  for (int d = d0; d < d1; d += 2) {
+    unsigned w[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      if (i < na && (j >= nb || A[i] <= B[j])) { w[t] = A[i]; pa[i] = (uint16_t)(d >> 1); ++i; ++leaves; }
+      else { w[t] = B[j]; pb[j] = (uint16_t)(d >> 1); ++j; }
+    }
+    wk[d >> 1] = w[0] + w[1];
+  }
+  return leaves;
+}
 
+// stage (global-scratch variant): shared memory for the tiles of the two
+// queues; ts: its other shared memory, the samples of both queues (which turn
+// each bound search into one global round trip) and the tile's results.
 template <typename IdT>
 __device__ void codebook_lengths(const CodebookArgs& a, CbArrays<IdT> V, int n, unsigned* scan_tmp,
-                                 unsigned* stage, int pre_passes = -1) {
+                                 unsigned* stage, int pre_passes = -1, const CbTileScratch* ts = nullptr) {
+  unsigned* const samp = ts ? ts->samp : nullptr;
   __shared__ unsigned s_lp, s_qp, s_qe, s_pl, s_pq, s_leaves, s_rounds, s_maxd, s_maxk;
   __shared__ int s_split;
   if (n <= 1) {
@@ -608,6 +687,11 @@ __device__ void codebook_lengths(const CodebookArgs& a, CbArrays<IdT> V, int n, 
     }  // !presorted
     const unsigned* lw = V.ka;
     const uint16_t* ls = V.sa;
+    unsigned* isamp = samp ? samp + kMaxDict / 64 : nullptr;
+    if (samp) {  // the leaves' samples (the last block's is the last leaf), once the sort's copies are in
+      __syncthreads();
+      for (int k = threadIdx.x; k < (n + 63) >> 6; k += blockDim.x) samp[k] = lw[min(64 * k + 63, n - 1)];
+    }
     if (threadIdx.x == 0) { s_lp = 0; s_qp = 0; s_qe = 0; s_rounds = 0; s_leaves = 0; }
     __syncthreads();
     // 2. parallel rounds of the two-queue construction.  Warp 0 folds the
@@ -630,17 +714,18 @@ __device__ void codebook_lengths(const CodebookArgs& a, CbArrays<IdT> V, int n, 
         unsigned lp = s_lp, qp = s_qp;
         const unsigned qe = s_qe;
         if (qe < (unsigned)(n - 1)) {
-          unsigned w[2];
-          for (int t = 0; t < 2; ++t) {
-            if (lp < (unsigned)n && (qp >= qe || lw[lp] <= V.iw[qp])) w[t] = lw[lp++];
-            else w[t] = V.iw[qp++];
-          }
-          const unsigned X = w[0] + w[1];
+          // the two smallest remaining weights: the first two of each queue,
+          // read together (a weight is below 2^31, so ~0u marks an empty slot)
+          const unsigned c0 = lp < (unsigned)n ? lw[lp] : ~0u, c1 = lp + 1 < (unsigned)n ? lw[lp + 1] : ~0u;
+          const unsigned d0 = qp < qe ? V.iw[qp] : ~0u, d1 = qp + 1 < qe ? V.iw[qp + 1] : ~0u;
+          const unsigned X = c0 <= d0 ? c0 + min(c1, d0) : d0 + min(c0, d1);
           if (threadIdx.x < 32) {
-            const int pl = warp_upper_bound_u32(lw, (int)s_lp, n, X) - (int)s_lp;
+            const int pl = (samp ? warp_upper_bound_sampled(lw, samp, (int)lp, n, (n + 63) >> 6, X)
+                                 : warp_upper_bound_u32(lw, (int)lp, n, X)) - (int)lp;
             if (threadIdx.x == 0) s_pl = (unsigned)pl;
           } else {
-            const int pq = warp_upper_bound_u32(V.iw, (int)s_qp, (int)qe, X) - (int)s_qp;
+            const int pq = (samp ? warp_upper_bound_sampled(V.iw, isamp, (int)qp, (int)qe, (int)(qe >> 6), X)
+                                 : warp_upper_bound_u32(V.iw, (int)qp, (int)qe, X)) - (int)qp;
             if (threadIdx.x == 32) s_pq = (unsigned)pq;
           }
         }
@@ -674,14 +759,38 @@ __device__ void codebook_lengths(const CodebookArgs& a, CbArrays<IdT> V, int n, 
         int ia = 0;
         for (int tb = 0; tb < T; tb += kCbTile) {
           const int te = min(T, tb + kCbTile);
-          if (threadIdx.x < 32) {
+          if (te == pl + pq) {  // every node of both queues
+            if (threadIdx.x == 0) s_split = pl;
+          } else if (te == T) {  // all but the last of the merged order (A first on equal weight)
+            if (threadIdx.x == 0) s_split = pq == 0 ? pl - 1 : pl == 0 ? 0 : A[pl - 1] <= Bq[pq - 1] ? pl : pl - 1;
+          } else if (threadIdx.x < 32) {
             const int ib = warp_merge_split(A, pl, Bq, pq, te);
             if (threadIdx.x == 0) s_split = ib;
           }
           __syncthreads();
           const int ib = s_split, ja = tb - ia, jb = te - ib;
-          for (int k = threadIdx.x; k < ib - ia; k += blockDim.x) sA[k] = A[ia + k];
-          for (int k = threadIdx.x; k < jb - ja; k += blockDim.x) sB[k] = Bq[ja + k];
+          for (int k0 = threadIdx.x; k0 < ib - ia; k0 += 8 * blockDim.x) {  // eight loads in flight
+            unsigned x[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+              const int k = k0 + t * (int)blockDim.x;
+              x[t] = k < ib - ia ? A[ia + k] : 0u;
+            }
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+              if (k0 + t * (int)blockDim.x < ib - ia) sA[k0 + t * blockDim.x] = x[t];
+          }
+          for (int k0 = threadIdx.x; k0 < jb - ja; k0 += 8 * blockDim.x) {
+            unsigned x[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+              const int k = k0 + t * (int)blockDim.x;
+              x[t] = k < jb - ja ? Bq[ja + k] : 0u;
+            }
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+              if (k0 + t * (int)blockDim.x < jb - ja) sB[k0 + t * blockDim.x] = x[t];
+          }
           __syncthreads();
           const int tl = te - tb, na = ib - ia, nb = jb - ja;
           const int seg = 2 * ((tl / 2 + (int)blockDim.x - 1) / (int)blockDim.x);
@@ -692,7 +801,17 @@ __device__ void codebook_lengths(const CodebookArgs& a, CbArrays<IdT> V, int n, 
               const int mid = (lo + hi) >> 1;
               if (sA[mid] <= sB[d0 - 1 - mid]) lo = mid + 1; else hi = mid;
             }
-            leaves += merge_pairs<IdT>(sA, na, sB, nb, d0, d1, lo, lp + ia, n + qp + ja, qe, tb, V.iw, V.parent, n);
+            leaves += merge_pairs_tile(sA, na, sB, nb, d0, d1, lo, ts->pa, ts->pb, ts->wk);
+          }
+          __syncthreads();
+          // the tile's parents and new weights, coalesced
+          const int kb0 = qe + (tb >> 1);
+          for (int k = threadIdx.x; k < na; k += blockDim.x) V.parent[lp + ia + k] = (IdT)(n + kb0 + ts->pa[k]);
+          for (int k = threadIdx.x; k < nb; k += blockDim.x) V.parent[n + qp + ja + k] = (IdT)(n + kb0 + ts->pb[k]);
+          for (int k = threadIdx.x; k < (tl >> 1); k += blockDim.x) {
+            const unsigned w = ts->wk[k];
+            V.iw[kb0 + k] = w;
+            if (((kb0 + k) & 63) == 63) isamp[(kb0 + k) >> 6] = w;
           }
           ia = ib;
           __syncthreads();
@@ -1366,7 +1485,8 @@ __device__ void codebook_block(const CodebookArgs& a) {
       codebook_emit<uint16_t>(a, V, n, S.scan_tmp, &S.ct);
     } else {  // the tree here; cb_emit_kernel emits the codes on many CTAs afterwards
       const CbArrays<unsigned> V = cb_big(a.big, S.wcnt);
-      codebook_lengths<unsigned>(a, V, n, S.scan_tmp, S.ka, passes);
+      const CbTileScratch ts = cb_tile_scratch(S);
+      codebook_lengths<unsigned>(a, V, n, S.scan_tmp, S.ka, passes, &ts);
     }
     return;
   }
@@ -1433,7 +1553,9 @@ __device__ void codebook_block(const CodebookArgs& a) {
     codebook_emit<uint16_t>(a, V, n, S.scan_tmp, &S.ct);
   } else {
     const CbArrays<unsigned> V = cb_big(a.big, S.wcnt);
-    codebook_lengths<unsigned>(a, V, n, S.scan_tmp, S.ka);  // S.ka and S.iw (adjacent) stage the tiles
+    // S.ka and S.iw (adjacent) stage the tiles
+    const CbTileScratch ts = cb_tile_scratch(S);
+    codebook_lengths<unsigned>(a, V, n, S.scan_tmp, S.ka, -1, &ts);
     codebook_emit<unsigned>(a, V, n, S.scan_tmp, &S.ct);
   }
 }

@@ -243,17 +243,18 @@ def _table_mode(codes, radius=32768):
     return 1 if 2 * win >= f.sum() and 5 * f[0] < f.sum() else 2
 
 
-@pytest.mark.parametrize("tol,mode", [(1e-2, 0), (1e-3, 3), (1e-4, 1), (1e-5, 2)])
+@pytest.mark.parametrize("tol,mode", [(1e-2, 0), (1e-3, 3), (1e-4, 1), (3e-5, 2)])
 def test_encoder_table_modes(bm, tol, mode):
-    """One compress call per table of the encoder: the same GRF at four
-    tolerances spans about 2,100 symbols (the small shared-memory window),
-    21,000 (the large window), the whole dictionary with 1 % of the symbols
-    outside the large window (looked up in the global table) and 2 % escapes,
-    and the whole dictionary with two thirds escapes (the global table)."""
-    shape = (40, 44, 48)
+    """One compress call per table of the encoder: the same 64^3 GRF at four
+    tolerances spans about 2,200 symbols (the small shared-memory window),
+    22,000 (the large window), the whole dictionary with a few symbols outside
+    the large window (looked up in the global table) and 1 % escapes, and the
+    whole dictionary with 27 % escapes (the global table); every stream is
+    Huffman-coded, none a raw copy."""
+    shape = (64, 64, 64)
     u = fields.power_law_grf(shape, seed=7, dtype=torch.float32).numpy()
-    _, codes = oracle.compress(u, tol, rel=True, B=9, K=2, M=2, want_codes=True)
-    assert _table_mode(codes) == mode
+    so, codes = oracle.compress(u, tol, rel=True, B=9, K=2, M=2, want_codes=True)
+    assert _table_mode(codes) == mode and not oracle.stream_header(so)["raw"]
     sg = bm.compress(torch.from_numpy(u).to(DEV), tol, block=9, levels=2, global_levels=2).cpu().numpy()
     check_stream_parity(bm, u, sg, tol, "rel", 9, 2, 2, label=f"encoder_mode{mode}")
 
