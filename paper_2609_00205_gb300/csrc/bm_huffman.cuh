@@ -11,6 +11,8 @@
 // weigh >= X and lose ties), so all those pairs are formed at once.
 #pragma once
 
+#include <stddef.h>
+
 #include <cooperative_groups.h>
 
 #include "bm_common.cuh"
@@ -490,20 +492,24 @@ static_assert(256 * 32 >= kCbSmemSyms, "run offsets over the sort counts");
 // parent), and per tile of merged ranks the new parent of each leaf and
 // internal node taken (pa, pb: tile-relative pair index, in depth and sa)
 // and the weights of the new nodes (wk, in csym), so that the global arrays
-// are written with coalesced stores.
+// are written with coalesced stores; after the rounds, the leaves' lengths
+// (lens, over all of these arrays), copied out in compact-index order.
 struct CbTileScratch {
   unsigned* samp;
   uint16_t* pa;
   uint16_t* pb;
   unsigned* wk;
+  uint8_t* lens;
 };
 static_assert(sizeof(CbSmem::parent) >= 2 * (kMaxDict / 64) * sizeof(unsigned), "queue samples");
 static_assert(sizeof(CbSmem::depth) >= kCbSmemSyms * sizeof(uint16_t) && sizeof(CbSmem::sa) >= kCbSmemSyms * 2 &&
                   sizeof(CbSmem::csym) >= kCbSmemSyms / 2 * sizeof(unsigned),
               "tile scratch");
+static_assert(offsetof(CbSmem, clen) + sizeof(CbSmem::clen) - offsetof(CbSmem, parent) >= kMaxDict,
+              "a length byte per leaf from parent to clen");
 __device__ __forceinline__ CbTileScratch cb_tile_scratch(CbSmem& S) {
   return {reinterpret_cast<unsigned*>(S.parent), reinterpret_cast<uint16_t*>(S.depth), S.sa,
-          reinterpret_cast<unsigned*>(S.csym)};
+          reinterpret_cast<unsigned*>(S.csym), reinterpret_cast<uint8_t*>(S.parent)};
 }
 
 // Global scratch of the large variant: n <= kMaxDict present symbols, 32-bit ids.
@@ -577,6 +583,7 @@ __device__ __forceinline__ CbPre* cb_pre(unsigned char* g) {
 // global-scratch variant.
 constexpr int kCbTile = 8192;
 static_assert(kCbTile == kCbSmemSyms, "a tile of each queue fills ka, then iw (adjacent)");
+static_assert(2 * kCbTile * sizeof(unsigned) >= kMaxDict, "the staging holds a depth byte per internal node");
 
 // Pairs of the ranks [d0, d1) of merge(A[0..na), B[0..nb)) (A first on equal
 // weight), d0 even, whose first i0 = split(d0) ranks came from A: appends
@@ -821,15 +828,26 @@ __device__ void codebook_lengths(const CodebookArgs& a, CbArrays<IdT> V, int n, 
       np_prev = npairs;
       __syncthreads();
     }
-    // 3. depths, rounds in reverse (a parent is always created in a later round)
+    // 3. depths, rounds in reverse (a parent is always created in a later
+    // round).  The global-scratch variant keeps the internal nodes' depths in
+    // the tile staging's shared memory (one byte each: a depth stays below 64
+    // for counts below 2^32), indexed by creation order.
     const int root = 2 * n - 2;
-    if (threadIdx.x == 0) { V.depth[root] = 0; s_maxd = 0; }
+    uint8_t* const dsh = stage ? reinterpret_cast<uint8_t*>(stage) : nullptr;
+    if (threadIdx.x == 0) {
+      if (dsh) dsh[n - 2] = 0;
+      else V.depth[root] = 0;
+      s_maxd = 0;
+    }
     __syncthreads();
     for (int r = (int)s_rounds - 1; r >= 0; --r) {
       const int jb = r ? (int)V.round_end[r - 1] : 0, je = (int)V.round_end[r];
       for (int j = jb + threadIdx.x; j < je; j += blockDim.x) {
         const int v = n + j;
-        if (v != root) V.depth[v] = V.depth[V.parent[v]] + 1;
+        if (v != root) {
+          if (dsh) dsh[j] = (uint8_t)(dsh[(int)V.parent[v] - n] + 1);
+          else V.depth[v] = V.depth[V.parent[v]] + 1;
+        }
       }
       __syncthreads();
     }
@@ -843,16 +861,24 @@ __device__ void codebook_lengths(const CodebookArgs& a, CbArrays<IdT> V, int n, 
         li[t] = i < n ? (unsigned)ls[i] : 0u;
       }
 #pragma unroll
-      for (int t = 0; t < 8; ++t) dd[t] = i0 + t * (int)blockDim.x < n ? (unsigned)V.depth[pa[t]] + 1u : 0u;
+      for (int t = 0; t < 8; ++t)
+        dd[t] = i0 + t * (int)blockDim.x < n ? (unsigned)(dsh ? dsh[pa[t] - (unsigned)n] : V.depth[pa[t]]) + 1u : 0u;
 #pragma unroll
       for (int t = 0; t < 8; ++t)
         if (i0 + t * (int)blockDim.x < n) {
-          V.clen[li[t]] = (uint8_t)min(dd[t], 255u);
+          // the global-scratch variant gathers the lengths in shared memory
+          // (scattered byte stores), then copies them out in order
+          if (ts) ts->lens[li[t]] = (uint8_t)min(dd[t], 255u);
+          else V.clen[li[t]] = (uint8_t)min(dd[t], 255u);
           md = max(md, dd[t]);
         }
     }
     if (md) atomicMax(&s_maxd, md);
     __syncthreads();
+    if (ts) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) V.clen[i] = ts->lens[i];
+      __syncthreads();
+    }
     if (s_maxd <= (unsigned)kMaxLen) break;
     __syncthreads();
   }
