@@ -259,6 +259,21 @@ def test_encoder_table_modes(bm, tol, mode):
     check_stream_parity(bm, u, sg, tol, "rel", 9, 2, 2, label=f"encoder_mode{mode}")
 
 
+def test_huffman_heavy_tails(bm):
+    """Two symbols far out in the tails of a 65,536-symbol dictionary (outside
+    the wide histogram's 49,152 shared-memory bins, so counted with global
+    atomics) with 6 M occurrences each beside a Laplace centre: counts, code
+    lengths and the stream must be the oracle's byte for byte."""
+    rng = np.random.default_rng(23)
+    centre = fields.laplace_symbols(1_200_003, 32768, 40.0, seed=29, escape_rate=0.0)
+    sym = np.concatenate([centre, np.full(6_000_000, 7, np.uint16), np.full(6_000_000, 61_000, np.uint16)])
+    rng.shuffle(sym)
+    so, mo = oracle.huffman_encode(sym, 65536, 2048)
+    sg, mg = bm.huffman_encode(torch.from_numpy(sym.view(np.int16)).to(DEV), 65536, 2048)
+    assert mg == mo
+    np.testing.assert_array_equal(sg.cpu().numpy(), so)
+
+
 def test_huffman_single_symbol(bm):
     sym = np.full(5000, 77, dtype=np.uint16)
     so, mo = oracle.huffman_encode(sym, 128, 256)
