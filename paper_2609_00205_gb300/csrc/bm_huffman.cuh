@@ -821,7 +821,7 @@ __device__ void codebook_lengths(const CodebookArgs& a, CbArrays<IdT> V, int n, 
             if (((kb0 + k) & 63) == 63) isamp[(kb0 + k) >> 6] = w;
           }
           ia = ib;
-          if (te < T) __syncthreads();  // after the last tile, the round's closing barrier below
+          __syncthreads();
         }
       }
       if (leaves) atomicAdd(&s_leaves, leaves);
